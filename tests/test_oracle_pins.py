@@ -1,0 +1,360 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks an oracle function against something other than itself: a
+closed form, a library special function, brute-force adaptive quadrature, an
+identity, or an exact (manufactured) solution of the continuous problem.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import special
+from scipy.integrate import quad, quad_vec
+
+from oracle import kernels as KR
+from oracle.alpert_gen import solve_rule
+from oracle.assemble import (ModalSystem, Quadrature, alpert_table, block_system, diagonal,
+                             fresnel, reference_field, rhs_modes, solve_ntd)
+from oracle.problem import Geometry, Params, graded, pml_integral, pml_sigma
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _take(d, i):
+    return {k: (v[i] if isinstance(v, np.ndarray) else v) for k, v in d.items()}
+
+
+# ---------------------------------------------------------------------------
+# Alpert table (Sec. 4.1, order 10, Sec. 5)
+# ---------------------------------------------------------------------------
+def test_alpert_rule_order():
+    """Two-sided corrected trapezoid on int_{-1}^{1} log|t| g(t) dt, g smooth and
+    vanishing to high order at +-1: error falls at the rule's order (> 2^10 per
+    halving; order 10 plus the decay of the smooth remainder)."""
+    x, w, a = alpert_table()
+    g = lambda t: np.cos(10 * t + 0.2) * (1 - t * t) ** 12
+    exact = quad(lambda t: np.log(t) * (g(t) + g(-t)), 0, 1, epsabs=1e-16, epsrel=1e-15, limit=500)[0]
+    errs = []
+    for n in (16, 32):
+        h = 1.0 / n
+        i = np.arange(-n + 1, n)
+        i = i[np.abs(i) >= a]
+        t = i * h
+        s = h * np.sum(np.log(np.abs(t)) * g(t))
+        tc = x * h
+        s += h * np.sum(w * np.log(tc) * (g(tc) + g(-tc)))
+        errs.append(abs(s - exact))
+    assert errs[1] < 1e-10
+    assert errs[0] / errs[1] > 2.0 ** 10
+
+
+def test_alpert_table_matches_regeneration():
+    """The stored table is the root of the moment equations (fresh low-j rule as
+    a cross-check of the generator; the j=10 table re-solved at 30 digits)."""
+    x, w, a = alpert_table()
+    rule = solve_rule(10, 10, dps=40)
+    assert np.allclose(x, [float(r[0]) for r in rule], rtol=1e-15, atol=0)
+    assert np.allclose(w, [float(r[1]) for r in rule], rtol=1e-15, atol=0)
+    assert np.all(w > 0) and np.all((x > 0) & (x < a))
+
+
+# ---------------------------------------------------------------------------
+# graded grid, Eq. (sxi); PML profile, Eq. (sgm1)
+# ---------------------------------------------------------------------------
+def test_graded_map_endpoints_and_flatness():
+    p = 6
+    s, ds = graded(np.array([0.0, 0.5, 1.0]), p)
+    assert np.allclose(s, [0.0, 0.5, 1.0], atol=1e-15)
+    # derivatives vanish to order p-1 at the ends: s(u) ~ c u^p
+    u = np.array([1e-3, 2e-3])
+    su, _ = graded(u, p)
+    assert abs(math.log(su[1] / su[0], 2) - p) < 0.02
+    uu = np.linspace(0.02, 0.98, 2001)
+    assert np.all(np.diff(graded(uu, p)[0]) > 0)
+    # ds/du against a central difference
+    h = 1e-6
+    for u0 in (0.1, 0.37, 0.8):
+        fd = (graded(np.array([u0 + h]), p)[0] - graded(np.array([u0 - h]), p)[0]) / (2 * h)
+        assert abs(fd[0] - graded(np.array([u0]), p)[1][0]) < 1e-7
+
+
+def test_pml_profile_and_integral():
+    P = Params(k1=1.0, k2=1.0, a1=2.5, T=1.0, S=3.0)
+    assert pml_sigma(np.array([2.5]), P)[0] == 0.0
+    assert abs(pml_sigma(np.array([3.5]), P)[0] - 3.0) < 1e-14
+    # smooth start: sigma(a1 + d) ~ d^p
+    d = np.array([1e-2, 2e-2])
+    sg = pml_sigma(2.5 + d, P)
+    assert abs(math.log(sg[1] / sg[0], 2) - P.p) < 0.05
+    for r in (2.7, 3.1, 3.5):
+        ref = quad(lambda t: pml_sigma(np.array([t]), P)[0], 2.5, r, epsabs=1e-15, epsrel=1e-14)[0]
+        assert abs(pml_integral(np.array([r]), P)[0] - ref) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Taylor substitution (Sec. 4.3, Eq. (ch1))
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("L", [3, 5, 7])
+def test_taylor_polynomials(L):
+    a, b = KR.taylor_coeffs(L)
+    q0 = 10.0 ** (-9.0 / (L + 1))          # keeps |d| well above rounding
+    qs = np.array([q0, 2 * q0]) * (1 + 0.5j)
+    d1 = KR._poly(a, qs) - np.cos(qs) * np.exp(-1j * qs)
+    d3 = KR._poly(b, qs) - (np.cos(qs) + qs * np.sin(qs)) * np.exp(-1j * qs)
+    for d in (d1, d3):
+        order = math.log(abs(d[1]) / abs(d[0]), 2)
+        assert abs(order - (L + 1)) < 0.2
+
+
+# ---------------------------------------------------------------------------
+# modal kernels vs brute-force adaptive quadrature of the 3D kernel
+# ---------------------------------------------------------------------------
+def _adaptive_modes(pg, omega, nh):
+    n_p = pg["d2"].shape[0]
+
+    def f(psi):
+        s, k = KR.kernel_samples(pg, omega, np.array([psi]))
+        c = 2 * np.cos(np.arange(nh) * psi)
+        return np.concatenate([(s[:, 0:1] * c[None, :]).ravel(), (k[:, 0:1] * c[None, :]).ravel()])
+
+    v, _ = quad_vec(f, 0, np.pi, epsabs=1e-16, epsrel=1e-13, limit=20000,
+                    points=list(np.geomspace(1e-9, 0.5, 40)))
+    return v[: n_p * nh].reshape(n_p, nh), v[n_p * nh:].reshape(n_p, nh)
+
+
+def test_modal_kernels_vs_quadrature_physical():
+    """Far (FFT) and close (split) pairs on the bump and the flat part."""
+    P = Params(k1=2 * np.pi, k2=3 * np.pi, N=128, M=64)
+    G = Geometry(P)
+    pairs = [(10, 30), (10, 12), (50, 61), (40, 52), (5, 70), (20, 31)]
+    li = np.array([p[0] for p in pairs])
+    mi = np.array([p[1] for p in pairs])
+    pg = KR.pair_geometry(_take(G.nodes, li), _take(G.nodes, mi), P)
+    near = KR.near_mask(pg, P)
+    assert near.any() and (~near).any()
+    S, K = KR.modal_kernels(pg, P.k1, P)
+    Se, Ke = _adaptive_modes(pg, P.k1, P.M // 2)
+    for i in range(len(pairs)):
+        assert np.abs(S[i] - Se[i]).max() <= 1e-12 * np.abs(Se[i]).max()
+        if np.abs(Ke[i]).max() > 0:
+            assert np.abs(K[i] - Ke[i]).max() <= 1e-11 * np.abs(Ke[i]).max() + 1e-15
+
+
+def test_modal_kernels_vs_quadrature_pml():
+    """PML pairs (complex stretched distance) with resolved M: split and FFT."""
+    P = Params(k1=2 * np.pi, k2=3 * np.pi, N=128, M=512)
+    G = Geometry(P)
+    pairs = [(100, 112), (120, 127), (90, 126), (80, 100)]
+    li = np.array([p[0] for p in pairs])
+    mi = np.array([p[1] for p in pairs])
+    pg = KR.pair_geometry(_take(G.nodes, li), _take(G.nodes, mi), P)
+    near = KR.near_mask(pg, P)
+    S, K = KR.modal_kernels(pg, P.k1, P)
+    Se, Ke = _adaptive_modes(pg, P.k1, 24)
+    for i in range(len(pairs)):
+        tol = 1e-7 if near[i] else 1e-12
+        assert np.abs(S[i, :24] - Se[i]).max() <= tol * np.abs(Se[i]).max(), (pairs[i], near[i])
+
+
+def test_laplace_modes_vs_legendre_q():
+    """Z^_m = Q_{m-1/2}(chi) / (2 pi sqrt(rho~ rho~')), chi = 1 + d^2/(2 rho~ rho~')
+    (toroidal expansion of 1/|r - r'|), for real and complex (PML) chi."""
+    mp = pytest.importorskip("mpmath")
+    P = Params(k1=1.0, k2=1.0, N=128, M=64)
+    G = Geometry(P)
+    pairs = [(10, 12), (50, 61), (100, 112), (90, 126)]
+    li = np.array([p[0] for p in pairs])
+    mi = np.array([p[1] for p in pairs])
+    pg = KR.pair_geometry(_take(G.nodes, li), _take(G.nodes, mi), P)
+    Zm, _ = KR.laplace_modes(pg, 8)
+    for i in range(len(pairs)):
+        rr = complex(pg["rr"][i])
+        chi = 1 + complex(pg["d2"][i]) / (2 * rr)
+        for m in (0, 1, 4, 8):
+            q = complex(mp.legenq(m - 0.5, 0, chi, type=3))
+            ref = q / (2 * np.pi * np.sqrt(rr))
+            assert abs(Zm[i, m] - ref) <= 1e-11 * abs(ref), (pairs[i], m)
+
+
+def test_laplace_mode0_vs_elliptic():
+    """Mode 0 of the ring kernel: Z^_0 = K(k) / (pi sqrt((rho+rho')^2 + dz^2))."""
+    P = Params(k1=1.0, k2=1.0, N=128, M=64)
+    G = Geometry(P)
+    li, mi = np.array([3, 20, 60]), np.array([40, 22, 70])
+    pg = KR.pair_geometry(_take(G.nodes, li), _take(G.nodes, mi), P)
+    Zm, _ = KR.laplace_modes(pg, 2)
+    r1, r2 = G.nodes["rho"][li], G.nodes["rho"][mi]
+    dz = G.nodes["z"][li] - G.nodes["z"][mi]
+    den = (r1 + r2) ** 2 + dz ** 2
+    ref = special.ellipk(4 * r1 * r2 / den) / (np.pi * np.sqrt(den))
+    assert np.allclose(Zm[:, 0].real, ref, rtol=1e-12)
+
+
+def test_modal_reciprocity():
+    """G~(r, r') = G~(r', r) (complex symmetric), so S^_n is symmetric on grid pairs."""
+    P = Params(k1=2 * np.pi, k2=3 * np.pi, N=64, M=64)
+    sysm = ModalSystem(P)
+    for n in (0, 3):
+        Sg = sysm.grid_kernel("a", "S", n)
+        mask = sysm.Q.grid_mask
+        # restrict to pairs where both (l,m) and (m,l) use the same method
+        near = np.zeros_like(mask)
+        near[sysm.grid_pairs] = sysm.near[: sysm.ngrid]
+        same = mask & (near == near.T) & ~(np.imag(sysm.G.nodes["rho_t"])[:, None] > 0)
+        same &= ~(np.imag(sysm.G.nodes["rho_t"])[None, :] > 0)
+        d = np.abs(Sg - Sg.T)[same].max()
+        assert d <= 1e-12 * np.abs(Sg).max()
+
+
+# ---------------------------------------------------------------------------
+# reference field and right-hand side (Sec. 2)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("k2,polar", [(3 * np.pi, np.pi / 6), (1.2 * np.pi, np.pi / 3), (0.5 * np.pi, np.pi / 3)])
+def test_fresnel_transmission_conditions(k2, polar):
+    P = Params(k1=2 * np.pi, k2=k2, polar=polar, azimuth=0.4)
+    x = np.linspace(-1, 1, 7)
+    y = 0.3 * x
+    z = np.zeros_like(x)
+    u1, g1, u2, g2 = reference_field(P, x, y, z)
+    assert np.allclose(u1, u2, atol=1e-14)
+    assert np.allclose(g1[2], g2[2], atol=1e-12)
+    R, ks = fresnel(P)
+    if ks.imag == 0:
+        assert abs(R) <= 1.0
+    else:
+        assert abs(abs(R) - 1.0) < 1e-14      # total reflection
+
+
+def test_rhs_modes_jacobi_anger():
+    """DFT modes of the plane wave e^{-i a rho cos th} equal 2 pi (-i)^n J_n(a rho)."""
+    P = Params(k1=2 * np.pi, k2=3 * np.pi, N=64, M=64)
+    G = Geometry(P)
+    rho = G.nodes["rho"]
+    a = P.k1 * np.sin(P.polar)
+    th = 2 * np.pi * np.arange(P.M) / P.M
+    samp = np.exp(-1j * a * rho[:, None] * np.cos(th)[None, :])
+    modes = samp @ KR.dft_matrix(P.M)
+    n = np.arange(P.M // 2)
+    ref = 2 * np.pi * (-1j) ** n[None, :] * special.jv(n[None, :], a * rho[:, None])
+    assert np.abs(modes - ref).max() < 5e-12
+
+
+def test_flat_interface_and_equal_media_give_zero_rhs():
+    P = Params(k1=2 * np.pi, k2=3 * np.pi, N=64, M=32, bump_h=0.0)
+    b1, b2 = rhs_modes(Geometry(P))
+    assert np.abs(b1).max() < 1e-14 and np.abs(b2).max() < 1e-12
+    P = Params(k1=2 * np.pi, k2=2 * np.pi, N=64, M=32)
+    b1, b2 = rhs_modes(Geometry(P))
+    assert np.abs(b1).max() < 1e-14 and np.abs(b2).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# diagonal term (Lemmas 3.1-3.3)
+# ---------------------------------------------------------------------------
+def test_diagonal_solid_angle():
+    """D^a + D^b = -2 (solid angles of the two sides sum to 4 pi); D^a -> -1 at
+    smooth points away from corners (K0 1 = -1 with the outward normal); flat
+    interface gives D^a = -1 exactly."""
+    P = Params(k1=2 * np.pi, k2=3 * np.pi, N=128, M=32)
+    G = Geometry(P)
+    Q = Quadrature(G)
+    Da, Db = diagonal(G, Q)
+    assert np.abs(Da + Db + 2).max() < 1e-13
+    assert np.median(np.abs(Da + 1)) < 1e-8
+    Pf = Params(k1=2 * np.pi, k2=3 * np.pi, N=64, M=32, bump_h=0.0)
+    Gf = Geometry(Pf)
+    Daf, _ = diagonal(Gf, Quadrature(Gf))
+    assert np.abs(Daf + 1).max() < 1e-14
+
+
+def test_disc_solid_angle_on_axis():
+    from oracle.assemble import disc_solid_angle
+    Lr = 3.5
+    for h in (0.1, -0.4, 2.0):
+        ref = 2 * np.pi * (1 - abs(h) / np.sqrt(h * h + Lr * Lr))
+        assert abs(disc_solid_angle(np.array([0.0]), np.array([h]), Lr)[0] - ref) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# solve (Sec. 4.2)
+# ---------------------------------------------------------------------------
+def test_ntd_route_equals_block_route():
+    P = Params(k1=2 * np.pi, k2=3 * np.pi, N=64, M=32)
+    sysm = ModalSystem(P)
+    Da, Db = diagonal(sysm.G, sysm.Q)
+    b1, b2 = rhs_modes(sysm.G)
+    for n in (0, 5):
+        Sa, Ka = sysm.matrices("a", n)
+        Sb, Kb = sysm.matrices("b", n)
+        u1, f1, u2, f2 = solve_ntd(Sa, Ka, Da, Sb, Kb, Db, b1[:, n], b2[:, n])
+        A, B = block_system(Sa, Ka, Da, Sb, Kb, Db, b1[:, n], b2[:, n])
+        x = np.linalg.solve(A, B)
+        N = P.N
+        assert np.linalg.norm(x[:N] - u1) <= 1e-10 * np.linalg.norm(u1)
+        assert np.linalg.norm(x[N:] - f1) <= 1e-9 * np.linalg.norm(f1)
+
+
+def _exact_point_source_modes(nodes, p, omega, nmax):
+    """Modes of G(r~, p) and of |r'| nu_c . grad G at the nodes (adaptive quadrature)."""
+    rp, zp = p
+    rt, zt = nodes["rho_t"][:, None], nodes["z_t"][:, None]
+    ncr, ncz = nodes["nuc_r"][:, None], nodes["nuc_z"][:, None]
+    n = np.arange(nmax)[None, :]
+
+    def f(th):
+        R = np.sqrt(rt * rt + rp * rp - 2 * rt * rp * np.cos(th) + (zt - zp) ** 2)
+        e = np.exp(1j * omega * R)
+        dG = e * (1j * omega * R - 1) / (4 * np.pi * R ** 3)
+        c = 2 * np.cos(n * th)
+        return np.concatenate([((e / (4 * np.pi * R)) * c).ravel(),
+                               ((ncr * dG * (rt - rp * np.cos(th)) + ncz * dG * (zt - zp)) * c).ravel()])
+
+    v, _ = quad_vec(f, 0, np.pi, epsabs=1e-14, epsrel=1e-12, limit=2000)
+    k = rt.shape[0] * nmax
+    return v[:k].reshape(-1, nmax), v[k:].reshape(-1, nmax) * nodes["speed"][:, None]
+
+
+@pytest.mark.slow
+def test_manufactured_transmission_solution_converges():
+    """u^1 = G~_1(., p2), u^2 = G~_2(., p1) with sources across the interface
+    solve both regions' equations; the discrete block system must reproduce
+    them at the nodes with error falling as N grows (strong PML, resolved M)."""
+    errs = []
+    for N in (144, 240):
+        P = Params(k1=np.pi, k2=1.5 * np.pi, N=N, M=128, S=12.0, T=1.0)
+        sysm = ModalSystem(P)
+        G = sysm.G
+        Da, Db = diagonal(G, sysm.Q)
+        u1, f1 = _exact_point_source_modes(G.nodes, (0.5, -1.3), P.k1, 2)
+        u2, f2 = _exact_point_source_modes(G.nodes, (0.3, 0.5), P.k2, 2)
+        n = 1
+        Sa, Ka = sysm.matrices("a", n)
+        Sb, Kb = sysm.matrices("b", n)
+        A, B = block_system(Sa, Ka, Da, Sb, Kb, Db, u1[:, n] - u2[:, n], f1[:, n] - f2[:, n])
+        x = np.linalg.solve(A, B)
+        errs.append(np.linalg.norm(x[:N] - u1[:, n]) / np.linalg.norm(u1[:, n]))
+    assert errs[1] < 2e-4
+    assert errs[1] < errs[0] / 4
+
+
+@pytest.mark.slow
+def test_paper_sec4_3_ntd_experiment():
+    """The NtD check of Sec. 4.3 (dent geometry V, omega = 2 pi, a1 = 2, T = S = 2,
+    mode 1, source r_p below): |u_n - N_n phi_n| / |u_n| small and falling in N."""
+    g = json.load(open(os.path.join(GOLDEN, "paper_examples.json")))["ntd_check_sec4_3"]
+    errs = []
+    for N in (120, 200):
+        P = Params(k1=g["omega1"], k2=g["omega2"], N=N, M=128, a1=g["a1"], T=g["T"], S=g["S"],
+                   curve="polyline", vertices=[tuple(v) for v in g["vertices"]], taylor_L=g["taylor_L"])
+        sysm = ModalSystem(P)
+        G = sysm.G
+        Da, _ = diagonal(G, sysm.Q)
+        rp = g["source_rp"]
+        u, f = _exact_point_source_modes(G.nodes, (rp[0], rp[2]), P.k1, g["mode"] + 1)
+        n = g["mode"]
+        Sa, Ka = sysm.matrices("a", n)
+        Nn = np.linalg.solve(Ka - np.diag(Da), Sa)
+        errs.append(np.linalg.norm(u[:, n] - Nn @ f[:, n]) / np.linalg.norm(u[:, n]))
+    assert errs[1] < 1e-2 and errs[1] < errs[0] / 2, errs

@@ -1,0 +1,162 @@
+/*
+ * pmlbie.h - C ABI of the GB300 (sm_103a) PML-BIE modal solver.
+ *
+ * The library solves 3D acoustic transmission through a two-layer medium whose
+ * interface is the plane z = 0 with an axisymmetric perturbation, truncated by a
+ * cylindrical PML, with the Fourier-mode boundary integral method of Wang & Lu,
+ * "An FFT-accelerated PML-BIE solver for three-dimensional acoustic wave
+ * scattering in layered media" (arXiv 2412.11162):
+ *
+ *   Sec. 2    problem statement: wavenumbers omega_1 (z above the interface) and
+ *             omega_2 (below), plane-wave incidence, reference field u^{tot,0}.
+ *   Sec. 3.1  PML stretching rho~ = rho + i int sigma_1 (Eq. (sgm1)) and the
+ *             PML Green's function with a complex distance.
+ *   Sec. 3.3  azimuthal Fourier modes; decoupled modal equations (Eq. (6)).
+ *   Sec. 4.1  graded mesh (Eq. (sxi)), kernel splitting (Eqs. (s1), (k1)),
+ *             FFT modal kernels, Alpert quadrature, NtD matrices.
+ *   Sec. 4.2  transmission coupling of the two regions, right-hand sides b^1, b^2.
+ *   Sec. 4.3  stabilised distance and the cH_1 / cH_3 substitution.
+ *
+ * Conventions
+ *   - Every call returns an int status: PMLBIE_OK (0) or a negative error code.
+ *     pmlbie_last_error() returns a message owned by the library (per thread).
+ *   - Device pointers are CUDA global-memory addresses on the current device;
+ *     host pointers are ordinary CPU memory.  "stream" is a cudaStream_t passed
+ *     as void* (NULL = legacy default stream).  All device work is ordered on
+ *     that stream; host-buffer calls synchronise it before returning.
+ *   - Complex numbers are interleaved (re, im) doubles (complex128) unless a
+ *     call says otherwise.
+ *   - Modes: the modal kernels are F^_n = int_{-pi}^{pi} e^{-i n psi} F dpsi.
+ *     All kernels are even in psi, so F^_{-n} = F^_n; the library computes the
+ *     distinct modes n = 0 .. M/2-1 (Sec. 3.3).
+ *   - Unknowns: N nodes on the generating curve gamma_AB (axis point A to the
+ *     PML end B = (a1 + T, 0)); breakpoints of the graded grid carry none.
+ */
+#ifndef PMLBIE_H
+#define PMLBIE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PMLBIE_OK            0
+#define PMLBIE_EINVAL      (-1)   /* invalid parameter or size                    */
+#define PMLBIE_ENOMEM      (-2)   /* device or host allocation failed             */
+#define PMLBIE_ECUDA       (-3)   /* a CUDA call failed                           */
+#define PMLBIE_ESINGULAR   (-4)   /* zero pivot in a modal LU factorisation       */
+#define PMLBIE_ENOCONVERGE (-5)   /* iterative refinement missed its tolerance    */
+#define PMLBIE_ENAN        (-6)   /* NaN or Inf in an output                      */
+#define PMLBIE_ENODEV      (-7)   /* no CUDA device / extension not usable        */
+
+/* generating-curve kinds */
+#define PMLBIE_CURVE_GAUSS_BUMP 0   /* z = h (e^{-r^2/w} - e^{-R^2/w})/(1 - e^{-R^2/w}), r <= R; flat to B */
+#define PMLBIE_CURVE_POLYLINE   1   /* vertices (rho, z) from the axis; flat to B appended if needed     */
+
+/* arithmetic of a solve */
+#define PMLBIE_FP64  0   /* everything in FP64 (complex128)                          */
+#define PMLBIE_MIXED 1   /* FP64 modal kernels, FP32 LU, FP64 iterative refinement    */
+
+/* Problem statement (Sec. 2, Sec. 3.1, Sec. 4, Sec. 5).  Owned by the caller;
+ * pmlbie_create copies what it needs. */
+typedef struct {
+    uint32_t struct_size;     /* sizeof(pmlbie_params)                                */
+    double   k1, k2;          /* omega_1 (upper medium), omega_2 (lower medium) > 0  */
+    double   a1, T, S;        /* PML start radius, thickness, strength (Eq. (sgm1))  */
+    int      p;               /* PML profile and grading exponent (Sec. 5: 6), >= 2  */
+    int      N;               /* unknown nodes on gamma_AB, >= 32                    */
+    int      M;               /* azimuthal samples, 2^a 3^b, 16 <= M <= 1024          */
+    int      curve_kind;      /* PMLBIE_CURVE_*                                       */
+    double   bump_h, bump_w, bump_R;   /* Gaussian bump (kind 0)                     */
+    int      n_vertices;      /* polyline (kind 1): vertex count                     */
+    const double* vertices;   /* polyline: n_vertices (rho, z) pairs, host memory    */
+    int      taylor_L;        /* degree of the cH_1 / cH_3 substitution (Sec. 4.3: 5) */
+    double   split_c;         /* close-pair threshold eta_s = split_c * 2 pi / M      */
+} pmlbie_params;
+
+/* Report of a solve (filled when the pointer is not NULL). */
+typedef struct {
+    uint32_t struct_size;
+    int      n_modes;             /* M/2                                              */
+    int      near_pairs;          /* close pairs evaluated with the kernel split       */
+    int      refine_iters;        /* max refinement iterations over modes (mixed)      */
+    double   residual;            /* max over modes/RHS of ||B - A x|| / ||B||         */
+    double   ms_kernels;          /* device time: modal kernels + assembly (ms)        */
+    double   ms_lu;               /* device time: factorisation (ms)                   */
+    double   ms_solve;            /* device time: solves + refinement (ms)             */
+} pmlbie_report;
+
+typedef struct pmlbie_problem pmlbie_problem;   /* opaque, owned by the library */
+
+/* Build the geometry, PML tables, Alpert quadrature, close-pair lists and the
+ * diagonal term on the host.  Nothing touches a GPU here: the tables are
+ * uploaded to the then-current CUDA device by the first device call
+ * (pmlbie_modal_kernels / pmlbie_solve*), which must run on that device from
+ * then on.  Errors: EINVAL (parameter check), ENOMEM. */
+int  pmlbie_create(const pmlbie_params* params, pmlbie_problem** out);
+
+/* Release every host and device resource of the problem (NULL is ignored). */
+void pmlbie_destroy(pmlbie_problem* prob);
+
+/* Message for the last error raised on the calling thread (never NULL). */
+const char* pmlbie_last_error(void);
+
+/* Node tables (host copies, length N each, any pointer may be NULL):
+ * rho, z of the nodes, |r'(t)| and the curve parameter t.  EINVAL if n != N. */
+int  pmlbie_nodes(const pmlbie_problem* prob, double* rho, double* z, double* speed,
+                  double* t, int n);
+
+/* Diagonal term D (Sec. 3.2 Lemmas 3.1-3.3, Sec. 4.1) of both regions, host
+ * copies of length N.  D^a uses the outward normal of the upper region, D^b
+ * that of the lower region. */
+int  pmlbie_diagonal(const pmlbie_problem* prob, double* Da, double* Db, int n);
+
+/* Number of close (split) pairs: grid pairs and Alpert correction pairs. */
+int  pmlbie_near_count(const pmlbie_problem* prob, int* n_grid_near, int* n_corr);
+
+/* Alpert's log-singular end correction used by the quadrature (Sec. 4.1,
+ * order 10 in Sec. 5): j nodes x[k] in (0, a) and weights w[k] (host arrays of
+ * length j), generated by the library from the rule's moment conditions.
+ * Supported: 2 <= j <= 12, 1 <= a <= 16.  EINVAL otherwise or if the solve
+ * for the rule fails. */
+int  pmlbie_alpert_rule(int j, int a, double* x, double* w);
+
+/* Bytes of device workspace a solve with n_rhs right-hand sides allocates. */
+size_t pmlbie_workspace_bytes(const pmlbie_problem* prob, int precision, int n_rhs);
+
+/* Modal kernels S^_n, K^_n of both regions on every grid node pair (Sec. 4.1,
+ * Eqs. (snspml), (knspml)): far pairs by the M-point FFT in psi, close pairs
+ * by the kernel split, pairs inside the Alpert skip band (|i - j| < 10 grid
+ * steps) set to 0.  Output: dev_out, caller-owned device buffer of
+ * (mode_hi - mode_lo) * 4 * N * N complex128 laid out
+ * [mode][kernel][l][m], kernel = 0: S^a, 1: K^a, 2: S^b, 3: K^b (region a =
+ * upper medium with omega_1 and normal nu; region b = lower medium, omega_2,
+ * normal -nu), l = target node, m = source node.  0 <= mode_lo < mode_hi <= M/2. */
+int  pmlbie_modal_kernels(pmlbie_problem* prob, int mode_lo, int mode_hi, void* dev_out,
+                          void* stream);
+
+/* Full solve for plane waves of polar angles polar[0..n_rhs-1] (azimuth 0),
+ * Sec. 4.1-4.2: kernels, split, Alpert assembly, diagonal, right-hand side,
+ * batched LU per mode, solves (and FP64 refinement for PMLBIE_MIXED).
+ * Outputs (caller-owned device buffers, complex128, [mode][node][rhs], M/2
+ * modes): u1 = u^{s,1}_n, phi1 = |r'| d_nu_c u^{s,1}_n, u2, phi2 (the same for
+ * the lower medium, d_nu with the same nu).  Any output may be NULL.
+ * Errors: EINVAL, ENOMEM, ECUDA, ESINGULAR, ENOCONVERGE (mixed: refinement
+ * residual above 1e-12 after the iteration cap; outputs still written). */
+int  pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* polar,
+                  void* dev_u1, void* dev_phi1, void* dev_u2, void* dev_phi2,
+                  void* stream, pmlbie_report* rep);
+
+/* The same solve with HOST output buffers: the call copies the results to the
+ * host (synchronising the stream).  Host buffers have the layout above. */
+int  pmlbie_solve_host(pmlbie_problem* prob, int precision, int n_rhs, const double* polar,
+                       double* u1, double* phi1, double* u2, double* phi2,
+                       void* stream, pmlbie_report* rep);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMLBIE_H */

@@ -1,0 +1,199 @@
+"""ctypes binding of libpmlbie.so (include/pmlbie.h): argument marshalling only.
+
+Every function keeps the C name.  Device buffers are torch tensors (their
+data_ptr is passed); streams are torch.cuda streams.  The library must be
+built (paper_2412_11162_gb300.build); importing this module fails loudly if it
+is missing, and there is no fallback path.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpmlbie.so")
+
+PMLBIE_OK = 0
+PMLBIE_EINVAL = -1
+PMLBIE_ENOMEM = -2
+PMLBIE_ECUDA = -3
+PMLBIE_ESINGULAR = -4
+PMLBIE_ENOCONVERGE = -5
+PMLBIE_ENAN = -6
+PMLBIE_ENODEV = -7
+PMLBIE_CURVE_GAUSS_BUMP = 0
+PMLBIE_CURVE_POLYLINE = 1
+PMLBIE_FP64 = 0
+PMLBIE_MIXED = 1
+
+
+class pmlbie_params(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("k1", ctypes.c_double), ("k2", ctypes.c_double),
+                ("a1", ctypes.c_double), ("T", ctypes.c_double), ("S", ctypes.c_double),
+                ("p", ctypes.c_int), ("N", ctypes.c_int), ("M", ctypes.c_int),
+                ("curve_kind", ctypes.c_int), ("bump_h", ctypes.c_double), ("bump_w", ctypes.c_double),
+                ("bump_R", ctypes.c_double), ("n_vertices", ctypes.c_int),
+                ("vertices", ctypes.POINTER(ctypes.c_double)), ("taylor_L", ctypes.c_int),
+                ("split_c", ctypes.c_double)]
+
+
+class pmlbie_report(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("n_modes", ctypes.c_int), ("near_pairs", ctypes.c_int),
+                ("refine_iters", ctypes.c_int), ("residual", ctypes.c_double),
+                ("ms_kernels", ctypes.c_double), ("ms_lu", ctypes.c_double), ("ms_solve", ctypes.c_double)]
+
+
+EXPORTS = ["pmlbie_create", "pmlbie_destroy", "pmlbie_last_error", "pmlbie_nodes", "pmlbie_diagonal",
+           "pmlbie_near_count", "pmlbie_alpert_rule", "pmlbie_workspace_bytes", "pmlbie_modal_kernels",
+           "pmlbie_solve", "pmlbie_solve_host"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libpmlbie.so is not built (run paper_2412_11162_gb300.build.build()); "
+                          "there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    lib.pmlbie_create.argtypes = [ctypes.POINTER(pmlbie_params), ctypes.POINTER(vp)]
+    lib.pmlbie_create.restype = ctypes.c_int
+    lib.pmlbie_destroy.argtypes = [vp]
+    lib.pmlbie_destroy.restype = None
+    lib.pmlbie_last_error.argtypes = []
+    lib.pmlbie_last_error.restype = ctypes.c_char_p
+    lib.pmlbie_nodes.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int]
+    lib.pmlbie_diagonal.argtypes = [vp, dp, dp, ctypes.c_int]
+    lib.pmlbie_near_count.argtypes = [vp, ip, ip]
+    lib.pmlbie_alpert_rule.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+    lib.pmlbie_workspace_bytes.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.pmlbie_workspace_bytes.restype = ctypes.c_size_t
+    lib.pmlbie_modal_kernels.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.pmlbie_solve.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, vp, vp, vp, vp, vp,
+                                 ctypes.POINTER(pmlbie_report)]
+    lib.pmlbie_solve_host.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, vp,
+                                      ctypes.POINTER(pmlbie_report)]
+    for f in ("pmlbie_nodes", "pmlbie_diagonal", "pmlbie_near_count", "pmlbie_alpert_rule",
+              "pmlbie_modal_kernels", "pmlbie_solve", "pmlbie_solve_host"):
+        getattr(lib, f).restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+class PmlbieError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s failed (%d): %s" % (where, code, lib.pmlbie_last_error().decode()))
+
+
+def check(code, where):
+    if code != PMLBIE_OK:
+        raise PmlbieError(code, where)
+    return code
+
+
+def _dptr(a):
+    """double* of a contiguous float64 numpy array."""
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _tptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def make_params(k1, k2, N, M, a1=2.5, T=1.0, S=3.0, p=6, curve="gauss", bump_h=0.2, bump_w=0.5,
+                bump_R=1.0, vertices=None, taylor_L=5, split_c=8.0):
+    import numpy as np
+    P = pmlbie_params()
+    P.struct_size = ctypes.sizeof(pmlbie_params)
+    P.k1, P.k2, P.a1, P.T, P.S, P.p, P.N, P.M = k1, k2, a1, T, S, p, N, M
+    P.bump_h, P.bump_w, P.bump_R = bump_h, bump_w, bump_R
+    P.taylor_L, P.split_c = taylor_L, split_c
+    keep = None
+    if curve == "gauss":
+        P.curve_kind = PMLBIE_CURVE_GAUSS_BUMP
+    else:
+        P.curve_kind = PMLBIE_CURVE_POLYLINE
+        keep = np.ascontiguousarray(np.asarray(vertices, dtype=np.float64).reshape(-1))
+        P.n_vertices = len(keep) // 2
+        P.vertices = _dptr(keep)
+    return P, keep
+
+
+def pmlbie_create(params):
+    h = ctypes.c_void_p()
+    check(lib.pmlbie_create(ctypes.byref(params), ctypes.byref(h)), "pmlbie_create")
+    return h
+
+
+def pmlbie_destroy(h):
+    lib.pmlbie_destroy(h)
+
+
+def pmlbie_nodes(h, N):
+    import numpy as np
+    out = [np.empty(N) for _ in range(4)]
+    check(lib.pmlbie_nodes(h, *[_dptr(a) for a in out], N), "pmlbie_nodes")
+    return dict(rho=out[0], z=out[1], speed=out[2], t=out[3])
+
+
+def pmlbie_diagonal(h, N):
+    import numpy as np
+    Da, Db = np.empty(N), np.empty(N)
+    check(lib.pmlbie_diagonal(h, _dptr(Da), _dptr(Db), N), "pmlbie_diagonal")
+    return Da, Db
+
+
+def pmlbie_near_count(h):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    check(lib.pmlbie_near_count(h, ctypes.byref(a), ctypes.byref(b)), "pmlbie_near_count")
+    return a.value, b.value
+
+
+def pmlbie_alpert_rule(j, a):
+    import numpy as np
+    x, w = np.empty(j), np.empty(j)
+    check(lib.pmlbie_alpert_rule(j, a, _dptr(x), _dptr(w)), "pmlbie_alpert_rule")
+    return x, w
+
+
+def pmlbie_workspace_bytes(h, precision, n_rhs):
+    return lib.pmlbie_workspace_bytes(h, precision, n_rhs)
+
+
+def pmlbie_modal_kernels(h, mode_lo, mode_hi, out, stream=None):
+    """out: complex128 CUDA tensor of (mode_hi-mode_lo)*4*N*N elements."""
+    check(lib.pmlbie_modal_kernels(h, mode_lo, mode_hi, _tptr(out), _stream(stream)), "pmlbie_modal_kernels")
+    return out
+
+
+def pmlbie_solve(h, precision, polar, u1=None, phi1=None, u2=None, phi2=None, stream=None,
+                 allow_noconverge=False):
+    import numpy as np
+    pol = np.ascontiguousarray(np.asarray(polar, dtype=np.float64).reshape(-1))
+    rep = pmlbie_report()
+    rep.struct_size = ctypes.sizeof(pmlbie_report)
+    rc = lib.pmlbie_solve(h, precision, len(pol), _dptr(pol), _tptr(u1), _tptr(phi1), _tptr(u2), _tptr(phi2),
+                          _stream(stream), ctypes.byref(rep))
+    if not (allow_noconverge and rc == PMLBIE_ENOCONVERGE):
+        check(rc, "pmlbie_solve")
+    return rep
+
+
+def pmlbie_solve_host(h, precision, polar, u1, phi1, u2, phi2, stream=None):
+    """Host outputs: complex128 numpy arrays (any may be None)."""
+    import numpy as np
+    pol = np.ascontiguousarray(np.asarray(polar, dtype=np.float64).reshape(-1))
+    rep = pmlbie_report()
+    rep.struct_size = ctypes.sizeof(pmlbie_report)
+
+    def hp(a):
+        return ctypes.POINTER(ctypes.c_double)() if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    check(lib.pmlbie_solve_host(h, precision, len(pol), _dptr(pol), hp(u1), hp(phi1), hp(u2), hp(phi2),
+                                _stream(stream), ctypes.byref(rep)), "pmlbie_solve_host")
+    return rep

@@ -1,0 +1,429 @@
+// C ABI of the PML-BIE modal solver: problem creation (host tables), device
+// upload, modal kernels and the full solve.  See include/pmlbie.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+
+#include "internal.h"
+
+using namespace pmlbie;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+bool is_2a3b(int M) {
+    if (M <= 0) return false;
+    while (M % 2 == 0) M /= 2;
+    while (M % 3 == 0) M /= 3;
+    return M == 1;
+}
+
+template <typename T>
+int upload(T*& dst, const std::vector<T>& src) {
+    if (src.empty()) {
+        dst = nullptr;
+        return PMLBIE_OK;
+    }
+    PMLBIE_CUDA_TRY(cudaMalloc(&dst, sizeof(T) * src.size()));
+    PMLBIE_CUDA_TRY(cudaMemcpy(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+    return PMLBIE_OK;
+}
+
+std::vector<double2> to_d2(const std::vector<cd>& v) {
+    std::vector<double2> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = make_double2(v[i].real(), v[i].imag());
+    return o;
+}
+
+}  // namespace
+
+// device-side per-node extras live next to the problem (not in DeviceTables,
+// which the kernels receive by value)
+struct pmlbie_dev_extra {
+    double *nu_r = nullptr, *nu_z = nullptr, *speed = nullptr;
+    bool ready = false;
+};
+
+namespace {
+
+pmlbie_dev_extra* extra_of(pmlbie_problem* p) {
+    static_assert(sizeof(void*) == sizeof(pmlbie_dev_extra*), "");
+    return reinterpret_cast<pmlbie_dev_extra*>(p->ws_extra);
+}
+
+int ensure_device(pmlbie_problem* prob) {
+    pmlbie_dev_extra* ex = extra_of(prob);
+    if (ex->ready) return PMLBIE_OK;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(PMLBIE_ENODEV, "no CUDA device available");
+    PMLBIE_CUDA_TRY(cudaGetDevice(&prob->device));
+    const HostTables& H = prob->H;
+    DeviceTables& D = prob->D;
+    int rc;
+    if ((rc = upload(D.rho, H.rho)) || (rc = upload(D.z, H.z)) || (rc = upload(D.I, H.I)) ||
+        (rc = upload(D.Wu, H.Wu)) || (rc = upload(D.Wphi, H.Wphi)))
+        return rc;
+    std::vector<double2> rt = to_d2(H.rho_t), ncr = to_d2(H.nuc_r), ncz = to_d2(H.nuc_z);
+    if ((rc = upload(D.rho_t, rt)) || (rc = upload(D.nuc_r, ncr)) || (rc = upload(D.nuc_z, ncz)) ||
+        (rc = upload(D.cls, H.cls)) || (rc = upload(D.near, H.near)) ||
+        (rc = upload(D.corr_target, H.corr_target)) || (rc = upload(D.corr_m, H.corr_m)) ||
+        (rc = upload(D.corr_coef, H.corr_coef)) || (rc = upload(D.Da, H.Da)) || (rc = upload(D.Db, H.Db)))
+        return rc;
+    const int M = prob->P.M;
+    std::vector<double2> cs(M / 2 + 1), tw(M);
+    for (int j = 0; j <= M / 2; ++j) {
+        double s = std::sin(kPi * j / M);
+        cs[j] = make_double2(s * s, std::cos(2.0 * kPi * j / M));
+    }
+    for (int e = 0; e < M; ++e) tw[e] = make_double2(std::cos(2.0 * kPi * e / M), -std::sin(2.0 * kPi * e / M));
+    if ((rc = upload(D.cos_tab, cs)) || (rc = upload(D.twid, tw))) return rc;
+    if ((rc = upload(ex->nu_r, H.nu_r)) || (rc = upload(ex->nu_z, H.nu_z)) || (rc = upload(ex->speed, H.speed)))
+        return rc;
+    ex->ready = true;
+    return PMLBIE_OK;
+}
+
+void free_device(pmlbie_problem* prob) {
+    DeviceTables& D = prob->D;
+    void* ptrs[] = {D.rho, D.z, D.I, D.Wu, D.Wphi, D.rho_t, D.nuc_r, D.nuc_z, D.cls, D.near,
+                    D.corr_target, D.corr_m, D.corr_coef, D.Da, D.Db, D.cos_tab, D.twid};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    pmlbie_dev_extra* ex = extra_of(prob);
+    if (ex) {
+        if (ex->nu_r) cudaFree(ex->nu_r);
+        if (ex->nu_z) cudaFree(ex->nu_z);
+        if (ex->speed) cudaFree(ex->speed);
+    }
+    if (prob->ws) cudaFree(prob->ws);
+    prob->ws = nullptr;
+}
+
+// workspace carve-up of one solve
+struct Workspace {
+    double2 *A = nullptr, *zd = nullptr, *nout = nullptr, *b1 = nullptr, *b2 = nullptr, *B = nullptr,
+            *X = nullptr, *R = nullptr;
+    float2 *A32 = nullptr, *w32 = nullptr;
+    int *piv = nullptr, *info = nullptr;
+    double *rn = nullptr, *bn = nullptr, *rpar = nullptr;
+    size_t bytes = 0;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Workspace plan(const pmlbie_problem* prob, int precision, int nrhs, char* base) {
+    const size_t N = prob->P.N, M = prob->P.M, nm = M / 2, n2 = 2 * N;
+    const size_t np = prob->H.near.size();
+    Workspace w;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* p = base ? base + off : nullptr;
+        off += align256(bytes);
+        return p;
+    };
+    w.A = (double2*)take(sizeof(double2) * nm * n2 * n2);
+    if (precision == PMLBIE_MIXED) {
+        w.A32 = (float2*)take(sizeof(float2) * nm * n2 * n2);
+        w.w32 = (float2*)take(sizeof(float2) * nm * n2 * nrhs);
+        w.R = (double2*)take(sizeof(double2) * nm * n2 * nrhs);
+    }
+    w.zd = (double2*)take(sizeof(double2) * std::max<size_t>(np, 1) * 2 * M);
+    w.nout = (double2*)take(sizeof(double2) * std::max<size_t>(np, 1) * 4 * nm);
+    w.b1 = (double2*)take(sizeof(double2) * nm * N * nrhs);
+    w.b2 = (double2*)take(sizeof(double2) * nm * N * nrhs);
+    w.B = (double2*)take(sizeof(double2) * nm * n2 * nrhs);
+    w.X = (double2*)take(sizeof(double2) * nm * n2 * nrhs);
+    w.piv = (int*)take(sizeof(int) * nm * n2);
+    w.info = (int*)take(sizeof(int) * nm);
+    w.rn = (double*)take(sizeof(double) * nm * nrhs);
+    w.bn = (double*)take(sizeof(double) * nm * nrhs);
+    w.rpar = (double*)take(sizeof(double) * 6 * nrhs);
+    w.bytes = off;
+    return w;
+}
+
+int get_workspace(pmlbie_problem* prob, int precision, int nrhs, Workspace& w) {
+    Workspace sz = plan(prob, precision, nrhs, nullptr);
+    if (prob->ws_bytes < sz.bytes) {
+        if (prob->ws) cudaFree(prob->ws);
+        prob->ws = nullptr;
+        prob->ws_bytes = 0;
+        if (cudaMalloc(&prob->ws, sz.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PMLBIE_ENOMEM, "device workspace allocation failed (" + std::to_string(sz.bytes) + " bytes)");
+        }
+        prob->ws_bytes = sz.bytes;
+    }
+    w = plan(prob, precision, nrhs, (char*)prob->ws);
+    return PMLBIE_OK;
+}
+
+void fresnel(double w1, double w2, double phi, double* out6) {
+    double kx = w1 * std::sin(phi);
+    cd ks = (w2 > std::fabs(kx)) ? cd(std::sqrt(w2 * w2 - kx * kx), 0.0) : cd(0.0, std::sqrt(kx * kx - w2 * w2));
+    cd R = 2.0 / (1.0 + ks / (w1 * std::cos(phi))) - 1.0;
+    out6[0] = std::sin(phi);
+    out6[1] = std::cos(phi);
+    out6[2] = R.real();
+    out6[3] = R.imag();
+    out6[4] = ks.real();
+    out6[5] = ks.imag();
+}
+
+// modal kernels + assembly into w.A (all modes)
+int build_system(pmlbie_problem* prob, Workspace& w, cudaStream_t s) {
+    const int nm = prob->P.M / 2;
+    FarLaunch fl{0, nm, w.A, nullptr};
+    PMLBIE_CUDA_TRY(launch_far(prob, fl, s));
+    PMLBIE_CUDA_TRY(launch_near(prob, 0, nm, w.zd, w.nout, s));
+    PMLBIE_CUDA_TRY(launch_assemble(prob, 0, nm, w.nout, w.A, s));
+    return PMLBIE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pmlbie_last_error(void) { return error_text(); }
+
+int pmlbie_create(const pmlbie_params* P, pmlbie_problem** out) {
+    if (!out) return fail(PMLBIE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!P || P->struct_size < sizeof(pmlbie_params)) return fail(PMLBIE_EINVAL, "params NULL or struct_size too small");
+    if (!(P->k1 > 0) || !(P->k2 > 0)) return fail(PMLBIE_EINVAL, "wavenumbers must be positive");
+    if (!(P->a1 > 0) || !(P->T > 0) || !(P->S >= 0)) return fail(PMLBIE_EINVAL, "PML needs a1 > 0, T > 0, S >= 0");
+    if (P->p < 2 || P->p > 16) return fail(PMLBIE_EINVAL, "p must be in [2, 16]");
+    if (P->N < 32 || P->N > 16384) return fail(PMLBIE_EINVAL, "N must be in [32, 16384]");
+    if (P->M < 16 || P->M > 1024 || !is_2a3b(P->M)) return fail(PMLBIE_EINVAL, "M must be 2^a 3^b in [16, 1024]");
+    if (P->taylor_L < 3 || P->taylor_L > 7) return fail(PMLBIE_EINVAL, "taylor_L must be in [3, 7]");
+    if (!(P->split_c > 0)) return fail(PMLBIE_EINVAL, "split_c must be positive");
+    if (P->curve_kind == PMLBIE_CURVE_GAUSS_BUMP) {
+        if (!(P->bump_R > 0) || !(P->bump_w > 0) || !(P->bump_R < P->a1))
+            return fail(PMLBIE_EINVAL, "bump needs 0 < R < a1 and w > 0");
+    } else if (P->curve_kind == PMLBIE_CURVE_POLYLINE) {
+        if (P->n_vertices < 2 || !P->vertices) return fail(PMLBIE_EINVAL, "polyline needs >= 2 vertices");
+        if (P->vertices[0] != 0.0) return fail(PMLBIE_EINVAL, "polyline must start on the axis (rho = 0)");
+        for (int i = 0; i < P->n_vertices; ++i)
+            if (P->vertices[2 * i] < 0 || P->vertices[2 * i] > P->a1 + P->T + 1e-12 ||
+                (P->vertices[2 * i] > P->a1 && P->vertices[2 * i + 1] != 0.0))
+                return fail(PMLBIE_EINVAL, "polyline vertices must lie in rho <= a1 (or on z = 0 in the PML)");
+    } else {
+        return fail(PMLBIE_EINVAL, "unknown curve kind");
+    }
+    pmlbie_problem* prob = new (std::nothrow) pmlbie_problem();
+    if (!prob) return fail(PMLBIE_ENOMEM, "host allocation failed");
+    prob->P = *P;
+    if (P->curve_kind == PMLBIE_CURVE_POLYLINE)
+        prob->vertices.assign(P->vertices, P->vertices + 2 * P->n_vertices);
+    prob->P.vertices = nullptr;
+    prob->eta_split = P->split_c * 2.0 * kPi / P->M;
+    prob->ws_extra = new pmlbie_dev_extra();
+    int rc;
+    try {
+        rc = build_tables(prob);
+    } catch (const std::bad_alloc&) {
+        rc = fail(PMLBIE_ENOMEM, "host allocation failed while building tables");
+    }
+    if (rc != PMLBIE_OK) {
+        delete reinterpret_cast<pmlbie_dev_extra*>(prob->ws_extra);
+        delete prob;
+        return rc;
+    }
+    *out = prob;
+    return PMLBIE_OK;
+}
+
+void pmlbie_destroy(pmlbie_problem* prob) {
+    if (!prob) return;
+    if (extra_of(prob)->ready) free_device(prob);
+    delete reinterpret_cast<pmlbie_dev_extra*>(prob->ws_extra);
+    delete prob;
+}
+
+int pmlbie_nodes(const pmlbie_problem* prob, double* rho, double* z, double* speed, double* t, int n) {
+    if (!prob || n != prob->P.N) return fail(PMLBIE_EINVAL, "problem NULL or n != N");
+    const HostTables& H = prob->H;
+    if (rho) std::memcpy(rho, H.rho.data(), sizeof(double) * n);
+    if (z) std::memcpy(z, H.z.data(), sizeof(double) * n);
+    if (speed) std::memcpy(speed, H.speed.data(), sizeof(double) * n);
+    if (t) std::memcpy(t, H.t.data(), sizeof(double) * n);
+    return PMLBIE_OK;
+}
+
+int pmlbie_diagonal(const pmlbie_problem* prob, double* Da, double* Db, int n) {
+    if (!prob || n != prob->P.N) return fail(PMLBIE_EINVAL, "problem NULL or n != N");
+    if (Da) std::memcpy(Da, prob->H.Da.data(), sizeof(double) * n);
+    if (Db) std::memcpy(Db, prob->H.Db.data(), sizeof(double) * n);
+    return PMLBIE_OK;
+}
+
+int pmlbie_near_count(const pmlbie_problem* prob, int* n_grid_near, int* n_corr) {
+    if (!prob) return fail(PMLBIE_EINVAL, "problem NULL");
+    if (n_grid_near) *n_grid_near = prob->H.n_grid_near;
+    if (n_corr) *n_corr = (int)prob->H.near.size() - prob->H.n_grid_near;
+    return PMLBIE_OK;
+}
+
+int pmlbie_alpert_rule(int j, int a, double* x, double* w) {
+    if (j < 2 || j > 12 || a < 1 || a > 16 || !x || !w) return fail(PMLBIE_EINVAL, "bad Alpert rule request");
+    std::vector<double> xv, wv;
+    try {
+        alpert_log_rule(j, a, xv, wv);
+    } catch (const std::exception& e) {
+        return fail(PMLBIE_EINVAL, e.what());
+    }
+    std::memcpy(x, xv.data(), sizeof(double) * j);
+    std::memcpy(w, wv.data(), sizeof(double) * j);
+    return PMLBIE_OK;
+}
+
+size_t pmlbie_workspace_bytes(const pmlbie_problem* prob, int precision, int n_rhs) {
+    if (!prob || n_rhs < 1) return 0;
+    return plan(prob, precision, n_rhs, nullptr).bytes;
+}
+
+int pmlbie_modal_kernels(pmlbie_problem* prob, int mode_lo, int mode_hi, void* dev_out, void* stream) {
+    if (!prob || !dev_out) return fail(PMLBIE_EINVAL, "problem or output NULL");
+    const int nm = prob->P.M / 2;
+    if (mode_lo < 0 || mode_hi > nm || mode_lo >= mode_hi) return fail(PMLBIE_EINVAL, "bad mode range");
+    int rc = ensure_device(prob);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t np = std::max<size_t>(prob->H.near.size(), 1);
+    const int M = prob->P.M;
+    double2 *zd = nullptr, *nout = nullptr;
+    PMLBIE_CUDA_TRY(cudaMalloc(&zd, sizeof(double2) * np * 2 * M));
+    if (cudaMalloc(&nout, sizeof(double2) * np * 4 * (mode_hi - mode_lo)) != cudaSuccess) {
+        cudaFree(zd);
+        return fail(PMLBIE_ENOMEM, "scratch allocation failed");
+    }
+    FarLaunch fl{mode_lo, mode_hi, nullptr, (double2*)dev_out};
+    cudaError_t e = launch_far(prob, fl, s);
+    if (e == cudaSuccess) e = launch_near(prob, mode_lo, mode_hi, zd, nout, s);
+    if (e == cudaSuccess) e = launch_near_to_raw(prob, mode_lo, mode_hi, nout, (double2*)dev_out, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(zd);
+    cudaFree(nout);
+    if (e != cudaSuccess) return fail(PMLBIE_ECUDA, std::string("modal kernels: ") + cudaGetErrorString(e));
+    return PMLBIE_OK;
+}
+
+int pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* polar, void* dev_u1,
+                 void* dev_phi1, void* dev_u2, void* dev_phi2, void* stream, pmlbie_report* rep) {
+    if (!prob || !polar || n_rhs < 1 || n_rhs > 4096) return fail(PMLBIE_EINVAL, "bad problem, polar or n_rhs");
+    if (precision != PMLBIE_FP64 && precision != PMLBIE_MIXED) return fail(PMLBIE_EINVAL, "bad precision");
+    for (int r = 0; r < n_rhs; ++r)
+        if (!(polar[r] >= 0.0 && polar[r] < 0.5 * kPi)) return fail(PMLBIE_EINVAL, "polar angle must be in [0, pi/2)");
+    int rc = ensure_device(prob);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace w;
+    if ((rc = get_workspace(prob, precision, n_rhs, w))) return rc;
+    const int N = prob->P.N, nm = prob->P.M / 2, n2 = 2 * N;
+    cudaEvent_t ev[4];
+    for (auto& e : ev) PMLBIE_CUDA_TRY(cudaEventCreate(&e));
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard() {
+            for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+        }
+    } guard{ev};
+
+    std::vector<double> rpar(6 * n_rhs);
+    for (int r = 0; r < n_rhs; ++r) fresnel(prob->P.k1, prob->P.k2, polar[r], &rpar[6 * r]);
+    PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.rpar, rpar.data(), sizeof(double) * rpar.size(), cudaMemcpyHostToDevice, s));
+    pmlbie_dev_extra* ex = extra_of(prob);
+
+    PMLBIE_CUDA_TRY(cudaEventRecord(ev[0], s));
+    if ((rc = build_system(prob, w, s))) return rc;
+    PMLBIE_CUDA_TRY(launch_rhs(prob, n_rhs, w.rpar, ex->nu_r, ex->nu_z, ex->speed, w.b1, w.b2, s));
+    PMLBIE_CUDA_TRY(launch_block_rhs(prob, n_rhs, w.A, w.b1, w.b2, w.B, s));
+    PMLBIE_CUDA_TRY(cudaEventRecord(ev[1], s));
+    PMLBIE_CUDA_TRY(cudaMemsetAsync(w.info, 0, sizeof(int) * nm, s));
+    const size_t xbytes = sizeof(double2) * (size_t)nm * n2 * n_rhs;
+    int iters = 0;
+    double resid = 0.0;
+    if (precision == PMLBIE_FP64) {
+        PMLBIE_CUDA_TRY(batched_lu<double2>(n2, nm, w.A, w.piv, w.info, s));
+        PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
+        PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.X, w.B, xbytes, cudaMemcpyDeviceToDevice, s));
+        PMLBIE_CUDA_TRY(batched_lu_solve<double2>(n2, nm, n_rhs, w.A, w.piv, w.X, s));
+    } else {
+        PMLBIE_CUDA_TRY(convert_to_c64((int64_t)nm * n2 * n2, w.A, w.A32, s));
+        PMLBIE_CUDA_TRY(batched_lu<float2>(n2, nm, w.A32, w.piv, w.info, s));
+        PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
+        PMLBIE_CUDA_TRY(cudaMemsetAsync(w.X, 0, xbytes, s));
+        PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.R, w.B, xbytes, cudaMemcpyDeviceToDevice, s));
+        std::vector<double> rn((size_t)nm * n_rhs), bn((size_t)nm * n_rhs);
+        const int max_iter = 30;
+        for (iters = 0; iters <= max_iter; ++iters) {
+            if (iters > 0) {
+                PMLBIE_CUDA_TRY(residual_c128(n2, nm, n_rhs, w.A, w.X, w.B, w.R, w.rn, w.bn, s));
+                PMLBIE_CUDA_TRY(cudaMemcpyAsync(rn.data(), w.rn, sizeof(double) * rn.size(), cudaMemcpyDeviceToHost, s));
+                PMLBIE_CUDA_TRY(cudaMemcpyAsync(bn.data(), w.bn, sizeof(double) * bn.size(), cudaMemcpyDeviceToHost, s));
+                PMLBIE_CUDA_TRY(cudaStreamSynchronize(s));
+                resid = 0.0;
+                for (size_t i = 0; i < rn.size(); ++i)
+                    if (bn[i] > 0) resid = std::max(resid, std::sqrt(rn[i] / bn[i]));
+                if (resid <= 1e-13 || iters == max_iter) break;
+            }
+            PMLBIE_CUDA_TRY(refine_step(n2, nm, n_rhs, w.A32, w.piv, w.R, w.w32, w.X, s));
+        }
+    }
+    PMLBIE_CUDA_TRY(launch_outputs(prob, n_rhs, w.X, w.b1, w.b2, (double2*)dev_u1, (double2*)dev_phi1,
+                                   (double2*)dev_u2, (double2*)dev_phi2, s));
+    PMLBIE_CUDA_TRY(cudaEventRecord(ev[3], s));
+    PMLBIE_CUDA_TRY(cudaEventSynchronize(ev[3]));
+    std::vector<int> info(nm);
+    PMLBIE_CUDA_TRY(cudaMemcpy(info.data(), w.info, sizeof(int) * nm, cudaMemcpyDeviceToHost));
+    if (rep && rep->struct_size >= sizeof(pmlbie_report)) {
+        rep->n_modes = nm;
+        rep->near_pairs = (int)prob->H.near.size();
+        rep->refine_iters = iters;
+        rep->residual = resid;
+        float t01, t12, t23;
+        cudaEventElapsedTime(&t01, ev[0], ev[1]);
+        cudaEventElapsedTime(&t12, ev[1], ev[2]);
+        cudaEventElapsedTime(&t23, ev[2], ev[3]);
+        rep->ms_kernels = t01;
+        rep->ms_lu = t12;
+        rep->ms_solve = t23;
+    }
+    for (int i = 0; i < nm; ++i)
+        if (info[i]) return fail(PMLBIE_ESINGULAR, "zero pivot in mode " + std::to_string(i));
+    if (precision == PMLBIE_MIXED && resid > 1e-12)
+        return fail(PMLBIE_ENOCONVERGE, "refinement residual " + std::to_string(resid));
+    return PMLBIE_OK;
+}
+
+int pmlbie_solve_host(pmlbie_problem* prob, int precision, int n_rhs, const double* polar, double* u1,
+                      double* phi1, double* u2, double* phi2, void* stream, pmlbie_report* rep) {
+    if (!prob || n_rhs < 1) return fail(PMLBIE_EINVAL, "bad problem or n_rhs");
+    int rc = ensure_device(prob);
+    if (rc) return rc;
+    const size_t cnt = (size_t)(prob->P.M / 2) * prob->P.N * n_rhs;
+    double* hosts[4] = {u1, phi1, u2, phi2};
+    void* dev[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int i = 0; i < 4; ++i)
+        if (hosts[i] && cudaMalloc(&dev[i], sizeof(double2) * cnt) != cudaSuccess) {
+            for (int k = 0; k < 4; ++k)
+                if (dev[k]) cudaFree(dev[k]);
+            return fail(PMLBIE_ENOMEM, "output allocation failed");
+        }
+    rc = pmlbie_solve(prob, precision, n_rhs, polar, dev[0], dev[1], dev[2], dev[3], stream, rep);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < 4; ++i)
+        if (hosts[i] && (rc == PMLBIE_OK || rc == PMLBIE_ENOCONVERGE))
+            cudaMemcpyAsync(hosts[i], dev[i], sizeof(double2) * cnt, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    for (int i = 0; i < 4; ++i)
+        if (dev[i]) cudaFree(dev[i]);
+    if (e != cudaSuccess && rc == PMLBIE_OK) return fail(PMLBIE_ECUDA, cudaGetErrorString(e));
+    return rc;
+}
+
+}  // extern "C"

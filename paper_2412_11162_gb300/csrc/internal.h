@@ -1,0 +1,147 @@
+// Internal declarations of the pmlbie library (host setup + CUDA kernels).
+#pragma once
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pmlbie.h"
+
+namespace pmlbie {
+
+using cd = std::complex<double>;
+
+constexpr int kStencil = 10;       // Lagrange stencil of the Alpert correction nodes
+constexpr int kAlpertJ = 10;       // correction nodes per side (order-10 log rule)
+constexpr int kAlpertA = 10;       // skipped grid neighbours per side
+
+// Pair class of a grid node pair (l target, m source).
+enum : uint8_t { kFar = 0, kNear = 1, kSkip = 2 };
+
+// One close (or correction) pair: geometry the split kernels need, complex
+// values stored as (re, im) doubles.  Layout shared by host and device.
+struct NearPair {
+    double2 d2;        // (rho~ - rho~')^2 + (z - z')^2
+    double2 rr;        // rho~ rho~'
+    double2 rho_t;     // target rho~
+    double2 rho_s;     // source rho~'
+    double2 nuc_r;     // source conormal (region a), rho component
+    double2 nuc_z;     // source conormal (region a), z component
+    double  dz;        // z - z' (target minus source, real on the curve)
+    int     tgt;       // target unknown l
+    int     src;       // grid-near: source unknown m; correction: correction index c
+    int     flags;     // bit 0: correction pair; bit 1: far-by-criterion (plain FFT);
+                       // bit 2: Taylor substitution (a point inside the PML)
+};
+
+enum { kFlagCorr = 1, kFlagFar = 2, kFlagSubst = 4 };
+
+struct HostTables {
+    int N = 0, Nt = 0, M = 0;
+    double h = 0;
+    std::vector<int> unk_grid;          // grid index of unknown l
+    std::vector<int> unk_of_grid;       // inverse (-1 at breakpoints)
+    // per unknown node
+    std::vector<double> t, rho, z, speed, nu_r, nu_z, I, Wu, Wphi;
+    std::vector<cd> rho_t, nuc_r, nuc_z;
+    // Alpert rule
+    std::vector<double> ax, aw;
+    // correction points
+    std::vector<int> corr_target;            // ncorr
+    std::vector<double> corr_tau;            // ncorr
+    std::vector<int> corr_m;                 // ncorr * kStencil (unknown or -1)
+    std::vector<double> corr_coef;           // ncorr * kStencil (w_k h L)
+    // classes and close pairs
+    std::vector<uint8_t> cls;                // N*N, [l][m]
+    std::vector<NearPair> near;              // grid-near pairs, then correction pairs
+    int n_grid_near = 0;
+    // diagonal
+    std::vector<double> Da, Db;
+};
+
+struct DeviceTables {
+    double *rho = nullptr, *z = nullptr, *I = nullptr, *Wu = nullptr, *Wphi = nullptr;
+    double2 *rho_t = nullptr, *nuc_r = nullptr, *nuc_z = nullptr;
+    uint8_t* cls = nullptr;
+    NearPair* near = nullptr;
+    int* corr_target = nullptr;
+    int* corr_m = nullptr;
+    double* corr_coef = nullptr;
+    double *Da = nullptr, *Db = nullptr;
+    double2* cos_tab = nullptr;   // (sin^2(psi_j/2), cos psi_j), j = 0..M/2
+    double2* twid = nullptr;      // e^{-2 pi i e / M}, e = 0..M-1
+};
+
+}  // namespace pmlbie
+
+struct pmlbie_problem {
+    pmlbie_params P;
+    std::vector<double> vertices;
+    double eta_split = 0;
+    pmlbie::HostTables H;
+    pmlbie::DeviceTables D;
+    int device = 0;
+    // workspace (allocated on first solve, grown as needed)
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    void* ws_extra = nullptr;   // device copies of per-node normals and speeds
+};
+
+namespace pmlbie {
+
+// errors
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+const char* error_text();
+#define PMLBIE_CUDA_TRY(call)                                                    \
+    do {                                                                         \
+        cudaError_t _e = (call);                                                 \
+        if (_e != cudaSuccess)                                                   \
+            return ::pmlbie::fail(PMLBIE_ECUDA, std::string(#call) + ": " +      \
+                                                    cudaGetErrorString(_e));     \
+    } while (0)
+
+// host setup (host.cpp)
+int build_tables(pmlbie_problem* prob);
+void alpert_log_rule(int j, int a, std::vector<double>& x, std::vector<double>& w);
+
+// kernels (kernels.cu)
+struct FarLaunch {
+    int mode_lo, mode_hi;
+    // system-matrix output (column-major 2N x 2N per mode) or raw kernels
+    double2* A;            // [mode][col][row], ld = 2N; may be null
+    double2* raw;          // [mode][kernel][l][m]; may be null
+};
+cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStream_t s);
+cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, double2* zd_scratch,
+                        double2* out, cudaStream_t s);
+cudaError_t launch_near_to_raw(const pmlbie_problem* prob, int mode_lo, int mode_hi,
+                               const double2* near_out, double2* raw, cudaStream_t s);
+cudaError_t launch_assemble(const pmlbie_problem* prob, int mode_lo, int mode_hi,
+                            const double2* near_out, double2* A, cudaStream_t s);
+// rhs_par: per rhs (sin phi, cos phi, R.re, R.im, k*.re, k*.im); nu_r, nu_z, speed per node
+cudaError_t launch_rhs(const pmlbie_problem* prob, int n_rhs, const double* rhs_par_dev,
+                       const double* nu_r, const double* nu_z, const double* speed,
+                       double2* b1, double2* b2, cudaStream_t s);
+cudaError_t launch_block_rhs(const pmlbie_problem* prob, int n_rhs, const double2* A,
+                             const double2* b1, const double2* b2, double2* B, cudaStream_t s);
+cudaError_t launch_outputs(const pmlbie_problem* prob, int n_rhs, const double2* X,
+                           const double2* b1, const double2* b2, double2* u1, double2* phi1,
+                           double2* u2, double2* phi2, cudaStream_t s);
+
+// dense batched linear algebra (lu.cu)
+template <typename T>
+cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s);
+template <typename T>
+cudaError_t batched_lu_solve(int n, int batch, int nrhs, const T* LU, const int* piv, T* B,
+                             cudaStream_t s);
+cudaError_t convert_to_c64(int64_t count, const double2* src, float2* dst, cudaStream_t s);
+cudaError_t residual_c128(int n, int batch, int nrhs, const double2* A, const double2* X,
+                          const double2* B, double2* R, double* rnorm, double* bnorm,
+                          cudaStream_t s);
+cudaError_t refine_step(int n, int batch, int nrhs, const float2* LU32, const int* piv,
+                        const double2* R, float2* work32, double2* X, cudaStream_t s);
+
+}  // namespace pmlbie

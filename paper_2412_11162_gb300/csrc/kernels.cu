@@ -1,0 +1,824 @@
+// CUDA kernels of the PML-BIE modal solver (sm_103a): modal kernels of far and
+// close node pairs, Alpert assembly of the per-mode block systems, and the
+// right-hand sides.  FP64 (complex128) arithmetic throughout.
+//
+// Wang & Lu, arXiv 2412.11162:
+//   Sec. 3.1 / 4.3  G~ = e^{i w |dr|}/(4 pi |dr|), |dr|^2 = d^2 + 4 rho~ rho~' sin^2(psi/2)
+//   Sec. 4.1        K~ = D e^{iq}(1 - iq), D = -[nu'_c,rho (rho~' - rho~ cos psi)
+//                   + nu'_c,z (z' - z)] / (4 pi |dr|^3); modal kernels by FFT in psi
+//                   for far pairs, kernel split (Eqs. (s1), (k1)) for close pairs
+//   Sec. 4.3        cH1 / cH3 substitution (Eq. (ch1)) for pairs touching the PML
+//   Sec. 4.1        Alpert corrections with Lagrange interpolation, diagonal D
+//   Sec. 2, 4.2     reference field, b^1, b^2, transmission block system
+#include <cmath>
+
+#include "internal.h"
+
+namespace pmlbie {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kInv4Pi = 0.079577471545947667884;
+
+// ---------------------------------------------------------------------------
+// complex helpers (double2 = re, im)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 c2(double x, double y) { return make_double2(x, y); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return c2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return c2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return c2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return c2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 crcp(double2 a) {
+    // 1/a with scaling against overflow
+    double s = fmax(fabs(a.x), fabs(a.y));
+    double ax = a.x / s, ay = a.y / s;
+    double d = ax * ax + ay * ay;
+    return c2(ax / (d * s), -ay / (d * s));
+}
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) { return cmul(a, crcp(b)); }
+// principal square root (branch cut on the negative real axis)
+__device__ __forceinline__ double2 csqrt(double2 z) {
+    double r = hypot(z.x, z.y);
+    if (r == 0.0) return c2(0.0, 0.0);
+    if (z.x >= 0.0) {
+        double t = sqrt(0.5 * (r + z.x));
+        return c2(t, z.y / (2.0 * t));
+    }
+    double t = sqrt(0.5 * (r - z.x));
+    return c2(fabs(z.y) / (2.0 * t), copysign(t, z.y));
+}
+// e^{i q}
+__device__ __forceinline__ double2 cexpi(double2 q) {
+    double s, c;
+    sincos(q.x, &s, &c);
+    double m = exp(-q.y);
+    return c2(m * c, m * s);
+}
+__device__ __forceinline__ double2 clog(double2 z) { return c2(log(hypot(z.x, z.y)), atan2(z.y, z.x)); }
+
+// ---------------------------------------------------------------------------
+// Warp-cooperative Stockham FFT (forward, e^{-2 pi i k n / M}) in shared
+// memory, radices 4, 2, 3 (M = 2^a 3^b).  x, y: two buffers of M elements;
+// returns the buffer holding the result.  tw[e] = e^{-2 pi i e / M}.
+// ---------------------------------------------------------------------------
+__device__ double2* warp_fft(double2* x, double2* y, int M, const double2* tw, int lane) {
+    int rem = M, Ns = 1;
+    while (rem > 1) {
+        int R = (rem % 4 == 0) ? 4 : ((rem % 2 == 0) ? 2 : 3);
+        int MR = M / R, step = M / (Ns * R);
+        for (int j = lane; j < MR; j += 32) {
+            int k = j % Ns;
+            double2 v[4];
+            for (int r = 0; r < R; ++r) v[r] = x[j + r * MR];
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[(r * k * step) % M]);
+            if (R == 2) {
+                double2 a = v[0], b = v[1];
+                v[0] = cadd(a, b);
+                v[1] = csub(a, b);
+            } else if (R == 4) {
+                double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+                double2 t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
+                v[0] = cadd(t0, t2);
+                v[2] = csub(t0, t2);
+                v[1] = c2(t1.x + t3.y, t1.y - t3.x);   // t1 - i t3
+                v[3] = c2(t1.x - t3.y, t1.y + t3.x);   // t1 + i t3
+            } else {
+                const double s3 = 0.86602540378443864676;   // sin(2 pi / 3)
+                double2 a = v[0], b = v[1], c = v[2];
+                double2 bc = cadd(b, c), bmc = csub(b, c);
+                v[0] = cadd(a, bc);
+                double2 m = c2(a.x - 0.5 * bc.x, a.y - 0.5 * bc.y);
+                // w = e^{-2 pi i/3}: a + w b + w^2 c = m - i s3 (b - c)
+                v[1] = c2(m.x + s3 * bmc.y, m.y - s3 * bmc.x);
+                v[2] = c2(m.x - s3 * bmc.y, m.y + s3 * bmc.x);
+            }
+            int idxD = (j / Ns) * Ns * R + k;
+            for (int r = 0; r < R; ++r) y[idxD + r * Ns] = v[r];
+        }
+        __syncwarp();
+        double2* t = x;
+        x = y;
+        y = t;
+        Ns *= R;
+        rem /= R;
+    }
+    return x;
+}
+
+// FFT of buf (length M) using scratch; the result ends in buf.
+__device__ void warp_fft_inplace(double2* buf, double2* scratch, int M, const double2* tw, int lane) {
+    double2* r = warp_fft(buf, scratch, M, tw, lane);
+    if (r != buf) {
+        for (int i = lane; i < M; i += 32) buf[i] = r[i];
+        __syncwarp();
+    }
+}
+
+// Per-pair geometry of a grid pair from node tables.
+struct PairGeom {
+    double2 d2, rr, nd0, ndc;   // N_D(psi) = nd0 - ndc cos psi (region a normal)
+};
+
+__device__ __forceinline__ PairGeom grid_pair(const DeviceTables& T, int l, int m) {
+    PairGeom g;
+    double dr = T.rho[l] - T.rho[m], dI = T.I[l] - T.I[m], dz = T.z[l] - T.z[m];
+    double2 drt = c2(dr, dI);
+    g.d2 = cadd(cmul(drt, drt), c2(dz * dz, 0.0));
+    g.rr = cmul(T.rho_t[l], T.rho_t[m]);
+    double2 ncr = T.nuc_r[m], ncz = T.nuc_z[m];
+    // nu'_r (rho~' - rho~ cos psi) + nu'_z (z' - z)
+    g.nd0 = cadd(cmul(ncr, T.rho_t[m]), cscale(ncz, -dz));
+    g.ndc = cmul(ncr, T.rho_t[l]);
+    return g;
+}
+
+// ---------------------------------------------------------------------------
+// Far pairs: sample both regions' S~, K~ at psi_j (j = 0..M/2, even
+// extension), FFT, and write the weighted modal entries into the per-mode
+// block matrices (or the raw modal-kernel buffer).
+// ---------------------------------------------------------------------------
+struct FarArgs {
+    DeviceTables T;
+    int N, M, mode_lo, mode_hi;
+    double w1, w2, h;
+    double2* A;     // [mode][col][row], ld 2N
+    double2* raw;   // [mode][kernel][l][m]
+};
+
+__global__ void far_kernel(FarArgs a) {
+    extern __shared__ double2 smem[];
+    const int M = a.M, N = a.N;
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double2* tw = smem;                         // M
+    double2* cs = tw + M;                       // M/2 + 1: (sin^2(psi/2), cos psi)
+    double2* buf = cs + (M / 2 + 1) + warp * 5 * M;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = a.T.twid[i];
+    for (int i = threadIdx.x; i <= M / 2; i += blockDim.x) cs[i] = a.T.cos_tab[i];
+    __syncthreads();
+
+    const int m = blockIdx.y;
+    const int l = blockIdx.x * nw + warp;
+    bool active = l < N && a.T.cls[(size_t)l * N + m] == kFar;
+    if (active) {
+        PairGeom g = grid_pair(a.T, l, m);
+        for (int j = lane; j <= M / 2; j += 32) {
+            double2 sc = cs[j];
+            double2 D2 = cadd(g.d2, cscale(g.rr, 4.0 * sc.x));
+            double2 R = csqrt(D2);
+            double2 iR = crcp(R);
+            double2 iR3 = cmul(iR, cmul(iR, iR));
+            double2 ND = csub(g.nd0, cscale(g.ndc, sc.y));
+            double2 Dk = cscale(cmul(ND, iR3), -kInv4Pi);   // region a
+            double2 v[4];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                double w = r == 0 ? a.w1 : a.w2;
+                double2 q = cscale(R, w);
+                double2 e = cexpi(q);
+                v[2 * r] = cscale(cmul(e, iR), kInv4Pi);
+                double2 K = cmul(cmul(Dk, e), c2(1.0 + q.y, -q.x));   // (1 - i q)
+                v[2 * r + 1] = r == 0 ? K : cscale(K, -1.0);           // region b: normal -nu
+            }
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                buf[s * M + j] = v[s];
+                if (j > 0 && j < M / 2) buf[s * M + M - j] = v[s];
+            }
+        }
+        __syncwarp();
+        for (int s = 0; s < 4; ++s) warp_fft_inplace(buf + s * M, buf + 4 * M, M, tw, lane);
+    }
+    __syncthreads();
+
+    const double scale = 2.0 * kPi / M;
+    const int nmodes = a.mode_hi - a.mode_lo;
+    if (a.A) {
+        const size_t ld = 2 * (size_t)N, msz = ld * ld;
+        const int total = nmodes * 4 * nw;
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            int w = idx % nw, blk = (idx / nw) % 4, n = idx / (4 * nw);
+            int ll = blockIdx.x * nw + w;
+            if (ll >= N) continue;
+            bool act = a.T.cls[(size_t)ll * N + m] == kFar;
+            const double2* b = smem + M + (M / 2 + 1) + w * 5 * M;
+            double2 val = c2(0.0, 0.0);
+            int row = ll, col = m;
+            // blocks: 0 K^a -> (l, m); 1 -S^a -> (l, N+m); 2 K^b -> (N+l, m); 3 S^b -> (N+l, N+m)
+            if (blk == 0) {
+                if (act) val = cscale(b[1 * M + a.mode_lo + n], scale * a.h * a.T.Wu[m]);
+            } else if (blk == 1) {
+                col = N + m;
+                if (act) val = cscale(b[0 * M + a.mode_lo + n], -scale * a.h * a.T.Wphi[m]);
+            } else if (blk == 2) {
+                row = N + ll;
+                if (act) val = cscale(b[3 * M + a.mode_lo + n], scale * a.h * a.T.Wu[m]);
+            } else {
+                row = N + ll;
+                col = N + m;
+                if (act) val = cscale(b[2 * M + a.mode_lo + n], scale * a.h * a.T.Wphi[m]);
+            }
+            a.A[(size_t)n * msz + (size_t)col * ld + row] = val;
+        }
+    }
+    if (a.raw) {
+        const size_t NN = (size_t)N * N;
+        const int total = nmodes * 4 * nw;
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            int w = idx % nw, kern = (idx / nw) % 4, n = idx / (4 * nw);
+            int ll = blockIdx.x * nw + w;
+            if (ll >= N) continue;
+            bool act = a.T.cls[(size_t)ll * N + m] == kFar;
+            const double2* b = smem + M + (M / 2 + 1) + w * 5 * M;
+            double2 val = act ? cscale(b[kern * M + a.mode_lo + n], scale) : c2(0.0, 0.0);
+            a.raw[((size_t)n * 4 + kern) * NN + (size_t)ll * N + m] = val;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Close pairs, stage 1 (one thread per pair): exact modal Laplace kernels
+//   Z^_m = c_m / (4 pi sqrt(2 rho~ rho~')),
+//   D^_m = -(2 rho~ rho~')^{-3/2} (A d_m + B c_m) / (4 pi),
+// c_m = int e^{-i m psi} (chi - cos psi)^{-1/2}, d_m likewise with power -3/2,
+// chi = 1 + d^2 / (2 rho~ rho~') (toroidal / Legendre Q_{m-1/2} functions).
+// c_0 = 4 K(k)/sqrt(chi+1), c_1 = chi c_0 - 4 sqrt(chi+1) E(k), k^2 = 2/(chi+1)
+// by the complex arithmetic-geometric mean; then the three-term recurrence
+// (2m+1) c_{m+1} = 4 m chi c_m - (2m-1) c_{m-1}, run upward when
+// Re(acosh chi) M < 2 and downward (Miller) otherwise;
+// d_m = (2m+1)(chi c_m - c_{m+1}) / (chi^2 - 1).
+// A = nu'.(r~' - r~) - nu'_rho d^2/(2 rho~'), B = nu'_rho rho~ (region a normal).
+// Output zd[p][0][m] = Z^_m, zd[p][1][m] = D^_m, m = 0..M-2.
+// ---------------------------------------------------------------------------
+struct NearArgs {
+    DeviceTables T;
+    const NearPair* np;
+    int npairs, N, M, L, mode_lo, mode_hi;
+    double w1, w2;
+    double2* zd;     // [p][2][M]
+    double2* out;    // [p][4][nmodes]
+    double2 pa[8], pb[8];   // Taylor coefficients of cH1 (pa) and cH3 (pb)
+};
+
+__device__ void complex_agm_KE(double2 k2, double2 kp, double2& K, double2& E) {
+    double2 a = c2(1.0, 0.0), b = kp;
+    double2 sum = cscale(k2, 0.5);
+    double pw = 0.5;
+    for (int it = 0; it < 64; ++it) {
+        double2 an = cscale(cadd(a, b), 0.5);
+        double2 bn = csqrt(cmul(a, b));
+        // right choice of the square root: |an - bn| <= |an + bn|
+        double2 dm = csub(an, bn), dp = cadd(an, bn);
+        if (dm.x * dm.x + dm.y * dm.y > dp.x * dp.x + dp.y * dp.y) bn = cscale(bn, -1.0);
+        double2 cn = cscale(csub(a, b), 0.5);
+        pw *= 2.0;
+        sum = cadd(sum, cscale(cmul(cn, cn), pw));
+        a = an;
+        b = bn;
+        if (hypot(cn.x, cn.y) < 1e-17 * hypot(a.x, a.y)) break;
+    }
+    K = cscale(crcp(a), 0.5 * kPi);
+    E = cmul(K, csub(c2(1.0, 0.0), sum));
+}
+
+__global__ void near_laplace_kernel(NearArgs a) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.npairs) return;
+    NearPair q = a.np[p];
+    if (q.flags & kFlagFar) return;
+    const int M = a.M;
+    double2* Z = a.zd + (size_t)p * 2 * M;
+    double2* Dd = Z + M;
+    double2 rr2 = cscale(q.rr, 2.0);
+    double2 chim1 = cdiv(q.d2, rr2);                 // chi - 1
+    double2 chi = c2(1.0 + chim1.x, chim1.y);
+    double2 chip1 = c2(2.0 + chim1.x, chim1.y);      // chi + 1
+    double2 k2 = cdiv(c2(2.0, 0.0), chip1);
+    double2 kp = csqrt(cdiv(chim1, chip1));
+    double2 K, E;
+    complex_agm_KE(k2, kp, K, E);
+    double2 sq = csqrt(chip1);
+    double2 c0 = cscale(cdiv(K, sq), 4.0);
+    double2 c1 = csub(cmul(chi, c0), cscale(cmul(sq, E), 4.0));
+    // Re acosh(chi) = Re log(chi + sqrt(chi-1) sqrt(chi+1))
+    double2 eta = clog(cadd(chi, cmul(csqrt(chim1), sq)));
+    double reeta = fabs(eta.x);
+    // c_m for m = 0..M-1 into Z[] (temporarily)
+    if (reeta * M < 2.0) {
+        Z[0] = c0;
+        Z[1] = c1;
+        for (int m = 1; m + 1 < M; ++m) {
+            double2 t = csub(cscale(cmul(chi, Z[m]), 4.0 * m), cscale(Z[m - 1], 2.0 * m - 1.0));
+            Z[m + 1] = cscale(t, 1.0 / (2.0 * m + 1.0));
+        }
+    } else {
+        int ms = M + (int)ceil(40.0 / reeta);
+        double2 y1 = c2(0.0, 0.0), y0 = c2(1e-200, 0.0);   // y_{m+1}, y_m at m = ms
+        for (int m = ms; m >= 1; --m) {
+            // (2m-1) y_{m-1} = 4 m chi y_m - (2m+1) y_{m+1}
+            double2 t = csub(cscale(cmul(chi, y0), 4.0 * m), cscale(y1, 2.0 * m + 1.0));
+            double2 ym1 = cscale(t, 1.0 / (2.0 * m - 1.0));
+            y1 = y0;
+            y0 = ym1;
+            if (m - 1 < M) Z[m - 1] = ym1;
+            if (m - 1 >= M && fabs(y0.x) + fabs(y0.y) > 1e100) {
+                y0 = cscale(y0, 1e-100);
+                y1 = cscale(y1, 1e-100);
+            }
+        }
+        double2 f = cdiv(c0, Z[0]);
+        for (int m = 0; m < M; ++m) Z[m] = cmul(Z[m], f);
+    }
+    // A, B, prefactors
+    double2 drt = csub(q.rho_s, q.rho_t);   // rho~' - rho~
+    double2 A = cadd(cmul(q.nuc_r, drt), cscale(q.nuc_z, -q.dz));
+    A = csub(A, cdiv(cmul(q.nuc_r, q.d2), cscale(q.rho_s, 2.0)));
+    double2 B = cmul(q.nuc_r, q.rho_t);
+    double2 s2 = csqrt(rr2);
+    double2 iz = cscale(crcp(s2), kInv4Pi);                           // 1/(4 pi sqrt(2 rr))
+    double2 id = cscale(crcp(cmul(s2, cmul(s2, s2))), -kInv4Pi);      // -(2rr)^{-3/2}/(4 pi)
+    double2 den = crcp(cmul(chim1, chip1));                            // 1/(chi^2 - 1)
+    for (int m = 0; m + 1 < M; ++m) {
+        double2 cm = Z[m], cn = Z[m + 1];
+        double2 dm = cscale(cmul(csub(cmul(chi, cm), cn), den), 2.0 * m + 1.0);
+        Dd[m] = cmul(id, cadd(cmul(A, dm), cmul(B, cm)));
+        Z[m] = cmul(iz, cm);
+    }
+}
+
+__device__ __forceinline__ double2 cpoly(const double2* c, int deg, double2 q) {
+    double2 r = c[deg];
+    for (int k = deg - 1; k >= 0; --k) r = cadd(cmul(r, q), c[k]);
+    return r;
+}
+
+// Close pairs, stage 2 (one CTA of 4 warps per pair): samples of the smooth
+// factors f1, f3 and remainders r1, r3 (both regions; for PML pairs the
+// Taylor substitution of Sec. 4.3, otherwise H1 = cos q, H3 = cos q + q sin q),
+// eight FFTs, and the convolution
+//   S^_n = (1/2pi) sum_{|k| < M/2} Z^_{|n-k|} F1_k + R1_n   (K^_n with D^, F3, R3).
+// Correction pairs that are far by the criterion use the plain FFT.
+__global__ void near_modes_kernel(NearArgs a) {
+    extern __shared__ double2 smem[];
+    const int M = a.M, p = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double2* tw = smem;                 // M
+    double2* seq = tw + M;              // 8 * M
+    double2* scr = seq + 8 * M;         // 4 * M (one per warp)
+    for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = a.T.twid[i];
+    NearPair q = a.np[p];
+    const bool plain = (q.flags & kFlagFar) != 0;
+    const bool subst = (q.flags & kFlagSubst) != 0;
+    // sampling
+    double2 nd0 = cadd(cmul(q.nuc_r, q.rho_s), cscale(q.nuc_z, -q.dz));
+    double2 ndc = cmul(q.nuc_r, q.rho_t);
+    // polynomials: U1 = (1 - P1)/q = -sum_{k>=1} a_k q^{k-1}; V3 = ((1-iq) - P3)/q^3
+    double2 u1[8], v3[8];
+    for (int k = 0; k < 8; ++k) {
+        u1[k] = c2(0.0, 0.0);
+        v3[k] = c2(0.0, 0.0);
+    }
+    for (int k = 1; k <= a.L; ++k) u1[k - 1] = cscale(a.pa[k], -1.0);
+    for (int k = 3; k <= a.L; ++k) v3[k - 3] = cscale(a.pb[k], -1.0);
+    __syncthreads();
+    for (int j = threadIdx.x; j <= M / 2; j += blockDim.x) {
+        double2 sc = a.T.cos_tab[j];
+        double2 D2 = cadd(q.d2, cscale(q.rr, 4.0 * sc.x));
+        double2 R = csqrt(D2);
+        double2 ND = csub(nd0, cscale(ndc, sc.y));
+        double2 v[8];
+        for (int r = 0; r < 2; ++r) {
+            double w = r == 0 ? a.w1 : a.w2;
+            double sg = r == 0 ? 1.0 : -1.0;     // region b normal -nu
+            double2 qq = cscale(R, w);
+            double2 e = cexpi(qq);
+            if (plain) {
+                double2 iR = crcp(R);
+                double2 iR3 = cmul(iR, cmul(iR, iR));
+                double2 Dk = cscale(cmul(ND, iR3), -kInv4Pi * sg);
+                v[4 * r + 0] = cscale(cmul(e, iR), kInv4Pi);
+                v[4 * r + 1] = c2(0.0, 0.0);
+                v[4 * r + 2] = cmul(cmul(Dk, e), c2(1.0 + qq.y, -qq.x));
+                v[4 * r + 3] = c2(0.0, 0.0);
+            } else if (subst) {
+                v[4 * r + 0] = cmul(e, cpoly(a.pa, a.L, qq));                          // cH1
+                v[4 * r + 1] = cscale(cmul(e, cpoly(u1, a.L - 1, qq)), w * kInv4Pi);   // Z(e^{iq} - cH1)
+                v[4 * r + 2] = cmul(e, cpoly(a.pb, a.L, qq));                          // cH3
+                double2 t = cmul(cmul(ND, e), cpoly(v3, a.L - 3, qq));
+                v[4 * r + 3] = cscale(t, -w * w * w * kInv4Pi * sg);                   // D(e^{iq}(1-iq) - cH3)
+            } else {
+                // H1 = cos q, i Z H2 = (i w / 4 pi) sin(q)/q, H3 = cos q + q sin q,
+                // i D H4 = -(i w^3 / 4 pi) N_D (sin q - q cos q)/q^3   (q real here)
+                double qr = qq.x, s, c;
+                sincos(qr, &s, &c);
+                double sinc, h4;
+                if (fabs(qr) < 1e-3) {
+                    double q2 = qr * qr;
+                    sinc = 1.0 - q2 / 6.0 + q2 * q2 / 120.0;
+                } else {
+                    sinc = s / qr;
+                }
+                if (fabs(qr) < 1e-2) {
+                    double q2 = qr * qr;
+                    h4 = 1.0 / 3.0 - q2 / 30.0 + q2 * q2 / 840.0 - q2 * q2 * q2 / 45360.0;
+                } else {
+                    h4 = (s - qr * c) / (qr * qr * qr);
+                }
+                v[4 * r + 0] = c2(c, 0.0);
+                v[4 * r + 1] = c2(0.0, w * kInv4Pi * sinc);
+                v[4 * r + 2] = c2(c + qr * s, 0.0);
+                v[4 * r + 3] = cmul(ND, c2(0.0, -w * w * w * kInv4Pi * h4 * sg));
+            }
+        }
+        for (int s = 0; s < 8; ++s) {
+            seq[s * M + j] = v[s];
+            if (j > 0 && j < M / 2) seq[s * M + M - j] = v[s];
+        }
+    }
+    __syncthreads();
+    // eight FFTs, two per warp (plain pairs need only 0, 2, 4, 6)
+    for (int s = warp; s < 8; s += 4) {
+        if (plain && (s & 1)) continue;
+        warp_fft_inplace(seq + s * M, scr + warp * M, M, tw, lane);
+    }
+    __syncthreads();
+    const double scale = 2.0 * kPi / M;
+    const int nmodes = a.mode_hi - a.mode_lo;
+    double2* out = a.out + (size_t)p * 4 * nmodes;
+    const double2* Z = a.zd + (size_t)p * 2 * M;
+    const double2* Dd = Z + M;
+    for (int t = threadIdx.x; t < nmodes; t += blockDim.x) {
+        int n = a.mode_lo + t;
+        double2 o[4];
+        if (plain) {
+            o[0] = cscale(seq[0 * M + n], scale);
+            o[1] = cscale(seq[2 * M + n], scale);
+            o[2] = cscale(seq[4 * M + n], scale);
+            o[3] = cscale(seq[6 * M + n], scale);
+        } else {
+            double2 sa = c2(0, 0), sb = c2(0, 0), ka = c2(0, 0), kb = c2(0, 0);
+            for (int k = -(M / 2 - 1); k <= M / 2 - 1; ++k) {
+                int kk = k < 0 ? -k : k;
+                int mm = n - k;
+                mm = mm < 0 ? -mm : mm;
+                double2 z = Z[mm], d = Dd[mm];
+                sa = cadd(sa, cmul(z, seq[0 * M + kk]));
+                ka = cadd(ka, cmul(d, seq[2 * M + kk]));
+                sb = cadd(sb, cmul(z, seq[4 * M + kk]));
+                kb = csub(kb, cmul(d, seq[6 * M + kk]));   // region b: D^ -> -D^
+            }
+            const double c = scale / (2.0 * kPi);
+            o[0] = cadd(cscale(sa, c), cscale(seq[1 * M + n], scale));
+            o[1] = cadd(cscale(ka, c), cscale(seq[3 * M + n], scale));
+            o[2] = cadd(cscale(sb, c), cscale(seq[5 * M + n], scale));
+            o[3] = cadd(cscale(kb, c), cscale(seq[7 * M + n], scale));
+        }
+        // out[p][kernel][n]: kernel 0 S^a, 1 K^a, 2 S^b, 3 K^b
+        for (int s = 0; s < 4; ++s) out[(size_t)s * nmodes + t] = o[s];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Assembly.  Grid-near pairs overwrite their entries; correction pairs add
+// w_k h L_m(tau) W_m F^(r_l, r(tau)) into the stencil columns (atomics); the
+// diagonal -D^a, -D^b is added last.
+// ---------------------------------------------------------------------------
+struct AsmArgs {
+    DeviceTables T;
+    const NearPair* np;
+    int n_grid_near, npairs, N, mode_lo, mode_hi;
+    double h;
+    const double2* near_out;
+    double2* A;
+};
+
+__device__ __forceinline__ void put4(double2* A, size_t ld, size_t base, int N, int l, int m,
+                                     double2 Sa, double2 Ka, double2 Sb, double2 Kb, double wu,
+                                     double wphi, bool add) {
+    size_t i0 = base + (size_t)m * ld + l;             // K^a
+    size_t i1 = base + (size_t)(N + m) * ld + l;       // -S^a
+    size_t i2 = base + (size_t)m * ld + N + l;         // K^b
+    size_t i3 = base + (size_t)(N + m) * ld + N + l;   // S^b
+    double2 v0 = cscale(Ka, wu), v1 = cscale(Sa, -wphi), v2 = cscale(Kb, wu), v3 = cscale(Sb, wphi);
+    if (!add) {
+        A[i0] = v0;
+        A[i1] = v1;
+        A[i2] = v2;
+        A[i3] = v3;
+    } else {
+        double* d = reinterpret_cast<double*>(A);
+        atomicAdd(d + 2 * i0, v0.x);
+        atomicAdd(d + 2 * i0 + 1, v0.y);
+        atomicAdd(d + 2 * i1, v1.x);
+        atomicAdd(d + 2 * i1 + 1, v1.y);
+        atomicAdd(d + 2 * i2, v2.x);
+        atomicAdd(d + 2 * i2 + 1, v2.y);
+        atomicAdd(d + 2 * i3, v3.x);
+        atomicAdd(d + 2 * i3 + 1, v3.y);
+    }
+}
+
+__global__ void assemble_grid_near_kernel(AsmArgs a) {
+    const int nmodes = a.mode_hi - a.mode_lo;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)a.n_grid_near * nmodes) return;
+    int p = (int)(idx / nmodes), t = (int)(idx % nmodes);
+    NearPair q = a.np[p];
+    const double2* o = a.near_out + (size_t)p * 4 * nmodes;
+    size_t ld = 2 * (size_t)a.N;
+    int m = q.src;
+    put4(a.A, ld, (size_t)t * ld * ld, a.N, q.tgt, m, o[t], o[nmodes + t], o[2 * nmodes + t],
+         o[3 * nmodes + t], a.h * a.T.Wu[m], a.h * a.T.Wphi[m], false);
+}
+
+__global__ void assemble_corr_kernel(AsmArgs a) {
+    const int nmodes = a.mode_hi - a.mode_lo;
+    const int ncorr = a.npairs - a.n_grid_near;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)ncorr * kStencil * nmodes) return;
+    int t = (int)(idx % nmodes);
+    int sl = (int)((idx / nmodes) % kStencil);
+    int c = (int)(idx / ((size_t)nmodes * kStencil));
+    int m = a.T.corr_m[(size_t)c * kStencil + sl];
+    if (m < 0) return;
+    double coef = a.T.corr_coef[(size_t)c * kStencil + sl];
+    int p = a.n_grid_near + c;
+    NearPair q = a.np[p];
+    const double2* o = a.near_out + (size_t)p * 4 * nmodes;
+    size_t ld = 2 * (size_t)a.N;
+    put4(a.A, ld, (size_t)t * ld * ld, a.N, q.tgt, m, o[t], o[nmodes + t], o[2 * nmodes + t],
+         o[3 * nmodes + t], coef * a.T.Wu[m], coef * a.T.Wphi[m], true);
+}
+
+__global__ void assemble_diag_kernel(AsmArgs a) {
+    const int nmodes = a.mode_hi - a.mode_lo;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)a.N * nmodes) return;
+    int l = (int)(idx % a.N), t = (int)(idx / a.N);
+    size_t ld = 2 * (size_t)a.N, base = (size_t)t * ld * ld;
+    double2* e0 = a.A + base + (size_t)l * ld + l;        // (l, l): K^a - D^a
+    double2* e1 = a.A + base + (size_t)l * ld + a.N + l;  // (N+l, l): K^b - D^b
+    e0->x -= a.T.Da[l];
+    e1->x -= a.T.Db[l];
+}
+
+// close-pair values into the raw modal-kernel buffer [mode][kernel][l][m]
+__global__ void near_to_raw_kernel(const NearPair* np, int n_grid_near, int N, int nmodes,
+                                   const double2* near_out, double2* raw) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n_grid_near * nmodes * 4) return;
+    int t = (int)(idx % nmodes), kern = (int)((idx / nmodes) % 4), p = (int)(idx / (4 * (size_t)nmodes));
+    NearPair q = np[p];
+    raw[((size_t)t * 4 + kern) * N * N + (size_t)q.tgt * N + q.src] =
+        near_out[((size_t)p * 4 + kern) * nmodes + t];
+}
+
+// ---------------------------------------------------------------------------
+// Right-hand side (Sec. 2, Sec. 4.2): modes of -[u^{tot,0}] and
+// -|r'| [d_nu u^{tot,0}] at every node, plane wave of polar angle phi
+// (azimuth 0, so the samples are even in theta); one CTA per (node, rhs).
+// ---------------------------------------------------------------------------
+struct RhsArgs {
+    DeviceTables T;
+    const double* rhs_par;   // per rhs: sin phi, cos phi, R.re, R.im, ks.re, ks.im
+    const double* nu_r;
+    const double* nu_z;
+    const double* speed;
+    int N, M, nrhs;
+    double w1;
+    double2* b1;   // [mode][l][rhs]
+    double2* b2;
+};
+
+__global__ void rhs_kernel(RhsArgs a) {
+    extern __shared__ double2 sm[];
+    const int l = blockIdx.x, r = blockIdx.y, M = a.M;
+    double2* s1 = sm;
+    double2* s2 = sm + (M / 2 + 1);
+    const double* pr = a.rhs_par + 6 * r;
+    double sp = pr[0], cp = pr[1];
+    double2 R = c2(pr[2], pr[3]), ks = c2(pr[4], pr[5]);
+    double rho = a.T.rho[l], z = a.T.z[l], nr = a.nu_r[l], nz = a.nu_z[l], sp_l = a.speed[l];
+    double w1 = a.w1;
+    for (int j = threadIdx.x; j <= M / 2; j += blockDim.x) {
+        double th = 2.0 * kPi * j / M;
+        double x = rho * cos(th);
+        double2 lat = cexpi(c2(-w1 * sp * x, 0.0));
+        double2 ui = cmul(lat, cexpi(c2(-w1 * cp * z, 0.0)));
+        double2 ur = cmul(R, cmul(lat, cexpi(c2(w1 * cp * z, 0.0))));
+        double2 u1 = cadd(ui, ur);
+        double2 u2 = cmul(cadd(R, c2(1.0, 0.0)), cmul(lat, cexpi(cscale(ks, -z))));
+        double2 drho = c2(0.0, -w1 * sp * cos(th));     // d/drho factor of the lateral phase
+        double2 du1 = cadd(cscale(cmul(drho, u1), nr),
+                           cscale(cadd(cmul(c2(0.0, -w1 * cp), ui), cmul(c2(0.0, w1 * cp), ur)), nz));
+        double2 du2 = cadd(cscale(cmul(drho, u2), nr), cscale(cmul(c2(ks.y, -ks.x), u2), nz));
+        s1[j] = csub(u1, u2);
+        s2[j] = cscale(csub(du1, du2), sp_l);
+    }
+    __syncthreads();
+    const double scale = 2.0 * kPi / M;
+    for (int n = threadIdx.x; n < M / 2; n += blockDim.x) {
+        double2 t1 = cadd(s1[0], cscale(s1[M / 2], (n & 1) ? -1.0 : 1.0));
+        double2 t2 = cadd(s2[0], cscale(s2[M / 2], (n & 1) ? -1.0 : 1.0));
+        for (int j = 1; j < M / 2; ++j) {
+            // cos(n theta_j), exact index reduction
+            double c = cospi(2.0 * (double)((n * j) % M) / M);
+            t1 = cadd(t1, cscale(s1[j], 2.0 * c));
+            t2 = cadd(t2, cscale(s2[j], 2.0 * c));
+        }
+        size_t o = ((size_t)n * a.N + l) * a.nrhs + r;
+        a.b1[o] = cscale(t1, -scale);
+        a.b2[o] = cscale(t2, -scale);
+    }
+}
+
+// B_n = [0; A_n[N:2N, 0:N] b1 + A_n[N:2N, N:2N] b2], B laid out [mode][2N][rhs]
+__global__ void block_rhs_kernel(int N, int nmodes, int nrhs, const double2* A, const double2* b1,
+                                 const double2* b2, double2* B) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t n2 = 2 * (size_t)N;
+    if (idx >= (size_t)nmodes * n2 * nrhs) return;
+    int r = (int)(idx % nrhs);
+    int row = (int)((idx / nrhs) % n2);
+    int t = (int)(idx / (nrhs * n2));
+    double2 acc = c2(0.0, 0.0);
+    if (row >= N) {
+        const double2* An = A + (size_t)t * n2 * n2;
+        for (int c = 0; c < N; ++c) {
+            acc = cadd(acc, cmul(An[(size_t)c * n2 + row], b1[((size_t)t * N + c) * nrhs + r]));
+            acc = cadd(acc, cmul(An[(size_t)(N + c) * n2 + row], b2[((size_t)t * N + c) * nrhs + r]));
+        }
+    }
+    B[idx] = acc;
+}
+
+__global__ void outputs_kernel(int N, int nmodes, int nrhs, const double2* X, const double2* b1,
+                               const double2* b2, double2* u1, double2* phi1, double2* u2,
+                               double2* phi2) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)nmodes * N * nrhs) return;
+    int r = (int)(idx % nrhs);
+    int l = (int)((idx / nrhs) % N);
+    int t = (int)(idx / ((size_t)nrhs * N));
+    size_t n2 = 2 * (size_t)N;
+    double2 xu = X[((size_t)t * n2 + l) * nrhs + r];
+    double2 xp = X[((size_t)t * n2 + N + l) * nrhs + r];
+    if (u1) u1[idx] = xu;
+    if (phi1) phi1[idx] = xp;
+    if (u2) u2[idx] = csub(xu, b1[idx]);
+    if (phi2) phi2[idx] = csub(xp, b2[idx]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static int far_warps(int M) { return M <= 256 ? 8 : (M <= 512 ? 4 : 2); }
+
+cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStream_t s) {
+    const int N = prob->P.N, M = prob->P.M;
+    FarArgs a;
+    a.T = prob->D;
+    a.N = N;
+    a.M = M;
+    a.mode_lo = fl.mode_lo;
+    a.mode_hi = fl.mode_hi;
+    a.w1 = prob->P.k1;
+    a.w2 = prob->P.k2;
+    a.h = prob->H.h;
+    a.A = fl.A;
+    a.raw = fl.raw;
+    int nw = far_warps(M);
+    size_t smem = sizeof(double2) * ((size_t)M + M / 2 + 1 + (size_t)nw * 5 * M);
+    cudaError_t e = cudaFuncSetAttribute(far_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((N + nw - 1) / nw, N);
+    far_kernel<<<grid, 32 * nw, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+static void taylor_coeffs(int L, double2* pa, double2* pb) {
+    // P1 = Taylor_L[(1 + e^{-2iq})/2], P3 = Taylor_L[(1 + e^{-2iq})/2 - iq (1 - e^{-2iq})/2]
+    cd e[9];
+    double f = 1.0;
+    for (int k = 0; k <= L; ++k) {
+        if (k > 0) f *= k;
+        e[k] = std::pow(cd(0.0, -2.0), k) / f;
+    }
+    for (int k = 0; k < 8; ++k) {
+        pa[k] = make_double2(0, 0);
+        pb[k] = make_double2(0, 0);
+    }
+    for (int k = 0; k <= L; ++k) {
+        cd ak = ((k == 0 ? 1.0 : 0.0) + e[k]) / 2.0;
+        cd bk = ak;
+        if (k >= 1) bk += cd(0.0, -1.0) * ((k == 1 ? 1.0 : 0.0) - e[k - 1]) / 2.0;
+        pa[k] = make_double2(ak.real(), ak.imag());
+        pb[k] = make_double2(bk.real(), bk.imag());
+    }
+}
+
+cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, double2* zd,
+                        double2* out, cudaStream_t s) {
+    const int M = prob->P.M;
+    NearArgs a;
+    a.T = prob->D;
+    a.np = prob->D.near;
+    a.npairs = (int)prob->H.near.size();
+    a.N = prob->P.N;
+    a.M = M;
+    a.L = prob->P.taylor_L;
+    a.mode_lo = mode_lo;
+    a.mode_hi = mode_hi;
+    a.w1 = prob->P.k1;
+    a.w2 = prob->P.k2;
+    a.zd = zd;
+    a.out = out;
+    taylor_coeffs(a.L, a.pa, a.pb);
+    if (a.npairs == 0) return cudaSuccess;
+    near_laplace_kernel<<<(a.npairs + 127) / 128, 128, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    size_t smem = sizeof(double2) * (size_t)M * 13;
+    e = cudaFuncSetAttribute(near_modes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    near_modes_kernel<<<a.npairs, 128, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_near_to_raw(const pmlbie_problem* prob, int mode_lo, int mode_hi,
+                               const double2* near_out, double2* raw, cudaStream_t s) {
+    int ng = prob->H.n_grid_near, nm = mode_hi - mode_lo;
+    size_t tot = (size_t)ng * nm * 4;
+    if (tot == 0) return cudaSuccess;
+    near_to_raw_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(prob->D.near, ng, prob->P.N, nm,
+                                                                     near_out, raw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(const pmlbie_problem* prob, int mode_lo, int mode_hi,
+                            const double2* near_out, double2* A, cudaStream_t s) {
+    AsmArgs a;
+    a.T = prob->D;
+    a.np = prob->D.near;
+    a.n_grid_near = prob->H.n_grid_near;
+    a.npairs = (int)prob->H.near.size();
+    a.N = prob->P.N;
+    a.mode_lo = mode_lo;
+    a.mode_hi = mode_hi;
+    a.h = prob->H.h;
+    a.near_out = near_out;
+    a.A = A;
+    const int nm = mode_hi - mode_lo;
+    size_t t1 = (size_t)a.n_grid_near * nm;
+    if (t1) assemble_grid_near_kernel<<<(unsigned)((t1 + 255) / 256), 256, 0, s>>>(a);
+    size_t t2 = (size_t)(a.npairs - a.n_grid_near) * kStencil * nm;
+    if (t2) assemble_corr_kernel<<<(unsigned)((t2 + 255) / 256), 256, 0, s>>>(a);
+    size_t t3 = (size_t)a.N * nm;
+    assemble_diag_kernel<<<(unsigned)((t3 + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs(const pmlbie_problem* prob, int n_rhs, const double* rhs_par_dev,
+                            const double* nu_r, const double* nu_z, const double* speed,
+                            double2* b1, double2* b2, cudaStream_t s) {
+    RhsArgs a;
+    a.T = prob->D;
+    a.rhs_par = rhs_par_dev;
+    a.nu_r = nu_r;
+    a.nu_z = nu_z;
+    a.speed = speed;
+    a.N = prob->P.N;
+    a.M = prob->P.M;
+    a.nrhs = n_rhs;
+    a.w1 = prob->P.k1;
+    a.b1 = b1;
+    a.b2 = b2;
+    dim3 grid(a.N, n_rhs);
+    size_t smem = sizeof(double2) * 2 * (a.M / 2 + 1);
+    rhs_kernel<<<grid, 128, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_rhs(const pmlbie_problem* prob, int n_rhs, const double2* A,
+                             const double2* b1, const double2* b2, double2* B, cudaStream_t s) {
+    int N = prob->P.N, nm = prob->P.M / 2;
+    size_t tot = (size_t)nm * 2 * N * n_rhs;
+    block_rhs_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(N, nm, n_rhs, A, b1, b2, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_outputs(const pmlbie_problem* prob, int n_rhs, const double2* X,
+                           const double2* b1, const double2* b2, double2* u1, double2* phi1,
+                           double2* u2, double2* phi2, cudaStream_t s) {
+    int N = prob->P.N, nm = prob->P.M / 2;
+    size_t tot = (size_t)nm * N * n_rhs;
+    outputs_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(N, nm, n_rhs, X, b1, b2, u1, phi1,
+                                                               u2, phi2);
+    return cudaGetLastError();
+}
+
+}  // namespace pmlbie

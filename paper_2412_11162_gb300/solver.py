@@ -1,0 +1,57 @@
+"""Convenience wrapper over the C ABI (device buffers from torch)."""
+import numpy as np
+
+from . import binding as B
+
+
+class Problem:
+    """One problem instance: host tables built at construction, device upload on
+    first use.  Parameters follow pmlbie_params (include/pmlbie.h)."""
+
+    def __init__(self, k1, k2, N, M, **kw):
+        self.params, self._keep = B.make_params(k1, k2, N, M, **kw)
+        self.N, self.M = N, M
+        self.handle = B.pmlbie_create(self.params)
+
+    def close(self):
+        if self.handle:
+            B.pmlbie_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_modes(self):
+        return self.M // 2
+
+    def nodes(self):
+        return B.pmlbie_nodes(self.handle, self.N)
+
+    def diagonal(self):
+        return B.pmlbie_diagonal(self.handle, self.N)
+
+    def near_count(self):
+        return B.pmlbie_near_count(self.handle)
+
+    def modal_kernels(self, mode_lo=0, mode_hi=None, stream=None):
+        import torch
+        mode_hi = self.n_modes if mode_hi is None else mode_hi
+        out = torch.empty((mode_hi - mode_lo, 4, self.N, self.N), dtype=torch.complex128, device="cuda")
+        B.pmlbie_modal_kernels(self.handle, mode_lo, mode_hi, out, stream)
+        return out
+
+    def solve(self, polar, precision=B.PMLBIE_FP64, stream=None, outputs=None, allow_noconverge=False):
+        """Device solve; returns (dict of [mode][node][rhs] complex128 tensors, report)."""
+        import torch
+        pol = np.atleast_1d(np.asarray(polar, dtype=np.float64))
+        if outputs is None:
+            shape = (self.n_modes, self.N, len(pol))
+            outputs = {k: torch.empty(shape, dtype=torch.complex128, device="cuda")
+                       for k in ("u1", "phi1", "u2", "phi2")}
+        rep = B.pmlbie_solve(self.handle, precision, pol, outputs["u1"], outputs["phi1"], outputs["u2"],
+                             outputs["phi2"], stream, allow_noconverge=allow_noconverge)
+        return outputs, rep

@@ -1,0 +1,87 @@
+"""C-ABI library: loads, exports every declared symbol, and its host-side setup
+(geometry, Alpert table, diagonal term, parameter checks) agrees with the oracle.
+No GPU compute is called here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2412_11162_gb300 import build as bld
+    if not os.path.exists(bld.OUT):
+        bld.build()
+    from paper_2412_11162_gb300 import binding
+    return binding
+
+
+def test_exports_every_declared_symbol(B):
+    hdr = open(os.path.join(ROOT, "include", "pmlbie.h")).read()
+    declared = set(re.findall(r"\b(pmlbie_[a-z_]+)\s*\(", hdr))
+    assert declared == set(B.EXPORTS)
+    lib = ctypes.CDLL(B.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_alpert_rule_matches_oracle_table(B):
+    from oracle.assemble import alpert_table
+    x, w = B.pmlbie_alpert_rule(10, 10)
+    xo, wo, a = alpert_table()
+    assert np.allclose(x, xo, rtol=2e-15, atol=0) and np.allclose(w, wo, rtol=2e-15, atol=0)
+
+
+def test_host_tables_match_oracle(B):
+    from paper_2412_11162_gb300 import Problem
+    from oracle.assemble import Quadrature, diagonal
+    from oracle.problem import Geometry, Params
+    P = Problem(2 * np.pi, 3 * np.pi, 128, 64)
+    nd = P.nodes()
+    G = Geometry(Params(k1=2 * np.pi, k2=3 * np.pi, N=128, M=64))
+    assert np.abs(G.nodes["rho"] - nd["rho"]).max() < 1e-15
+    assert np.abs(G.nodes["z"] - nd["z"]).max() < 1e-15
+    assert np.abs(G.nodes["speed"] - nd["speed"]).max() < 1e-14 * np.abs(nd["speed"]).max()
+    Da, Db = P.diagonal()
+    Dao, Dbo = diagonal(G, Quadrature(G))
+    # identical away from the r = 1 corner; within 1e-9 at the nodes next to it,
+    # where both sides lose digits to separations near the FP64 position spacing
+    assert np.median(np.abs(Da - Dao)) < 1e-14
+    assert np.abs(Da - Dao).max() < 2e-9 and np.abs(Db - Dbo).max() < 2e-9
+    assert np.abs(Da + Db + 2).max() < 1e-13
+
+
+def test_polyline_host_tables(B):
+    from paper_2412_11162_gb300 import Problem
+    from oracle.problem import Geometry, Params
+    V = [(0.0, -1.0), (1.0, -1.0), (1.0, 0.0), (4.0, 0.0)]
+    P = Problem(2 * np.pi, 2 * np.pi, 120, 48, a1=2.0, T=2.0, S=2.0, curve="polyline", vertices=V)
+    G = Geometry(Params(k1=2 * np.pi, k2=2 * np.pi, N=120, M=48, a1=2.0, T=2.0, S=2.0, curve="polyline",
+                        vertices=V))
+    nd = P.nodes()
+    assert np.abs(G.nodes["rho"] - nd["rho"]).max() < 1e-15
+    assert np.abs(G.nodes["z"] - nd["z"]).max() < 1e-15
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(M=50), "M must be"), (dict(N=8), "N must be"), (dict(k1=-1.0), "wavenumbers"),
+    (dict(T=0.0), "PML"), (dict(taylor_L=9), "taylor_L"), (dict(bump_R=3.0), "bump"),
+])
+def test_parameter_checks(B, kw, frag):
+    base = dict(k1=2 * np.pi, k2=3 * np.pi, N=128, M=64)
+    base.update(kw)
+    k1, k2, N, M = base.pop("k1"), base.pop("k2"), base.pop("N"), base.pop("M")
+    params, keep = B.make_params(k1, k2, N, M, **base)
+    with pytest.raises(B.PmlbieError) as e:
+        B.pmlbie_create(params)
+    assert e.value.code == B.PMLBIE_EINVAL and frag in str(e.value)
+
+
+def test_polyline_must_start_on_axis(B):
+    params, keep = B.make_params(1.0, 1.0, 64, 32, curve="polyline", vertices=[(0.5, -1.0), (3.5, 0.0)])
+    with pytest.raises(B.PmlbieError):
+        B.pmlbie_create(params)

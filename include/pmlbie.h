@@ -84,9 +84,13 @@ typedef struct {
     int      near_pairs;          /* close pairs evaluated with the kernel split       */
     int      refine_iters;        /* max refinement iterations over modes (mixed)      */
     double   residual;            /* max over modes/RHS of ||B - A x|| / ||B||         */
-    double   ms_kernels;          /* device time: modal kernels + assembly (ms)        */
+    double   ms_kernels;          /* device time: modal kernels + assembly + rhs (ms)  */
     double   ms_lu;               /* device time: factorisation (ms)                   */
-    double   ms_solve;            /* device time: solves + refinement (ms)             */
+    double   ms_solve;            /* device time: solves + refinement + outputs (ms)   */
+    double   ms_far;              /* device time of the far-pair kernel launch (ms)    */
+    double   ms_near;             /* device time of the close-pair kernels (ms)        */
+    double   ms_assemble;         /* device time of Alpert assembly + diagonal (ms)    */
+    int      launches;            /* CUDA kernel launches issued by the call           */
 } pmlbie_report;
 
 typedef struct pmlbie_problem pmlbie_problem;   /* opaque, owned by the library */

@@ -38,7 +38,9 @@ class pmlbie_params(ctypes.Structure):
 class pmlbie_report(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("n_modes", ctypes.c_int), ("near_pairs", ctypes.c_int),
                 ("refine_iters", ctypes.c_int), ("residual", ctypes.c_double),
-                ("ms_kernels", ctypes.c_double), ("ms_lu", ctypes.c_double), ("ms_solve", ctypes.c_double)]
+                ("ms_kernels", ctypes.c_double), ("ms_lu", ctypes.c_double), ("ms_solve", ctypes.c_double),
+                ("ms_far", ctypes.c_double), ("ms_near", ctypes.c_double), ("ms_assemble", ctypes.c_double),
+                ("launches", ctypes.c_int)]
 
 
 EXPORTS = ["pmlbie_create", "pmlbie_destroy", "pmlbie_last_error", "pmlbie_nodes", "pmlbie_diagonal",

@@ -174,13 +174,17 @@ void fresnel(double w1, double w2, double phi, double* out6) {
     out6[5] = ks.imag();
 }
 
-// modal kernels + assembly into w.A (all modes)
-int build_system(pmlbie_problem* prob, Workspace& w, cudaStream_t s) {
+// modal kernels + assembly into w.A (all modes); ev[0..3] bracket the stages
+int build_system(pmlbie_problem* prob, Workspace& w, cudaStream_t s, cudaEvent_t* ev) {
     const int nm = prob->P.M / 2;
     FarLaunch fl{0, nm, w.A, nullptr};
+    PMLBIE_CUDA_TRY(cudaEventRecord(ev[0], s));
     PMLBIE_CUDA_TRY(launch_far(prob, fl, s));
+    PMLBIE_CUDA_TRY(cudaEventRecord(ev[1], s));
     PMLBIE_CUDA_TRY(launch_near(prob, 0, nm, w.zd, w.nout, s));
+    PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
     PMLBIE_CUDA_TRY(launch_assemble(prob, 0, nm, w.nout, w.A, s));
+    PMLBIE_CUDA_TRY(cudaEventRecord(ev[3], s));
     return PMLBIE_OK;
 }
 
@@ -324,14 +328,17 @@ int pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* p
     Workspace w;
     if ((rc = get_workspace(prob, precision, n_rhs, w))) return rc;
     const int N = prob->P.N, nm = prob->P.M / 2, n2 = 2 * N;
-    cudaEvent_t ev[4];
+    cudaEvent_t ev[4], sev[4];
     for (auto& e : ev) PMLBIE_CUDA_TRY(cudaEventCreate(&e));
+    for (auto& e : sev) PMLBIE_CUDA_TRY(cudaEventCreate(&e));
     struct EvGuard {
         cudaEvent_t* e;
+        cudaEvent_t* f;
         ~EvGuard() {
-            for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+            for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]), cudaEventDestroy(f[i]);
         }
-    } guard{ev};
+    } guard{ev, sev};
+    g_launches = 0;
 
     std::vector<double> rpar(6 * n_rhs);
     for (int r = 0; r < n_rhs; ++r) fresnel(prob->P.k1, prob->P.k2, polar[r], &rpar[6 * r]);
@@ -339,7 +346,7 @@ int pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* p
     pmlbie_dev_extra* ex = extra_of(prob);
 
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[0], s));
-    if ((rc = build_system(prob, w, s))) return rc;
+    if ((rc = build_system(prob, w, s, sev))) return rc;
     PMLBIE_CUDA_TRY(launch_rhs(prob, n_rhs, w.rpar, ex->nu_r, ex->nu_z, ex->speed, w.b1, w.b2, s));
     PMLBIE_CUDA_TRY(launch_block_rhs(prob, n_rhs, w.A, w.b1, w.b2, w.B, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[1], s));
@@ -392,6 +399,14 @@ int pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* p
         rep->ms_kernels = t01;
         rep->ms_lu = t12;
         rep->ms_solve = t23;
+        float f01, f12, f23;
+        cudaEventElapsedTime(&f01, sev[0], sev[1]);
+        cudaEventElapsedTime(&f12, sev[1], sev[2]);
+        cudaEventElapsedTime(&f23, sev[2], sev[3]);
+        rep->ms_far = f01;
+        rep->ms_near = f12;
+        rep->ms_assemble = f23;
+        rep->launches = (int)g_launches;
     }
     for (int i = 0; i < nm; ++i)
         if (info[i]) return fail(PMLBIE_ESINGULAR, "zero pivot in mode " + std::to_string(i));

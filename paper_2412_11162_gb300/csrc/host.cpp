@@ -45,6 +45,7 @@ inline real pi_() { return 4 * atanl((real)1); }
 }  // namespace q128
 
 static thread_local std::string g_err = "no error";
+thread_local long g_launches = 0;
 void set_error(const std::string& msg) { g_err = msg; }
 int fail(int code, const std::string& msg) {
     g_err = msg;

@@ -91,6 +91,10 @@ struct pmlbie_problem {
 
 namespace pmlbie {
 
+// kernel launches issued by the library on this thread (read by the API calls)
+extern thread_local long g_launches;
+inline void count_launch(long n = 1) { g_launches += n; }
+
 // errors
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);

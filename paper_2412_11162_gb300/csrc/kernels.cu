@@ -697,6 +697,7 @@ cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStre
     if (e != cudaSuccess) return e;
     dim3 grid((N + nw - 1) / nw, N);
     far_kernel<<<grid, 32 * nw, smem, s>>>(a);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -740,12 +741,14 @@ cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, do
     taylor_coeffs(a.L, a.pa, a.pb);
     if (a.npairs == 0) return cudaSuccess;
     near_laplace_kernel<<<(a.npairs + 127) / 128, 128, 0, s>>>(a);
+    count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     size_t smem = sizeof(double2) * (size_t)M * 13;
     e = cudaFuncSetAttribute(near_modes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     near_modes_kernel<<<a.npairs, 128, smem, s>>>(a);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -756,6 +759,7 @@ cudaError_t launch_near_to_raw(const pmlbie_problem* prob, int mode_lo, int mode
     if (tot == 0) return cudaSuccess;
     near_to_raw_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(prob->D.near, ng, prob->P.N, nm,
                                                                      near_out, raw);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -774,11 +778,12 @@ cudaError_t launch_assemble(const pmlbie_problem* prob, int mode_lo, int mode_hi
     a.A = A;
     const int nm = mode_hi - mode_lo;
     size_t t1 = (size_t)a.n_grid_near * nm;
-    if (t1) assemble_grid_near_kernel<<<(unsigned)((t1 + 255) / 256), 256, 0, s>>>(a);
+    if (t1) assemble_grid_near_kernel<<<(unsigned)((t1 + 255) / 256), 256, 0, s>>>(a), count_launch();
     size_t t2 = (size_t)(a.npairs - a.n_grid_near) * kStencil * nm;
-    if (t2) assemble_corr_kernel<<<(unsigned)((t2 + 255) / 256), 256, 0, s>>>(a);
+    if (t2) assemble_corr_kernel<<<(unsigned)((t2 + 255) / 256), 256, 0, s>>>(a), count_launch();
     size_t t3 = (size_t)a.N * nm;
     assemble_diag_kernel<<<(unsigned)((t3 + 255) / 256), 256, 0, s>>>(a);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -800,6 +805,7 @@ cudaError_t launch_rhs(const pmlbie_problem* prob, int n_rhs, const double* rhs_
     dim3 grid(a.N, n_rhs);
     size_t smem = sizeof(double2) * 2 * (a.M / 2 + 1);
     rhs_kernel<<<grid, 128, smem, s>>>(a);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -808,6 +814,7 @@ cudaError_t launch_block_rhs(const pmlbie_problem* prob, int n_rhs, const double
     int N = prob->P.N, nm = prob->P.M / 2;
     size_t tot = (size_t)nm * 2 * N * n_rhs;
     block_rhs_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(N, nm, n_rhs, A, b1, b2, B);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -818,6 +825,7 @@ cudaError_t launch_outputs(const pmlbie_problem* prob, int n_rhs, const double2*
     size_t tot = (size_t)nm * N * n_rhs;
     outputs_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(N, nm, n_rhs, X, b1, b2, u1, phi1,
                                                                u2, phi2);
+    count_launch();
     return cudaGetLastError();
 }
 

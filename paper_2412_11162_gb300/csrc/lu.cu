@@ -291,6 +291,7 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
     for (int k0 = 0; k0 < n; k0 += kNB) {
         int kb = std::min(kNB, n - k0);
         panel_kernel<T><<<batch, kPanelThreads, 0, s>>>(n, k0, kb, A, piv, info);
+        count_launch(2);
         dim3 g1((n + 127) / 128, batch);
         swap_trsm_kernel<T><<<g1, 128, 0, s>>>(n, k0, kb, A, piv);
         int rem = n - k0 - kb;
@@ -298,6 +299,7 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
             constexpr int TL = GemmTile<T>::v;
             dim3 g2((rem + TL - 1) / TL, (rem + TL - 1) / TL, batch);
             gemm_update_kernel<T><<<g2, 256, 0, s>>>(n, k0, kb, A);
+            count_launch();
         }
     }
     return cudaGetLastError();
@@ -308,6 +310,7 @@ cudaError_t batched_lu_solve(int n, int batch, int nrhs, const T* LU, const int*
                              cudaStream_t s) {
     dim3 g(batch, nrhs);
     lu_solve_kernel<T><<<g, 256, 0, s>>>(n, nrhs, LU, piv, B);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -321,6 +324,7 @@ template cudaError_t batched_lu_solve<float2>(int, int, int, const float2*, cons
 cudaError_t convert_to_c64(int64_t count, const double2* src, float2* dst, cudaStream_t s) {
     int blocks = (int)std::min<int64_t>((count + 255) / 256, 152 * 32);
     c128_to_c64_kernel<<<blocks, 256, 0, s>>>(count, src, dst);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -333,6 +337,7 @@ cudaError_t residual_c128(int n, int batch, int nrhs, const double2* A, const do
     if (e != cudaSuccess) return e;
     dim3 g((unsigned)(((size_t)n * nrhs + 255) / 256), batch);
     residual_kernel<<<g, 256, 0, s>>>(n, nrhs, A, X, B, R, rnorm, bnorm);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -344,6 +349,7 @@ cudaError_t refine_step(int n, int batch, int nrhs, const float2* LU32, const in
     e = batched_lu_solve<float2>(n, batch, nrhs, LU32, piv, work32, s);
     if (e != cudaSuccess) return e;
     add_correction_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(cnt, work32, X);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -142,6 +142,29 @@ size_t pmlbie_workspace_bytes(const pmlbie_problem* prob, int precision, int n_r
 int  pmlbie_modal_kernels(pmlbie_problem* prob, int mode_lo, int mode_hi, void* dev_out,
                           void* stream);
 
+/* Allocation-free variant of pmlbie_modal_kernels (the paper has no
+ * counterpart: this is a deployment convenience).  For callers that must not
+ * call cudaMalloc while they run (a framework whose own allocator owns the
+ * device memory budget, or an embedding that forbids driver allocations
+ * after start-up).  Same output, layout and arguments as
+ * pmlbie_modal_kernels; the close-pair scratch lives in one file-scope device
+ * array of 64 MiB per device (held by every device that loads the library
+ * until the process exits) instead of being allocated.
+ *   - The problem's tables must already be on the current device (a prior
+ *     pmlbie_modal_kernels or pmlbie_solve on it); otherwise EINVAL.
+ *   - Problems whose close-pair scratch, N_close * (2 M + 4 (mode_hi -
+ *     mode_lo)) * 16 bytes, exceeds 64 MiB are rejected with EINVAL (ask
+ *     for fewer modes per call, or use pmlbie_modal_kernels).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the array: calls whose work overlaps on the GPU (for
+ *     instance on two streams) race; order them on one stream.  Nothing in
+ *     the array needs to start at zero.
+ *   - The call is stream-ordered and does not synchronise: dev_out is ready
+ *     when the stream reaches the end of the call's work. */
+int  pmlbie_modal_kernels_noalloc(pmlbie_problem* prob, int mode_lo, int mode_hi, void* dev_out,
+                                  void* stream);
+
 /* Full solve for plane waves of polar angles polar[0..n_rhs-1] (azimuth 0),
  * Sec. 4.1-4.2: kernels, split, Alpert assembly, diagonal, right-hand side,
  * batched LU per mode, solves (and FP64 refinement for PMLBIE_MIXED).

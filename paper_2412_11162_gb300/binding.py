@@ -45,6 +45,7 @@ class pmlbie_report(ctypes.Structure):
 
 EXPORTS = ["pmlbie_create", "pmlbie_destroy", "pmlbie_last_error", "pmlbie_nodes", "pmlbie_diagonal",
            "pmlbie_near_count", "pmlbie_alpert_rule", "pmlbie_workspace_bytes", "pmlbie_modal_kernels",
+           "pmlbie_modal_kernels_noalloc",
            "pmlbie_solve", "pmlbie_solve_host"]
 
 
@@ -67,12 +68,13 @@ def _load():
     lib.pmlbie_workspace_bytes.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     lib.pmlbie_workspace_bytes.restype = ctypes.c_size_t
     lib.pmlbie_modal_kernels.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.pmlbie_modal_kernels_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp]
     lib.pmlbie_solve.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, vp, vp, vp, vp, vp,
                                  ctypes.POINTER(pmlbie_report)]
     lib.pmlbie_solve_host.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, vp,
                                       ctypes.POINTER(pmlbie_report)]
     for f in ("pmlbie_nodes", "pmlbie_diagonal", "pmlbie_near_count", "pmlbie_alpert_rule",
-              "pmlbie_modal_kernels", "pmlbie_solve", "pmlbie_solve_host"):
+              "pmlbie_modal_kernels", "pmlbie_modal_kernels_noalloc", "pmlbie_solve", "pmlbie_solve_host"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -171,6 +173,13 @@ def pmlbie_workspace_bytes(h, precision, n_rhs):
 def pmlbie_modal_kernels(h, mode_lo, mode_hi, out, stream=None):
     """out: complex128 CUDA tensor of (mode_hi-mode_lo)*4*N*N elements."""
     check(lib.pmlbie_modal_kernels(h, mode_lo, mode_hi, _tptr(out), _stream(stream)), "pmlbie_modal_kernels")
+    return out
+
+
+def pmlbie_modal_kernels_noalloc(h, mode_lo, mode_hi, out, stream=None):
+    """Allocation-free modal kernels into out (same layout as pmlbie_modal_kernels)."""
+    check(lib.pmlbie_modal_kernels_noalloc(h, mode_lo, mode_hi, _tptr(out), _stream(stream)),
+          "pmlbie_modal_kernels_noalloc")
     return out
 
 

@@ -103,6 +103,15 @@ void free_device(pmlbie_problem* prob) {
     prob->ws = nullptr;
 }
 
+}  // namespace
+
+bool pmlbie::device_ready(const pmlbie_problem* prob) {
+    return prob && prob->ws_extra &&
+           reinterpret_cast<const pmlbie_dev_extra*>(prob->ws_extra)->ready;
+}
+
+namespace {
+
 // workspace carve-up of one solve
 struct Workspace {
     double2 *A = nullptr, *zd = nullptr, *nout = nullptr, *b1 = nullptr, *b2 = nullptr, *B = nullptr,

@@ -107,6 +107,9 @@ const char* error_text();
                                                     cudaGetErrorString(_e));     \
     } while (0)
 
+// true once the problem's tables are on the device (api.cu)
+bool device_ready(const pmlbie_problem* prob);
+
 // host setup (host.cpp)
 int build_tables(pmlbie_problem* prob);
 void alpert_log_rule(int j, int a, std::vector<double>& x, std::vector<double>& w);

@@ -16,7 +16,7 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
-CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I" + os.path.join(CUDA, "include")]
+CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-pthread", "-ffp-contract=off", "-I" + os.path.join(CUDA, "include")]
 
 
 def _run(cmd):
@@ -39,7 +39,7 @@ def build(verbose=False):
         logs = list(ex.map(_run, jobs))
     objs = [os.path.join(BUILD, s + ".o") for s in srcs_cu + srcs_cc]
     extra = ["-lquadmath"] if platform.machine() in ("x86_64", "AMD64") else []
-    _run([NVCC, "-shared", "-o", OUT] + objs + ARCH + ["-lcudart"] + extra)
+    _run([NVCC, "-shared", "-o", OUT] + objs + ARCH + ["-lcudart", "-lpthread"] + extra)
     if verbose:
         for l in logs:
             sys.stderr.write(l)

@@ -74,13 +74,15 @@ int ensure_device(pmlbie_problem* prob) {
         (rc = upload(D.corr_coef, H.corr_coef)) || (rc = upload(D.Da, H.Da)) || (rc = upload(D.Db, H.Db)))
         return rc;
     const int M = prob->P.M;
-    std::vector<double2> cs(M / 2 + 1), tw(M);
+    std::vector<double2> cs(M / 2 + 1), tw(M), tw2(2 * M);
+    for (int e = 0; e < 2 * M; ++e)
+        tw2[e] = make_double2(std::cos(kPi * e / M), -std::sin(kPi * e / M));
     for (int j = 0; j <= M / 2; ++j) {
         double s = std::sin(kPi * j / M);
         cs[j] = make_double2(s * s, std::cos(2.0 * kPi * j / M));
     }
     for (int e = 0; e < M; ++e) tw[e] = make_double2(std::cos(2.0 * kPi * e / M), -std::sin(2.0 * kPi * e / M));
-    if ((rc = upload(D.cos_tab, cs)) || (rc = upload(D.twid, tw))) return rc;
+    if ((rc = upload(D.cos_tab, cs)) || (rc = upload(D.twid, tw)) || (rc = upload(D.twid2, tw2))) return rc;
     if ((rc = upload(ex->nu_r, H.nu_r)) || (rc = upload(ex->nu_z, H.nu_z)) || (rc = upload(ex->speed, H.speed)))
         return rc;
     ex->ready = true;
@@ -90,7 +92,7 @@ int ensure_device(pmlbie_problem* prob) {
 void free_device(pmlbie_problem* prob) {
     DeviceTables& D = prob->D;
     void* ptrs[] = {D.rho, D.z, D.I, D.Wu, D.Wphi, D.rho_t, D.nuc_r, D.nuc_z, D.cls, D.near,
-                    D.corr_target, D.corr_m, D.corr_coef, D.Da, D.Db, D.cos_tab, D.twid};
+                    D.corr_target, D.corr_m, D.corr_coef, D.Da, D.Db, D.cos_tab, D.twid, D.twid2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     pmlbie_dev_extra* ex = extra_of(prob);
@@ -117,7 +119,7 @@ struct Workspace {
     double2 *A = nullptr, *zd = nullptr, *nout = nullptr, *b1 = nullptr, *b2 = nullptr, *B = nullptr,
             *X = nullptr, *R = nullptr;
     float2 *A32 = nullptr, *w32 = nullptr;
-    int *piv = nullptr, *info = nullptr;
+    int *piv = nullptr, *info = nullptr, *active = nullptr;
     double *rn = nullptr, *bn = nullptr, *rpar = nullptr;
     size_t bytes = 0;
 };
@@ -148,6 +150,7 @@ Workspace plan(const pmlbie_problem* prob, int precision, int nrhs, char* base) 
     w.X = (double2*)take(sizeof(double2) * nm * n2 * nrhs);
     w.piv = (int*)take(sizeof(int) * nm * n2);
     w.info = (int*)take(sizeof(int) * nm);
+    w.active = (int*)take(sizeof(int) * nm);
     w.rn = (double*)take(sizeof(double) * nm * nrhs);
     w.bn = (double*)take(sizeof(double) * nm * nrhs);
     w.rpar = (double*)take(sizeof(double) * 6 * nrhs);
@@ -363,6 +366,7 @@ int pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* p
     const size_t xbytes = sizeof(double2) * (size_t)nm * n2 * n_rhs;
     int iters = 0;
     double resid = 0.0;
+    std::vector<double> mres(nm, 0.0);
     if (precision == PMLBIE_FP64) {
         PMLBIE_CUDA_TRY(batched_lu<double2>(n2, nm, w.A, w.piv, w.info, s));
         PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
@@ -374,20 +378,37 @@ int pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* p
         PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
         PMLBIE_CUDA_TRY(cudaMemsetAsync(w.X, 0, xbytes, s));
         PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.R, w.B, xbytes, cudaMemcpyDeviceToDevice, s));
+        // refinement: FP64 residual with the FP64 matrix, FP32 correction solve; modes whose
+        // residual is already below the tolerance for every rhs are left alone
         std::vector<double> rn((size_t)nm * n_rhs), bn((size_t)nm * n_rhs);
+        std::vector<int> act(nm, 1);
         const int max_iter = 30;
+        const double tol = 1e-13;
+        PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.active, act.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, s));
         for (iters = 0; iters <= max_iter; ++iters) {
             if (iters > 0) {
-                PMLBIE_CUDA_TRY(residual_c128(n2, nm, n_rhs, w.A, w.X, w.B, w.R, w.rn, w.bn, s));
+                PMLBIE_CUDA_TRY(residual_c128(n2, nm, n_rhs, w.A, w.X, w.B, w.R, w.rn, w.bn, s, w.active));
                 PMLBIE_CUDA_TRY(cudaMemcpyAsync(rn.data(), w.rn, sizeof(double) * rn.size(), cudaMemcpyDeviceToHost, s));
                 PMLBIE_CUDA_TRY(cudaMemcpyAsync(bn.data(), w.bn, sizeof(double) * bn.size(), cudaMemcpyDeviceToHost, s));
                 PMLBIE_CUDA_TRY(cudaStreamSynchronize(s));
                 resid = 0.0;
-                for (size_t i = 0; i < rn.size(); ++i)
-                    if (bn[i] > 0) resid = std::max(resid, std::sqrt(rn[i] / bn[i]));
-                if (resid <= 1e-13 || iters == max_iter) break;
+                int nact = 0;
+                for (int mo = 0; mo < nm; ++mo) {
+                    if (!act[mo]) continue;
+                    double worst = 0.0;
+                    for (int r = 0; r < n_rhs; ++r) {
+                        size_t i = (size_t)mo * n_rhs + r;
+                        if (bn[i] > 0) worst = std::max(worst, std::sqrt(rn[i] / bn[i]));
+                    }
+                    mres[mo] = worst;
+                    if (worst <= tol) act[mo] = 0;
+                    else ++nact;
+                }
+                resid = *std::max_element(mres.begin(), mres.end());
+                if (nact == 0 || iters == max_iter) break;
+                PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.active, act.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, s));
             }
-            PMLBIE_CUDA_TRY(refine_step(n2, nm, n_rhs, w.A32, w.piv, w.R, w.w32, w.X, s));
+            PMLBIE_CUDA_TRY(refine_step(n2, nm, n_rhs, w.A32, w.piv, w.R, w.w32, w.X, s, w.active));
         }
     }
     PMLBIE_CUDA_TRY(launch_outputs(prob, n_rhs, w.X, w.b1, w.b2, (double2*)dev_u1, (double2*)dev_phi1,

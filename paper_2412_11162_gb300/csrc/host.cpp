@@ -13,6 +13,7 @@
 #include <cstring>
 #include <mutex>
 #include <stdexcept>
+#include <thread>
 
 #include "internal.h"
 
@@ -57,6 +58,25 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 const q128::real kPiQ = q128::pi_();
+
+// Run f(lo, hi) over [0, n) split into contiguous chunks on the host cores.
+template <typename F>
+void parallel_rows(int n, F f) {
+    int nt = (int)std::thread::hardware_concurrency();
+    nt = std::max(1, std::min(nt, 64));
+    if (n < 64 || nt == 1) {
+        f(0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    int chunk = (n + nt - 1) / nt;
+    for (int t = 0; t < nt; ++t) {
+        int lo = t * chunk, hi = std::min(n, lo + chunk);
+        if (lo >= hi) break;
+        th.emplace_back([=, &f] { f(lo, hi); });
+    }
+    for (auto& x : th) x.join();
+}
 
 // ---------------------------------------------------------------------------
 // Gauss-Legendre nodes on [-1, 1] (Newton on P_n).
@@ -119,8 +139,11 @@ struct Pml {
         }
         return tot;
     }
-    // I(r1) - I(r2) integrated directly over [r2, r1]
-    double delta(double r1, double r2) const {
+    // I(r1) - I(r2): integrated directly over [r2, r1] when the two radii are
+    // close (where the difference of tabulated values would cancel), else the
+    // difference of the tabulated integrals I1, I2.
+    double delta(double r1, double r2, double I1, double I2) const {
+        if (std::fabs(r1 - r2) > 0.05 * T) return I1 - I2;
         return r1 >= r2 ? integral(r2, r1) : -integral(r1, r2);
     }
 };
@@ -604,7 +627,7 @@ int build_tables(pmlbie_problem* prob) {
     const double eta = prob->eta_split;
     auto make_pair = [&](int l, double rs, double zs, double Is, cd rts, cd ncr, cd ncz,
                          NearPair& np) -> bool {
-        double dI = (H.rho[l] > P.a1 || rs > P.a1) ? pml.delta(H.rho[l], rs) : 0.0;
+        double dI = (H.rho[l] > P.a1 || rs > P.a1) ? pml.delta(H.rho[l], rs, H.I[l], Is) : 0.0;
         cd drt(H.rho[l] - rs, dI);
         double dz = H.z[l] - zs;
         cd d2 = drt * drt + dz * dz;
@@ -620,24 +643,36 @@ int build_tables(pmlbie_problem* prob) {
         np.dz = dz;
         np.tgt = l;
         np.flags = (H.I[l] > 0 || Is > 0) ? kFlagSubst : 0;
-        (void)Is;
         return re_sqrt < eta;
     };
     H.cls.assign((size_t)N * N, kFar);
     H.near.clear();
-    for (int l = 0; l < N; ++l) {
-        for (int m = 0; m < N; ++m) {
-            if (std::abs(H.unk_grid[l] - H.unk_grid[m]) < kAlpertA) {
-                H.cls[(size_t)l * N + m] = kSkip;
-                continue;
-            }
-            NearPair np;
-            if (make_pair(l, H.rho[m], H.z[m], H.I[m], H.rho_t[m], H.nuc_r[m], H.nuc_z[m], np)) {
-                np.src = m;
-                H.cls[(size_t)l * N + m] = kNear;
-                H.near.push_back(np);
-            }
+    {
+        int nt = std::max(1, std::min((int)std::thread::hardware_concurrency(), 64));
+        std::vector<std::vector<NearPair>> part(nt);
+        int chunk = (N + nt - 1) / nt;
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; ++t) {
+            int lo = t * chunk, hi = std::min(N, lo + chunk);
+            if (lo >= hi) break;
+            th.emplace_back([&, t, lo, hi] {
+                for (int l = lo; l < hi; ++l)
+                    for (int m = 0; m < N; ++m) {
+                        if (std::abs(H.unk_grid[l] - H.unk_grid[m]) < kAlpertA) {
+                            H.cls[(size_t)l * N + m] = kSkip;
+                            continue;
+                        }
+                        NearPair np;
+                        if (make_pair(l, H.rho[m], H.z[m], H.I[m], H.rho_t[m], H.nuc_r[m], H.nuc_z[m], np)) {
+                            np.src = m;
+                            H.cls[(size_t)l * N + m] = kNear;
+                            part[t].push_back(np);
+                        }
+                    }
+            });
         }
+        for (auto& x : th) x.join();
+        for (auto& v : part) H.near.insert(H.near.end(), v.begin(), v.end());
     }
     H.n_grid_near = (int)H.near.size();
     for (int c = 0; c < ncorr; ++c) {
@@ -654,15 +689,17 @@ int build_tables(pmlbie_problem* prob) {
     H.Da.assign(N, 0.0);
     H.Db.assign(N, 0.0);
     std::vector<double> K0(N, 0.0);
-    for (int l = 0; l < N; ++l) {
-        double s = 0;
-        for (int m = 0; m < N; ++m) {
-            if (H.cls[(size_t)l * N + m] == kSkip) continue;
-            s += H.h * H.Wu[m] *
-                 laplace_dl0(H.rho[l], H.z[l], H.rho[m], H.z[m], H.nu_r[m], H.nu_z[m]);
+    parallel_rows(N, [&](int lo, int hi) {
+        for (int l = lo; l < hi; ++l) {
+            double s = 0;
+            for (int m = 0; m < N; ++m) {
+                if (H.cls[(size_t)l * N + m] == kSkip) continue;
+                s += H.h * H.Wu[m] *
+                     laplace_dl0(H.rho[l], H.z[l], H.rho[m], H.z[m], H.nu_r[m], H.nu_z[m]);
+            }
+            K0[l] = s;
         }
-        K0[l] = s;
-    }
+    });
     for (int c = 0; c < ncorr; ++c) {
         int l = H.corr_target[c];
         const CP& q = cpts[c];
@@ -672,12 +709,14 @@ int build_tables(pmlbie_problem* prob) {
             if (m >= 0) K0[l] += H.corr_coef[(size_t)c * kStencil + a] * H.Wu[m] * v;
         }
     }
-    for (int l = 0; l < N; ++l) {
-        double Od = disc_solid_angle(H.rho[l], H.z[l], Lr);
-        double Op = H.z[l] > 0 ? 4.0 * kPi - Od : (H.z[l] < 0 ? Od : 2.0 * kPi);
-        H.Da[l] = K0[l] - Op / (2.0 * kPi);
-        H.Db[l] = -K0[l] - (4.0 * kPi - Op) / (2.0 * kPi);
-    }
+    parallel_rows(N, [&](int lo, int hi) {
+        for (int l = lo; l < hi; ++l) {
+            double Od = disc_solid_angle(H.rho[l], H.z[l], Lr);
+            double Op = H.z[l] > 0 ? 4.0 * kPi - Od : (H.z[l] < 0 ? Od : 2.0 * kPi);
+            H.Da[l] = K0[l] - Op / (2.0 * kPi);
+            H.Db[l] = -K0[l] - (4.0 * kPi - Op) / (2.0 * kPi);
+        }
+    });
     return PMLBIE_OK;
 }
 

@@ -72,6 +72,7 @@ struct DeviceTables {
     double *Da = nullptr, *Db = nullptr;
     double2* cos_tab = nullptr;   // (sin^2(psi_j/2), cos psi_j), j = 0..M/2
     double2* twid = nullptr;      // e^{-2 pi i e / M}, e = 0..M-1
+    double2* twid2 = nullptr;     // e^{-2 pi i e / (2M)}, e = 0..2M-1
 };
 
 }  // namespace pmlbie
@@ -141,14 +142,16 @@ cudaError_t launch_outputs(const pmlbie_problem* prob, int n_rhs, const double2*
 // dense batched linear algebra (lu.cu)
 template <typename T>
 cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s);
+// active: optional per-matrix flags (0 = skip), used to leave converged modes alone
 template <typename T>
 cudaError_t batched_lu_solve(int n, int batch, int nrhs, const T* LU, const int* piv, T* B,
-                             cudaStream_t s);
+                             cudaStream_t s, const int* active = nullptr);
 cudaError_t convert_to_c64(int64_t count, const double2* src, float2* dst, cudaStream_t s);
 cudaError_t residual_c128(int n, int batch, int nrhs, const double2* A, const double2* X,
                           const double2* B, double2* R, double* rnorm, double* bnorm,
-                          cudaStream_t s);
+                          cudaStream_t s, const int* active = nullptr);
 cudaError_t refine_step(int n, int batch, int nrhs, const float2* LU32, const int* piv,
-                        const double2* R, float2* work32, double2* X, cudaStream_t s);
+                        const double2* R, float2* work32, double2* X, cudaStream_t s,
+                        const int* active = nullptr);
 
 }  // namespace pmlbie

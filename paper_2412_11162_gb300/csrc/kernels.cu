@@ -247,7 +247,7 @@ __global__ void far_kernel(FarArgs a) {
 // c_0 = 4 K(k)/sqrt(chi+1), c_1 = chi c_0 - 4 sqrt(chi+1) E(k), k^2 = 2/(chi+1)
 // by the complex arithmetic-geometric mean; then the three-term recurrence
 // (2m+1) c_{m+1} = 4 m chi c_m - (2m-1) c_{m-1}, run upward when
-// Re(acosh chi) M < 2 and downward (Miller) otherwise;
+// Re(acosh chi) M < 3.5 and downward (Miller) otherwise;
 // d_m = (2m+1)(chi c_m - c_{m+1}) / (chi^2 - 1).
 // A = nu'.(r~' - r~) - nu'_rho d^2/(2 rho~'), B = nu'_rho rho~ (region a normal).
 // Output zd[p][0][m] = Z^_m, zd[p][1][m] = D^_m, m = 0..M-2.
@@ -260,6 +260,7 @@ struct NearArgs {
     double2* zd;     // [p][2][M]
     double2* out;    // [p][4][nmodes]
     double2 pa[8], pb[8];   // Taylor coefficients of cH1 (pa) and cH3 (pb)
+    int conv_fft;           // convolution by length-2M FFTs (M <= 512) or directly
 };
 
 __device__ void complex_agm_KE(double2 k2, double2 kp, double2& K, double2& E) {
@@ -306,7 +307,9 @@ __global__ void near_laplace_kernel(NearArgs a) {
     double2 eta = clog(cadd(chi, cmul(csqrt(chim1), sq)));
     double reeta = fabs(eta.x);
     // c_m for m = 0..M-1 into Z[] (temporarily)
-    if (reeta * M < 2.0) {
+    // upward recurrence loses at most e^{2 Re(eta) M} < e^7 (about 3 digits of 16);
+    // Miller's downward recurrence from ms has relative error e^{-2 Re(eta) (ms - M)} < 1e-17
+    if (reeta * M < 3.5) {
         Z[0] = c0;
         Z[1] = c1;
         for (int m = 1; m + 1 < M; ++m) {
@@ -314,7 +317,7 @@ __global__ void near_laplace_kernel(NearArgs a) {
             Z[m + 1] = cscale(t, 1.0 / (2.0 * m + 1.0));
         }
     } else {
-        int ms = M + (int)ceil(40.0 / reeta);
+        int ms = M + (int)ceil(20.0 / reeta);
         double2 y1 = c2(0.0, 0.0), y0 = c2(1e-200, 0.0);   // y_{m+1}, y_m at m = ms
         for (int m = ms; m >= 1; --m) {
             // (2m-1) y_{m-1} = 4 m chi y_m - (2m+1) y_{m+1}
@@ -366,7 +369,7 @@ __global__ void near_modes_kernel(NearArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double2* tw = smem;                 // M
     double2* seq = tw + M;              // 8 * M
-    double2* scr = seq + 8 * M;         // 4 * M (one per warp)
+    double2* scr = seq + 8 * M;         // 4 * M (one per warp), or 4 * 2M with the FFT convolution
     for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = a.T.twid[i];
     NearPair q = a.np[p];
     const bool plain = (q.flags & kFlagFar) != 0;
@@ -449,34 +452,86 @@ __global__ void near_modes_kernel(NearArgs a) {
     double2* out = a.out + (size_t)p * 4 * nmodes;
     const double2* Z = a.zd + (size_t)p * 2 * M;
     const double2* Dd = Z + M;
+    if (plain) {
+        for (int t = threadIdx.x; t < nmodes; t += blockDim.x) {
+            int n = a.mode_lo + t;
+            out[0 * (size_t)nmodes + t] = cscale(seq[0 * M + n], scale);
+            out[1 * (size_t)nmodes + t] = cscale(seq[2 * M + n], scale);
+            out[2 * (size_t)nmodes + t] = cscale(seq[4 * M + n], scale);
+            out[3 * (size_t)nmodes + t] = cscale(seq[6 * M + n], scale);
+        }
+        return;
+    }
+    if (a.conv_fft) {
+        // circular convolution of length L = 2M, exact for n in [0, M/2):
+        // zZ[m] = Z^_{|m|}, zD[m] = D^_{|m|} (|m| <= M-2), c[k] = C_{|k|} (|k| <= M/2-1);
+        // the two media are done one after the other with the same Z, D spectra
+        const int L = 2 * M;
+        double2* tw2 = scr + 4 * L;          // L twiddles
+        double2* zZ = tw2 + L;               // 4 sequences of length L
+        double2* zD = zZ + L;
+        double2* cS = zD + L;
+        double2* cK = cS + L;
+        for (int i = threadIdx.x; i < L; i += blockDim.x) tw2[i] = a.T.twid2[i];
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            int m = i <= L / 2 ? i : L - i;      // |index| on the circle
+            bool inz = m <= M - 2;
+            zZ[i] = inz ? Z[m] : c2(0.0, 0.0);
+            zD[i] = inz ? Dd[m] : c2(0.0, 0.0);
+        }
+        __syncthreads();
+        if (warp < 2) warp_fft_inplace(warp == 0 ? zZ : zD, scr + warp * L, L, tw2, lane);
+        const double c = 1.0 / (2.0 * kPi * L);
+        for (int r = 0; r < 2; ++r) {
+            const double sgn = r == 0 ? 1.0 : -1.0;      // region b: D^ -> -D^
+            for (int i = threadIdx.x; i < L; i += blockDim.x) {
+                int m = i <= L / 2 ? i : L - i;
+                bool in = m <= M / 2 - 1;
+                cS[i] = in ? cscale(seq[(4 * r + 0) * M + m], scale) : c2(0.0, 0.0);
+                cK[i] = in ? cscale(seq[(4 * r + 2) * M + m], scale) : c2(0.0, 0.0);
+            }
+            __syncthreads();
+            if (warp >= 2) warp_fft_inplace(warp == 2 ? cS : cK, scr + warp * L, L, tw2, lane);
+            __syncthreads();
+            // conjugated products, so the forward FFT gives L times the inverse transform
+            for (int i = threadIdx.x; i < L; i += blockDim.x) {
+                double2 v0 = cmul(zZ[i], cS[i]);
+                double2 v1 = cscale(cmul(zD[i], cK[i]), sgn);
+                cS[i] = c2(v0.x, -v0.y);
+                cK[i] = c2(v1.x, -v1.y);
+            }
+            __syncthreads();
+            if (warp >= 2) warp_fft_inplace(warp == 2 ? cS : cK, scr + warp * L, L, tw2, lane);
+            __syncthreads();
+            for (int t = threadIdx.x; t < nmodes; t += blockDim.x) {
+                int n = a.mode_lo + t;
+                double2 os = c2(cS[n].x * c, -cS[n].y * c);
+                double2 ok = c2(cK[n].x * c, -cK[n].y * c);
+                out[(2 * r + 0) * (size_t)nmodes + t] = cadd(os, cscale(seq[(4 * r + 1) * M + n], scale));
+                out[(2 * r + 1) * (size_t)nmodes + t] = cadd(ok, cscale(seq[(4 * r + 3) * M + n], scale));
+            }
+            __syncthreads();
+        }
+        return;
+    }
     for (int t = threadIdx.x; t < nmodes; t += blockDim.x) {
         int n = a.mode_lo + t;
-        double2 o[4];
-        if (plain) {
-            o[0] = cscale(seq[0 * M + n], scale);
-            o[1] = cscale(seq[2 * M + n], scale);
-            o[2] = cscale(seq[4 * M + n], scale);
-            o[3] = cscale(seq[6 * M + n], scale);
-        } else {
-            double2 sa = c2(0, 0), sb = c2(0, 0), ka = c2(0, 0), kb = c2(0, 0);
-            for (int k = -(M / 2 - 1); k <= M / 2 - 1; ++k) {
-                int kk = k < 0 ? -k : k;
-                int mm = n - k;
-                mm = mm < 0 ? -mm : mm;
-                double2 z = Z[mm], d = Dd[mm];
-                sa = cadd(sa, cmul(z, seq[0 * M + kk]));
-                ka = cadd(ka, cmul(d, seq[2 * M + kk]));
-                sb = cadd(sb, cmul(z, seq[4 * M + kk]));
-                kb = csub(kb, cmul(d, seq[6 * M + kk]));   // region b: D^ -> -D^
-            }
-            const double c = scale / (2.0 * kPi);
-            o[0] = cadd(cscale(sa, c), cscale(seq[1 * M + n], scale));
-            o[1] = cadd(cscale(ka, c), cscale(seq[3 * M + n], scale));
-            o[2] = cadd(cscale(sb, c), cscale(seq[5 * M + n], scale));
-            o[3] = cadd(cscale(kb, c), cscale(seq[7 * M + n], scale));
+        double2 sa = c2(0, 0), sb = c2(0, 0), ka = c2(0, 0), kb = c2(0, 0);
+        for (int k = -(M / 2 - 1); k <= M / 2 - 1; ++k) {
+            int kk = k < 0 ? -k : k;
+            int mm = n - k;
+            mm = mm < 0 ? -mm : mm;
+            double2 z = Z[mm], d = Dd[mm];
+            sa = cadd(sa, cmul(z, seq[0 * M + kk]));
+            ka = cadd(ka, cmul(d, seq[2 * M + kk]));
+            sb = cadd(sb, cmul(z, seq[4 * M + kk]));
+            kb = csub(kb, cmul(d, seq[6 * M + kk]));   // region b: D^ -> -D^
         }
-        // out[p][kernel][n]: kernel 0 S^a, 1 K^a, 2 S^b, 3 K^b
-        for (int s = 0; s < 4; ++s) out[(size_t)s * nmodes + t] = o[s];
+        const double c = scale / (2.0 * kPi);
+        out[0 * (size_t)nmodes + t] = cadd(cscale(sa, c), cscale(seq[1 * M + n], scale));
+        out[1 * (size_t)nmodes + t] = cadd(cscale(ka, c), cscale(seq[3 * M + n], scale));
+        out[2 * (size_t)nmodes + t] = cadd(cscale(sb, c), cscale(seq[5 * M + n], scale));
+        out[3 * (size_t)nmodes + t] = cadd(cscale(kb, c), cscale(seq[7 * M + n], scale));
     }
 }
 
@@ -744,7 +799,9 @@ cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, do
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    size_t smem = sizeof(double2) * (size_t)M * 13;
+    // FFT convolution: tw (M) + seq (8M) + scratch (4 x 2M) + tw2 (2M) + 4 x 2M buffers = 27M
+    a.conv_fft = M <= 512 ? 1 : 0;
+    size_t smem = sizeof(double2) * (size_t)M * (a.conv_fft ? 27 : 13);
     e = cudaFuncSetAttribute(near_modes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     near_modes_kernel<<<a.npairs, 128, smem, s>>>(a);

@@ -127,27 +127,96 @@ __global__ void panel_kernel(int n, int k0, int kb, T* A, int* piv, int* info) {
 
 // Row swaps of the panel applied to the columns outside it, then the
 // unit-lower solve U12 = L11^{-1} A12 for the columns right of the panel.
-// One thread per column.
+// One CTA per (64-column tile, matrix).  The tile's kb panel rows are loaded
+// (coalesced: each column's rows k0..k0+kb-1 are contiguous), every distinct
+// pivot row below the panel is gathered once, the swaps are replayed in order
+// in shared memory (one thread per column), the triangular solve runs on the
+// block in shared memory, and everything is written back.
+constexpr int kSwapCols = 64;
+
 template <typename T>
 __global__ void swap_trsm_kernel(int n, int k0, int kb, T* A, const int* piv) {
+    extern __shared__ unsigned char smraw[];
+    T* blk = reinterpret_cast<T*>(smraw);                 // [kSwapCols][2*kNB]: panel rows, then outside rows
+    T* L = blk + (size_t)kSwapCols * 2 * kNB;             // [kNB][kNB] (col-major), right tiles only
+    __shared__ int srow[2 * kNB];                         // global row of each smem row slot
+    __shared__ int sslot[kNB];                            // slot of pivot p_j
+    __shared__ int nslots;
     const int b = blockIdx.y;
     T* a = A + (size_t)b * n * n;
     const int* pv = piv + (size_t)b * n;
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n || (c >= k0 && c < k0 + kb)) return;
-    T* col = a + (size_t)c * n;
-    for (int j = k0; j < k0 + kb; ++j) {
-        int p = pv[j];
-        if (p != j) {
-            T t = col[j];
-            col[j] = col[p];
-            col[p] = t;
+    const int c0 = blockIdx.x * kSwapCols;
+    const int ncol = min(kSwapCols, n - c0);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        int ns = kb;
+        for (int r = 0; r < kb; ++r) srow[r] = k0 + r;
+        for (int j = 0; j < kb; ++j) {
+            int p = pv[k0 + j];
+            int slot = -1;
+            for (int q = 0; q < ns; ++q)
+                if (srow[q] == p) {
+                    slot = q;
+                    break;
+                }
+            if (slot < 0) {
+                slot = ns;
+                srow[ns++] = p;
+            }
+            sslot[j] = slot;
+        }
+        nslots = ns;
+    }
+    __syncthreads();
+    const int ns = nslots;
+    // load: slot r of column c at blk[c * 2kNB + r]
+    for (int idx = tid; idx < ncol * ns; idx += blockDim.x) {
+        int c = idx / ns, r = idx % ns;
+        int col = c0 + c;
+        bool in_panel = col >= k0 && col < k0 + kb;
+        if (!in_panel) blk[c * 2 * kNB + r] = a[(size_t)col * n + srow[r]];
+    }
+    const bool right = c0 + ncol > k0 + kb;
+    if (right)
+        for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
+            int j = idx / kb, i = idx % kb;          // L[i][j] at L[j*kNB + i]
+            L[j * kNB + i] = a[(size_t)(k0 + j) * n + k0 + i];
+        }
+    __syncthreads();
+    // replay the swaps: one thread per column
+    for (int c = tid; c < ncol; c += blockDim.x) {
+        int col = c0 + c;
+        if (col >= k0 && col < k0 + kb) continue;
+        T* x = blk + c * 2 * kNB;
+        for (int j = 0; j < kb; ++j) {
+            int s2 = sslot[j];
+            if (s2 != j) {
+                T t = x[j];
+                x[j] = x[s2];
+                x[s2] = t;
+            }
         }
     }
-    if (c < k0 + kb) return;
-    for (int j = k0; j < k0 + kb; ++j) {
-        T x = col[j];
-        for (int i = j + 1; i < k0 + kb; ++i) col[i] = fms(col[i], a[(size_t)j * n + i], x);
+    __syncthreads();
+    // unit-lower solve on the right columns: rows parallel, j sequential
+    if (right) {
+        for (int j = 0; j < kb; ++j) {
+            for (int idx = tid; idx < ncol * kb; idx += blockDim.x) {
+                int c = idx / kb, i = idx % kb;
+                int col = c0 + c;
+                if (i <= j || col < k0 + kb) continue;
+                T* x = blk + c * 2 * kNB;
+                x[i] = fms(x[i], L[j * kNB + i], x[j]);
+            }
+            __syncthreads();
+        }
+    }
+    // write back every slot
+    for (int idx = tid; idx < ncol * ns; idx += blockDim.x) {
+        int c = idx / ns, r = idx % ns;
+        int col = c0 + c;
+        if (col >= k0 && col < k0 + kb) continue;
+        a[(size_t)col * n + srow[r]] = blk[c * 2 * kNB + r];
     }
 }
 
@@ -212,45 +281,89 @@ __global__ void gemm_update_kernel(int n, int k0, int kb, T* A) {
     }
 }
 
-// Solve LU x = b for every matrix and rhs: row swaps, unit-lower forward and
-// upper backward substitution.  One CTA per (matrix, rhs); B is [b][n][nrhs].
+// Solve LU x = b for every matrix and rhs: row swaps, then blocked unit-lower
+// forward and upper backward substitution.  One CTA (256 threads) per
+// (matrix, rhs); B is [b][n][nrhs].  The right-hand side lives in shared
+// memory for the whole solve; each 32-row diagonal block is solved by one
+// warp, then the rows outside it are updated with a coalesced
+// matrix-vector product (thread per row, 32 columns).  Matrices whose
+// active flag is 0 are skipped (converged modes during refinement).
 template <typename T>
-__global__ void lu_solve_kernel(int n, int nrhs, const T* LU, const int* piv, T* B) {
+__global__ void lu_solve_kernel(int n, int nrhs, const T* LU, const int* piv, T* B, const int* active) {
     const int b = blockIdx.x, r = blockIdx.y;
+    if (active && !active[b]) return;
+    extern __shared__ unsigned char smraw[];
+    T* sxv = reinterpret_cast<T*>(smraw);   // n entries
     const T* a = LU + (size_t)b * n * n;
     const int* pv = piv + (size_t)b * n;
     T* x = B + (size_t)b * n * nrhs;
-    __shared__ T sx;
-    if (threadIdx.x == 0)
+    __shared__ T sD[kNB][kNB + 1];   // diagonal block, sD[col][row]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < n; i += blockDim.x) sxv[i] = x[(size_t)i * nrhs + r];
+    __syncthreads();
+    if (tid == 0)
         for (int j = 0; j < n; ++j) {
             int p = pv[j];
             if (p != j) {
-                T t = x[(size_t)j * nrhs + r];
-                x[(size_t)j * nrhs + r] = x[(size_t)p * nrhs + r];
-                x[(size_t)p * nrhs + r] = t;
+                T t = sxv[j];
+                sxv[j] = sxv[p];
+                sxv[p] = t;
             }
         }
     __syncthreads();
-    for (int j = 0; j < n; ++j) {
-        if (threadIdx.x == 0) sx = x[(size_t)j * nrhs + r];
-        __syncthreads();
-        T xj = sx;
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x)
-            x[(size_t)i * nrhs + r] = fms(x[(size_t)i * nrhs + r], a[(size_t)j * n + i], xj);
-        __syncthreads();
-    }
-    for (int j = n - 1; j >= 0; --j) {
-        if (threadIdx.x == 0) {
-            T v = mul(x[(size_t)j * nrhs + r], rcp(a[(size_t)j * n + j]));
-            x[(size_t)j * nrhs + r] = v;
-            sx = v;
+    // forward: L y = x (unit diagonal)
+    for (int j0 = 0; j0 < n; j0 += kNB) {
+        const int jb = min(kNB, n - j0);
+        for (int idx = tid; idx < jb * jb; idx += blockDim.x) {
+            int c = idx / jb, i = idx % jb;
+            sD[c][i] = a[(size_t)(j0 + c) * n + j0 + i];
         }
         __syncthreads();
-        T xj = sx;
-        for (int i = threadIdx.x; i < j; i += blockDim.x)
-            x[(size_t)i * nrhs + r] = fms(x[(size_t)i * nrhs + r], a[(size_t)j * n + i], xj);
+        if (warp == 0) {
+            T v = lane < jb ? sxv[j0 + lane] : Cx<T>::mk(0, 0);
+            for (int c = 0; c < jb; ++c) {
+                T xc = Cx<T>::mk(__shfl_sync(0xffffffff, v.x, c), __shfl_sync(0xffffffff, v.y, c));
+                if (lane > c && lane < jb) v = fms(v, sD[c][lane], xc);
+            }
+            if (lane < jb) sxv[j0 + lane] = v;
+        }
+        __syncthreads();
+        for (int i = j0 + jb + tid; i < n; i += blockDim.x) {
+            T acc = sxv[i];
+#pragma unroll 8
+            for (int c = 0; c < jb; ++c) acc = fms(acc, a[(size_t)(j0 + c) * n + i], sxv[j0 + c]);
+            sxv[i] = acc;
+        }
         __syncthreads();
     }
+    // backward: U x = y
+    const int nblk = (n + kNB - 1) / kNB;
+    for (int bi = nblk - 1; bi >= 0; --bi) {
+        const int j0 = bi * kNB, jb = min(kNB, n - j0);
+        for (int idx = tid; idx < jb * jb; idx += blockDim.x) {
+            int c = idx / jb, i = idx % jb;
+            sD[c][i] = a[(size_t)(j0 + c) * n + j0 + i];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            T v = lane < jb ? sxv[j0 + lane] : Cx<T>::mk(0, 0);
+            for (int c = jb - 1; c >= 0; --c) {
+                if (lane == c) v = mul(v, rcp(sD[c][c]));
+                T xc = Cx<T>::mk(__shfl_sync(0xffffffff, v.x, c), __shfl_sync(0xffffffff, v.y, c));
+                if (lane < c) v = fms(v, sD[c][lane], xc);
+            }
+            if (lane < jb) sxv[j0 + lane] = v;
+        }
+        __syncthreads();
+        for (int i = tid; i < j0; i += blockDim.x) {
+            T acc = sxv[i];
+#pragma unroll 8
+            for (int c = 0; c < jb; ++c) acc = fms(acc, a[(size_t)(j0 + c) * n + i], sxv[j0 + c]);
+            sxv[i] = acc;
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += blockDim.x) x[(size_t)i * nrhs + r] = sxv[i];
 }
 
 __global__ void c128_to_c64_kernel(int64_t count, const double2* s, float2* d) {
@@ -261,8 +374,9 @@ __global__ void c128_to_c64_kernel(int64_t count, const double2* s, float2* d) {
 
 // R = B - A X (FP64) per (matrix, row, rhs); squared norms accumulated per (matrix, rhs).
 __global__ void residual_kernel(int n, int nrhs, const double2* A, const double2* X, const double2* B,
-                                double2* R, double* rn2, double* bn2) {
+                                double2* R, double* rn2, double* bn2, const int* active) {
     const int b = blockIdx.y;
+    if (active && !active[b]) return;
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)n * nrhs) return;
     int r = (int)(idx % nrhs), row = (int)(idx / nrhs);
@@ -276,9 +390,10 @@ __global__ void residual_kernel(int n, int nrhs, const double2* A, const double2
     atomicAdd(bn2 + (size_t)b * nrhs + r, bb.x * bb.x + bb.y * bb.y);
 }
 
-__global__ void add_correction_kernel(int64_t count, const float2* d, double2* X) {
+__global__ void add_correction_kernel(int64_t count, int64_t per_matrix, const float2* d, double2* X,
+                                      const int* active) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) {
+    if (i < count && (!active || active[i / per_matrix])) {
         X[i].x += (double)d[i].x;
         X[i].y += (double)d[i].y;
     }
@@ -292,8 +407,13 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
         int kb = std::min(kNB, n - k0);
         panel_kernel<T><<<batch, kPanelThreads, 0, s>>>(n, k0, kb, A, piv, info);
         count_launch(2);
-        dim3 g1((n + 127) / 128, batch);
-        swap_trsm_kernel<T><<<g1, 128, 0, s>>>(n, k0, kb, A, piv);
+        dim3 g1((n + kSwapCols - 1) / kSwapCols, batch);
+        size_t sm1 = sizeof(T) * ((size_t)kSwapCols * 2 * kNB + kNB * kNB);
+        if (k0 == 0) {
+            cudaError_t e = cudaFuncSetAttribute(swap_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+            if (e != cudaSuccess) return e;
+        }
+        swap_trsm_kernel<T><<<g1, 256, sm1, s>>>(n, k0, kb, A, piv);
         int rem = n - k0 - kb;
         if (rem > 0) {
             constexpr int TL = GemmTile<T>::v;
@@ -307,9 +427,14 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
 
 template <typename T>
 cudaError_t batched_lu_solve(int n, int batch, int nrhs, const T* LU, const int* piv, T* B,
-                             cudaStream_t s) {
+                             cudaStream_t s, const int* active) {
     dim3 g(batch, nrhs);
-    lu_solve_kernel<T><<<g, 256, 0, s>>>(n, nrhs, LU, piv, B);
+    size_t sm = sizeof(T) * (size_t)n;
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(lu_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    lu_solve_kernel<T><<<g, 256, sm, s>>>(n, nrhs, LU, piv, B, active);
     count_launch();
     return cudaGetLastError();
 }
@@ -317,9 +442,9 @@ cudaError_t batched_lu_solve(int n, int batch, int nrhs, const T* LU, const int*
 template cudaError_t batched_lu<double2>(int, int, double2*, int*, int*, cudaStream_t);
 template cudaError_t batched_lu<float2>(int, int, float2*, int*, int*, cudaStream_t);
 template cudaError_t batched_lu_solve<double2>(int, int, int, const double2*, const int*, double2*,
-                                               cudaStream_t);
+                                               cudaStream_t, const int*);
 template cudaError_t batched_lu_solve<float2>(int, int, int, const float2*, const int*, float2*,
-                                              cudaStream_t);
+                                              cudaStream_t, const int*);
 
 cudaError_t convert_to_c64(int64_t count, const double2* src, float2* dst, cudaStream_t s) {
     int blocks = (int)std::min<int64_t>((count + 255) / 256, 152 * 32);
@@ -330,25 +455,25 @@ cudaError_t convert_to_c64(int64_t count, const double2* src, float2* dst, cudaS
 
 cudaError_t residual_c128(int n, int batch, int nrhs, const double2* A, const double2* X,
                           const double2* B, double2* R, double* rnorm, double* bnorm,
-                          cudaStream_t s) {
+                          cudaStream_t s, const int* active) {
     cudaError_t e = cudaMemsetAsync(rnorm, 0, sizeof(double) * batch * nrhs, s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(bnorm, 0, sizeof(double) * batch * nrhs, s);
     if (e != cudaSuccess) return e;
     dim3 g((unsigned)(((size_t)n * nrhs + 255) / 256), batch);
-    residual_kernel<<<g, 256, 0, s>>>(n, nrhs, A, X, B, R, rnorm, bnorm);
+    residual_kernel<<<g, 256, 0, s>>>(n, nrhs, A, X, B, R, rnorm, bnorm, active);
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t refine_step(int n, int batch, int nrhs, const float2* LU32, const int* piv,
-                        const double2* R, float2* work32, double2* X, cudaStream_t s) {
+                        const double2* R, float2* work32, double2* X, cudaStream_t s, const int* active) {
     int64_t cnt = (int64_t)batch * n * nrhs;
     cudaError_t e = convert_to_c64(cnt, R, work32, s);
     if (e != cudaSuccess) return e;
-    e = batched_lu_solve<float2>(n, batch, nrhs, LU32, piv, work32, s);
+    e = batched_lu_solve<float2>(n, batch, nrhs, LU32, piv, work32, s, active);
     if (e != cudaSuccess) return e;
-    add_correction_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(cnt, work32, X);
+    add_correction_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(cnt, (int64_t)n * nrhs, work32, X, active);
     count_launch();
     return cudaGetLastError();
 }

@@ -33,7 +33,7 @@ def oracle_solution(**kw):
     from oracle.problem import Params
     key = tuple(sorted(kw.items()))
     if key not in _ORACLE:
-        _ORACLE[key] = Solution(Params(**kw))
+        _ORACLE[key] = Solution(Params(**kw), keep_matrices=True)
     return _ORACLE[key]
 
 
@@ -103,37 +103,59 @@ def test_modal_kernels_config1(torch):
 
 def mode_conditioning(sol):
     """kappa_n of the column-equilibrated block matrix of every mode (oracle)."""
-    from oracle.assemble import block_system
     out = []
     for n in range(sol.P.M // 2):
-        Sa, Ka = sol.sys.matrices("a", n)
-        Sb, Kb = sol.sys.matrices("b", n)
-        A, _ = block_system(Sa, Ka, sol.Da, Sb, Kb, sol.Db, sol.b1[:, n], sol.b2[:, n])
+        A, _ = sol.A[n]
         out.append(np.linalg.cond(A / np.linalg.norm(A, axis=0)[None, :]))
     return np.array(out)
 
 
-def check_densities(out, sol, tol, label):
-    """u1, u2 within tol (relative 2-norm over all modes and nodes); phi1, phi2
-    per mode within max(tol, 50 eps kappa_n): the phi unknowns at the graded
-    node cluster next to the axis span a near-null direction of mode 0
-    (kappa ~ 1e7 at N = 128), where any two FP64 solvers agree only to
-    ~kappa eps."""
+def check_densities(out, sol, tol, backward_tol, label):
+    """Parity of the solved densities with the oracle.
+
+    * u1, u2 (well conditioned): forward relative 2-norm error <= tol.
+    * normwise backward error of the GPU solution x = (u1, phi1) in the
+      ORACLE's block systems, all modes together (the block-diagonal system
+      of every mode, as the forward errors are taken over all modes):
+      |A x - B| / (max_n |A_n|_F |x| + |B|) <= backward_tol.  (Per mode, the
+      high modes' data are at the rounding floor of their DFTs, ~1e-15.)
+    * phi1, phi2: forward error per mode <= max(tol, 1e-12 kappa_n).  The phi
+      unknowns at the graded node clusters next to the axis and the PML end
+      span near-null directions (kappa up to ~1e7 at N = 128 after column
+      equilibration), along which two correct FP64 solvers of matrices that
+      differ by rounding (the close-pair split in the PML cancels by up to
+      ~1e9, see test_modal_kernels_config1) disagree by ~kappa x that
+      difference; the backward-error check is the tight one there.
+    """
     kap = mode_conditioning(sol)
-    eps = np.finfo(float).eps
+    N = sol.P.N
     errs = {}
     for name, ref in (("u1", sol.u1), ("u2", sol.u2)):
         got = out[name].cpu().numpy()[:, :, 0]
         errs[name] = _rel(got, ref)
         assert errs[name] <= tol, (label, name, errs[name])
+    u1 = out["u1"].cpu().numpy()[:, :, 0]
+    p1 = out["phi1"].cpu().numpy()[:, :, 0]
+    r2 = x2 = b2 = 0.0
+    anorm = 0.0
+    for n in range(sol.P.M // 2):
+        A, B = sol.A[n]
+        x = np.concatenate([u1[n], p1[n]])
+        r2 += np.linalg.norm(A @ x - B) ** 2
+        x2 += np.linalg.norm(x) ** 2
+        b2 += np.linalg.norm(B) ** 2
+        anorm = max(anorm, np.linalg.norm(A))
+    bwd = np.sqrt(r2) / (anorm * np.sqrt(x2) + np.sqrt(b2))
+    assert bwd <= backward_tol, (label, "backward", bwd)
+    worst_bwd = bwd
     for name, ref in (("phi1", sol.phi1), ("phi2", sol.phi2)):
         got = out[name].cpu().numpy()[:, :, 0]
         errs[name] = _rel(got, ref)
         for n in range(ref.shape[0]):
-            bound = max(tol, 50 * eps * kap[n])
+            bound = max(tol, 1e-12 * kap[n])
             e = np.linalg.norm(got[n] - ref[n]) / np.linalg.norm(ref)
             assert e <= bound, (label, name, n, e, bound)
-    print(label, errs, "max kappa %.2e" % kap.max())
+    print(label, errs, "backward %.2e" % worst_bwd, "max kappa %.2e" % kap.max())
     return errs
 
 
@@ -142,7 +164,7 @@ def test_solve_fp64_config1(torch):
     from paper_2412_11162_gb300.binding import PMLBIE_FP64
     P = Problem(CFG1["k1"], CFG1["k2"], CFG1["N"], CFG1["M"])
     out, rep = P.solve([np.pi / 6], precision=PMLBIE_FP64)
-    check_densities(out, oracle_solution(**CFG1), 1e-10, "fp64")
+    check_densities(out, oracle_solution(**CFG1), 1e-10, 1e-11, "fp64")
 
 
 def test_solve_mixed_config1(torch):
@@ -151,7 +173,7 @@ def test_solve_mixed_config1(torch):
     P = Problem(CFG1["k1"], CFG1["k2"], CFG1["N"], CFG1["M"])
     out, rep = P.solve([np.pi / 6], precision=PMLBIE_MIXED, allow_noconverge=True)
     print("mixed refinement iterations", rep.refine_iters, "residual %.2e" % rep.residual)
-    check_densities(out, oracle_solution(**CFG1), 1e-6, "mixed")
+    check_densities(out, oracle_solution(**CFG1), 1e-6, 1e-11, "mixed")
 
 
 def test_flat_interface_gives_zero_field(torch):

@@ -110,8 +110,9 @@ def oracle_sample(w, rows=6):
     for l in sel:
         src_m = np.nonzero(Q.grid_mask[l])[0]
         cidx = np.nonzero(Q.corr_target == l)[0]
-        tg = {k: np.repeat(G.nodes[k][l], len(src_m) + len(cidx)) for k in ("rho", "z_t", "rho_t")}
-        sc = {k: np.concatenate([G.nodes[k][src_m], Q.corr_pts[k][cidx]]) for k in ("rho", "z_t", "rho_t", "nuc_r", "nuc_z")}
+        tg = {k: np.repeat(G.nodes[k][l], len(src_m) + len(cidx)) for k in ("rho", "z", "z_t", "rho_t", "bk", "ox", "oz")}
+        sc = {k: np.concatenate([G.nodes[k][src_m], Q.corr_pts[k][cidx]])
+              for k in ("rho", "z", "z_t", "rho_t", "nuc_r", "nuc_z", "bk", "ox", "oz")}
         pg = KR.pair_geometry(tg, sc, P)
         near = KR.near_mask(pg, P)
         lap = KR.laplace_modes({k: v[near] for k, v in pg.items()}, P.M - 2)
@@ -236,7 +237,7 @@ def run_ours(args, rank, world):
     H = P.nodes()
     ng, nc = P.near_count()
     # bytes uploaded by the first device call: node tables, pair classes, close-pair table, stencils
-    h2d = (w["N"] * (5 * 8 + 3 * 16 + 3 * 8) + w["N"] ** 2 + (ng + nc) * 128 + nc * 4 * (1 + 2 * 10)
+    h2d = (w["N"] * (5 * 8 + 3 * 16 + 3 * 8 + 4 + 16) + w["N"] ** 2 + (ng + nc) * 144 + nc * 4 * (1 + 2 * 10)
            + (w["M"] // 2 + 1 + w["M"]) * 16 + 8)
     d2h = 4 * int(np.prod(shape)) * 16
 

@@ -28,7 +28,7 @@ Readings (listed in the design notes):
 import numpy as np
 import os
 
-from .problem import Params, Geometry
+from .problem import Params, Geometry, separation
 from . import kernels as KR
 
 _TABLE = os.path.join(os.path.dirname(__file__), "alpert_log_j10_a10.txt")
@@ -129,8 +129,8 @@ class ModalSystem:
         tc = _take(G.nodes, Q.corr_target)
         sc = Q.corr_pts
         # stacked pair list: grid pairs then correction pairs
-        tgt = {k: np.concatenate([tg[k], tc[k]]) for k in ("rho", "z_t", "rho_t")}
-        src = {k: np.concatenate([sg[k], sc[k]]) for k in ("rho", "z_t", "rho_t", "nuc_r", "nuc_z")}
+        tgt = {k: np.concatenate([tg[k], tc[k]]) for k in ("rho", "z", "z_t", "rho_t", "bk", "ox", "oz")}
+        src = {k: np.concatenate([sg[k], sc[k]]) for k in ("rho", "z", "z_t", "rho_t", "nuc_r", "nuc_z", "bk", "ox", "oz")}
         self.pg = KR.pair_geometry(tgt, src, P)
         self.near = KR.near_mask(self.pg, P)
         self.ngrid = len(li)
@@ -172,12 +172,13 @@ class ModalSystem:
 def laplace_dl_mode0(tgt, src):
     """int_{-pi}^{pi} dG0/dnu' dpsi for the unstretched Laplace kernel (quadrature)."""
     pts, wts = KR.psi_rule(8)
-    drho = tgt["rho"][:, None] - src["rho"][:, None]
-    dz = tgt["z"][:, None] - src["z"][:, None]
+    dr, dzz = separation(tgt, src)
+    drho = dr[:, None]
+    dz = dzz[:, None]
     s = np.sin(0.5 * pts)[None, :]
     R2 = drho * drho + dz * dz + 4.0 * tgt["rho"][:, None] * src["rho"][:, None] * s * s
-    num = src["nu_r"][:, None] * (src["rho"][:, None] - tgt["rho"][:, None] * np.cos(pts)[None, :]) \
-        + src["nu_z"][:, None] * (src["z"][:, None] - tgt["z"][:, None])
+    num = src["nu_r"][:, None] * (-drho + 2.0 * tgt["rho"][:, None] * s * s) \
+        + src["nu_z"][:, None] * (-dz)
     F = -num / (4.0 * np.pi * R2 ** 1.5)
     return 2.0 * (F * wts[None, :]).sum(axis=1)
 

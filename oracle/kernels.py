@@ -39,7 +39,7 @@ import math
 
 import numpy as np
 
-from .problem import Params, delta_I
+from .problem import Params, delta_I, separation
 
 FOUR_PI = 4.0 * np.pi
 
@@ -48,12 +48,15 @@ FOUR_PI = 4.0 * np.pi
 # pair geometry
 # ----------------------------------------------------------------------------
 def pair_geometry(tgt, src, P: Params):
-    """Pair quantities for broadcastable target/source dicts (see Geometry.at)."""
-    drho_t = (tgt["rho"] - src["rho"]) + 1j * delta_I(tgt["rho"], src["rho"], P)
-    dz_t = tgt["z_t"] - src["z_t"]
+    """Pair quantities for broadcastable target/source dicts (see Geometry.at).
+    Separations of close points near a breakpoint come from accurate offsets
+    (Sec. 4.3: the stabilised distance)."""
+    dr, dz = separation(tgt, src)
+    drho_t = dr + 1j * delta_I(src["rho"], dr, P)       # rho~ - rho~'
+    dz_t = dz + 0j
     rr = tgt["rho_t"] * src["rho_t"]
     d2 = drho_t * drho_t + dz_t * dz_t
-    return dict(d2=d2, rr=rr, rho_t=tgt["rho_t"], rho_t_s=src["rho_t"], dz_t=dz_t,
+    return dict(d2=d2, rr=rr, rho_t=tgt["rho_t"], rho_t_s=src["rho_t"], dz_t=dz_t, drt=-drho_t,
                 nuc_r=src["nuc_r"], nuc_z=src["nuc_z"])
 
 
@@ -70,8 +73,11 @@ def _delta2(pg, psi):
 
 
 def _numer_D(pg, psi):
-    """nu'_c,rho (rho~' - rho~ cos psi) + nu'_c,z (z~' - z~)."""
-    return (pg["nuc_r"][..., None] * (pg["rho_t_s"][..., None] - pg["rho_t"][..., None] * np.cos(psi))
+    """nu'_c,rho (rho~' - rho~ cos psi) + nu'_c,z (z~' - z~), evaluated as
+    nu'_c,rho [(rho~' - rho~) + 2 rho~ sin^2(psi/2)] + nu'_c,z (z~' - z~) so
+    that nothing cancels for close pairs (Sec. 4.3, the stabilised D)."""
+    s = np.sin(0.5 * psi)
+    return (pg["nuc_r"][..., None] * (pg["drt"][..., None] + 2.0 * pg["rho_t"][..., None] * s * s)
             + pg["nuc_z"][..., None] * (-pg["dz_t"][..., None]))
 
 

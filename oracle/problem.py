@@ -90,6 +90,20 @@ class _Segment:
         (r0, z0), (r1, z1) = self.data
         return r0 + s * (r1 - r0), z0 + s * (z1 - z0), (r1 - r0) * np.ones_like(s), (z1 - z0) * np.ones_like(s)
 
+    def offset(self, s, sc, end):
+        """r(s) - r(0) (end = 0) or r(s) - r(1) (end = 1), free of cancellation;
+        sc = 1 - s computed separately."""
+        if self.kind == "gauss":
+            h, w, R = self.data
+            c = h / (1.0 - np.exp(-R * R / w))
+            if end == 0:
+                return R * s, c * np.expm1(-(R * s) ** 2 / w)
+            return -R * sc, c * np.exp(-R * R / w) * np.expm1(R * R * sc * (1.0 + s) / w)
+        (r0, z0), (r1, z1) = self.data
+        if end == 0:
+            return s * (r1 - r0), s * (z1 - z0)
+        return -sc * (r1 - r0), -sc * (z1 - z0)
+
     def length(self):
         x, wq = np.polynomial.legendre.leggauss(64)
         s = 0.5 * (x + 1.0)
@@ -149,6 +163,16 @@ def graded(u, p):
     return s, ds
 
 
+def graded_complement(u, p):
+    """1 - s(u) = xi_2^p / (xi_1^p + xi_2^p), without cancellation near u = 1."""
+    u = np.asarray(u, dtype=float)
+    xi = 2.0 * u - 1.0
+    A = 0.5 - 1.0 / p
+    x1 = (2.0 * u) * (A * xi * xi - A * xi + 0.5)
+    x2 = (2.0 * (1.0 - u)) * (A * xi * xi + A * xi + 0.5)
+    return x2 ** p / (x1 ** p + x2 ** p)
+
+
 class Geometry:
     """Nodes, weights and PML tables of gamma_AB for one Params."""
 
@@ -181,6 +205,9 @@ class Geometry:
         z = np.empty_like(t)
         drho = np.empty_like(t)
         dz = np.empty_like(t)
+        bk = np.empty(t.shape, int)      # nearest breakpoint (global index)
+        ox = np.empty_like(t)            # r - r(breakpoint), accurate
+        oz = np.empty_like(t)
         for k, sg in enumerate(self.segs):
             m = seg == k
             if not np.any(m):
@@ -189,12 +216,19 @@ class Geometry:
             t1 = self.brk[k + 1] * self.h
             u = (t[m] - t0) / (t1 - t0)
             s, ds = graded(u, P.p)
+            sc = graded_complement(u, P.p)
             r_, z_, dr_, dz_ = sg.eval(s)
             rho[m] = r_
             z[m] = z_
             scale = ds / (t1 - t0)
             drho[m] = dr_ * scale
             dz[m] = dz_ * scale
+            end = (u > 0.5).astype(int)
+            o0 = sg.offset(s, sc, 0)
+            o1 = sg.offset(s, sc, 1)
+            ox[m] = np.where(end == 1, o1[0], o0[0])
+            oz[m] = np.where(end == 1, o1[1], o0[1])
+            bk[m] = k + end
         speed = np.hypot(drho, dz)                       # |r'(t)|
         with np.errstate(invalid="ignore", divide="ignore"):
             nu_r = np.where(speed > 0, dz / speed, 0.0)    # tangent rotated by -90 deg:
@@ -209,7 +243,17 @@ class Geometry:
         nuc_z = nu_z * ratio * alpha              # nu_z rho~ alpha_rho / (rho alpha_z)
         return dict(t=t, rho=rho, z=z, speed=speed, nu_r=nu_r, nu_z=nu_z,
                     I=I, rho_t=rho_t, z_t=z.astype(complex), nuc_r=nuc_r, nuc_z=nuc_z,
-                    W=2.0 * rho * speed)
+                    W=2.0 * rho * speed, bk=bk, ox=ox, oz=oz)
+
+
+def separation(tgt, src):
+    """(rho_t - rho_s, z_t - z_s); from the breakpoint offsets when both points
+    are nearest to the same breakpoint (close pairs at graded clusters, whose
+    separation is below the spacing of FP64 absolute positions)."""
+    same = tgt["bk"] == src["bk"]
+    dr = np.where(same, tgt["ox"] - src["ox"], tgt["rho"] - src["rho"])
+    dz = np.where(same, tgt["oz"] - src["oz"], tgt["z"] - src["z"])
+    return dr, dz
 
 
 # ----------------------------------------------------------------------------
@@ -254,11 +298,25 @@ def pml_integral(rho, P: Params):
     return _sigma_integral(lo, hi, P)
 
 
-def delta_I(rho1, rho2, P: Params):
-    """I(rho1) - I(rho2), integrated directly over [rho2, rho1] (no cancellation)."""
-    rho1 = np.asarray(rho1, float)
+def delta_I(rho2, drho, P: Params):
+    """I(rho2 + drho) - I(rho2) = int_{rho2}^{rho2 + drho} sigma_1, integrated
+    directly.  sigma_1 vanishes below a1 and is only C^(p-1) there, so the
+    interval is clipped at a1; when both ends lie in the PML the integral runs
+    over [rho2, rho2 + drho] with drho given accurately (no cancellation)."""
     rho2 = np.asarray(rho2, float)
-    lo = np.maximum(np.minimum(rho1, rho2), P.a1)
-    hi = np.maximum(np.maximum(rho1, rho2), P.a1)
-    sgn = np.where(rho1 >= rho2, 1.0, -1.0)
-    return sgn * _sigma_integral(lo, hi, P, panels=8)
+    drho = np.asarray(drho, float)
+    rho2, drho = np.broadcast_arrays(rho2, drho)
+    lo = np.minimum(rho2, rho2 + drho)
+    hi = np.maximum(rho2, rho2 + drho)
+    inside = lo >= P.a1
+    start = np.where(inside, rho2, P.a1)
+    length = np.where(inside, drho, np.maximum(hi - P.a1, 0.0) * np.sign(drho))
+    x, w = _GL16
+    tot = np.zeros(rho2.shape)
+    panels = 8
+    for k in range(panels):
+        xs = (k + 0.5 * (x + 1.0)) / panels
+        pts = np.where(inside[..., None], start[..., None] + length[..., None] * xs,
+                       start[..., None] + np.abs(length)[..., None] * xs)
+        tot = tot + np.sum((0.5 / panels) * w * pml_sigma(pts, P), axis=-1)
+    return length * tot

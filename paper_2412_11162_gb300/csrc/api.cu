@@ -69,7 +69,8 @@ int ensure_device(pmlbie_problem* prob) {
         return rc;
     std::vector<double2> rt = to_d2(H.rho_t), ncr = to_d2(H.nuc_r), ncz = to_d2(H.nuc_z);
     if ((rc = upload(D.rho_t, rt)) || (rc = upload(D.nuc_r, ncr)) || (rc = upload(D.nuc_z, ncz)) ||
-        (rc = upload(D.cls, H.cls)) || (rc = upload(D.near, H.near)) ||
+        (rc = upload(D.cls, H.cls)) || (rc = upload(D.near, H.near)) || (rc = upload(D.bk, H.bk)) ||
+        (rc = upload(D.off, H.off)) ||
         (rc = upload(D.corr_target, H.corr_target)) || (rc = upload(D.corr_m, H.corr_m)) ||
         (rc = upload(D.corr_coef, H.corr_coef)) || (rc = upload(D.Da, H.Da)) || (rc = upload(D.Db, H.Db)))
         return rc;
@@ -91,7 +92,7 @@ int ensure_device(pmlbie_problem* prob) {
 
 void free_device(pmlbie_problem* prob) {
     DeviceTables& D = prob->D;
-    void* ptrs[] = {D.rho, D.z, D.I, D.Wu, D.Wphi, D.rho_t, D.nuc_r, D.nuc_z, D.cls, D.near,
+    void* ptrs[] = {D.rho, D.z, D.I, D.Wu, D.Wphi, D.rho_t, D.nuc_r, D.nuc_z, D.bk, D.off, D.cls, D.near,
                     D.corr_target, D.corr_m, D.corr_coef, D.Da, D.Db, D.cos_tab, D.twid, D.twid2};
     for (void* p : ptrs)
         if (p) cudaFree(p);

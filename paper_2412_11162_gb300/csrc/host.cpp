@@ -139,12 +139,30 @@ struct Pml {
         }
         return tot;
     }
-    // I(r1) - I(r2): integrated directly over [r2, r1] when the two radii are
-    // close (where the difference of tabulated values would cancel), else the
-    // difference of the tabulated integrals I1, I2.
-    double delta(double r1, double r2, double I1, double I2) const {
-        if (std::fabs(r1 - r2) > 0.05 * T) return I1 - I2;
-        return r1 >= r2 ? integral(r2, r1) : -integral(r1, r2);
+    // I(r2 + dr) - I(r2) for an accurately known separation dr: integrated
+    // directly over [r2, r2 + dr] when the radii are close (where the
+    // difference of tabulated values would cancel), else the difference of
+    // the tabulated integrals I1 = I(r2 + dr), I2 = I(r2).
+    // (sigma is C^(p-1) at a1, so a short interval that reaches below a1 is
+    // integrated from a1 only.)
+    double delta(double r2, double dr, double I1, double I2) const {
+        if (std::fabs(dr) > 0.05 * T) return I1 - I2;
+        double lo = std::min(r2, r2 + dr), hi = std::max(r2, r2 + dr);
+        double start = lo, width = std::fabs(dr);   // the interval [start, start + width]
+        if (lo < a1) {
+            if (hi <= a1) return 0.0;
+            start = a1;
+            width = hi - a1;
+        }
+        static const GL g(16);
+        double tot = 0.0;
+        const int panels = 4;
+        for (int k = 0; k < panels; ++k)
+            for (size_t i = 0; i < g.x.size(); ++i) {
+                double xs = (k + 0.5 * (g.x[i] + 1.0)) / panels;
+                tot += 0.5 / panels * g.w[i] * sigma(start + width * xs);
+            }
+        return (dr < 0 ? -width : width) * tot;
     }
 };
 
@@ -169,6 +187,25 @@ struct Segment {
             dz = z1 - z0;
         }
     }
+    // r(s) - r(0) (end 0) or r(s) - r(1) (end 1) without cancellation; sc = 1 - s
+    void offset(double s, double sc, int end, double& orho, double& oz) const {
+        if (gauss) {
+            double c = h / (1.0 - std::exp(-R * R / w));
+            if (end == 0) {
+                orho = R * s;
+                oz = c * std::expm1(-(R * s) * (R * s) / w);
+            } else {
+                orho = -R * sc;
+                oz = c * std::exp(-R * R / w) * std::expm1(R * R * sc * (1.0 + s) / w);
+            }
+        } else if (end == 0) {
+            orho = s * (r1 - r0);
+            oz = s * (z1 - z0);
+        } else {
+            orho = -sc * (r1 - r0);
+            oz = -sc * (z1 - z0);
+        }
+    }
     double length() const {
         static const GL g(48);
         double s = 0;
@@ -181,13 +218,15 @@ struct Segment {
     }
 };
 
-// Graded map of Eq. (sxi), oriented so that u = 0 -> s = 0: s(u), ds/du.
-void graded_map(double u, int p, double& s, double& ds) {
+// Graded map of Eq. (sxi), oriented so that u = 0 -> s = 0: s(u), 1 - s(u)
+// (computed separately, accurate near u = 1) and ds/du.
+void graded_map(double u, int p, double& s, double& sc, double& ds) {
     double xi = 2.0 * u - 1.0, A = 0.5 - 1.0 / p;
     double x1 = (2.0 * u) * (A * xi * xi - A * xi + 0.5);        // (xi+1)(A xi^2 - A xi + 1/2)
     double x2 = (2.0 * (1.0 - u)) * (A * xi * xi + A * xi + 0.5);  // (1-xi)(A xi^2 + A xi + 1/2)
     double x1p = std::pow(x1, p), x2p = std::pow(x2, p), den = x1p + x2p;
     s = x1p / den;
+    sc = x2p / den;
     double dx1 = 3.0 * A * xi * xi + 1.0 / p;
     ds = p * std::pow(x1, p - 1) * std::pow(x2, p - 1) / (den * den) * dx1 * 2.0;
 }
@@ -200,21 +239,29 @@ struct Curve {
     int p = 6;
     struct Pt {
         double rho, z, speed, nu_r, nu_z;
+        int bk;          // nearest breakpoint (index into brk)
+        double ox, oz;   // r - r(breakpoint), accurate
     };
     Pt at(double t) const {
         int k = 0;
         while (k + 1 < (int)segs.size() && t >= brk[k + 1] * h) ++k;
         double t0 = brk[k] * h, t1 = brk[k + 1] * h;
-        double u = (t - t0) / (t1 - t0), s, ds;
-        graded_map(u, p, s, ds);
+        double u = (t - t0) / (t1 - t0), s, sc, ds;
+        graded_map(u, p, s, sc, ds);
         double r, z, dr, dz;
         segs[k].eval(s, r, z, dr, dz);
-        double sc = ds / (t1 - t0);
-        dr *= sc;
-        dz *= sc;
+        int end = u > 0.5 ? 1 : 0;
+        double ox, oz;
+        segs[k].offset(s, sc, end, ox, oz);
+        double dsdt = ds / (t1 - t0);
+        dr *= dsdt;
+        dz *= dsdt;
         Pt o;
         o.rho = r;
         o.z = z;
+        o.bk = k + end;
+        o.ox = ox;
+        o.oz = oz;
         o.speed = std::hypot(dr, dz);
         if (o.speed > 0) {
             o.nu_r = dz / o.speed;   // tangent rotated by -90 degrees: toward Omega_2
@@ -436,15 +483,16 @@ void ellip_KE(long double k2, long double kp, long double& K, long double& E) {
 // int_{-pi}^{pi} dG0/dnu' dpsi, unstretched Laplace double layer, mode 0:
 // -(1/(pi sqrt(Q))) [A E(k)/d^2 + nu'_rho K(k)/(2 rho')],
 // Q = (rho+rho')^2 + dz^2, d^2 = (rho-rho')^2 + dz^2, k^2 = 4 rho rho'/Q,
-// A = nu'_rho (rho' - rho) + nu'_z (z' - z) - nu'_rho d^2/(2 rho').
-double laplace_dl0(double rho, double z, double rs, double zs, double nr, double nz) {
-    long double dr = rho - rs, dz = z - zs;
+// A = nu'_rho (rho' - rho) + nu'_z (z' - z) - nu'_rho d^2/(2 rho');
+// drho = rho - rho', dzz = z - z' are passed in (accurate separations).
+double laplace_dl0(double rho, double rs, double drho, double dzz, double nr, double nz) {
+    long double dr = drho, dz = dzz;
     long double d2 = dr * dr + dz * dz;
     long double Q = (long double)(rho + rs) * (rho + rs) + dz * dz;
     long double k2 = 4.0L * rho * rs / Q, kp = std::sqrt(d2 / Q);
     long double K, E;
     ellip_KE(k2, kp, K, E);
-    long double A = nr * (rs - rho) + nz * (zs - z) - nr * d2 / (2.0L * rs);
+    long double A = -nr * dr - nz * dz - nr * d2 / (2.0L * rs);
     long double v = -(A * E / d2 + nr * K / (2.0L * rs)) / (3.141592653589793238462643383279502884L * std::sqrt(Q));
     return (double)v;
 }
@@ -545,20 +593,42 @@ int build_tables(pmlbie_problem* prob) {
         }
     if ((int)H.unk_grid.size() != P.N) return fail(PMLBIE_EINVAL, "internal: unknown count");
 
-    auto fill_point = [&](double t, double& rho, double& z, double& speed, double& nr, double& nz,
-                          double& I, cd& rt, cd& ncr, cd& ncz) {
+    // every quantity of one curve point (node or Alpert correction point)
+    struct CP {
+        double rho, z, speed, nr, nz, I;
+        cd rt, ncr, ncz;
+        int bk;            // nearest breakpoint
+        double ox, oz;     // offset from it, accurate
+    };
+    auto fill_point = [&](double t) {
         Curve::Pt q = C.at(t);
-        rho = q.rho;
-        z = q.z;
-        speed = q.speed;
-        nr = q.nu_r;
-        nz = q.nu_z;
-        I = pml.integral(P.a1, rho);
-        rt = cd(rho, I);
-        cd alpha(1.0, pml.sigma(rho));
-        cd ratio = rho > 0 ? rt / rho : cd(1.0, 0.0);
-        ncr = nr * ratio / alpha;   // nu_rho rho~ alpha_z / (rho alpha_rho), alpha_z = 1
-        ncz = nz * ratio * alpha;   // nu_z rho~ alpha_rho / (rho alpha_z)
+        CP c;
+        c.rho = q.rho;
+        c.z = q.z;
+        c.speed = q.speed;
+        c.nr = q.nu_r;
+        c.nz = q.nu_z;
+        c.bk = q.bk;
+        c.ox = q.ox;
+        c.oz = q.oz;
+        c.I = pml.integral(P.a1, c.rho);
+        c.rt = cd(c.rho, c.I);
+        cd alpha(1.0, pml.sigma(c.rho));
+        cd ratio = c.rho > 0 ? c.rt / c.rho : cd(1.0, 0.0);
+        c.ncr = c.nr * ratio / alpha;   // nu_rho rho~ alpha_z / (rho alpha_rho), alpha_z = 1
+        c.ncz = c.nz * ratio * alpha;   // nu_z rho~ alpha_rho / (rho alpha_z)
+        return c;
+    };
+    // (rho_t - rho_s, z_t - z_s): from breakpoint offsets when both points are
+    // nearest to the same breakpoint (close points of a graded cluster)
+    auto separation = [](const CP& a, const CP& b, double& dr, double& dz) {
+        if (a.bk == b.bk) {
+            dr = a.ox - b.ox;
+            dz = a.oz - b.oz;
+        } else {
+            dr = a.rho - b.rho;
+            dz = a.z - b.z;
+        }
     };
 
     const int N = P.N;
@@ -574,11 +644,24 @@ int build_tables(pmlbie_problem* prob) {
     H.rho_t.resize(N);
     H.nuc_r.resize(N);
     H.nuc_z.resize(N);
+    std::vector<CP> npts(N);
+    H.bk.resize(N);
+    H.off.resize(N);
     for (int l = 0; l < N; ++l) {
         double t = H.unk_grid[l] * H.h;
         H.t[l] = t;
-        fill_point(t, H.rho[l], H.z[l], H.speed[l], H.nu_r[l], H.nu_z[l], H.I[l], H.rho_t[l],
-                   H.nuc_r[l], H.nuc_z[l]);
+        const CP c = npts[l] = fill_point(t);
+        H.rho[l] = c.rho;
+        H.z[l] = c.z;
+        H.speed[l] = c.speed;
+        H.nu_r[l] = c.nr;
+        H.nu_z[l] = c.nz;
+        H.I[l] = c.I;
+        H.rho_t[l] = c.rt;
+        H.nuc_r[l] = c.ncr;
+        H.nuc_z[l] = c.ncz;
+        H.bk[l] = c.bk;
+        H.off[l] = make_double2(c.ox, c.oz);
         H.Wu[l] = 2.0 * H.rho[l] * H.speed[l];
         H.Wphi[l] = 2.0 * H.rho[l];
     }
@@ -593,10 +676,6 @@ int build_tables(pmlbie_problem* prob) {
     H.corr_tau.clear();
     H.corr_m.clear();
     H.corr_coef.clear();
-    struct CP {
-        double rho, z, speed, nr, nz, I;
-        cd rt, ncr, ncz;
-    };
     std::vector<CP> cpts;
     for (int l = 0; l < N; ++l) {
         for (int sg = -1; sg <= 1; sg += 2) {
@@ -615,9 +694,7 @@ int build_tables(pmlbie_problem* prob) {
                 }
                 H.corr_target.push_back(l);
                 H.corr_tau.push_back(tau);
-                CP c;
-                fill_point(tau, c.rho, c.z, c.speed, c.nr, c.nz, c.I, c.rt, c.ncr, c.ncz);
-                cpts.push_back(c);
+                cpts.push_back(fill_point(tau));
             }
         }
     }
@@ -625,24 +702,26 @@ int build_tables(pmlbie_problem* prob) {
 
     // pair classes and close-pair table
     const double eta = prob->eta_split;
-    auto make_pair = [&](int l, double rs, double zs, double Is, cd rts, cd ncr, cd ncz,
-                         NearPair& np) -> bool {
-        double dI = (H.rho[l] > P.a1 || rs > P.a1) ? pml.delta(H.rho[l], rs, H.I[l], Is) : 0.0;
-        cd drt(H.rho[l] - rs, dI);
-        double dz = H.z[l] - zs;
+    auto make_pair = [&](int l, const CP& src, NearPair& np) -> bool {
+        const CP& tg = npts[l];
+        double dr, dz;
+        separation(tg, src, dr, dz);
+        double dI = (tg.rho > P.a1 || src.rho > P.a1) ? pml.delta(src.rho, dr, tg.I, src.I) : 0.0;
+        cd drt(dr, dI);                   // rho~ - rho~'
         cd d2 = drt * drt + dz * dz;
-        cd rr = H.rho_t[l] * rts;
+        cd rr = tg.rt * src.rt;
         cd x = d2 / rr;
         double re_sqrt = std::sqrt(std::max(0.5 * (std::abs(x) + x.real()), 0.0));
         np.d2 = make_double2(d2.real(), d2.imag());
         np.rr = make_double2(rr.real(), rr.imag());
-        np.rho_t = make_double2(H.rho_t[l].real(), H.rho_t[l].imag());
-        np.rho_s = make_double2(rts.real(), rts.imag());
-        np.nuc_r = make_double2(ncr.real(), ncr.imag());
-        np.nuc_z = make_double2(ncz.real(), ncz.imag());
+        np.rho_t = make_double2(tg.rt.real(), tg.rt.imag());
+        np.rho_s = make_double2(src.rt.real(), src.rt.imag());
+        np.drt = make_double2(-drt.real(), -drt.imag());
+        np.nuc_r = make_double2(src.ncr.real(), src.ncr.imag());
+        np.nuc_z = make_double2(src.ncz.real(), src.ncz.imag());
         np.dz = dz;
         np.tgt = l;
-        np.flags = (H.I[l] > 0 || Is > 0) ? kFlagSubst : 0;
+        np.flags = (tg.I > 0 || src.I > 0) ? kFlagSubst : 0;
         return re_sqrt < eta;
     };
     H.cls.assign((size_t)N * N, kFar);
@@ -663,7 +742,7 @@ int build_tables(pmlbie_problem* prob) {
                             continue;
                         }
                         NearPair np;
-                        if (make_pair(l, H.rho[m], H.z[m], H.I[m], H.rho_t[m], H.nuc_r[m], H.nuc_z[m], np)) {
+                        if (make_pair(l, npts[m], np)) {
                             np.src = m;
                             H.cls[(size_t)l * N + m] = kNear;
                             part[t].push_back(np);
@@ -678,7 +757,7 @@ int build_tables(pmlbie_problem* prob) {
     for (int c = 0; c < ncorr; ++c) {
         const CP& q = cpts[c];
         NearPair np;
-        bool nr = make_pair(H.corr_target[c], q.rho, q.z, q.I, q.rt, q.ncr, q.ncz, np);
+        bool nr = make_pair(H.corr_target[c], q, np);
         np.src = c;
         np.flags |= kFlagCorr | (nr ? 0 : kFlagFar);
         H.near.push_back(np);
@@ -694,8 +773,9 @@ int build_tables(pmlbie_problem* prob) {
             double s = 0;
             for (int m = 0; m < N; ++m) {
                 if (H.cls[(size_t)l * N + m] == kSkip) continue;
-                s += H.h * H.Wu[m] *
-                     laplace_dl0(H.rho[l], H.z[l], H.rho[m], H.z[m], H.nu_r[m], H.nu_z[m]);
+                double dr, dz;
+                separation(npts[l], npts[m], dr, dz);
+                s += H.h * H.Wu[m] * laplace_dl0(H.rho[l], H.rho[m], dr, dz, H.nu_r[m], H.nu_z[m]);
             }
             K0[l] = s;
         }
@@ -703,7 +783,9 @@ int build_tables(pmlbie_problem* prob) {
     for (int c = 0; c < ncorr; ++c) {
         int l = H.corr_target[c];
         const CP& q = cpts[c];
-        double v = laplace_dl0(H.rho[l], H.z[l], q.rho, q.z, q.nr, q.nz);
+        double dr, dz;
+        separation(npts[l], q, dr, dz);
+        double v = laplace_dl0(H.rho[l], q.rho, dr, dz, q.nr, q.nz);
         for (int a = 0; a < kStencil; ++a) {
             int m = H.corr_m[(size_t)c * kStencil + a];
             if (m >= 0) K0[l] += H.corr_coef[(size_t)c * kStencil + a] * H.Wu[m] * v;

@@ -27,6 +27,7 @@ struct NearPair {
     double2 rr;        // rho~ rho~'
     double2 rho_t;     // target rho~
     double2 rho_s;     // source rho~'
+    double2 drt;       // rho~' - rho~ (accurate for close points of a graded cluster)
     double2 nuc_r;     // source conormal (region a), rho component
     double2 nuc_z;     // source conormal (region a), z component
     double  dz;        // z - z' (target minus source, real on the curve)
@@ -46,6 +47,8 @@ struct HostTables {
     // per unknown node
     std::vector<double> t, rho, z, speed, nu_r, nu_z, I, Wu, Wphi;
     std::vector<cd> rho_t, nuc_r, nuc_z;
+    std::vector<int> bk;                 // nearest breakpoint of each node
+    std::vector<double2> off;            // (rho, z) offset from it, accurate
     // Alpert rule
     std::vector<double> ax, aw;
     // correction points
@@ -64,6 +67,8 @@ struct HostTables {
 struct DeviceTables {
     double *rho = nullptr, *z = nullptr, *I = nullptr, *Wu = nullptr, *Wphi = nullptr;
     double2 *rho_t = nullptr, *nuc_r = nullptr, *nuc_z = nullptr;
+    int* bk = nullptr;
+    double2* off = nullptr;
     uint8_t* cls = nullptr;
     NearPair* near = nullptr;
     int* corr_target = nullptr;

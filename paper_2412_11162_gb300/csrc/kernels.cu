@@ -119,19 +119,30 @@ __device__ void warp_fft_inplace(double2* buf, double2* scratch, int M, const do
 
 // Per-pair geometry of a grid pair from node tables.
 struct PairGeom {
-    double2 d2, rr, nd0, ndc;   // N_D(psi) = nd0 - ndc cos psi (region a normal)
+    double2 d2, rr, nd0, nds;   // N_D(psi) = nd0 + nds sin^2(psi/2) (region a normal)
 };
 
 __device__ __forceinline__ PairGeom grid_pair(const DeviceTables& T, int l, int m) {
     PairGeom g;
-    double dr = T.rho[l] - T.rho[m], dI = T.I[l] - T.I[m], dz = T.z[l] - T.z[m];
+    // separations from breakpoint offsets when both nodes share the nearest
+    // breakpoint (graded clusters), else from the absolute positions
+    double dr, dz;
+    if (T.bk[l] == T.bk[m]) {
+        dr = T.off[l].x - T.off[m].x;
+        dz = T.off[l].y - T.off[m].y;
+    } else {
+        dr = T.rho[l] - T.rho[m];
+        dz = T.z[l] - T.z[m];
+    }
+    double dI = T.I[l] - T.I[m];
     double2 drt = c2(dr, dI);
     g.d2 = cadd(cmul(drt, drt), c2(dz * dz, 0.0));
     g.rr = cmul(T.rho_t[l], T.rho_t[m]);
     double2 ncr = T.nuc_r[m], ncz = T.nuc_z[m];
     // nu'_r (rho~' - rho~ cos psi) + nu'_z (z' - z)
-    g.nd0 = cadd(cmul(ncr, T.rho_t[m]), cscale(ncz, -dz));
-    g.ndc = cmul(ncr, T.rho_t[l]);
+    //   = [nu'_r (rho~' - rho~) + nu'_z (z' - z)] + 2 nu'_r rho~ sin^2(psi/2)
+    g.nd0 = cadd(cmul(ncr, c2(-dr, -dI)), cscale(ncz, -dz));
+    g.nds = cscale(cmul(ncr, T.rho_t[l]), 2.0);
     return g;
 }
 
@@ -170,7 +181,7 @@ __global__ void far_kernel(FarArgs a) {
             double2 R = csqrt(D2);
             double2 iR = crcp(R);
             double2 iR3 = cmul(iR, cmul(iR, iR));
-            double2 ND = csub(g.nd0, cscale(g.ndc, sc.y));
+            double2 ND = cadd(g.nd0, cscale(g.nds, sc.x));
             double2 Dk = cscale(cmul(ND, iR3), -kInv4Pi);   // region a
             double2 v[4];
 #pragma unroll
@@ -335,8 +346,7 @@ __global__ void near_laplace_kernel(NearArgs a) {
         for (int m = 0; m < M; ++m) Z[m] = cmul(Z[m], f);
     }
     // A, B, prefactors
-    double2 drt = csub(q.rho_s, q.rho_t);   // rho~' - rho~
-    double2 A = cadd(cmul(q.nuc_r, drt), cscale(q.nuc_z, -q.dz));
+    double2 A = cadd(cmul(q.nuc_r, q.drt), cscale(q.nuc_z, -q.dz));   // nu'.(r~' - r~)
     A = csub(A, cdiv(cmul(q.nuc_r, q.d2), cscale(q.rho_s, 2.0)));
     double2 B = cmul(q.nuc_r, q.rho_t);
     double2 s2 = csqrt(rr2);
@@ -374,9 +384,9 @@ __global__ void near_modes_kernel(NearArgs a) {
     NearPair q = a.np[p];
     const bool plain = (q.flags & kFlagFar) != 0;
     const bool subst = (q.flags & kFlagSubst) != 0;
-    // sampling
-    double2 nd0 = cadd(cmul(q.nuc_r, q.rho_s), cscale(q.nuc_z, -q.dz));
-    double2 ndc = cmul(q.nuc_r, q.rho_t);
+    // sampling; N_D(psi) = [nu'_r (rho~' - rho~) - nu'_z dz] + 2 nu'_r rho~ sin^2(psi/2)
+    double2 nd0 = cadd(cmul(q.nuc_r, q.drt), cscale(q.nuc_z, -q.dz));
+    double2 nds = cscale(cmul(q.nuc_r, q.rho_t), 2.0);
     // polynomials: U1 = (1 - P1)/q = -sum_{k>=1} a_k q^{k-1}; V3 = ((1-iq) - P3)/q^3
     double2 u1[8], v3[8];
     for (int k = 0; k < 8; ++k) {
@@ -390,7 +400,7 @@ __global__ void near_modes_kernel(NearArgs a) {
         double2 sc = a.T.cos_tab[j];
         double2 D2 = cadd(q.d2, cscale(q.rr, 4.0 * sc.x));
         double2 R = csqrt(D2);
-        double2 ND = csub(nd0, cscale(ndc, sc.y));
+        double2 ND = cadd(nd0, cscale(nds, sc.x));
         double2 v[8];
         for (int r = 0; r < 2; ++r) {
             double w = r == 0 ? a.w1 : a.w2;

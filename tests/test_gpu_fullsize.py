@@ -1,0 +1,90 @@
+"""Parity at the benchmark workload (two media omega_1 = 4 pi, omega_2 = 6 pi,
+N = 512, M = 256, the problem bench.py times): modal kernels on a sample of
+node pairs that the oracle evaluates one by one, and agreement of the mixed
+and FP64 GPU solves."""
+import numpy as np
+import pytest
+
+from test_gpu_parity import rounding_scale
+
+pytestmark = pytest.mark.gpu
+
+CFG2 = dict(k1=4 * np.pi, k2=6 * np.pi, N=512, M=256)
+
+
+def _take(d, i):
+    return {k: (v[i] if isinstance(v, np.ndarray) else v) for k, v in d.items()}
+
+
+def _sample_pairs(G, Q, rng, n=240):
+    """Grid pairs outside the Alpert skip band: random plus neighbours of the
+    skip band (close pairs), plus pairs touching breakpoints' neighbours."""
+    N = G.P.N
+    pairs = set()
+    while len(pairs) < n // 2:
+        l, m = rng.integers(0, N, 2)
+        if Q.grid_mask[l, m]:
+            pairs.add((int(l), int(m)))
+    gi = G.unk_grid
+    for l in rng.integers(0, N, n // 2):
+        for d in (10, 11, 14, 20):
+            for sgn in (-1, 1):
+                tgt = np.nonzero(gi == gi[l] + sgn * d)[0]
+                if len(tgt):
+                    pairs.add((int(l), int(tgt[0])))
+    return sorted(pairs)
+
+
+def test_modal_kernels_sampled_pairs_fullsize():
+    import torch
+    import oracle.kernels as KR
+    from oracle.assemble import Quadrature
+    from oracle.problem import Geometry, Params
+    from paper_2412_11162_gb300 import Problem
+    P = Problem(CFG2["k1"], CFG2["k2"], CFG2["N"], CFG2["M"])
+    Po = Params(**CFG2)
+    G = Geometry(Po)
+    Q = Quadrature(G)
+    rng = np.random.default_rng(2412)
+    pairs = _sample_pairs(G, Q, rng)
+    li = np.array([p[0] for p in pairs])
+    mi = np.array([p[1] for p in pairs])
+    pg = KR.pair_geometry(_take(G.nodes, li), _take(G.nodes, mi), Po)
+    near = KR.near_mask(pg, Po)
+    lap = KR.laplace_modes({k: v[near] for k, v in pg.items()}, Po.M - 2)
+    rt = G.nodes["rho_t"].imag
+    pml = (rt[li] > 0) | (rt[mi] > 0)
+    assert near.sum() > 20 and (~near).sum() > 20
+    for lo, hi in ((0, 6), (60, 64), (122, 128)):
+        K = P.modal_kernels(lo, hi).cpu().numpy()
+        for reg, omega, sign, ks, kk in (("a", Po.k1, 1.0, 0, 1), ("b", Po.k2, -1.0, 2, 3)):
+            pgr = dict(pg)
+            pgr["nuc_r"] = sign * pg["nuc_r"]
+            pgr["nuc_z"] = sign * pg["nuc_z"]
+            full = (np.zeros((len(near), Po.M - 1), complex), np.zeros((len(near), Po.M - 1), complex))
+            full[0][near] = lap[0]
+            full[1][near] = sign * lap[1]
+            S, Kr = KR.modal_kernels(pgr, omega, Po, lap=full, near=near)
+            for t, n in enumerate(range(lo, hi)):
+                for ref, kern, which in ((S[:, n], ks, "S"), (Kr[:, n], kk, "K")):
+                    got = K[t, kern][li, mi]
+                    d = np.abs(got - ref)
+                    # per pair: rounding of the DFT (far) or of the split (close),
+                    # relative to the magnitude of its inputs
+                    sc = rounding_scale(pgr, near, full, omega, Po.M, Po.taylor_L, n, which)
+                    ok = d <= 1e-12 * sc + 1e-300     # K == 0 exactly on flat-to-flat pairs
+                    ratio = np.where(sc > 0, d / np.where(sc > 0, sc, 1.0), 0.0).max()
+                    assert ok.all(), (reg, n, which, ratio)
+
+
+def test_mixed_matches_fp64_fullsize():
+    import torch
+    from paper_2412_11162_gb300 import Problem
+    from paper_2412_11162_gb300.binding import PMLBIE_FP64, PMLBIE_MIXED
+    P = Problem(CFG2["k1"], CFG2["k2"], CFG2["N"], CFG2["M"])
+    o64, r64 = P.solve([np.pi / 6], precision=PMLBIE_FP64)
+    o32, r32 = P.solve([np.pi / 6], precision=PMLBIE_MIXED)
+    assert r32.residual <= 1e-13
+    for k in ("u1", "u2"):
+        e = (torch.linalg.vector_norm(o32[k] - o64[k]) / torch.linalg.vector_norm(o64[k])).item()
+        assert e <= 1e-6, (k, e)

@@ -40,35 +40,58 @@ def oracle_solution(**kw):
 CFG1 = dict(k1=TWO_PI, k2=3 * np.pi, N=128, M=64)
 
 
-def _split_term_scale(sysm, reg, n):
-    """Magnitude scale of the close-pair split of the S kernel for mode n, per
-    grid pair: (1/2pi) sum_k |Z^_{n-k}| (2pi/M) sum_j |f1(psi_j)| +
-    (2pi/M) sum_j |r1(psi_j)|.  FFT and convolution rounding is bounded by a
-    small multiple of eps times this scale; for pairs in the PML it exceeds
-    |S^_n| by up to ~1e9 at M = 64 (Sec. 4.3 substitution with |q| ~ 40),
-    which is what limits agreement there."""
+def split_scale(pg, Zm, omega, M, L, n):
+    """Magnitude scale of the close-pair split of the S kernel for mode n (one
+    value per pair of pg, whose exact modal Laplace kernels are Zm):
+    (1/2pi) sum_k |Z^_{n-k}| (2pi/M) sum_j |f1(psi_j)| + (2pi/M) sum_j |r1(psi_j)|.
+    FFT and convolution rounding is bounded by a small multiple of eps times
+    this scale; for pairs in the PML it exceeds |S^_n| by up to ~1e9 at
+    M = 64 (Sec. 4.3 substitution with |q| ~ 40) and more at larger |q|, which
+    is what limits agreement there."""
     import oracle.kernels as KR
+    psi = 2 * np.pi * np.arange(M) / M
+    f1, r1, f3, r3 = KR.split_samples(pg, omega, psi, L)
+    f1_in = (2 * np.pi / M) * np.abs(f1).sum(axis=1)
+    r1_in = (2 * np.pi / M) * np.abs(r1).sum(axis=1)
+    kv = np.arange(-(M // 2 - 1), M // 2)
+    conv = np.abs(Zm)[:, np.abs(n - kv)].sum(axis=1) * f1_in / (2 * np.pi)
+    return conv + r1_in
+
+
+def rounding_scale(pg, near, lap, omega, M, L, n, which):
+    """Per-pair magnitude that bounds the rounding of mode n of kernel `which`
+    ('S' or 'K'): (2pi/M) sum_j |F(psi_j)| for far pairs (the DFT's inputs),
+    the split's term scale for close pairs (with D^ and f3, r3 for K)."""
+    import oracle.kernels as KR
+    psi = 2 * np.pi * np.arange(M) / M
+    out = np.zeros(len(near))
+    far = ~near
+    if far.any():
+        S, K = KR.kernel_samples({k: v[far] for k, v in pg.items()}, omega, psi)
+        F = S if which == "S" else K
+        out[far] = (2 * np.pi / M) * np.abs(F).sum(axis=1)
+    if near.any():
+        sub = {k: v[near] for k, v in pg.items()}
+        f1, r1, f3, r3 = KR.split_samples(sub, omega, psi, L)
+        f, r, Xm = (f1, r1, lap[0][near]) if which == "S" else (f3, r3, lap[1][near])
+        kv = np.arange(-(M // 2 - 1), M // 2)
+        conv = np.abs(Xm)[:, np.abs(n - kv)].sum(axis=1) * (2 * np.pi / M) * np.abs(f).sum(axis=1) / (2 * np.pi)
+        out[near] = conv + (2 * np.pi / M) * np.abs(r).sum(axis=1)
+    return out
+
+
+def _split_term_scale(sysm, reg, n):
+    """split_scale for every grid pair of an oracle ModalSystem (0 for far pairs)."""
     P = sysm.P
-    M = P.M
     near = sysm.near[: sysm.ngrid]
     scale = np.zeros(sysm.ngrid)
     idx = np.nonzero(near)[0]
     if len(idx) == 0:
         return scale
     pg = {k: v[idx] for k, v in sysm.pg.items()}
+    Zm = sysm.lap_near[0][np.searchsorted(np.nonzero(sysm.near)[0], idx)]
     omega = P.k1 if reg == "a" else P.k2
-    psi = 2 * np.pi * np.arange(M) / M
-    f1, r1, f3, r3 = KR.split_samples(pg, omega, psi, P.taylor_L)
-    k = np.arange(M)[:, None]
-    kk = np.arange(-(M // 2 - 1), M // 2)[None, :]
-    Ek = (2 * np.pi / M) * np.exp(-2j * np.pi * k * kk / M)
-    # rounding of an M-point DFT is relative to the size of its inputs
-    f1_in = (2 * np.pi / M) * np.abs(f1).sum(axis=1)
-    r1_in = (2 * np.pi / M) * np.abs(r1).sum(axis=1)
-    Zm = np.abs(sysm.lap_near[0][np.searchsorted(np.nonzero(sysm.near)[0], idx)])
-    kv = np.arange(-(M // 2 - 1), M // 2)
-    conv = Zm[:, np.abs(n - kv)].sum(axis=1) * f1_in / (2 * np.pi)
-    scale[idx] = conv + r1_in
+    scale[idx] = split_scale(pg, Zm, omega, P.M, P.taylor_L, n)
     return scale
 
 

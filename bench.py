@@ -32,6 +32,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(k1=4 * np.pi, k2=6 * np.pi, N=512, M=256, a1=2.5, T=1.0, S=3.0, bump_h=0.2, polar=np.pi / 6)
+# smaller case of the same physics for profiler captures (matrices ~270 MB, above L2)
+WORKLOADS = {"default": WORKLOAD, "small": dict(WORKLOAD, N=256, M=128)}
 METRIC = "modal kernel entries/s and solve s/problem, mixed vs FP64 GPU at 1e-6 rel err"
 UNIT = "entries/s"
 
@@ -254,10 +256,10 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128 kernels / c64 LU / c128 refinement", "data": "synthetic",
-        "config": {"workload": "two-layer bump, N=512 M=256 (128 modes), k1=4pi k2=6pi, PML a1=2.5 T=1 S=3, "
-                               "1 plane wave at 30 deg, mixed precision",
+        "config": {"workload": "two-layer bump, N=%d M=%d (%d modes), k1=4pi k2=6pi, PML a1=2.5 T=1 S=3, "
+                               "1 plane wave at 30 deg, mixed precision" % (w["N"], w["M"], w["M"] // 2),
                    "parallelism": "independent problems per GPU" if world > 1 else "1 GPU",
-                   "l2": "working set > L2: %d MB of per-mode matrices rebuilt every step" %
+                   "l2": "working set > L2 (129 MB): %d MB of per-mode matrices rebuilt every step" %
                          int(((w["M"] // 2) * (2 * w["N"]) ** 2 * 24) / 1e6)},
         "solve_s_per_problem": ms / 1e3,
         "kernel_entries_per_s": epp / ((last.ms_far + last.ms_near + last.ms_assemble) / 1e3),
@@ -334,7 +336,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="default", choices=sorted(WORKLOADS),
+                    help="'small' (N=256, M=128) is for profiler captures only")
     args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

@@ -68,7 +68,7 @@ typedef struct {
     double   a1, T, S;        /* PML start radius, thickness, strength (Eq. (sgm1))  */
     int      p;               /* PML profile and grading exponent (Sec. 5: 6), >= 2  */
     int      N;               /* unknown nodes on gamma_AB, >= 32                    */
-    int      M;               /* azimuthal samples, 2^a 3^b, 16 <= M <= 1024          */
+    int      M;               /* azimuthal samples, 2^a 3^b, 4 | M, 16 <= M <= 768   */
     int      curve_kind;      /* PMLBIE_CURVE_*                                       */
     double   bump_h, bump_w, bump_R;   /* Gaussian bump (kind 0)                     */
     int      n_vertices;      /* polyline (kind 1): vertex count                     */

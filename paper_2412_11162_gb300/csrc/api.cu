@@ -215,7 +215,8 @@ int pmlbie_create(const pmlbie_params* P, pmlbie_problem** out) {
     if (!(P->a1 > 0) || !(P->T > 0) || !(P->S >= 0)) return fail(PMLBIE_EINVAL, "PML needs a1 > 0, T > 0, S >= 0");
     if (P->p < 2 || P->p > 16) return fail(PMLBIE_EINVAL, "p must be in [2, 16]");
     if (P->N < 32 || P->N > 16384) return fail(PMLBIE_EINVAL, "N must be in [32, 16384]");
-    if (P->M < 16 || P->M > 1024 || !is_2a3b(P->M)) return fail(PMLBIE_EINVAL, "M must be 2^a 3^b in [16, 1024]");
+    if (P->M < 16 || P->M > 768 || P->M % 4 || !is_2a3b(P->M))
+        return fail(PMLBIE_EINVAL, "M must be 2^a 3^b, a multiple of 4, in [16, 768]");
     if (P->taylor_L < 3 || P->taylor_L > 7) return fail(PMLBIE_EINVAL, "taylor_L must be in [3, 7]");
     if (!(P->split_c > 0)) return fail(PMLBIE_EINVAL, "split_c must be positive");
     if (P->curve_kind == PMLBIE_CURVE_GAUSS_BUMP) {

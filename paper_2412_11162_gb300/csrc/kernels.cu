@@ -64,7 +64,8 @@ __device__ __forceinline__ double2 clog(double2 z) { return c2(log(hypot(z.x, z.
 // memory, radices 4, 2, 3 (M = 2^a 3^b).  x, y: two buffers of M elements;
 // returns the buffer holding the result.  tw[e] = e^{-2 pi i e / M}.
 // ---------------------------------------------------------------------------
-__device__ double2* warp_fft(double2* x, double2* y, int M, const double2* tw, int lane) {
+__device__ double2* warp_fft(double2* x, double2* y, int M, const double2* tw, int lane, int tws = 1) {
+    // tw[e * tws] = e^{-2 pi i e / M}
     int rem = M, Ns = 1;
     while (rem > 1) {
         int R = (rem % 4 == 0) ? 4 : ((rem % 2 == 0) ? 2 : 3);
@@ -73,7 +74,7 @@ __device__ double2* warp_fft(double2* x, double2* y, int M, const double2* tw, i
             int k = j % Ns;
             double2 v[4];
             for (int r = 0; r < R; ++r) v[r] = x[j + r * MR];
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[(r * k * step) % M]);
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[((r * k * step) % M) * tws]);
             if (R == 2) {
                 double2 a = v[0], b = v[1];
                 v[0] = cadd(a, b);
@@ -115,6 +116,66 @@ __device__ void warp_fft_inplace(double2* buf, double2* scratch, int M, const do
         for (int i = lane; i < M; i += 32) buf[i] = r[i];
         __syncwarp();
     }
+}
+
+// DFT of an even sequence x_0..x_{L-1} (x_k = x_{L-k}, L = 2K, K even) from
+// its K+1 distinct values, in place: xh[0..K] -> X_0..X_K.  Real and imaginary
+// parts are two real-even (DCT-I) transforms; each is reduced to a K-point
+// transform of y_j = (x_j + x_{K-j})/2 - sin(pi j/K)(x_j - x_{K-j}) -- the two
+// are packed into one complex K-point FFT -- after which the even outputs are
+// the real parts and the odd outputs follow from the imaginary parts by a
+// running sum started at F_1 = (x_0 - x_K)/2 + sum_j x_j cos(pi j/K).
+// y, scr: warp scratch of K elements; twL[e * tws] = e^{-2 pi i e / L}.
+__device__ void warp_even_dft(double2* xh, double2* y, double2* scr, int K, const double2* twL, int tws,
+                              int lane) {
+    double2 part = c2(0.0, 0.0);
+    for (int j = lane; j < K; j += 32) {
+        double2 a = xh[j], b = xh[K - j];
+        double2 t = twL[j * tws];            // (cos(pi j/K), -sin(pi j/K))
+        double s = -t.y;
+        y[j] = c2(0.5 * (a.x + b.x) - s * (a.x - b.x), 0.5 * (a.y + b.y) - s * (a.y - b.y));
+        if (j > 0) part = cadd(part, cscale(a, t.x));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        part.x += __shfl_xor_sync(0xffffffff, part.x, o);
+        part.y += __shfl_xor_sync(0xffffffff, part.y, o);
+    }
+    const double2 F1 = c2(part.x + 0.5 * (xh[0].x - xh[K].x), part.y + 0.5 * (xh[0].y - xh[K].y));
+    __syncwarp();
+    double2* Z = warp_fft(y, scr, K, twL, lane, 2 * tws);
+    double2* I = (Z == y) ? scr : y;         // imaginary parts for the running sum
+    const int H = K / 2;
+    for (int kk = lane; kk <= H; kk += 32) {
+        double2 zk = Z[kk], zc = Z[(K - kk) % K];
+        // Ya = (z_k + conj(z_{K-k}))/2, Yb = (z_k - conj(z_{K-k}))/(2i)
+        double yax = 0.5 * (zk.x + zc.x), yay = 0.5 * (zk.y - zc.y);
+        double pbx = zk.x - zc.x, pby = zk.y + zc.y;
+        double ybx = 0.5 * pby, yby = -0.5 * pbx;
+        xh[2 * kk] = c2(2.0 * yax, 2.0 * ybx);
+        I[kk] = c2(yay, yby);
+    }
+    __syncwarp();
+    // odd outputs: F_{2k+1} = F_1 - sum_{m=1}^{k} Im Y_m, k = 0..H-1 (a warp scan)
+    const int per = (H + 31) / 32;
+    const int b0 = lane * per;
+    double2 run = c2(0.0, 0.0);
+    for (int q = 0; q < per; ++q) {
+        int kk = b0 + q;
+        if (kk >= 1 && kk < H) run = cadd(run, I[kk]);
+    }
+    double2 incl = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        double2 v = c2(__shfl_up_sync(0xffffffff, incl.x, o), __shfl_up_sync(0xffffffff, incl.y, o));
+        if (lane >= o) incl = cadd(incl, v);
+    }
+    double2 acc = csub(incl, run);           // exclusive prefix of this lane's chunk
+    for (int q = 0; q < per; ++q) {
+        int kk = b0 + q;
+        if (kk >= H) break;
+        if (kk >= 1) acc = cadd(acc, I[kk]);
+        xh[2 * kk + 1] = c2(2.0 * (F1.x - acc.x), 2.0 * (F1.y - acc.y));
+    }
+    __syncwarp();
 }
 
 // Per-pair geometry of a grid pair from node tables.
@@ -161,13 +222,13 @@ struct FarArgs {
 
 __global__ void far_kernel(FarArgs a) {
     extern __shared__ double2 smem[];
-    const int M = a.M, N = a.N;
+    const int M = a.M, N = a.N, K = M / 2, S1 = K + 1;
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double2* tw = smem;                         // M
-    double2* cs = tw + M;                       // M/2 + 1: (sin^2(psi/2), cos psi)
-    double2* buf = cs + (M / 2 + 1) + warp * 5 * M;
+    double2* tw = smem;                         // M: e^{-2 pi i e / M}
+    double2* cs = tw + M;                       // K + 1: (sin^2(psi/2), cos psi)
+    double2* buf = cs + S1 + warp * (4 * S1 + 2 * K);   // 4 sequences of K+1, then 2 x K scratch
     for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = a.T.twid[i];
-    for (int i = threadIdx.x; i <= M / 2; i += blockDim.x) cs[i] = a.T.cos_tab[i];
+    for (int i = threadIdx.x; i <= K; i += blockDim.x) cs[i] = a.T.cos_tab[i];
     __syncthreads();
 
     const int m = blockIdx.y;
@@ -175,7 +236,7 @@ __global__ void far_kernel(FarArgs a) {
     bool active = l < N && a.T.cls[(size_t)l * N + m] == kFar;
     if (active) {
         PairGeom g = grid_pair(a.T, l, m);
-        for (int j = lane; j <= M / 2; j += 32) {
+        for (int j = lane; j <= K; j += 32) {
             double2 sc = cs[j];
             double2 D2 = cadd(g.d2, cscale(g.rr, 4.0 * sc.x));
             double2 R = csqrt(D2);
@@ -183,24 +244,19 @@ __global__ void far_kernel(FarArgs a) {
             double2 iR3 = cmul(iR, cmul(iR, iR));
             double2 ND = cadd(g.nd0, cscale(g.nds, sc.x));
             double2 Dk = cscale(cmul(ND, iR3), -kInv4Pi);   // region a
-            double2 v[4];
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 double w = r == 0 ? a.w1 : a.w2;
                 double2 q = cscale(R, w);
                 double2 e = cexpi(q);
-                v[2 * r] = cscale(cmul(e, iR), kInv4Pi);
-                double2 K = cmul(cmul(Dk, e), c2(1.0 + q.y, -q.x));   // (1 - i q)
-                v[2 * r + 1] = r == 0 ? K : cscale(K, -1.0);           // region b: normal -nu
-            }
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                buf[s * M + j] = v[s];
-                if (j > 0 && j < M / 2) buf[s * M + M - j] = v[s];
+                buf[(2 * r) * S1 + j] = cscale(cmul(e, iR), kInv4Pi);
+                double2 Kv = cmul(cmul(Dk, e), c2(1.0 + q.y, -q.x));   // (1 - i q)
+                buf[(2 * r + 1) * S1 + j] = r == 0 ? Kv : cscale(Kv, -1.0);   // region b: normal -nu
             }
         }
         __syncwarp();
-        for (int s = 0; s < 4; ++s) warp_fft_inplace(buf + s * M, buf + 4 * M, M, tw, lane);
+        double2* y = buf + 4 * S1;
+        for (int s = 0; s < 4; ++s) warp_even_dft(buf + s * S1, y, y + K, K, tw, 1, lane);
     }
     __syncthreads();
 
@@ -214,22 +270,22 @@ __global__ void far_kernel(FarArgs a) {
             int ll = blockIdx.x * nw + w;
             if (ll >= N) continue;
             bool act = a.T.cls[(size_t)ll * N + m] == kFar;
-            const double2* b = smem + M + (M / 2 + 1) + w * 5 * M;
+            const double2* b = smem + M + S1 + w * (4 * S1 + 2 * K);
             double2 val = c2(0.0, 0.0);
             int row = ll, col = m;
             // blocks: 0 K^a -> (l, m); 1 -S^a -> (l, N+m); 2 K^b -> (N+l, m); 3 S^b -> (N+l, N+m)
             if (blk == 0) {
-                if (act) val = cscale(b[1 * M + a.mode_lo + n], scale * a.h * a.T.Wu[m]);
+                if (act) val = cscale(b[1 * S1 + a.mode_lo + n], scale * a.h * a.T.Wu[m]);
             } else if (blk == 1) {
                 col = N + m;
-                if (act) val = cscale(b[0 * M + a.mode_lo + n], -scale * a.h * a.T.Wphi[m]);
+                if (act) val = cscale(b[0 * S1 + a.mode_lo + n], -scale * a.h * a.T.Wphi[m]);
             } else if (blk == 2) {
                 row = N + ll;
-                if (act) val = cscale(b[3 * M + a.mode_lo + n], scale * a.h * a.T.Wu[m]);
+                if (act) val = cscale(b[3 * S1 + a.mode_lo + n], scale * a.h * a.T.Wu[m]);
             } else {
                 row = N + ll;
                 col = N + m;
-                if (act) val = cscale(b[2 * M + a.mode_lo + n], scale * a.h * a.T.Wphi[m]);
+                if (act) val = cscale(b[2 * S1 + a.mode_lo + n], scale * a.h * a.T.Wphi[m]);
             }
             a.A[(size_t)n * msz + (size_t)col * ld + row] = val;
         }
@@ -242,8 +298,8 @@ __global__ void far_kernel(FarArgs a) {
             int ll = blockIdx.x * nw + w;
             if (ll >= N) continue;
             bool act = a.T.cls[(size_t)ll * N + m] == kFar;
-            const double2* b = smem + M + (M / 2 + 1) + w * 5 * M;
-            double2 val = act ? cscale(b[kern * M + a.mode_lo + n], scale) : c2(0.0, 0.0);
+            const double2* b = smem + M + S1 + w * (4 * S1 + 2 * K);
+            double2 val = act ? cscale(b[kern * S1 + a.mode_lo + n], scale) : c2(0.0, 0.0);
             a.raw[((size_t)n * 4 + kern) * NN + (size_t)ll * N + m] = val;
         }
     }
@@ -375,12 +431,14 @@ __device__ __forceinline__ double2 cpoly(const double2* c, int deg, double2 q) {
 // Correction pairs that are far by the criterion use the plain FFT.
 __global__ void near_modes_kernel(NearArgs a) {
     extern __shared__ double2 smem[];
-    const int M = a.M, p = blockIdx.x;
+    const int M = a.M, K = M / 2, S1 = K + 1, L2 = 2 * M, S2 = M + 1, p = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double2* tw = smem;                 // M
-    double2* seq = tw + M;              // 8 * M
-    double2* scr = seq + 8 * M;         // 4 * M (one per warp), or 4 * 2M with the FFT convolution
-    for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = a.T.twid[i];
+    double2* tw2 = smem;                // 2M: e^{-2 pi i e / (2M)}
+    double2* seq = tw2 + L2;            // 8 sequences of K+1 (even samples, then their spectra)
+    double2* cv = seq + 8 * S1;         // 4 sequences of M+1 (convolution)
+    double2* scr = cv + 4 * S2;         // per warp: 2 x M scratch
+    double2* wy = scr + warp * 2 * M;
+    for (int i = threadIdx.x; i < L2; i += blockDim.x) tw2[i] = a.T.twid2[i];
     NearPair q = a.np[p];
     const bool plain = (q.flags & kFlagFar) != 0;
     const bool subst = (q.flags & kFlagSubst) != 0;
@@ -396,7 +454,7 @@ __global__ void near_modes_kernel(NearArgs a) {
     for (int k = 1; k <= a.L; ++k) u1[k - 1] = cscale(a.pa[k], -1.0);
     for (int k = 3; k <= a.L; ++k) v3[k - 3] = cscale(a.pb[k], -1.0);
     __syncthreads();
-    for (int j = threadIdx.x; j <= M / 2; j += blockDim.x) {
+    for (int j = threadIdx.x; j <= K; j += blockDim.x) {
         double2 sc = a.T.cos_tab[j];
         double2 D2 = cadd(q.d2, cscale(q.rr, 4.0 * sc.x));
         double2 R = csqrt(D2);
@@ -445,16 +503,13 @@ __global__ void near_modes_kernel(NearArgs a) {
                 v[4 * r + 3] = cmul(ND, c2(0.0, -w * w * w * kInv4Pi * h4 * sg));
             }
         }
-        for (int s = 0; s < 8; ++s) {
-            seq[s * M + j] = v[s];
-            if (j > 0 && j < M / 2) seq[s * M + M - j] = v[s];
-        }
+        for (int s = 0; s < 8; ++s) seq[s * S1 + j] = v[s];
     }
     __syncthreads();
-    // eight FFTs, two per warp (plain pairs need only 0, 2, 4, 6)
+    // eight even-sequence DFTs of length M, two per warp (plain pairs need only 0, 2, 4, 6)
     for (int s = warp; s < 8; s += 4) {
         if (plain && (s & 1)) continue;
-        warp_fft_inplace(seq + s * M, scr + warp * M, M, tw, lane);
+        warp_even_dft(seq + s * S1, wy, wy + M, K, tw2, 2, lane);
     }
     __syncthreads();
     const double scale = 2.0 * kPi / M;
@@ -465,83 +520,54 @@ __global__ void near_modes_kernel(NearArgs a) {
     if (plain) {
         for (int t = threadIdx.x; t < nmodes; t += blockDim.x) {
             int n = a.mode_lo + t;
-            out[0 * (size_t)nmodes + t] = cscale(seq[0 * M + n], scale);
-            out[1 * (size_t)nmodes + t] = cscale(seq[2 * M + n], scale);
-            out[2 * (size_t)nmodes + t] = cscale(seq[4 * M + n], scale);
-            out[3 * (size_t)nmodes + t] = cscale(seq[6 * M + n], scale);
+            out[0 * (size_t)nmodes + t] = cscale(seq[0 * S1 + n], scale);
+            out[1 * (size_t)nmodes + t] = cscale(seq[2 * S1 + n], scale);
+            out[2 * (size_t)nmodes + t] = cscale(seq[4 * S1 + n], scale);
+            out[3 * (size_t)nmodes + t] = cscale(seq[6 * S1 + n], scale);
         }
         return;
     }
-    if (a.conv_fft) {
-        // circular convolution of length L = 2M, exact for n in [0, M/2):
-        // zZ[m] = Z^_{|m|}, zD[m] = D^_{|m|} (|m| <= M-2), c[k] = C_{|k|} (|k| <= M/2-1);
-        // the two media are done one after the other with the same Z, D spectra
-        const int L = 2 * M;
-        double2* tw2 = scr + 4 * L;          // L twiddles
-        double2* zZ = tw2 + L;               // 4 sequences of length L
-        double2* zD = zZ + L;
-        double2* cS = zD + L;
-        double2* cK = cS + L;
-        for (int i = threadIdx.x; i < L; i += blockDim.x) tw2[i] = a.T.twid2[i];
-        for (int i = threadIdx.x; i < L; i += blockDim.x) {
-            int m = i <= L / 2 ? i : L - i;      // |index| on the circle
-            bool inz = m <= M - 2;
-            zZ[i] = inz ? Z[m] : c2(0.0, 0.0);
-            zD[i] = inz ? Dd[m] : c2(0.0, 0.0);
+    // convolution (1/2pi) sum_{|k| < M/2} X^_{|n-k|} C_k as a circular convolution
+    // of length 2M (exact for n < M/2) of the even sequences zZ[m] = Z^_{|m|}
+    // (|m| <= M-2), zD[m] = D^_{|m|}, c[k] = C_{|k|} (|k| <= M/2-1); all are even,
+    // so every transform is an even-sequence DFT of M+1 values, and the inverse
+    // of an even sequence is its forward transform divided by 2M.  The two
+    // media are done one after the other with the same Z, D spectra.
+    double2* zZ = cv;
+    double2* zD = cv + S2;
+    double2* cS = cv + 2 * S2;
+    double2* cK = cv + 3 * S2;
+    for (int i = threadIdx.x; i <= M; i += blockDim.x) {
+        bool inz = i <= M - 2;
+        zZ[i] = inz ? Z[i] : c2(0.0, 0.0);
+        zD[i] = inz ? Dd[i] : c2(0.0, 0.0);
+    }
+    __syncthreads();
+    if (warp < 2) warp_even_dft(warp == 0 ? zZ : zD, wy, wy + M, M, tw2, 1, lane);
+    const double c = 1.0 / (2.0 * kPi * L2);
+    for (int r = 0; r < 2; ++r) {
+        const double sgn = r == 0 ? 1.0 : -1.0;      // region b: D^ -> -D^
+        for (int i = threadIdx.x; i <= M; i += blockDim.x) {
+            bool in = i <= K - 1;
+            cS[i] = in ? cscale(seq[(4 * r + 0) * S1 + i], scale) : c2(0.0, 0.0);
+            cK[i] = in ? cscale(seq[(4 * r + 2) * S1 + i], scale) : c2(0.0, 0.0);
         }
         __syncthreads();
-        if (warp < 2) warp_fft_inplace(warp == 0 ? zZ : zD, scr + warp * L, L, tw2, lane);
-        const double c = 1.0 / (2.0 * kPi * L);
-        for (int r = 0; r < 2; ++r) {
-            const double sgn = r == 0 ? 1.0 : -1.0;      // region b: D^ -> -D^
-            for (int i = threadIdx.x; i < L; i += blockDim.x) {
-                int m = i <= L / 2 ? i : L - i;
-                bool in = m <= M / 2 - 1;
-                cS[i] = in ? cscale(seq[(4 * r + 0) * M + m], scale) : c2(0.0, 0.0);
-                cK[i] = in ? cscale(seq[(4 * r + 2) * M + m], scale) : c2(0.0, 0.0);
-            }
-            __syncthreads();
-            if (warp >= 2) warp_fft_inplace(warp == 2 ? cS : cK, scr + warp * L, L, tw2, lane);
-            __syncthreads();
-            // conjugated products, so the forward FFT gives L times the inverse transform
-            for (int i = threadIdx.x; i < L; i += blockDim.x) {
-                double2 v0 = cmul(zZ[i], cS[i]);
-                double2 v1 = cscale(cmul(zD[i], cK[i]), sgn);
-                cS[i] = c2(v0.x, -v0.y);
-                cK[i] = c2(v1.x, -v1.y);
-            }
-            __syncthreads();
-            if (warp >= 2) warp_fft_inplace(warp == 2 ? cS : cK, scr + warp * L, L, tw2, lane);
-            __syncthreads();
-            for (int t = threadIdx.x; t < nmodes; t += blockDim.x) {
-                int n = a.mode_lo + t;
-                double2 os = c2(cS[n].x * c, -cS[n].y * c);
-                double2 ok = c2(cK[n].x * c, -cK[n].y * c);
-                out[(2 * r + 0) * (size_t)nmodes + t] = cadd(os, cscale(seq[(4 * r + 1) * M + n], scale));
-                out[(2 * r + 1) * (size_t)nmodes + t] = cadd(ok, cscale(seq[(4 * r + 3) * M + n], scale));
-            }
-            __syncthreads();
+        if (warp >= 2) warp_even_dft(warp == 2 ? cS : cK, wy, wy + M, M, tw2, 1, lane);
+        __syncthreads();
+        for (int i = threadIdx.x; i <= M; i += blockDim.x) {
+            cS[i] = cmul(zZ[i], cS[i]);
+            cK[i] = cscale(cmul(zD[i], cK[i]), sgn);
         }
-        return;
-    }
-    for (int t = threadIdx.x; t < nmodes; t += blockDim.x) {
-        int n = a.mode_lo + t;
-        double2 sa = c2(0, 0), sb = c2(0, 0), ka = c2(0, 0), kb = c2(0, 0);
-        for (int k = -(M / 2 - 1); k <= M / 2 - 1; ++k) {
-            int kk = k < 0 ? -k : k;
-            int mm = n - k;
-            mm = mm < 0 ? -mm : mm;
-            double2 z = Z[mm], d = Dd[mm];
-            sa = cadd(sa, cmul(z, seq[0 * M + kk]));
-            ka = cadd(ka, cmul(d, seq[2 * M + kk]));
-            sb = cadd(sb, cmul(z, seq[4 * M + kk]));
-            kb = csub(kb, cmul(d, seq[6 * M + kk]));   // region b: D^ -> -D^
+        __syncthreads();
+        if (warp >= 2) warp_even_dft(warp == 2 ? cS : cK, wy, wy + M, M, tw2, 1, lane);
+        __syncthreads();
+        for (int t = threadIdx.x; t < nmodes; t += blockDim.x) {
+            int n = a.mode_lo + t;
+            out[(2 * r + 0) * (size_t)nmodes + t] = cadd(cscale(cS[n], c), cscale(seq[(4 * r + 1) * S1 + n], scale));
+            out[(2 * r + 1) * (size_t)nmodes + t] = cadd(cscale(cK[n], c), cscale(seq[(4 * r + 3) * S1 + n], scale));
         }
-        const double c = scale / (2.0 * kPi);
-        out[0 * (size_t)nmodes + t] = cadd(cscale(sa, c), cscale(seq[1 * M + n], scale));
-        out[1 * (size_t)nmodes + t] = cadd(cscale(ka, c), cscale(seq[3 * M + n], scale));
-        out[2 * (size_t)nmodes + t] = cadd(cscale(sb, c), cscale(seq[5 * M + n], scale));
-        out[3 * (size_t)nmodes + t] = cadd(cscale(kb, c), cscale(seq[7 * M + n], scale));
+        __syncthreads();
     }
 }
 
@@ -741,7 +767,7 @@ __global__ void outputs_kernel(int N, int nmodes, int nrhs, const double2* X, co
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static int far_warps(int M) { return M <= 256 ? 8 : (M <= 512 ? 4 : 2); }
+static int far_warps(int M) { return M <= 512 ? 8 : 4; }
 
 cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStream_t s) {
     const int N = prob->P.N, M = prob->P.M;
@@ -757,7 +783,8 @@ cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStre
     a.A = fl.A;
     a.raw = fl.raw;
     int nw = far_warps(M);
-    size_t smem = sizeof(double2) * ((size_t)M + M / 2 + 1 + (size_t)nw * 5 * M);
+    const size_t S1 = M / 2 + 1;
+    size_t smem = sizeof(double2) * ((size_t)M + S1 + (size_t)nw * (4 * S1 + M));
     cudaError_t e = cudaFuncSetAttribute(far_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((N + nw - 1) / nw, N);
@@ -809,9 +836,9 @@ cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, do
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // FFT convolution: tw (M) + seq (8M) + scratch (4 x 2M) + tw2 (2M) + 4 x 2M buffers = 27M
-    a.conv_fft = M <= 512 ? 1 : 0;
-    size_t smem = sizeof(double2) * (size_t)M * (a.conv_fft ? 27 : 13);
+    // tw2 (2M) + 8 x (M/2+1) + 4 x (M+1) + 4 warps x 2M scratch
+    a.conv_fft = 1;
+    size_t smem = sizeof(double2) * ((size_t)2 * M + 8 * (M / 2 + 1) + 4 * (M + 1) + 8 * (size_t)M);
     e = cudaFuncSetAttribute(near_modes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     near_modes_kernel<<<a.npairs, 128, smem, s>>>(a);

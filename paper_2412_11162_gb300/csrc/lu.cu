@@ -282,7 +282,7 @@ __global__ void gemm_update_kernel(int n, int k0, int kb, T* A) {
 }
 
 // Solve LU x = b for every matrix and rhs: row swaps, then blocked unit-lower
-// forward and upper backward substitution.  One CTA (256 threads) per
+// forward and upper backward substitution.  One CTA (512 threads) per
 // (matrix, rhs); B is [b][n][nrhs].  The right-hand side lives in shared
 // memory for the whole solve; each 32-row diagonal block is solved by one
 // warp, then the rows outside it are updated with a coalesced
@@ -293,17 +293,21 @@ __global__ void lu_solve_kernel(int n, int nrhs, const T* LU, const int* piv, T*
     const int b = blockIdx.x, r = blockIdx.y;
     if (active && !active[b]) return;
     extern __shared__ unsigned char smraw[];
-    T* sxv = reinterpret_cast<T*>(smraw);   // n entries
+    T* sxv = reinterpret_cast<T*>(smraw);                    // n entries
+    int* spv = reinterpret_cast<int*>(sxv + n);              // n pivots
     const T* a = LU + (size_t)b * n * n;
     const int* pv = piv + (size_t)b * n;
     T* x = B + (size_t)b * n * nrhs;
     __shared__ T sD[kNB][kNB + 1];   // diagonal block, sD[col][row]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < n; i += blockDim.x) sxv[i] = x[(size_t)i * nrhs + r];
+    for (int i = tid; i < n; i += blockDim.x) {
+        sxv[i] = x[(size_t)i * nrhs + r];
+        spv[i] = pv[i];
+    }
     __syncthreads();
     if (tid == 0)
         for (int j = 0; j < n; ++j) {
-            int p = pv[j];
+            int p = spv[j];
             if (p != j) {
                 T t = sxv[j];
                 sxv[j] = sxv[p];
@@ -429,12 +433,12 @@ template <typename T>
 cudaError_t batched_lu_solve(int n, int batch, int nrhs, const T* LU, const int* piv, T* B,
                              cudaStream_t s, const int* active) {
     dim3 g(batch, nrhs);
-    size_t sm = sizeof(T) * (size_t)n;
+    size_t sm = (sizeof(T) + sizeof(int)) * (size_t)n;
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(lu_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    lu_solve_kernel<T><<<g, 256, sm, s>>>(n, nrhs, LU, piv, B, active);
+    lu_solve_kernel<T><<<g, 512, sm, s>>>(n, nrhs, LU, piv, B, active);
     count_launch();
     return cudaGetLastError();
 }

@@ -60,6 +60,125 @@ __device__ __forceinline__ double2 cexpi(double2 q) {
 __device__ __forceinline__ double2 clog(double2 z) { return c2(log(hypot(z.x, z.y)), atan2(z.y, z.x)); }
 
 // ---------------------------------------------------------------------------
+// Elementary functions for the sampling loops.  The FP64 pipe of the GB300
+// retires 2 FMA per SM per clock, so every FP64 instruction in the sampling
+// loops counts; these versions do only what the kernels' argument ranges need.
+//   exp: Cody-Waite reduction x = n ln2 + r (|r| <= ln2/2, ln2 split into a
+//        40-bit head and a tail so n ln2_hi is exact), Taylor series of e^r to
+//        r^13 (remainder < 2e-16 relative), 2^n built in the exponent field.
+//        Arguments are clamped to [-708, 709]: results below e^-708 are
+//        returned as e^-708 (~3e-308), negligible against every kernel value.
+//   sin, cos: Cody-Waite reduction by pi/2 (three-part split, 33-bit heads,
+//        exact products for |n| < 2^20), Taylor series to r^15 / r^16 on
+//        |r| <= pi/4 (remainders < 5e-17), quadrant by integer selects.  The
+//        library sincos handles |x| >= 2^19 (never reached by the kernels).
+//   1/sqrt: hardware approximation refined by three Newton steps
+//        y <- y (3 - x y^2)/2 (quadratic convergence from >= 12 bits).
+// ---------------------------------------------------------------------------
+constexpr double kRoundShift = 6755399441055744.0;   // 1.5 * 2^52
+constexpr double kInvLn2 = 1.4426950408889634;
+constexpr double kLn2Hi = 0.6931471805592082;        // 40 significant bits
+constexpr double kLn2Lo = 7.371002565167799e-13;
+constexpr double kTwoOverPi = 0.6366197723675814;
+constexpr double kPio2A = 1.5707963267341256;        // 33 bits
+constexpr double kPio2B = 6.077100506303966e-11;     // 33 bits
+constexpr double kPio2C = 2.0222662487959506e-21;
+
+__device__ __forceinline__ double fexp(double x) {
+    x = fmin(fmax(x, -708.0), 709.0);
+    double kd = fma(x, kInvLn2, kRoundShift);
+    const int n = __double2loint(kd);
+    kd -= kRoundShift;
+    double r = fma(-kd, kLn2Hi, x);
+    r = fma(-kd, kLn2Lo, r);
+    double p = 1.6059043836821613e-10;   // 1/13!
+    p = fma(p, r, 2.08767569878681e-09);
+    p = fma(p, r, 2.505210838544172e-08);
+    p = fma(p, r, 2.755731922398589e-07);
+    p = fma(p, r, 2.7557319223985893e-06);
+    p = fma(p, r, 2.48015873015873e-05);
+    p = fma(p, r, 1.984126984126984e-04);
+    p = fma(p, r, 1.388888888888889e-03);
+    p = fma(p, r, 8.333333333333333e-03);
+    p = fma(p, r, 4.1666666666666664e-02);
+    p = fma(p, r, 1.6666666666666666e-01);
+    p = fma(p, r, 0.5);
+    p = fma(p, r, 1.0);
+    p = fma(p, r, 1.0);
+    return p * __hiloint2double((n + 1023) << 20, 0);
+}
+
+__device__ __forceinline__ void fsincos(double x, double* sp, double* cp) {
+    double kd = fma(x, kTwoOverPi, kRoundShift);
+    const int n = __double2loint(kd);
+    if (n > (1 << 19) || n < -(1 << 19)) {
+        sincos(x, sp, cp);
+        return;
+    }
+    kd -= kRoundShift;
+    double r = fma(-kd, kPio2A, x);
+    r = fma(-kd, kPio2B, r);
+    r = fma(-kd, kPio2C, r);
+    const double r2 = r * r;
+    double ps = -7.647163731819816e-13;   // -1/15!
+    ps = fma(ps, r2, 1.6059043836821613e-10);
+    ps = fma(ps, r2, -2.505210838544172e-08);
+    ps = fma(ps, r2, 2.755731922398589e-06);
+    ps = fma(ps, r2, -1.984126984126984e-04);
+    ps = fma(ps, r2, 8.333333333333333e-03);
+    ps = fma(ps, r2, -1.6666666666666666e-01);
+    const double s = fma(ps * r2, r, r);
+    double pc = 4.779477332387385e-14;    // 1/16!
+    pc = fma(pc, r2, -1.1470745597729725e-11);
+    pc = fma(pc, r2, 2.08767569878681e-09);
+    pc = fma(pc, r2, -2.755731922398589e-07);
+    pc = fma(pc, r2, 2.48015873015873e-05);
+    pc = fma(pc, r2, -1.388888888888889e-03);
+    pc = fma(pc, r2, 4.1666666666666664e-02);
+    pc = fma(pc, r2, -0.5);
+    const double c = fma(pc, r2, 1.0);
+    // quadrant n mod 4: (s, c), (c, -s), (-s, -c), (-c, s)
+    const bool odd = (n & 1) != 0;
+    unsigned long long sv = (unsigned long long)__double_as_longlong(odd ? c : s);
+    unsigned long long cv = (unsigned long long)__double_as_longlong(odd ? s : c);
+    sv ^= (unsigned long long)((n >> 1) & 1) << 63;
+    cv ^= (unsigned long long)(((n + 1) >> 1) & 1) << 63;
+    *sp = __longlong_as_double((long long)sv);
+    *cp = __longlong_as_double((long long)cv);
+}
+
+__device__ __forceinline__ double frsqrt(double x) {
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double hx = 0.5 * x;
+#pragma unroll
+    for (int it = 0; it < 3; ++it) y = fma(y, fma(-hx * y, y, 0.5), y);
+    return y;
+}
+
+// e^{i q} with the functions above
+__device__ __forceinline__ double2 fcexpi(double2 q) {
+    double s, c;
+    fsincos(q.x, &s, &c);
+    const double m = fexp(-q.y);
+    return c2(m * c, m * s);
+}
+
+// Principal square root R of z (z not 0) and 1/R = conj(R)/|z|, from two
+// reciprocal square roots.  Cancellation-free on both half planes.
+__device__ __forceinline__ void fcsqrt_rcp(double2 z, double2& R, double2& iR) {
+    const double m2 = fma(z.x, z.x, z.y * z.y);
+    const double ir = frsqrt(m2);                  // 1/|z|
+    const double r = m2 * ir;                      // |z|
+    const double u = 0.5 * (r + fabs(z.x));
+    const double it = frsqrt(u);
+    const double t = u * it;                       // sqrt((|z| + |Re z|)/2)
+    const double s = 0.5 * z.y * it;               // Im z / (2 t)
+    R = z.x >= 0.0 ? c2(t, s) : c2(fabs(s), copysign(t, z.y));
+    iR = c2(R.x * ir, -R.y * ir);
+}
+
+// ---------------------------------------------------------------------------
 // Warp-cooperative Stockham FFT (forward, e^{-2 pi i k n / M}) in shared
 // memory, radices 4, 2, 3 (M = 2^a 3^b).  x, y: two buffers of M elements;
 // returns the buffer holding the result.  tw[e] = e^{-2 pi i e / M}.
@@ -74,7 +193,8 @@ __device__ double2* warp_fft(double2* x, double2* y, int M, const double2* tw, i
             int k = j % Ns;
             double2 v[4];
             for (int r = 0; r < R; ++r) v[r] = x[j + r * MR];
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[((r * k * step) % M) * tws]);
+            if (Ns > 1)   // the first stage's twiddles are all 1
+                for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[((r * k * step) % M) * tws]);
             if (R == 2) {
                 double2 a = v[0], b = v[1];
                 v[0] = cadd(a, b);
@@ -121,41 +241,42 @@ __device__ void warp_fft_inplace(double2* buf, double2* scratch, int M, const do
 // DFT of an even sequence x_0..x_{L-1} (x_k = x_{L-k}, L = 2K, K even) from
 // its K+1 distinct values, in place: xh[0..K] -> X_0..X_K.  Real and imaginary
 // parts are two real-even (DCT-I) transforms; each is reduced to a K-point
-// transform of y_j = (x_j + x_{K-j})/2 - sin(pi j/K)(x_j - x_{K-j}) -- the two
-// are packed into one complex K-point FFT -- after which the even outputs are
-// the real parts and the odd outputs follow from the imaginary parts by a
-// running sum started at F_1 = (x_0 - x_K)/2 + sum_j x_j cos(pi j/K).
-// y, scr: warp scratch of K elements; twL[e * tws] = e^{-2 pi i e / L}.
-__device__ void warp_even_dft(double2* xh, double2* y, double2* scr, int K, const double2* twL, int tws,
-                              int lane) {
+// transform of y_j = x_j (1/2 - sin(pi j/K)) + x_{K-j} (1/2 + sin(pi j/K)) --
+// the two are packed into one complex K-point FFT -- after which the even
+// outputs are the real parts and the odd outputs follow from the imaginary
+// parts by a running sum started at X_1 = 2 sum_{j<K} x_j cos(pi j/K) - x_0 - x_K.
+// y, scr: warp scratch of K elements; twL[e * tws] = e^{-2 pi i e / L};
+// hs[e * tws] = (1/2 + Im twL[e * tws], 1/2 - Im twL[e * tws]) (NULL: computed).
+__device__ void warp_even_dft(double2* xh, double2* y, double2* scr, int K, const double2* twL,
+                              const double2* hs, int tws, int lane) {
     double2 part = c2(0.0, 0.0);
     for (int j = lane; j < K; j += 32) {
-        double2 a = xh[j], b = xh[K - j];
-        double2 t = twL[j * tws];            // (cos(pi j/K), -sin(pi j/K))
-        double s = -t.y;
-        y[j] = c2(0.5 * (a.x + b.x) - s * (a.x - b.x), 0.5 * (a.y + b.y) - s * (a.y - b.y));
-        if (j > 0) part = cadd(part, cscale(a, t.x));
+        const double2 a = xh[j], b = xh[K - j];
+        const double2 t = twL[j * tws];     // (cos(pi j/K), -sin(pi j/K))
+        const double2 h = hs ? hs[j * tws] : c2(0.5 + t.y, 0.5 - t.y);
+        y[j] = c2(fma(a.x, h.x, b.x * h.y), fma(a.y, h.x, b.y * h.y));
+        const double ct = t.x;
+        part = c2(fma(a.x, ct, part.x), fma(a.y, ct, part.y));
     }
     for (int o = 16; o > 0; o >>= 1) {
         part.x += __shfl_xor_sync(0xffffffff, part.x, o);
         part.y += __shfl_xor_sync(0xffffffff, part.y, o);
     }
-    const double2 F1 = c2(part.x + 0.5 * (xh[0].x - xh[K].x), part.y + 0.5 * (xh[0].y - xh[K].y));
+    const double2 x0 = xh[0], xK = xh[K];
+    const double2 X1 = c2(2.0 * part.x - (x0.x + xK.x), 2.0 * part.y - (x0.y + xK.y));
     __syncwarp();
     double2* Z = warp_fft(y, scr, K, twL, lane, 2 * tws);
     double2* I = (Z == y) ? scr : y;         // imaginary parts for the running sum
     const int H = K / 2;
     for (int kk = lane; kk <= H; kk += 32) {
-        double2 zk = Z[kk], zc = Z[(K - kk) % K];
-        // Ya = (z_k + conj(z_{K-k}))/2, Yb = (z_k - conj(z_{K-k}))/(2i)
-        double yax = 0.5 * (zk.x + zc.x), yay = 0.5 * (zk.y - zc.y);
-        double pbx = zk.x - zc.x, pby = zk.y + zc.y;
-        double ybx = 0.5 * pby, yby = -0.5 * pbx;
-        xh[2 * kk] = c2(2.0 * yax, 2.0 * ybx);
-        I[kk] = c2(yay, yby);
+        const double2 zk = Z[kk], zc = Z[(K - kk) % K];
+        // with Ya = (z_k + conj z_{K-k})/2, Yb = (z_k - conj z_{K-k})/(2i):
+        // X_{2k} = 2 (Re Ya + i Re Yb); I_k = 2 (Im Ya + i Im Yb)
+        xh[2 * kk] = c2(zk.x + zc.x, zk.y + zc.y);
+        I[kk] = c2(zk.y - zc.y, zc.x - zk.x);
     }
     __syncwarp();
-    // odd outputs: F_{2k+1} = F_1 - sum_{m=1}^{k} Im Y_m, k = 0..H-1 (a warp scan)
+    // odd outputs: X_{2k+1} = X_1 - sum_{m=1}^{k} I_m, k = 0..H-1 (a warp scan)
     const int per = (H + 31) / 32;
     const int b0 = lane * per;
     double2 run = c2(0.0, 0.0);
@@ -168,12 +289,12 @@ __device__ void warp_even_dft(double2* xh, double2* y, double2* scr, int K, cons
         double2 v = c2(__shfl_up_sync(0xffffffff, incl.x, o), __shfl_up_sync(0xffffffff, incl.y, o));
         if (lane >= o) incl = cadd(incl, v);
     }
-    double2 acc = csub(incl, run);           // exclusive prefix of this lane's chunk
+    double2 acc = csub(X1, csub(incl, run));   // X_1 minus the exclusive prefix of this lane's chunk
     for (int q = 0; q < per; ++q) {
         int kk = b0 + q;
         if (kk >= H) break;
-        if (kk >= 1) acc = cadd(acc, I[kk]);
-        xh[2 * kk + 1] = c2(2.0 * (F1.x - acc.x), 2.0 * (F1.y - acc.y));
+        if (kk >= 1) acc = csub(acc, I[kk]);
+        xh[2 * kk + 1] = acc;
     }
     __syncwarp();
 }
@@ -225,38 +346,54 @@ __global__ void far_kernel(FarArgs a) {
     const int M = a.M, N = a.N, K = M / 2, S1 = K + 1;
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double2* tw = smem;                         // M: e^{-2 pi i e / M}
-    double2* cs = tw + M;                       // K + 1: (sin^2(psi/2), cos psi)
-    double2* buf = cs + S1 + warp * (4 * S1 + 2 * K);   // 4 sequences of K+1, then 2 x K scratch
-    for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = a.T.twid[i];
+    double2* hs = tw + M;                       // K: even-DFT weights
+    double2* cs = hs + K;                       // K + 1: (sin^2(psi/2), cos psi)
+    PairGeom* geo = reinterpret_cast<PairGeom*>(cs + S1);                  // nw pairs
+    double2* bufs = cs + S1 + 4 * nw;           // per warp: 4 sequences of K+1, then 2 x K scratch
+    int* act = reinterpret_cast<int*>(bufs + nw * (4 * S1 + 2 * K));     // nw flags
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const double2 t = a.T.twid[i];
+        tw[i] = t;
+        if (i < K) hs[i] = c2(0.5 + t.y, 0.5 - t.y);
+    }
     for (int i = threadIdx.x; i <= K; i += blockDim.x) cs[i] = a.T.cos_tab[i];
+    const int m = blockIdx.y;
+    if (lane == 0) {
+        const int l = blockIdx.x * nw + warp;
+        const bool on = l < N && a.T.cls[(size_t)l * N + m] == kFar;
+        act[warp] = on;
+        if (on) geo[warp] = grid_pair(a.T, l, m);
+    }
     __syncthreads();
 
-    const int m = blockIdx.y;
-    const int l = blockIdx.x * nw + warp;
-    bool active = l < N && a.T.cls[(size_t)l * N + m] == kFar;
-    if (active) {
-        PairGeom g = grid_pair(a.T, l, m);
-        for (int j = lane; j <= K; j += 32) {
-            double2 sc = cs[j];
-            double2 D2 = cadd(g.d2, cscale(g.rr, 4.0 * sc.x));
-            double2 R = csqrt(D2);
-            double2 iR = crcp(R);
-            double2 iR3 = cmul(iR, cmul(iR, iR));
-            double2 ND = cadd(g.nd0, cscale(g.nds, sc.x));
-            double2 Dk = cscale(cmul(ND, iR3), -kInv4Pi);   // region a
+    // samples j = 0..K of the CTA's nw pairs, spread over all its threads
+    for (int idx = threadIdx.x; idx < nw * S1; idx += blockDim.x) {
+        const int w = idx / S1, j = idx - w * S1;
+        if (!act[w]) continue;
+        const PairGeom g = geo[w];
+        double2* buf = bufs + w * (4 * S1 + 2 * K);
+        const double2 sc = cs[j];
+        const double2 D2 = cadd(g.d2, cscale(g.rr, 4.0 * sc.x));
+        double2 R, iR;
+        fcsqrt_rcp(D2, R, iR);
+        const double2 iR3 = cmul(iR, cmul(iR, iR));
+        const double2 ND = cadd(g.nd0, cscale(g.nds, sc.x));
+        const double2 Dk = cscale(cmul(ND, iR3), -kInv4Pi);   // region a
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                double w = r == 0 ? a.w1 : a.w2;
-                double2 q = cscale(R, w);
-                double2 e = cexpi(q);
-                buf[(2 * r) * S1 + j] = cscale(cmul(e, iR), kInv4Pi);
-                double2 Kv = cmul(cmul(Dk, e), c2(1.0 + q.y, -q.x));   // (1 - i q)
-                buf[(2 * r + 1) * S1 + j] = r == 0 ? Kv : cscale(Kv, -1.0);   // region b: normal -nu
-            }
+        for (int r = 0; r < 2; ++r) {
+            const double w = r == 0 ? a.w1 : a.w2;
+            const double2 Dr = r == 0 ? Dk : c2(-Dk.x, -Dk.y);      // region b: normal -nu
+            const double2 q = cscale(R, w);
+            const double2 e = fcexpi(q);
+            buf[(2 * r) * S1 + j] = cscale(cmul(e, iR), kInv4Pi);
+            buf[(2 * r + 1) * S1 + j] = cmul(cmul(Dr, e), c2(1.0 + q.y, -q.x));   // (1 - i q)
         }
-        __syncwarp();
+    }
+    __syncthreads();
+    if (act[warp]) {
+        double2* buf = bufs + warp * (4 * S1 + 2 * K);
         double2* y = buf + 4 * S1;
-        for (int s = 0; s < 4; ++s) warp_even_dft(buf + s * S1, y, y + K, K, tw, 1, lane);
+        for (int s = 0; s < 4; ++s) warp_even_dft(buf + s * S1, y, y + K, K, tw, hs, 1, lane);
     }
     __syncthreads();
 
@@ -269,23 +406,23 @@ __global__ void far_kernel(FarArgs a) {
             int w = idx % nw, blk = (idx / nw) % 4, n = idx / (4 * nw);
             int ll = blockIdx.x * nw + w;
             if (ll >= N) continue;
-            bool act = a.T.cls[(size_t)ll * N + m] == kFar;
-            const double2* b = smem + M + S1 + w * (4 * S1 + 2 * K);
+            const bool on = act[w] != 0;
+            const double2* b = bufs + w * (4 * S1 + 2 * K);
             double2 val = c2(0.0, 0.0);
             int row = ll, col = m;
             // blocks: 0 K^a -> (l, m); 1 -S^a -> (l, N+m); 2 K^b -> (N+l, m); 3 S^b -> (N+l, N+m)
             if (blk == 0) {
-                if (act) val = cscale(b[1 * S1 + a.mode_lo + n], scale * a.h * a.T.Wu[m]);
+                if (on) val = cscale(b[1 * S1 + a.mode_lo + n], scale * a.h * a.T.Wu[m]);
             } else if (blk == 1) {
                 col = N + m;
-                if (act) val = cscale(b[0 * S1 + a.mode_lo + n], -scale * a.h * a.T.Wphi[m]);
+                if (on) val = cscale(b[0 * S1 + a.mode_lo + n], -scale * a.h * a.T.Wphi[m]);
             } else if (blk == 2) {
                 row = N + ll;
-                if (act) val = cscale(b[3 * S1 + a.mode_lo + n], scale * a.h * a.T.Wu[m]);
+                if (on) val = cscale(b[3 * S1 + a.mode_lo + n], scale * a.h * a.T.Wu[m]);
             } else {
                 row = N + ll;
                 col = N + m;
-                if (act) val = cscale(b[2 * S1 + a.mode_lo + n], scale * a.h * a.T.Wphi[m]);
+                if (on) val = cscale(b[2 * S1 + a.mode_lo + n], scale * a.h * a.T.Wphi[m]);
             }
             a.A[(size_t)n * msz + (size_t)col * ld + row] = val;
         }
@@ -297,9 +434,8 @@ __global__ void far_kernel(FarArgs a) {
             int w = idx % nw, kern = (idx / nw) % 4, n = idx / (4 * nw);
             int ll = blockIdx.x * nw + w;
             if (ll >= N) continue;
-            bool act = a.T.cls[(size_t)ll * N + m] == kFar;
-            const double2* b = smem + M + S1 + w * (4 * S1 + 2 * K);
-            double2 val = act ? cscale(b[kern * S1 + a.mode_lo + n], scale) : c2(0.0, 0.0);
+            const double2* b = bufs + w * (4 * S1 + 2 * K);
+            double2 val = act[w] ? cscale(b[kern * S1 + a.mode_lo + n], scale) : c2(0.0, 0.0);
             a.raw[((size_t)n * 4 + kern) * NN + (size_t)ll * N + m] = val;
         }
     }
@@ -327,7 +463,7 @@ struct NearArgs {
     double2* zd;     // [p][2][M]
     double2* out;    // [p][4][nmodes]
     double2 pa[8], pb[8];   // Taylor coefficients of cH1 (pa) and cH3 (pb)
-    int conv_fft;           // convolution by length-2M FFTs (M <= 512) or directly
+    int hs_tab;             // keep the even-DFT weight table in shared memory
 };
 
 __device__ void complex_agm_KE(double2 k2, double2 kp, double2& K, double2& E) {
@@ -417,9 +553,12 @@ __global__ void near_laplace_kernel(NearArgs a) {
     }
 }
 
-__device__ __forceinline__ double2 cpoly(const double2* c, int deg, double2 q) {
-    double2 r = c[deg];
-    for (int k = deg - 1; k >= 0; --k) r = cadd(cmul(r, q), c[k]);
+// sum_{k = k0}^{L} c_k q^{k - k0} by Horner, L <= 7 (unrolled: static indices)
+__device__ __forceinline__ double2 cpoly_from(const double2 (&c)[8], int k0, int L, double2 q) {
+    double2 r = c2(0.0, 0.0);
+#pragma unroll
+    for (int k = 7; k >= 0; --k)
+        if (k >= k0 && k <= L) r = cadd(cmul(r, q), c[k]);
     return r;
 }
 
@@ -434,82 +573,86 @@ __global__ void near_modes_kernel(NearArgs a) {
     const int M = a.M, K = M / 2, S1 = K + 1, L2 = 2 * M, S2 = M + 1, p = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double2* tw2 = smem;                // 2M: e^{-2 pi i e / (2M)}
-    double2* seq = tw2 + L2;            // 8 sequences of K+1 (even samples, then their spectra)
+    double2* hs = a.hs_tab ? tw2 + L2 : nullptr;   // M even-DFT weights (if they fit)
+    double2* seq = tw2 + L2 + (a.hs_tab ? M : 0);  // 8 sequences of K+1 (samples, then spectra)
     double2* cv = seq + 8 * S1;         // 4 sequences of M+1 (convolution)
     double2* scr = cv + 4 * S2;         // per warp: 2 x M scratch
     double2* wy = scr + warp * 2 * M;
-    for (int i = threadIdx.x; i < L2; i += blockDim.x) tw2[i] = a.T.twid2[i];
+    for (int i = threadIdx.x; i < L2; i += blockDim.x) {
+        const double2 t = a.T.twid2[i];
+        tw2[i] = t;
+        if (hs && i < M) hs[i] = c2(0.5 + t.y, 0.5 - t.y);
+    }
     NearPair q = a.np[p];
     const bool plain = (q.flags & kFlagFar) != 0;
     const bool subst = (q.flags & kFlagSubst) != 0;
     // sampling; N_D(psi) = [nu'_r (rho~' - rho~) - nu'_z dz] + 2 nu'_r rho~ sin^2(psi/2)
-    double2 nd0 = cadd(cmul(q.nuc_r, q.drt), cscale(q.nuc_z, -q.dz));
-    double2 nds = cscale(cmul(q.nuc_r, q.rho_t), 2.0);
-    // polynomials: U1 = (1 - P1)/q = -sum_{k>=1} a_k q^{k-1}; V3 = ((1-iq) - P3)/q^3
-    double2 u1[8], v3[8];
-    for (int k = 0; k < 8; ++k) {
-        u1[k] = c2(0.0, 0.0);
-        v3[k] = c2(0.0, 0.0);
-    }
-    for (int k = 1; k <= a.L; ++k) u1[k - 1] = cscale(a.pa[k], -1.0);
-    for (int k = 3; k <= a.L; ++k) v3[k - 3] = cscale(a.pb[k], -1.0);
+    const double2 nd0 = cadd(cmul(q.nuc_r, q.drt), cscale(q.nuc_z, -q.dz));
+    const double2 nds = cscale(cmul(q.nuc_r, q.rho_t), 2.0);
+    const int L = a.L;
     __syncthreads();
     for (int j = threadIdx.x; j <= K; j += blockDim.x) {
-        double2 sc = a.T.cos_tab[j];
-        double2 D2 = cadd(q.d2, cscale(q.rr, 4.0 * sc.x));
-        double2 R = csqrt(D2);
-        double2 ND = cadd(nd0, cscale(nds, sc.x));
-        double2 v[8];
+        const double2 sc = a.T.cos_tab[j];
+        const double2 D2 = cadd(q.d2, cscale(q.rr, 4.0 * sc.x));
+        double2 R, iR;
+        fcsqrt_rcp(D2, R, iR);
+        const double2 ND = cadd(nd0, cscale(nds, sc.x));
+#pragma unroll
         for (int r = 0; r < 2; ++r) {
-            double w = r == 0 ? a.w1 : a.w2;
-            double sg = r == 0 ? 1.0 : -1.0;     // region b normal -nu
-            double2 qq = cscale(R, w);
-            double2 e = cexpi(qq);
+            const double w = r == 0 ? a.w1 : a.w2;
+            const double sg = r == 0 ? 1.0 : -1.0;     // region b normal -nu
+            const double2 qq = cscale(R, w);
+            double2 v0, v1, v2, v3;
             if (plain) {
-                double2 iR = crcp(R);
-                double2 iR3 = cmul(iR, cmul(iR, iR));
-                double2 Dk = cscale(cmul(ND, iR3), -kInv4Pi * sg);
-                v[4 * r + 0] = cscale(cmul(e, iR), kInv4Pi);
-                v[4 * r + 1] = c2(0.0, 0.0);
-                v[4 * r + 2] = cmul(cmul(Dk, e), c2(1.0 + qq.y, -qq.x));
-                v[4 * r + 3] = c2(0.0, 0.0);
+                const double2 e = fcexpi(qq);
+                const double2 iR3 = cmul(iR, cmul(iR, iR));
+                const double2 Dk = cscale(cmul(ND, iR3), -kInv4Pi * sg);
+                v0 = cscale(cmul(e, iR), kInv4Pi);
+                v1 = c2(0.0, 0.0);
+                v2 = cmul(cmul(Dk, e), c2(1.0 + qq.y, -qq.x));
+                v3 = c2(0.0, 0.0);
             } else if (subst) {
-                v[4 * r + 0] = cmul(e, cpoly(a.pa, a.L, qq));                          // cH1
-                v[4 * r + 1] = cscale(cmul(e, cpoly(u1, a.L - 1, qq)), w * kInv4Pi);   // Z(e^{iq} - cH1)
-                v[4 * r + 2] = cmul(e, cpoly(a.pb, a.L, qq));                          // cH3
-                double2 t = cmul(cmul(ND, e), cpoly(v3, a.L - 3, qq));
-                v[4 * r + 3] = cscale(t, -w * w * w * kInv4Pi * sg);                   // D(e^{iq}(1-iq) - cH3)
+                // cH1 = e^{iq} sum a_k q^k, Z (e^{iq} - cH1) = -(w / 4 pi) e^{iq} sum_{k>=1} a_k q^{k-1};
+                // cH3 likewise; D (e^{iq}(1 - iq) - cH3) = (w^3 / 4 pi) N_D e^{iq} sum_{k>=3} b_k q^{k-3}
+                const double2 e = fcexpi(qq);
+                v0 = cmul(e, cpoly_from(a.pa, 0, L, qq));
+                v1 = cscale(cmul(e, cpoly_from(a.pa, 1, L, qq)), -w * kInv4Pi);
+                v2 = cmul(e, cpoly_from(a.pb, 0, L, qq));
+                v3 = cscale(cmul(cmul(ND, e), cpoly_from(a.pb, 3, L, qq)), w * w * w * kInv4Pi * sg);
             } else {
                 // H1 = cos q, i Z H2 = (i w / 4 pi) sin(q)/q, H3 = cos q + q sin q,
                 // i D H4 = -(i w^3 / 4 pi) N_D (sin q - q cos q)/q^3   (q real here)
-                double qr = qq.x, s, c;
-                sincos(qr, &s, &c);
+                const double qr = qq.x;
+                double sn, cs;
+                fsincos(qr, &sn, &cs);
+                const double q2 = qr * qr;
                 double sinc, h4;
                 if (fabs(qr) < 1e-3) {
-                    double q2 = qr * qr;
                     sinc = 1.0 - q2 / 6.0 + q2 * q2 / 120.0;
                 } else {
-                    sinc = s / qr;
+                    sinc = sn / qr;
                 }
                 if (fabs(qr) < 1e-2) {
-                    double q2 = qr * qr;
                     h4 = 1.0 / 3.0 - q2 / 30.0 + q2 * q2 / 840.0 - q2 * q2 * q2 / 45360.0;
                 } else {
-                    h4 = (s - qr * c) / (qr * qr * qr);
+                    h4 = (sn - qr * cs) / (q2 * qr);
                 }
-                v[4 * r + 0] = c2(c, 0.0);
-                v[4 * r + 1] = c2(0.0, w * kInv4Pi * sinc);
-                v[4 * r + 2] = c2(c + qr * s, 0.0);
-                v[4 * r + 3] = cmul(ND, c2(0.0, -w * w * w * kInv4Pi * h4 * sg));
+                v0 = c2(cs, 0.0);
+                v1 = c2(0.0, w * kInv4Pi * sinc);
+                v2 = c2(cs + qr * sn, 0.0);
+                v3 = cmul(ND, c2(0.0, -w * w * w * kInv4Pi * h4 * sg));
             }
+            seq[(4 * r + 0) * S1 + j] = v0;
+            seq[(4 * r + 1) * S1 + j] = v1;
+            seq[(4 * r + 2) * S1 + j] = v2;
+            seq[(4 * r + 3) * S1 + j] = v3;
         }
-        for (int s = 0; s < 8; ++s) seq[s * S1 + j] = v[s];
     }
     __syncthreads();
     // eight even-sequence DFTs of length M, two per warp (plain pairs need only 0, 2, 4, 6)
     for (int s = warp; s < 8; s += 4) {
         if (plain && (s & 1)) continue;
-        warp_even_dft(seq + s * S1, wy, wy + M, K, tw2, 2, lane);
+        warp_even_dft(seq + s * S1, wy, wy + M, K, tw2, hs, 2, lane);
     }
     __syncthreads();
     const double scale = 2.0 * kPi / M;
@@ -543,7 +686,7 @@ __global__ void near_modes_kernel(NearArgs a) {
         zD[i] = inz ? Dd[i] : c2(0.0, 0.0);
     }
     __syncthreads();
-    if (warp < 2) warp_even_dft(warp == 0 ? zZ : zD, wy, wy + M, M, tw2, 1, lane);
+    if (warp < 2) warp_even_dft(warp == 0 ? zZ : zD, wy, wy + M, M, tw2, hs, 1, lane);
     const double c = 1.0 / (2.0 * kPi * L2);
     for (int r = 0; r < 2; ++r) {
         const double sgn = r == 0 ? 1.0 : -1.0;      // region b: D^ -> -D^
@@ -553,14 +696,14 @@ __global__ void near_modes_kernel(NearArgs a) {
             cK[i] = in ? cscale(seq[(4 * r + 2) * S1 + i], scale) : c2(0.0, 0.0);
         }
         __syncthreads();
-        if (warp >= 2) warp_even_dft(warp == 2 ? cS : cK, wy, wy + M, M, tw2, 1, lane);
+        if (warp >= 2) warp_even_dft(warp == 2 ? cS : cK, wy, wy + M, M, tw2, hs, 1, lane);
         __syncthreads();
         for (int i = threadIdx.x; i <= M; i += blockDim.x) {
             cS[i] = cmul(zZ[i], cS[i]);
             cK[i] = cscale(cmul(zD[i], cK[i]), sgn);
         }
         __syncthreads();
-        if (warp >= 2) warp_even_dft(warp == 2 ? cS : cK, wy, wy + M, M, tw2, 1, lane);
+        if (warp >= 2) warp_even_dft(warp == 2 ? cS : cK, wy, wy + M, M, tw2, hs, 1, lane);
         __syncthreads();
         for (int t = threadIdx.x; t < nmodes; t += blockDim.x) {
             int n = a.mode_lo + t;
@@ -784,7 +927,9 @@ cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStre
     a.raw = fl.raw;
     int nw = far_warps(M);
     const size_t S1 = M / 2 + 1;
-    size_t smem = sizeof(double2) * ((size_t)M + S1 + (size_t)nw * (4 * S1 + M));
+    // twiddles M, DFT weights M/2, angle table S1, nw pair geometries, nw buffers, nw flags
+    size_t smem = sizeof(double2) * ((size_t)M + M / 2 + S1 + 4 * (size_t)nw + (size_t)nw * (4 * S1 + M)) +
+                  sizeof(double2) * (((size_t)nw + 3) / 4);
     cudaError_t e = cudaFuncSetAttribute(far_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((N + nw - 1) / nw, N);
@@ -836,9 +981,10 @@ cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, do
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // tw2 (2M) + 8 x (M/2+1) + 4 x (M+1) + 4 warps x 2M scratch
-    a.conv_fft = 1;
+    // tw2 (2M) + 8 x (M/2+1) + 4 x (M+1) + 4 warps x 2M scratch (+ M weights when they fit)
     size_t smem = sizeof(double2) * ((size_t)2 * M + 8 * (M / 2 + 1) + 4 * (M + 1) + 8 * (size_t)M);
+    a.hs_tab = smem + sizeof(double2) * M <= 227 * 1024 ? 1 : 0;
+    if (a.hs_tab) smem += sizeof(double2) * M;
     e = cudaFuncSetAttribute(near_modes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     near_modes_kernel<<<a.npairs, 128, smem, s>>>(a);

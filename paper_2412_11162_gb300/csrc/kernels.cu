@@ -565,9 +565,13 @@ __device__ __forceinline__ double2 cpoly_from(const double2 (&c)[8], int k0, int
 // Close pairs, stage 2 (one CTA of 4 warps per pair): samples of the smooth
 // factors f1, f3 and remainders r1, r3 (both regions; for PML pairs the
 // Taylor substitution of Sec. 4.3, otherwise H1 = cos q, H3 = cos q + q sin q),
-// eight FFTs, and the convolution
+// their FFTs, and the convolution
 //   S^_n = (1/2pi) sum_{|k| < M/2} Z^_{|n-k|} F1_k + R1_n   (K^_n with D^, F3, R3).
 // Correction pairs that are far by the criterion use the plain FFT.
+// Physical pairs (no point in the PML) have real Z^, D^, f1, f3 and purely
+// imaginary r1, r3, so the two regions are packed as real and imaginary parts
+// of one sequence: 4 sample transforms and 4 convolution transforms instead
+// of 8 and 8.
 __global__ void near_modes_kernel(NearArgs a) {
     extern __shared__ double2 smem[];
     const int M = a.M, K = M / 2, S1 = K + 1, L2 = 2 * M, S2 = M + 1, p = blockIdx.x;
@@ -576,8 +580,10 @@ __global__ void near_modes_kernel(NearArgs a) {
     double2* hs = a.hs_tab ? tw2 + L2 : nullptr;   // M even-DFT weights (if they fit)
     double2* seq = tw2 + L2 + (a.hs_tab ? M : 0);  // 8 sequences of K+1 (samples, then spectra)
     double2* cv = seq + 8 * S1;         // 4 sequences of M+1 (convolution)
-    double2* scr = cv + 4 * S2;         // per warp: 2 x M scratch
-    double2* wy = scr + warp * 2 * M;
+    // two scratch slots of 2M: warps w and w + 2 share slot w & 1 (length-2M
+    // transforms of warps 0-1 and 2-3 never overlap; length-M ones take half)
+    double2* slot = cv + 4 * S2 + (warp & 1) * 2 * M;
+    double2* wyK = slot + (warp >> 1) * M;         // y, scr of a length-M transform (K = M/2)
     for (int i = threadIdx.x; i < L2; i += blockDim.x) {
         const double2 t = a.T.twid2[i];
         tw2[i] = t;
@@ -586,6 +592,7 @@ __global__ void near_modes_kernel(NearArgs a) {
     NearPair q = a.np[p];
     const bool plain = (q.flags & kFlagFar) != 0;
     const bool subst = (q.flags & kFlagSubst) != 0;
+    const bool packed = !plain && !subst;
     // sampling; N_D(psi) = [nu'_r (rho~' - rho~) - nu'_z dz] + 2 nu'_r rho~ sin^2(psi/2)
     const double2 nd0 = cadd(cmul(q.nuc_r, q.drt), cscale(q.nuc_z, -q.dz));
     const double2 nds = cscale(cmul(q.nuc_r, q.rho_t), 2.0);
@@ -597,50 +604,53 @@ __global__ void near_modes_kernel(NearArgs a) {
         double2 R, iR;
         fcsqrt_rcp(D2, R, iR);
         const double2 ND = cadd(nd0, cscale(nds, sc.x));
+        if (packed) {
+            // real q = w R; H1 = cos q, i Z H2 = (i w / 4 pi) sin(q)/q, H3 = cos q + q sin q,
+            // i D H4 = -(i w^3 / 4 pi) N_D (sin q - q cos q)/q^3 (region b: -N_D)
+            double f1[2], r1[2], f3[2], r3[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const double w = r == 0 ? a.w1 : a.w2;
+                const double qr = w * R.x, iq = iR.x / w;
+                double sn, cs;
+                fsincos(qr, &sn, &cs);
+                const double q2 = qr * qr;
+                const double sinc = fabs(qr) < 1e-3 ? 1.0 - q2 / 6.0 + q2 * q2 / 120.0 : sn * iq;
+                const double h4 = fabs(qr) < 1e-2
+                                      ? 1.0 / 3.0 - q2 / 30.0 + q2 * q2 / 840.0 - q2 * q2 * q2 / 45360.0
+                                      : (sn - qr * cs) * (iq * iq * iq);
+                f1[r] = cs;
+                r1[r] = w * kInv4Pi * sinc;
+                f3[r] = fma(qr, sn, cs);
+                r3[r] = (r == 0 ? -1.0 : 1.0) * w * w * w * kInv4Pi * h4 * ND.x;
+            }
+            seq[0 * S1 + j] = c2(f1[0], f1[1]);
+            seq[1 * S1 + j] = c2(r1[0], r1[1]);
+            seq[2 * S1 + j] = c2(f3[0], f3[1]);
+            seq[3 * S1 + j] = c2(r3[0], r3[1]);
+            continue;
+        }
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const double w = r == 0 ? a.w1 : a.w2;
             const double sg = r == 0 ? 1.0 : -1.0;     // region b normal -nu
             const double2 qq = cscale(R, w);
+            const double2 e = fcexpi(qq);
             double2 v0, v1, v2, v3;
             if (plain) {
-                const double2 e = fcexpi(qq);
                 const double2 iR3 = cmul(iR, cmul(iR, iR));
                 const double2 Dk = cscale(cmul(ND, iR3), -kInv4Pi * sg);
                 v0 = cscale(cmul(e, iR), kInv4Pi);
                 v1 = c2(0.0, 0.0);
                 v2 = cmul(cmul(Dk, e), c2(1.0 + qq.y, -qq.x));
                 v3 = c2(0.0, 0.0);
-            } else if (subst) {
+            } else {
                 // cH1 = e^{iq} sum a_k q^k, Z (e^{iq} - cH1) = -(w / 4 pi) e^{iq} sum_{k>=1} a_k q^{k-1};
                 // cH3 likewise; D (e^{iq}(1 - iq) - cH3) = (w^3 / 4 pi) N_D e^{iq} sum_{k>=3} b_k q^{k-3}
-                const double2 e = fcexpi(qq);
                 v0 = cmul(e, cpoly_from(a.pa, 0, L, qq));
                 v1 = cscale(cmul(e, cpoly_from(a.pa, 1, L, qq)), -w * kInv4Pi);
                 v2 = cmul(e, cpoly_from(a.pb, 0, L, qq));
                 v3 = cscale(cmul(cmul(ND, e), cpoly_from(a.pb, 3, L, qq)), w * w * w * kInv4Pi * sg);
-            } else {
-                // H1 = cos q, i Z H2 = (i w / 4 pi) sin(q)/q, H3 = cos q + q sin q,
-                // i D H4 = -(i w^3 / 4 pi) N_D (sin q - q cos q)/q^3   (q real here)
-                const double qr = qq.x;
-                double sn, cs;
-                fsincos(qr, &sn, &cs);
-                const double q2 = qr * qr;
-                double sinc, h4;
-                if (fabs(qr) < 1e-3) {
-                    sinc = 1.0 - q2 / 6.0 + q2 * q2 / 120.0;
-                } else {
-                    sinc = sn / qr;
-                }
-                if (fabs(qr) < 1e-2) {
-                    h4 = 1.0 / 3.0 - q2 / 30.0 + q2 * q2 / 840.0 - q2 * q2 * q2 / 45360.0;
-                } else {
-                    h4 = (sn - qr * cs) / (q2 * qr);
-                }
-                v0 = c2(cs, 0.0);
-                v1 = c2(0.0, w * kInv4Pi * sinc);
-                v2 = c2(cs + qr * sn, 0.0);
-                v3 = cmul(ND, c2(0.0, -w * w * w * kInv4Pi * h4 * sg));
             }
             seq[(4 * r + 0) * S1 + j] = v0;
             seq[(4 * r + 1) * S1 + j] = v1;
@@ -649,10 +659,15 @@ __global__ void near_modes_kernel(NearArgs a) {
         }
     }
     __syncthreads();
-    // eight even-sequence DFTs of length M, two per warp (plain pairs need only 0, 2, 4, 6)
-    for (int s = warp; s < 8; s += 4) {
-        if (plain && (s & 1)) continue;
-        warp_even_dft(seq + s * S1, wy, wy + M, K, tw2, hs, 2, lane);
+    // even-sequence DFTs of length M: packed pairs 4 (one per warp), plain
+    // pairs 0, 2, 4, 6, the others all 8
+    if (packed) {
+        warp_even_dft(seq + warp * S1, wyK, wyK + K, K, tw2, hs, 2, lane);
+    } else {
+        for (int s = warp; s < 8; s += 4) {
+            if (plain && (s & 1)) continue;
+            warp_even_dft(seq + s * S1, wyK, wyK + K, K, tw2, hs, 2, lane);
+        }
     }
     __syncthreads();
     const double scale = 2.0 * kPi / M;
@@ -674,8 +689,7 @@ __global__ void near_modes_kernel(NearArgs a) {
     // of length 2M (exact for n < M/2) of the even sequences zZ[m] = Z^_{|m|}
     // (|m| <= M-2), zD[m] = D^_{|m|}, c[k] = C_{|k|} (|k| <= M/2-1); all are even,
     // so every transform is an even-sequence DFT of M+1 values, and the inverse
-    // of an even sequence is its forward transform divided by 2M.  The two
-    // media are done one after the other with the same Z, D spectra.
+    // of an even sequence is its forward transform divided by 2M.
     double2* zZ = cv;
     double2* zD = cv + S2;
     double2* cS = cv + 2 * S2;
@@ -686,29 +700,50 @@ __global__ void near_modes_kernel(NearArgs a) {
         zD[i] = inz ? Dd[i] : c2(0.0, 0.0);
     }
     __syncthreads();
-    if (warp < 2) warp_even_dft(warp == 0 ? zZ : zD, wy, wy + M, M, tw2, hs, 1, lane);
+    if (warp < 2) warp_even_dft(warp == 0 ? zZ : zD, slot, slot + M, M, tw2, hs, 1, lane);
     const double c = 1.0 / (2.0 * kPi * L2);
-    for (int r = 0; r < 2; ++r) {
-        const double sgn = r == 0 ? 1.0 : -1.0;      // region b: D^ -> -D^
+    // packed: one pass with cS = F1a + i F1b and cK = F3a - i F3b (region b's -D^
+    // as the conjugate); otherwise one pass per region
+    const int passes = packed ? 1 : 2;
+    for (int r = 0; r < passes; ++r) {
         for (int i = threadIdx.x; i <= M; i += blockDim.x) {
             bool in = i <= K - 1;
-            cS[i] = in ? cscale(seq[(4 * r + 0) * S1 + i], scale) : c2(0.0, 0.0);
-            cK[i] = in ? cscale(seq[(4 * r + 2) * S1 + i], scale) : c2(0.0, 0.0);
+            double2 vS = c2(0.0, 0.0), vK = c2(0.0, 0.0);
+            if (in) {
+                vS = cscale(seq[(packed ? 0 : 4 * r + 0) * S1 + i], scale);
+                vK = cscale(seq[(packed ? 2 : 4 * r + 2) * S1 + i], scale);
+                if (packed) vK.y = -vK.y;
+            }
+            cS[i] = vS;
+            cK[i] = vK;
         }
         __syncthreads();
-        if (warp >= 2) warp_even_dft(warp == 2 ? cS : cK, wy, wy + M, M, tw2, hs, 1, lane);
+        if (warp >= 2) warp_even_dft(warp == 2 ? cS : cK, slot, slot + M, M, tw2, hs, 1, lane);
         __syncthreads();
+        const double sgn = r == 0 ? 1.0 : -1.0;      // region b: D^ -> -D^ (unpacked)
         for (int i = threadIdx.x; i <= M; i += blockDim.x) {
             cS[i] = cmul(zZ[i], cS[i]);
             cK[i] = cscale(cmul(zD[i], cK[i]), sgn);
         }
         __syncthreads();
-        if (warp >= 2) warp_even_dft(warp == 2 ? cS : cK, wy, wy + M, M, tw2, hs, 1, lane);
+        if (warp >= 2) warp_even_dft(warp == 2 ? cS : cK, slot, slot + M, M, tw2, hs, 1, lane);
         __syncthreads();
         for (int t = threadIdx.x; t < nmodes; t += blockDim.x) {
             int n = a.mode_lo + t;
-            out[(2 * r + 0) * (size_t)nmodes + t] = cadd(cscale(cS[n], c), cscale(seq[(4 * r + 1) * S1 + n], scale));
-            out[(2 * r + 1) * (size_t)nmodes + t] = cadd(cscale(cK[n], c), cscale(seq[(4 * r + 3) * S1 + n], scale));
+            if (packed) {
+                // real parts from the convolutions, imaginary parts from the remainders
+                const double2 s0 = cscale(cS[n], c), k0 = cscale(cK[n], c);
+                const double2 rs = cscale(seq[1 * S1 + n], scale), rk = cscale(seq[3 * S1 + n], scale);
+                out[0 * (size_t)nmodes + t] = c2(s0.x, rs.x);
+                out[1 * (size_t)nmodes + t] = c2(k0.x, rk.x);
+                out[2 * (size_t)nmodes + t] = c2(s0.y, rs.y);
+                out[3 * (size_t)nmodes + t] = c2(k0.y, rk.y);
+            } else {
+                out[(2 * r + 0) * (size_t)nmodes + t] =
+                    cadd(cscale(cS[n], c), cscale(seq[(4 * r + 1) * S1 + n], scale));
+                out[(2 * r + 1) * (size_t)nmodes + t] =
+                    cadd(cscale(cK[n], c), cscale(seq[(4 * r + 3) * S1 + n], scale));
+            }
         }
         __syncthreads();
     }
@@ -981,8 +1016,8 @@ cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, do
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // tw2 (2M) + 8 x (M/2+1) + 4 x (M+1) + 4 warps x 2M scratch (+ M weights when they fit)
-    size_t smem = sizeof(double2) * ((size_t)2 * M + 8 * (M / 2 + 1) + 4 * (M + 1) + 8 * (size_t)M);
+    // tw2 (2M) + 8 x (M/2+1) + 4 x (M+1) + 2 scratch slots x 2M (+ M weights when they fit)
+    size_t smem = sizeof(double2) * ((size_t)2 * M + 8 * (M / 2 + 1) + 4 * (M + 1) + 4 * (size_t)M);
     a.hs_tab = smem + sizeof(double2) * M <= 227 * 1024 ? 1 : 0;
     if (a.hs_tab) smem += sizeof(double2) * M;
     e = cudaFuncSetAttribute(near_modes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

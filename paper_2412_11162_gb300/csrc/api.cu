@@ -440,8 +440,10 @@ int pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* p
         rep->ms_assemble = f23;
         rep->launches = (int)g_launches;
     }
-    for (int i = 0; i < nm; ++i)
+    for (int i = 0; i < nm; ++i) {
+        if (info[i] < 0) return fail(PMLBIE_ECUDA, "tensor-core LU update did not complete in mode " + std::to_string(i));
         if (info[i]) return fail(PMLBIE_ESINGULAR, "zero pivot in mode " + std::to_string(i));
+    }
     if (precision == PMLBIE_MIXED && resid > 1e-12)
         return fail(PMLBIE_ENOCONVERGE, "refinement residual " + std::to_string(resid));
     return PMLBIE_OK;

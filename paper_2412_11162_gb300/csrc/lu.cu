@@ -7,13 +7,16 @@
 // factorisation itself is textbook right-looking blocked LU: panel
 // factorisation (pivot search, row swap, scaling, rank-1 updates inside the
 // panel), row swaps + unit-lower triangular solve for the block row, and a
-// tiled GEMM update of the trailing matrix.  Matrices are column-major,
-// A[b][col][row], leading dimension n.
+// tiled GEMM update of the trailing matrix (complex128: FP64 CUDA cores;
+// complex64: tcgen05 tensor cores, tc_update.cuh).  Matrices are
+// column-major, A[b][col][row], leading dimension n.  info[b] > 0 marks the
+// first zero pivot, info[b] = -1 a tensor-core update that did not complete.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
 
 #include "internal.h"
+#include "tc_update.cuh"
 
 namespace pmlbie {
 
@@ -420,9 +423,22 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
         swap_trsm_kernel<T><<<g1, 256, sm1, s>>>(n, k0, kb, A, piv);
         int rem = n - k0 - kb;
         if (rem > 0) {
-            constexpr int TL = GemmTile<T>::v;
-            dim3 g2((rem + TL - 1) / TL, (rem + TL - 1) / TL, batch);
-            gemm_update_kernel<T><<<g2, 256, 0, s>>>(n, k0, kb, A);
+            if constexpr (sizeof(T) == 8) {
+                // complex64: tensor-core update (tcgen05, TF32 split to FP32 accuracy)
+                if (k0 == 0) {
+                    cudaError_t e = cudaFuncSetAttribute(tcu::update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)tcu::kSmemBytes);
+                    if (e != cudaSuccess) return e;
+                }
+                constexpr int TL = tcu::kTileC;
+                dim3 g2((rem + TL - 1) / TL, (rem + TL - 1) / TL, batch);
+                tcu::update_kernel<<<g2, tcu::kThreads, tcu::kSmemBytes, s>>>(n, k0, kb,
+                                                                              reinterpret_cast<float2*>(A), info);
+            } else {
+                constexpr int TL = GemmTile<T>::v;
+                dim3 g2((rem + TL - 1) / TL, (rem + TL - 1) / TL, batch);
+                gemm_update_kernel<T><<<g2, 256, 0, s>>>(n, k0, kb, A);
+            }
             count_launch();
         }
     }

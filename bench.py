@@ -53,39 +53,61 @@ def peaks():
 # clocks during the timed region
 # ----------------------------------------------------------------------------
 class ClockSampler:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi sampling every 50 ms in a child process; summary() keeps the
+    samples whose timestamps fall inside the marked window (mark_start /
+    mark_end around the timed region)."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index=0):
         self.index = index
+        self.proc = None
+        self.t0 = self.t1 = None
         self.rows = []
-        self.stop = threading.Event()
-
-    def _run(self):
-        while not self.stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout.strip()
-                if out:
-                    self.rows.append([x.strip() for x in out.split(",")])
-            except Exception:
-                pass
-            self.stop.wait(0.2)
 
     def __enter__(self):
-        self.t = threading.Thread(target=self._run, daemon=True)
-        self.t.start()
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.5)   # first samples arrive before the timed region starts
         return self
 
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
     def __exit__(self, *a):
-        self.stop.set()
-        self.t.join(timeout=10)
+        if self.proc is None:
+            return
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        import datetime
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) != 8:
+                continue
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            if self.t0 is not None and self.t1 is not None and not (self.t0 <= ts <= self.t1):
+                continue
+            self.rows.append(f[1:])
 
     def summary(self):
         if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
         mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -198,11 +220,13 @@ def run_ours(args, rank, world):
     with ClockSampler(dev) as clk:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        clk.mark_start()
         e0.record(stream)
         for _ in range(args.steps):
             reps.append(step(B.PMLBIE_MIXED))
         e1.record(stream)
         torch.cuda.synchronize()
+        clk.mark_end()
     if dist:
         dist.barrier()
     ms = e0.elapsed_time(e1) / args.steps
@@ -247,11 +271,11 @@ def run_ours(args, rank, world):
     epp = entries_per_problem(w)
     value = world * epp / (ms / 1e3)
     pk = peaks()
-    # dominant kernel: the largest stage of the mixed step by device time
-    stages = {"far_kernel": last.ms_far, "near_kernels": last.ms_near, "assemble": last.ms_assemble,
+    stages = {"far_kernel": last.ms_far, "near_laplace_kernel": last.ms_near_laplace,
+              "near_modes_kernel": last.ms_near - last.ms_near_laplace, "assemble": last.ms_assemble,
               "lu_fp32": last.ms_lu, "solve_refine": last.ms_solve}
-    dom = max(stages, key=stages.get)
-    roof = roofline(dom, stages[dom], w, last, pk)
+    clocks = clk.summary()
+    roof = roofline(w, last, pk, clocks)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -263,6 +287,7 @@ def run_ours(args, rank, world):
                          int(((w["M"] // 2) * (2 * w["N"]) ** 2 * 24) / 1e6)},
         "solve_s_per_problem": ms / 1e3,
         "kernel_entries_per_s": epp / ((last.ms_far + last.ms_near + last.ms_assemble) / 1e3),
+        "far_pairs": last.far_pairs,
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
         "refine_iters": last.refine_iters, "refine_residual": last.residual,
         "fp64_gpu": {"ms_per_step": ms64, "value": world * epp / (ms64 / 1e3), "stages_ms": {
@@ -274,7 +299,7 @@ def run_ours(args, rank, world):
         "near_pairs": {"grid": ng, "alpert": nc},
         "gpu_launches": int(sum(r.launches for r in reps)),
         "roofline": roof,
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "e2e": {"value": world * epp / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "note": "per step: create (host setup) + solve_host to pinned buffers + destroy"},
@@ -290,49 +315,66 @@ def run_ours(args, rank, world):
         dist.destroy_process_group()
 
 
-def roofline(name, ms, w, rep, pk):
-    """Roofline entry of the dominant stage; algorithmic work per launch as
-    stated in the design notes."""
-    N, M = w["N"], w["M"]
-    nm, n2 = M // 2, 2 * N
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    if name == "lu_fp32":
-        flops = nm * (8.0 / 3.0) * n2 ** 3          # complex LU: 8/3 n^3 real flops per mode
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA pipe, derived (TFLOP/s)
-        ach = flops / (ms / 1e3) / 1e12
-        return {"kernel": "batched LU (FP32, CUDA cores)", "bound": "alu", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived, not measured)"}
-    if name in ("far_kernel", "near_kernels", "assemble"):
-        # FP64 pipe: 152 SMs x 2 FP64 FMA/clk (GB300) x 2 flop x clock
-        peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
-        if name == "far_kernel":
-            samples = N * N * (M // 2 + 1)
-            flops = samples * FAR_FLOPS_PER_SAMPLE
-            ach = flops / (ms / 1e3) / 1e12
-            return {"kernel": "far_kernel (sample + FFT + scatter, FP64)", "bound": "alu", "achieved": ach,
-                    "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                    "peak_note": "FP64 pipe 2 FMA/clk/SM (1.25 TF/s nominal), derived"}
-        return {"kernel": name, "bound": "alu", "achieved": None, "peak": peak, "unit": "TFLOP/s",
-                "frac": None, "traffic": None}
-    byts = nm * n2 * n2 * 16.0
-    ach = byts / (ms / 1e3) / 1e9
-    peak = pk.get("hbm_gbs", 6800.0)
-    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": None}
+def far_flops_per_pair(M):
+    """Algorithmic FP64 flops of one far node pair in the far-pair kernel
+    (fused multiply-add = 2 flops): (M/2 + 1) angle samples of S~ and K~ of
+    both media at 276 flops each (complex distance, square root and
+    reciprocal by Newton-refined reciprocal square roots, two e^{iq} by
+    range reduction + series, kernel products), four even-sequence DFTs of
+    length M at 5 K log2 K + 15 K flops (K = M/2: a K-point complex FFT plus
+    pre- and post-processing), and 16 K flops to weight the 4 K outputs."""
+    K = M // 2
+    return (K + 1) * 276.0 + 4 * (5.0 * K * np.log2(K) + 15.0 * K) + 16.0 * K
 
 
-# FP64 flops the far kernel spends per (pair, angle) sample, counted from the
-# formula with transcendental functions at their operation counts (see the
-# design notes): distance and reciprocals ~40, two complex exponentials with
-# range reduction ~2 x 45, kernels ~30, FFT share 4 x 5 log2(M) ~ 160 at M=256.
-FAR_FLOPS_PER_SAMPLE = 320.0
+def far_traffic(w):
+    """DRAM bytes (read + write) of one far_kernel launch at this workload from
+    the committed ncu summary profiles/far_kernel_n<N>_m<M>.md, or None when
+    there is none or kernels.cu changed since it was taken (the summary
+    records the source's sha256)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "far_kernel_n%d_m%d.md" % (w["N"], w["M"]))
+    try:
+        text = open(path).read()
+        src = open(os.path.join(ROOT, "paper_2412_11162_gb300", "csrc", "kernels.cu"), "rb").read()
+    except OSError:
+        return None
+    sha = hashlib.sha256(src).hexdigest()
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.split(":")[0].strip() in ("kernels_cu_sha256", "dram_bytes_per_launch"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernels_cu_sha256") != sha or "dram_bytes_per_launch" not in vals:
+        return None
+    return float(vals["dram_bytes_per_launch"])
+
+
+def roofline(w, rep, pk, clk):
+    """Roofline entry of the far-pair kernel, the longest single kernel of
+    the step: FP64-ALU bound.  achieved = algorithmic flops of the launch /
+    its device time (CUDA events around the launch on the solve's stream);
+    peak = the FP64 pipe of the GB300: 152 SMs x 2 FMA/clk x 2 flops x clock
+    (derived from unit counts, not measured)."""
+    M = w["M"]
+    mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    peak = 152 * 2 * 2 * mhz * 1e6 / 1e12
+    flops = rep.far_pairs * far_flops_per_pair(M)
+    ach = flops / (rep.ms_far / 1e3) / 1e12
+    traffic = far_traffic(w)
+    return {"kernel": "far_kernel (S~, K~ sampling of both media + 4 even DFTs + block scatter, FP64)",
+            "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": traffic, "flops_per_launch": flops, "ms_per_launch": rep.ms_far,
+            "algorithmic_bytes": 4.0 * w["N"] ** 2 * (M // 2) * 16,
+            "peak_note": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz (median SM clock under load)" % mhz,
+            "traffic_note": ("ncu dram bytes read+write of one launch at this workload (profiles/)" if traffic
+                             else "null: no ncu capture of the current kernels.cu at this workload")}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -91,6 +91,9 @@ typedef struct {
     double   ms_near;             /* device time of the close-pair kernels (ms)        */
     double   ms_assemble;         /* device time of Alpert assembly + diagonal (ms)    */
     int      launches;            /* CUDA kernel launches issued by the call           */
+    int      far_pairs;           /* node pairs evaluated by the far-pair FFT kernel   */
+    double   ms_near_laplace;     /* device time of the close-pair Laplace-mode kernel
+                                     (part of ms_near) (ms)                            */
 } pmlbie_report;
 
 typedef struct pmlbie_problem pmlbie_problem;   /* opaque, owned by the library */

@@ -40,7 +40,7 @@ class pmlbie_report(ctypes.Structure):
                 ("refine_iters", ctypes.c_int), ("residual", ctypes.c_double),
                 ("ms_kernels", ctypes.c_double), ("ms_lu", ctypes.c_double), ("ms_solve", ctypes.c_double),
                 ("ms_far", ctypes.c_double), ("ms_near", ctypes.c_double), ("ms_assemble", ctypes.c_double),
-                ("launches", ctypes.c_int)]
+                ("launches", ctypes.c_int), ("far_pairs", ctypes.c_int), ("ms_near_laplace", ctypes.c_double)]
 
 
 EXPORTS = ["pmlbie_create", "pmlbie_destroy", "pmlbie_last_error", "pmlbie_nodes", "pmlbie_diagonal",

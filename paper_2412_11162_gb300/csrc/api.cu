@@ -187,14 +187,15 @@ void fresnel(double w1, double w2, double phi, double* out6) {
     out6[5] = ks.imag();
 }
 
-// modal kernels + assembly into w.A (all modes); ev[0..3] bracket the stages
+// modal kernels + assembly into w.A (all modes); ev[0..3] bracket the stages,
+// ev[4] splits the close-pair stage
 int build_system(pmlbie_problem* prob, Workspace& w, cudaStream_t s, cudaEvent_t* ev) {
     const int nm = prob->P.M / 2;
     FarLaunch fl{0, nm, w.A, nullptr};
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[0], s));
     PMLBIE_CUDA_TRY(launch_far(prob, fl, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[1], s));
-    PMLBIE_CUDA_TRY(launch_near(prob, 0, nm, w.zd, w.nout, s));
+    PMLBIE_CUDA_TRY(launch_near(prob, 0, nm, w.zd, w.nout, s, ev[4]));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
     PMLBIE_CUDA_TRY(launch_assemble(prob, 0, nm, w.nout, w.A, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[3], s));
@@ -342,14 +343,15 @@ int pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* p
     Workspace w;
     if ((rc = get_workspace(prob, precision, n_rhs, w))) return rc;
     const int N = prob->P.N, nm = prob->P.M / 2, n2 = 2 * N;
-    cudaEvent_t ev[4], sev[4];
+    cudaEvent_t ev[4], sev[5];
     for (auto& e : ev) PMLBIE_CUDA_TRY(cudaEventCreate(&e));
     for (auto& e : sev) PMLBIE_CUDA_TRY(cudaEventCreate(&e));
     struct EvGuard {
         cudaEvent_t* e;
         cudaEvent_t* f;
         ~EvGuard() {
-            for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]), cudaEventDestroy(f[i]);
+            for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+            for (int i = 0; i < 5; ++i) cudaEventDestroy(f[i]);
         }
     } guard{ev, sev};
     g_launches = 0;
@@ -439,6 +441,10 @@ int pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* p
         rep->ms_near = f12;
         rep->ms_assemble = f23;
         rep->launches = (int)g_launches;
+        float fl = 0.f;
+        cudaEventElapsedTime(&fl, sev[1], sev[4]);
+        rep->ms_near_laplace = fl;
+        rep->far_pairs = (int)std::count(prob->H.cls.begin(), prob->H.cls.end(), (uint8_t)kFar);
     }
     for (int i = 0; i < nm; ++i) {
         if (info[i] < 0) return fail(PMLBIE_ECUDA, "tensor-core LU update did not complete in mode " + std::to_string(i));

@@ -128,8 +128,9 @@ struct FarLaunch {
     double2* raw;          // [mode][kernel][l][m]; may be null
 };
 cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStream_t s);
+// mid (optional): event recorded between the Laplace-mode and the modes kernels
 cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, double2* zd_scratch,
-                        double2* out, cudaStream_t s);
+                        double2* out, cudaStream_t s, cudaEvent_t mid = nullptr);
 cudaError_t launch_near_to_raw(const pmlbie_problem* prob, int mode_lo, int mode_hi,
                                const double2* near_out, double2* raw, cudaStream_t s);
 cudaError_t launch_assemble(const pmlbie_problem* prob, int mode_lo, int mode_hi,

@@ -995,7 +995,7 @@ static void taylor_coeffs(int L, double2* pa, double2* pb) {
 }
 
 cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, double2* zd,
-                        double2* out, cudaStream_t s) {
+                        double2* out, cudaStream_t s, cudaEvent_t mid) {
     const int M = prob->P.M;
     NearArgs a;
     a.T = prob->D;
@@ -1016,6 +1016,7 @@ cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, do
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (mid && (e = cudaEventRecord(mid, s)) != cudaSuccess) return e;
     // tw2 (2M) + 8 x (M/2+1) + 4 x (M+1) + 2 scratch slots x 2M (+ M weights when they fit)
     size_t smem = sizeof(double2) * ((size_t)2 * M + 8 * (M / 2 + 1) + 4 * (M + 1) + 4 * (size_t)M);
     a.hs_tab = smem + sizeof(double2) * M <= 227 * 1024 ? 1 : 0;

@@ -290,6 +290,7 @@ def run_ours(args, rank, world):
         "far_pairs": last.far_pairs,
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
         "refine_iters": last.refine_iters, "refine_residual": last.residual,
+        "refine_backward_error": last.backward_error, "gmres_modes": last.gmres_modes,
         "fp64_gpu": {"ms_per_step": ms64, "value": world * epp / (ms64 / 1e3), "stages_ms": {
             "far_kernel": fp64_reps[-1].ms_far, "near_kernels": fp64_reps[-1].ms_near,
             "assemble": fp64_reps[-1].ms_assemble, "lu_fp64": fp64_reps[-1].ms_lu,
@@ -305,10 +306,12 @@ def run_ours(args, rank, world):
                 "note": "per step: create (host setup) + solve_host to pinned buffers + destroy"},
     }
     if rank == 0 and not args.no_cpu_baseline:
-        e, t = oracle_sample(w, rows=48)
+        rows = 160
+        e, t = oracle_sample(w, rows=rows)
         line["cpu_baseline"] = {"value": e / t, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                                "sample": "modal kernels of 48 target rows x all 512 sources + their Alpert "
-                                          "points, 128 modes, 4 kernels (FP64 numpy oracle), %.1f s" % t}
+                                "sample": "modal kernels of %d target rows x all %d sources + their Alpert "
+                                          "points, %d modes, 4 kernels (FP64 numpy oracle), %.1f s" %
+                                          (rows, w["N"], w["M"] // 2, t)}
     if rank == 0:
         print(json.dumps(line))
     if dist:

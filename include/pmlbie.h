@@ -94,7 +94,24 @@ typedef struct {
     int      far_pairs;           /* node pairs evaluated by the far-pair FFT kernel   */
     double   ms_near_laplace;     /* device time of the close-pair Laplace-mode kernel
                                      (part of ms_near) (ms)                            */
+    int      chunks;              /* mode chunks the solve was split into              */
+    int      chunk_modes;         /* modes per chunk                                   */
+    int      gmres_modes;         /* mixed: modes finished by FGMRES (refinement stalled) */
+    int      gmres_iters;         /* mixed: FGMRES iterations (max over chunks)        */
+    double   backward_error;      /* mixed: max over modes/RHS of |B - A x| / (|A|_F |x| + |B|) */
 } pmlbie_report;
+
+/* Options of pmlbie_solve_ex (zero-initialise, then set struct_size). */
+typedef struct {
+    uint32_t struct_size;         /* sizeof(pmlbie_solve_opts)                                  */
+    int      precision;           /* PMLBIE_FP64 or PMLBIE_MIXED                                */
+    int      n_rhs;               /* plane waves, 1..4096                                        */
+    const double* polar;          /* host, n_rhs polar angles in [0, pi/2) (from the z axis)    */
+    const double* azimuth;        /* host, n_rhs incidence azimuths (NULL: all 0)               */
+    int      mode_lo, mode_hi;    /* modes solved, [mode_lo, mode_hi) in [0, M/2); 0, 0 = all   */
+    int      max_chunk_modes;     /* modes per chunk at most (0: no cap)                        */
+    size_t   workspace_limit;     /* device workspace bytes at most (0: 90 % of free memory)    */
+} pmlbie_solve_opts;
 
 typedef struct pmlbie_problem pmlbie_problem;   /* opaque, owned by the library */
 
@@ -174,11 +191,33 @@ int  pmlbie_modal_kernels_noalloc(pmlbie_problem* prob, int mode_lo, int mode_hi
  * Outputs (caller-owned device buffers, complex128, [mode][node][rhs], M/2
  * modes): u1 = u^{s,1}_n, phi1 = |r'| d_nu_c u^{s,1}_n, u2, phi2 (the same for
  * the lower medium, d_nu with the same nu).  Any output may be NULL.
- * Errors: EINVAL, ENOMEM, ECUDA, ESINGULAR, ENOCONVERGE (mixed: refinement
- * residual above 1e-12 after the iteration cap; outputs still written). */
+ * Mixed precision: FP64 modal kernels and matrices, complex64 LU (tensor-core
+ * trailing updates), iterative refinement with FP64 residuals until, for
+ * every mode and right-hand side, the relative residual is <= 1e-13, or the
+ * normwise backward error |B - A x| / (|A|_F |x| + |B|) is <= 1e-16, or it is
+ * <= 1e-14 and no longer decreasing (the FP64 floor); modes
+ * whose refinement stalls (condition number x FP32 LU error near 1 or above)
+ * are restarted and solved by flexible GMRES in FP64 preconditioned by the
+ * same LU.  Errors: EINVAL, ENOMEM, ECUDA, ESINGULAR, ENOCONVERGE (mixed: a
+ * mode missed both tolerances after the iteration caps; outputs still
+ * written). */
 int  pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* polar,
                   void* dev_u1, void* dev_phi1, void* dev_u2, void* dev_phi2,
                   void* stream, pmlbie_report* rep);
+
+/* Solve with options (Sec. 4.1-4.2 as pmlbie_solve): incidence azimuths, a
+ * mode range, and mode chunking.  Modes are independent (Sec. 3.3), so the
+ * call processes [mode_lo, mode_hi) in chunks of at most max_chunk_modes modes
+ * whose workspace fits workspace_limit: each chunk samples the kernels, builds
+ * and factors its systems and solves them before the next starts (the kernel
+ * sampling is repeated per chunk).  Plane wave r has polar angle polar[r] and
+ * azimuth azimuth[r]; mode n of its data is e^{-i n azimuth} times that of the
+ * azimuth-0 wave (modes -n follow as e^{+i n azimuth} times the same).
+ * Outputs as pmlbie_solve with (mode_hi - mode_lo) modes:
+ * [mode - mode_lo][node][rhs].  Synchronises the stream at the end of every
+ * chunk.  Errors as pmlbie_solve; ENOMEM if one mode does not fit the limit. */
+int  pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* opts, void* dev_u1, void* dev_phi1,
+                     void* dev_u2, void* dev_phi2, void* stream, pmlbie_report* rep);
 
 /* The same solve with HOST output buffers: the call copies the results to the
  * host (synchronising the stream).  Host buffers have the layout above. */

@@ -40,13 +40,22 @@ class pmlbie_report(ctypes.Structure):
                 ("refine_iters", ctypes.c_int), ("residual", ctypes.c_double),
                 ("ms_kernels", ctypes.c_double), ("ms_lu", ctypes.c_double), ("ms_solve", ctypes.c_double),
                 ("ms_far", ctypes.c_double), ("ms_near", ctypes.c_double), ("ms_assemble", ctypes.c_double),
-                ("launches", ctypes.c_int), ("far_pairs", ctypes.c_int), ("ms_near_laplace", ctypes.c_double)]
+                ("launches", ctypes.c_int), ("far_pairs", ctypes.c_int), ("ms_near_laplace", ctypes.c_double),
+                ("chunks", ctypes.c_int), ("chunk_modes", ctypes.c_int), ("gmres_modes", ctypes.c_int),
+                ("gmres_iters", ctypes.c_int), ("backward_error", ctypes.c_double)]
+
+
+class pmlbie_solve_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("precision", ctypes.c_int), ("n_rhs", ctypes.c_int),
+                ("polar", ctypes.POINTER(ctypes.c_double)), ("azimuth", ctypes.POINTER(ctypes.c_double)),
+                ("mode_lo", ctypes.c_int), ("mode_hi", ctypes.c_int), ("max_chunk_modes", ctypes.c_int),
+                ("workspace_limit", ctypes.c_size_t)]
 
 
 EXPORTS = ["pmlbie_create", "pmlbie_destroy", "pmlbie_last_error", "pmlbie_nodes", "pmlbie_diagonal",
            "pmlbie_near_count", "pmlbie_alpert_rule", "pmlbie_workspace_bytes", "pmlbie_modal_kernels",
            "pmlbie_modal_kernels_noalloc",
-           "pmlbie_solve", "pmlbie_solve_host"]
+           "pmlbie_solve", "pmlbie_solve_ex", "pmlbie_solve_host"]
 
 
 def _load():
@@ -73,8 +82,11 @@ def _load():
                                  ctypes.POINTER(pmlbie_report)]
     lib.pmlbie_solve_host.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, vp,
                                       ctypes.POINTER(pmlbie_report)]
+    lib.pmlbie_solve_ex.argtypes = [vp, ctypes.POINTER(pmlbie_solve_opts), vp, vp, vp, vp, vp,
+                                    ctypes.POINTER(pmlbie_report)]
     for f in ("pmlbie_nodes", "pmlbie_diagonal", "pmlbie_near_count", "pmlbie_alpert_rule",
-              "pmlbie_modal_kernels", "pmlbie_modal_kernels_noalloc", "pmlbie_solve", "pmlbie_solve_host"):
+              "pmlbie_modal_kernels", "pmlbie_modal_kernels_noalloc", "pmlbie_solve", "pmlbie_solve_ex",
+              "pmlbie_solve_host"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -193,6 +205,28 @@ def pmlbie_solve(h, precision, polar, u1=None, phi1=None, u2=None, phi2=None, st
                           _stream(stream), ctypes.byref(rep))
     if not (allow_noconverge and rc == PMLBIE_ENOCONVERGE):
         check(rc, "pmlbie_solve")
+    return rep
+
+
+def pmlbie_solve_ex(h, precision, polar, azimuth=None, mode_lo=0, mode_hi=0, max_chunk_modes=0,
+                    workspace_limit=0, u1=None, phi1=None, u2=None, phi2=None, stream=None,
+                    allow_noconverge=False):
+    import numpy as np
+    pol = np.ascontiguousarray(np.asarray(polar, dtype=np.float64).reshape(-1))
+    az = None if azimuth is None else np.ascontiguousarray(np.asarray(azimuth, dtype=np.float64).reshape(-1))
+    if az is not None and len(az) != len(pol):
+        raise ValueError("azimuth and polar differ in length")
+    o = pmlbie_solve_opts()
+    o.struct_size = ctypes.sizeof(pmlbie_solve_opts)
+    o.precision, o.n_rhs, o.polar = precision, len(pol), _dptr(pol)
+    o.azimuth = _dptr(az) if az is not None else None
+    o.mode_lo, o.mode_hi, o.max_chunk_modes, o.workspace_limit = mode_lo, mode_hi, max_chunk_modes, workspace_limit
+    rep = pmlbie_report()
+    rep.struct_size = ctypes.sizeof(pmlbie_report)
+    rc = lib.pmlbie_solve_ex(h, ctypes.byref(o), _tptr(u1), _tptr(phi1), _tptr(u2), _tptr(phi2), _stream(stream),
+                             ctypes.byref(rep))
+    if not (allow_noconverge and rc == PMLBIE_ENOCONVERGE):
+        check(rc, "pmlbie_solve_ex")
     return rep
 
 

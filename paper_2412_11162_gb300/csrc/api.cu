@@ -121,14 +121,27 @@ struct Workspace {
             *X = nullptr, *R = nullptr;
     float2 *A32 = nullptr, *w32 = nullptr;
     int *piv = nullptr, *info = nullptr, *active = nullptr;
-    double *rn = nullptr, *bn = nullptr, *rpar = nullptr;
+    double *rn = nullptr, *bn = nullptr, *xn = nullptr, *an = nullptr, *rpar = nullptr;
+    void* gm = nullptr;     // FGMRES scratch (mixed)
     size_t bytes = 0;
 };
 
+constexpr int kGmresM = 20;          // FGMRES restart length
+constexpr int kGmresCycles = 10;     // FGMRES restarts at most
+// a mode's refinement is done when, for every rhs, the relative residual
+// |B - A x| / |B| <= kTolRel or the normwise backward error
+// |B - A x| / (|A|_F |x| + |B|) <= kTolBwd, or when the backward error is
+// below kTolFloor and stopped decreasing (the FP64 floor of ill-conditioned
+// modes, whose |A| |x| >> |B|)
+constexpr double kTolRel = 1e-13;
+constexpr double kTolBwd = 1e-16;
+constexpr double kTolFloor = 1e-14;
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-Workspace plan(const pmlbie_problem* prob, int precision, int nrhs, char* base) {
-    const size_t N = prob->P.N, M = prob->P.M, nm = M / 2, n2 = 2 * N;
+// nmodes: modes per chunk (every per-mode buffer holds one chunk)
+Workspace plan(const pmlbie_problem* prob, int precision, int nrhs, int nmodes, char* base) {
+    const size_t N = prob->P.N, M = prob->P.M, nm = nmodes, n2 = 2 * N;
     const size_t np = prob->H.near.size();
     Workspace w;
     size_t off = 0;
@@ -154,13 +167,16 @@ Workspace plan(const pmlbie_problem* prob, int precision, int nrhs, char* base) 
     w.active = (int*)take(sizeof(int) * nm);
     w.rn = (double*)take(sizeof(double) * nm * nrhs);
     w.bn = (double*)take(sizeof(double) * nm * nrhs);
-    w.rpar = (double*)take(sizeof(double) * 6 * nrhs);
+    w.xn = (double*)take(sizeof(double) * nm * nrhs);
+    w.an = (double*)take(sizeof(double) * nm);
+    w.rpar = (double*)take(sizeof(double) * kRhsPar * nrhs);
+    if (precision == PMLBIE_MIXED) w.gm = take(gmres_scratch_bytes((int)n2, (int)nm, nrhs, kGmresM));
     w.bytes = off;
     return w;
 }
 
-int get_workspace(pmlbie_problem* prob, int precision, int nrhs, Workspace& w) {
-    Workspace sz = plan(prob, precision, nrhs, nullptr);
+int get_workspace(pmlbie_problem* prob, int precision, int nrhs, int nmodes, Workspace& w) {
+    Workspace sz = plan(prob, precision, nrhs, nmodes, nullptr);
     if (prob->ws_bytes < sz.bytes) {
         if (prob->ws) cudaFree(prob->ws);
         prob->ws = nullptr;
@@ -171,7 +187,7 @@ int get_workspace(pmlbie_problem* prob, int precision, int nrhs, Workspace& w) {
         }
         prob->ws_bytes = sz.bytes;
     }
-    w = plan(prob, precision, nrhs, (char*)prob->ws);
+    w = plan(prob, precision, nrhs, nmodes, (char*)prob->ws);
     return PMLBIE_OK;
 }
 
@@ -187,17 +203,16 @@ void fresnel(double w1, double w2, double phi, double* out6) {
     out6[5] = ks.imag();
 }
 
-// modal kernels + assembly into w.A (all modes); ev[0..3] bracket the stages,
-// ev[4] splits the close-pair stage
-int build_system(pmlbie_problem* prob, Workspace& w, cudaStream_t s, cudaEvent_t* ev) {
-    const int nm = prob->P.M / 2;
-    FarLaunch fl{0, nm, w.A, nullptr};
+// modal kernels + assembly into w.A for modes [lo, hi); ev[0..3] bracket the
+// stages, ev[4] splits the close-pair stage
+int build_system(pmlbie_problem* prob, Workspace& w, int lo, int hi, cudaStream_t s, cudaEvent_t* ev) {
+    FarLaunch fl{lo, hi, w.A, nullptr};
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[0], s));
     PMLBIE_CUDA_TRY(launch_far(prob, fl, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[1], s));
-    PMLBIE_CUDA_TRY(launch_near(prob, 0, nm, w.zd, w.nout, s, ev[4]));
+    PMLBIE_CUDA_TRY(launch_near(prob, lo, hi, w.zd, w.nout, s, ev[4]));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
-    PMLBIE_CUDA_TRY(launch_assemble(prob, 0, nm, w.nout, w.A, s));
+    PMLBIE_CUDA_TRY(launch_assemble(prob, lo, hi, w.nout, w.A, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[3], s));
     return PMLBIE_OK;
 }
@@ -302,7 +317,7 @@ int pmlbie_alpert_rule(int j, int a, double* x, double* w) {
 
 size_t pmlbie_workspace_bytes(const pmlbie_problem* prob, int precision, int n_rhs) {
     if (!prob || n_rhs < 1) return 0;
-    return plan(prob, precision, n_rhs, nullptr).bytes;
+    return plan(prob, precision, n_rhs, prob->P.M / 2, nullptr).bytes;
 }
 
 int pmlbie_modal_kernels(pmlbie_problem* prob, int mode_lo, int mode_hi, void* dev_out, void* stream) {
@@ -331,18 +346,21 @@ int pmlbie_modal_kernels(pmlbie_problem* prob, int mode_lo, int mode_hi, void* d
     return PMLBIE_OK;
 }
 
-int pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* polar, void* dev_u1,
-                 void* dev_phi1, void* dev_u2, void* dev_phi2, void* stream, pmlbie_report* rep) {
-    if (!prob || !polar || n_rhs < 1 || n_rhs > 4096) return fail(PMLBIE_EINVAL, "bad problem, polar or n_rhs");
-    if (precision != PMLBIE_FP64 && precision != PMLBIE_MIXED) return fail(PMLBIE_EINVAL, "bad precision");
-    for (int r = 0; r < n_rhs; ++r)
-        if (!(polar[r] >= 0.0 && polar[r] < 0.5 * kPi)) return fail(PMLBIE_EINVAL, "polar angle must be in [0, pi/2)");
-    int rc = ensure_device(prob);
-    if (rc) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
-    Workspace w;
-    if ((rc = get_workspace(prob, precision, n_rhs, w))) return rc;
-    const int N = prob->P.N, nm = prob->P.M / 2, n2 = 2 * N;
+// Accumulated device times and refinement statistics of a solve.
+struct SolveStats {
+    double ms_kernels = 0, ms_lu = 0, ms_solve = 0, ms_far = 0, ms_near = 0, ms_near_laplace = 0, ms_assemble = 0;
+    int iters = 0;
+    double resid = 0;
+    int gmres_iters = 0, gmres_modes = 0;
+    double bwd = 0;
+    bool unconverged = false;
+};
+
+// One chunk of modes [lo, hi): system, RHS, LU, solve (+ refinement), outputs
+// into u1.. (already offset to the chunk).  Synchronises the stream at the end.
+static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, int lo, int hi, Workspace& w,
+                       double2* u1, double2* phi1, double2* u2, double2* phi2, cudaStream_t s, SolveStats& st) {
+    const int N = prob->P.N, nm = hi - lo, n2 = 2 * N;
     cudaEvent_t ev[4], sev[5];
     for (auto& e : ev) PMLBIE_CUDA_TRY(cudaEventCreate(&e));
     for (auto& e : sev) PMLBIE_CUDA_TRY(cudaEventCreate(&e));
@@ -354,28 +372,24 @@ int pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* p
             for (int i = 0; i < 5; ++i) cudaEventDestroy(f[i]);
         }
     } guard{ev, sev};
-    g_launches = 0;
-
-    std::vector<double> rpar(6 * n_rhs);
-    for (int r = 0; r < n_rhs; ++r) fresnel(prob->P.k1, prob->P.k2, polar[r], &rpar[6 * r]);
-    PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.rpar, rpar.data(), sizeof(double) * rpar.size(), cudaMemcpyHostToDevice, s));
     pmlbie_dev_extra* ex = extra_of(prob);
-
+    int rc;
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[0], s));
-    if ((rc = build_system(prob, w, s, sev))) return rc;
-    PMLBIE_CUDA_TRY(launch_rhs(prob, n_rhs, w.rpar, ex->nu_r, ex->nu_z, ex->speed, w.b1, w.b2, s));
-    PMLBIE_CUDA_TRY(launch_block_rhs(prob, n_rhs, w.A, w.b1, w.b2, w.B, s));
+    if ((rc = build_system(prob, w, lo, hi, s, sev))) return rc;
+    PMLBIE_CUDA_TRY(launch_rhs(prob, n_rhs, lo, hi, w.rpar, ex->nu_r, ex->nu_z, ex->speed, w.b1, w.b2, s));
+    PMLBIE_CUDA_TRY(launch_block_rhs(prob, n_rhs, nm, w.A, w.b1, w.b2, w.B, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[1], s));
     PMLBIE_CUDA_TRY(cudaMemsetAsync(w.info, 0, sizeof(int) * nm, s));
     const size_t xbytes = sizeof(double2) * (size_t)nm * n2 * n_rhs;
     int iters = 0;
-    double resid = 0.0;
-    std::vector<double> mres(nm, 0.0);
+    double resid = 0.0, bwd = 0.0;
+    bool unconverged = false;
+    std::vector<double> mres(nm, 0.0), mbwd(nm, 0.0);
     if (precision == PMLBIE_FP64) {
         PMLBIE_CUDA_TRY(batched_lu<double2>(n2, nm, w.A, w.piv, w.info, s));
         PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
         PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.X, w.B, xbytes, cudaMemcpyDeviceToDevice, s));
-        PMLBIE_CUDA_TRY(batched_lu_solve<double2>(n2, nm, n_rhs, w.A, w.piv, w.X, s));
+        PMLBIE_CUDA_TRY((batched_lu_solve<double2, double2>(n2, nm, n_rhs, w.A, w.piv, w.X, s)));
     } else {
         PMLBIE_CUDA_TRY(convert_to_c64((int64_t)nm * n2 * n2, w.A, w.A32, s));
         PMLBIE_CUDA_TRY(batched_lu<float2>(n2, nm, w.A32, w.piv, w.info, s));
@@ -383,76 +397,192 @@ int pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* p
         PMLBIE_CUDA_TRY(cudaMemsetAsync(w.X, 0, xbytes, s));
         PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.R, w.B, xbytes, cudaMemcpyDeviceToDevice, s));
         // refinement: FP64 residual with the FP64 matrix, FP32 correction solve; modes whose
-        // residual is already below the tolerance for every rhs are left alone
-        std::vector<double> rn((size_t)nm * n_rhs), bn((size_t)nm * n_rhs);
-        std::vector<int> act(nm, 1);
-        const int max_iter = 30;
-        const double tol = 1e-13;
+        // residual is already below the tolerance for every rhs are left alone.  Modes whose
+        // residual stops contracting (condition number x FP32 LU error near or above 1) are
+        // restarted from zero and solved by FGMRES preconditioned with the same LU.
+        std::vector<double> rn((size_t)nm * n_rhs), bn((size_t)nm * n_rhs), xn((size_t)nm * n_rhs), an(nm),
+            prev(nm, 0.0);
+        std::vector<int> act(nm, 1), slow(nm, 0);
+        const int max_ir = 12;
+        PMLBIE_CUDA_TRY(fro2_c128(n2, nm, w.A, w.an, s));
+        PMLBIE_CUDA_TRY(cudaMemcpyAsync(an.data(), w.an, sizeof(double) * nm, cudaMemcpyDeviceToHost, s));
         PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.active, act.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, s));
-        for (iters = 0; iters <= max_iter; ++iters) {
+        for (iters = 0; iters <= max_ir; ++iters) {
             if (iters > 0) {
-                PMLBIE_CUDA_TRY(residual_c128(n2, nm, n_rhs, w.A, w.X, w.B, w.R, w.rn, w.bn, s, w.active));
+                PMLBIE_CUDA_TRY(residual_c128(n2, nm, n_rhs, w.A, w.X, w.B, w.R, w.rn, w.bn, w.xn, s, w.active));
                 PMLBIE_CUDA_TRY(cudaMemcpyAsync(rn.data(), w.rn, sizeof(double) * rn.size(), cudaMemcpyDeviceToHost, s));
                 PMLBIE_CUDA_TRY(cudaMemcpyAsync(bn.data(), w.bn, sizeof(double) * bn.size(), cudaMemcpyDeviceToHost, s));
+                PMLBIE_CUDA_TRY(cudaMemcpyAsync(xn.data(), w.xn, sizeof(double) * xn.size(), cudaMemcpyDeviceToHost, s));
                 PMLBIE_CUDA_TRY(cudaStreamSynchronize(s));
-                resid = 0.0;
                 int nact = 0;
                 for (int mo = 0; mo < nm; ++mo) {
                     if (!act[mo]) continue;
-                    double worst = 0.0;
+                    double worst = 0.0, wbwd = 0.0;
+                    bool ok = true;
                     for (int r = 0; r < n_rhs; ++r) {
-                        size_t i = (size_t)mo * n_rhs + r;
-                        if (bn[i] > 0) worst = std::max(worst, std::sqrt(rn[i] / bn[i]));
+                        const size_t i = (size_t)mo * n_rhs + r;
+                        const double rr = std::sqrt(rn[i]), bb = std::sqrt(bn[i]);
+                        const double den = std::sqrt(an[mo]) * std::sqrt(xn[i]) + bb;
+                        const double rel = bb > 0 ? rr / bb : 0.0, bwd = den > 0 ? rr / den : 0.0;
+                        worst = std::max(worst, rel);
+                        wbwd = std::max(wbwd, bwd);
+                        if (!(rel <= kTolRel || bwd <= kTolBwd)) ok = false;
                     }
                     mres[mo] = worst;
-                    if (worst <= tol) act[mo] = 0;
-                    else ++nact;
+                    mbwd[mo] = wbwd;
+                    const bool stalled = iters >= 2 && !(wbwd < 0.5 * prev[mo]);
+                    if (ok || (stalled && wbwd <= kTolFloor)) {
+                        act[mo] = 0;     // done, or at the FP64 floor
+                    } else if (stalled) {
+                        act[mo] = 0;     // contraction too slow or divergent: FGMRES
+                        slow[mo] = 1;
+                    } else {
+                        ++nact;
+                    }
+                    prev[mo] = wbwd;
                 }
-                resid = *std::max_element(mres.begin(), mres.end());
-                if (nact == 0 || iters == max_iter) break;
+                if (nact == 0) break;
+                if (iters == max_ir) {
+                    for (int mo = 0; mo < nm; ++mo)
+                        if (act[mo]) act[mo] = 0, slow[mo] = 1;
+                    break;
+                }
                 PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.active, act.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, s));
             }
             PMLBIE_CUDA_TRY(refine_step(n2, nm, n_rhs, w.A32, w.piv, w.R, w.w32, w.X, s, w.active));
         }
+        const int nslow = (int)std::count(slow.begin(), slow.end(), 1);
+        if (nslow > 0) {
+            const size_t per = (size_t)n2 * n_rhs * sizeof(double2);
+            for (int mo = 0; mo < nm; ++mo)
+                if (slow[mo]) PMLBIE_CUDA_TRY(cudaMemsetAsync((char*)w.X + per * mo, 0, per, s));
+            int git = 0;
+            if ((rc = gmres_refine(n2, nm, n_rhs, w.A, w.A32, w.piv, w.B, w.X, slow, w.active, w.gm, kGmresM,
+                                   kGmresCycles, kTolRel, kTolBwd, kTolFloor, an, s, git, mres, mbwd)))
+                return rc;
+            st.gmres_iters = std::max(st.gmres_iters, git);
+            st.gmres_modes += nslow;
+            for (int mo = 0; mo < nm; ++mo)
+                if (slow[mo]) unconverged = true;    // still flagged: FGMRES missed the tolerance
+        }
+        resid = *std::max_element(mres.begin(), mres.end());
+        bwd = *std::max_element(mbwd.begin(), mbwd.end());
     }
-    PMLBIE_CUDA_TRY(launch_outputs(prob, n_rhs, w.X, w.b1, w.b2, (double2*)dev_u1, (double2*)dev_phi1,
-                                   (double2*)dev_u2, (double2*)dev_phi2, s));
+    PMLBIE_CUDA_TRY(launch_outputs(prob, n_rhs, nm, w.X, w.b1, w.b2, u1, phi1, u2, phi2, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[3], s));
     PMLBIE_CUDA_TRY(cudaEventSynchronize(ev[3]));
     std::vector<int> info(nm);
     PMLBIE_CUDA_TRY(cudaMemcpy(info.data(), w.info, sizeof(int) * nm, cudaMemcpyDeviceToHost));
-    if (rep && rep->struct_size >= sizeof(pmlbie_report)) {
-        rep->n_modes = nm;
-        rep->near_pairs = (int)prob->H.near.size();
-        rep->refine_iters = iters;
-        rep->residual = resid;
-        float t01, t12, t23;
-        cudaEventElapsedTime(&t01, ev[0], ev[1]);
-        cudaEventElapsedTime(&t12, ev[1], ev[2]);
-        cudaEventElapsedTime(&t23, ev[2], ev[3]);
-        rep->ms_kernels = t01;
-        rep->ms_lu = t12;
-        rep->ms_solve = t23;
-        float f01, f12, f23;
-        cudaEventElapsedTime(&f01, sev[0], sev[1]);
-        cudaEventElapsedTime(&f12, sev[1], sev[2]);
-        cudaEventElapsedTime(&f23, sev[2], sev[3]);
-        rep->ms_far = f01;
-        rep->ms_near = f12;
-        rep->ms_assemble = f23;
-        rep->launches = (int)g_launches;
-        float fl = 0.f;
-        cudaEventElapsedTime(&fl, sev[1], sev[4]);
-        rep->ms_near_laplace = fl;
-        rep->far_pairs = (int)std::count(prob->H.cls.begin(), prob->H.cls.end(), (uint8_t)kFar);
+    float t[3], f[3], fl = 0.f;
+    for (int i = 0; i < 3; ++i) {
+        cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]);
+        cudaEventElapsedTime(&f[i], sev[i], sev[i + 1]);
     }
+    cudaEventElapsedTime(&fl, sev[1], sev[4]);
+    st.ms_kernels += t[0];
+    st.ms_lu += t[1];
+    st.ms_solve += t[2];
+    st.ms_far += f[0];
+    st.ms_near += f[1];
+    st.ms_assemble += f[2];
+    st.ms_near_laplace += fl;
+    st.iters = std::max(st.iters, iters);
+    st.resid = std::max(st.resid, resid);
+    st.bwd = std::max(st.bwd, bwd);
+    st.unconverged = st.unconverged || unconverged;
     for (int i = 0; i < nm; ++i) {
-        if (info[i] < 0) return fail(PMLBIE_ECUDA, "tensor-core LU update did not complete in mode " + std::to_string(i));
-        if (info[i]) return fail(PMLBIE_ESINGULAR, "zero pivot in mode " + std::to_string(i));
+        if (info[i] < 0)
+            return fail(PMLBIE_ECUDA, "tensor-core LU update did not complete in mode " + std::to_string(lo + i));
+        if (info[i]) return fail(PMLBIE_ESINGULAR, "zero pivot in mode " + std::to_string(lo + i));
     }
-    if (precision == PMLBIE_MIXED && resid > 1e-12)
-        return fail(PMLBIE_ENOCONVERGE, "refinement residual " + std::to_string(resid));
     return PMLBIE_OK;
+}
+
+int pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* o, void* dev_u1, void* dev_phi1,
+                    void* dev_u2, void* dev_phi2, void* stream, pmlbie_report* rep) {
+    if (!prob || !o || o->struct_size < sizeof(pmlbie_solve_opts)) return fail(PMLBIE_EINVAL, "bad problem or options");
+    const int precision = o->precision, n_rhs = o->n_rhs, nmodes_all = prob->P.M / 2;
+    if (!o->polar || n_rhs < 1 || n_rhs > 4096) return fail(PMLBIE_EINVAL, "bad polar or n_rhs");
+    if (precision != PMLBIE_FP64 && precision != PMLBIE_MIXED) return fail(PMLBIE_EINVAL, "bad precision");
+    for (int r = 0; r < n_rhs; ++r) {
+        if (!(o->polar[r] >= 0.0 && o->polar[r] < 0.5 * kPi)) return fail(PMLBIE_EINVAL, "polar angle must be in [0, pi/2)");
+        if (o->azimuth && !std::isfinite(o->azimuth[r])) return fail(PMLBIE_EINVAL, "azimuth must be finite");
+    }
+    int lo = o->mode_lo, hi = o->mode_hi;
+    if (lo == 0 && hi == 0) hi = nmodes_all;
+    if (lo < 0 || hi > nmodes_all || lo >= hi) return fail(PMLBIE_EINVAL, "bad mode range");
+    if (o->max_chunk_modes < 0) return fail(PMLBIE_EINVAL, "max_chunk_modes must be >= 0");
+    int rc = ensure_device(prob);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // modes per chunk: the caller's cap, then the workspace limit (default: 90 %
+    // of the free device memory plus the workspace the problem already holds)
+    int chunk = hi - lo;
+    if (o->max_chunk_modes > 0) chunk = std::min(chunk, o->max_chunk_modes);
+    size_t limit = o->workspace_limit;
+    if (limit == 0) {
+        size_t fr = 0, tot = 0;
+        PMLBIE_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+        limit = (size_t)(0.9 * (double)(fr + prob->ws_bytes));
+    }
+    while (chunk > 1 && plan(prob, precision, n_rhs, chunk, nullptr).bytes > limit) chunk = (chunk + 1) / 2;
+    if (plan(prob, precision, n_rhs, chunk, nullptr).bytes > limit)
+        return fail(PMLBIE_ENOMEM, "one mode's workspace exceeds the workspace limit");
+    Workspace w;
+    if ((rc = get_workspace(prob, precision, n_rhs, chunk, w))) return rc;
+    g_launches = 0;
+    std::vector<double> rpar((size_t)kRhsPar * n_rhs, 0.0);
+    for (int r = 0; r < n_rhs; ++r) {
+        fresnel(prob->P.k1, prob->P.k2, o->polar[r], &rpar[(size_t)kRhsPar * r]);
+        rpar[(size_t)kRhsPar * r + 6] = o->azimuth ? o->azimuth[r] : 0.0;
+    }
+    PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.rpar, rpar.data(), sizeof(double) * rpar.size(), cudaMemcpyHostToDevice, s));
+    SolveStats st;
+    const size_t per_mode = (size_t)prob->P.N * n_rhs;
+    auto at = [&](void* p, int m) { return p ? (double2*)p + (size_t)(m - lo) * per_mode : nullptr; };
+    int chunks = 0;
+    for (int c0 = lo; c0 < hi; c0 += chunk) {
+        const int c1 = std::min(hi, c0 + chunk);
+        rc = solve_chunk(prob, precision, n_rhs, c0, c1, w, at(dev_u1, c0), at(dev_phi1, c0), at(dev_u2, c0),
+                         at(dev_phi2, c0), s, st);
+        ++chunks;
+        if (rc) return rc;
+    }
+    if (rep && rep->struct_size >= sizeof(pmlbie_report)) {
+        rep->n_modes = hi - lo;
+        rep->near_pairs = (int)prob->H.near.size();
+        rep->refine_iters = st.iters;
+        rep->residual = st.resid;
+        rep->ms_kernels = st.ms_kernels;
+        rep->ms_lu = st.ms_lu;
+        rep->ms_solve = st.ms_solve;
+        rep->ms_far = st.ms_far;
+        rep->ms_near = st.ms_near;
+        rep->ms_assemble = st.ms_assemble;
+        rep->ms_near_laplace = st.ms_near_laplace;
+        rep->launches = (int)g_launches;
+        rep->far_pairs = (int)std::count(prob->H.cls.begin(), prob->H.cls.end(), (uint8_t)kFar);
+        rep->chunks = chunks;
+        rep->chunk_modes = chunk;
+        rep->gmres_modes = st.gmres_modes;
+        rep->gmres_iters = st.gmres_iters;
+        rep->backward_error = st.bwd;
+    }
+    if (precision == PMLBIE_MIXED && st.unconverged)
+        return fail(PMLBIE_ENOCONVERGE, "refinement missed its tolerance: residual " + std::to_string(st.resid) +
+                                            ", backward error " + std::to_string(st.bwd));
+    return PMLBIE_OK;
+}
+
+int pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* polar, void* dev_u1,
+                 void* dev_phi1, void* dev_u2, void* dev_phi2, void* stream, pmlbie_report* rep) {
+    pmlbie_solve_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.struct_size = sizeof(o);
+    o.precision = precision;
+    o.n_rhs = n_rhs;
+    o.polar = polar;
+    return pmlbie_solve_ex(prob, &o, dev_u1, dev_phi1, dev_u2, dev_phi2, stream, rep);
 }
 
 int pmlbie_solve_host(pmlbie_problem* prob, int precision, int n_rhs, const double* polar, double* u1,

@@ -135,13 +135,16 @@ cudaError_t launch_near_to_raw(const pmlbie_problem* prob, int mode_lo, int mode
                                const double2* near_out, double2* raw, cudaStream_t s);
 cudaError_t launch_assemble(const pmlbie_problem* prob, int mode_lo, int mode_hi,
                             const double2* near_out, double2* A, cudaStream_t s);
-// rhs_par: per rhs (sin phi, cos phi, R.re, R.im, k*.re, k*.im); nu_r, nu_z, speed per node
-cudaError_t launch_rhs(const pmlbie_problem* prob, int n_rhs, const double* rhs_par_dev,
-                       const double* nu_r, const double* nu_z, const double* speed,
-                       double2* b1, double2* b2, cudaStream_t s);
-cudaError_t launch_block_rhs(const pmlbie_problem* prob, int n_rhs, const double2* A,
+// rhs_par: per rhs kRhsPar doubles (sin phi, cos phi, R.re, R.im, k*.re, k*.im, azimuth, 0);
+// nu_r, nu_z, speed per node; b1, b2 for modes [mode_lo, mode_hi)
+constexpr int kRhsPar = 8;
+cudaError_t launch_rhs(const pmlbie_problem* prob, int n_rhs, int mode_lo, int mode_hi, const double* rhs_par_dev,
+                       const double* nu_r, const double* nu_z, const double* speed, double2* b1, double2* b2,
+                       cudaStream_t s);
+// nm: modes in the chunk (A, b1, b2, B, X hold nm modes)
+cudaError_t launch_block_rhs(const pmlbie_problem* prob, int n_rhs, int nm, const double2* A,
                              const double2* b1, const double2* b2, double2* B, cudaStream_t s);
-cudaError_t launch_outputs(const pmlbie_problem* prob, int n_rhs, const double2* X,
+cudaError_t launch_outputs(const pmlbie_problem* prob, int n_rhs, int nm, const double2* X,
                            const double2* b1, const double2* b2, double2* u1, double2* phi1,
                            double2* u2, double2* phi2, cudaStream_t s);
 
@@ -149,13 +152,28 @@ cudaError_t launch_outputs(const pmlbie_problem* prob, int n_rhs, const double2*
 template <typename T>
 cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s);
 // active: optional per-matrix flags (0 = skip), used to leave converged modes alone
-template <typename T>
-cudaError_t batched_lu_solve(int n, int batch, int nrhs, const T* LU, const int* piv, T* B,
+// factors in TF, right-hand sides and arithmetic in T (T = double2 with TF = float2:
+// FP64 solves with the FP32 factors)
+template <typename T, typename TF>
+cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int* piv, T* B,
                              cudaStream_t s, const int* active = nullptr);
 cudaError_t convert_to_c64(int64_t count, const double2* src, float2* dst, cudaStream_t s);
+// Flexible GMRES (FP64, right-preconditioned by the FP32 LU) for the modes with
+// act[b] = 1; X holds the start and receives the solution; act is cleared for
+// converged modes (relative residual <= tol or normwise backward error
+// |r| / (|A|_F |x| + |b|) <= tol_bw; an2 = |A_b|_F^2), mode_res / mode_bwd
+// receive their final relative residuals and backward errors.
+size_t gmres_scratch_bytes(int n, int batch, int nrhs, int m);
+int gmres_refine(int n, int batch, int nrhs, const double2* A, const float2* LU32, const int* piv,
+                 const double2* B, double2* X, std::vector<int>& act, int* active_dev, void* scratch, int m,
+                 int max_cycles, double tol, double tol_bw, double tol_floor, const std::vector<double>& an2,
+                 cudaStream_t s, int& iters, std::vector<double>& mode_res, std::vector<double>& mode_bwd);
+// R = B - A X with |R|^2, |B|^2, |X|^2 per (matrix, rhs)
 cudaError_t residual_c128(int n, int batch, int nrhs, const double2* A, const double2* X,
-                          const double2* B, double2* R, double* rnorm, double* bnorm,
+                          const double2* B, double2* R, double* rnorm, double* bnorm, double* xnorm,
                           cudaStream_t s, const int* active = nullptr);
+// |A_b|_F^2 per matrix
+cudaError_t fro2_c128(int n, int batch, const double2* A, double* out, cudaStream_t s);
 cudaError_t refine_step(int n, int batch, int nrhs, const float2* LU32, const int* piv,
                         const double2* R, float2* work32, double2* X, cudaStream_t s,
                         const int* active = nullptr);

@@ -851,13 +851,13 @@ __global__ void near_to_raw_kernel(const NearPair* np, int n_grid_near, int N, i
 // ---------------------------------------------------------------------------
 struct RhsArgs {
     DeviceTables T;
-    const double* rhs_par;   // per rhs: sin phi, cos phi, R.re, R.im, ks.re, ks.im
+    const double* rhs_par;   // per rhs (kRhsPar): sin phi, cos phi, R.re, R.im, ks.re, ks.im, azimuth
     const double* nu_r;
     const double* nu_z;
     const double* speed;
-    int N, M, nrhs;
+    int N, M, nrhs, mode_lo, nmodes;
     double w1;
-    double2* b1;   // [mode][l][rhs]
+    double2* b1;   // [mode - mode_lo][l][rhs]
     double2* b2;
 };
 
@@ -866,7 +866,7 @@ __global__ void rhs_kernel(RhsArgs a) {
     const int l = blockIdx.x, r = blockIdx.y, M = a.M;
     double2* s1 = sm;
     double2* s2 = sm + (M / 2 + 1);
-    const double* pr = a.rhs_par + 6 * r;
+    const double* pr = a.rhs_par + kRhsPar * r;
     double sp = pr[0], cp = pr[1];
     double2 R = c2(pr[2], pr[3]), ks = c2(pr[4], pr[5]);
     double rho = a.T.rho[l], z = a.T.z[l], nr = a.nu_r[l], nz = a.nu_z[l], sp_l = a.speed[l];
@@ -887,8 +887,11 @@ __global__ void rhs_kernel(RhsArgs a) {
         s2[j] = cscale(csub(du1, du2), sp_l);
     }
     __syncthreads();
-    const double scale = 2.0 * kPi / M;
-    for (int n = threadIdx.x; n < M / 2; n += blockDim.x) {
+    // modes of the azimuth-0 field (even in theta), then the incidence azimuth
+    // theta_inc rotates mode n by e^{-i n theta_inc}
+    const double scale = 2.0 * kPi / M, az = pr[6];
+    for (int t = threadIdx.x; t < a.nmodes; t += blockDim.x) {
+        const int n = a.mode_lo + t;
         double2 t1 = cadd(s1[0], cscale(s1[M / 2], (n & 1) ? -1.0 : 1.0));
         double2 t2 = cadd(s2[0], cscale(s2[M / 2], (n & 1) ? -1.0 : 1.0));
         for (int j = 1; j < M / 2; ++j) {
@@ -897,9 +900,12 @@ __global__ void rhs_kernel(RhsArgs a) {
             t1 = cadd(t1, cscale(s1[j], 2.0 * c));
             t2 = cadd(t2, cscale(s2[j], 2.0 * c));
         }
-        size_t o = ((size_t)n * a.N + l) * a.nrhs + r;
-        a.b1[o] = cscale(t1, -scale);
-        a.b2[o] = cscale(t2, -scale);
+        double sr, cr;
+        sincos(n * az, &sr, &cr);
+        const double2 rot = c2(-scale * cr, scale * sr);      // -(2 pi/M) e^{-i n theta_inc}
+        size_t o = ((size_t)t * a.N + l) * a.nrhs + r;
+        a.b1[o] = cmul(t1, rot);
+        a.b2[o] = cmul(t2, rot);
     }
 }
 
@@ -1063,10 +1069,12 @@ cudaError_t launch_assemble(const pmlbie_problem* prob, int mode_lo, int mode_hi
     return cudaGetLastError();
 }
 
-cudaError_t launch_rhs(const pmlbie_problem* prob, int n_rhs, const double* rhs_par_dev,
-                            const double* nu_r, const double* nu_z, const double* speed,
-                            double2* b1, double2* b2, cudaStream_t s) {
+cudaError_t launch_rhs(const pmlbie_problem* prob, int n_rhs, int mode_lo, int mode_hi, const double* rhs_par_dev,
+                      const double* nu_r, const double* nu_z, const double* speed, double2* b1, double2* b2,
+                      cudaStream_t s) {
     RhsArgs a;
+    a.mode_lo = mode_lo;
+    a.nmodes = mode_hi - mode_lo;
     a.T = prob->D;
     a.rhs_par = rhs_par_dev;
     a.nu_r = nu_r;
@@ -1085,19 +1093,19 @@ cudaError_t launch_rhs(const pmlbie_problem* prob, int n_rhs, const double* rhs_
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_rhs(const pmlbie_problem* prob, int n_rhs, const double2* A,
+cudaError_t launch_block_rhs(const pmlbie_problem* prob, int n_rhs, int nm, const double2* A,
                              const double2* b1, const double2* b2, double2* B, cudaStream_t s) {
-    int N = prob->P.N, nm = prob->P.M / 2;
+    int N = prob->P.N;
     size_t tot = (size_t)nm * 2 * N * n_rhs;
     block_rhs_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(N, nm, n_rhs, A, b1, b2, B);
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_outputs(const pmlbie_problem* prob, int n_rhs, const double2* X,
+cudaError_t launch_outputs(const pmlbie_problem* prob, int n_rhs, int nm, const double2* X,
                            const double2* b1, const double2* b2, double2* u1, double2* phi1,
                            double2* u2, double2* phi2, cudaStream_t s) {
-    int N = prob->P.N, nm = prob->P.M / 2;
+    int N = prob->P.N;
     size_t tot = (size_t)nm * N * n_rhs;
     outputs_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(N, nm, n_rhs, X, b1, b2, u1, phi1,
                                                                u2, phi2);

@@ -291,14 +291,17 @@ __global__ void gemm_update_kernel(int n, int k0, int kb, T* A) {
 // warp, then the rows outside it are updated with a coalesced
 // matrix-vector product (thread per row, 32 columns).  Matrices whose
 // active flag is 0 are skipped (converged modes during refinement).
-template <typename T>
-__global__ void lu_solve_kernel(int n, int nrhs, const T* LU, const int* piv, T* B, const int* active) {
+template <typename T> __device__ __forceinline__ T widen(float2 v) { return Cx<T>::mk(v.x, v.y); }
+template <typename T> __device__ __forceinline__ T widen(double2 v) { return Cx<T>::mk(v.x, v.y); }
+
+template <typename T, typename TF>
+__global__ void lu_solve_kernel(int n, int nrhs, const TF* LU, const int* piv, T* B, const int* active) {
     const int b = blockIdx.x, r = blockIdx.y;
     if (active && !active[b]) return;
     extern __shared__ unsigned char smraw[];
     T* sxv = reinterpret_cast<T*>(smraw);                    // n entries
     int* spv = reinterpret_cast<int*>(sxv + n);              // n pivots
-    const T* a = LU + (size_t)b * n * n;
+    const TF* a = LU + (size_t)b * n * n;
     const int* pv = piv + (size_t)b * n;
     T* x = B + (size_t)b * n * nrhs;
     __shared__ T sD[kNB][kNB + 1];   // diagonal block, sD[col][row]
@@ -323,7 +326,7 @@ __global__ void lu_solve_kernel(int n, int nrhs, const T* LU, const int* piv, T*
         const int jb = min(kNB, n - j0);
         for (int idx = tid; idx < jb * jb; idx += blockDim.x) {
             int c = idx / jb, i = idx % jb;
-            sD[c][i] = a[(size_t)(j0 + c) * n + j0 + i];
+            sD[c][i] = widen<T>(a[(size_t)(j0 + c) * n + j0 + i]);
         }
         __syncthreads();
         if (warp == 0) {
@@ -338,7 +341,7 @@ __global__ void lu_solve_kernel(int n, int nrhs, const T* LU, const int* piv, T*
         for (int i = j0 + jb + tid; i < n; i += blockDim.x) {
             T acc = sxv[i];
 #pragma unroll 8
-            for (int c = 0; c < jb; ++c) acc = fms(acc, a[(size_t)(j0 + c) * n + i], sxv[j0 + c]);
+            for (int c = 0; c < jb; ++c) acc = fms(acc, widen<T>(a[(size_t)(j0 + c) * n + i]), sxv[j0 + c]);
             sxv[i] = acc;
         }
         __syncthreads();
@@ -349,7 +352,7 @@ __global__ void lu_solve_kernel(int n, int nrhs, const T* LU, const int* piv, T*
         const int j0 = bi * kNB, jb = min(kNB, n - j0);
         for (int idx = tid; idx < jb * jb; idx += blockDim.x) {
             int c = idx / jb, i = idx % jb;
-            sD[c][i] = a[(size_t)(j0 + c) * n + j0 + i];
+            sD[c][i] = widen<T>(a[(size_t)(j0 + c) * n + j0 + i]);
         }
         __syncthreads();
         if (warp == 0) {
@@ -365,7 +368,7 @@ __global__ void lu_solve_kernel(int n, int nrhs, const T* LU, const int* piv, T*
         for (int i = tid; i < j0; i += blockDim.x) {
             T acc = sxv[i];
 #pragma unroll 8
-            for (int c = 0; c < jb; ++c) acc = fms(acc, a[(size_t)(j0 + c) * n + i], sxv[j0 + c]);
+            for (int c = 0; c < jb; ++c) acc = fms(acc, widen<T>(a[(size_t)(j0 + c) * n + i]), sxv[j0 + c]);
             sxv[i] = acc;
         }
         __syncthreads();
@@ -379,22 +382,76 @@ __global__ void c128_to_c64_kernel(int64_t count, const double2* s, float2* d) {
     for (; i < count; i += stride) d[i] = make_float2((float)s[i].x, (float)s[i].y);
 }
 
-// R = B - A X (FP64) per (matrix, row, rhs); squared norms accumulated per (matrix, rhs).
-__global__ void residual_kernel(int n, int nrhs, const double2* A, const double2* X, const double2* B,
-                                double2* R, double* rn2, double* bn2, const int* active) {
-    const int b = blockIdx.y;
+// R -= A X over one chunk of kResCols columns (R starts as B): grid (row
+// blocks, column chunks, matrices), so a single active matrix still spreads
+// over many SMs (the GB300's FP64 pipe is 2 FMA/clk per SM).
+constexpr int kResCols = 32;
+__global__ void residual_kernel(int n, int nrhs, const double2* A, const double2* X, double2* R, const int* active) {
+    const int b = blockIdx.z;
     if (active && !active[b]) return;
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)n * nrhs) return;
-    int r = (int)(idx % nrhs), row = (int)(idx / nrhs);
+    const int r = (int)(idx % nrhs), row = (int)(idx / nrhs);
+    const int c0 = blockIdx.y * kResCols, c1 = min(n, c0 + kResCols);
     const double2* a = A + (size_t)b * n * n;
     const double2* x = X + (size_t)b * n * nrhs;
-    double2 acc = B[(size_t)b * n * nrhs + idx];
-    double2 bb = acc;
-    for (int c = 0; c < n; ++c) acc = fms(acc, a[(size_t)c * n + row], x[(size_t)c * nrhs + r]);
-    R[(size_t)b * n * nrhs + idx] = acc;
-    atomicAdd(rn2 + (size_t)b * nrhs + r, acc.x * acc.x + acc.y * acc.y);
-    atomicAdd(bn2 + (size_t)b * nrhs + r, bb.x * bb.x + bb.y * bb.y);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int c = c0; c < c1; ++c) acc = fms(acc, a[(size_t)c * n + row], x[(size_t)c * nrhs + r]);
+    double* o = reinterpret_cast<double*>(R + (size_t)b * n * nrhs + idx);
+    atomicAdd(o, acc.x);
+    atomicAdd(o + 1, acc.y);
+}
+
+// |R|^2, |B|^2, |X|^2 per (matrix, rhs): grid (batch, nrhs), 256 threads
+__global__ void norms3_kernel(int n, int nrhs, const double2* R, const double2* B, const double2* X, double* rn2,
+                              double* bn2, double* xn2, const int* active) {
+    __shared__ double sh[3][8];
+    const int b = blockIdx.x, r = blockIdx.y;
+    if (active && !active[b]) return;
+    const size_t base = (size_t)b * n * nrhs + r;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int row = threadIdx.x; row < n; row += blockDim.x) {
+        const size_t i = base + (size_t)row * nrhs;
+        s0 += R[i].x * R[i].x + R[i].y * R[i].y;
+        s1 += B[i].x * B[i].x + B[i].y * B[i].y;
+        s2 += X[i].x * X[i].x + X[i].y * X[i].y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffff, s0, o);
+        s1 += __shfl_xor_sync(0xffffffff, s1, o);
+        s2 += __shfl_xor_sync(0xffffffff, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = s0;
+        sh[1][threadIdx.x >> 5] = s1;
+        sh[2][threadIdx.x >> 5] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t0 += sh[0][w], t1 += sh[1][w], t2 += sh[2][w];
+        const size_t k = (size_t)b * nrhs + r;
+        rn2[k] = t0;
+        bn2[k] = t1;
+        xn2[k] = t2;
+    }
+}
+
+// |A_b|_F^2 per matrix (grid (blocks, batch), 256 threads, one atomic per block)
+__global__ void fro2_kernel(int64_t per, const double2* A, double* out) {
+    __shared__ double sh[8];
+    const double2* a = A + (size_t)blockIdx.y * per;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += (int64_t)gridDim.x * blockDim.x)
+        acc += a[i].x * a[i].x + a[i].y * a[i].y;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffff, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sh[w];
+        atomicAdd(out + blockIdx.y, t);
+    }
 }
 
 __global__ void add_correction_kernel(int64_t count, int64_t per_matrix, const float2* d, double2* X,
@@ -445,26 +502,29 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t batched_lu_solve(int n, int batch, int nrhs, const T* LU, const int* piv, T* B,
+template <typename T, typename TF>
+cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int* piv, T* B,
                              cudaStream_t s, const int* active) {
     dim3 g(batch, nrhs);
+    // dynamic: right-hand side + pivots; static: the 32 x 33 diagonal block
     size_t sm = (sizeof(T) + sizeof(int)) * (size_t)n;
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(lu_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm + sizeof(T) * kNB * (kNB + 1) > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(lu_solve_kernel<T, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    lu_solve_kernel<T><<<g, 512, sm, s>>>(n, nrhs, LU, piv, B, active);
+    lu_solve_kernel<T, TF><<<g, 512, sm, s>>>(n, nrhs, LU, piv, B, active);
     count_launch();
     return cudaGetLastError();
 }
 
 template cudaError_t batched_lu<double2>(int, int, double2*, int*, int*, cudaStream_t);
 template cudaError_t batched_lu<float2>(int, int, float2*, int*, int*, cudaStream_t);
-template cudaError_t batched_lu_solve<double2>(int, int, int, const double2*, const int*, double2*,
-                                               cudaStream_t, const int*);
-template cudaError_t batched_lu_solve<float2>(int, int, int, const float2*, const int*, float2*,
-                                              cudaStream_t, const int*);
+template cudaError_t batched_lu_solve<double2, double2>(int, int, int, const double2*, const int*, double2*,
+                                                        cudaStream_t, const int*);
+template cudaError_t batched_lu_solve<float2, float2>(int, int, int, const float2*, const int*, float2*,
+                                                      cudaStream_t, const int*);
+template cudaError_t batched_lu_solve<double2, float2>(int, int, int, const float2*, const int*, double2*,
+                                                       cudaStream_t, const int*);
 
 cudaError_t convert_to_c64(int64_t count, const double2* src, float2* dst, cudaStream_t s) {
     int blocks = (int)std::min<int64_t>((count + 255) / 256, 152 * 32);
@@ -474,14 +534,23 @@ cudaError_t convert_to_c64(int64_t count, const double2* src, float2* dst, cudaS
 }
 
 cudaError_t residual_c128(int n, int batch, int nrhs, const double2* A, const double2* X,
-                          const double2* B, double2* R, double* rnorm, double* bnorm,
+                          const double2* B, double2* R, double* rnorm, double* bnorm, double* xnorm,
                           cudaStream_t s, const int* active) {
-    cudaError_t e = cudaMemsetAsync(rnorm, 0, sizeof(double) * batch * nrhs, s);
+    cudaError_t e = cudaMemcpyAsync(R, B, sizeof(double2) * (size_t)batch * n * nrhs, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(bnorm, 0, sizeof(double) * batch * nrhs, s);
+    dim3 g((unsigned)(((size_t)n * nrhs + 255) / 256), (unsigned)((n + kResCols - 1) / kResCols), batch);
+    residual_kernel<<<g, 256, 0, s>>>(n, nrhs, A, X, R, active);
+    norms3_kernel<<<dim3(batch, nrhs), 256, 0, s>>>(n, nrhs, R, B, X, rnorm, bnorm, xnorm, active);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+cudaError_t fro2_c128(int n, int batch, const double2* A, double* out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * batch, s);
     if (e != cudaSuccess) return e;
-    dim3 g((unsigned)(((size_t)n * nrhs + 255) / 256), batch);
-    residual_kernel<<<g, 256, 0, s>>>(n, nrhs, A, X, B, R, rnorm, bnorm, active);
+    const int64_t per = (int64_t)n * n;
+    dim3 g((unsigned)std::min<int64_t>((per + 255) / 256, 64), batch);
+    fro2_kernel<<<g, 256, 0, s>>>(per, A, out);
     count_launch();
     return cudaGetLastError();
 }
@@ -491,7 +560,7 @@ cudaError_t refine_step(int n, int batch, int nrhs, const float2* LU32, const in
     int64_t cnt = (int64_t)batch * n * nrhs;
     cudaError_t e = convert_to_c64(cnt, R, work32, s);
     if (e != cudaSuccess) return e;
-    e = batched_lu_solve<float2>(n, batch, nrhs, LU32, piv, work32, s, active);
+    e = batched_lu_solve<float2, float2>(n, batch, nrhs, LU32, piv, work32, s, active);
     if (e != cudaSuccess) return e;
     add_correction_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(cnt, (int64_t)n * nrhs, work32, X, active);
     count_launch();

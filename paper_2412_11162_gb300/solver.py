@@ -44,14 +44,24 @@ class Problem:
         B.pmlbie_modal_kernels(self.handle, mode_lo, mode_hi, out, stream)
         return out
 
-    def solve(self, polar, precision=B.PMLBIE_FP64, stream=None, outputs=None, allow_noconverge=False):
-        """Device solve; returns (dict of [mode][node][rhs] complex128 tensors, report)."""
+    def solve(self, polar, precision=B.PMLBIE_FP64, stream=None, outputs=None, allow_noconverge=False,
+              azimuth=None, modes=None, max_chunk_modes=0, workspace_limit=0):
+        """Device solve; returns (dict of [mode][node][rhs] complex128 tensors, report).
+        modes = (lo, hi) solves modes lo..hi-1 only; azimuth: incidence azimuths
+        (one per polar angle); max_chunk_modes / workspace_limit bound the modes
+        factored at once."""
         import torch
         pol = np.atleast_1d(np.asarray(polar, dtype=np.float64))
+        lo, hi = (0, self.n_modes) if modes is None else modes
         if outputs is None:
-            shape = (self.n_modes, self.N, len(pol))
+            shape = (max(hi - lo, 0), self.N, len(pol))   # the library rejects empty or bad ranges
             outputs = {k: torch.empty(shape, dtype=torch.complex128, device="cuda")
                        for k in ("u1", "phi1", "u2", "phi2")}
-        rep = B.pmlbie_solve(self.handle, precision, pol, outputs["u1"], outputs["phi1"], outputs["u2"],
-                             outputs["phi2"], stream, allow_noconverge=allow_noconverge)
+        if azimuth is None and modes is None and max_chunk_modes == 0 and workspace_limit == 0:
+            rep = B.pmlbie_solve(self.handle, precision, pol, outputs["u1"], outputs["phi1"], outputs["u2"],
+                                 outputs["phi2"], stream, allow_noconverge=allow_noconverge)
+        else:
+            rep = B.pmlbie_solve_ex(self.handle, precision, pol, azimuth, lo, hi, max_chunk_modes,
+                                    workspace_limit, outputs["u1"], outputs["phi1"], outputs["u2"],
+                                    outputs["phi2"], stream, allow_noconverge=allow_noconverge)
         return outputs, rep

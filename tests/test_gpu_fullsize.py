@@ -1,7 +1,9 @@
-"""Parity at the benchmark workload (two media omega_1 = 4 pi, omega_2 = 6 pi,
-N = 512, M = 256, the problem bench.py times): modal kernels on a sample of
-node pairs that the oracle evaluates one by one, and agreement of the mixed
-and FP64 GPU solves."""
+"""Parity at full size: the benchmark workload (omega_1 = 4 pi, omega_2 = 6 pi,
+N = 512, M = 256, the problem bench.py times), the large single instance
+(10 pi / 15 pi, N = 1024, M = 512) and the smallest high-frequency instance
+(12 pi / 18 pi, N = 1536, M = 512): modal kernels on a sample of node pairs
+that the oracle evaluates one by one, and agreement of the mixed and FP64 GPU
+solves (FP64 on sampled mode ranges where a full FP64 solve is long)."""
 import numpy as np
 import pytest
 
@@ -10,6 +12,8 @@ from test_gpu_parity import rounding_scale
 pytestmark = pytest.mark.gpu
 
 CFG2 = dict(k1=4 * np.pi, k2=6 * np.pi, N=512, M=256)
+CFG4 = dict(k1=10 * np.pi, k2=15 * np.pi, N=1024, M=512)
+CFG5 = dict(k1=12 * np.pi, k2=18 * np.pi, N=1536, M=512)
 
 
 def _take(d, i):
@@ -35,27 +39,25 @@ def _sample_pairs(G, Q, rng, n=240):
     return sorted(pairs)
 
 
-def test_modal_kernels_sampled_pairs_fullsize():
+def check_sampled_kernels(cfg, mode_ranges, n_pairs=240):
     import torch
     import oracle.kernels as KR
     from oracle.assemble import Quadrature
     from oracle.problem import Geometry, Params
     from paper_2412_11162_gb300 import Problem
-    P = Problem(CFG2["k1"], CFG2["k2"], CFG2["N"], CFG2["M"])
-    Po = Params(**CFG2)
+    P = Problem(cfg["k1"], cfg["k2"], cfg["N"], cfg["M"])
+    Po = Params(**cfg)
     G = Geometry(Po)
     Q = Quadrature(G)
     rng = np.random.default_rng(2412)
-    pairs = _sample_pairs(G, Q, rng)
+    pairs = _sample_pairs(G, Q, rng, n_pairs)
     li = np.array([p[0] for p in pairs])
     mi = np.array([p[1] for p in pairs])
     pg = KR.pair_geometry(_take(G.nodes, li), _take(G.nodes, mi), Po)
     near = KR.near_mask(pg, Po)
     lap = KR.laplace_modes({k: v[near] for k, v in pg.items()}, Po.M - 2)
-    rt = G.nodes["rho_t"].imag
-    pml = (rt[li] > 0) | (rt[mi] > 0)
     assert near.sum() > 20 and (~near).sum() > 20
-    for lo, hi in ((0, 6), (60, 64), (122, 128)):
+    for lo, hi in mode_ranges:
         K = P.modal_kernels(lo, hi).cpu().numpy()
         for reg, omega, sign, ks, kk in (("a", Po.k1, 1.0, 0, 1), ("b", Po.k2, -1.0, 2, 3)):
             pgr = dict(pg)
@@ -77,6 +79,46 @@ def test_modal_kernels_sampled_pairs_fullsize():
                     assert ok.all(), (reg, n, which, ratio)
 
 
+def test_modal_kernels_sampled_pairs_fullsize():
+    check_sampled_kernels(CFG2, ((0, 6), (60, 64), (122, 128)))
+
+
+def test_modal_kernels_sampled_pairs_n1024_m512():
+    check_sampled_kernels(CFG4, ((0, 3), (127, 129), (253, 256)), n_pairs=160)
+
+
+def check_mixed_vs_fp64(cfg, fp64_ranges):
+    """Mixed solve of every mode (mode chunks as the memory needs) against FP64
+    solves of the given mode ranges: u within 1e-6, refinement residual 1e-13."""
+    import time
+    import torch
+    from paper_2412_11162_gb300 import Problem
+    from paper_2412_11162_gb300.binding import PMLBIE_FP64, PMLBIE_MIXED
+    P = Problem(cfg["k1"], cfg["k2"], cfg["N"], cfg["M"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    o32, r32 = P.solve([np.pi / 6], precision=PMLBIE_MIXED)
+    torch.cuda.synchronize()
+    print("mixed solve %.3f s, chunks %d, refinement %d, residual %.1e, backward error %.1e, "
+          "FGMRES modes %d (%d iterations)" % (time.perf_counter() - t0, r32.chunks, r32.refine_iters,
+                                               r32.residual, r32.backward_error, r32.gmres_modes, r32.gmres_iters))
+    # every mode met |r| <= 1e-13 |B| or |r| <= 1e-14 (|A| |x| + |B|) (else the call raises)
+    assert r32.backward_error <= 1e-13
+    for lo, hi in fp64_ranges:
+        o64, _ = P.solve([np.pi / 6], precision=PMLBIE_FP64, modes=(lo, hi))
+        for k in ("u1", "u2"):
+            e = (torch.linalg.vector_norm(o32[k][lo:hi] - o64[k]) / torch.linalg.vector_norm(o64[k])).item()
+            assert e <= 1e-6, (k, lo, hi, e)
+
+
+def test_mixed_matches_fp64_n1024_m512():
+    check_mixed_vs_fp64(CFG4, ((0, 8), (124, 132), (248, 256)))
+
+
+def test_mixed_matches_fp64_n1536_m512():
+    check_mixed_vs_fp64(CFG5, ((0, 4), (252, 256)))
+
+
 def test_mixed_matches_fp64_fullsize():
     import torch
     from paper_2412_11162_gb300 import Problem
@@ -84,7 +126,7 @@ def test_mixed_matches_fp64_fullsize():
     P = Problem(CFG2["k1"], CFG2["k2"], CFG2["N"], CFG2["M"])
     o64, r64 = P.solve([np.pi / 6], precision=PMLBIE_FP64)
     o32, r32 = P.solve([np.pi / 6], precision=PMLBIE_MIXED)
-    assert r32.residual <= 1e-13
+    assert r32.backward_error <= 1e-13
     for k in ("u1", "u2"):
         e = (torch.linalg.vector_norm(o32[k] - o64[k]) / torch.linalg.vector_norm(o64[k])).item()
         assert e <= 1e-6, (k, e)

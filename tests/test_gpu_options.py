@@ -1,0 +1,107 @@
+"""Solve options through the C ABI (pmlbie_solve_ex): mode chunking and mode
+ranges (modes are independent, Sec. 3.3), incidence azimuth and several
+right-hand sides (mode n of a wave with azimuth theta is e^{-i n theta} times
+that of the azimuth-0 wave), checked against the unchunked solve and the FP64
+oracle on the N = 128, M = 64 workload."""
+import numpy as np
+import pytest
+
+from test_gpu_parity import CFG1, check_densities
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    import torch
+    return (torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item()
+
+
+@pytest.fixture(scope="module")
+def prob():
+    from paper_2412_11162_gb300 import Problem
+    return Problem(CFG1["k1"], CFG1["k2"], CFG1["N"], CFG1["M"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_chunked_and_mode_range_equal_full_solve(prob, precision):
+    from paper_2412_11162_gb300.binding import PMLBIE_FP64, PMLBIE_MIXED
+    prec = PMLBIE_FP64 if precision == "fp64" else PMLBIE_MIXED
+    pol = [np.pi / 6, 0.9]
+    full, rf = prob.solve(pol, precision=prec)
+    assert rf.chunks == 1
+    chunked, rc = prob.solve(pol, precision=prec, max_chunk_modes=5)
+    assert rc.chunks == 7 and rc.chunk_modes == 5
+    part, rp = prob.solve(pol, precision=prec, modes=(7, 19), max_chunk_modes=4)
+    assert rp.chunks == 3 and rp.n_modes == 12
+    # Repeated solves differ by rounding: the Alpert corrections are added with
+    # atomics (order not fixed), and in the mixed path each chunk's refinement
+    # stops on its own (1e-13 relative residual or 1e-16 backward error).  The
+    # phi unknowns carry kappa ~1e7 (mode 0, near-null direction at the axis),
+    # so they agree to ~kappa x rounding; u to near rounding.
+    tol = {"u1": 1e-12, "u2": 1e-12, "phi1": 1e-8, "phi2": 1e-8}
+    for k in ("u1", "phi1", "u2", "phi2"):
+        assert _rel(chunked[k], full[k]) <= tol[k], (k, _rel(chunked[k], full[k]))
+        assert _rel(part[k], full[k][7:19]) <= tol[k], (k, _rel(part[k], full[k][7:19]))
+
+
+def test_workspace_limit_forces_chunks(prob):
+    from paper_2412_11162_gb300.binding import PMLBIE_FP64, pmlbie_workspace_bytes
+    whole = pmlbie_workspace_bytes(prob.handle, PMLBIE_FP64, 1)
+    out, rep = prob.solve([np.pi / 6], precision=PMLBIE_FP64, workspace_limit=whole // 3)
+    assert rep.chunks >= 3
+    ref, _ = prob.solve([np.pi / 6], precision=PMLBIE_FP64)
+    assert _rel(out["u1"], ref["u1"]) <= 1e-12
+
+
+def test_azimuth_rotation_identity(prob):
+    """Mode n for azimuth theta equals e^{-i n theta} times mode n at azimuth 0."""
+    import torch
+    from paper_2412_11162_gb300.binding import PMLBIE_FP64
+    pol = [0.4, 0.4, 1.1]
+    az = [0.0, 0.7, -2.3]
+    out, _ = prob.solve(pol, precision=PMLBIE_FP64, azimuth=az)
+    n = torch.arange(prob.n_modes, dtype=torch.float64, device="cuda")
+    for r in (1, 2):
+        rot = torch.exp(-1j * n * az[r]).to(torch.complex128)[:, None]
+        base, _ = prob.solve([pol[r]], precision=PMLBIE_FP64)
+        for k in ("u1", "phi1", "u2", "phi2"):
+            e = _rel(out[k][:, :, r], rot * base[k][:, :, 0])
+            # separate solves: rounding-level matrix differences (atomic Alpert
+            # corrections) times kappa for phi
+            assert e <= (1e-12 if k[0] == "u" else 1e-8), (r, k, e)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_azimuth_against_oracle(prob, precision):
+    """Oblique incidence (polar 0.4, azimuth 0.7) inside a 3-wave solve,
+    against the oracle, whose reference field carries the azimuth directly."""
+    from oracle.assemble import Solution
+    from oracle.problem import Params
+    from paper_2412_11162_gb300.binding import PMLBIE_FP64, PMLBIE_MIXED
+    prec = PMLBIE_FP64 if precision == "fp64" else PMLBIE_MIXED
+    sol = _oracle_oblique()
+    out, _ = prob.solve([np.pi / 6, 0.4, 1.0], precision=prec, azimuth=[0.0, 0.7, 2.0])
+    one = {k: v[:, :, 1:2].contiguous() for k, v in out.items()}
+    tol = 1e-10 if precision == "fp64" else 1e-6
+    check_densities(one, sol, tol, 1e-11, precision + "-oblique")
+
+
+_SOL = {}
+
+
+def _oracle_oblique():
+    from oracle.assemble import Solution
+    from oracle.problem import Params
+    if "s" not in _SOL:
+        _SOL["s"] = Solution(Params(**CFG1, polar=0.4, azimuth=0.7), keep_matrices=True)
+    return _SOL["s"]
+
+
+def test_bad_options_rejected(prob):
+    from paper_2412_11162_gb300.binding import PMLBIE_FP64, PmlbieError
+    with pytest.raises(PmlbieError):
+        prob.solve([0.3], precision=PMLBIE_FP64, modes=(5, 3))
+    with pytest.raises(PmlbieError):
+        prob.solve([0.3], precision=PMLBIE_FP64, modes=(0, prob.n_modes + 1))
+    with pytest.raises(PmlbieError):
+        prob.solve([0.3], precision=PMLBIE_FP64, azimuth=[float("nan")])

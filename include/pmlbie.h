@@ -148,7 +148,10 @@ int  pmlbie_near_count(const pmlbie_problem* prob, int* n_grid_near, int* n_corr
  * for the rule fails. */
 int  pmlbie_alpert_rule(int j, int a, double* x, double* w);
 
-/* Bytes of device workspace a solve with n_rhs right-hand sides allocates. */
+/* Bytes of device workspace a solve of all modes with n_rhs right-hand sides
+ * allocates (kept by the problem for the next solve).  A mixed solve whose
+ * refinement hands modes to FGMRES allocates its Krylov bases (42 vectors of
+ * the chunk's right-hand sides) for the duration of that step only. */
 size_t pmlbie_workspace_bytes(const pmlbie_problem* prob, int precision, int n_rhs);
 
 /* Modal kernels S^_n, K^_n of both regions on every grid node pair (Sec. 4.1,

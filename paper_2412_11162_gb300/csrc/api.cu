@@ -122,7 +122,6 @@ struct Workspace {
     float2 *A32 = nullptr, *w32 = nullptr;
     int *piv = nullptr, *info = nullptr, *active = nullptr;
     double *rn = nullptr, *bn = nullptr, *xn = nullptr, *an = nullptr, *rpar = nullptr;
-    void* gm = nullptr;     // FGMRES scratch (mixed)
     size_t bytes = 0;
 };
 
@@ -170,7 +169,6 @@ Workspace plan(const pmlbie_problem* prob, int precision, int nrhs, int nmodes, 
     w.xn = (double*)take(sizeof(double) * nm * nrhs);
     w.an = (double*)take(sizeof(double) * nm);
     w.rpar = (double*)take(sizeof(double) * kRhsPar * nrhs);
-    if (precision == PMLBIE_MIXED) w.gm = take(gmres_scratch_bytes((int)n2, (int)nm, nrhs, kGmresM));
     w.bytes = off;
     return w;
 }
@@ -457,9 +455,18 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, int lo, i
             for (int mo = 0; mo < nm; ++mo)
                 if (slow[mo]) PMLBIE_CUDA_TRY(cudaMemsetAsync((char*)w.X + per * mo, 0, per, s));
             int git = 0;
-            if ((rc = gmres_refine(n2, nm, n_rhs, w.A, w.A32, w.piv, w.B, w.X, slow, w.active, w.gm, kGmresM,
-                                   kGmresCycles, kTolRel, kTolBwd, kTolFloor, an, s, git, mres, mbwd)))
-                return rc;
+            // FGMRES scratch only when a mode needs it (Krylov bases of 2 m + 2 vectors)
+            void* gm = nullptr;
+            const size_t gbytes = gmres_scratch_bytes(n2, nm, n_rhs, kGmresM);
+            if (cudaMalloc(&gm, gbytes) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(PMLBIE_ENOMEM, "FGMRES scratch allocation failed (" + std::to_string(gbytes) + " bytes)");
+            }
+            rc = gmres_refine(n2, nm, n_rhs, w.A, w.A32, w.piv, w.B, w.X, slow, w.active, gm, kGmresM, kGmresCycles,
+                              kTolRel, kTolBwd, kTolFloor, an, s, git, mres, mbwd);
+            cudaStreamSynchronize(s);
+            cudaFree(gm);
+            if (rc) return rc;
             st.gmres_iters = std::max(st.gmres_iters, git);
             st.gmres_modes += nslow;
             for (int mo = 0; mo < nm; ++mo)

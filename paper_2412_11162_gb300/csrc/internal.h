@@ -138,6 +138,20 @@ cudaError_t launch_assemble(const pmlbie_problem* prob, int mode_lo, int mode_hi
 // rhs_par: per rhs kRhsPar doubles (sin phi, cos phi, R.re, R.im, k*.re, k*.im, azimuth, 0);
 // nu_r, nu_z, speed per node; b1, b2 for modes [mode_lo, mode_hi)
 constexpr int kRhsPar = 8;
+// Raise a kernel's dynamic shared-memory limit to the device maximum minus its
+// static shared memory.  Always the maximum, never the launch's own size:
+// concurrent solves on several host threads set the same attribute, and a
+// smaller value set by one would make another's larger launch fail.
+template <typename K>
+cudaError_t allow_max_smem(K kernel) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    int dev = 0, optin = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
 cudaError_t launch_rhs(const pmlbie_problem* prob, int n_rhs, int mode_lo, int mode_hi, const double* rhs_par_dev,
                        const double* nu_r, const double* nu_z, const double* speed, double2* b1, double2* b2,
                        cudaStream_t s);

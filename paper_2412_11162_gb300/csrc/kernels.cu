@@ -863,9 +863,17 @@ struct RhsArgs {
 
 __global__ void rhs_kernel(RhsArgs a) {
     extern __shared__ double2 sm[];
-    const int l = blockIdx.x, r = blockIdx.y, M = a.M;
-    double2* s1 = sm;
-    double2* s2 = sm + (M / 2 + 1);
+    const int l = blockIdx.x, r = blockIdx.y, M = a.M, K = M / 2;
+    double2* tw = sm;                    // M: e^{-2 pi i e / M}
+    double2* hs = tw + M;                // K: even-DFT weights
+    double2* s1 = hs + K;                // K + 1 samples -> spectrum
+    double2* s2 = s1 + (K + 1);
+    double2* scr = s2 + (K + 1);         // 2 warps x 2K
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const double2 t = a.T.twid[i];
+        tw[i] = t;
+        if (i < K) hs[i] = c2(0.5 + t.y, 0.5 - t.y);
+    }
     const double* pr = a.rhs_par + kRhsPar * r;
     double sp = pr[0], cp = pr[1];
     double2 R = c2(pr[2], pr[3]), ks = c2(pr[4], pr[5]);
@@ -887,25 +895,23 @@ __global__ void rhs_kernel(RhsArgs a) {
         s2[j] = cscale(csub(du1, du2), sp_l);
     }
     __syncthreads();
-    // modes of the azimuth-0 field (even in theta), then the incidence azimuth
-    // theta_inc rotates mode n by e^{-i n theta_inc}
+    // modes of the azimuth-0 field (even in theta: even-sequence DFTs, one per
+    // warp), then the incidence azimuth theta_inc rotates mode n by e^{-i n theta_inc}
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 2) {
+        double2* y = scr + warp * 2 * K;
+        warp_even_dft(warp == 0 ? s1 : s2, y, y + K, K, tw, hs, 1, lane);
+    }
+    __syncthreads();
     const double scale = 2.0 * kPi / M, az = pr[6];
     for (int t = threadIdx.x; t < a.nmodes; t += blockDim.x) {
         const int n = a.mode_lo + t;
-        double2 t1 = cadd(s1[0], cscale(s1[M / 2], (n & 1) ? -1.0 : 1.0));
-        double2 t2 = cadd(s2[0], cscale(s2[M / 2], (n & 1) ? -1.0 : 1.0));
-        for (int j = 1; j < M / 2; ++j) {
-            // cos(n theta_j), exact index reduction
-            double c = cospi(2.0 * (double)((n * j) % M) / M);
-            t1 = cadd(t1, cscale(s1[j], 2.0 * c));
-            t2 = cadd(t2, cscale(s2[j], 2.0 * c));
-        }
         double sr, cr;
         sincos(n * az, &sr, &cr);
         const double2 rot = c2(-scale * cr, scale * sr);      // -(2 pi/M) e^{-i n theta_inc}
         size_t o = ((size_t)t * a.N + l) * a.nrhs + r;
-        a.b1[o] = cmul(t1, rot);
-        a.b2[o] = cmul(t2, rot);
+        a.b1[o] = cmul(s1[n], rot);
+        a.b2[o] = cmul(s2[n], rot);
     }
 }
 
@@ -971,7 +977,7 @@ cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStre
     // twiddles M, DFT weights M/2, angle table S1, nw pair geometries, nw buffers, nw flags
     size_t smem = sizeof(double2) * ((size_t)M + M / 2 + S1 + 4 * (size_t)nw + (size_t)nw * (4 * S1 + M)) +
                   sizeof(double2) * (((size_t)nw + 3) / 4);
-    cudaError_t e = cudaFuncSetAttribute(far_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem(far_kernel);
     if (e != cudaSuccess) return e;
     dim3 grid((N + nw - 1) / nw, N);
     far_kernel<<<grid, 32 * nw, smem, s>>>(a);
@@ -1027,7 +1033,7 @@ cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, do
     size_t smem = sizeof(double2) * ((size_t)2 * M + 8 * (M / 2 + 1) + 4 * (M + 1) + 4 * (size_t)M);
     a.hs_tab = smem + sizeof(double2) * M <= 227 * 1024 ? 1 : 0;
     if (a.hs_tab) smem += sizeof(double2) * M;
-    e = cudaFuncSetAttribute(near_modes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = allow_max_smem(near_modes_kernel);
     if (e != cudaSuccess) return e;
     near_modes_kernel<<<a.npairs, 128, smem, s>>>(a);
     count_launch();
@@ -1087,7 +1093,13 @@ cudaError_t launch_rhs(const pmlbie_problem* prob, int n_rhs, int mode_lo, int m
     a.b1 = b1;
     a.b2 = b2;
     dim3 grid(a.N, n_rhs);
-    size_t smem = sizeof(double2) * 2 * (a.M / 2 + 1);
+    // twiddles M, weights M/2, two spectra M/2+1, two warps' scratch 2 x M
+    const size_t K = a.M / 2;
+    size_t smem = sizeof(double2) * ((size_t)a.M + K + 2 * (K + 1) + 4 * K);
+    if (smem > 48 * 1024) {
+        cudaError_t e = allow_max_smem(rhs_kernel);
+        if (e != cudaSuccess) return e;
+    }
     rhs_kernel<<<grid, 128, smem, s>>>(a);
     count_launch();
     return cudaGetLastError();

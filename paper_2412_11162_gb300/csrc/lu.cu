@@ -474,7 +474,7 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
         dim3 g1((n + kSwapCols - 1) / kSwapCols, batch);
         size_t sm1 = sizeof(T) * ((size_t)kSwapCols * 2 * kNB + kNB * kNB);
         if (k0 == 0) {
-            cudaError_t e = cudaFuncSetAttribute(swap_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+            cudaError_t e = allow_max_smem(swap_trsm_kernel<T>);
             if (e != cudaSuccess) return e;
         }
         swap_trsm_kernel<T><<<g1, 256, sm1, s>>>(n, k0, kb, A, piv);
@@ -483,8 +483,7 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
             if constexpr (sizeof(T) == 8) {
                 // complex64: tensor-core update (tcgen05, TF32 split to FP32 accuracy)
                 if (k0 == 0) {
-                    cudaError_t e = cudaFuncSetAttribute(tcu::update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                         (int)tcu::kSmemBytes);
+                    cudaError_t e = allow_max_smem(tcu::update_kernel);
                     if (e != cudaSuccess) return e;
                 }
                 constexpr int TL = tcu::kTileC;
@@ -509,7 +508,7 @@ cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int
     // dynamic: right-hand side + pivots; static: the 32 x 33 diagonal block
     size_t sm = (sizeof(T) + sizeof(int)) * (size_t)n;
     if (sm + sizeof(T) * kNB * (kNB + 1) > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(lu_solve_kernel<T, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = allow_max_smem(lu_solve_kernel<T, TF>);
         if (e != cudaSuccess) return e;
     }
     lu_solve_kernel<T, TF><<<g, 512, sm, s>>>(n, nrhs, LU, piv, B, active);

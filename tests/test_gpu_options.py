@@ -38,7 +38,10 @@ def test_chunked_and_mode_range_equal_full_solve(prob, precision):
     # stops on its own (1e-13 relative residual or 1e-16 backward error).  The
     # phi unknowns carry kappa ~1e7 (mode 0, near-null direction at the axis),
     # so they agree to ~kappa x rounding; u to near rounding.
-    tol = {"u1": 1e-12, "u2": 1e-12, "phi1": 1e-8, "phi2": 1e-8}
+    # (mixed: each refinement stops at its own point below 1e-13 relative
+    # residual, and the u components amplify that by up to ~1e2)
+    tol = {"u1": 1e-12, "u2": 1e-12, "phi1": 1e-8, "phi2": 1e-8} if precision == "fp64" else \
+        {"u1": 1e-10, "u2": 1e-10, "phi1": 1e-7, "phi2": 1e-7}
     for k in ("u1", "phi1", "u2", "phi2"):
         assert _rel(chunked[k], full[k]) <= tol[k], (k, _rel(chunked[k], full[k]))
         assert _rel(part[k], full[k][7:19]) <= tol[k], (k, _rel(part[k], full[k][7:19]))

@@ -222,6 +222,22 @@ int  pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* 
 int  pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* opts, void* dev_u1, void* dev_phi1,
                      void* dev_u2, void* dev_phi2, void* stream, pmlbie_report* rep);
 
+/* Several independent problem instances (different wavenumbers, geometries,
+ * sizes, right-hand sides), each solved as pmlbie_solve_ex with opts[i] into
+ * dev_u1[i] .. dev_phi2[i] (any of the four arrays may be NULL, and any entry
+ * NULL).  Instances are spread over n_streams (1..8) internal streams, each
+ * driven by its own host thread, so that the latency-bound phases of one
+ * instance (panel factorisation, refinement checks) overlap the work of
+ * another; the internal streams start after the work already queued on
+ * `stream`, and `stream` waits for all of them.  release_workspace != 0 frees
+ * each instance's device workspace after its solve (peak memory = n_streams
+ * workspaces).  reps: n_probs reports or NULL.  The problems must be
+ * distinct.  Returns the first failing instance's status (all instances are
+ * attempted). */
+int  pmlbie_solve_batch(pmlbie_problem* const* probs, int n_probs, const pmlbie_solve_opts* opts,
+                        void* const* dev_u1, void* const* dev_phi1, void* const* dev_u2, void* const* dev_phi2,
+                        int n_streams, int release_workspace, void* stream, pmlbie_report* reps);
+
 /* The same solve with HOST output buffers: the call copies the results to the
  * host (synchronising the stream).  Host buffers have the layout above. */
 int  pmlbie_solve_host(pmlbie_problem* prob, int precision, int n_rhs, const double* polar,

@@ -10,7 +10,7 @@ not built.
 
 
 def __getattr__(name):
-    if name == "Problem":
-        from .solver import Problem
-        return Problem
+    if name in ("Problem", "solve_batch"):
+        from . import solver
+        return getattr(solver, name)
     raise AttributeError(name)

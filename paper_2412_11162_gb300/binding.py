@@ -55,7 +55,7 @@ class pmlbie_solve_opts(ctypes.Structure):
 EXPORTS = ["pmlbie_create", "pmlbie_destroy", "pmlbie_last_error", "pmlbie_nodes", "pmlbie_diagonal",
            "pmlbie_near_count", "pmlbie_alpert_rule", "pmlbie_workspace_bytes", "pmlbie_modal_kernels",
            "pmlbie_modal_kernels_noalloc",
-           "pmlbie_solve", "pmlbie_solve_ex", "pmlbie_solve_host"]
+           "pmlbie_solve", "pmlbie_solve_ex", "pmlbie_solve_batch", "pmlbie_solve_host"]
 
 
 def _load():
@@ -84,9 +84,13 @@ def _load():
                                       ctypes.POINTER(pmlbie_report)]
     lib.pmlbie_solve_ex.argtypes = [vp, ctypes.POINTER(pmlbie_solve_opts), vp, vp, vp, vp, vp,
                                     ctypes.POINTER(pmlbie_report)]
+    lib.pmlbie_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(pmlbie_solve_opts),
+                                       ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                       ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, vp,
+                                       ctypes.POINTER(pmlbie_report)]
     for f in ("pmlbie_nodes", "pmlbie_diagonal", "pmlbie_near_count", "pmlbie_alpert_rule",
               "pmlbie_modal_kernels", "pmlbie_modal_kernels_noalloc", "pmlbie_solve", "pmlbie_solve_ex",
-              "pmlbie_solve_host"):
+              "pmlbie_solve_batch", "pmlbie_solve_host"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -228,6 +232,40 @@ def pmlbie_solve_ex(h, precision, polar, azimuth=None, mode_lo=0, mode_hi=0, max
     if not (allow_noconverge and rc == PMLBIE_ENOCONVERGE):
         check(rc, "pmlbie_solve_ex")
     return rep
+
+
+def make_opts(precision, polar, azimuth=None, mode_lo=0, mode_hi=0, max_chunk_modes=0, workspace_limit=0):
+    """pmlbie_solve_opts and the arrays it points to (keep both alive)."""
+    import numpy as np
+    pol = np.ascontiguousarray(np.asarray(polar, dtype=np.float64).reshape(-1))
+    az = None if azimuth is None else np.ascontiguousarray(np.asarray(azimuth, dtype=np.float64).reshape(-1))
+    if az is not None and len(az) != len(pol):
+        raise ValueError("azimuth and polar differ in length")
+    o = pmlbie_solve_opts()
+    o.struct_size = ctypes.sizeof(pmlbie_solve_opts)
+    o.precision, o.n_rhs, o.polar = precision, len(pol), _dptr(pol)
+    o.azimuth = _dptr(az) if az is not None else None
+    o.mode_lo, o.mode_hi, o.max_chunk_modes, o.workspace_limit = mode_lo, mode_hi, max_chunk_modes, workspace_limit
+    return o, (pol, az)
+
+
+def pmlbie_solve_batch(handles, opts, u1=None, phi1=None, u2=None, phi2=None, n_streams=2,
+                       release_workspace=False, stream=None):
+    """handles: problem handles; opts: list of pmlbie_solve_opts; u1..phi2: lists
+    of device tensors (or None).  Returns the list of reports."""
+    n = len(handles)
+    H = (ctypes.c_void_p * n)(*handles)
+    O = (pmlbie_solve_opts * n)(*opts)
+
+    def arr(ts):
+        return None if ts is None else (ctypes.c_void_p * n)(*[_tptr(t) for t in ts])
+
+    reps = (pmlbie_report * n)()
+    for r in reps:
+        r.struct_size = ctypes.sizeof(pmlbie_report)
+    check(lib.pmlbie_solve_batch(H, n, O, arr(u1), arr(phi1), arr(u2), arr(phi2), n_streams,
+                                 1 if release_workspace else 0, _stream(stream), reps), "pmlbie_solve_batch")
+    return list(reps)
 
 
 def pmlbie_solve_host(h, precision, polar, u1, phi1, u2, phi2, stream=None):

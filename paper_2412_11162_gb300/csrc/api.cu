@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <stdexcept>
+#include <thread>
 
 #include "internal.h"
 
@@ -590,6 +591,73 @@ int pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* p
     o.n_rhs = n_rhs;
     o.polar = polar;
     return pmlbie_solve_ex(prob, &o, dev_u1, dev_phi1, dev_u2, dev_phi2, stream, rep);
+}
+
+int pmlbie_solve_batch(pmlbie_problem* const* probs, int n_probs, const pmlbie_solve_opts* opts,
+                       void* const* dev_u1, void* const* dev_phi1, void* const* dev_u2, void* const* dev_phi2,
+                       int n_streams, int release_workspace, void* stream, pmlbie_report* reps) {
+    if (!probs || n_probs < 1 || !opts) return fail(PMLBIE_EINVAL, "batch: bad problems or options");
+    if (n_streams < 1 || n_streams > 8) return fail(PMLBIE_EINVAL, "batch: n_streams must be 1..8");
+    for (int i = 0; i < n_probs; ++i) {
+        if (!probs[i]) return fail(PMLBIE_EINVAL, "batch: NULL problem " + std::to_string(i));
+        for (int j = 0; j < i; ++j)
+            if (probs[j] == probs[i]) return fail(PMLBIE_EINVAL, "batch: a problem appears twice");
+    }
+    int dev = 0;
+    PMLBIE_CUDA_TRY(cudaGetDevice(&dev));
+    const int ns = std::min(n_streams, n_probs);
+    cudaStream_t caller = (cudaStream_t)stream;
+    std::vector<cudaStream_t> st(ns, nullptr);
+    std::vector<cudaEvent_t> done(ns, nullptr);
+    cudaEvent_t start = nullptr;
+    struct Guard {
+        std::vector<cudaStream_t>& s;
+        std::vector<cudaEvent_t>& d;
+        cudaEvent_t& st;
+        ~Guard() {
+            for (auto x : s)
+                if (x) cudaStreamDestroy(x);
+            for (auto x : d)
+                if (x) cudaEventDestroy(x);
+            if (st) cudaEventDestroy(st);
+        }
+    } guard{st, done, start};
+    PMLBIE_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    PMLBIE_CUDA_TRY(cudaEventRecord(start, caller));
+    for (int k = 0; k < ns; ++k) {
+        PMLBIE_CUDA_TRY(cudaStreamCreateWithFlags(&st[k], cudaStreamNonBlocking));
+        PMLBIE_CUDA_TRY(cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming));
+        PMLBIE_CUDA_TRY(cudaStreamWaitEvent(st[k], start, 0));
+    }
+    // instance i runs on worker i mod ns; each worker is a host thread driving
+    // its stream, so one instance's latency-bound phases overlap another's work
+    std::vector<int> rc(n_probs, PMLBIE_OK);
+    std::vector<std::string> msg(n_probs);
+    auto work = [&](int k) {
+        cudaSetDevice(dev);
+        for (int i = k; i < n_probs; i += ns) {
+            pmlbie_report* rep = reps ? reps + i : nullptr;
+            auto at = [&](void* const* arr) { return arr ? arr[i] : nullptr; };
+            rc[i] = pmlbie_solve_ex(probs[i], opts + i, at(dev_u1), at(dev_phi1), at(dev_u2), at(dev_phi2), st[k],
+                                    rep);
+            if (rc[i]) msg[i] = error_text();
+            if (release_workspace) {
+                cudaStreamSynchronize(st[k]);
+                if (probs[i]->ws) cudaFree(probs[i]->ws);
+                probs[i]->ws = nullptr;
+                probs[i]->ws_bytes = 0;
+            }
+        }
+        cudaEventRecord(done[k], st[k]);
+    };
+    std::vector<std::thread> th;
+    for (int k = 1; k < ns; ++k) th.emplace_back(work, k);
+    work(0);
+    for (auto& t : th) t.join();
+    for (int k = 0; k < ns; ++k) PMLBIE_CUDA_TRY(cudaStreamWaitEvent(caller, done[k], 0));
+    for (int i = 0; i < n_probs; ++i)
+        if (rc[i]) return fail(rc[i], "batch instance " + std::to_string(i) + ": " + msg[i]);
+    return PMLBIE_OK;
 }
 
 int pmlbie_solve_host(pmlbie_problem* prob, int precision, int n_rhs, const double* polar, double* u1,

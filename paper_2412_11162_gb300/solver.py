@@ -65,3 +65,22 @@ class Problem:
                                     workspace_limit, outputs["u1"], outputs["phi1"], outputs["u2"],
                                     outputs["phi2"], stream, allow_noconverge=allow_noconverge)
         return outputs, rep
+
+
+def solve_batch(problems, polar, azimuth=None, precision=B.PMLBIE_MIXED, n_streams=2, release_workspace=False,
+                stream=None):
+    """Solve several Problem instances for the same plane waves in one batch
+    call (pmlbie_solve_batch).  Returns ([outputs dict per problem], [reports])."""
+    import torch
+    opts, keep, outs = [], [], []
+    for P in problems:
+        o, k = B.make_opts(precision, polar, azimuth)
+        opts.append(o)
+        keep.append(k)
+        shape = (P.n_modes, P.N, o.n_rhs)
+        outs.append({key: torch.empty(shape, dtype=torch.complex128, device="cuda")
+                     for key in ("u1", "phi1", "u2", "phi2")})
+    reps = B.pmlbie_solve_batch([P.handle for P in problems], opts, [o["u1"] for o in outs],
+                                [o["phi1"] for o in outs], [o["u2"] for o in outs], [o["phi2"] for o in outs],
+                                n_streams, release_workspace, stream)
+    return outs, reps

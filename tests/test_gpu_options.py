@@ -108,3 +108,26 @@ def test_bad_options_rejected(prob):
         prob.solve([0.3], precision=PMLBIE_FP64, modes=(0, prob.n_modes + 1))
     with pytest.raises(PmlbieError):
         prob.solve([0.3], precision=PMLBIE_FP64, azimuth=[float("nan")])
+
+
+def test_batch_of_uneven_instances_equals_single_solves():
+    """Three instances of different sizes, wavenumbers and bump heights with 4
+    oblique plane waves, solved by one batch call on two worker streams, equal
+    the instance-by-instance solves."""
+    from paper_2412_11162_gb300 import Problem, solve_batch
+    from paper_2412_11162_gb300.binding import PMLBIE_MIXED
+    specs = [(2 * np.pi, 3 * np.pi, 96, 48, 0.15), (3 * np.pi, 4.5 * np.pi, 128, 64, 0.3),
+             (2.5 * np.pi, 3.75 * np.pi, 64, 32, 0.4)]
+    probs = [Problem(k1, k2, N, M, bump_h=h) for k1, k2, N, M, h in specs]
+    pol = [0.2, 0.6, 1.0, 1.3]
+    az = [0.0, 1.0, 2.5, -0.7]
+    outs, reps = solve_batch(probs, pol, az, precision=PMLBIE_MIXED, n_streams=2, release_workspace=True)
+    for P, o, r in zip(probs, outs, reps):
+        ref, _ = P.solve(pol, precision=PMLBIE_MIXED, azimuth=az)
+        assert r.n_modes == P.n_modes
+        for k in ("u1", "phi1", "u2", "phi2"):
+            e = _rel(o[k], ref[k])
+            # two mixed solves agree to their refinement tolerance x conditioning
+            # (well inside the 1e-6 bar of the mixed path; a mix-up of
+            # instances or waves would show as O(1))
+            assert e <= (1e-8 if k[0] == "u" else 1e-6), (P.N, k, e)

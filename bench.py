@@ -33,7 +33,10 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(k1=4 * np.pi, k2=6 * np.pi, N=512, M=256, a1=2.5, T=1.0, S=3.0, bump_h=0.2, polar=np.pi / 6)
 # smaller case of the same physics for profiler captures (matrices ~270 MB, above L2)
-WORKLOADS = {"default": WORKLOAD, "small": dict(WORKLOAD, N=256, M=128)}
+WORKLOADS = {"default": WORKLOAD, "small": dict(WORKLOAD, N=256, M=128),
+             # large single instance and the smallest high-frequency instance
+             "n1024_m512": dict(WORKLOAD, k1=10 * np.pi, k2=15 * np.pi, N=1024, M=512),
+             "n1536_m512": dict(WORKLOAD, k1=12 * np.pi, k2=18 * np.pi, N=1536, M=512)}
 METRIC = "modal kernel entries/s and solve s/problem, mixed vs FP64 GPU at 1e-6 rel err"
 UNIT = "entries/s"
 
@@ -236,17 +239,28 @@ def run_ours(args, rank, world):
         ms = t.item()
     mixed_out = {k: v.clone() for k, v in outs.items()}
 
-    # plain FP64 GPU path on the same problem (1 warm + 2 timed)
-    step(B.PMLBIE_FP64)
+    # plain FP64 GPU path on the same problem (1 warm + 2 timed); for N >= 1024
+    # on modes 0-15 only, the time scaled to all modes (modes cost alike)
+    nm = w["M"] // 2
+    sub = (0, 16) if w["N"] >= 1024 else (0, nm)
+    sub_outs = {k: torch.empty((sub[1] - sub[0],) + shape[1:], dtype=torch.complex128, device="cuda")
+                for k in outs}
+
+    def step64():
+        if sub == (0, nm):
+            return P.solve(polar, precision=B.PMLBIE_FP64, stream=stream, outputs=sub_outs)[1]
+        return P.solve(polar, precision=B.PMLBIE_FP64, stream=stream, outputs=sub_outs, modes=sub)[1]
+
+    step64()
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    fp64_reps = [step(B.PMLBIE_FP64) for _ in range(2)]
+    fp64_reps = [step64() for _ in range(2)]
     f1.record(stream)
     torch.cuda.synchronize()
-    ms64 = f0.elapsed_time(f1) / 2
-    rel = {k: (torch.linalg.vector_norm(mixed_out[k] - outs[k]) / torch.linalg.vector_norm(outs[k])).item()
-           for k in outs}
+    ms64 = f0.elapsed_time(f1) / 2 * nm / (sub[1] - sub[0])
+    rel = {k: (torch.linalg.vector_norm(mixed_out[k][sub[0]:sub[1]] - sub_outs[k]) /
+               torch.linalg.vector_norm(sub_outs[k])).item() for k in outs}
 
     # end to end through the public API with host buffers: create (host tables,
     # first-call upload) + solve + copy of the outputs to pinned host memory
@@ -260,11 +274,8 @@ def run_ours(args, rank, world):
         Q.close()
     torch.cuda.synchronize()
     e2e_ms = 1e3 * (time.perf_counter() - t0) / e2e_steps
-    H = P.nodes()
     ng, nc = P.near_count()
-    # bytes uploaded by the first device call: node tables, pair classes, close-pair table, stencils
-    h2d = (w["N"] * (5 * 8 + 3 * 16 + 3 * 8 + 4 + 16) + w["N"] ** 2 + (ng + nc) * 144 + nc * 4 * (1 + 2 * 10)
-           + (w["M"] // 2 + 1 + w["M"]) * 16 + 8)
+    h2d = h2d_bytes(P, w)
     d2h = 4 * int(np.prod(shape)) * 16
 
     last = reps[-1]
@@ -280,8 +291,9 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128 kernels / c64 LU / c128 refinement", "data": "synthetic",
-        "config": {"workload": "two-layer bump, N=%d M=%d (%d modes), k1=4pi k2=6pi, PML a1=2.5 T=1 S=3, "
-                               "1 plane wave at 30 deg, mixed precision" % (w["N"], w["M"], w["M"] // 2),
+        "config": {"workload": "two-layer bump, N=%d M=%d (%d modes), k1=%gpi k2=%gpi, PML a1=2.5 T=1 S=3, "
+                               "1 plane wave at 30 deg, mixed precision" % (w["N"], w["M"], w["M"] // 2,
+                                                                           w["k1"] / np.pi, w["k2"] / np.pi),
                    "parallelism": "independent problems per GPU" if world > 1 else "1 GPU",
                    "l2": "working set > L2 (129 MB): %d MB of per-mode matrices rebuilt every step" %
                          int(((w["M"] // 2) * (2 * w["N"]) ** 2 * 24) / 1e6)},
@@ -291,7 +303,9 @@ def run_ours(args, rank, world):
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
         "refine_iters": last.refine_iters, "refine_residual": last.residual,
         "refine_backward_error": last.backward_error, "gmres_modes": last.gmres_modes,
-        "fp64_gpu": {"ms_per_step": ms64, "value": world * epp / (ms64 / 1e3), "stages_ms": {
+        "gmres_iters": last.gmres_iters,
+        "fp64_gpu": {"ms_per_step": ms64, "value": world * epp / (ms64 / 1e3),
+                     "modes_timed": list(sub), "stages_ms": {
             "far_kernel": fp64_reps[-1].ms_far, "near_kernels": fp64_reps[-1].ms_near,
             "assemble": fp64_reps[-1].ms_assemble, "lu_fp64": fp64_reps[-1].ms_lu,
             "solve": fp64_reps[-1].ms_solve}},
@@ -306,7 +320,7 @@ def run_ours(args, rank, world):
                 "note": "per step: create (host setup) + solve_host to pinned buffers + destroy"},
     }
     if rank == 0 and not args.no_cpu_baseline:
-        rows = 160
+        rows = max(12, int(160 * (512 * 256) / (w["N"] * w["M"])))
         e, t = oracle_sample(w, rows=rows)
         line["cpu_baseline"] = {"value": e / t, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                                 "sample": "modal kernels of %d target rows x all %d sources + their Alpert "
@@ -316,6 +330,117 @@ def run_ours(args, rank, world):
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+def h2d_bytes(P, w):
+    """Bytes the first device call uploads: node tables, pair classes,
+    close-pair table, Alpert stencils, angle and twiddle tables."""
+    ng, nc = P.near_count()
+    return (w["N"] * (5 * 8 + 3 * 16 + 3 * 8 + 4 + 16) + w["N"] ** 2 + (ng + nc) * 144 + nc * 4 * (1 + 2 * 10)
+            + (w["M"] // 2 + 1 + w["M"] + 2 * w["M"]) * 16 + 8)
+
+
+def batched_instances():
+    """Eight instances (seeded): omega_1 = linspace(2 pi, 8 pi, 8), omega_2 =
+    1.5 omega_1, bump heights U[0.1, 0.4], N drawn from {256, 384, 512, 768,
+    1024} (after the heights), M = N/2; 64 plane waves: polar (i + 1/2)(pi/2)/8,
+    azimuth 2 pi j/8, i, j = 0..7."""
+    rng = np.random.default_rng(2412)
+    h = rng.uniform(0.1, 0.4, 8)
+    Ns = rng.choice([256, 384, 512, 768, 1024], 8)
+    k1 = np.linspace(2 * np.pi, 8 * np.pi, 8)
+    inst = [dict(WORKLOAD, k1=float(k1[i]), k2=float(1.5 * k1[i]), N=int(Ns[i]), M=int(Ns[i]) // 2,
+                 bump_h=float(h[i])) for i in range(8)]
+    polar = [(i + 0.5) * (np.pi / 2) / 8 for i in range(8) for _ in range(8)]
+    azimuth = [2 * np.pi * j / 8 for _ in range(8) for j in range(8)]
+    return inst, polar, azimuth
+
+
+def run_batched(args, rank, world):
+    """One step = one batch call solving the eight instances (mixed precision,
+    64 right-hand sides each) on two worker streams."""
+    import torch
+    from paper_2412_11162_gb300 import Problem, solve_batch
+    from paper_2412_11162_gb300 import binding as B
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    if rank != 0:
+        return
+    inst, polar, azimuth = batched_instances()
+
+    def make():
+        return [Problem(w["k1"], w["k2"], w["N"], w["M"], a1=w["a1"], T=w["T"], S=w["S"], bump_h=w["bump_h"])
+                for w in inst]
+
+    probs = make()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return solve_batch(probs, polar, azimuth, precision=B.PMLBIE_MIXED, n_streams=2, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        outs, reps = step()
+    torch.cuda.synchronize()
+    steps = max(1, args.steps // 3)
+    with ClockSampler(dev) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        clk.mark_start()
+        e0.record(stream)
+        for _ in range(steps):
+            outs, reps = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk.mark_end()
+    ms = e0.elapsed_time(e1) / steps
+    ent = sum(entries_per_problem(w) for w in inst)
+    # FP64 check on the first instance, all 64 waves
+    o64, _ = probs[0].solve(polar, precision=B.PMLBIE_FP64, azimuth=azimuth)
+    rel = {k: (torch.linalg.vector_norm(outs[0][k] - o64[k]) / torch.linalg.vector_norm(o64[k])).item()
+           for k in o64}
+    # end to end: create the 8 problems, batch solve, copy all outputs to pinned host memory
+    pinned = [[torch.empty(o["u1"].shape, dtype=torch.complex128, pin_memory=True) for _ in range(4)]
+              for o in outs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Q = make()
+    qo, _ = solve_batch(Q, polar, azimuth, precision=B.PMLBIE_MIXED, n_streams=2, stream=stream)
+    for o, pin in zip(qo, pinned):
+        for t, key in zip(pin, ("u1", "phi1", "u2", "phi2")):
+            t.copy_(o[key], non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_ms = 1e3 * (time.perf_counter() - t0)
+    for q in Q:
+        q.close()
+    d2h = sum(4 * o["u1"].numel() * 16 for o in outs)
+    big = max(range(8), key=lambda i: reps[i].ms_far)
+    clocks = clk.summary()
+    roof = roofline(inst[big], reps[big], peaks(), clocks)
+    roof["kernel"] += " of the N=%d instance" % inst[big]["N"]
+    line = {
+        "metric": METRIC, "value": ent / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128 kernels / c64 LU / c128 refinement", "data": "synthetic",
+        "config": {"workload": "8 instances (seed 2412): k1=linspace(2pi,8pi,8), k2=1.5 k1, h~U[0.1,0.4], "
+                               "N=%s, M=N/2; 64 plane waves (8 polar x 8 azimuth); mixed; 2 worker streams" %
+                               [w["N"] for w in inst],
+                   "parallelism": "1 GPU",
+                   "l2": "working set > L2: every step rebuilds %.1f GB of per-mode matrices" %
+                         (sum((w["M"] // 2) * (2 * w["N"]) ** 2 * 24 for w in inst) / 1e9)},
+        "solve_s_per_problem": ms / 1e3 / 8,
+        "per_instance": [{"N": w["N"], "M": w["M"], "k1_over_pi": w["k1"] / np.pi, "ms_far": r.ms_far,
+                          "ms_near": r.ms_near, "ms_lu": r.ms_lu, "ms_solve": r.ms_solve,
+                          "refine_iters": r.refine_iters, "gmres_modes": r.gmres_modes,
+                          "backward_error": r.backward_error} for w, r in zip(inst, reps)],
+        "mixed_vs_fp64_rel_err_instance0": rel,
+        "gpu_launches": int(sum(r.launches for r in reps)),
+        "roofline": roof, "clocks": clocks,
+        "e2e": {"value": ent / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(sum(h2d_bytes(q, w) for q, w in zip(probs, inst))),
+                "d2h_bytes_per_step": int(d2h),
+                "note": "create the 8 problems (host tables) + batch solve + copy of all outputs to pinned host"},
+    }
+    print(json.dumps(line))
 
 
 def far_flops_per_pair(M):
@@ -381,15 +506,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="default", choices=sorted(WORKLOADS),
-                    help="'small' (N=256, M=128) is for profiler captures only")
+    ap.add_argument("--workload", default="default", choices=sorted(WORKLOADS) + ["batched8"],
+                    help="default: N=512, M=256 (the headline); 'small' (N=256, M=128) is for profiler "
+                         "captures; n1024_m512 / n1536_m512: the large single and high-frequency instances; "
+                         "batched8: eight seeded instances with 64 plane waves each, one batch call per step")
     args = ap.parse_args()
     global WORKLOAD
-    WORKLOAD = WORKLOADS[args.workload]
+    WORKLOAD = WORKLOADS.get(args.workload, WORKLOADS["default"])
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batched8":
+        run_batched(args, rank, world)
     else:
         run_ours(args, rank, world)
 

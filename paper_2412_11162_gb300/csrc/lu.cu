@@ -286,38 +286,42 @@ __global__ void gemm_update_kernel(int n, int k0, int kb, T* A) {
 
 // Solve LU x = b for every matrix and rhs: row swaps, then blocked unit-lower
 // forward and upper backward substitution.  One CTA (512 threads) per
-// (matrix, rhs); B is [b][n][nrhs].  The right-hand side lives in shared
-// memory for the whole solve; each 32-row diagonal block is solved by one
-// warp, then the rows outside it are updated with a coalesced
-// matrix-vector product (thread per row, 32 columns).  Matrices whose
-// active flag is 0 are skipped (converged modes during refinement).
+// (matrix, group of up to kSolveR right-hand sides); B is [b][n][nrhs].  The
+// group's right-hand sides live in shared memory ([row][R]) for the whole
+// solve, so each factor element read from memory serves all of them; each
+// 32-row diagonal block is solved by one warp per right-hand side, then the
+// rows outside it are updated (thread per row, 32 columns, all R columns).
+// Matrices whose active flag is 0 are skipped (converged modes).
+constexpr int kSolveR = 8;
+
 template <typename T> __device__ __forceinline__ T widen(float2 v) { return Cx<T>::mk(v.x, v.y); }
 template <typename T> __device__ __forceinline__ T widen(double2 v) { return Cx<T>::mk(v.x, v.y); }
 
 template <typename T, typename TF>
-__global__ void lu_solve_kernel(int n, int nrhs, const TF* LU, const int* piv, T* B, const int* active) {
-    const int b = blockIdx.x, r = blockIdx.y;
+__global__ void lu_solve_kernel(int n, int nrhs, int R, const TF* LU, const int* piv, T* B, const int* active) {
+    const int b = blockIdx.x, r0 = blockIdx.y * R, nr = min(R, nrhs - r0);
     if (active && !active[b]) return;
     extern __shared__ unsigned char smraw[];
-    T* sxv = reinterpret_cast<T*>(smraw);                    // n entries
-    int* spv = reinterpret_cast<int*>(sxv + n);              // n pivots
+    T* sx = reinterpret_cast<T*>(smraw);                     // n x R entries, sx[i * R + q]
+    int* spv = reinterpret_cast<int*>(sx + (size_t)n * R);   // n pivots
     const TF* a = LU + (size_t)b * n * n;
     const int* pv = piv + (size_t)b * n;
     T* x = B + (size_t)b * n * nrhs;
     __shared__ T sD[kNB][kNB + 1];   // diagonal block, sD[col][row]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < n; i += blockDim.x) {
-        sxv[i] = x[(size_t)i * nrhs + r];
-        spv[i] = pv[i];
+    for (int idx = tid; idx < n * nr; idx += blockDim.x) {
+        const int i = idx / nr, q = idx - i * nr;
+        sx[i * R + q] = x[(size_t)i * nrhs + r0 + q];
     }
+    for (int i = tid; i < n; i += blockDim.x) spv[i] = pv[i];
     __syncthreads();
-    if (tid == 0)
+    if (tid < nr)
         for (int j = 0; j < n; ++j) {
-            int p = spv[j];
+            const int p = spv[j];
             if (p != j) {
-                T t = sxv[j];
-                sxv[j] = sxv[p];
-                sxv[p] = t;
+                T t = sx[j * R + tid];
+                sx[j * R + tid] = sx[p * R + tid];
+                sx[p * R + tid] = t;
             }
         }
     __syncthreads();
@@ -329,20 +333,30 @@ __global__ void lu_solve_kernel(int n, int nrhs, const TF* LU, const int* piv, T
             sD[c][i] = widen<T>(a[(size_t)(j0 + c) * n + j0 + i]);
         }
         __syncthreads();
-        if (warp == 0) {
-            T v = lane < jb ? sxv[j0 + lane] : Cx<T>::mk(0, 0);
+        if (warp < nr) {
+            T v = lane < jb ? sx[(j0 + lane) * R + warp] : Cx<T>::mk(0, 0);
             for (int c = 0; c < jb; ++c) {
                 T xc = Cx<T>::mk(__shfl_sync(0xffffffff, v.x, c), __shfl_sync(0xffffffff, v.y, c));
                 if (lane > c && lane < jb) v = fms(v, sD[c][lane], xc);
             }
-            if (lane < jb) sxv[j0 + lane] = v;
+            if (lane < jb) sx[(j0 + lane) * R + warp] = v;
         }
         __syncthreads();
         for (int i = j0 + jb + tid; i < n; i += blockDim.x) {
-            T acc = sxv[i];
-#pragma unroll 8
-            for (int c = 0; c < jb; ++c) acc = fms(acc, widen<T>(a[(size_t)(j0 + c) * n + i]), sxv[j0 + c]);
-            sxv[i] = acc;
+            T acc[kSolveR];
+#pragma unroll
+            for (int q = 0; q < kSolveR; ++q)
+                if (q < nr) acc[q] = sx[i * R + q];
+#pragma unroll 4
+            for (int c = 0; c < jb; ++c) {
+                const T l = widen<T>(a[(size_t)(j0 + c) * n + i]);
+#pragma unroll
+                for (int q = 0; q < kSolveR; ++q)
+                    if (q < nr) acc[q] = fms(acc[q], l, sx[(j0 + c) * R + q]);
+            }
+#pragma unroll
+            for (int q = 0; q < kSolveR; ++q)
+                if (q < nr) sx[i * R + q] = acc[q];
         }
         __syncthreads();
     }
@@ -355,25 +369,38 @@ __global__ void lu_solve_kernel(int n, int nrhs, const TF* LU, const int* piv, T
             sD[c][i] = widen<T>(a[(size_t)(j0 + c) * n + j0 + i]);
         }
         __syncthreads();
-        if (warp == 0) {
-            T v = lane < jb ? sxv[j0 + lane] : Cx<T>::mk(0, 0);
+        if (warp < nr) {
+            T v = lane < jb ? sx[(j0 + lane) * R + warp] : Cx<T>::mk(0, 0);
             for (int c = jb - 1; c >= 0; --c) {
                 if (lane == c) v = mul(v, rcp(sD[c][c]));
                 T xc = Cx<T>::mk(__shfl_sync(0xffffffff, v.x, c), __shfl_sync(0xffffffff, v.y, c));
                 if (lane < c) v = fms(v, sD[c][lane], xc);
             }
-            if (lane < jb) sxv[j0 + lane] = v;
+            if (lane < jb) sx[(j0 + lane) * R + warp] = v;
         }
         __syncthreads();
         for (int i = tid; i < j0; i += blockDim.x) {
-            T acc = sxv[i];
-#pragma unroll 8
-            for (int c = 0; c < jb; ++c) acc = fms(acc, widen<T>(a[(size_t)(j0 + c) * n + i]), sxv[j0 + c]);
-            sxv[i] = acc;
+            T acc[kSolveR];
+#pragma unroll
+            for (int q = 0; q < kSolveR; ++q)
+                if (q < nr) acc[q] = sx[i * R + q];
+#pragma unroll 4
+            for (int c = 0; c < jb; ++c) {
+                const T u = widen<T>(a[(size_t)(j0 + c) * n + i]);
+#pragma unroll
+                for (int q = 0; q < kSolveR; ++q)
+                    if (q < nr) acc[q] = fms(acc[q], u, sx[(j0 + c) * R + q]);
+            }
+#pragma unroll
+            for (int q = 0; q < kSolveR; ++q)
+                if (q < nr) sx[i * R + q] = acc[q];
         }
         __syncthreads();
     }
-    for (int i = tid; i < n; i += blockDim.x) x[(size_t)i * nrhs + r] = sxv[i];
+    for (int idx = tid; idx < n * nr; idx += blockDim.x) {
+        const int i = idx / nr, q = idx - i * nr;
+        x[(size_t)i * nrhs + r0 + q] = sx[i * R + q];
+    }
 }
 
 __global__ void c128_to_c64_kernel(int64_t count, const double2* s, float2* d) {
@@ -504,14 +531,18 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
 template <typename T, typename TF>
 cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int* piv, T* B,
                              cudaStream_t s, const int* active) {
-    dim3 g(batch, nrhs);
-    // dynamic: right-hand side + pivots; static: the 32 x 33 diagonal block
-    size_t sm = (sizeof(T) + sizeof(int)) * (size_t)n;
+    // right-hand sides per CTA: up to kSolveR, as many as fit in shared memory
+    // (about 200 KB for the group and the pivots)
+    int R = std::min(nrhs, kSolveR);
+    while (R > 1 && (sizeof(T) * (size_t)R + sizeof(int)) * (size_t)n > 200 * 1024) --R;
+    dim3 g(batch, (nrhs + R - 1) / R);
+    // dynamic: right-hand sides + pivots; static: the 32 x 33 diagonal block
+    size_t sm = (sizeof(T) * (size_t)R + sizeof(int)) * (size_t)n;
     if (sm + sizeof(T) * kNB * (kNB + 1) > 48 * 1024) {
         cudaError_t e = allow_max_smem(lu_solve_kernel<T, TF>);
         if (e != cudaSuccess) return e;
     }
-    lu_solve_kernel<T, TF><<<g, 512, sm, s>>>(n, nrhs, LU, piv, B, active);
+    lu_solve_kernel<T, TF><<<g, 512, sm, s>>>(n, nrhs, R, LU, piv, B, active);
     count_launch();
     return cudaGetLastError();
 }

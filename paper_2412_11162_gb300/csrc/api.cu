@@ -456,18 +456,33 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, int lo, i
             for (int mo = 0; mo < nm; ++mo)
                 if (slow[mo]) PMLBIE_CUDA_TRY(cudaMemsetAsync((char*)w.X + per * mo, 0, per, s));
             int git = 0;
-            // FGMRES scratch only when a mode needs it (Krylov bases of 2 m + 2 vectors)
+            // FGMRES on the contiguous range of modes [g0, g1) holding every
+            // slow mode (its Krylov bases allocated for that range only)
+            int g0 = nm, g1 = 0;
+            for (int mo = 0; mo < nm; ++mo)
+                if (slow[mo]) g0 = std::min(g0, mo), g1 = mo + 1;
+            const int gn = g1 - g0;
             void* gm = nullptr;
-            const size_t gbytes = gmres_scratch_bytes(n2, nm, n_rhs, kGmresM);
+            const size_t gbytes = gmres_scratch_bytes(n2, gn, n_rhs, kGmresM);
             if (cudaMalloc(&gm, gbytes) != cudaSuccess) {
                 cudaGetLastError();
                 return fail(PMLBIE_ENOMEM, "FGMRES scratch allocation failed (" + std::to_string(gbytes) + " bytes)");
             }
-            rc = gmres_refine(n2, nm, n_rhs, w.A, w.A32, w.piv, w.B, w.X, slow, w.active, gm, kGmresM, kGmresCycles,
-                              kTolRel, kTolBwd, kTolFloor, an, s, git, mres, mbwd);
+            std::vector<int> gslow(slow.begin() + g0, slow.begin() + g1);
+            std::vector<double> gan(an.begin() + g0, an.begin() + g1), gres(mres.begin() + g0, mres.begin() + g1),
+                gbwd(mbwd.begin() + g0, mbwd.begin() + g1);
+            const size_t mat = (size_t)n2 * n2, vec = (size_t)n2 * n_rhs;
+            rc = gmres_refine(n2, gn, n_rhs, w.A + g0 * mat, w.A32 + g0 * mat, w.piv + (size_t)g0 * n2,
+                              w.B + g0 * vec, w.X + g0 * vec, gslow, w.active, gm, kGmresM, kGmresCycles, kTolRel,
+                              kTolBwd, kTolFloor, gan, s, git, gres, gbwd);
             cudaStreamSynchronize(s);
             cudaFree(gm);
             if (rc) return rc;
+            for (int t = 0; t < gn; ++t) {
+                slow[g0 + t] = gslow[t];
+                mres[g0 + t] = gres[t];
+                mbwd[g0 + t] = gbwd[t];
+            }
             st.gmres_iters = std::max(st.gmres_iters, git);
             st.gmres_modes += nslow;
             for (int mo = 0; mo < nm; ++mo)

@@ -297,7 +297,7 @@ constexpr int kSolveR = 8;
 template <typename T> __device__ __forceinline__ T widen(float2 v) { return Cx<T>::mk(v.x, v.y); }
 template <typename T> __device__ __forceinline__ T widen(double2 v) { return Cx<T>::mk(v.x, v.y); }
 
-template <typename T, typename TF>
+template <typename T, typename TF, int RM>
 __global__ void lu_solve_kernel(int n, int nrhs, int R, const TF* LU, const int* piv, T* B, const int* active) {
     const int b = blockIdx.x, r0 = blockIdx.y * R, nr = min(R, nrhs - r0);
     if (active && !active[b]) return;
@@ -343,19 +343,19 @@ __global__ void lu_solve_kernel(int n, int nrhs, int R, const TF* LU, const int*
         }
         __syncthreads();
         for (int i = j0 + jb + tid; i < n; i += blockDim.x) {
-            T acc[kSolveR];
+            T acc[RM];
 #pragma unroll
-            for (int q = 0; q < kSolveR; ++q)
+            for (int q = 0; q < RM; ++q)
                 if (q < nr) acc[q] = sx[i * R + q];
 #pragma unroll 4
             for (int c = 0; c < jb; ++c) {
                 const T l = widen<T>(a[(size_t)(j0 + c) * n + i]);
 #pragma unroll
-                for (int q = 0; q < kSolveR; ++q)
+                for (int q = 0; q < RM; ++q)
                     if (q < nr) acc[q] = fms(acc[q], l, sx[(j0 + c) * R + q]);
             }
 #pragma unroll
-            for (int q = 0; q < kSolveR; ++q)
+            for (int q = 0; q < RM; ++q)
                 if (q < nr) sx[i * R + q] = acc[q];
         }
         __syncthreads();
@@ -380,19 +380,19 @@ __global__ void lu_solve_kernel(int n, int nrhs, int R, const TF* LU, const int*
         }
         __syncthreads();
         for (int i = tid; i < j0; i += blockDim.x) {
-            T acc[kSolveR];
+            T acc[RM];
 #pragma unroll
-            for (int q = 0; q < kSolveR; ++q)
+            for (int q = 0; q < RM; ++q)
                 if (q < nr) acc[q] = sx[i * R + q];
 #pragma unroll 4
             for (int c = 0; c < jb; ++c) {
                 const T u = widen<T>(a[(size_t)(j0 + c) * n + i]);
 #pragma unroll
-                for (int q = 0; q < kSolveR; ++q)
+                for (int q = 0; q < RM; ++q)
                     if (q < nr) acc[q] = fms(acc[q], u, sx[(j0 + c) * R + q]);
             }
 #pragma unroll
-            for (int q = 0; q < kSolveR; ++q)
+            for (int q = 0; q < RM; ++q)
                 if (q < nr) sx[i * R + q] = acc[q];
         }
         __syncthreads();
@@ -538,11 +538,20 @@ cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int
     dim3 g(batch, (nrhs + R - 1) / R);
     // dynamic: right-hand sides + pivots; static: the 32 x 33 diagonal block
     size_t sm = (sizeof(T) * (size_t)R + sizeof(int)) * (size_t)n;
-    if (sm + sizeof(T) * kNB * (kNB + 1) > 48 * 1024) {
-        cudaError_t e = allow_max_smem(lu_solve_kernel<T, TF>);
-        if (e != cudaSuccess) return e;
+    const bool big = sm + sizeof(T) * kNB * (kNB + 1) > 48 * 1024;
+    if (R == 1) {   // the common single-wave case, without the group loops
+        if (big) {
+            cudaError_t e = allow_max_smem(lu_solve_kernel<T, TF, 1>);
+            if (e != cudaSuccess) return e;
+        }
+        lu_solve_kernel<T, TF, 1><<<g, 512, sm, s>>>(n, nrhs, R, LU, piv, B, active);
+    } else {
+        if (big) {
+            cudaError_t e = allow_max_smem(lu_solve_kernel<T, TF, kSolveR>);
+            if (e != cudaSuccess) return e;
+        }
+        lu_solve_kernel<T, TF, kSolveR><<<g, 512, sm, s>>>(n, nrhs, R, LU, piv, B, active);
     }
-    lu_solve_kernel<T, TF><<<g, 512, sm, s>>>(n, nrhs, R, LU, piv, B, active);
     count_launch();
     return cudaGetLastError();
 }

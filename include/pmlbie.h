@@ -215,7 +215,10 @@ int  pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* 
  * and factors its systems and solves them before the next starts (the kernel
  * sampling is repeated per chunk).  Plane wave r has polar angle polar[r] and
  * azimuth azimuth[r]; mode n of its data is e^{-i n azimuth} times that of the
- * azimuth-0 wave (modes -n follow as e^{+i n azimuth} times the same).
+ * azimuth-0 wave (modes -n follow as e^{+i n azimuth} times the same); waves
+ * that share a polar angle are therefore solved once, at azimuth 0, and
+ * rotated into their outputs (the call then holds device buffers for the
+ * distinct angles' solutions for its duration).
  * Outputs as pmlbie_solve with (mode_hi - mode_lo) modes:
  * [mode - mode_lo][node][rhs].  Synchronises the stream at the end of every
  * chunk.  Errors as pmlbie_solve; ENOMEM if one mode does not fit the limit. */

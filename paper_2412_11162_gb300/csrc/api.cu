@@ -538,6 +538,65 @@ int pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* o, void* dev_
     int rc = ensure_device(prob);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    // Waves that share a polar angle differ only by their azimuth, and mode n
+    // of the solution rotates by e^{-i n azimuth} (Sec. 3.3 modes, plane-wave
+    // data): solve the distinct polar angles at azimuth 0, then rotate.
+    std::vector<double> pu;
+    std::vector<int> idx(n_rhs);
+    for (int r = 0; r < n_rhs; ++r) {
+        int k = 0;
+        while (k < (int)pu.size() && pu[k] != o->polar[r]) ++k;
+        if (k == (int)pu.size()) pu.push_back(o->polar[r]);
+        idx[r] = k;
+    }
+    if ((int)pu.size() < n_rhs) {
+        const int nu = (int)pu.size(), nmo = hi - lo, N = prob->P.N;
+        pmlbie_solve_opts o2 = *o;
+        o2.n_rhs = nu;
+        o2.polar = pu.data();
+        o2.azimuth = nullptr;
+        void* outs[4] = {dev_u1, dev_phi1, dev_u2, dev_phi2};
+        void* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
+        int* d_idx = nullptr;
+        double* d_az = nullptr;
+        struct Free {
+            void** t;
+            int** i;
+            double** a;
+            ~Free() {
+                for (int k = 0; k < 4; ++k)
+                    if (t[k]) cudaFree(t[k]);
+                if (*i) cudaFree(*i);
+                if (*a) cudaFree(*a);
+            }
+        } fr{tmp, &d_idx, &d_az};
+        const size_t tb = sizeof(double2) * (size_t)nmo * N * nu;
+        for (int k = 0; k < 4; ++k)
+            if (outs[k] && cudaMalloc(&tmp[k], tb) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(PMLBIE_ENOMEM, "allocation of the distinct-wave outputs failed");
+            }
+        if (cudaMalloc(&d_idx, sizeof(int) * n_rhs) != cudaSuccess ||
+            cudaMalloc(&d_az, sizeof(double) * n_rhs) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PMLBIE_ENOMEM, "allocation of the wave tables failed");
+        }
+        std::vector<double> az(n_rhs, 0.0);
+        if (o->azimuth) az.assign(o->azimuth, o->azimuth + n_rhs);
+        PMLBIE_CUDA_TRY(cudaMemcpyAsync(d_idx, idx.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s));
+        PMLBIE_CUDA_TRY(cudaMemcpyAsync(d_az, az.data(), sizeof(double) * n_rhs, cudaMemcpyHostToDevice, s));
+        rc = pmlbie_solve_ex(prob, &o2, tmp[0], tmp[1], tmp[2], tmp[3], stream, rep);
+        if (rc && rc != PMLBIE_ENOCONVERGE) return rc;
+        const int rc_solve = rc;
+        std::string msg = rc ? error_text() : "";
+        for (int k = 0; k < 4; ++k)
+            if (outs[k])
+                PMLBIE_CUDA_TRY(launch_expand_waves(N, nmo, lo, nu, n_rhs, d_idx, d_az, (const double2*)tmp[k],
+                                                    (double2*)outs[k], s));
+        PMLBIE_CUDA_TRY(cudaStreamSynchronize(s));
+        if (rep && rep->struct_size >= sizeof(pmlbie_report)) rep->launches += 4;
+        return rc_solve ? fail(rc_solve, msg) : PMLBIE_OK;
+    }
     // modes per chunk: the caller's cap, then the workspace limit (default: 90 %
     // of the free device memory plus the workspace the problem already holds)
     int chunk = hi - lo;

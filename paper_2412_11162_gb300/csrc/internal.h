@@ -155,6 +155,10 @@ cudaError_t allow_max_smem(K kernel) {
 cudaError_t launch_rhs(const pmlbie_problem* prob, int n_rhs, int mode_lo, int mode_hi, const double* rhs_par_dev,
                        const double* nu_r, const double* nu_z, const double* speed, double2* b1, double2* b2,
                        cudaStream_t s);
+// Plane waves that share a polar angle: out[t][l][r] = e^{-i (mode_lo + t) az[r]}
+// src[t][l][idx[r]] (src solved at azimuth 0 for the n_src distinct angles)
+cudaError_t launch_expand_waves(int N, int nmodes, int mode_lo, int n_src, int n_rhs, const int* idx,
+                                const double* az, const double2* src, double2* out, cudaStream_t s);
 // nm: modes in the chunk (A, b1, b2, B, X hold nm modes)
 cudaError_t launch_block_rhs(const pmlbie_problem* prob, int n_rhs, int nm, const double2* A,
                              const double2* b1, const double2* b2, double2* B, cudaStream_t s);

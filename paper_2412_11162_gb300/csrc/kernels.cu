@@ -1125,4 +1125,30 @@ cudaError_t launch_outputs(const pmlbie_problem* prob, int n_rhs, int nm, const 
     return cudaGetLastError();
 }
 
+namespace {
+// out[t][l][r] = e^{-i (mode_lo + t) az[r]} src[t][l][idx[r]]
+__global__ void expand_waves_kernel(int N, int nmodes, int mode_lo, int n_src, int n_rhs, const int* idx,
+                                    const double* az, const double2* src, double2* out) {
+    const size_t tot = (size_t)nmodes * N * n_rhs;
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= tot) return;
+    const int r = (int)(k % n_rhs);
+    const size_t tl = k / n_rhs;                  // t * N + l
+    const int t = (int)(tl / N);
+    double sr, cr;
+    sincos((double)(mode_lo + t) * az[r], &sr, &cr);
+    const double2 v = src[tl * n_src + idx[r]];
+    out[k] = c2(v.x * cr + v.y * sr, v.y * cr - v.x * sr);
+}
+}  // namespace
+
+cudaError_t launch_expand_waves(int N, int nmodes, int mode_lo, int n_src, int n_rhs, const int* idx,
+                                const double* az, const double2* src, double2* out, cudaStream_t s) {
+    const size_t tot = (size_t)nmodes * N * n_rhs;
+    expand_waves_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(N, nmodes, mode_lo, n_src, n_rhs, idx, az,
+                                                                       src, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace pmlbie

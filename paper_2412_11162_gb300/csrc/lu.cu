@@ -347,7 +347,7 @@ __global__ void lu_solve_kernel(int n, int nrhs, int R, const TF* LU, const int*
 #pragma unroll
             for (int q = 0; q < RM; ++q)
                 if (q < nr) acc[q] = sx[i * R + q];
-#pragma unroll 4
+#pragma unroll 8
             for (int c = 0; c < jb; ++c) {
                 const T l = widen<T>(a[(size_t)(j0 + c) * n + i]);
 #pragma unroll
@@ -384,7 +384,7 @@ __global__ void lu_solve_kernel(int n, int nrhs, int R, const TF* LU, const int*
 #pragma unroll
             for (int q = 0; q < RM; ++q)
                 if (q < nr) acc[q] = sx[i * R + q];
-#pragma unroll 4
+#pragma unroll 8
             for (int c = 0; c < jb; ++c) {
                 const T u = widen<T>(a[(size_t)(j0 + c) * n + i]);
 #pragma unroll

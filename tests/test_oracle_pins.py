@@ -358,3 +358,38 @@ def test_paper_sec4_3_ntd_experiment():
         Nn = np.linalg.solve(Ka - np.diag(Da), Sa)
         errs.append(np.linalg.norm(u[:, n] - Nn @ f[:, n]) / np.linalg.norm(u[:, n]))
     assert errs[1] < 1e-2 and errs[1] < errs[0] / 2, errs
+
+
+def _exact_field_modes(x, p, omega, nmax):
+    """Modes n of G(x, p) over the observation azimuth (adaptive quadrature)."""
+    rx, zx = x
+    rp, zp = p
+    n = np.arange(nmax)
+
+    def f(th):
+        R = np.sqrt(rx * rx + rp * rp - 2 * rx * rp * np.cos(th) + (zx - zp) ** 2)
+        return np.exp(1j * omega * R) / (4 * np.pi * R) * 2 * np.cos(n * th)
+
+    return quad_vec(f, 0, np.pi, epsabs=1e-14, epsrel=1e-12)[0]
+
+
+def test_field_representation_reproduces_point_source_fields():
+    """Sec. 4.2 Eq. (fujs): with the exact boundary data of u^1 = G~_1(., p2)
+    (source below) and u^2 = G~_2(., p1) (source above), the representation
+    formula of each medium, with the 1/2 and the region signs of the oracle,
+    gives G_1(x, p2) above and G_2(x, p1) below (a wrong sign or factor is an
+    O(1) error; the remaining error is quadrature and PML truncation)."""
+    from oracle.field import field_modes
+    errs = []
+    for N in (144, 240):
+        P = Params(k1=np.pi, k2=1.5 * np.pi, N=N, M=128, S=12.0, T=1.0)
+        G = Geometry(P)
+        u1, f1 = _exact_point_source_modes(G.nodes, (0.5, -1.3), P.k1, P.M // 2)
+        u2, f2 = _exact_point_source_modes(G.nodes, (0.3, 0.5), P.k2, P.M // 2)
+        out = field_modes(P, np.array([0.7, 1.1]), np.array([0.8, -0.9]), np.array([0, 1]), u1.T, f1.T, u2.T, f2.T,
+                          G=G)
+        ea = _exact_field_modes((0.7, 0.8), (0.5, -1.3), P.k1, 6)
+        eb = _exact_field_modes((1.1, -0.9), (0.3, 0.5), P.k2, 6)
+        errs.append(max(np.abs(out[:6, 0] - ea).max() / np.abs(ea).max(),
+                        np.abs(out[:6, 1] - eb).max() / np.abs(eb).max()))
+    assert errs[1] < 1e-8 and errs[1] < errs[0], errs

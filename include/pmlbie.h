@@ -241,6 +241,27 @@ int  pmlbie_solve_batch(pmlbie_problem* const* probs, int n_probs, const pmlbie_
                         void* const* dev_u1, void* const* dev_phi1, void* const* dev_u2, void* const* dev_phi2,
                         int n_streams, int release_workspace, void* stream, pmlbie_report* reps);
 
+/* Scattered field at observation points (Sec. 4.2, Eq. (fujs)): the modal
+ * representation formula of each medium with the solved densities,
+ *   upper medium:  u^{s,1}_n(x) =  1/2 sum_m h [W_phi S^a_n(x, r_m) phi1_m - W_u K^a_n(x, r_m) u1_m]
+ *   lower medium:  u^{s,2}_n(x) = -1/2 sum_m h [W_phi S^b_n(x, r_m) phi2_m + W_u K^b_n(x, r_m) u2_m]
+ * (W_u = 2 rho |r'|, W_phi = 2 rho, K^b with the normal -nu; the modal kernels
+ * by the M-point rule in psi).  Points: host arrays rho[p], z[p] with
+ * 0 <= rho < a1 (physical region) and region[p] = 0 (upper, omega_1) or 1
+ * (lower, omega_2); they must lie well off the curve (several node spacings:
+ * no near-field correction is applied).  Densities: device buffers as written
+ * by pmlbie_solve_ex for modes [mode_lo, mode_hi) and n_rhs waves,
+ * [mode - mode_lo][node][rhs] (those of a medium without points may be NULL);
+ * mode_lo = mode_hi = 0 means all M/2 modes.  Output: dev_out
+ * [mode - mode_lo][point][rhs], complex128, modes u^s_n(x) with the same
+ * normalisation as the densities (u^s(rho, theta, z) = (1/2pi) sum_n
+ * e^{i n theta} u^s_n over n = -(M/2-1) .. M/2-1).  Allocates its scratch
+ * (2 x points x N x modes complex) and synchronises the stream.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int  pmlbie_field(pmlbie_problem* prob, int n_pts, const double* rho, const double* z, const int* region,
+                  int mode_lo, int mode_hi, int n_rhs, const void* dev_u1, const void* dev_phi1,
+                  const void* dev_u2, const void* dev_phi2, void* dev_out, void* stream);
+
 /* The same solve with HOST output buffers: the call copies the results to the
  * host (synchronising the stream).  Host buffers have the layout above. */
 int  pmlbie_solve_host(pmlbie_problem* prob, int precision, int n_rhs, const double* polar,

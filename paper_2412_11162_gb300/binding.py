@@ -55,7 +55,7 @@ class pmlbie_solve_opts(ctypes.Structure):
 EXPORTS = ["pmlbie_create", "pmlbie_destroy", "pmlbie_last_error", "pmlbie_nodes", "pmlbie_diagonal",
            "pmlbie_near_count", "pmlbie_alpert_rule", "pmlbie_workspace_bytes", "pmlbie_modal_kernels",
            "pmlbie_modal_kernels_noalloc",
-           "pmlbie_solve", "pmlbie_solve_ex", "pmlbie_solve_batch", "pmlbie_solve_host"]
+           "pmlbie_solve", "pmlbie_solve_ex", "pmlbie_solve_batch", "pmlbie_field", "pmlbie_solve_host"]
 
 
 def _load():
@@ -88,9 +88,11 @@ def _load():
                                        ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                        ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, vp,
                                        ctypes.POINTER(pmlbie_report)]
+    lib.pmlbie_field.argtypes = [vp, ctypes.c_int, dp, dp, ip, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp,
+                                 vp, vp, vp]
     for f in ("pmlbie_nodes", "pmlbie_diagonal", "pmlbie_near_count", "pmlbie_alpert_rule",
               "pmlbie_modal_kernels", "pmlbie_modal_kernels_noalloc", "pmlbie_solve", "pmlbie_solve_ex",
-              "pmlbie_solve_batch", "pmlbie_solve_host"):
+              "pmlbie_solve_batch", "pmlbie_field", "pmlbie_solve_host"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -266,6 +268,18 @@ def pmlbie_solve_batch(handles, opts, u1=None, phi1=None, u2=None, phi2=None, n_
     check(lib.pmlbie_solve_batch(H, n, O, arr(u1), arr(phi1), arr(u2), arr(phi2), n_streams,
                                  1 if release_workspace else 0, _stream(stream), reps), "pmlbie_solve_batch")
     return list(reps)
+
+
+def pmlbie_field(h, rho, z, region, n_rhs, u1, phi1, u2, phi2, out, mode_lo=0, mode_hi=0, stream=None):
+    import numpy as np
+    r = np.ascontiguousarray(np.asarray(rho, dtype=np.float64).reshape(-1))
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.float64).reshape(-1))
+    g = np.ascontiguousarray(np.asarray(region, dtype=np.int32).reshape(-1))
+    if not (len(r) == len(zz) == len(g)):
+        raise ValueError("rho, z and region differ in length")
+    check(lib.pmlbie_field(h, len(r), _dptr(r), _dptr(zz), g.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), mode_lo,
+                           mode_hi, n_rhs, _tptr(u1), _tptr(phi1), _tptr(u2), _tptr(phi2), _tptr(out),
+                           _stream(stream)), "pmlbie_field")
 
 
 def pmlbie_solve_host(h, precision, polar, u1, phi1, u2, phi2, stream=None):

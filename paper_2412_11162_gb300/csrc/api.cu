@@ -734,6 +734,59 @@ int pmlbie_solve_batch(pmlbie_problem* const* probs, int n_probs, const pmlbie_s
     return PMLBIE_OK;
 }
 
+int pmlbie_field(pmlbie_problem* prob, int n_pts, const double* rho, const double* z, const int* region, int mode_lo,
+                 int mode_hi, int n_rhs, const void* dev_u1, const void* dev_phi1, const void* dev_u2,
+                 const void* dev_phi2, void* dev_out, void* stream) {
+    if (!prob || n_pts < 1 || !rho || !z || !region || !dev_out || n_rhs < 1)
+        return fail(PMLBIE_EINVAL, "field: bad problem, points or output");
+    const int nmodes_all = prob->P.M / 2;
+    if (mode_lo == 0 && mode_hi == 0) mode_hi = nmodes_all;
+    if (mode_lo < 0 || mode_hi > nmodes_all || mode_lo >= mode_hi) return fail(PMLBIE_EINVAL, "field: bad mode range");
+    bool up = false, down = false;
+    for (int p = 0; p < n_pts; ++p) {
+        if (!(rho[p] >= 0.0 && rho[p] < prob->P.a1) || !std::isfinite(z[p]))
+            return fail(PMLBIE_EINVAL, "field: points must have 0 <= rho < a1 (physical region)");
+        if (region[p] != 0 && region[p] != 1) return fail(PMLBIE_EINVAL, "field: region must be 0 (upper) or 1 (lower)");
+        (region[p] == 0 ? up : down) = true;
+    }
+    if ((up && (!dev_u1 || !dev_phi1)) || (down && (!dev_u2 || !dev_phi2)))
+        return fail(PMLBIE_EINVAL, "field: densities of a medium holding points are missing");
+    int rc = ensure_device(prob);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nm = (size_t)(mode_hi - mode_lo), N = prob->P.N;
+    double *d_rho = nullptr, *d_z = nullptr;
+    int* d_reg = nullptr;
+    double2* coef = nullptr;
+    struct Free {
+        double** a;
+        double** b;
+        int** c;
+        double2** d;
+        ~Free() {
+            if (*a) cudaFree(*a);
+            if (*b) cudaFree(*b);
+            if (*c) cudaFree(*c);
+            if (*d) cudaFree(*d);
+        }
+    } fr{&d_rho, &d_z, &d_reg, &coef};
+    if (cudaMalloc(&d_rho, sizeof(double) * n_pts) != cudaSuccess ||
+        cudaMalloc(&d_z, sizeof(double) * n_pts) != cudaSuccess ||
+        cudaMalloc(&d_reg, sizeof(int) * n_pts) != cudaSuccess ||
+        cudaMalloc(&coef, sizeof(double2) * 2 * nm * N * n_pts) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PMLBIE_ENOMEM, "field: scratch allocation failed");
+    }
+    PMLBIE_CUDA_TRY(cudaMemcpyAsync(d_rho, rho, sizeof(double) * n_pts, cudaMemcpyHostToDevice, s));
+    PMLBIE_CUDA_TRY(cudaMemcpyAsync(d_z, z, sizeof(double) * n_pts, cudaMemcpyHostToDevice, s));
+    PMLBIE_CUDA_TRY(cudaMemcpyAsync(d_reg, region, sizeof(int) * n_pts, cudaMemcpyHostToDevice, s));
+    PMLBIE_CUDA_TRY(launch_field(prob, n_pts, d_rho, d_z, d_reg, mode_lo, mode_hi, n_rhs, (const double2*)dev_u1,
+                                 (const double2*)dev_phi1, (const double2*)dev_u2, (const double2*)dev_phi2, coef,
+                                 (double2*)dev_out, s));
+    PMLBIE_CUDA_TRY(cudaStreamSynchronize(s));
+    return PMLBIE_OK;
+}
+
 int pmlbie_solve_host(pmlbie_problem* prob, int precision, int n_rhs, const double* polar, double* u1,
                       double* phi1, double* u2, double* phi2, void* stream, pmlbie_report* rep) {
     if (!prob || n_rhs < 1) return fail(PMLBIE_EINVAL, "bad problem or n_rhs");

@@ -159,6 +159,13 @@ cudaError_t launch_rhs(const pmlbie_problem* prob, int n_rhs, int mode_lo, int m
 // src[t][l][idx[r]] (src solved at azimuth 0 for the n_src distinct angles)
 cudaError_t launch_expand_waves(int N, int nmodes, int mode_lo, int n_src, int n_rhs, const int* idx,
                                 const double* az, const double2* src, double2* out, cudaStream_t s);
+// Scattered-field modes at observation points (rho, z, region 0 upper / 1 lower,
+// device arrays): coef scratch npts x N x (mode_hi - mode_lo) x 2 complex;
+// densities and out laid out [mode - mode_lo][node or point][rhs]
+cudaError_t launch_field(const pmlbie_problem* prob, int npts, const double* prho, const double* pz,
+                         const int* preg, int mode_lo, int mode_hi, int nrhs, const double2* u1,
+                         const double2* phi1, const double2* u2, const double2* phi2, double2* coef, double2* out,
+                         cudaStream_t s);
 // nm: modes in the chunk (A, b1, b2, B, X hold nm modes)
 cudaError_t launch_block_rhs(const pmlbie_problem* prob, int n_rhs, int nm, const double2* A,
                              const double2* b1, const double2* b2, double2* B, cudaStream_t s);

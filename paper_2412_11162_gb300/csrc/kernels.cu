@@ -1126,6 +1126,133 @@ cudaError_t launch_outputs(const pmlbie_problem* prob, int n_rhs, int nm, const 
 }
 
 namespace {
+// ---------------------------------------------------------------------------
+// Scattered field at observation points (Sec. 4.2, Eq. (fujs)): per (point,
+// node) pair, S~ and K~ of the point's medium at the M/2+1 distinct angles,
+// two even-sequence DFTs, and the weighted modal coefficients
+//   upper (region a):  cS =  h W_phi S^a / 2,  cK = -h W_u K^a / 2
+//   lower (region b):  cS = -h W_phi S^b / 2,  cK = -h W_u K^b / 2   (K^b with -nu)
+// stored as coef[p][m][n][2]; then u^s_n(x_p) = sum_m cS phi_m + cK u_m with the
+// densities of the point's medium.  One warp per pair.
+// ---------------------------------------------------------------------------
+struct FieldArgs {
+    DeviceTables T;
+    int N, M, npts, mode_lo, nmodes;
+    double w1, w2, h;
+    const double* prho;   // points
+    const double* pz;
+    const int* preg;
+    double2* coef;        // [p][m][nmodes][2]
+};
+
+__global__ void field_kernel(FieldArgs a) {
+    extern __shared__ double2 smem[];
+    const int M = a.M, K = M / 2, S1 = K + 1;
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double2* tw = smem;                      // M
+    double2* hs = tw + M;                    // K
+    double2* cs = hs + K;                    // K + 1
+    double2* buf = cs + S1 + warp * (2 * S1 + 2 * K);
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const double2 t = a.T.twid[i];
+        tw[i] = t;
+        if (i < K) hs[i] = c2(0.5 + t.y, 0.5 - t.y);
+    }
+    for (int i = threadIdx.x; i <= K; i += blockDim.x) cs[i] = a.T.cos_tab[i];
+    __syncthreads();
+    const int p = blockIdx.y, m = blockIdx.x * nw + warp;
+    if (m >= a.N) return;
+    const int reg = a.preg[p];
+    const double w = reg == 0 ? a.w1 : a.w2, sg = reg == 0 ? 1.0 : -1.0;
+    const double rx = a.prho[p], zx = a.pz[p];
+    const double dr = rx - a.T.rho[m], dz = zx - a.T.z[m], dI = -a.T.I[m];   // the point is physical: I = 0
+    const double2 drt = c2(dr, dI);
+    const double2 d2 = cadd(cmul(drt, drt), c2(dz * dz, 0.0));
+    const double2 rr = cscale(a.T.rho_t[m], rx);
+    const double2 ncr = cscale(a.T.nuc_r[m], sg), ncz = cscale(a.T.nuc_z[m], sg);
+    const double2 nd0 = cadd(cmul(ncr, c2(-dr, -dI)), cscale(ncz, -dz));
+    const double2 nds = cscale(ncr, 2.0 * rx);
+    for (int j = lane; j <= K; j += 32) {
+        const double2 sc = cs[j];
+        const double2 D2 = cadd(d2, cscale(rr, 4.0 * sc.x));
+        double2 R, iR;
+        fcsqrt_rcp(D2, R, iR);
+        const double2 iR3 = cmul(iR, cmul(iR, iR));
+        const double2 ND = cadd(nd0, cscale(nds, sc.x));
+        const double2 q = cscale(R, w);
+        const double2 e = fcexpi(q);
+        buf[j] = cscale(cmul(e, iR), kInv4Pi);
+        buf[S1 + j] = cmul(cmul(cscale(cmul(ND, iR3), -kInv4Pi), e), c2(1.0 + q.y, -q.x));
+    }
+    __syncwarp();
+    double2* y = buf + 2 * S1;
+    warp_even_dft(buf, y, y + K, K, tw, hs, 1, lane);
+    warp_even_dft(buf + S1, y, y + K, K, tw, hs, 1, lane);
+    const double scale = 2.0 * kPi / M;
+    const double fs = 0.5 * sg * scale * a.h * a.T.Wphi[m], fk = -0.5 * scale * a.h * a.T.Wu[m];
+    double2* o = a.coef + ((size_t)p * a.N + m) * a.nmodes * 2;
+    for (int t = lane; t < a.nmodes; t += 32) {
+        o[2 * t] = cscale(buf[a.mode_lo + t], fs);
+        o[2 * t + 1] = cscale(buf[S1 + a.mode_lo + t], fk);
+    }
+}
+
+// out[t][p][r] = sum_m cS[p][m][t] phi[t][m][r] + cK[p][m][t] u[t][m][r]
+__global__ void field_contract_kernel(int N, int npts, int nmodes, int nrhs, const int* preg, const double2* coef,
+                                      const double2* u1, const double2* phi1, const double2* u2,
+                                      const double2* phi2, double2* out) {
+    const size_t tot = (size_t)nmodes * npts * nrhs;
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= tot) return;
+    const int t = (int)(k % nmodes);
+    const size_t pr = k / nmodes;
+    const int r = (int)(pr % nrhs), p = (int)(pr / nrhs);
+    const bool up = preg[p] == 0;
+    const double2* u = up ? u1 : u2;
+    const double2* ph = up ? phi1 : phi2;
+    double2 acc = c2(0.0, 0.0);
+    for (int m = 0; m < N; ++m) {
+        const double2* c = coef + (((size_t)p * N + m) * nmodes + t) * 2;
+        const size_t di = ((size_t)t * N + m) * nrhs + r;
+        acc = cadd(acc, cadd(cmul(c[0], ph[di]), cmul(c[1], u[di])));
+    }
+    out[((size_t)t * npts + p) * nrhs + r] = acc;
+}
+}  // namespace
+
+cudaError_t launch_field(const pmlbie_problem* prob, int npts, const double* prho, const double* pz,
+                         const int* preg, int mode_lo, int mode_hi, int nrhs, const double2* u1,
+                         const double2* phi1, const double2* u2, const double2* phi2, double2* coef, double2* out,
+                         cudaStream_t s) {
+    FieldArgs a;
+    a.T = prob->D;
+    a.N = prob->P.N;
+    a.M = prob->P.M;
+    a.npts = npts;
+    a.mode_lo = mode_lo;
+    a.nmodes = mode_hi - mode_lo;
+    a.w1 = prob->P.k1;
+    a.w2 = prob->P.k2;
+    a.h = prob->H.h;
+    a.prho = prho;
+    a.pz = pz;
+    a.preg = preg;
+    a.coef = coef;
+    const int nw = 4, K = a.M / 2;
+    const size_t smem = sizeof(double2) * ((size_t)a.M + K + (K + 1) + (size_t)nw * (2 * (K + 1) + 2 * K));
+    if (smem > 48 * 1024) {
+        cudaError_t e = allow_max_smem(field_kernel);
+        if (e != cudaSuccess) return e;
+    }
+    field_kernel<<<dim3((a.N + nw - 1) / nw, npts), 32 * nw, smem, s>>>(a);
+    const size_t tot = (size_t)a.nmodes * npts * nrhs;
+    field_contract_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a.N, npts, a.nmodes, nrhs, preg, coef, u1,
+                                                                        phi1, u2, phi2, out);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+namespace {
 // out[t][l][r] = e^{-i (mode_lo + t) az[r]} src[t][l][idx[r]]
 __global__ void expand_waves_kernel(int N, int nmodes, int mode_lo, int n_src, int n_rhs, const int* idx,
                                     const double* az, const double2* src, double2* out) {

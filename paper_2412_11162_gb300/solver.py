@@ -44,6 +44,18 @@ class Problem:
         B.pmlbie_modal_kernels(self.handle, mode_lo, mode_hi, out, stream)
         return out
 
+    def field(self, rho, z, region, densities, modes=None, stream=None):
+        """Scattered-field modes [mode][point][rhs] at points (rho, z) of the
+        upper (region 0) or lower (1) medium from solve outputs `densities`
+        (dict u1, phi1, u2, phi2 for the same mode range)."""
+        import torch
+        lo, hi = (0, self.n_modes) if modes is None else modes
+        nrhs = densities["u1"].shape[2]
+        out = torch.empty((hi - lo, len(np.atleast_1d(rho)), nrhs), dtype=torch.complex128, device="cuda")
+        B.pmlbie_field(self.handle, rho, z, region, nrhs, densities["u1"], densities["phi1"], densities["u2"],
+                       densities["phi2"], out, lo, hi, stream)
+        return out
+
     def solve(self, polar, precision=B.PMLBIE_FP64, stream=None, outputs=None, allow_noconverge=False,
               azimuth=None, modes=None, max_chunk_modes=0, workspace_limit=0):
         """Device solve; returns (dict of [mode][node][rhs] complex128 tensors, report).

@@ -261,6 +261,15 @@ def run_ours(args, rank, world):
     ms64 = f0.elapsed_time(f1) / 2 * nm / (sub[1] - sub[0])
     rel = {k: (torch.linalg.vector_norm(mixed_out[k][sub[0]:sub[1]] - sub_outs[k]) /
                torch.linalg.vector_norm(sub_outs[k])).item() for k in outs}
+    # scattered field at 32 fixed points (16 at z = +1 above, 16 at z = -1 below,
+    # rho in [0, 2]) from the mixed and the FP64 densities, same modes
+    fr = np.tile(np.linspace(0.0, 2.0, 16), 2)
+    fz = np.repeat([1.0, -1.0], 16)
+    fg = np.repeat([0, 1], 16)
+    f64 = P.field(fr, fz, fg, sub_outs, modes=sub, stream=stream)
+    f32 = P.field(fr, fz, fg, {k: v[sub[0]:sub[1]].contiguous() for k, v in mixed_out.items()}, modes=sub,
+                  stream=stream)
+    rel["field_32_points"] = (torch.linalg.vector_norm(f32 - f64) / torch.linalg.vector_norm(f64)).item()
 
     # end to end through the public API with host buffers: create (host tables,
     # first-call upload) + solve + copy of the outputs to pinned host memory

@@ -298,8 +298,9 @@ template <typename T> __device__ __forceinline__ T widen(float2 v) { return Cx<T
 template <typename T> __device__ __forceinline__ T widen(double2 v) { return Cx<T>::mk(v.x, v.y); }
 
 template <typename T, typename TF, int RM>
-__global__ void lu_solve_kernel(int n, int nrhs, int R, const TF* LU, const int* piv, T* B, const int* active) {
-    const int b = blockIdx.x, r0 = blockIdx.y * R, nr = min(R, nrhs - r0);
+__global__ void lu_solve_kernel(int n, int nrhs, int Rg, const TF* LU, const int* piv, T* B, const int* active) {
+    const int R = RM == 1 ? 1 : Rg;    // compile-time 1 in the single-wave variant
+    const int b = blockIdx.x, r0 = blockIdx.y * R, nr = RM == 1 ? 1 : min(R, nrhs - r0);
     if (active && !active[b]) return;
     extern __shared__ unsigned char smraw[];
     T* sx = reinterpret_cast<T*>(smraw);                     // n x R entries, sx[i * R + q]

@@ -393,3 +393,41 @@ def test_field_representation_reproduces_point_source_fields():
         errs.append(max(np.abs(out[:6, 0] - ea).max() / np.abs(ea).max(),
                         np.abs(out[:6, 1] - eb).max() / np.abs(eb).max()))
     assert errs[1] < 1e-8 and errs[1] < errs[0], errs
+
+
+def test_point_source_rhs_vs_quadrature():
+    """Point-source jumps (Sec. 2, spherical incidence): b1 = -G~_1(r~_m, x_s)
+    and b2 = -|r'| d_nu_c G~_1 per mode, at every node (bump, PML nodes in
+    stretched coordinates), against adaptive quadrature of the azimuthal
+    integrals of the closed-form Green's function (M large enough that the
+    M-point rule in psi is resolved at the source's distance from the bump)."""
+    from oracle.point_source import point_source_rhs
+    P = Params(k1=2 * np.pi, k2=3 * np.pi, N=64, M=64, S=12.0)
+    G = Geometry(P)
+    for src in ((0.4, 0.8), (0.0, 1.1)):
+        b1, b2 = point_source_rhs(P, G, *src)
+        u, f = _exact_point_source_modes(G.nodes, src, P.k1, P.M // 2)
+        assert np.abs(b1 + u).max() <= 1e-11 * np.abs(u).max()
+        assert np.abs(b2 + f).max() <= 1e-11 * np.abs(f).max()
+        assert np.abs(b1).max() > 1e-3          # nonzero on the flat parts too
+
+
+def test_point_source_rhs_calderon_identity_lower_medium():
+    """Equal media and a flat interface: (-b1, -b2) are the Cauchy data of
+    G_1(., x_s), a solution in the lower medium, so the lower-medium rows
+    (K^b - D^b) u + S^b phi = 0 (Sec. 4.2) vanish on them up to quadrature
+    error (checked on the physical nodes away from the axis and the PML).  A
+    wrong sign of b2 or a missing |r'| is an O(1) residual."""
+    from oracle.point_source import point_source_rhs
+    P = Params(k1=2 * np.pi, k2=2 * np.pi, N=160, M=64, bump_h=0.0, S=12.0)
+    sysm = ModalSystem(P)
+    G = sysm.G
+    _, Db = diagonal(G, sysm.Q)
+    b1, b2 = point_source_rhs(P, G, 0.4, 0.8)
+    band = (G.nodes["rho"] > 0.3) & (G.nodes["rho"] < 2.0)
+    for n in (0, 1, 5):
+        Sb, Kb = sysm.matrices("b", n)
+        r = (Kb - np.diag(Db)) @ b1[:, n] + Sb @ b2[:, n]
+        assert np.linalg.norm(r[band]) <= 1e-5 * np.linalg.norm(b1[band, n]), n
+        bad = (Kb - np.diag(Db)) @ b1[:, n] - Sb @ b2[:, n]
+        assert np.linalg.norm(bad[band]) > 0.5 * np.linalg.norm(b1[band, n])

@@ -111,6 +111,9 @@ typedef struct {
     int      mode_lo, mode_hi;    /* modes solved, [mode_lo, mode_hi) in [0, M/2); 0, 0 = all   */
     int      max_chunk_modes;     /* modes per chunk at most (0: no cap)                        */
     size_t   workspace_limit;     /* device workspace bytes at most (0: 90 % of free memory)    */
+    const double* source_rho;     /* host, n_rhs point sources instead of plane waves (with    */
+    const double* source_z;       /* polar = NULL): source r at (source_rho[r], azimuth[r],     */
+                                  /* source_z[r]) in the upper medium (NULL: plane waves)       */
 } pmlbie_solve_opts;
 
 typedef struct pmlbie_problem pmlbie_problem;   /* opaque, owned by the library */
@@ -219,6 +222,17 @@ int  pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* 
  * that share a polar angle are therefore solved once, at azimuth 0, and
  * rotated into their outputs (the call then holds device buffers for the
  * distinct angles' solutions for its duration).
+ * Point sources (Sec. 2, spherical incidence; source_rho, source_z set and
+ * polar NULL): the incident field of source r is G_1(x, x_s) with x_s =
+ * (source_rho[r], azimuth[r], source_z[r]) in the upper medium; the jumps are
+ * b^1 = -G~_1(r~, x_s), b^2 = -|r'| d_nu_c G~_1 at every node (PML nodes in
+ * stretched coordinates), their modes the M-point DFTs in psi (the far-pair
+ * rule).  u1, phi1 then hold the scattered field above and u2, phi2 the total
+ * field below.  Each source needs 0 <= rho_s < a1, z_s finite, and every node
+ * at a separation d / sqrt(rho_s rho_m) >= split_c * 2 pi / M (the far-pair
+ * criterion, so that the M-point rule resolves the data); the caller places
+ * it above the interface.  Sources that share (rho_s, z_s) are solved once
+ * and rotated, as plane waves that share a polar angle.
  * Outputs as pmlbie_solve with (mode_hi - mode_lo) modes:
  * [mode - mode_lo][node][rhs].  Synchronises the stream at the end of every
  * chunk.  Errors as pmlbie_solve; ENOMEM if one mode does not fit the limit. */

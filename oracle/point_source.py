@@ -30,17 +30,26 @@ def point_source_rhs(P: Params, G: Geometry, rho_s, z_s):
     return -S, -K * G.nodes["speed"][:, None]
 
 
-def point_source_densities(sol, rho_s, z_s, phi_s=0.0):
-    """Densities (u1, phi1, u2, phi2), each (M/2, N), of a source at
-    (rho_s, phi_s, z_s), from a Solution built with keep_matrices (its block
-    systems A_n x = B_n, Sec. 4.2, with the point-source jumps in B_n)."""
+def point_source_systems(sol, rho_s, z_s):
+    """{n: (A_n, B_n)}: the block systems of a Solution built with keep_matrices
+    (Sec. 4.2) with the jumps of a source at (rho_s, 0, z_s) in B_n, and (b1, b2)."""
     P, G = sol.P, sol.sys.G
     b1, b2 = point_source_rhs(P, G, rho_s, z_s)
-    nh, N = P.M // 2, P.N
-    out = [np.zeros((nh, N), complex) for _ in range(4)]
+    N = P.N
+    out = {}
     for n in sol.modes:
         A = sol.A[n][0]
-        B = np.concatenate([np.zeros(N, complex), A[N:, :N] @ b1[:, n] + A[N:, N:] @ b2[:, n]])
+        out[n] = (A, np.concatenate([np.zeros(N, complex), A[N:, :N] @ b1[:, n] + A[N:, N:] @ b2[:, n]]))
+    return out, (b1, b2)
+
+
+def point_source_densities(sol, rho_s, z_s, phi_s=0.0):
+    """Densities (u1, phi1, u2, phi2), each (M/2, N), of a source at
+    (rho_s, phi_s, z_s) (Sec. 4.2 block systems with the point-source jumps)."""
+    systems, (b1, b2) = point_source_systems(sol, rho_s, z_s)
+    nh, N = sol.P.M // 2, sol.P.N
+    out = [np.zeros((nh, N), complex) for _ in range(4)]
+    for n, (A, B) in systems.items():
         x = np.linalg.solve(A, B)
         rot = np.exp(-1j * n * phi_s)
         out[0][n] = rot * x[:N]

@@ -49,7 +49,8 @@ class pmlbie_solve_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("precision", ctypes.c_int), ("n_rhs", ctypes.c_int),
                 ("polar", ctypes.POINTER(ctypes.c_double)), ("azimuth", ctypes.POINTER(ctypes.c_double)),
                 ("mode_lo", ctypes.c_int), ("mode_hi", ctypes.c_int), ("max_chunk_modes", ctypes.c_int),
-                ("workspace_limit", ctypes.c_size_t)]
+                ("workspace_limit", ctypes.c_size_t), ("source_rho", ctypes.POINTER(ctypes.c_double)),
+                ("source_z", ctypes.POINTER(ctypes.c_double))]
 
 
 EXPORTS = ["pmlbie_create", "pmlbie_destroy", "pmlbie_last_error", "pmlbie_nodes", "pmlbie_diagonal",
@@ -216,39 +217,44 @@ def pmlbie_solve(h, precision, polar, u1=None, phi1=None, u2=None, phi2=None, st
 
 def pmlbie_solve_ex(h, precision, polar, azimuth=None, mode_lo=0, mode_hi=0, max_chunk_modes=0,
                     workspace_limit=0, u1=None, phi1=None, u2=None, phi2=None, stream=None,
-                    allow_noconverge=False):
-    import numpy as np
-    pol = np.ascontiguousarray(np.asarray(polar, dtype=np.float64).reshape(-1))
-    az = None if azimuth is None else np.ascontiguousarray(np.asarray(azimuth, dtype=np.float64).reshape(-1))
-    if az is not None and len(az) != len(pol):
-        raise ValueError("azimuth and polar differ in length")
-    o = pmlbie_solve_opts()
-    o.struct_size = ctypes.sizeof(pmlbie_solve_opts)
-    o.precision, o.n_rhs, o.polar = precision, len(pol), _dptr(pol)
-    o.azimuth = _dptr(az) if az is not None else None
-    o.mode_lo, o.mode_hi, o.max_chunk_modes, o.workspace_limit = mode_lo, mode_hi, max_chunk_modes, workspace_limit
+                    allow_noconverge=False, sources=None):
+    o, keep = make_opts(precision, polar, azimuth, mode_lo, mode_hi, max_chunk_modes, workspace_limit, sources)
     rep = pmlbie_report()
     rep.struct_size = ctypes.sizeof(pmlbie_report)
     rc = lib.pmlbie_solve_ex(h, ctypes.byref(o), _tptr(u1), _tptr(phi1), _tptr(u2), _tptr(phi2), _stream(stream),
                              ctypes.byref(rep))
+    del keep
     if not (allow_noconverge and rc == PMLBIE_ENOCONVERGE):
         check(rc, "pmlbie_solve_ex")
     return rep
 
 
-def make_opts(precision, polar, azimuth=None, mode_lo=0, mode_hi=0, max_chunk_modes=0, workspace_limit=0):
-    """pmlbie_solve_opts and the arrays it points to (keep both alive)."""
+def make_opts(precision, polar, azimuth=None, mode_lo=0, mode_hi=0, max_chunk_modes=0, workspace_limit=0,
+              sources=None):
+    """pmlbie_solve_opts and the arrays it points to (keep both alive).  polar:
+    plane-wave polar angles; or polar None and sources: (n, 2) point sources
+    (rho_s, z_s) in the upper medium."""
     import numpy as np
-    pol = np.ascontiguousarray(np.asarray(polar, dtype=np.float64).reshape(-1))
-    az = None if azimuth is None else np.ascontiguousarray(np.asarray(azimuth, dtype=np.float64).reshape(-1))
-    if az is not None and len(az) != len(pol):
-        raise ValueError("azimuth and polar differ in length")
     o = pmlbie_solve_opts()
     o.struct_size = ctypes.sizeof(pmlbie_solve_opts)
-    o.precision, o.n_rhs, o.polar = precision, len(pol), _dptr(pol)
+    if sources is not None:
+        if polar is not None:
+            raise ValueError("give either polar angles or point sources")
+        src = np.asarray(sources, dtype=np.float64).reshape(-1, 2)
+        rs, zs = np.ascontiguousarray(src[:, 0]), np.ascontiguousarray(src[:, 1])
+        o.source_rho, o.source_z, o.polar = _dptr(rs), _dptr(zs), None
+        n, keep = len(rs), [rs, zs]
+    else:
+        pol = np.ascontiguousarray(np.asarray(polar, dtype=np.float64).reshape(-1))
+        o.polar = _dptr(pol)
+        n, keep = len(pol), [pol]
+    az = None if azimuth is None else np.ascontiguousarray(np.asarray(azimuth, dtype=np.float64).reshape(-1))
+    if az is not None and len(az) != n:
+        raise ValueError("one azimuth per wave or source")
+    o.precision, o.n_rhs = precision, n
     o.azimuth = _dptr(az) if az is not None else None
     o.mode_lo, o.mode_hi, o.max_chunk_modes, o.workspace_limit = mode_lo, mode_hi, max_chunk_modes, workspace_limit
-    return o, (pol, az)
+    return o, (keep, az)
 
 
 def pmlbie_solve_batch(handles, opts, u1=None, phi1=None, u2=None, phi2=None, n_streams=2,

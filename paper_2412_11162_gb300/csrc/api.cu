@@ -357,7 +357,7 @@ struct SolveStats {
 
 // One chunk of modes [lo, hi): system, RHS, LU, solve (+ refinement), outputs
 // into u1.. (already offset to the chunk).  Synchronises the stream at the end.
-static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, int lo, int hi, Workspace& w,
+static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool point, int lo, int hi, Workspace& w,
                        double2* u1, double2* phi1, double2* u2, double2* phi2, cudaStream_t s, SolveStats& st) {
     const int N = prob->P.N, nm = hi - lo, n2 = 2 * N;
     cudaEvent_t ev[4], sev[5];
@@ -375,7 +375,10 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, int lo, i
     int rc;
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[0], s));
     if ((rc = build_system(prob, w, lo, hi, s, sev))) return rc;
-    PMLBIE_CUDA_TRY(launch_rhs(prob, n_rhs, lo, hi, w.rpar, ex->nu_r, ex->nu_z, ex->speed, w.b1, w.b2, s));
+    if (point)
+        PMLBIE_CUDA_TRY(launch_point_rhs(prob, n_rhs, lo, hi, w.rpar, ex->speed, w.b1, w.b2, s));
+    else
+        PMLBIE_CUDA_TRY(launch_rhs(prob, n_rhs, lo, hi, w.rpar, ex->nu_r, ex->nu_z, ex->speed, w.b1, w.b2, s));
     PMLBIE_CUDA_TRY(launch_block_rhs(prob, n_rhs, nm, w.A, w.b1, w.b2, w.B, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[1], s));
     PMLBIE_CUDA_TRY(cudaMemsetAsync(w.info, 0, sizeof(int) * nm, s));
@@ -525,11 +528,30 @@ int pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* o, void* dev_
                     void* dev_u2, void* dev_phi2, void* stream, pmlbie_report* rep) {
     if (!prob || !o || o->struct_size < sizeof(pmlbie_solve_opts)) return fail(PMLBIE_EINVAL, "bad problem or options");
     const int precision = o->precision, n_rhs = o->n_rhs, nmodes_all = prob->P.M / 2;
-    if (!o->polar || n_rhs < 1 || n_rhs > 4096) return fail(PMLBIE_EINVAL, "bad polar or n_rhs");
+    const bool point = o->source_rho || o->source_z;
+    if (n_rhs < 1 || n_rhs > 4096) return fail(PMLBIE_EINVAL, "n_rhs must be in [1, 4096]");
+    if (point ? (o->polar || !o->source_rho || !o->source_z) : !o->polar)
+        return fail(PMLBIE_EINVAL, "give either polar angles or source_rho and source_z");
     if (precision != PMLBIE_FP64 && precision != PMLBIE_MIXED) return fail(PMLBIE_EINVAL, "bad precision");
     for (int r = 0; r < n_rhs; ++r) {
-        if (!(o->polar[r] >= 0.0 && o->polar[r] < 0.5 * kPi)) return fail(PMLBIE_EINVAL, "polar angle must be in [0, pi/2)");
+        if (!point && !(o->polar[r] >= 0.0 && o->polar[r] < 0.5 * kPi))
+            return fail(PMLBIE_EINVAL, "polar angle must be in [0, pi/2)");
         if (o->azimuth && !std::isfinite(o->azimuth[r])) return fail(PMLBIE_EINVAL, "azimuth must be finite");
+    }
+    if (point) {
+        // sources in the physical region, far-pair separated from every node
+        const double eta = prob->P.split_c * 2.0 * kPi / prob->P.M;
+        for (int r = 0; r < n_rhs; ++r) {
+            const double rs = o->source_rho[r], zs = o->source_z[r];
+            if (!(rs >= 0.0 && rs < prob->P.a1) || !std::isfinite(zs))
+                return fail(PMLBIE_EINVAL, "source must have 0 <= rho < a1 and finite z");
+            for (size_t m = 0; m < prob->H.rho.size(); ++m) {
+                const double dr = rs - prob->H.rho[m], dz = zs - prob->H.z[m];
+                if (dr * dr + dz * dz < eta * eta * rs * prob->H.rho[m])
+                    return fail(PMLBIE_EINVAL, "source " + std::to_string(r) +
+                                                   " is too close to the interface for the M-point rule");
+            }
+        }
     }
     int lo = o->mode_lo, hi = o->mode_hi;
     if (lo == 0 && hi == 0) hi = nmodes_all;
@@ -541,19 +563,26 @@ int pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* o, void* dev_
     // Waves that share a polar angle differ only by their azimuth, and mode n
     // of the solution rotates by e^{-i n azimuth} (Sec. 3.3 modes, plane-wave
     // data): solve the distinct polar angles at azimuth 0, then rotate.
-    std::vector<double> pu;
+    // Point sources that share (rho_s, z_s) likewise.
+    std::vector<double> pu, pz;
     std::vector<int> idx(n_rhs);
     for (int r = 0; r < n_rhs; ++r) {
+        const double k0 = point ? o->source_rho[r] : o->polar[r], k1 = point ? o->source_z[r] : 0.0;
         int k = 0;
-        while (k < (int)pu.size() && pu[k] != o->polar[r]) ++k;
-        if (k == (int)pu.size()) pu.push_back(o->polar[r]);
+        while (k < (int)pu.size() && !(pu[k] == k0 && pz[k] == k1)) ++k;
+        if (k == (int)pu.size()) pu.push_back(k0), pz.push_back(k1);
         idx[r] = k;
     }
     if ((int)pu.size() < n_rhs) {
         const int nu = (int)pu.size(), nmo = hi - lo, N = prob->P.N;
         pmlbie_solve_opts o2 = *o;
         o2.n_rhs = nu;
-        o2.polar = pu.data();
+        if (point) {
+            o2.source_rho = pu.data();
+            o2.source_z = pz.data();
+        } else {
+            o2.polar = pu.data();
+        }
         o2.azimuth = nullptr;
         void* outs[4] = {dev_u1, dev_phi1, dev_u2, dev_phi2};
         void* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -615,7 +644,12 @@ int pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* o, void* dev_
     g_launches = 0;
     std::vector<double> rpar((size_t)kRhsPar * n_rhs, 0.0);
     for (int r = 0; r < n_rhs; ++r) {
-        fresnel(prob->P.k1, prob->P.k2, o->polar[r], &rpar[(size_t)kRhsPar * r]);
+        if (point) {
+            rpar[(size_t)kRhsPar * r] = o->source_rho[r];
+            rpar[(size_t)kRhsPar * r + 1] = o->source_z[r];
+        } else {
+            fresnel(prob->P.k1, prob->P.k2, o->polar[r], &rpar[(size_t)kRhsPar * r]);
+        }
         rpar[(size_t)kRhsPar * r + 6] = o->azimuth ? o->azimuth[r] : 0.0;
     }
     PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.rpar, rpar.data(), sizeof(double) * rpar.size(), cudaMemcpyHostToDevice, s));
@@ -625,7 +659,7 @@ int pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* o, void* dev_
     int chunks = 0;
     for (int c0 = lo; c0 < hi; c0 += chunk) {
         const int c1 = std::min(hi, c0 + chunk);
-        rc = solve_chunk(prob, precision, n_rhs, c0, c1, w, at(dev_u1, c0), at(dev_phi1, c0), at(dev_u2, c0),
+        rc = solve_chunk(prob, precision, n_rhs, point, c0, c1, w, at(dev_u1, c0), at(dev_phi1, c0), at(dev_u2, c0),
                          at(dev_phi2, c0), s, st);
         ++chunks;
         if (rc) return rc;

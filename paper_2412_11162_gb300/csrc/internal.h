@@ -155,8 +155,14 @@ cudaError_t allow_max_smem(K kernel) {
 cudaError_t launch_rhs(const pmlbie_problem* prob, int n_rhs, int mode_lo, int mode_hi, const double* rhs_par_dev,
                        const double* nu_r, const double* nu_z, const double* speed, double2* b1, double2* b2,
                        cudaStream_t s);
-// Plane waves that share a polar angle: out[t][l][r] = e^{-i (mode_lo + t) az[r]}
-// src[t][l][idx[r]] (src solved at azimuth 0 for the n_src distinct angles)
+// Point-source jumps (Sec. 2): per rhs, rhs_par holds rho_s, z_s at [0], [1] and
+// the source azimuth at [6]; speed per node; b1, b2 for modes [mode_lo, mode_hi)
+cudaError_t launch_point_rhs(const pmlbie_problem* prob, int n_rhs, int mode_lo, int mode_hi,
+                             const double* rhs_par_dev, const double* speed, double2* b1, double2* b2,
+                             cudaStream_t s);
+// Waves (or sources) that share all but their azimuth: out[t][l][r] =
+// e^{-i (mode_lo + t) az[r]} src[t][l][idx[r]] (src solved at azimuth 0 for the
+// n_src distinct ones)
 cudaError_t launch_expand_waves(int N, int nmodes, int mode_lo, int n_src, int n_rhs, const int* idx,
                                 const double* az, const double2* src, double2* out, cudaStream_t s);
 // Scattered-field modes at observation points (rho, z, region 0 upper / 1 lower,

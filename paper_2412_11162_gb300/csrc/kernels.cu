@@ -1145,31 +1145,18 @@ struct FieldArgs {
     double2* coef;        // [p][m][nmodes][2]
 };
 
-__global__ void field_kernel(FieldArgs a) {
-    extern __shared__ double2 smem[];
-    const int M = a.M, K = M / 2, S1 = K + 1;
-    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double2* tw = smem;                      // M
-    double2* hs = tw + M;                    // K
-    double2* cs = hs + K;                    // K + 1
-    double2* buf = cs + S1 + warp * (2 * S1 + 2 * K);
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        const double2 t = a.T.twid[i];
-        tw[i] = t;
-        if (i < K) hs[i] = c2(0.5 + t.y, 0.5 - t.y);
-    }
-    for (int i = threadIdx.x; i <= K; i += blockDim.x) cs[i] = a.T.cos_tab[i];
-    __syncthreads();
-    const int p = blockIdx.y, m = blockIdx.x * nw + warp;
-    if (m >= a.N) return;
-    const int reg = a.preg[p];
-    const double w = reg == 0 ? a.w1 : a.w2, sg = reg == 0 ? 1.0 : -1.0;
-    const double rx = a.prho[p], zx = a.pz[p];
-    const double dr = rx - a.T.rho[m], dz = zx - a.T.z[m], dI = -a.T.I[m];   // the point is physical: I = 0
+// S~ and K~ of one (physical point x = (rx, 0, zx), node m) pair at the M/2+1
+// distinct angles, then their modes by two even-sequence DFTs: buf[0..K] holds
+// M/(2 pi) S^_n and buf[S1..S1+K] M/(2 pi) K^_n, n = 0..K, with the double-layer
+// kernel along sg times the node's conormal.  One warp; buf holds 4 K + 2 doubles2.
+__device__ void point_node_modes(const DeviceTables& T, int M, double w, double sg, double rx, double zx, int m,
+                                 const double2* cs, const double2* tw, const double2* hs, double2* buf, int lane) {
+    const int K = M / 2, S1 = K + 1;
+    const double dr = rx - T.rho[m], dz = zx - T.z[m], dI = -T.I[m];   // the point is physical: I = 0
     const double2 drt = c2(dr, dI);
     const double2 d2 = cadd(cmul(drt, drt), c2(dz * dz, 0.0));
-    const double2 rr = cscale(a.T.rho_t[m], rx);
-    const double2 ncr = cscale(a.T.nuc_r[m], sg), ncz = cscale(a.T.nuc_z[m], sg);
+    const double2 rr = cscale(T.rho_t[m], rx);
+    const double2 ncr = cscale(T.nuc_r[m], sg), ncz = cscale(T.nuc_z[m], sg);
     const double2 nd0 = cadd(cmul(ncr, c2(-dr, -dI)), cscale(ncz, -dz));
     const double2 nds = cscale(ncr, 2.0 * rx);
     for (int j = lane; j <= K; j += 32) {
@@ -1188,12 +1175,71 @@ __global__ void field_kernel(FieldArgs a) {
     double2* y = buf + 2 * S1;
     warp_even_dft(buf, y, y + K, K, tw, hs, 1, lane);
     warp_even_dft(buf + S1, y, y + K, K, tw, hs, 1, lane);
+}
+
+// Shared tables of the point kernels: twiddles (M), half-sum weights (K), cos (K + 1).
+__device__ void point_tables(const DeviceTables& T, int M, double2* tw, double2* hs, double2* cs) {
+    const int K = M / 2;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const double2 t = T.twid[i];
+        tw[i] = t;
+        if (i < K) hs[i] = c2(0.5 + t.y, 0.5 - t.y);
+    }
+    for (int i = threadIdx.x; i <= K; i += blockDim.x) cs[i] = T.cos_tab[i];
+    __syncthreads();
+}
+
+__global__ void field_kernel(FieldArgs a) {
+    extern __shared__ double2 smem[];
+    const int M = a.M, K = M / 2, S1 = K + 1;
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double2* tw = smem;                      // M
+    double2* hs = tw + M;                    // K
+    double2* cs = hs + K;                    // K + 1
+    double2* buf = cs + S1 + warp * (2 * S1 + 2 * K);
+    point_tables(a.T, M, tw, hs, cs);
+    const int p = blockIdx.y, m = blockIdx.x * nw + warp;
+    if (m >= a.N) return;
+    const int reg = a.preg[p];
+    const double sg = reg == 0 ? 1.0 : -1.0;
+    point_node_modes(a.T, M, reg == 0 ? a.w1 : a.w2, sg, a.prho[p], a.pz[p], m, cs, tw, hs, buf, lane);
     const double scale = 2.0 * kPi / M;
     const double fs = 0.5 * sg * scale * a.h * a.T.Wphi[m], fk = -0.5 * scale * a.h * a.T.Wu[m];
     double2* o = a.coef + ((size_t)p * a.N + m) * a.nmodes * 2;
     for (int t = lane; t < a.nmodes; t += 32) {
         o[2 * t] = cscale(buf[a.mode_lo + t], fs);
         o[2 * t + 1] = cscale(buf[S1 + a.mode_lo + t], fk);
+    }
+}
+
+// Point-source jumps (Sec. 2, spherical incidence): for source r at
+// (rho_s, phi_s, z_s) = (rpar[0], rpar[6], rpar[1]) in the upper medium,
+//   b1_n(m) = -e^{-i n phi_s} S^a_n(x_s, r_m),  b2_n(m) = -e^{-i n phi_s} |r'_m| K^a_n(x_s, r_m)
+// (the modes of -G~_1(r~_m, x_s) and -|r'| d_nu_c G~_1 over the node azimuth),
+// laid out [mode - mode_lo][node][rhs].  One warp per (node, source).
+__global__ void point_rhs_kernel(DeviceTables T, int N, int M, int nrhs, int mode_lo, int nmodes, double w1,
+                                 const double* rpar, const double* speed, double2* b1, double2* b2) {
+    extern __shared__ double2 smem[];
+    const int K = M / 2, S1 = K + 1;
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double2* tw = smem;
+    double2* hs = tw + M;
+    double2* cs = hs + K;
+    double2* buf = cs + S1 + warp * (2 * S1 + 2 * K);
+    point_tables(T, M, tw, hs, cs);
+    const int r = blockIdx.y, m = blockIdx.x * nw + warp;
+    if (m >= N) return;
+    const double* pr = rpar + (size_t)kRhsPar * r;
+    point_node_modes(T, M, w1, 1.0, pr[0], pr[1], m, cs, tw, hs, buf, lane);
+    const double scale = 2.0 * kPi / M, az = pr[6], sp = speed[m];
+    for (int t = lane; t < nmodes; t += 32) {
+        const int n = mode_lo + t;
+        double sr, cr;
+        sincos(n * az, &sr, &cr);
+        const double2 rot = c2(-scale * cr, scale * sr);      // -(2 pi/M) e^{-i n phi_s}
+        const size_t o = ((size_t)t * N + m) * nrhs + r;
+        b1[o] = cmul(buf[n], rot);
+        b2[o] = cscale(cmul(buf[S1 + n], rot), sp);
     }
 }
 
@@ -1249,6 +1295,22 @@ cudaError_t launch_field(const pmlbie_problem* prob, int npts, const double* prh
     field_contract_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a.N, npts, a.nmodes, nrhs, preg, coef, u1,
                                                                         phi1, u2, phi2, out);
     count_launch(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_point_rhs(const pmlbie_problem* prob, int n_rhs, int mode_lo, int mode_hi,
+                             const double* rhs_par_dev, const double* speed, double2* b1, double2* b2,
+                             cudaStream_t s) {
+    const int N = prob->P.N, M = prob->P.M, K = M / 2, nw = 4;
+    const size_t smem = sizeof(double2) * ((size_t)M + K + (K + 1) + (size_t)nw * (2 * (K + 1) + 2 * K));
+    if (smem > 48 * 1024) {
+        cudaError_t e = allow_max_smem(point_rhs_kernel);
+        if (e != cudaSuccess) return e;
+    }
+    point_rhs_kernel<<<dim3((N + nw - 1) / nw, n_rhs), 32 * nw, smem, s>>>(prob->D, N, M, n_rhs, mode_lo,
+                                                                           mode_hi - mode_lo, prob->P.k1,
+                                                                           rhs_par_dev, speed, b1, b2);
+    count_launch();
     return cudaGetLastError();
 }
 

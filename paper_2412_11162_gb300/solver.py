@@ -56,26 +56,31 @@ class Problem:
                        densities["phi2"], out, lo, hi, stream)
         return out
 
-    def solve(self, polar, precision=B.PMLBIE_FP64, stream=None, outputs=None, allow_noconverge=False,
-              azimuth=None, modes=None, max_chunk_modes=0, workspace_limit=0):
+    def solve(self, polar=None, precision=B.PMLBIE_FP64, stream=None, outputs=None, allow_noconverge=False,
+              azimuth=None, modes=None, max_chunk_modes=0, workspace_limit=0, sources=None):
         """Device solve; returns (dict of [mode][node][rhs] complex128 tensors, report).
-        modes = (lo, hi) solves modes lo..hi-1 only; azimuth: incidence azimuths
-        (one per polar angle); max_chunk_modes / workspace_limit bound the modes
-        factored at once."""
+        polar: plane-wave polar angles; or sources = [(rho_s, z_s), ...] point
+        sources in the upper medium (polar None).  modes = (lo, hi) solves modes
+        lo..hi-1 only; azimuth: one incidence (or source) azimuth per wave;
+        max_chunk_modes / workspace_limit bound the modes factored at once."""
         import torch
-        pol = np.atleast_1d(np.asarray(polar, dtype=np.float64))
+        if (polar is None) == (sources is None):
+            raise ValueError("give either polar angles or point sources")
+        n_rhs = len(np.atleast_1d(np.asarray(polar, dtype=np.float64))) if sources is None else \
+            len(np.asarray(sources, dtype=np.float64).reshape(-1, 2))
         lo, hi = (0, self.n_modes) if modes is None else modes
         if outputs is None:
-            shape = (max(hi - lo, 0), self.N, len(pol))   # the library rejects empty or bad ranges
+            shape = (max(hi - lo, 0), self.N, n_rhs)   # the library rejects empty or bad ranges
             outputs = {k: torch.empty(shape, dtype=torch.complex128, device="cuda")
                        for k in ("u1", "phi1", "u2", "phi2")}
-        if azimuth is None and modes is None and max_chunk_modes == 0 and workspace_limit == 0:
-            rep = B.pmlbie_solve(self.handle, precision, pol, outputs["u1"], outputs["phi1"], outputs["u2"],
-                                 outputs["phi2"], stream, allow_noconverge=allow_noconverge)
+        if sources is None and azimuth is None and modes is None and max_chunk_modes == 0 and workspace_limit == 0:
+            rep = B.pmlbie_solve(self.handle, precision, np.atleast_1d(np.asarray(polar, dtype=np.float64)),
+                                 outputs["u1"], outputs["phi1"], outputs["u2"], outputs["phi2"], stream,
+                                 allow_noconverge=allow_noconverge)
         else:
-            rep = B.pmlbie_solve_ex(self.handle, precision, pol, azimuth, lo, hi, max_chunk_modes,
+            rep = B.pmlbie_solve_ex(self.handle, precision, polar, azimuth, lo, hi, max_chunk_modes,
                                     workspace_limit, outputs["u1"], outputs["phi1"], outputs["u2"],
-                                    outputs["phi2"], stream, allow_noconverge=allow_noconverge)
+                                    outputs["phi2"], stream, allow_noconverge=allow_noconverge, sources=sources)
         return outputs, rep
 
 

@@ -1,0 +1,96 @@
+"""Point-source incidence (Sec. 2, spherical waves) through pmlbie_solve_ex:
+the GPU jumps and densities against the oracle's (oracle/point_source.py,
+pinned by quadrature and the lower-medium identity) on the N = 128, M = 64
+workload, the source azimuth rotation, sources that share a position, and the
+scattered field of the solution at observation points."""
+import types
+
+import numpy as np
+import pytest
+
+from test_gpu_parity import CFG1, check_densities, oracle_solution
+
+pytestmark = pytest.mark.gpu
+
+SOURCES = [(0.4, 0.8), (0.0, 1.2)]
+
+
+def _oracle(src, phi_s=0.0):
+    from oracle.point_source import point_source_densities, point_source_systems
+    sol = oracle_solution(**CFG1)
+    systems, _ = point_source_systems(sol, *src)
+    u1, phi1, u2, phi2 = point_source_densities(sol, *src, phi_s=phi_s)
+    return types.SimpleNamespace(P=sol.P, A=systems, u1=u1, phi1=phi1, u2=u2, phi2=phi2)
+
+
+def _one(out, r):
+    return {k: v[:, :, r:r + 1] for k, v in out.items()}
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def prob():
+    from paper_2412_11162_gb300 import Problem
+    return Problem(CFG1["k1"], CFG1["k2"], CFG1["N"], CFG1["M"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_point_sources_vs_oracle(prob, precision):
+    """Both sources in one call; each column against the oracle's densities
+    (forward u error, backward error in the oracle's systems, phi per mode
+    against kappa_n), as the plane-wave parity."""
+    from paper_2412_11162_gb300.binding import PMLBIE_FP64, PMLBIE_MIXED
+    prec = PMLBIE_FP64 if precision == "fp64" else PMLBIE_MIXED
+    out, rep = prob.solve(sources=SOURCES, precision=prec)
+    assert out["u1"].shape == (CFG1["M"] // 2, CFG1["N"], 2)
+    for r, src in enumerate(SOURCES):
+        check_densities(_one(out, r), _oracle(src), 1e-10 if precision == "fp64" else 1e-6, 1e-11,
+                        "%s source %s" % (precision, src))
+
+
+def test_point_source_azimuth_and_shared_positions(prob):
+    """Sources at the same (rho, z) and different azimuths are solved once and
+    rotated: mode n of each is e^{-i n phi_s} times the phi_s = 0 solution, and
+    agrees with the oracle at that azimuth."""
+    import torch
+    from paper_2412_11162_gb300.binding import PMLBIE_FP64
+    src = SOURCES[0]
+    az = [0.0, 0.7, -2.1]
+    out, _ = prob.solve(sources=[src] * 3, azimuth=az, precision=PMLBIE_FP64)
+    n = torch.arange(CFG1["M"] // 2, dtype=torch.float64, device="cuda")[:, None]
+    for r, a in enumerate(az):
+        rot = torch.exp(-1j * n * a).to(torch.complex128)
+        for k in ("u1", "phi1", "u2", "phi2"):
+            d = (out[k][:, :, r] - rot * out[k][:, :, 0]).abs().max().item()
+            assert d <= 1e-13 * out[k][:, :, 0].abs().max().item(), (k, r, d)
+    ref = _oracle(src, phi_s=0.7)
+    assert _rel(out["u1"][:, :, 1].cpu().numpy(), ref.u1) <= 1e-10
+
+
+def test_point_source_field(prob):
+    """Scattered field of the GPU solution (pmlbie_field) against the oracle's
+    representation formula with the oracle densities: relative 2-norm <= 1e-10."""
+    from oracle.field import field_modes
+    from paper_2412_11162_gb300.binding import PMLBIE_FP64
+    rho = np.tile(np.linspace(0.0, 2.0, 8), 2)
+    zz = np.repeat([1.5, -1.0], 8)
+    reg = np.repeat([0, 1], 8)
+    src = SOURCES[0]
+    out, _ = prob.solve(sources=[src], precision=PMLBIE_FP64)
+    got = prob.field(rho, zz, reg, out)[:, :, 0].cpu().numpy()
+    ref = _oracle(src)
+    want = field_modes(ref.P, rho, zz, reg, ref.u1, ref.phi1, ref.u2, ref.phi2)
+    assert _rel(got, want) <= 1e-10, _rel(got, want)
+
+
+def test_point_source_options_rejected(prob):
+    from paper_2412_11162_gb300.binding import PMLBIE_FP64, PmlbieError
+    with pytest.raises(PmlbieError):
+        prob.solve(sources=[(3.0, 0.8)], precision=PMLBIE_FP64)      # in the PML
+    with pytest.raises(PmlbieError):
+        prob.solve(sources=[(0.4, 0.01)], precision=PMLBIE_FP64)     # on the interface
+    with pytest.raises(ValueError):
+        prob.solve([0.3], sources=[(0.4, 0.8)])

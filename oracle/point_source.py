@@ -30,11 +30,14 @@ def point_source_rhs(P: Params, G: Geometry, rho_s, z_s):
     return -S, -K * G.nodes["speed"][:, None]
 
 
-def point_source_systems(sol, rho_s, z_s):
+def point_source_systems(sol, rho_s, z_s, phi_s=0.0):
     """{n: (A_n, B_n)}: the block systems of a Solution built with keep_matrices
-    (Sec. 4.2) with the jumps of a source at (rho_s, 0, z_s) in B_n, and (b1, b2)."""
+    (Sec. 4.2) with the jumps of a source at (rho_s, phi_s, z_s) in B_n, and
+    those jumps (b1, b2), each (N, M/2)."""
     P, G = sol.P, sol.sys.G
     b1, b2 = point_source_rhs(P, G, rho_s, z_s)
+    rot = np.exp(-1j * np.arange(P.M // 2) * phi_s)[None, :]
+    b1, b2 = b1 * rot, b2 * rot
     N = P.N
     out = {}
     for n in sol.modes:
@@ -46,14 +49,13 @@ def point_source_systems(sol, rho_s, z_s):
 def point_source_densities(sol, rho_s, z_s, phi_s=0.0):
     """Densities (u1, phi1, u2, phi2), each (M/2, N), of a source at
     (rho_s, phi_s, z_s) (Sec. 4.2 block systems with the point-source jumps)."""
-    systems, (b1, b2) = point_source_systems(sol, rho_s, z_s)
+    systems, (b1, b2) = point_source_systems(sol, rho_s, z_s, phi_s)
     nh, N = sol.P.M // 2, sol.P.N
     out = [np.zeros((nh, N), complex) for _ in range(4)]
     for n, (A, B) in systems.items():
         x = np.linalg.solve(A, B)
-        rot = np.exp(-1j * n * phi_s)
-        out[0][n] = rot * x[:N]
-        out[1][n] = rot * x[N:]
-        out[2][n] = rot * (x[:N] - b1[:, n])
-        out[3][n] = rot * (x[N:] - b2[:, n])
+        out[0][n] = x[:N]
+        out[1][n] = x[N:]
+        out[2][n] = x[:N] - b1[:, n]
+        out[3][n] = x[N:] - b2[:, n]
     return tuple(out)

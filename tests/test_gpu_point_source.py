@@ -2,13 +2,24 @@
 the GPU jumps and densities against the oracle's (oracle/point_source.py,
 pinned by quadrature and the lower-medium identity) on the N = 128, M = 64
 workload, the source azimuth rotation, sources that share a position, and the
-scattered field of the solution at observation points."""
+scattered field of the solution at observation points.
+
+Unlike plane-wave data, which vanish on the flat parts of the interface, the
+point-source jumps are O(1) on the PML part of the curve.  There the close-pair
+split of Sec. 4.3 cancels by up to ~1e9, so the GPU's and the oracle's
+matrices differ by ~1e9 eps in those entries, and two backward-stable solves
+of them differ by about kappa_n times that along the modes' near-null
+directions (measured: u1 6e-10 relative in modes 1-3, kappa 3e4, with a
+backward error of 4e-15 in the oracle's systems).  The checks are therefore:
+the jumps b1 = u1 - u2, b2 = phi1 - phi2 to 1e-13; the normwise backward error
+of the GPU densities in the oracle's block systems to 1e-13; and each mode's
+forward error to max(tol, 1e-12 kappa_n), tol = 1e-10 (FP64) or 1e-6 (mixed)."""
 import types
 
 import numpy as np
 import pytest
 
-from test_gpu_parity import CFG1, check_densities, oracle_solution
+from test_gpu_parity import CFG1, oracle_solution
 
 pytestmark = pytest.mark.gpu
 
@@ -18,7 +29,7 @@ SOURCES = [(0.4, 0.8), (0.0, 1.2)]
 def _oracle(src, phi_s=0.0):
     from oracle.point_source import point_source_densities, point_source_systems
     sol = oracle_solution(**CFG1)
-    systems, _ = point_source_systems(sol, *src)
+    systems, _ = point_source_systems(sol, *src, phi_s=phi_s)
     u1, phi1, u2, phi2 = point_source_densities(sol, *src, phi_s=phi_s)
     return types.SimpleNamespace(P=sol.P, A=systems, u1=u1, phi1=phi1, u2=u2, phi2=phi2)
 
@@ -37,18 +48,39 @@ def prob():
     return Problem(CFG1["k1"], CFG1["k2"], CFG1["N"], CFG1["M"])
 
 
+def check_point(out, r, ref, tol, label):
+    """Column r of the GPU outputs against the oracle's point-source solution."""
+    from test_gpu_parity import mode_conditioning
+    kap = mode_conditioning(oracle_solution(**CFG1))
+    g = {k: v[:, :, r].cpu().numpy() for k, v in out.items()}
+    for got, want in ((g["u1"] - g["u2"], ref.u1 - ref.u2), (g["phi1"] - g["phi2"], ref.phi1 - ref.phi2)):
+        assert _rel(got, want) <= 1e-13, (label, "jumps", _rel(got, want))
+    r2 = x2 = b2 = anorm = 0.0
+    for n, (A, B) in ref.A.items():
+        x = np.concatenate([g["u1"][n], g["phi1"][n]])
+        r2 += np.linalg.norm(A @ x - B) ** 2
+        x2 += np.linalg.norm(x) ** 2
+        b2 += np.linalg.norm(B) ** 2
+        anorm = max(anorm, np.linalg.norm(A))
+    bwd = np.sqrt(r2) / (anorm * np.sqrt(x2) + np.sqrt(b2))
+    assert bwd <= 1e-13, (label, "backward", bwd)
+    for k in ("u1", "phi1", "u2", "phi2"):
+        want = getattr(ref, k)
+        for n in range(want.shape[0]):
+            e = np.linalg.norm(g[k][n] - want[n]) / np.linalg.norm(want)
+            assert e <= max(tol, 1e-12 * kap[n]), (label, k, n, e, kap[n])
+    print(label, "backward %.1e" % bwd, {k: "%.1e" % _rel(g[k], getattr(ref, k)) for k in g})
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_point_sources_vs_oracle(prob, precision):
-    """Both sources in one call; each column against the oracle's densities
-    (forward u error, backward error in the oracle's systems, phi per mode
-    against kappa_n), as the plane-wave parity."""
+    """Both sources in one call; each column against the oracle's densities."""
     from paper_2412_11162_gb300.binding import PMLBIE_FP64, PMLBIE_MIXED
     prec = PMLBIE_FP64 if precision == "fp64" else PMLBIE_MIXED
     out, rep = prob.solve(sources=SOURCES, precision=prec)
     assert out["u1"].shape == (CFG1["M"] // 2, CFG1["N"], 2)
     for r, src in enumerate(SOURCES):
-        check_densities(_one(out, r), _oracle(src), 1e-10 if precision == "fp64" else 1e-6, 1e-11,
-                        "%s source %s" % (precision, src))
+        check_point(out, r, _oracle(src), 1e-10 if precision == "fp64" else 1e-6, "%s source %s" % (precision, src))
 
 
 def test_point_source_azimuth_and_shared_positions(prob):
@@ -66,13 +98,14 @@ def test_point_source_azimuth_and_shared_positions(prob):
         for k in ("u1", "phi1", "u2", "phi2"):
             d = (out[k][:, :, r] - rot * out[k][:, :, 0]).abs().max().item()
             assert d <= 1e-13 * out[k][:, :, 0].abs().max().item(), (k, r, d)
-    ref = _oracle(src, phi_s=0.7)
-    assert _rel(out["u1"][:, :, 1].cpu().numpy(), ref.u1) <= 1e-10
+    check_point(out, 1, _oracle(src, phi_s=0.7), 1e-10, "azimuth 0.7")
 
 
 def test_point_source_field(prob):
     """Scattered field of the GPU solution (pmlbie_field) against the oracle's
-    representation formula with the oracle densities: relative 2-norm <= 1e-10."""
+    representation formula: with the GPU densities (the field kernels alone)
+    to 1e-12, and end to end with the oracle densities to 1e-9 (the densities'
+    PML-node differences described above enter through the weights there)."""
     from oracle.field import field_modes
     from paper_2412_11162_gb300.binding import PMLBIE_FP64
     rho = np.tile(np.linspace(0.0, 2.0, 8), 2)
@@ -82,8 +115,11 @@ def test_point_source_field(prob):
     out, _ = prob.solve(sources=[src], precision=PMLBIE_FP64)
     got = prob.field(rho, zz, reg, out)[:, :, 0].cpu().numpy()
     ref = _oracle(src)
+    g = {k: v[:, :, 0].cpu().numpy() for k, v in out.items()}
+    same = field_modes(ref.P, rho, zz, reg, g["u1"], g["phi1"], g["u2"], g["phi2"])
+    assert _rel(got, same) <= 1e-12, _rel(got, same)
     want = field_modes(ref.P, rho, zz, reg, ref.u1, ref.phi1, ref.u2, ref.phi2)
-    assert _rel(got, want) <= 1e-10, _rel(got, want)
+    assert _rel(got, want) <= 1e-9, _rel(got, want)
 
 
 def test_point_source_options_rejected(prob):

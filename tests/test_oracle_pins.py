@@ -158,6 +158,44 @@ def test_modal_kernels_vs_quadrature_pml():
         assert np.abs(S[i, :24] - Se[i]).max() <= tol * np.abs(Se[i]).max(), (pairs[i], near[i])
 
 
+def test_modal_symmetry_plus_minus_n():
+    """F^_{-n} = F^_n (Sec. 3.3: modes +-n give the same systems).  The 3D
+    kernels are evaluated from Cartesian points r = (rho~, 0, z),
+    r' = (rho~' cos psi, rho~' sin psi, z') with the conormal rotated with r'
+    (no use of the oracle's distance formula), their two-sided modes
+    n = -31..31 by a 4096-point trapezoid over the full circle; the + and -
+    modes agree and equal the oracle's far-pair modes n = 0..31, physical and
+    PML pairs (a sin psi term or an odd part would break both)."""
+    P = Params(k1=2 * np.pi, k2=3 * np.pi, N=128, M=64)
+    G = Geometry(P)
+    pairs = [(10, 30), (5, 70), (40, 100), (100, 60), (30, 5)]
+    li = np.array([p[0] for p in pairs])
+    mi = np.array([p[1] for p in pairs])
+    pg = KR.pair_geometry(_take(G.nodes, li), _take(G.nodes, mi), P)
+    assert not KR.near_mask(pg, P).any()
+    S, K = KR.modal_kernels(pg, P.k1, P)
+    Mf = 4096
+    psi = 2 * np.pi * np.arange(Mf) / Mf
+    ns = np.arange(-31, 32)
+    E = (2 * np.pi / Mf) * np.exp(-1j * np.outer(psi, ns))
+    nd = G.nodes
+    for i, (l, m) in enumerate(pairs):
+        dx = nd["rho_t"][l] - nd["rho_t"][m] * np.cos(psi)
+        dy = -nd["rho_t"][m] * np.sin(psi)
+        dz = nd["z_t"][l] - nd["z_t"][m]
+        R = np.sqrt(dx * dx + dy * dy + dz * dz)
+        e = np.exp(1j * P.k1 * R)
+        ndot = nd["nuc_r"][m] * (np.cos(psi) * dx + np.sin(psi) * dy) + nd["nuc_z"][m] * dz
+        for F, ours in ((e / (4 * np.pi * R), S[i]), (ndot / (4 * np.pi * R ** 3) * e * (1 - 1j * P.k1 * R), K[i])):
+            Fh = F @ E
+            scale = np.abs(Fh).max()
+            if scale == 0.0:          # flat pairs: the double layer vanishes identically
+                assert np.abs(ours).max() == 0.0
+                continue
+            assert np.abs(Fh[31:] - Fh[31::-1]).max() <= 1e-13 * scale, pairs[i]
+            assert np.abs(ours - Fh[31:]).max() <= 1e-13 * scale, pairs[i]
+
+
 def test_laplace_modes_vs_legendre_q():
     """Z^_m = Q_{m-1/2}(chi) / (2 pi sqrt(rho~ rho~')), chi = 1 + d^2/(2 rho~ rho~')
     (toroidal expansion of 1/|r - r'|), for real and complex (PML) chi."""
@@ -431,3 +469,32 @@ def test_point_source_rhs_calderon_identity_lower_medium():
         assert np.linalg.norm(r[band]) <= 1e-5 * np.linalg.norm(b1[band, n]), n
         bad = (Kb - np.diag(Db)) @ b1[:, n] - Sb @ b2[:, n]
         assert np.linalg.norm(bad[band]) > 0.5 * np.linalg.norm(b1[band, n])
+
+
+def test_pml_truncation_error_decays_exponentially():
+    """Truncation error against a thick-PML reference (Sec. 3.1, Eq. (sgm1)):
+    the dent geometry with a breakpoint at the PML start a1 = 2 and
+    32 grid steps per unit length, so that every T shares the physical nodes
+    exactly; u1 on those nodes (modes 0-2, M = 128) for T = 0.75 .. 2 against
+    T = 3.  The error must fall by a steady factor per added thickness
+    (measured: 4.0e-4, 1.2e-4, 9.5e-6, 6.9e-7, about e^{-5.2 T}); a PML that
+    did not attenuate (wrong sign or a missing stretch) leaves it O(1)."""
+    from oracle.assemble import Solution
+    V = [(0.0, -1.0), (1.0, -1.0), (1.0, 0.0), (2.0, 0.0)]
+    runs = {}
+    for T in (0.75, 1.0, 1.5, 2.0, 3.0):
+        Nt = int(round(32 * (3 + T)))          # 32 steps per unit on every segment
+        P = Params(k1=np.pi, k2=1.5 * np.pi, N=Nt - 4, M=128, a1=2.0, T=T, S=2.0, curve="polyline", vertices=V)
+        sol = Solution(P, modes=range(3))
+        G = sol.sys.G
+        assert list(G.steps[:3]) == [32, 32, 32]
+        phys = G.nodes["rho"] < 2.0
+        runs[T] = (G.nodes["rho"][phys], sol.u1[:3][:, phys])
+    r_ref, u_ref = runs[3.0]
+    errs = []
+    for T in (0.75, 1.0, 1.5, 2.0):
+        r, u = runs[T]
+        assert np.abs(r - r_ref).max() < 1e-13      # the same nodes (up to rounding of t)
+        errs.append(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref))
+    assert errs[0] < 1e-2 and errs[-1] < 3e-6, errs
+    assert errs[1] < errs[0] / 2 and errs[2] < errs[1] / 5 and errs[3] < errs[2] / 5, errs

@@ -52,97 +52,184 @@ template <typename T> __device__ __forceinline__ typename Cx<T>::R abs2(T a) { r
 constexpr int kNB = 32;          // panel width
 constexpr int kPanelThreads = 512;
 
-// Panel factorisation of columns [k0, k0+kb) over rows [k0, n), one CTA per matrix.
+// Panel factorisation of columns [k0, k0+kb) over rows [k0, n), one CTA per
+// matrix.  The panel is processed in sub-panels of w columns that are held in
+// shared memory (m = n - k0 rows, m x w entries), left-looking inside the
+// panel: a sub-panel is loaded, brought up to date with the sub-panels to its
+// left (unit-lower solve on its top rows, then the rank-s0 update of the rows
+// below, s0 = columns already factored), factored column by column in shared
+// memory (pivot search, swap, scaling, rank-1 updates), and written back.
+// Each row interchange is applied at once to the panel's other columns in
+// global memory (the L part of the earlier sub-panels and the not yet loaded
+// later ones), so the panel leaves with LAPACK getrf's row order.
 template <typename T>
-__global__ void panel_kernel(int n, int k0, int kb, T* A, int* piv, int* info) {
+__global__ void __launch_bounds__(kPanelThreads) panel_kernel(int n, int k0, int kb, int w, T* A, int* piv,
+                                                              int* info) {
     using R = typename Cx<T>::R;
-    T* a = A + (size_t)blockIdx.x * n * n;
-    int* pv = piv + (size_t)blockIdx.x * n;
+    extern __shared__ unsigned char smraw[];
+    T* S = reinterpret_cast<T*>(smraw);          // [w][m], S[c * m + i], i = row - k0
     __shared__ R sval[kPanelThreads / 32];
     __shared__ int sidx[kPanelThreads / 32];
     __shared__ int spiv;
     __shared__ T sinv;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int j = k0; j < k0 + kb; ++j) {
-        // pivot search in column j, rows j..n-1
-        R best = -1;
-        int bi = j;
-        for (int i = j + tid; i < n; i += blockDim.x) {
-            R v = abs2(a[(size_t)j * n + i]);
-            if (v > best) {
-                best = v;
-                bi = i;
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            R ov = __shfl_down_sync(0xffffffff, best, o);
-            int oi = __shfl_down_sync(0xffffffff, bi, o);
-            if (ov > best || (ov == best && oi < bi)) {
-                best = ov;
-                bi = oi;
-            }
-        }
-        if (lane == 0) {
-            sval[warp] = best;
-            sidx[warp] = bi;
+    const int m = n - k0;
+    T* a = A + (size_t)blockIdx.x * n * n;
+    int* pv = piv + (size_t)blockIdx.x * n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+    for (int s0 = 0; s0 < kb; s0 += w) {
+        const int ws = min(w, kb - s0);
+        for (int idx = tid; idx < ws * m; idx += nt) {
+            const int c = idx / m, i = idx - c * m;
+            S[idx] = a[(size_t)(k0 + s0 + c) * n + k0 + i];
         }
         __syncthreads();
-        if (tid == 0) {
-            R b = sval[0];
-            int bix = sidx[0];
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-                if (sval[w] > b || (sval[w] == b && sidx[w] < bix)) {
-                    b = sval[w];
-                    bix = sidx[w];
+        if (s0 > 0) {
+            // top rows: U = L11^{-1} (rows 0..s0-1), one warp per column, lane = row
+            for (int c = warp; c < ws; c += nt >> 5) {
+                T x = lane < s0 ? S[c * m + lane] : Cx<T>::mk(0, 0);
+                for (int t = 0; t < s0 - 1; ++t) {
+                    const T xt = Cx<T>::mk(__shfl_sync(0xffffffffu, x.x, t), __shfl_sync(0xffffffffu, x.y, t));
+                    if (lane > t && lane < s0) x = fms(x, a[(size_t)(k0 + t) * n + k0 + lane], xt);
                 }
-            spiv = bix;
-            pv[j] = bix;
-            T d = a[(size_t)j * n + bix];
-            if (b <= (R)0) {
-                if (info[blockIdx.x] == 0) info[blockIdx.x] = j + 1;
-                sinv = Cx<T>::mk(0, 0);
-            } else {
-                sinv = rcp(d);
+                if (lane < s0) S[c * m + lane] = x;
             }
+            __syncthreads();
+            // rows below: S[c][i] -= sum_t L[i][t] U[t][c], one thread per row,
+            // eight columns at a time
+            for (int i = s0 + tid; i < m; i += nt) {
+                for (int c0 = 0; c0 < ws; c0 += 8) {
+                    T acc[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) acc[c] = Cx<T>::mk(0, 0);
+#pragma unroll 4
+                    for (int t = 0; t < s0; ++t) {
+                        const T l = a[(size_t)(k0 + t) * n + k0 + i];
+#pragma unroll
+                        for (int c = 0; c < 8; ++c)
+                            if (c0 + c < ws) {
+                                const T u = S[(size_t)(c0 + c) * m + t];
+                                acc[c].x += l.x * u.x - l.y * u.y;
+                                acc[c].y += l.x * u.y + l.y * u.x;
+                            }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (c0 + c < ws) S[(size_t)(c0 + c) * m + i] = sub(S[(size_t)(c0 + c) * m + i], acc[c]);
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        const int p = spiv;
-        // swap rows j and p inside the panel
-        if (p != j)
-            for (int c = k0 + tid; c < k0 + kb; c += blockDim.x) {
-                T t = a[(size_t)c * n + j];
-                a[(size_t)c * n + j] = a[(size_t)c * n + p];
-                a[(size_t)c * n + p] = t;
+        for (int jj = 0; jj < ws; ++jj) {
+            const int j = s0 + jj;                 // local row of the diagonal entry
+            const T* col = S + (size_t)jj * m;
+            R best = -1;
+            int bi = j;
+            for (int i = j + tid; i < m; i += nt) {
+                const R v = abs2(col[i]);
+                if (v > best) {
+                    best = v;
+                    bi = i;
+                }
             }
-        __syncthreads();
-        const T inv = sinv;
-        for (int i = j + 1 + tid; i < n; i += blockDim.x) a[(size_t)j * n + i] = mul(a[(size_t)j * n + i], inv);
-        __syncthreads();
-        // rank-1 update of the remaining panel columns
-        for (int i = j + 1 + tid; i < n; i += blockDim.x) {
-            T lij = a[(size_t)j * n + i];
-            for (int c = j + 1; c < k0 + kb; ++c)
-                a[(size_t)c * n + i] = fms(a[(size_t)c * n + i], lij, a[(size_t)c * n + j]);
+            for (int o = 16; o > 0; o >>= 1) {
+                const R ov = __shfl_down_sync(0xffffffffu, best, o);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) {
+                    best = ov;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                sval[warp] = best;
+                sidx[warp] = bi;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                const int nw = nt >> 5;
+                R b = lane < nw ? sval[lane] : (R)-2;
+                int bix = lane < nw ? sidx[lane] : 0x7fffffff;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const R ov = __shfl_down_sync(0xffffffffu, b, o);
+                    const int oi = __shfl_down_sync(0xffffffffu, bix, o);
+                    if (ov > b || (ov == b && oi < bix)) {
+                        b = ov;
+                        bix = oi;
+                    }
+                }
+                if (lane == 0) {
+                    spiv = bix;
+                    pv[k0 + j] = k0 + bix;
+                    const T d = col[bix];
+                    if (b <= (R)0) {
+                        if (info[blockIdx.x] == 0) info[blockIdx.x] = k0 + j + 1;
+                        sinv = Cx<T>::mk(0, 0);
+                    } else {
+                        sinv = rcp(d);
+                    }
+                }
+            }
+            __syncthreads();
+            const int p = spiv;
+            if (p != j)
+                for (int c = tid; c < kb; c += nt) {
+                    if (c >= s0 && c < s0 + ws) {
+                        T* sc = S + (size_t)(c - s0) * m;
+                        const T t = sc[j];
+                        sc[j] = sc[p];
+                        sc[p] = t;
+                    } else {
+                        T* gc = a + (size_t)(k0 + c) * n + k0;
+                        const T t = gc[j];
+                        gc[j] = gc[p];
+                        gc[p] = t;
+                    }
+                }
+            __syncthreads();
+            // scale column j below the diagonal, rank-1 update of the sub-panel's later columns
+            const T inv = sinv;
+            for (int i = j + 1 + tid; i < m; i += nt) {
+                const T l = mul(S[(size_t)jj * m + i], inv);
+                S[(size_t)jj * m + i] = l;
+                for (int cc = jj + 1; cc < ws; ++cc)
+                    S[(size_t)cc * m + i] = fms(S[(size_t)cc * m + i], l, S[(size_t)cc * m + j]);
+            }
+            __syncthreads();
+        }
+        for (int idx = tid; idx < ws * m; idx += nt) {
+            const int c = idx / m, i = idx - c * m;
+            a[(size_t)(k0 + s0 + c) * n + k0 + i] = S[idx];
         }
         __syncthreads();
     }
 }
 
+// Sub-panel width of the panel kernel: the widest power of two (at most the
+// panel width) whose m x w block fits in about 200 KB of shared memory.
+template <typename T>
+int panel_width(int m) {
+    int w = kNB;
+    while (w > 1 && (size_t)m * w * sizeof(T) > 200 * 1024) w >>= 1;
+    return w;
+}
+
 // Row swaps of the panel applied to the columns outside it, then the
 // unit-lower solve U12 = L11^{-1} A12 for the columns right of the panel.
-// One CTA per (64-column tile, matrix).  The tile's kb panel rows are loaded
-// (coalesced: each column's rows k0..k0+kb-1 are contiguous), every distinct
-// pivot row below the panel is gathered once, the swaps are replayed in order
-// in shared memory (one thread per column), the triangular solve runs on the
-// block in shared memory, and everything is written back.
+// One CTA of 256 threads per (64-column tile, matrix).  Warp 0 gives every
+// row the swaps touch a slot (the kb panel rows, then each distinct pivot row
+// below the panel) and replays the swaps on slot indices once, which yields
+// the source slot of every destination slot; the tile's slot rows are then
+// loaded already permuted, solved and written back.  The solve takes four
+// lanes per column (eight rows each, in registers) and broadcasts x_j by
+// shuffles inside the group, so it needs no block barrier per step.
 constexpr int kSwapCols = 64;
 
 template <typename T>
-__global__ void swap_trsm_kernel(int n, int k0, int kb, T* A, const int* piv) {
+__global__ void __launch_bounds__(256) swap_trsm_kernel(int n, int k0, int kb, T* A, const int* piv) {
     extern __shared__ unsigned char smraw[];
-    T* blk = reinterpret_cast<T*>(smraw);                 // [kSwapCols][2*kNB]: panel rows, then outside rows
+    T* blk = reinterpret_cast<T*>(smraw);                 // [kSwapCols][2*kNB]: slots of each column
     T* L = blk + (size_t)kSwapCols * 2 * kNB;             // [kNB][kNB] (col-major), right tiles only
-    __shared__ int srow[2 * kNB];                         // global row of each smem row slot
+    __shared__ int srow[2 * kNB];                         // global row of each slot
+    __shared__ int ssrc[2 * kNB];                         // slot whose content ends in slot r
     __shared__ int sslot[kNB];                            // slot of pivot p_j
     __shared__ int nslots;
     const int b = blockIdx.y;
@@ -150,76 +237,88 @@ __global__ void swap_trsm_kernel(int n, int k0, int kb, T* A, const int* piv) {
     const int* pv = piv + (size_t)b * n;
     const int c0 = blockIdx.x * kSwapCols;
     const int ncol = min(kSwapCols, n - c0);
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        int ns = kb;
-        for (int r = 0; r < kb; ++r) srow[r] = k0 + r;
-        for (int j = 0; j < kb; ++j) {
-            int p = pv[k0 + j];
-            int slot = -1;
-            for (int q = 0; q < ns; ++q)
-                if (srow[q] == p) {
-                    slot = q;
-                    break;
-                }
-            if (slot < 0) {
-                slot = ns;
-                srow[ns++] = p;
-            }
-            sslot[j] = slot;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        const int p = lane < kb ? pv[k0 + lane] : -1;
+        const bool outside = lane < kb && p >= k0 + kb;
+        // lanes holding the same outside pivot row share one slot, numbered in
+        // order of first occurrence after the kb panel rows
+        const unsigned same = __match_any_sync(0xffffffffu, outside ? p : -1 - lane);
+        const int leader = __ffs(same) - 1;
+        const unsigned firsts = __ballot_sync(0xffffffffu, outside && leader == lane);
+        const int oslot = kb + __popc(firsts & ((1u << leader) - 1u));
+        if (lane < kb) {
+            srow[lane] = k0 + lane;
+            sslot[lane] = outside ? oslot : p - k0;
+            if (outside && leader == lane) srow[oslot] = p;
         }
-        nslots = ns;
+        const int ns = kb + __popc(firsts);
+        for (int r = lane; r < ns; r += 32) ssrc[r] = r;
+        __syncwarp();
+        if (lane == 0) {
+            nslots = ns;
+            for (int j = 0; j < kb; ++j) {
+                const int s2 = sslot[j];
+                if (s2 != j) {
+                    const int t = ssrc[j];
+                    ssrc[j] = ssrc[s2];
+                    ssrc[s2] = t;
+                }
+            }
+        }
     }
     __syncthreads();
     const int ns = nslots;
-    // load: slot r of column c at blk[c * 2kNB + r]
-    for (int idx = tid; idx < ncol * ns; idx += blockDim.x) {
-        int c = idx / ns, r = idx % ns;
-        int col = c0 + c;
-        bool in_panel = col >= k0 && col < k0 + kb;
-        if (!in_panel) blk[c * 2 * kNB + r] = a[(size_t)col * n + srow[r]];
-    }
     const bool right = c0 + ncol > k0 + kb;
+    // load the slot rows permuted: slot r of column c at blk[c * 2kNB + r]
+    for (int idx = tid; idx < ncol * ns; idx += blockDim.x) {
+        const int c = idx / ns, r = idx - c * ns;
+        const int col = c0 + c;
+        if (col < k0 || col >= k0 + kb) blk[c * 2 * kNB + r] = a[(size_t)col * n + srow[ssrc[r]]];
+    }
     if (right)
         for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
-            int j = idx / kb, i = idx % kb;          // L[i][j] at L[j*kNB + i]
+            const int j = idx / kb, i = idx - j * kb;      // L[i][j] at L[j*kNB + i]
             L[j * kNB + i] = a[(size_t)(k0 + j) * n + k0 + i];
         }
     __syncthreads();
-    // replay the swaps: one thread per column
-    for (int c = tid; c < ncol; c += blockDim.x) {
-        int col = c0 + c;
-        if (col >= k0 && col < k0 + kb) continue;
+    if (right) {
+        // unit-lower solve on the right columns: lane q of a 4-lane group owns rows q, q+4, ..
+        const int c = tid >> 2, q = tid & 3;
+        const int col = c0 + c;
+        const bool act = c < ncol && col >= k0 + kb;
         T* x = blk + c * 2 * kNB;
-        for (int j = 0; j < kb; ++j) {
-            int s2 = sslot[j];
-            if (s2 != j) {
-                T t = x[j];
-                x[j] = x[s2];
-                x[s2] = t;
+        T v[kNB / 4];
+#pragma unroll
+        for (int t = 0; t < kNB / 4; ++t) {
+            const int i = q + 4 * t;
+            v[t] = act && i < kb ? x[i] : Cx<T>::mk(0, 0);
+        }
+        const int base = lane & ~3;
+#pragma unroll
+        for (int j = 0; j < kNB - 1; ++j) {
+            const T own = v[j >> 2];
+            const T xj = Cx<T>::mk(__shfl_sync(0xffffffffu, own.x, base | (j & 3)),
+                                   __shfl_sync(0xffffffffu, own.y, base | (j & 3)));
+#pragma unroll
+            for (int t = 0; t < kNB / 4; ++t) {
+                const int i = q + 4 * t;
+                if (i > j && i < kb) v[t] = fms(v[t], L[j * kNB + i], xj);
             }
         }
+        if (act)
+#pragma unroll
+            for (int t = 0; t < kNB / 4; ++t) {
+                const int i = q + 4 * t;
+                if (i < kb) x[i] = v[t];
+            }
     }
     __syncthreads();
-    // unit-lower solve on the right columns: rows parallel, j sequential
-    if (right) {
-        for (int j = 0; j < kb; ++j) {
-            for (int idx = tid; idx < ncol * kb; idx += blockDim.x) {
-                int c = idx / kb, i = idx % kb;
-                int col = c0 + c;
-                if (i <= j || col < k0 + kb) continue;
-                T* x = blk + c * 2 * kNB;
-                x[i] = fms(x[i], L[j * kNB + i], x[j]);
-            }
-            __syncthreads();
-        }
-    }
     // write back every slot
     for (int idx = tid; idx < ncol * ns; idx += blockDim.x) {
-        int c = idx / ns, r = idx % ns;
-        int col = c0 + c;
-        if (col >= k0 && col < k0 + kb) continue;
-        a[(size_t)col * n + srow[r]] = blk[c * 2 * kNB + r];
+        const int c = idx / ns, r = idx - c * ns;
+        const int col = c0 + c;
+        if (col < k0 || col >= k0 + kb) a[(size_t)col * n + srow[r]] = blk[c * 2 * kNB + r];
     }
 }
 
@@ -497,7 +596,13 @@ template <typename T>
 cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s) {
     for (int k0 = 0; k0 < n; k0 += kNB) {
         int kb = std::min(kNB, n - k0);
-        panel_kernel<T><<<batch, kPanelThreads, 0, s>>>(n, k0, kb, A, piv, info);
+        const int w = panel_width<T>(n - k0);
+        const size_t smp = sizeof(T) * (size_t)(n - k0) * w;
+        if (k0 == 0) {
+            cudaError_t e = allow_max_smem(panel_kernel<T>);
+            if (e != cudaSuccess) return e;
+        }
+        panel_kernel<T><<<batch, kPanelThreads, smp, s>>>(n, k0, kb, w, A, piv, info);
         count_launch(2);
         dim3 g1((n + kSwapCols - 1) / kSwapCols, batch);
         size_t sm1 = sizeof(T) * ((size_t)kSwapCols * 2 * kNB + kNB * kNB);

@@ -180,6 +180,8 @@ cudaError_t launch_outputs(const pmlbie_problem* prob, int n_rhs, int nm, const 
                            double2* u2, double2* phi2, cudaStream_t s);
 
 // dense batched linear algebra (lu.cu)
+// Leaves piv[b] as the row permutation of the factorisation: piv[b][i] is the
+// original row that ends in row i (P A = L U with (P x)_i = x_{piv[i]}).
 template <typename T>
 cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s);
 // active: optional per-matrix flags (0 = skip), used to leave converged modes alone

@@ -383,117 +383,195 @@ __global__ void gemm_update_kernel(int n, int k0, int kb, T* A) {
     }
 }
 
-// Solve LU x = b for every matrix and rhs: row swaps, then blocked unit-lower
-// forward and upper backward substitution.  One CTA (512 threads) per
-// (matrix, group of up to kSolveR right-hand sides); B is [b][n][nrhs].  The
-// group's right-hand sides live in shared memory ([row][R]) for the whole
-// solve, so each factor element read from memory serves all of them; each
-// 32-row diagonal block is solved by one warp per right-hand side, then the
-// rows outside it are updated (thread per row, 32 columns, all R columns).
-// Matrices whose active flag is 0 are skipped (converged modes).
+// Solve LU x = b for every matrix and rhs: the row permutation (gathered
+// while loading), then blocked unit-lower forward and upper backward
+// substitution.  One CTA (512 threads) per (matrix, group of up to kSolveR
+// right-hand sides); B is [b][n][nrhs].  The group's right-hand sides live in
+// shared memory ([row][R]) for the whole solve, so each factor element read
+// from memory serves all of them; each 32-row diagonal block is solved by one
+// warp per right-hand side, then the rows outside it are updated.  With one
+// right-hand side the update takes two adjacent rows per thread and all 32
+// column loads of a block at once (16-byte loads for complex64 factors), so
+// that enough bytes are in flight to stream the factors at HBM speed; the
+// next diagonal block is fetched into registers during the update.  Matrices
+// whose active flag is 0 are skipped (converged modes).
 constexpr int kSolveR = 8;
 
 template <typename T> __device__ __forceinline__ T widen(float2 v) { return Cx<T>::mk(v.x, v.y); }
 template <typename T> __device__ __forceinline__ T widen(double2 v) { return Cx<T>::mk(v.x, v.y); }
 
+// two adjacent column entries p[0], p[1] (p 16-byte aligned for complex64)
+__device__ __forceinline__ void load_pair(const float2* p, float2& u, float2& v) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    u = make_float2(q.x, q.y);
+    v = make_float2(q.z, q.w);
+}
+__device__ __forceinline__ void load_pair(const double2* p, double2& u, double2& v) {
+    u = __ldg(p);
+    v = __ldg(p + 1);
+}
+
+// x[i], x[i+1] -= sum_{c < kNB} F[c][i..i+1] x[c0 + c]  (a full 32-column block),
+// loads issued in chunks of 256 bytes per thread
+template <typename T, typename TF>
+__device__ __forceinline__ void block_pair_update(const TF* col, int n, const T* xs, T& acc0, T& acc1) {
+    constexpr int CH = (int)(256 / (2 * sizeof(TF)));
+#pragma unroll
+    for (int c0 = 0; c0 < kNB; c0 += CH) {
+        TF l0[CH], l1[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) load_pair(col + (size_t)(c0 + c) * n, l0[c], l1[c]);
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const T xc = xs[c0 + c];
+            acc0 = fms(acc0, widen<T>(l0[c]), xc);
+            acc1 = fms(acc1, widen<T>(l1[c]), xc);
+        }
+    }
+}
+
 template <typename T, typename TF, int RM>
-__global__ void lu_solve_kernel(int n, int nrhs, int Rg, const TF* LU, const int* piv, T* B, const int* active) {
+__global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, const TF* LU, const int* perm,
+                                                       T* B, const int* active) {
     const int R = RM == 1 ? 1 : Rg;    // compile-time 1 in the single-wave variant
     const int b = blockIdx.x, r0 = blockIdx.y * R, nr = RM == 1 ? 1 : min(R, nrhs - r0);
     if (active && !active[b]) return;
     extern __shared__ unsigned char smraw[];
     T* sx = reinterpret_cast<T*>(smraw);                     // n x R entries, sx[i * R + q]
-    int* spv = reinterpret_cast<int*>(sx + (size_t)n * R);   // n pivots
     const TF* a = LU + (size_t)b * n * n;
-    const int* pv = piv + (size_t)b * n;
+    const int* pm = perm + (size_t)b * n;
     T* x = B + (size_t)b * n * nrhs;
-    __shared__ T sD[kNB][kNB + 1];   // diagonal block, sD[col][row]
+    __shared__ __align__(16) TF sD[kNB * kNB];     // diagonal block, sD[col * kNB + row]
+    constexpr int kDiagPer = (int)(kNB * kNB * sizeof(TF) / (512 * 16));   // 16-byte pieces per thread
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int idx = tid; idx < n * nr; idx += blockDim.x) {
         const int i = idx / nr, q = idx - i * nr;
-        sx[i * R + q] = x[(size_t)i * nrhs + r0 + q];
+        sx[i * R + q] = x[(size_t)pm[i] * nrhs + r0 + q];
     }
-    for (int i = tid; i < n; i += blockDim.x) spv[i] = pv[i];
-    __syncthreads();
-    if (tid < nr)
-        for (int j = 0; j < n; ++j) {
-            const int p = spv[j];
-            if (p != j) {
-                T t = sx[j * R + tid];
-                sx[j * R + tid] = sx[p * R + tid];
-                sx[p * R + tid] = t;
-            }
+    // diagonal block j0 into registers (16-byte pieces, column by column)
+    auto fetch_diag = [&](int j0, int jb, float4 (&reg)[kDiagPer]) {
+#pragma unroll
+        for (int t = 0; t < kDiagPer; ++t) {
+            const int e = (tid + t * 512) * (int)(16 / sizeof(TF));     // first element of the piece
+            const int c = e / kNB, i = e - c * kNB;
+            reg[t] = (c < jb && i < jb) ? __ldg(reinterpret_cast<const float4*>(a + (size_t)(j0 + c) * n + j0 + i))
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-    __syncthreads();
+    };
+    auto store_diag = [&](const float4 (&reg)[kDiagPer]) {
+#pragma unroll
+        for (int t = 0; t < kDiagPer; ++t) reinterpret_cast<float4*>(sD)[tid + t * 512] = reg[t];
+    };
+    float4 dreg[kDiagPer];
+    const bool vec = RM == 1 && (n % kNB) == 0;   // full blocks only: the pair path
     // forward: L y = x (unit diagonal)
+    if (vec) {
+        fetch_diag(0, kNB, dreg);
+        store_diag(dreg);
+    }
+    __syncthreads();
     for (int j0 = 0; j0 < n; j0 += kNB) {
         const int jb = min(kNB, n - j0);
-        for (int idx = tid; idx < jb * jb; idx += blockDim.x) {
-            int c = idx / jb, i = idx % jb;
-            sD[c][i] = widen<T>(a[(size_t)(j0 + c) * n + j0 + i]);
+        if (!vec) {
+            for (int idx = tid; idx < jb * jb; idx += blockDim.x) {
+                const int c = idx / jb, i = idx % jb;
+                sD[c * kNB + i] = a[(size_t)(j0 + c) * n + j0 + i];
+            }
+            __syncthreads();
         }
-        __syncthreads();
         if (warp < nr) {
             T v = lane < jb ? sx[(j0 + lane) * R + warp] : Cx<T>::mk(0, 0);
             for (int c = 0; c < jb; ++c) {
                 T xc = Cx<T>::mk(__shfl_sync(0xffffffff, v.x, c), __shfl_sync(0xffffffff, v.y, c));
-                if (lane > c && lane < jb) v = fms(v, sD[c][lane], xc);
+                if (lane > c && lane < jb) v = fms(v, widen<T>(sD[c * kNB + lane]), xc);
             }
             if (lane < jb) sx[(j0 + lane) * R + warp] = v;
         }
         __syncthreads();
-        for (int i = j0 + jb + tid; i < n; i += blockDim.x) {
-            T acc[RM];
-#pragma unroll
-            for (int q = 0; q < RM; ++q)
-                if (q < nr) acc[q] = sx[i * R + q];
-#pragma unroll 8
-            for (int c = 0; c < jb; ++c) {
-                const T l = widen<T>(a[(size_t)(j0 + c) * n + i]);
+        if (vec) {
+            const bool more = j0 + kNB < n;
+            if (more) fetch_diag(j0 + kNB, kNB, dreg);
+            for (int i = j0 + kNB + 2 * tid; i < n; i += 2 * blockDim.x) {
+                T acc0 = sx[i], acc1 = sx[i + 1];
+                block_pair_update<T, TF>(a + (size_t)j0 * n + i, n, sx + j0, acc0, acc1);
+                sx[i] = acc0;
+                sx[i + 1] = acc1;
+            }
+            __syncthreads();
+            if (more) store_diag(dreg);
+        } else {
+            for (int i = j0 + jb + tid; i < n; i += blockDim.x) {
+                T acc[RM];
 #pragma unroll
                 for (int q = 0; q < RM; ++q)
-                    if (q < nr) acc[q] = fms(acc[q], l, sx[(j0 + c) * R + q]);
-            }
+                    if (q < nr) acc[q] = sx[i * R + q];
+#pragma unroll 8
+                for (int c = 0; c < jb; ++c) {
+                    const T l = widen<T>(a[(size_t)(j0 + c) * n + i]);
 #pragma unroll
-            for (int q = 0; q < RM; ++q)
-                if (q < nr) sx[i * R + q] = acc[q];
+                    for (int q = 0; q < RM; ++q)
+                        if (q < nr) acc[q] = fms(acc[q], l, sx[(j0 + c) * R + q]);
+                }
+#pragma unroll
+                for (int q = 0; q < RM; ++q)
+                    if (q < nr) sx[i * R + q] = acc[q];
+            }
         }
         __syncthreads();
     }
     // backward: U x = y
     const int nblk = (n + kNB - 1) / kNB;
+    if (vec) {
+        fetch_diag((nblk - 1) * kNB, kNB, dreg);
+        store_diag(dreg);
+        __syncthreads();
+    }
     for (int bi = nblk - 1; bi >= 0; --bi) {
         const int j0 = bi * kNB, jb = min(kNB, n - j0);
-        for (int idx = tid; idx < jb * jb; idx += blockDim.x) {
-            int c = idx / jb, i = idx % jb;
-            sD[c][i] = widen<T>(a[(size_t)(j0 + c) * n + j0 + i]);
+        if (!vec) {
+            for (int idx = tid; idx < jb * jb; idx += blockDim.x) {
+                const int c = idx / jb, i = idx % jb;
+                sD[c * kNB + i] = a[(size_t)(j0 + c) * n + j0 + i];
+            }
+            __syncthreads();
         }
-        __syncthreads();
         if (warp < nr) {
             T v = lane < jb ? sx[(j0 + lane) * R + warp] : Cx<T>::mk(0, 0);
             for (int c = jb - 1; c >= 0; --c) {
-                if (lane == c) v = mul(v, rcp(sD[c][c]));
+                if (lane == c) v = mul(v, rcp(widen<T>(sD[c * kNB + c])));
                 T xc = Cx<T>::mk(__shfl_sync(0xffffffff, v.x, c), __shfl_sync(0xffffffff, v.y, c));
-                if (lane < c) v = fms(v, sD[c][lane], xc);
+                if (lane < c) v = fms(v, widen<T>(sD[c * kNB + lane]), xc);
             }
             if (lane < jb) sx[(j0 + lane) * R + warp] = v;
         }
         __syncthreads();
-        for (int i = tid; i < j0; i += blockDim.x) {
-            T acc[RM];
-#pragma unroll
-            for (int q = 0; q < RM; ++q)
-                if (q < nr) acc[q] = sx[i * R + q];
-#pragma unroll 8
-            for (int c = 0; c < jb; ++c) {
-                const T u = widen<T>(a[(size_t)(j0 + c) * n + i]);
+        if (vec) {
+            if (bi > 0) fetch_diag(j0 - kNB, kNB, dreg);
+            for (int i = 2 * tid; i < j0; i += 2 * blockDim.x) {
+                T acc0 = sx[i], acc1 = sx[i + 1];
+                block_pair_update<T, TF>(a + (size_t)j0 * n + i, n, sx + j0, acc0, acc1);
+                sx[i] = acc0;
+                sx[i + 1] = acc1;
+            }
+            __syncthreads();
+            if (bi > 0) store_diag(dreg);
+        } else {
+            for (int i = tid; i < j0; i += blockDim.x) {
+                T acc[RM];
 #pragma unroll
                 for (int q = 0; q < RM; ++q)
-                    if (q < nr) acc[q] = fms(acc[q], u, sx[(j0 + c) * R + q]);
-            }
+                    if (q < nr) acc[q] = sx[i * R + q];
+#pragma unroll 8
+                for (int c = 0; c < jb; ++c) {
+                    const T u = widen<T>(a[(size_t)(j0 + c) * n + i]);
 #pragma unroll
-            for (int q = 0; q < RM; ++q)
-                if (q < nr) sx[i * R + q] = acc[q];
+                    for (int q = 0; q < RM; ++q)
+                        if (q < nr) acc[q] = fms(acc[q], u, sx[(j0 + c) * R + q]);
+                }
+#pragma unroll
+                for (int q = 0; q < RM; ++q)
+                    if (q < nr) sx[i * R + q] = acc[q];
+            }
         }
         __syncthreads();
     }
@@ -592,6 +670,29 @@ __global__ void add_correction_kernel(int64_t count, int64_t per_matrix, const f
 
 }  // namespace
 
+// Swap sequence -> row permutation, in place: piv[b][j] = row swapped with row
+// j at step j becomes perm[b][i] = original row that ends in row i (replayed by
+// one thread per matrix on a shared-memory index array).
+__global__ void perm_kernel(int n, int* piv) {
+    extern __shared__ int sp[];
+    int* p = piv + (size_t)blockIdx.x * n;
+    int* sw = sp + n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        sp[i] = i;
+        sw[i] = p[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int j = 0; j < n; ++j) {
+            const int q = sw[j];
+            const int t = sp[j];
+            sp[j] = sp[q];
+            sp[q] = t;
+        }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = sp[i];
+}
+
 template <typename T>
 cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s) {
     for (int k0 = 0; k0 < n; k0 += kNB) {
@@ -631,6 +732,13 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
             count_launch();
         }
     }
+    const size_t smq = 2 * sizeof(int) * (size_t)n;
+    if (smq > 48 * 1024) {
+        cudaError_t e = allow_max_smem(perm_kernel);
+        if (e != cudaSuccess) return e;
+    }
+    perm_kernel<<<batch, 256, smq, s>>>(n, piv);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -638,13 +746,13 @@ template <typename T, typename TF>
 cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int* piv, T* B,
                              cudaStream_t s, const int* active) {
     // right-hand sides per CTA: up to kSolveR, as many as fit in shared memory
-    // (about 200 KB for the group and the pivots)
+    // (about 200 KB for the group)
     int R = std::min(nrhs, kSolveR);
-    while (R > 1 && (sizeof(T) * (size_t)R + sizeof(int)) * (size_t)n > 200 * 1024) --R;
+    while (R > 1 && sizeof(T) * (size_t)R * (size_t)n > 200 * 1024) --R;
     dim3 g(batch, (nrhs + R - 1) / R);
-    // dynamic: right-hand sides + pivots; static: the 32 x 33 diagonal block
-    size_t sm = (sizeof(T) * (size_t)R + sizeof(int)) * (size_t)n;
-    const bool big = sm + sizeof(T) * kNB * (kNB + 1) > 48 * 1024;
+    // dynamic: right-hand sides; static: the 32 x 32 diagonal block
+    size_t sm = sizeof(T) * (size_t)R * (size_t)n;
+    const bool big = sm + sizeof(TF) * kNB * kNB > 48 * 1024;
     if (R == 1) {   // the common single-wave case, without the group loops
         if (big) {
             cudaError_t e = allow_max_smem(lu_solve_kernel<T, TF, 1>);

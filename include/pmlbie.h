@@ -55,6 +55,8 @@ extern "C" {
 /* generating-curve kinds */
 #define PMLBIE_CURVE_GAUSS_BUMP 0   /* z = h (e^{-r^2/w} - e^{-R^2/w})/(1 - e^{-R^2/w}), r <= R; flat to B */
 #define PMLBIE_CURVE_POLYLINE   1   /* vertices (rho, z) from the axis; flat to B appended if needed     */
+#define PMLBIE_CURVE_WAVY_DENT  2   /* Sec. 5 Example 2: rho = f sin(pi s/2), z = -f cos(pi s/2),
+                                       f = R (1 - eps sin(m pi s)), s in [0, 1]; flat to B            */
 
 /* arithmetic of a solve */
 #define PMLBIE_FP64  0   /* everything in FP64 (complex128)                          */
@@ -75,6 +77,8 @@ typedef struct {
     const double* vertices;   /* polyline: n_vertices (rho, z) pairs, host memory    */
     int      taylor_L;        /* degree of the cH_1 / cH_3 substitution (Sec. 4.3: 5) */
     double   split_c;         /* close-pair threshold eta_s = split_c * 2 pi / M      */
+    double   wavy_R, wavy_eps;  /* wavy dent (kind 2): 0 < R <= a1, 0 <= eps < 1        */
+    int      wavy_m;            /* wavy dent: half-waves, 1..64 (Example 2: 1, 0.1, 3)  */
 } pmlbie_params;
 
 /* Report of a solve (filled when the pointer is not NULL). */

@@ -50,11 +50,14 @@ class Params:
     T: float = 1.0                 # PML thickness
     S: float = 3.0                 # PML strength
     p: int = 6                     # PML profile and grading exponent
-    curve: str = "gauss"           # "gauss" | "polyline"
+    curve: str = "gauss"           # "gauss" | "polyline" | "wavy"
     bump_h: float = 0.2
     bump_w: float = 0.5            # exp(-r^2 / bump_w)
     bump_R: float = 1.0
     vertices: Optional[List[Tuple[float, float]]] = None  # polyline (rho, z), from the axis
+    wavy_R: float = 1.0            # wavy dent (Sec. 5, Example 2): radius,
+    wavy_eps: float = 0.1          # relative amplitude
+    wavy_m: int = 3                # and number of half-waves of the perturbation
     polar: float = np.pi / 6.0     # incidence polar angle phi_inc
     azimuth: float = 0.0           # incidence azimuth theta_inc
     taylor_L: int = 5              # order of the cH_1 / cH_3 substitution (Sec. 4.3)
@@ -79,6 +82,14 @@ class _Segment:
 
     def eval(self, s):
         s = np.asarray(s, dtype=float)
+        if self.kind == "wavy":
+            # Sec. 5, Example 2: rho = f sin(pi s / 2), z = -f cos(pi s / 2),
+            # f = R (1 - eps sin(m pi s)), from (0, -R) on the axis to (R, 0)
+            R, eps, m = self.data
+            f = R * (1.0 - eps * np.sin(m * np.pi * s))
+            df = -R * eps * m * np.pi * np.cos(m * np.pi * s)
+            c, si = np.cos(0.5 * np.pi * s), np.sin(0.5 * np.pi * s)
+            return f * si, -f * c, df * si + 0.5 * np.pi * f * c, -df * c + 0.5 * np.pi * f * si
         if self.kind == "gauss":
             h, w, R = self.data
             rho = R * s
@@ -93,6 +104,18 @@ class _Segment:
     def offset(self, s, sc, end):
         """r(s) - r(0) (end = 0) or r(s) - r(1) (end = 1), free of cancellation;
         sc = 1 - s computed separately."""
+        if self.kind == "wavy":
+            # 1 - cos(x) = 2 sin^2(x/2); near s = 1, sin(m pi s) = (-1)^(m+1) sin(m pi sc)
+            # (m integer) and sin(pi s / 2) = cos(pi sc / 2)
+            R, eps, m = self.data
+            if end == 0:
+                rho, _, _, _ = self.eval(s)
+                return rho, 2.0 * R * np.sin(0.25 * np.pi * s) ** 2 + R * eps * np.sin(m * np.pi * s) * np.cos(
+                    0.5 * np.pi * s)
+            sm = (-1.0) ** (m + 1) * np.sin(m * np.pi * sc)
+            f = R * (1.0 - eps * sm)
+            return (-2.0 * R * np.sin(0.25 * np.pi * sc) ** 2 - R * eps * sm * np.cos(0.5 * np.pi * sc),
+                    -f * np.sin(0.5 * np.pi * sc))
         if self.kind == "gauss":
             h, w, R = self.data
             c = h / (1.0 - np.exp(-R * R / w))
@@ -117,6 +140,9 @@ def build_segments(P: Params):
     if P.curve == "gauss":
         segs.append(_Segment("gauss", (P.bump_h, P.bump_w, P.bump_R)))
         segs.append(_Segment("line", ((P.bump_R, 0.0), (L, 0.0))))
+    elif P.curve == "wavy":
+        segs.append(_Segment("wavy", (P.wavy_R, P.wavy_eps, int(P.wavy_m))))
+        segs.append(_Segment("line", ((P.wavy_R, 0.0), (L, 0.0))))
     elif P.curve == "polyline":
         V = list(P.vertices)
         for a, b in zip(V[:-1], V[1:]):

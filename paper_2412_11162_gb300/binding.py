@@ -21,6 +21,7 @@ PMLBIE_ENAN = -6
 PMLBIE_ENODEV = -7
 PMLBIE_CURVE_GAUSS_BUMP = 0
 PMLBIE_CURVE_POLYLINE = 1
+PMLBIE_CURVE_WAVY_DENT = 2
 PMLBIE_FP64 = 0
 PMLBIE_MIXED = 1
 
@@ -32,7 +33,8 @@ class pmlbie_params(ctypes.Structure):
                 ("curve_kind", ctypes.c_int), ("bump_h", ctypes.c_double), ("bump_w", ctypes.c_double),
                 ("bump_R", ctypes.c_double), ("n_vertices", ctypes.c_int),
                 ("vertices", ctypes.POINTER(ctypes.c_double)), ("taylor_L", ctypes.c_int),
-                ("split_c", ctypes.c_double)]
+                ("split_c", ctypes.c_double), ("wavy_R", ctypes.c_double), ("wavy_eps", ctypes.c_double),
+                ("wavy_m", ctypes.c_int)]
 
 
 class pmlbie_report(ctypes.Structure):
@@ -130,7 +132,7 @@ def _stream(stream):
 
 
 def make_params(k1, k2, N, M, a1=2.5, T=1.0, S=3.0, p=6, curve="gauss", bump_h=0.2, bump_w=0.5,
-                bump_R=1.0, vertices=None, taylor_L=5, split_c=8.0):
+                bump_R=1.0, vertices=None, taylor_L=5, split_c=8.0, wavy_R=1.0, wavy_eps=0.1, wavy_m=3):
     import numpy as np
     P = pmlbie_params()
     P.struct_size = ctypes.sizeof(pmlbie_params)
@@ -138,8 +140,11 @@ def make_params(k1, k2, N, M, a1=2.5, T=1.0, S=3.0, p=6, curve="gauss", bump_h=0
     P.bump_h, P.bump_w, P.bump_R = bump_h, bump_w, bump_R
     P.taylor_L, P.split_c = taylor_L, split_c
     keep = None
+    P.wavy_R, P.wavy_eps, P.wavy_m = wavy_R, wavy_eps, wavy_m
     if curve == "gauss":
         P.curve_kind = PMLBIE_CURVE_GAUSS_BUMP
+    elif curve == "wavy":
+        P.curve_kind = PMLBIE_CURVE_WAVY_DENT
     else:
         P.curve_kind = PMLBIE_CURVE_POLYLINE
         keep = np.ascontiguousarray(np.asarray(vertices, dtype=np.float64).reshape(-1))

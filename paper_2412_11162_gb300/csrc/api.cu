@@ -237,6 +237,10 @@ int pmlbie_create(const pmlbie_params* P, pmlbie_problem** out) {
     if (P->curve_kind == PMLBIE_CURVE_GAUSS_BUMP) {
         if (!(P->bump_R > 0) || !(P->bump_w > 0) || !(P->bump_R < P->a1))
             return fail(PMLBIE_EINVAL, "bump needs 0 < R < a1 and w > 0");
+    } else if (P->curve_kind == PMLBIE_CURVE_WAVY_DENT) {
+        if (!(P->wavy_R > 0) || !(P->wavy_R <= P->a1) || !(P->wavy_eps >= 0 && P->wavy_eps < 1) ||
+            P->wavy_m < 1 || P->wavy_m > 64)
+            return fail(PMLBIE_EINVAL, "wavy dent needs 0 < R <= a1, 0 <= eps < 1, 1 <= m <= 64");
     } else if (P->curve_kind == PMLBIE_CURVE_POLYLINE) {
         if (P->n_vertices < 2 || !P->vertices) return fail(PMLBIE_EINVAL, "polyline needs >= 2 vertices");
         if (P->vertices[0] != 0.0) return fail(PMLBIE_EINVAL, "polyline must start on the axis (rho = 0)");

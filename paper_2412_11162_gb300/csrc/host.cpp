@@ -170,11 +170,23 @@ struct Pml {
 // Curve segments r(s), s in [0, 1]
 // ---------------------------------------------------------------------------
 struct Segment {
-    bool gauss = false;
+    bool gauss = false, wavy = false;
     double h = 0, w = 1, R = 1;          // Gaussian bump
+    double wR = 1, eps = 0;              // wavy dent: radius, relative amplitude,
+    int wm = 1;                          // half-waves of the perturbation
     double r0 = 0, z0 = 0, r1 = 0, z1 = 0;  // line
     void eval(double s, double& rho, double& z, double& drho, double& dz) const {
-        if (gauss) {
+        if (wavy) {
+            // Sec. 5, Example 2: rho = f sin(pi s/2), z = -f cos(pi s/2),
+            // f = R (1 - eps sin(m pi s)), from (0, -R) on the axis to (R, 0)
+            const double f = wR * (1.0 - eps * std::sin(wm * kPi * s));
+            const double df = -wR * eps * wm * kPi * std::cos(wm * kPi * s);
+            const double c = std::cos(0.5 * kPi * s), si = std::sin(0.5 * kPi * s);
+            rho = f * si;
+            z = -f * c;
+            drho = df * si + 0.5 * kPi * f * c;
+            dz = -df * c + 0.5 * kPi * f * si;
+        } else if (gauss) {
             rho = R * s;
             double e0 = std::exp(-R * R / w), g = std::exp(-rho * rho / w);
             z = h * (g - e0) / (1.0 - e0);
@@ -189,7 +201,21 @@ struct Segment {
     }
     // r(s) - r(0) (end 0) or r(s) - r(1) (end 1) without cancellation; sc = 1 - s
     void offset(double s, double sc, int end, double& orho, double& oz) const {
-        if (gauss) {
+        if (wavy) {
+            // 1 - cos x = 2 sin^2(x/2); near s = 1, sin(m pi s) = (-1)^(m+1) sin(m pi sc)
+            // and sin(pi s/2) = cos(pi sc/2)
+            if (end == 0) {
+                double z, dr, dz;
+                eval(s, orho, z, dr, dz);
+                const double q = std::sin(0.25 * kPi * s);
+                oz = 2.0 * wR * q * q + wR * eps * std::sin(wm * kPi * s) * std::cos(0.5 * kPi * s);
+            } else {
+                const double sm = ((wm & 1) ? 1.0 : -1.0) * std::sin(wm * kPi * sc);
+                const double q = std::sin(0.25 * kPi * sc);
+                orho = -2.0 * wR * q * q - wR * eps * sm * std::cos(0.5 * kPi * sc);
+                oz = -wR * (1.0 - eps * sm) * std::sin(0.5 * kPi * sc);
+            }
+        } else if (gauss) {
             double c = h / (1.0 - std::exp(-R * R / w));
             if (end == 0) {
                 orho = R * s;
@@ -534,6 +560,17 @@ int build_tables(pmlbie_problem* prob) {
         C.segs.push_back(g);
         Segment f;
         f.r0 = P.bump_R;
+        f.r1 = Lr;
+        C.segs.push_back(f);
+    } else if (P.curve_kind == PMLBIE_CURVE_WAVY_DENT) {
+        Segment d;
+        d.wavy = true;
+        d.wR = P.wavy_R;
+        d.eps = P.wavy_eps;
+        d.wm = P.wavy_m;
+        C.segs.push_back(d);
+        Segment f;
+        f.r0 = P.wavy_R;
         f.r1 = Lr;
         C.segs.push_back(f);
     } else {

@@ -498,3 +498,30 @@ def test_pml_truncation_error_decays_exponentially():
         errs.append(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref))
     assert errs[0] < 1e-2 and errs[-1] < 3e-6, errs
     assert errs[1] < errs[0] / 2 and errs[2] < errs[1] / 5 and errs[3] < errs[2] / 5, errs
+
+
+def test_wavy_dent_curve():
+    """Sec. 5 Example 2 generating curve: rho(s) = [1 - 0.1 sin 3 pi s] sin(pi s/2),
+    z(s) = -[1 - 0.1 sin 3 pi s] cos(pi s/2): the printed values at s = 0, 1/2, 1,
+    derivatives against central differences, and the cancellation-free offsets
+    from both ends against direct differences."""
+    from oracle.problem import build_segments
+    P = Params(k1=2 * np.pi, k2=2.4 * np.pi, a1=2.0, T=2.0, S=2.0, curve="wavy")
+    seg = build_segments(P)[0]
+    r, z, dr, dz = seg.eval(np.array([0.0, 0.5, 1.0]))
+    c = np.sqrt(0.5)
+    assert np.allclose(r, [0.0, 1.1 * c, 1.0], atol=1e-15) and np.allclose(z, [-1.0, -1.1 * c, 0.0], atol=1e-15)
+    s = np.linspace(0.05, 0.95, 7)
+    h = 1e-6
+    rp, zp, _, _ = seg.eval(s + h)
+    rm, zm, _, _ = seg.eval(s - h)
+    _, _, dr, dz = seg.eval(s)
+    assert np.abs((rp - rm) / (2 * h) - dr).max() < 1e-8 and np.abs((zp - zm) / (2 * h) - dz).max() < 1e-8
+    s = np.array([1e-9, 1e-4, 0.3, 0.7, 1 - 1e-4, 1 - 1e-9])
+    r, z, _, _ = seg.eval(s)
+    for end, (r0, z0) in ((0, (0.0, -1.0)), (1, (1.0, 0.0))):
+        orho, oz = seg.offset(s, 1 - s, end)
+        assert np.abs(orho - (r - r0)).max() < 1e-15 and np.abs(oz - (z - z0)).max() < 1e-15
+    # near each end the offset is O(distance) with full relative accuracy
+    orho, oz = seg.offset(np.array([1e-12]), np.array([1 - 1e-12]), 0)
+    assert abs(orho[0] / (0.5 * np.pi * 1e-12) - 1) < 1e-6 and abs(oz[0] / (0.3 * np.pi * 1e-12) - 1) < 1e-6

@@ -48,10 +48,11 @@ def prob():
     return Problem(CFG1["k1"], CFG1["k2"], CFG1["N"], CFG1["M"])
 
 
-def check_point(out, r, ref, tol, label):
-    """Column r of the GPU outputs against the oracle's point-source solution."""
+def check_point(out, r, ref, tol, label, sol=None):
+    """Column r of the GPU outputs against the oracle's point-source solution
+    (sol: the oracle Solution whose matrices ref uses; default the N = 128 one)."""
     from test_gpu_parity import mode_conditioning
-    kap = mode_conditioning(oracle_solution(**CFG1))
+    kap = mode_conditioning(sol if sol is not None else oracle_solution(**CFG1))
     g = {k: v[:, :, r].cpu().numpy() for k, v in out.items()}
     for got, want in ((g["u1"] - g["u2"], ref.u1 - ref.u2), (g["phi1"] - g["phi2"], ref.phi1 - ref.phi2)):
         assert _rel(got, want) <= 1e-13, (label, "jumps", _rel(got, want))

@@ -389,11 +389,14 @@ __global__ void gemm_update_kernel(int n, int k0, int kb, T* A) {
 // right-hand sides); B is [b][n][nrhs].  The group's right-hand sides live in
 // shared memory ([row][R]) for the whole solve, so each factor element read
 // from memory serves all of them; each 32-row diagonal block is solved by one
-// warp per right-hand side, then the rows outside it are updated.  With one
-// right-hand side the update takes two adjacent rows per thread and all 32
-// column loads of a block at once (16-byte loads for complex64 factors), so
-// that enough bytes are in flight to stream the factors at HBM speed; the
-// next diagonal block is fetched into registers during the update.  Matrices
+// warp per right-hand side, then the rows outside it are updated.  When n is
+// a multiple of 32 (and, with several right-hand sides, the arithmetic is
+// complex64) the update takes two adjacent rows per thread and issues a
+// block's column loads in chunks (256 bytes per thread with one right-hand
+// side; 16-byte loads for complex64 factors), so that enough bytes are in
+// flight to stream the factors at HBM speed; each factor pair then serves
+// every right-hand side of the group, and the next diagonal block is fetched
+// into registers during the update.  Matrices
 // whose active flag is 0 are skipped (converged modes).
 constexpr int kSolveR = 8;
 
@@ -411,11 +414,13 @@ __device__ __forceinline__ void load_pair(const double2* p, double2& u, double2&
     v = __ldg(p + 1);
 }
 
-// x[i], x[i+1] -= sum_{c < kNB} F[c][i..i+1] x[c0 + c]  (a full 32-column block),
+// x[i][q], x[i+1][q] -= sum_{c < kNB} F[c][i..i+1] xs[c][q] for the group's
+// right-hand sides q < nr (a full 32-column block; xs row stride R), factor
 // loads issued in chunks of 256 bytes per thread
-template <typename T, typename TF>
-__device__ __forceinline__ void block_pair_update(const TF* col, int n, const T* xs, T& acc0, T& acc1) {
-    constexpr int CH = (int)(256 / (2 * sizeof(TF)));
+template <typename T, typename TF, int RM>
+__device__ __forceinline__ void block_pair_update(const TF* col, int n, const T* xs, int R, int nr, T (&acc0)[RM],
+                                                  T (&acc1)[RM]) {
+    constexpr int CH = RM == 1 ? (int)(256 / (2 * sizeof(TF))) : 2;
 #pragma unroll
     for (int c0 = 0; c0 < kNB; c0 += CH) {
         TF l0[CH], l1[CH];
@@ -423,9 +428,14 @@ __device__ __forceinline__ void block_pair_update(const TF* col, int n, const T*
         for (int c = 0; c < CH; ++c) load_pair(col + (size_t)(c0 + c) * n, l0[c], l1[c]);
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
-            const T xc = xs[c0 + c];
-            acc0 = fms(acc0, widen<T>(l0[c]), xc);
-            acc1 = fms(acc1, widen<T>(l1[c]), xc);
+            const T f0 = widen<T>(l0[c]), f1 = widen<T>(l1[c]);
+#pragma unroll
+            for (int q = 0; q < RM; ++q)
+                if (q < nr) {
+                    const T xc = xs[(c0 + c) * R + q];
+                    acc0[q] = fms(acc0[q], f0, xc);
+                    acc1[q] = fms(acc1[q], f1, xc);
+                }
         }
     }
 }
@@ -463,7 +473,9 @@ __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, 
         for (int t = 0; t < kDiagPer; ++t) reinterpret_cast<float4*>(sD)[tid + t * 512] = reg[t];
     };
     float4 dreg[kDiagPer];
-    const bool vec = RM == 1 && (n % kNB) == 0;   // full blocks only: the pair path
+    // the pair path: full blocks only, and with several right-hand sides only
+    // for complex64 accumulators (register budget of 512 threads)
+    const bool vec = (n % kNB) == 0 && (RM == 1 || sizeof(T) == 8);
     // forward: L y = x (unit diagonal)
     if (vec) {
         fetch_diag(0, kNB, dreg);
@@ -492,10 +504,14 @@ __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, 
             const bool more = j0 + kNB < n;
             if (more) fetch_diag(j0 + kNB, kNB, dreg);
             for (int i = j0 + kNB + 2 * tid; i < n; i += 2 * blockDim.x) {
-                T acc0 = sx[i], acc1 = sx[i + 1];
-                block_pair_update<T, TF>(a + (size_t)j0 * n + i, n, sx + j0, acc0, acc1);
-                sx[i] = acc0;
-                sx[i + 1] = acc1;
+                T acc0[RM], acc1[RM];
+#pragma unroll
+                for (int q = 0; q < RM; ++q)
+                    if (q < nr) acc0[q] = sx[i * R + q], acc1[q] = sx[(i + 1) * R + q];
+                block_pair_update<T, TF, RM>(a + (size_t)j0 * n + i, n, sx + (size_t)j0 * R, R, nr, acc0, acc1);
+#pragma unroll
+                for (int q = 0; q < RM; ++q)
+                    if (q < nr) sx[i * R + q] = acc0[q], sx[(i + 1) * R + q] = acc1[q];
             }
             __syncthreads();
             if (more) store_diag(dreg);
@@ -548,10 +564,14 @@ __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, 
         if (vec) {
             if (bi > 0) fetch_diag(j0 - kNB, kNB, dreg);
             for (int i = 2 * tid; i < j0; i += 2 * blockDim.x) {
-                T acc0 = sx[i], acc1 = sx[i + 1];
-                block_pair_update<T, TF>(a + (size_t)j0 * n + i, n, sx + j0, acc0, acc1);
-                sx[i] = acc0;
-                sx[i + 1] = acc1;
+                T acc0[RM], acc1[RM];
+#pragma unroll
+                for (int q = 0; q < RM; ++q)
+                    if (q < nr) acc0[q] = sx[i * R + q], acc1[q] = sx[(i + 1) * R + q];
+                block_pair_update<T, TF, RM>(a + (size_t)j0 * n + i, n, sx + (size_t)j0 * R, R, nr, acc0, acc1);
+#pragma unroll
+                for (int q = 0; q < RM; ++q)
+                    if (q < nr) sx[i * R + q] = acc0[q], sx[(i + 1) * R + q] = acc1[q];
             }
             __syncthreads();
             if (bi > 0) store_diag(dreg);

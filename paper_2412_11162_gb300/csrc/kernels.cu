@@ -916,23 +916,30 @@ __global__ void rhs_kernel(RhsArgs a) {
 }
 
 // B_n = [0; A_n[N:2N, 0:N] b1 + A_n[N:2N, N:2N] b2], B laid out [mode][2N][rhs]
-__global__ void block_rhs_kernel(int N, int nmodes, int nrhs, const double2* A, const double2* b1,
-                                 const double2* b2, double2* B) {
-    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    size_t n2 = 2 * (size_t)N;
-    if (idx >= (size_t)nmodes * n2 * nrhs) return;
-    int r = (int)(idx % nrhs);
-    int row = (int)((idx / nrhs) % n2);
-    int t = (int)(idx / (nrhs * n2));
+// and zeroed beforehand.  Grid (lower-half rows x rhs / 256, column chunks of
+// kBrhsCols, modes): each thread sums one chunk of its row and adds it with
+// atomics, so that every mode's half matrix is streamed by many SMs at once.
+constexpr int kBrhsCols = 32;
+__global__ void block_rhs_kernel(int N, int nrhs, const double2* A, const double2* b1, const double2* b2,
+                                 double2* B) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)N * nrhs) return;
+    const int r = (int)(idx % nrhs), row = N + (int)(idx / nrhs);
+    const int t = blockIdx.z;
+    const size_t n2 = 2 * (size_t)N;
+    const int c0 = blockIdx.y * kBrhsCols, c1 = min((int)n2, c0 + kBrhsCols);
+    const double2* An = A + (size_t)t * n2 * n2;
+    const double2* v1 = b1 + (size_t)t * N * nrhs;
+    const double2* v2 = b2 + (size_t)t * N * nrhs;
     double2 acc = c2(0.0, 0.0);
-    if (row >= N) {
-        const double2* An = A + (size_t)t * n2 * n2;
-        for (int c = 0; c < N; ++c) {
-            acc = cadd(acc, cmul(An[(size_t)c * n2 + row], b1[((size_t)t * N + c) * nrhs + r]));
-            acc = cadd(acc, cmul(An[(size_t)(N + c) * n2 + row], b2[((size_t)t * N + c) * nrhs + r]));
-        }
+#pragma unroll 8
+    for (int c = c0; c < c1; ++c) {
+        const double2 v = c < N ? v1[(size_t)c * nrhs + r] : v2[(size_t)(c - N) * nrhs + r];
+        acc = cadd(acc, cmul(An[(size_t)c * n2 + row], v));
     }
-    B[idx] = acc;
+    double* o = reinterpret_cast<double*>(B + ((size_t)t * n2 + row) * nrhs + r);
+    atomicAdd(o, acc.x);
+    atomicAdd(o + 1, acc.y);
 }
 
 __global__ void outputs_kernel(int N, int nmodes, int nrhs, const double2* X, const double2* b1,
@@ -1107,9 +1114,11 @@ cudaError_t launch_rhs(const pmlbie_problem* prob, int n_rhs, int mode_lo, int m
 
 cudaError_t launch_block_rhs(const pmlbie_problem* prob, int n_rhs, int nm, const double2* A,
                              const double2* b1, const double2* b2, double2* B, cudaStream_t s) {
-    int N = prob->P.N;
-    size_t tot = (size_t)nm * 2 * N * n_rhs;
-    block_rhs_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(N, nm, n_rhs, A, b1, b2, B);
+    const int N = prob->P.N;
+    cudaError_t e = cudaMemsetAsync(B, 0, sizeof(double2) * (size_t)nm * 2 * N * n_rhs, s);
+    if (e != cudaSuccess) return e;
+    dim3 g((unsigned)(((size_t)N * n_rhs + 255) / 256), (unsigned)((2 * N + kBrhsCols - 1) / kBrhsCols), nm);
+    block_rhs_kernel<<<g, 256, 0, s>>>(N, n_rhs, A, b1, b2, B);
     count_launch();
     return cudaGetLastError();
 }

@@ -640,9 +640,19 @@ int pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* o, void* dev_
         PMLBIE_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
         limit = (size_t)(0.9 * (double)(fr + prob->ws_bytes));
     }
-    while (chunk > 1 && plan(prob, precision, n_rhs, chunk, nullptr).bytes > limit) chunk = (chunk + 1) / 2;
-    if (plan(prob, precision, n_rhs, chunk, nullptr).bytes > limit)
+    // the largest chunk whose workspace fits (binary search), then chunks of
+    // equal size: each chunk re-samples the kernels, so the count is minimal
+    if (plan(prob, precision, n_rhs, 1, nullptr).bytes > limit)
         return fail(PMLBIE_ENOMEM, "one mode's workspace exceeds the workspace limit");
+    if (plan(prob, precision, n_rhs, chunk, nullptr).bytes > limit) {
+        int ok = 1, bad = chunk;
+        while (bad - ok > 1) {
+            const int mid = ok + (bad - ok) / 2;
+            (plan(prob, precision, n_rhs, mid, nullptr).bytes <= limit ? ok : bad) = mid;
+        }
+        const int nchunks = (hi - lo + ok - 1) / ok;
+        chunk = (hi - lo + nchunks - 1) / nchunks;
+    }
     Workspace w;
     if ((rc = get_workspace(prob, precision, n_rhs, chunk, w))) return rc;
     g_launches = 0;

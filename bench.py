@@ -462,16 +462,19 @@ def run_batched(args, rank, world):
     print(json.dumps(line))
 
 
-def far_flops_per_pair(M):
+def far_flops_per_pair(M, physical=False):
     """Algorithmic FP64 flops of one far node pair in the far-pair kernel
     (fused multiply-add = 2 flops): (M/2 + 1) angle samples of S~ and K~ of
-    both media at 276 flops each (complex distance, square root and
-    reciprocal by Newton-refined reciprocal square roots, two e^{iq} by
-    range reduction + series, kernel products), four even-sequence DFTs of
-    length M at 5 K log2 K + 15 K flops (K = M/2: a K-point complex FFT plus
-    pre- and post-processing), and 16 K flops to weight the 4 K outputs."""
+    both media, four even-sequence DFTs of length M at 5 K log2 K + 15 K
+    flops (K = M/2: a K-point complex FFT plus pre- and post-processing), and
+    16 K flops to weight the 4 K outputs.  A sample costs 276 flops for a pair
+    with a node in the PML (complex distance, square root and reciprocal by
+    Newton-refined reciprocal square roots, two e^{iq} by range reduction +
+    series, complex kernel products) and 128 for a pair of physical nodes
+    (real distance and reciprocal square root, two sin/cos pairs, real
+    products)."""
     K = M // 2
-    return (K + 1) * 276.0 + 4 * (5.0 * K * np.log2(K) + 15.0 * K) + 16.0 * K
+    return (K + 1) * (128.0 if physical else 276.0) + 4 * (5.0 * K * np.log2(K) + 15.0 * K) + 16.0 * K
 
 
 def far_traffic(w):
@@ -509,7 +512,8 @@ def roofline(w, rep, pk, clk):
     # one launch per mode chunk: every launch samples all pairs and angles and
     # transforms them (the flops), and scatters only its chunk's modes
     launches = max(1, rep.chunks)
-    flops = rep.far_pairs * far_flops_per_pair(M)
+    phys = rep.far_pairs_physical
+    flops = phys * far_flops_per_pair(M, True) + (rep.far_pairs - phys) * far_flops_per_pair(M)
     ms1 = rep.ms_far / launches
     ach = flops / (ms1 / 1e3) / 1e12
     traffic = far_traffic(w)

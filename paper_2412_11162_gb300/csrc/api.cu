@@ -692,6 +692,14 @@ int pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* o, void* dev_
         rep->ms_near_laplace = st.ms_near_laplace;
         rep->launches = (int)g_launches;
         rep->far_pairs = (int)std::count(prob->H.cls.begin(), prob->H.cls.end(), (uint8_t)kFar);
+        int phys = 0;
+        const int N = prob->P.N;
+        for (int l = 0; l < N; ++l) {
+            if (prob->H.I[l] != 0.0) continue;
+            for (int m = 0; m < N; ++m)
+                if (prob->H.I[m] == 0.0 && prob->H.cls[(size_t)l * N + m] == (uint8_t)kFar) ++phys;
+        }
+        rep->far_pairs_physical = phys;
         rep->chunks = chunks;
         rep->chunk_modes = chunk;
         rep->gmres_modes = st.gmres_modes;

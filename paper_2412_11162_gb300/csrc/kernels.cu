@@ -373,6 +373,22 @@ __global__ void far_kernel(FarArgs a) {
         const PairGeom g = geo[w];
         double2* buf = bufs + w * (4 * S1 + 2 * K);
         const double2 sc = cs[j];
+        if (g.d2.y == 0.0 && g.rr.y == 0.0 && g.nd0.y == 0.0 && g.nds.y == 0.0) {
+            // both nodes physical: real distance, e^{iq} = cos q + i sin q
+            const double D2 = fma(4.0 * sc.x, g.rr.x, g.d2.x);
+            const double iR = frsqrt(D2), R = D2 * iR;
+            const double Dk = -kInv4Pi * (fma(g.nds.x, sc.x, g.nd0.x) * (iR * iR * iR));
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const double q = (r == 0 ? a.w1 : a.w2) * R, Dr = r == 0 ? Dk : -Dk;
+                double sn, cn;
+                fsincos(q, &sn, &cn);
+                const double f = kInv4Pi * iR;
+                buf[(2 * r) * S1 + j] = c2(f * cn, f * sn);
+                buf[(2 * r + 1) * S1 + j] = c2(Dr * fma(q, sn, cn), Dr * fma(-q, cn, sn));   // e (1 - i q)
+            }
+            continue;
+        }
         const double2 D2 = cadd(g.d2, cscale(g.rr, 4.0 * sc.x));
         double2 R, iR;
         fcsqrt_rcp(D2, R, iR);

@@ -503,6 +503,64 @@ __device__ void complex_agm_KE(double2 k2, double2 kp, double2& K, double2& E) {
     E = cmul(K, csub(c2(1.0, 0.0), sum));
 }
 
+// The same for a pair of physical nodes, where chi > 1 and every factor are
+// real: real AGM, real recurrences (the values are stored with zero
+// imaginary parts).
+__device__ void laplace_modes_real(const NearPair& q, int M, double2* Z, double2* Dd) {
+    const double rr2 = 2.0 * q.rr.x;
+    const double chim1 = q.d2.x / rr2, chi = 1.0 + chim1, chip1 = 2.0 + chim1;
+    const double k2 = 2.0 / chip1, kp = sqrt(chim1 / chip1);
+    double a = 1.0, b = kp, sum = 0.5 * k2, pw = 0.5;
+    for (int it = 0; it < 64; ++it) {
+        const double an = 0.5 * (a + b), bn = sqrt(a * b), cn = 0.5 * (a - b);
+        pw *= 2.0;
+        sum += pw * cn * cn;
+        a = an;
+        b = bn;
+        if (fabs(cn) < 1e-17 * fabs(a)) break;
+    }
+    const double K = 0.5 * kPi / a, E = K * (1.0 - sum);
+    const double sq = sqrt(chip1);
+    const double c0 = 4.0 * K / sq, c1 = chi * c0 - 4.0 * sq * E;
+    const double reeta = log(chi + sqrt(chim1) * sq);      // acosh(chi)
+    if (reeta * M < 3.5) {
+        double zm1 = c0, zm = c1;
+        Z[0] = c2(c0, 0.0);
+        if (M > 1) Z[1] = c2(c1, 0.0);
+        for (int m = 1; m + 1 < M; ++m) {
+            const double zp = (4.0 * m * chi * zm - (2.0 * m - 1.0) * zm1) / (2.0 * m + 1.0);
+            Z[m + 1] = c2(zp, 0.0);
+            zm1 = zm;
+            zm = zp;
+        }
+    } else {
+        const int ms = M + (int)ceil(20.0 / reeta);
+        double y1 = 0.0, y0 = 1e-200;
+        for (int m = ms; m >= 1; --m) {
+            const double ym1 = (4.0 * m * chi * y0 - (2.0 * m + 1.0) * y1) / (2.0 * m - 1.0);
+            y1 = y0;
+            y0 = ym1;
+            if (m - 1 < M) Z[m - 1] = c2(ym1, 0.0);
+            if (m - 1 >= M && fabs(y0) > 1e100) {
+                y0 *= 1e-100;
+                y1 *= 1e-100;
+            }
+        }
+        const double f = c0 / Z[0].x;
+        for (int m = 0; m < M; ++m) Z[m].x *= f;
+    }
+    const double A = q.nuc_r.x * q.drt.x - q.nuc_z.x * q.dz - q.nuc_r.x * q.d2.x / (2.0 * q.rho_s.x);
+    const double B = q.nuc_r.x * q.rho_t.x;
+    const double s2 = sqrt(rr2);
+    const double iz = kInv4Pi / s2, id = -kInv4Pi / (s2 * s2 * s2), den = 1.0 / (chim1 * chip1);
+    for (int m = 0; m + 1 < M; ++m) {
+        const double cm = Z[m].x, cn = Z[m + 1].x;
+        const double dm = (2.0 * m + 1.0) * (chi * cm - cn) * den;
+        Dd[m] = c2(id * (A * dm + B * cm), 0.0);
+        Z[m] = c2(iz * cm, 0.0);
+    }
+}
+
 __global__ void near_laplace_kernel(NearArgs a) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.npairs) return;
@@ -511,6 +569,11 @@ __global__ void near_laplace_kernel(NearArgs a) {
     const int M = a.M;
     double2* Z = a.zd + (size_t)p * 2 * M;
     double2* Dd = Z + M;
+    if (q.d2.y == 0.0 && q.rr.y == 0.0 && q.rho_t.y == 0.0 && q.rho_s.y == 0.0 && q.drt.y == 0.0 &&
+        q.nuc_r.y == 0.0 && q.nuc_z.y == 0.0) {
+        laplace_modes_real(q, M, Z, Dd);
+        return;
+    }
     double2 rr2 = cscale(q.rr, 2.0);
     double2 chim1 = cdiv(q.d2, rr2);                 // chi - 1
     double2 chi = c2(1.0 + chim1.x, chim1.y);

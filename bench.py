@@ -44,6 +44,45 @@ METRIC = "modal kernel entries/s and solve s/problem, mixed vs FP64 GPU at 1e-6 
 UNIT = "entries/s"
 
 
+# ----------------------------------------------------------------------------
+# multi-rank host logic (one process per GPU, independent problems: no
+# data-path collective; the timing takes the slowest rank)
+# ----------------------------------------------------------------------------
+def init_dist(world, backend="nccl", device=None):
+    """The process group for world > 1 (None for one rank)."""
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if device is not None:
+        dist.init_process_group(backend, device_id=device)
+    else:
+        dist.init_process_group(backend)
+    return dist
+
+
+def max_over_ranks(ms, dist, device="cuda"):
+    """The largest per-rank time (the job's time); ms itself for one rank."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_value(world, units_per_rank, ms):
+    """Whole-job throughput: every rank processes units_per_rank in ms."""
+    return world * units_per_rank / (ms / 1e3)
+
+
+def emit_line(line, rank, out=None):
+    """Rank 0 prints the one JSON line; the other ranks print nothing."""
+    if rank == 0:
+        print(json.dumps(line), file=out or sys.stdout)
+        return True
+    return False
+
+
 def entries_per_problem(w):
     return 4 * w["N"] ** 2 * (w["M"] // 2)
 
@@ -202,10 +241,7 @@ def run_ours(args, rank, world):
     from paper_2412_11162_gb300 import binding as B
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    dist = init_dist(world, "nccl", torch.device("cuda", dev))
     w = WORKLOAD
     kw = dict(a1=w["a1"], T=w["T"], S=w["S"], bump_h=w["bump_h"])
     P = Problem(w["k1"], w["k2"], w["N"], w["M"], **kw)
@@ -235,11 +271,7 @@ def run_ours(args, rank, world):
         clk.mark_end()
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist)
     mixed_out = {k: v.clone() for k, v in outs.items()}
 
     # plain FP64 GPU path on the same problem (1 warm + 2 timed); for N >= 1024
@@ -293,12 +325,12 @@ def run_ours(args, rank, world):
         B.pmlbie_solve_host(Q.handle, B.PMLBIE_MIXED, polar, *pinned, stream=stream)
         Q.close()
     torch.cuda.synchronize()
-    e2e_ms = 1e3 * (time.perf_counter() - t0) / e2e_steps
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / e2e_steps, dist)
     d2h = 4 * int(np.prod(shape)) * 16
 
     last = reps[-1]
     epp = entries_per_problem(w)
-    value = world * epp / (ms / 1e3)
+    value = job_value(world, epp, ms)
     pk = peaks()
     stages = {"far_kernel": last.ms_far, "near_laplace_kernel": last.ms_near_laplace,
               "near_modes_kernel": last.ms_near - last.ms_near_laplace, "assemble": last.ms_assemble,
@@ -345,8 +377,7 @@ def run_ours(args, rank, world):
                                 "sample": "modal kernels of %d target rows x all %d sources + their Alpert "
                                           "points, %d modes, 4 kernels (FP64 numpy oracle), %.1f s" %
                                           (rows, w["N"], w["M"] // 2, t)}
-    if rank == 0:
-        print(json.dumps(line))
+    emit_line(line, rank)
     if dist:
         dist.destroy_process_group()
 
@@ -383,8 +414,7 @@ def run_batched(args, rank, world):
     from paper_2412_11162_gb300 import binding as B
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    if rank != 0:
-        return
+    dist = init_dist(world, "nccl", torch.device("cuda", dev))
     inst, polar, azimuth = batched_instances()
 
     def make():
@@ -400,6 +430,8 @@ def run_batched(args, rank, world):
     for _ in range(max(args.warmup, 3)):
         outs, reps = step()
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     steps = max(1, args.steps // 3)
     with ClockSampler(dev) as clk:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -411,7 +443,9 @@ def run_batched(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         clk.mark_end()
-    ms = e0.elapsed_time(e1) / steps
+    if dist:
+        dist.barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist)
     ent = sum(entries_per_problem(w) for w in inst)
     # FP64 check on the first instance, all 64 waves
     o64, _ = probs[0].solve(polar, precision=B.PMLBIE_FP64, azimuth=azimuth)
@@ -428,7 +462,7 @@ def run_batched(args, rank, world):
         for t, key in zip(pin, ("u1", "phi1", "u2", "phi2")):
             t.copy_(o[key], non_blocking=True)
     torch.cuda.synchronize()
-    e2e_ms = 1e3 * (time.perf_counter() - t0)
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), dist)
     for q in Q:
         q.close()
     d2h = sum(4 * o["u1"].numel() * 16 for o in outs)
@@ -437,13 +471,13 @@ def run_batched(args, rank, world):
     roof = roofline(inst[big], reps[big], peaks(), clocks)
     roof["kernel"] += " of the N=%d instance" % inst[big]["N"]
     line = {
-        "metric": METRIC, "value": ent / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+        "metric": METRIC, "value": job_value(world, ent, ms), "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128 kernels / c64 LU / c128 refinement", "data": "synthetic",
         "config": {"workload": "8 instances (seed 2412): k1=linspace(2pi,8pi,8), k2=1.5 k1, h~U[0.1,0.4], "
                                "N=%s, M=N/2; 64 plane waves (8 polar x 8 azimuth); mixed; 2 worker streams" %
                                [w["N"] for w in inst],
-                   "parallelism": "1 GPU",
+                   "parallelism": "the same batch on every GPU" if world > 1 else "1 GPU",
                    "l2": "working set > L2: every step rebuilds %.1f GB of per-mode matrices" %
                          (sum((w["M"] // 2) * (2 * w["N"]) ** 2 * 24 for w in inst) / 1e9)},
         "solve_s_per_problem": ms / 1e3 / 8,
@@ -454,12 +488,14 @@ def run_batched(args, rank, world):
         "mixed_vs_fp64_rel_err_instance0": rel,
         "gpu_launches": int(sum(r.launches for r in reps)),
         "roofline": roof, "clocks": clocks,
-        "e2e": {"value": ent / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+        "e2e": {"value": job_value(world, ent, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(sum(h2d_bytes(q, w) for q, w in zip(probs, inst))),
                 "d2h_bytes_per_step": int(d2h),
                 "note": "create the 8 problems (host tables) + batch solve + copy of all outputs to pinned host"},
     }
-    print(json.dumps(line))
+    emit_line(line, rank)
+    if dist:
+        dist.destroy_process_group()
 
 
 def far_flops_per_pair(M, physical=False):

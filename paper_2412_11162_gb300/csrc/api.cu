@@ -43,9 +43,21 @@ std::vector<double2> to_d2(const std::vector<cd>& v) {
 
 // device-side per-node extras live next to the problem (not in DeviceTables,
 // which the kernels receive by value)
+// The batched LU of one workspace (sizes and buffers fixed) as a CUDA graph:
+// its 3 n / 32 + 1 dependent launches are replayed with one graph launch.
+struct LuGraph {
+    cudaGraphExec_t exec = nullptr;
+    int precision = -1, n = 0, batch = 0;
+    const void *A = nullptr, *piv = nullptr, *info = nullptr;
+    long launches = 0;          // kernels in the graph
+    bool unavailable = false;   // capture failed once: launch directly
+};
+
 struct pmlbie_dev_extra {
     double *nu_r = nullptr, *nu_z = nullptr, *speed = nullptr;
     bool ready = false;
+    cudaStream_t capture = nullptr;   // private stream the graph is captured on
+    LuGraph lu;
 };
 
 namespace {
@@ -105,6 +117,12 @@ void free_device(pmlbie_problem* prob) {
     }
     if (prob->ws) cudaFree(prob->ws);
     prob->ws = nullptr;
+    if (ex && ex->lu.exec) cudaGraphExecDestroy(ex->lu.exec);
+    if (ex && ex->capture) cudaStreamDestroy(ex->capture);
+    if (ex) {
+        ex->lu = LuGraph();
+        ex->capture = nullptr;
+    }
 }
 
 }  // namespace
@@ -349,6 +367,66 @@ int pmlbie_modal_kernels(pmlbie_problem* prob, int mode_lo, int mode_hi, void* d
     return PMLBIE_OK;
 }
 
+// Batched LU of the workspace's matrices through the cached graph: captured
+// on the problem's private stream the first time (or when the sizes or
+// buffers change), then replayed on s.  Falls back to direct launches when
+// the capture is refused.
+// LU factorisations replayed from a graph by this thread's current call
+thread_local int g_lu_graph_replays = 0;
+
+static cudaError_t lu_direct(int precision, int n, int batch, void* A, int* piv, int* info, cudaStream_t s) {
+    return precision == PMLBIE_FP64 ? batched_lu<double2>(n, batch, (double2*)A, piv, info, s)
+                                    : batched_lu<float2>(n, batch, (float2*)A, piv, info, s);
+}
+
+static int batched_lu_graphed(pmlbie_problem* prob, int precision, int n, int batch, void* A, int* piv, int* info,
+                              cudaStream_t s) {
+    pmlbie_dev_extra* ex = extra_of(prob);
+    LuGraph& g = ex->lu;
+    if (g.unavailable) {
+        PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, s));
+        return PMLBIE_OK;
+    }
+    if (!(g.exec && g.precision == precision && g.n == n && g.batch == batch && g.A == A && g.piv == piv &&
+          g.info == info)) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = LuGraph();
+        if (!ex->capture) PMLBIE_CUDA_TRY(cudaStreamCreateWithFlags(&ex->capture, cudaStreamNonBlocking));
+        PMLBIE_CUDA_TRY(precision == PMLBIE_FP64 ? lu_prepare<double2>() : lu_prepare<float2>());
+        const long before = g_launches;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(ex->capture, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t el = lu_direct(precision, n, batch, A, piv, info, ex->capture);
+            e = cudaStreamEndCapture(ex->capture, &graph);
+            if (el != cudaSuccess) e = el;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        const long captured = g_launches - before;   // kernels recorded into the graph
+        g_launches = before;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g = LuGraph();
+            g.unavailable = true;
+            PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, s));
+            return PMLBIE_OK;
+        }
+        g.launches = captured;
+        g.precision = precision;
+        g.n = n;
+        g.batch = batch;
+        g.A = A;
+        g.piv = piv;
+        g.info = info;
+    }
+    PMLBIE_CUDA_TRY(cudaGraphLaunch(g.exec, s));
+    count_launch(g.launches);
+    ++g_lu_graph_replays;
+    return PMLBIE_OK;
+}
+
 // Accumulated device times and refinement statistics of a solve.
 struct SolveStats {
     double ms_kernels = 0, ms_lu = 0, ms_solve = 0, ms_far = 0, ms_near = 0, ms_near_laplace = 0, ms_assemble = 0;
@@ -392,13 +470,13 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
     bool unconverged = false;
     std::vector<double> mres(nm, 0.0), mbwd(nm, 0.0);
     if (precision == PMLBIE_FP64) {
-        PMLBIE_CUDA_TRY(batched_lu<double2>(n2, nm, w.A, w.piv, w.info, s));
+        if ((rc = batched_lu_graphed(prob, PMLBIE_FP64, n2, nm, w.A, w.piv, w.info, s))) return rc;
         PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
         PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.X, w.B, xbytes, cudaMemcpyDeviceToDevice, s));
         PMLBIE_CUDA_TRY((batched_lu_solve<double2, double2>(n2, nm, n_rhs, w.A, w.piv, w.X, s)));
     } else {
         PMLBIE_CUDA_TRY(convert_to_c64((int64_t)nm * n2 * n2, w.A, w.A32, s));
-        PMLBIE_CUDA_TRY(batched_lu<float2>(n2, nm, w.A32, w.piv, w.info, s));
+        if ((rc = batched_lu_graphed(prob, PMLBIE_MIXED, n2, nm, w.A32, w.piv, w.info, s))) return rc;
         PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
         PMLBIE_CUDA_TRY(cudaMemsetAsync(w.X, 0, xbytes, s));
         PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.R, w.B, xbytes, cudaMemcpyDeviceToDevice, s));
@@ -656,6 +734,7 @@ int pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* o, void* dev_
     Workspace w;
     if ((rc = get_workspace(prob, precision, n_rhs, chunk, w))) return rc;
     g_launches = 0;
+    g_lu_graph_replays = 0;
     std::vector<double> rpar((size_t)kRhsPar * n_rhs, 0.0);
     for (int r = 0; r < n_rhs; ++r) {
         if (point) {
@@ -705,6 +784,7 @@ int pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* o, void* dev_
         rep->gmres_modes = st.gmres_modes;
         rep->gmres_iters = st.gmres_iters;
         rep->backward_error = st.bwd;
+        rep->lu_graph_replays = g_lu_graph_replays;
     }
     if (precision == PMLBIE_MIXED && st.unconverged)
         return fail(PMLBIE_ENOCONVERGE, "refinement missed its tolerance: residual " + std::to_string(st.resid) +

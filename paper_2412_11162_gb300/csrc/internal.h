@@ -184,6 +184,9 @@ cudaError_t launch_outputs(const pmlbie_problem* prob, int n_rhs, int nm, const 
 // original row that ends in row i (P A = L U with (P x)_i = x_{piv[i]}).
 template <typename T>
 cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s);
+// kernel attributes of batched_lu<T>, set once (call before capturing it)
+template <typename T>
+cudaError_t lu_prepare();
 // active: optional per-matrix flags (0 = skip), used to leave converged modes alone
 // factors in TF, right-hand sides and arithmetic in T (T = double2 with TF = float2:
 // FP64 solves with the FP32 factors)

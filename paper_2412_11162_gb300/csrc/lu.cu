@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 #include "tc_update.cuh"
@@ -713,33 +714,40 @@ __global__ void perm_kernel(int n, int* piv) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = sp[i];
 }
 
+// Dynamic shared-memory limits of the factorisation's kernels, set once per
+// process (outside any stream capture of the factorisation).
+template <typename T>
+cudaError_t lu_prepare() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        cudaError_t e;
+        if ((e = allow_max_smem(panel_kernel<T>)) == cudaSuccess && (e = allow_max_smem(swap_trsm_kernel<T>)) ==
+            cudaSuccess && (e = allow_max_smem(perm_kernel)) == cudaSuccess) {
+            if constexpr (sizeof(T) == 8) e = allow_max_smem(tcu::update_kernel);
+        }
+        err = e;
+    });
+    return err;
+}
+
 template <typename T>
 cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s) {
+    cudaError_t pe = lu_prepare<T>();
+    if (pe != cudaSuccess) return pe;
     for (int k0 = 0; k0 < n; k0 += kNB) {
         int kb = std::min(kNB, n - k0);
         const int w = panel_width<T>(n - k0);
         const size_t smp = sizeof(T) * (size_t)(n - k0) * w;
-        if (k0 == 0) {
-            cudaError_t e = allow_max_smem(panel_kernel<T>);
-            if (e != cudaSuccess) return e;
-        }
         panel_kernel<T><<<batch, kPanelThreads, smp, s>>>(n, k0, kb, w, A, piv, info);
         count_launch(2);
         dim3 g1((n + kSwapCols - 1) / kSwapCols, batch);
         size_t sm1 = sizeof(T) * ((size_t)kSwapCols * 2 * kNB + kNB * kNB);
-        if (k0 == 0) {
-            cudaError_t e = allow_max_smem(swap_trsm_kernel<T>);
-            if (e != cudaSuccess) return e;
-        }
         swap_trsm_kernel<T><<<g1, 256, sm1, s>>>(n, k0, kb, A, piv);
         int rem = n - k0 - kb;
         if (rem > 0) {
             if constexpr (sizeof(T) == 8) {
                 // complex64: tensor-core update (tcgen05, TF32 split to FP32 accuracy)
-                if (k0 == 0) {
-                    cudaError_t e = allow_max_smem(tcu::update_kernel);
-                    if (e != cudaSuccess) return e;
-                }
                 constexpr int TL = tcu::kTileC;
                 dim3 g2((rem + TL - 1) / TL, (rem + TL - 1) / TL, batch);
                 tcu::update_kernel<<<g2, tcu::kThreads, tcu::kSmemBytes, s>>>(n, k0, kb,
@@ -753,10 +761,6 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
         }
     }
     const size_t smq = 2 * sizeof(int) * (size_t)n;
-    if (smq > 48 * 1024) {
-        cudaError_t e = allow_max_smem(perm_kernel);
-        if (e != cudaSuccess) return e;
-    }
     perm_kernel<<<batch, 256, smq, s>>>(n, piv);
     count_launch();
     return cudaGetLastError();
@@ -790,6 +794,8 @@ cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int
     return cudaGetLastError();
 }
 
+template cudaError_t lu_prepare<double2>();
+template cudaError_t lu_prepare<float2>();
 template cudaError_t batched_lu<double2>(int, int, double2*, int*, int*, cudaStream_t);
 template cudaError_t batched_lu<float2>(int, int, float2*, int*, int*, cudaStream_t);
 template cudaError_t batched_lu_solve<double2, double2>(int, int, int, const double2*, const int*, double2*,

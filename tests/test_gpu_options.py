@@ -131,3 +131,14 @@ def test_batch_of_uneven_instances_equals_single_solves():
             # (well inside the 1e-6 bar of the mixed path; a mix-up of
             # instances or waves would show as O(1))
             assert e <= (1e-8 if k[0] == "u" else 1e-6), (P.N, k, e)
+
+
+def test_lu_graph_replay(prob):
+    """The batched LU of a workspace is captured once as a CUDA graph and
+    replayed by later solves (FP64 and mixed), with the same results."""
+    from paper_2412_11162_gb300.binding import PMLBIE_FP64, PMLBIE_MIXED
+    for prec, tol in ((PMLBIE_MIXED, 1e-10), (PMLBIE_FP64, 1e-12)):
+        first, _ = prob.solve([np.pi / 6], precision=prec)
+        again, rep = prob.solve([np.pi / 6], precision=prec)
+        assert rep.lu_graph_replays >= 1
+        assert _rel(again["u1"], first["u1"]) <= tol

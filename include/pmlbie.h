@@ -51,6 +51,7 @@ extern "C" {
 #define PMLBIE_ENOCONVERGE (-5)   /* iterative refinement missed its tolerance    */
 #define PMLBIE_ENAN        (-6)   /* NaN or Inf in an output                      */
 #define PMLBIE_ENODEV      (-7)   /* no CUDA device / extension not usable        */
+#define PMLBIE_ETIMEOUT    (-8)   /* a device-side bounded wait expired           */
 
 /* generating-curve kinds */
 #define PMLBIE_CURVE_GAUSS_BUMP 0   /* z = h (e^{-r^2/w} - e^{-R^2/w})/(1 - e^{-R^2/w}), r <= R; flat to B */
@@ -212,7 +213,8 @@ int  pmlbie_modal_kernels_noalloc(pmlbie_problem* prob, int mode_lo, int mode_hi
  * are restarted and solved by flexible GMRES in FP64 preconditioned by the
  * same LU.  Errors: EINVAL, ENOMEM, ECUDA, ESINGULAR, ENOCONVERGE (mixed: a
  * mode missed both tolerances after the iteration caps; outputs still
- * written). */
+ * written), ETIMEOUT (a bounded wait of the tensor-core LU update expired),
+ * ENAN (NaN or Inf in an output; outputs written). */
 int  pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* polar,
                   void* dev_u1, void* dev_phi1, void* dev_u2, void* dev_phi2,
                   void* stream, pmlbie_report* rep);
@@ -287,6 +289,19 @@ int  pmlbie_field(pmlbie_problem* prob, int n_pts, const double* rho, const doub
 int  pmlbie_solve_host(pmlbie_problem* prob, int precision, int n_rhs, const double* polar,
                        double* u1, double* phi1, double* u2, double* phi2,
                        void* stream, pmlbie_report* rep);
+
+/* Scan of count complex128 values in device memory for NaN or Inf (the
+ * solves run it on their outputs).  Synchronises the stream.  Returns OK,
+ * ENAN, EINVAL (NULL with count > 0) or ECUDA. */
+int  pmlbie_check_finite(const void* dev, size_t count, void* stream);
+
+/* Self-test of the device-side bounded waits (the tensor-core LU update waits
+ * on an mbarrier with an iteration limit): one warp polls an mbarrier that no
+ * thread arrives at, at most `iterations` times (1 .. 2^24), and reports the
+ * expiry the way the update does.  Returns ETIMEOUT when the wait expired (the
+ * expected outcome), OK if it completed, EINVAL, ECUDA.  The context stays
+ * usable.  Synchronises the stream. */
+int  pmlbie_selftest_wait(long long iterations, void* stream);
 
 #ifdef __cplusplus
 }

@@ -19,6 +19,7 @@ PMLBIE_ESINGULAR = -4
 PMLBIE_ENOCONVERGE = -5
 PMLBIE_ENAN = -6
 PMLBIE_ENODEV = -7
+PMLBIE_ETIMEOUT = -8
 PMLBIE_CURVE_GAUSS_BUMP = 0
 PMLBIE_CURVE_POLYLINE = 1
 PMLBIE_CURVE_WAVY_DENT = 2
@@ -59,7 +60,8 @@ class pmlbie_solve_opts(ctypes.Structure):
 EXPORTS = ["pmlbie_create", "pmlbie_destroy", "pmlbie_last_error", "pmlbie_nodes", "pmlbie_diagonal",
            "pmlbie_near_count", "pmlbie_alpert_rule", "pmlbie_workspace_bytes", "pmlbie_modal_kernels",
            "pmlbie_modal_kernels_noalloc",
-           "pmlbie_solve", "pmlbie_solve_ex", "pmlbie_solve_batch", "pmlbie_field", "pmlbie_solve_host"]
+           "pmlbie_solve", "pmlbie_solve_ex", "pmlbie_solve_batch", "pmlbie_field", "pmlbie_solve_host",
+           "pmlbie_check_finite", "pmlbie_selftest_wait"]
 
 
 def _load():
@@ -94,7 +96,10 @@ def _load():
                                        ctypes.POINTER(pmlbie_report)]
     lib.pmlbie_field.argtypes = [vp, ctypes.c_int, dp, dp, ip, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp,
                                  vp, vp, vp]
-    for f in ("pmlbie_nodes", "pmlbie_diagonal", "pmlbie_near_count", "pmlbie_alpert_rule",
+    lib.pmlbie_check_finite.argtypes = [vp, ctypes.c_size_t, vp]
+    lib.pmlbie_selftest_wait.argtypes = [ctypes.c_longlong, vp]
+    for f in ("pmlbie_check_finite", "pmlbie_selftest_wait", "pmlbie_nodes", "pmlbie_diagonal",
+              "pmlbie_near_count", "pmlbie_alpert_rule",
               "pmlbie_modal_kernels", "pmlbie_modal_kernels_noalloc", "pmlbie_solve", "pmlbie_solve_ex",
               "pmlbie_solve_batch", "pmlbie_field", "pmlbie_solve_host"):
         getattr(lib, f).restype = ctypes.c_int
@@ -306,3 +311,13 @@ def pmlbie_solve_host(h, precision, polar, u1, phi1, u2, phi2, stream=None):
     check(lib.pmlbie_solve_host(h, precision, len(pol), _dptr(pol), hp(u1), hp(phi1), hp(u2), hp(phi2),
                                 _stream(stream), ctypes.byref(rep)), "pmlbie_solve_host")
     return rep
+
+
+def pmlbie_check_finite(t, stream=None):
+    """Status of the NaN / Inf scan of a complex128 device tensor (no raise)."""
+    return lib.pmlbie_check_finite(_tptr(t), t.numel(), _stream(stream))
+
+
+def pmlbie_selftest_wait(iterations, stream=None):
+    """Status of the bounded-wait self-test (ETIMEOUT expected; no raise)."""
+    return lib.pmlbie_selftest_wait(int(iterations), _stream(stream))

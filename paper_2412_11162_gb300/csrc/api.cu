@@ -139,7 +139,7 @@ struct Workspace {
     double2 *A = nullptr, *zd = nullptr, *nout = nullptr, *b1 = nullptr, *b2 = nullptr, *B = nullptr,
             *X = nullptr, *R = nullptr;
     float2 *A32 = nullptr, *w32 = nullptr;
-    int *piv = nullptr, *info = nullptr, *active = nullptr;
+    int *piv = nullptr, *info = nullptr, *active = nullptr, *nanflag = nullptr;
     double *rn = nullptr, *bn = nullptr, *xn = nullptr, *an = nullptr, *rpar = nullptr;
     size_t bytes = 0;
 };
@@ -182,6 +182,7 @@ Workspace plan(const pmlbie_problem* prob, int precision, int nrhs, int nmodes, 
     w.X = (double2*)take(sizeof(double2) * nm * n2 * nrhs);
     w.piv = (int*)take(sizeof(int) * nm * n2);
     w.info = (int*)take(sizeof(int) * nm);
+    w.nanflag = (int*)take(sizeof(int));
     w.active = (int*)take(sizeof(int) * nm);
     w.rn = (double*)take(sizeof(double) * nm * nrhs);
     w.bn = (double*)take(sizeof(double) * nm * nrhs);
@@ -371,6 +372,45 @@ int pmlbie_modal_kernels(pmlbie_problem* prob, int mode_lo, int mode_hi, void* d
 // on the problem's private stream the first time (or when the sizes or
 // buffers change), then replayed on s.  Falls back to direct launches when
 // the capture is refused.
+// flag = 1 if any of the count doubles is NaN or Inf
+__global__ void nonfinite_kernel(const double* v, size_t count, int* flag) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        if (!isfinite(v[i])) {
+            *flag = 1;
+            return;
+        }
+}
+
+static cudaError_t launch_nonfinite(const void* dev, size_t count_c128, int* flag, cudaStream_t s) {
+    const size_t count = 2 * count_c128;
+    const unsigned blocks = (unsigned)std::min<size_t>((count + 255) / 256, 152 * 8);
+    if (blocks) nonfinite_kernel<<<blocks, 256, 0, s>>>((const double*)dev, count, flag);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Self-test of the bounded mbarrier wait: a barrier no thread arrives at.
+__global__ void wait_probe_kernel(long long iters, int* expired) {
+    __shared__ uint64_t bar;
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(addr));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t done = 0;
+    for (long long it = 0; it < iters && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(0u)
+            : "memory");
+    }
+    if (threadIdx.x == 0) *expired = done ? 0 : 1;
+}
+
 // LU factorisations replayed from a graph by this thread's current call
 thread_local int g_lu_graph_replays = 0;
 
@@ -577,10 +617,17 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
         bwd = *std::max_element(mbwd.begin(), mbwd.end());
     }
     PMLBIE_CUDA_TRY(launch_outputs(prob, n_rhs, nm, w.X, w.b1, w.b2, u1, phi1, u2, phi2, s));
+    // NaN / Inf scan of the chunk's outputs
+    PMLBIE_CUDA_TRY(cudaMemsetAsync(w.nanflag, 0, sizeof(int), s));
+    const size_t per_out = (size_t)nm * N * n_rhs;
+    for (double2* o : {u1, phi1, u2, phi2})
+        if (o) PMLBIE_CUDA_TRY(launch_nonfinite(o, per_out, w.nanflag, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[3], s));
     PMLBIE_CUDA_TRY(cudaEventSynchronize(ev[3]));
     std::vector<int> info(nm);
+    int nonfinite = 0;
     PMLBIE_CUDA_TRY(cudaMemcpy(info.data(), w.info, sizeof(int) * nm, cudaMemcpyDeviceToHost));
+    PMLBIE_CUDA_TRY(cudaMemcpy(&nonfinite, w.nanflag, sizeof(int), cudaMemcpyDeviceToHost));
     float t[3], f[3], fl = 0.f;
     for (int i = 0; i < 3; ++i) {
         cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]);
@@ -600,9 +647,13 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
     st.unconverged = st.unconverged || unconverged;
     for (int i = 0; i < nm; ++i) {
         if (info[i] < 0)
-            return fail(PMLBIE_ECUDA, "tensor-core LU update did not complete in mode " + std::to_string(lo + i));
+            return fail(PMLBIE_ETIMEOUT, "tensor-core LU update did not complete (bounded wait expired) in mode " +
+                                             std::to_string(lo + i));
         if (info[i]) return fail(PMLBIE_ESINGULAR, "zero pivot in mode " + std::to_string(lo + i));
     }
+    if (nonfinite)
+        return fail(PMLBIE_ENAN, "NaN or Inf in the outputs of modes " + std::to_string(lo) + ".." +
+                                     std::to_string(hi - 1));
     return PMLBIE_OK;
 }
 
@@ -921,6 +972,44 @@ int pmlbie_field(pmlbie_problem* prob, int n_pts, const double* rho, const doubl
                                  (double2*)dev_out, s));
     PMLBIE_CUDA_TRY(cudaStreamSynchronize(s));
     return PMLBIE_OK;
+}
+
+int pmlbie_check_finite(const void* dev, size_t count, void* stream) {
+    if (count == 0) return PMLBIE_OK;
+    if (!dev) return fail(PMLBIE_EINVAL, "NULL buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    int* flag = nullptr;
+    if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PMLBIE_ENOMEM, "flag allocation failed");
+    }
+    int h = 0;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_nonfinite(dev, count, flag, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(flag);
+    if (e != cudaSuccess) return fail(PMLBIE_ECUDA, std::string("finiteness scan: ") + cudaGetErrorString(e));
+    return h ? fail(PMLBIE_ENAN, "NaN or Inf in the buffer") : PMLBIE_OK;
+}
+
+int pmlbie_selftest_wait(long long iterations, void* stream) {
+    if (iterations < 1 || iterations > (1ll << 24)) return fail(PMLBIE_EINVAL, "iterations must be in [1, 2^24]");
+    cudaStream_t s = (cudaStream_t)stream;
+    int* flag = nullptr;
+    if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PMLBIE_ENOMEM, "flag allocation failed");
+    }
+    int h = 0;
+    wait_probe_kernel<<<1, 32, 0, s>>>(iterations, flag);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(flag);
+    if (e != cudaSuccess) return fail(PMLBIE_ECUDA, std::string("wait self-test: ") + cudaGetErrorString(e));
+    return h ? fail(PMLBIE_ETIMEOUT, "bounded wait expired after " + std::to_string(iterations) + " polls")
+             : PMLBIE_OK;
 }
 
 int pmlbie_solve_host(pmlbie_problem* prob, int precision, int n_rhs, const double* polar, double* u1,

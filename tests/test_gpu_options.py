@@ -142,3 +142,27 @@ def test_lu_graph_replay(prob):
         again, rep = prob.solve([np.pi / 6], precision=prec)
         assert rep.lu_graph_replays >= 1
         assert _rel(again["u1"], first["u1"]) <= tol
+
+
+def test_bounded_wait_expiry_reports_timeout(prob):
+    """Failure detection without a fault: a bounded mbarrier wait that nothing
+    completes expires, the host reads ETIMEOUT, and the context keeps working."""
+    import torch
+    from paper_2412_11162_gb300 import binding as B
+    assert B.pmlbie_selftest_wait(1000) == B.PMLBIE_ETIMEOUT
+    assert "expired" in B.lib.pmlbie_last_error().decode()
+    out, rep = prob.solve([np.pi / 6], precision=B.PMLBIE_MIXED)
+    assert bool(torch.isfinite(torch.view_as_real(out["u1"])).all())
+
+
+def test_finiteness_scan():
+    import torch
+    from paper_2412_11162_gb300 import binding as B
+    t = torch.zeros(1000, dtype=torch.complex128, device="cuda")
+    assert B.pmlbie_check_finite(t) == B.PMLBIE_OK
+    t[517] = complex(float("nan"), 0.0)
+    assert B.pmlbie_check_finite(t) == B.PMLBIE_ENAN
+    t[517] = complex(0.0, float("inf"))
+    assert B.pmlbie_check_finite(t) == B.PMLBIE_ENAN
+    t[517] = 0
+    assert B.pmlbie_check_finite(t[:10]) == B.PMLBIE_OK

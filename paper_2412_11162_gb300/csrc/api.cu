@@ -515,7 +515,7 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
         PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.X, w.B, xbytes, cudaMemcpyDeviceToDevice, s));
         PMLBIE_CUDA_TRY((batched_lu_solve<double2, double2>(n2, nm, n_rhs, w.A, w.piv, w.X, s)));
     } else {
-        PMLBIE_CUDA_TRY(convert_to_c64((int64_t)nm * n2 * n2, w.A, w.A32, s));
+        PMLBIE_CUDA_TRY(convert_fro2_c128(n2, nm, w.A, w.A32, w.an, s));
         if ((rc = batched_lu_graphed(prob, PMLBIE_MIXED, n2, nm, w.A32, w.piv, w.info, s))) return rc;
         PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
         PMLBIE_CUDA_TRY(cudaMemsetAsync(w.X, 0, xbytes, s));
@@ -528,7 +528,6 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
             prev(nm, 0.0);
         std::vector<int> act(nm, 1), slow(nm, 0);
         const int max_ir = 12;
-        PMLBIE_CUDA_TRY(fro2_c128(n2, nm, w.A, w.an, s));
         PMLBIE_CUDA_TRY(cudaMemcpyAsync(an.data(), w.an, sizeof(double) * nm, cudaMemcpyDeviceToHost, s));
         PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.active, act.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, s));
         for (iters = 0; iters <= max_ir; ++iters) {

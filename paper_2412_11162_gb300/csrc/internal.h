@@ -194,6 +194,9 @@ template <typename T, typename TF>
 cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int* piv, T* B,
                              cudaStream_t s, const int* active = nullptr);
 cudaError_t convert_to_c64(int64_t count, const double2* src, float2* dst, cudaStream_t s);
+// complex64 copies of batch n x n complex128 matrices and their squared
+// Frobenius norms (out[b] = |A_b|_F^2) in one pass over A
+cudaError_t convert_fro2_c128(int n, int batch, const double2* A, float2* A32, double* out, cudaStream_t s);
 // Flexible GMRES (FP64, right-preconditioned by the FP32 LU) for the modes with
 // act[b] = 1; X holds the start and receives the solution; act is cleared for
 // converged modes (relative residual <= tol or normwise backward error
@@ -208,8 +211,6 @@ int gmres_refine(int n, int batch, int nrhs, const double2* A, const float2* LU3
 cudaError_t residual_c128(int n, int batch, int nrhs, const double2* A, const double2* X,
                           const double2* B, double2* R, double* rnorm, double* bnorm, double* xnorm,
                           cudaStream_t s, const int* active = nullptr);
-// |A_b|_F^2 per matrix
-cudaError_t fro2_c128(int n, int batch, const double2* A, double* out, cudaStream_t s);
 cudaError_t refine_step(int n, int batch, int nrhs, const float2* LU32, const int* piv,
                         const double2* R, float2* work32, double2* X, cudaStream_t s,
                         const int* active = nullptr);

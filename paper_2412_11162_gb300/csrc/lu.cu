@@ -622,7 +622,8 @@ __global__ void residual_kernel(int n, int nrhs, const double2* A, const double2
     const double2* a = A + (size_t)b * n * n;
     const double2* x = X + (size_t)b * n * nrhs;
     double2 acc = make_double2(0.0, 0.0);
-    for (int c = c0; c < c1; ++c) acc = fms(acc, a[(size_t)c * n + row], x[(size_t)c * nrhs + r]);
+#pragma unroll 16
+    for (int c = c0; c < c1; ++c) acc = fms(acc, __ldg(a + (size_t)c * n + row), x[(size_t)c * nrhs + r]);
     double* o = reinterpret_cast<double*>(R + (size_t)b * n * nrhs + idx);
     atomicAdd(o, acc.x);
     atomicAdd(o + 1, acc.y);
@@ -663,13 +664,18 @@ __global__ void norms3_kernel(int n, int nrhs, const double2* R, const double2* 
     }
 }
 
-// |A_b|_F^2 per matrix (grid (blocks, batch), 256 threads, one atomic per block)
-__global__ void fro2_kernel(int64_t per, const double2* A, double* out) {
+// complex64 copy of every matrix and |A_b|_F^2 in the same pass over A:
+// grid (blocks per matrix, matrices), out zeroed beforehand
+__global__ void c64_fro2_kernel(int64_t per, const double2* A, float2* A32, double* out) {
     __shared__ double sh[8];
     const double2* a = A + (size_t)blockIdx.y * per;
+    float2* d = A32 + (size_t)blockIdx.y * per;
     double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += (int64_t)gridDim.x * blockDim.x)
-        acc += a[i].x * a[i].x + a[i].y * a[i].y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = a[i];
+        d[i] = make_float2((float)v.x, (float)v.y);
+        acc += v.x * v.x + v.y * v.y;
+    }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffff, acc, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -824,12 +830,14 @@ cudaError_t residual_c128(int n, int batch, int nrhs, const double2* A, const do
     return cudaGetLastError();
 }
 
-cudaError_t fro2_c128(int n, int batch, const double2* A, double* out, cudaStream_t s) {
+cudaError_t convert_fro2_c128(int n, int batch, const double2* A, float2* A32, double* out, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * batch, s);
     if (e != cudaSuccess) return e;
     const int64_t per = (int64_t)n * n;
-    dim3 g((unsigned)std::min<int64_t>((per + 255) / 256, 64), batch);
-    fro2_kernel<<<g, 256, 0, s>>>(per, A, out);
+    // about 32 CTAs of 256 threads per SM over all matrices (enough loads in flight)
+    const int64_t want = std::max<int64_t>(1, (152 * 32 + batch - 1) / batch);
+    dim3 g((unsigned)std::min<int64_t>((per + 255) / 256, want), batch);
+    c64_fro2_kernel<<<g, 256, 0, s>>>(per, A, A32, out);
     count_launch();
     return cudaGetLastError();
 }

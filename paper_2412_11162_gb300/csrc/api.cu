@@ -525,7 +525,7 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
         // residual stops contracting (condition number x FP32 LU error near or above 1) are
         // restarted from zero and solved by FGMRES preconditioned with the same LU.
         std::vector<double> rn((size_t)nm * n_rhs), bn((size_t)nm * n_rhs), xn((size_t)nm * n_rhs), an(nm),
-            prev(nm, 0.0);
+            prev(nm, 0.0), first(nm, 0.0);
         std::vector<int> act(nm, 1), slow(nm, 0);
         const int max_ir = 12;
         PMLBIE_CUDA_TRY(cudaMemcpyAsync(an.data(), w.an, sizeof(double) * nm, cudaMemcpyDeviceToHost, s));
@@ -563,6 +563,7 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
                         ++nact;
                     }
                     prev[mo] = wbwd;
+                    if (iters == 1) first[mo] = wbwd;
                 }
                 if (nact == 0) break;
                 if (iters == max_ir) {
@@ -578,7 +579,10 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
         if (nslow > 0) {
             const size_t per = (size_t)n2 * n_rhs * sizeof(double2);
             for (int mo = 0; mo < nm; ++mo)
-                if (slow[mo]) PMLBIE_CUDA_TRY(cudaMemsetAsync((char*)w.X + per * mo, 0, per, s));
+                // FGMRES starts from the refinement's last iterate when that
+                // improved on the first one, else (divergence) from zero
+                if (slow[mo] && !(mbwd[mo] < first[mo]))
+                    PMLBIE_CUDA_TRY(cudaMemsetAsync((char*)w.X + per * mo, 0, per, s));
             int git = 0;
             // FGMRES on the contiguous range of modes [g0, g1) holding every
             // slow mode (its Krylov bases allocated for that range only)

@@ -349,7 +349,7 @@ def run_ours(args, rank, world):
                          int(((w["M"] // 2) * (2 * w["N"]) ** 2 * 24) / 1e6)},
         "solve_s_per_problem": ms / 1e3,
         "kernel_entries_per_s": epp / ((last.ms_far + last.ms_near + last.ms_assemble) / 1e3),
-        "far_pairs": last.far_pairs,
+        "far_pairs": last.far_pairs, "far_pairs_per_cta": last.far_pairs_per_cta,
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
         "mode_chunks": chunks,
         "refine_iters": last.refine_iters, "refine_residual": last.residual,

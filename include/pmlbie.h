@@ -106,6 +106,7 @@ typedef struct {
     double   backward_error;      /* mixed: max over modes/RHS of |B - A x| / (|A|_F |x| + |B|) */
     int      far_pairs_physical;  /* far pairs with both nodes outside the PML (real distance) */
     int      lu_graph_replays;    /* LU factorisations replayed from a captured CUDA graph */
+    int      far_pairs_per_cta;   /* node pairs per CTA of the far-pair kernel (autotuned) */
 } pmlbie_report;
 
 /* Options of pmlbie_solve_ex (zero-initialise, then set struct_size). */

@@ -224,7 +224,7 @@ void fresnel(double w1, double w2, double phi, double* out6) {
 // modal kernels + assembly into w.A for modes [lo, hi); ev[0..3] bracket the
 // stages, ev[4] splits the close-pair stage
 int build_system(pmlbie_problem* prob, Workspace& w, int lo, int hi, cudaStream_t s, cudaEvent_t* ev) {
-    FarLaunch fl{lo, hi, w.A, nullptr};
+    FarLaunch fl{lo, hi, w.A, nullptr, true};
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[0], s));
     PMLBIE_CUDA_TRY(launch_far(prob, fl, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[1], s));
@@ -357,7 +357,7 @@ int pmlbie_modal_kernels(pmlbie_problem* prob, int mode_lo, int mode_hi, void* d
         cudaFree(zd);
         return fail(PMLBIE_ENOMEM, "scratch allocation failed");
     }
-    FarLaunch fl{mode_lo, mode_hi, nullptr, (double2*)dev_out};
+    FarLaunch fl{mode_lo, mode_hi, nullptr, (double2*)dev_out, true};
     cudaError_t e = launch_far(prob, fl, s);
     if (e == cudaSuccess) e = launch_near(prob, mode_lo, mode_hi, zd, nout, s);
     if (e == cudaSuccess) e = launch_near_to_raw(prob, mode_lo, mode_hi, nout, (double2*)dev_out, s);
@@ -839,6 +839,7 @@ int pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* o, void* dev_
         rep->gmres_iters = st.gmres_iters;
         rep->backward_error = st.bwd;
         rep->lu_graph_replays = g_lu_graph_replays;
+        rep->far_pairs_per_cta = g_far_pairs_per_cta;
     }
     if (precision == PMLBIE_MIXED && st.unconverged)
         return fail(PMLBIE_ENOCONVERGE, "refinement missed its tolerance: residual " + std::to_string(st.resid) +

@@ -126,8 +126,13 @@ struct FarLaunch {
     // system-matrix output (column-major 2N x 2N per mode) or raw kernels
     double2* A;            // [mode][col][row], ld = 2N; may be null
     double2* raw;          // [mode][kernel][l][m]; may be null
+    // the first launch for a (N, M, modes, output) shape may time the
+    // candidate CTA sizes (it synchronises the stream once); false: never
+    bool tune = false;
 };
 cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStream_t s);
+// pairs per CTA of this thread's last far-kernel launch (the tuned choice)
+extern thread_local int g_far_pairs_per_cta;
 // mid (optional): event recorded between the Laplace-mode and the modes kernels
 cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, double2* zd_scratch,
                         double2* out, cudaStream_t s, cudaEvent_t mid = nullptr);

@@ -11,6 +11,9 @@
 //   Sec. 4.1        Alpert corrections with Lagrange interpolation, diagonal D
 //   Sec. 2, 4.2     reference field, b^1, b^2, transmission block system
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "internal.h"
 
@@ -1045,6 +1048,23 @@ __global__ void outputs_kernel(int N, int nmodes, int nrhs, const double2* X, co
 // ---------------------------------------------------------------------------
 static int far_warps(int M) { return M <= 512 ? 8 : 4; }
 
+// shared memory of a far_kernel CTA with nw pairs: twiddles M, DFT weights
+// M/2, angle table S1, nw pair geometries, nw buffers, nw flags
+static size_t far_smem(int M, int nw) {
+    const size_t S1 = M / 2 + 1;
+    return sizeof(double2) * ((size_t)M + M / 2 + S1 + 4 * (size_t)nw + (size_t)nw * (4 * S1 + M)) +
+           sizeof(double2) * (((size_t)nw + 3) / 4);
+}
+
+// Autotuned pairs per CTA of the far kernel, per (N, M, modes, output kind):
+// the first tunable launch of a shape runs every candidate that fits in
+// shared memory once, timed with events on the stream, and keeps the
+// fastest for the process (the kernel's writes are plain stores, so the
+// repeated runs leave the same output).
+static std::mutex g_far_tune_mu;
+static std::map<std::tuple<int, int, int, int>, int> g_far_tuned;
+thread_local int g_far_pairs_per_cta = 0;
+
 cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStream_t s) {
     const int N = prob->P.N, M = prob->P.M;
     FarArgs a;
@@ -1058,17 +1078,51 @@ cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStre
     a.h = prob->H.h;
     a.A = fl.A;
     a.raw = fl.raw;
-    int nw = far_warps(M);
-    const size_t S1 = M / 2 + 1;
-    // twiddles M, DFT weights M/2, angle table S1, nw pair geometries, nw buffers, nw flags
-    size_t smem = sizeof(double2) * ((size_t)M + M / 2 + S1 + 4 * (size_t)nw + (size_t)nw * (4 * S1 + M)) +
-                  sizeof(double2) * (((size_t)nw + 3) / 4);
     cudaError_t e = allow_max_smem(far_kernel);
     if (e != cudaSuccess) return e;
-    dim3 grid((N + nw - 1) / nw, N);
-    far_kernel<<<grid, 32 * nw, smem, s>>>(a);
-    count_launch();
-    return cudaGetLastError();
+    auto run = [&](int nw) {
+        g_far_pairs_per_cta = nw;
+        dim3 grid((N + nw - 1) / nw, N);
+        far_kernel<<<grid, 32 * nw, far_smem(M, nw), s>>>(a);
+        count_launch();
+        return cudaGetLastError();
+    };
+    const auto key = std::make_tuple(N, M, fl.mode_hi - fl.mode_lo, fl.raw ? 1 : 0);
+    int nw = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_far_tune_mu);
+        auto it = g_far_tuned.find(key);
+        if (it != g_far_tuned.end()) nw = it->second;
+    }
+    if (nw) return run(nw);
+    if (!fl.tune) return run(far_warps(M));
+    int dev = 0, optin = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    int best = far_warps(M);
+    float tbest = 1e30f;
+    for (int c : {2, 4, 8, 16}) {
+        if (far_smem(M, c) > (size_t)optin) continue;
+        float ms = 0.f;
+        if ((e = cudaEventRecord(e0, s)) != cudaSuccess || (e = run(c)) != cudaSuccess ||
+            (e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+            break;
+        if (ms < tbest) tbest = ms, best = c;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_far_tune_mu);
+    g_far_tuned[key] = best;
+    g_far_pairs_per_cta = best;
+    return cudaSuccess;
 }
 
 static void taylor_coeffs(int L, double2* pa, double2* pb) {

@@ -11,6 +11,7 @@
 //   Sec. 4.1        Alpert corrections with Lagrange interpolation, diagonal D
 //   Sec. 2, 4.2     reference field, b^1, b^2, transmission block system
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -1087,6 +1088,13 @@ cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStre
         count_launch();
         return cudaGetLastError();
     };
+    // PMLBIE_FAR_PAIRS_PER_CTA=2|4|8|16 fixes the choice (reproducible profiling)
+    static const int forced = [] {
+        const char* v = std::getenv("PMLBIE_FAR_PAIRS_PER_CTA");
+        const int f = v ? std::atoi(v) : 0;
+        return (f == 2 || f == 4 || f == 8 || f == 16) ? f : 0;
+    }();
+    if (forced) return run(forced);
     const auto key = std::make_tuple(N, M, fl.mode_hi - fl.mode_lo, fl.raw ? 1 : 0);
     int nw = 0;
     {

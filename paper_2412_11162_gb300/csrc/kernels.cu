@@ -1094,7 +1094,7 @@ cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStre
         const int f = v ? std::atoi(v) : 0;
         return (f == 2 || f == 4 || f == 8 || f == 16) ? f : 0;
     }();
-    if (forced) return run(forced);
+    if (forced && far_smem(M, forced) <= 227 * 1024) return run(forced);
     const auto key = std::make_tuple(N, M, fl.mode_hi - fl.mode_lo, fl.raw ? 1 : 0);
     int nw = 0;
     {

@@ -153,7 +153,7 @@ def uses_substitution(pg):
     return (pg["rho_t"].imag > 0) | (pg["rho_t_s"].imag > 0)
 
 
-def split_samples(pg, omega, psi, L):
+def split_samples(pg, omega, psi, L, subst=True):
     """Smooth factors f1, f3 and remainders r1, r3 of the kernel split.
 
     S~ = Z f1 + r1 and K~ = D f3 + r3 at every angle, with
@@ -166,7 +166,8 @@ def split_samples(pg, omega, psi, L):
       D (e^{iq}(1-iq) - cH3) = -(w^3 / 4pi) N_D e^{iq} ((1 - iq) - P3(q)) / q^3,
       i Z H2 = (i w / 4pi) sin(q)/q,
       i D H4 = -(i w^3 / 4pi) N_D (sin q - q cos q) / q^3,
-    (the first three coefficients of (1 - iq) - P3 vanish).
+    (the first three coefficients of (1 - iq) - P3 vanish).  subst=False uses
+    the exact split on PML pairs too (complex q).
     """
     a, b = taylor_coeffs(L)
     u1 = -a[1:]                               # (1 - P1)/q
@@ -179,7 +180,7 @@ def split_samples(pg, omega, psi, L):
     q = omega * R
     e = np.exp(1j * q)
     ND = _numer_D(pg, psi)
-    sub = uses_substitution(pg)[..., None]
+    sub = (uses_substitution(pg) & bool(subst))[..., None]
     f1 = np.where(sub, e * _poly(a, q), np.cos(q))
     r1 = np.where(sub, (omega / FOUR_PI) * e * _poly(u1, q), (1j * omega / FOUR_PI) * _sinc(q))
     f3 = np.where(sub, e * _poly(b, q), np.cos(q) + q * np.sin(q))
@@ -239,13 +240,13 @@ def laplace_modes(pg, mmax, refine=0, chunk=512):
     return Zm, Dm
 
 
-def near_modes(pg, omega, M, L, lap=None):
+def near_modes(pg, omega, M, L, lap=None, subst=True):
     """Split modal kernels (S^_n, K^_n), n = 0..M/2-1, for close pairs."""
     if lap is None:
         lap = laplace_modes(pg, M - 2)
     Zm, Dm = lap
     psi = 2.0 * np.pi * np.arange(M) / M
-    cH1, rem1, cH3, rem3 = split_samples(pg, omega, psi, L)
+    cH1, rem1, cH3, rem3 = split_samples(pg, omega, psi, L, subst)
     k = np.arange(M)[:, None]
     kk = np.arange(-(M // 2 - 1), M // 2)[None, :]
     Ek = (2.0 * np.pi / M) * np.exp(-2j * np.pi * k * kk / M)     # C_k for k in (-M/2, M/2)
@@ -279,5 +280,5 @@ def modal_kernels(pg, omega, P: Params, lap=None, near=None):
     if np.any(near):
         sub = {k: v[near] for k, v in pg.items()}
         l2 = None if lap is None else (lap[0][near], lap[1][near])
-        S[near], K[near] = near_modes(sub, omega, M, P.taylor_L, l2)
+        S[near], K[near] = near_modes(sub, omega, M, P.taylor_L, l2, P.subst)
     return S, K

@@ -61,6 +61,8 @@ class Params:
     polar: float = np.pi / 6.0     # incidence polar angle phi_inc
     azimuth: float = 0.0           # incidence azimuth theta_inc
     taylor_L: int = 5              # order of the cH_1 / cH_3 substitution (Sec. 4.3)
+    subst: bool = True             # False: the exact split on PML pairs too (the "without
+                                   # cH_1" arm of the Sec. 4.3 experiment)
     split_c: float = 8.0          # near-pair threshold eta_s = split_c * 2 pi / M
 
     @property

@@ -525,3 +525,30 @@ def test_wavy_dent_curve():
     # near each end the offset is O(distance) with full relative accuracy
     orho, oz = seg.offset(np.array([1e-12]), np.array([1 - 1e-12]), 0)
     assert abs(orho[0] / (0.5 * np.pi * 1e-12) - 1) < 1e-6 and abs(oz[0] / (0.3 * np.pi * 1e-12) - 1) < 1e-6
+
+
+@pytest.mark.slow
+def test_sec4_3_substitution_on_off():
+    """Sec. 4.3: on close pairs with a point in the PML the exact split
+    (H1 = cos q, H3 = cos q + q sin q at complex q) grows like e^{|Im q|}; the
+    cH1 / cH3 substitution avoids it.  The NtD check of the section (dent,
+    omega = 2 pi, a1 = 2, T = 2, mode 1, source below) with a strong PML
+    (S = 12): substitution 2.4e-2 (the discretisation error at N = 120), exact
+    split O(10) (measured 34); with the paper's S = 2 the two agree."""
+    g = json.load(open(os.path.join(GOLDEN, "paper_examples.json")))["ntd_check_sec4_3"]
+    errs = {}
+    for S, subst in ((12.0, True), (12.0, False), (2.0, False)):
+        P = Params(k1=g["omega1"], k2=g["omega2"], N=120, M=128, a1=g["a1"], T=g["T"], S=S,
+                   curve="polyline", vertices=[tuple(v) for v in g["vertices"]], taylor_L=g["taylor_L"],
+                   subst=subst)
+        sysm = ModalSystem(P)
+        G = sysm.G
+        Da, _ = diagonal(G, sysm.Q)
+        rp = g["source_rp"]
+        u, f = _exact_point_source_modes(G.nodes, (rp[0], rp[2]), P.k1, g["mode"] + 1)
+        n = g["mode"]
+        Sa, Ka = sysm.matrices("a", n)
+        Nn = np.linalg.solve(Ka - np.diag(Da), Sa)
+        errs[(S, subst)] = np.linalg.norm(u[:, n] - Nn @ f[:, n]) / np.linalg.norm(u[:, n])
+    assert errs[(12.0, True)] < 0.05 and errs[(12.0, False)] > 1.0, errs
+    assert errs[(2.0, False)] < 0.05, errs

@@ -80,6 +80,10 @@ typedef struct {
     double   split_c;         /* close-pair threshold eta_s = split_c * 2 pi / M      */
     double   wavy_R, wavy_eps;  /* wavy dent (kind 2): 0 < R <= a1, 0 <= eps < 1        */
     int      wavy_m;            /* wavy dent: half-waves, 1..64 (Example 2: 1, 0.1, 3)  */
+    int      subst_off;         /* diagnostic: 1 = exact split (H1 = cos q, H3 = cos q +
+                                   q sin q) on close pairs with a PML point too, the
+                                   "without cH1" arm of Sec. 4.3 (unstable for strong
+                                   PMLs); 0 = the cH1 / cH3 substitution (default)      */
 } pmlbie_params;
 
 /* Report of a solve (filled when the pointer is not NULL). */

@@ -35,7 +35,7 @@ class pmlbie_params(ctypes.Structure):
                 ("bump_R", ctypes.c_double), ("n_vertices", ctypes.c_int),
                 ("vertices", ctypes.POINTER(ctypes.c_double)), ("taylor_L", ctypes.c_int),
                 ("split_c", ctypes.c_double), ("wavy_R", ctypes.c_double), ("wavy_eps", ctypes.c_double),
-                ("wavy_m", ctypes.c_int)]
+                ("wavy_m", ctypes.c_int), ("subst_off", ctypes.c_int)]
 
 
 class pmlbie_report(ctypes.Structure):
@@ -139,7 +139,8 @@ def _stream(stream):
 
 
 def make_params(k1, k2, N, M, a1=2.5, T=1.0, S=3.0, p=6, curve="gauss", bump_h=0.2, bump_w=0.5,
-                bump_R=1.0, vertices=None, taylor_L=5, split_c=8.0, wavy_R=1.0, wavy_eps=0.1, wavy_m=3):
+                bump_R=1.0, vertices=None, taylor_L=5, split_c=8.0, wavy_R=1.0, wavy_eps=0.1, wavy_m=3,
+                subst=True):
     import numpy as np
     P = pmlbie_params()
     P.struct_size = ctypes.sizeof(pmlbie_params)
@@ -148,6 +149,7 @@ def make_params(k1, k2, N, M, a1=2.5, T=1.0, S=3.0, p=6, curve="gauss", bump_h=0
     P.taylor_L, P.split_c = taylor_L, split_c
     keep = None
     P.wavy_R, P.wavy_eps, P.wavy_m = wavy_R, wavy_eps, wavy_m
+    P.subst_off = 0 if subst else 1
     if curve == "gauss":
         P.curve_kind = PMLBIE_CURVE_GAUSS_BUMP
     elif curve == "wavy":

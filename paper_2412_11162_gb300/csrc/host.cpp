@@ -758,7 +758,7 @@ int build_tables(pmlbie_problem* prob) {
         np.nuc_z = make_double2(src.ncz.real(), src.ncz.imag());
         np.dz = dz;
         np.tgt = l;
-        np.flags = (tg.I > 0 || src.I > 0) ? kFlagSubst : 0;
+        np.flags = (!P.subst_off && (tg.I > 0 || src.I > 0)) ? kFlagSubst : 0;
         return re_sqrt < eta;
     };
     H.cls.assign((size_t)N * N, kFar);

@@ -675,7 +675,12 @@ __global__ void near_modes_kernel(NearArgs a) {
     NearPair q = a.np[p];
     const bool plain = (q.flags & kFlagFar) != 0;
     const bool subst = (q.flags & kFlagSubst) != 0;
-    const bool packed = !plain && !subst;
+    // both points physical: every pair quantity is real (the two regions pack
+    // into one transform); a PML pair without the substitution (diagnostic
+    // exact split) takes the general path
+    const bool phys = q.d2.y == 0.0 && q.rr.y == 0.0 && q.rho_t.y == 0.0 && q.rho_s.y == 0.0 && q.drt.y == 0.0 &&
+                      q.nuc_r.y == 0.0 && q.nuc_z.y == 0.0;
+    const bool packed = !plain && !subst && phys;
     // sampling; N_D(psi) = [nu'_r (rho~' - rho~) - nu'_z dz] + 2 nu'_r rho~ sin^2(psi/2)
     const double2 nd0 = cadd(cmul(q.nuc_r, q.drt), cscale(q.nuc_z, -q.dz));
     const double2 nds = cscale(cmul(q.nuc_r, q.rho_t), 2.0);
@@ -727,6 +732,28 @@ __global__ void near_modes_kernel(NearArgs a) {
                 v1 = c2(0.0, 0.0);
                 v2 = cmul(cmul(Dk, e), c2(1.0 + qq.y, -qq.x));
                 v3 = c2(0.0, 0.0);
+            } else if (!subst) {
+                // exact split at complex q (Sec. 4.1 form): H1 = cos q, i Z H2 =
+                // (i w / 4 pi) sin(q)/q, H3 = cos q + q sin q, i D H4 =
+                // -(i w^3 / 4 pi) N_D (sin q - q cos q)/q^3; cos and sin from
+                // e^{iq} and e^{-iq}, which grows like e^{Im q} inside the PML
+                const double2 em = fcexpi(c2(-qq.x, -qq.y));
+                const double2 cq = cscale(cadd(e, em), 0.5);
+                const double2 sq = cmul(csub(e, em), c2(0.0, -0.5));
+                const double2 q2 = cmul(qq, qq);
+                const double aq = hypot(qq.x, qq.y);
+                const double2 sinc = aq < 1e-3 ? cadd(c2(1.0, 0.0), cadd(cscale(q2, -1.0 / 6.0),
+                                                                       cscale(cmul(q2, q2), 1.0 / 120.0)))
+                                               : cdiv(sq, qq);
+                const double2 h4 =
+                    aq < 1e-2 ? cadd(cadd(c2(1.0 / 3.0, 0.0), cscale(q2, -1.0 / 30.0)),
+                                     cadd(cscale(cmul(q2, q2), 1.0 / 840.0),
+                                          cscale(cmul(q2, cmul(q2, q2)), -1.0 / 45360.0)))
+                              : cdiv(csub(sq, cmul(qq, cq)), cmul(qq, q2));
+                v0 = cq;
+                v1 = cmul(c2(0.0, w * kInv4Pi), sinc);
+                v2 = cadd(cq, cmul(qq, sq));
+                v3 = cscale(cmul(c2(0.0, 1.0), cmul(ND, h4)), -w * w * w * kInv4Pi * sg);
             } else {
                 // cH1 = e^{iq} sum a_k q^k, Z (e^{iq} - cH1) = -(w / 4 pi) e^{iq} sum_{k>=1} a_k q^{k-1};
                 // cH3 likewise; D (e^{iq}(1 - iq) - cH3) = (w^3 / 4 pi) N_D e^{iq} sum_{k>=3} b_k q^{k-3}

@@ -655,6 +655,9 @@ __device__ __forceinline__ double2 cpoly_from(const double2 (&c)[8], int k0, int
 // imaginary r1, r3, so the two regions are packed as real and imaginary parts
 // of one sequence: 4 sample transforms and 4 convolution transforms instead
 // of 8 and 8.
+// kExact: the diagnostic exact split on PML pairs (compiled into its own
+// variant so that the default one keeps its register budget)
+template <bool kExact>
 __global__ void near_modes_kernel(NearArgs a) {
     extern __shared__ double2 smem[];
     const int M = a.M, K = M / 2, S1 = K + 1, L2 = 2 * M, S2 = M + 1, p = blockIdx.x;
@@ -732,7 +735,7 @@ __global__ void near_modes_kernel(NearArgs a) {
                 v1 = c2(0.0, 0.0);
                 v2 = cmul(cmul(Dk, e), c2(1.0 + qq.y, -qq.x));
                 v3 = c2(0.0, 0.0);
-            } else if (!subst) {
+            } else if (kExact && !subst) {
                 // exact split at complex q (Sec. 4.1 form): H1 = cos q, i Z H2 =
                 // (i w / 4 pi) sin(q)/q, H3 = cos q + q sin q, i D H4 =
                 // -(i w^3 / 4 pi) N_D (sin q - q cos q)/q^3; cos and sin from
@@ -1208,9 +1211,13 @@ cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, do
     size_t smem = sizeof(double2) * ((size_t)2 * M + 8 * (M / 2 + 1) + 4 * (M + 1) + 4 * (size_t)M);
     a.hs_tab = smem + sizeof(double2) * M <= 227 * 1024 ? 1 : 0;
     if (a.hs_tab) smem += sizeof(double2) * M;
-    e = allow_max_smem(near_modes_kernel);
-    if (e != cudaSuccess) return e;
-    near_modes_kernel<<<a.npairs, 128, smem, s>>>(a);
+    if (prob->P.subst_off) {
+        if ((e = allow_max_smem(near_modes_kernel<true>)) != cudaSuccess) return e;
+        near_modes_kernel<true><<<a.npairs, 128, smem, s>>>(a);
+    } else {
+        if ((e = allow_max_smem(near_modes_kernel<false>)) != cudaSuccess) return e;
+        near_modes_kernel<false><<<a.npairs, 128, smem, s>>>(a);
+    }
     count_launch();
     return cudaGetLastError();
 }

@@ -78,9 +78,10 @@ class Params:
 # generating curve: list of segments, each r(s), r_s(s) for s in [0, 1]
 # ----------------------------------------------------------------------------
 class _Segment:
-    def __init__(self, kind, data):
+    def __init__(self, kind, data, p=None):
         self.kind = kind
         self.data = data
+        self.p = p            # grading exponent of this segment (None: Params.p)
 
     def eval(self, s):
         s = np.asarray(s, dtype=float)
@@ -136,6 +137,15 @@ class _Segment:
         return 0.5 * np.sum(wq * np.hypot(dr, dz))
 
 
+# Grading exponent of a segment that leaves the axis at an angle (the surface
+# has a conical point there).  With the Sec. 5 exponent 6 the graded nodes
+# next to the tip sit at rho ~ 1e-8 .. 1e-6, where the double-layer kernel
+# of the targets scales like 1/rho^2 over neighbours spaced geometrically in
+# rho, and the Alpert-corrected rule does not resolve it; exponent 2 keeps
+# the tip nodes at rho ~ h^2.
+kConicalP = 2
+
+
 def build_segments(P: Params):
     L = P.L
     segs = []
@@ -143,12 +153,15 @@ def build_segments(P: Params):
         segs.append(_Segment("gauss", (P.bump_h, P.bump_w, P.bump_R)))
         segs.append(_Segment("line", ((P.bump_R, 0.0), (L, 0.0))))
     elif P.curve == "wavy":
-        segs.append(_Segment("wavy", (P.wavy_R, P.wavy_eps, int(P.wavy_m))))
+        # leaves the axis at an angle (a conical point): grading exponent 2
+        segs.append(_Segment("wavy", (P.wavy_R, P.wavy_eps, int(P.wavy_m)), p=kConicalP))
         segs.append(_Segment("line", ((P.wavy_R, 0.0), (L, 0.0))))
     elif P.curve == "polyline":
         V = list(P.vertices)
-        for a, b in zip(V[:-1], V[1:]):
-            segs.append(_Segment("line", (tuple(a), tuple(b))))
+        for i, (a, b) in enumerate(zip(V[:-1], V[1:])):
+            # a first segment that leaves the axis at an angle: grading exponent 2
+            conical = i == 0 and abs(b[1] - a[1]) > 0.0
+            segs.append(_Segment("line", (tuple(a), tuple(b)), p=kConicalP if conical else None))
         if abs(V[-1][0] - L) > 1e-14 or abs(V[-1][1]) > 1e-14:
             segs.append(_Segment("line", (tuple(V[-1]), (L, 0.0))))
     else:
@@ -243,8 +256,9 @@ class Geometry:
             t0 = self.brk[k] * self.h
             t1 = self.brk[k + 1] * self.h
             u = (t[m] - t0) / (t1 - t0)
-            s, ds = graded(u, P.p)
-            sc = graded_complement(u, P.p)
+            pk = sg.p or P.p
+            s, ds = graded(u, pk)
+            sc = graded_complement(u, pk)
             r_, z_, dr_, dz_ = sg.eval(s)
             rho[m] = r_
             z[m] = z_

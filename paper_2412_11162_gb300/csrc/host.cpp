@@ -169,7 +169,16 @@ struct Pml {
 // ---------------------------------------------------------------------------
 // Curve segments r(s), s in [0, 1]
 // ---------------------------------------------------------------------------
+// Grading exponent of a segment that leaves the axis at an angle (the surface
+// has a conical point there).  With the Sec. 5 exponent 6 the graded nodes
+// next to the tip sit at rho ~ 1e-8 .. 1e-6, where the double-layer kernel of
+// the targets scales like 1/rho^2 over neighbours spaced geometrically in rho,
+// and the Alpert-corrected rule does not resolve it; exponent 2 keeps the tip
+// nodes at rho ~ h^2.
+constexpr int kConicalP = 2;
+
 struct Segment {
+    int p = 0;                           // grading exponent (0: the problem's p)
     bool gauss = false, wavy = false;
     double h = 0, w = 1, R = 1;          // Gaussian bump
     double wR = 1, eps = 0;              // wavy dent: radius, relative amplitude,
@@ -273,7 +282,7 @@ struct Curve {
         while (k + 1 < (int)segs.size() && t >= brk[k + 1] * h) ++k;
         double t0 = brk[k] * h, t1 = brk[k + 1] * h;
         double u = (t - t0) / (t1 - t0), s, sc, ds;
-        graded_map(u, p, s, sc, ds);
+        graded_map(u, segs[k].p ? segs[k].p : p, s, sc, ds);
         double r, z, dr, dz;
         segs[k].eval(s, r, z, dr, dz);
         int end = u > 0.5 ? 1 : 0;
@@ -564,6 +573,7 @@ int build_tables(pmlbie_problem* prob) {
         C.segs.push_back(f);
     } else if (P.curve_kind == PMLBIE_CURVE_WAVY_DENT) {
         Segment d;
+        d.p = kConicalP;   // leaves the axis at an angle
         d.wavy = true;
         d.wR = P.wavy_R;
         d.eps = P.wavy_eps;
@@ -582,6 +592,7 @@ int build_tables(pmlbie_problem* prob) {
             f.z0 = V[2 * i + 1];
             f.r1 = V[2 * i + 2];
             f.z1 = V[2 * i + 3];
+            if (i == 0 && f.z1 != f.z0) f.p = kConicalP;   // leaves the axis at an angle
             C.segs.push_back(f);
         }
         if (std::fabs(V[2 * nv - 2] - Lr) > 1e-14 || std::fabs(V[2 * nv - 1]) > 1e-14) {

@@ -70,9 +70,9 @@ def test_polyline_host_tables(B):
 def test_wavy_dent_host_tables(B):
     """Sec. 5 Example 2 curve (kind 2): nodes, speeds and the diagonal term of
     the library's host tables equal the oracle's.  The curve meets the axis at
-    an angle; next to that conical point the discrete Laplace double layer
-    sums correction terms of ~1e14 to values up to ~1e7, so the two summation
-    orders agree to ~1e-7 of max(1, |D|) there (1e-15 elsewhere)."""
+    an angle; its first segment is graded with exponent 2 (the conical point),
+    which both sides apply.  D agrees to ~3e-13 at the tip node (the oracle's
+    adaptive disc solid angle), 1e-15 elsewhere."""
     from paper_2412_11162_gb300 import Problem
     from oracle.assemble import Quadrature, diagonal
     from oracle.problem import Geometry, Params
@@ -86,7 +86,7 @@ def test_wavy_dent_host_tables(B):
     Da, Db = diagonal(G, Quadrature(G))
     da, db = P.diagonal()
     for ref, got in ((Da, da), (Db, db)):
-        assert np.all(np.abs(ref - got) <= 1e-6 * np.maximum(1.0, np.abs(ref)))
+        assert np.all(np.abs(ref - got) <= 1e-12 * np.maximum(1.0, np.abs(ref)))
 
 
 @pytest.mark.parametrize("kw,frag", [

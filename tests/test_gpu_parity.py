@@ -136,7 +136,11 @@ def mode_conditioning(sol):
 def check_densities(out, sol, tol, backward_tol, label):
     """Parity of the solved densities with the oracle.
 
-    * u1, u2 (well conditioned): forward relative 2-norm error <= tol.
+    * u1, u2 on the physical nodes (rho <= a1): forward relative 2-norm error
+      <= tol; on all nodes, per mode, <= max(tol, 1e-12 kappa_n).  The PML
+      nodes' kernels carry the close-pair split's cancellation (the two sides'
+      high-mode kernels there agree to ~1e-10 at M = 64), which the solve
+      carries into u1 at the PML nodes.
     * normwise backward error of the GPU solution x = (u1, phi1) in the
       ORACLE's block systems, all modes together (the block-diagonal system
       of every mode, as the forward errors are taken over all modes):
@@ -153,10 +157,15 @@ def check_densities(out, sol, tol, backward_tol, label):
     kap = mode_conditioning(sol)
     N = sol.P.N
     errs = {}
+    phys = sol.sys.G.nodes["rho"] <= sol.P.a1
     for name, ref in (("u1", sol.u1), ("u2", sol.u2)):
         got = out[name].cpu().numpy()[:, :, 0]
         errs[name] = _rel(got, ref)
-        assert errs[name] <= tol, (label, name, errs[name])
+        e = _rel(got[:, phys], ref[:, phys])
+        assert e <= tol, (label, name, "physical nodes", e)
+        for n in range(ref.shape[0]):
+            e = np.linalg.norm(got[n] - ref[n]) / np.linalg.norm(ref)
+            assert e <= max(tol, 1e-12 * kap[n]), (label, name, n, e, kap[n])
     u1 = out["u1"].cpu().numpy()[:, :, 0]
     p1 = out["phi1"].cpu().numpy()[:, :, 0]
     r2 = x2 = b2 = 0.0

@@ -48,9 +48,14 @@ def prob():
     return Problem(CFG1["k1"], CFG1["k2"], CFG1["N"], CFG1["M"])
 
 
-def check_point(out, r, ref, tol, label, sol=None):
+def check_point(out, r, ref, tol, label, sol=None, backward_tol=1e-13, kappa_coef=1e-12):
     """Column r of the GPU outputs against the oracle's point-source solution
-    (sol: the oracle Solution whose matrices ref uses; default the N = 128 one)."""
+    (sol: the oracle Solution whose matrices ref uses; default the N = 128 one).
+    The backward error of the GPU solution in the oracle's systems is bounded
+    below by the two sides' matrix difference, itself within the modal-kernel
+    parity bound (1e-10 per mode, reached by the PML pairs' high modes).
+    Per mode the forward error is held to max(tol, kappa_coef kappa_n), the
+    matrix agreement times the mode's conditioning."""
     from test_gpu_parity import mode_conditioning
     kap = mode_conditioning(sol if sol is not None else oracle_solution(**CFG1))
     g = {k: v[:, :, r].cpu().numpy() for k, v in out.items()}
@@ -64,12 +69,12 @@ def check_point(out, r, ref, tol, label, sol=None):
         b2 += np.linalg.norm(B) ** 2
         anorm = max(anorm, np.linalg.norm(A))
     bwd = np.sqrt(r2) / (anorm * np.sqrt(x2) + np.sqrt(b2))
-    assert bwd <= 1e-13, (label, "backward", bwd)
+    assert bwd <= backward_tol, (label, "backward", bwd)
     for k in ("u1", "phi1", "u2", "phi2"):
         want = getattr(ref, k)
         for n in range(want.shape[0]):
             e = np.linalg.norm(g[k][n] - want[n]) / np.linalg.norm(want)
-            assert e <= max(tol, 1e-12 * kap[n]), (label, k, n, e, kap[n])
+            assert e <= max(tol, kappa_coef * kap[n]), (label, k, n, e, kap[n])
     print(label, "backward %.1e" % bwd, {k: "%.1e" % _rel(g[k], getattr(ref, k)) for k in g})
 
 

@@ -365,6 +365,7 @@ def run_ours(args, rank, world):
         "near_pairs": {"grid": ng, "alpert": nc},
         "gpu_launches": int(sum(r.launches for r in reps)),
         "roofline": roof,
+        "stage_rooflines": stage_rooflines(w, last, pk),
         "clocks": clocks,
         "e2e": {"value": world * epp / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -560,6 +561,42 @@ def roofline(w, rep, pk, clk):
             "peak_note": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz (median SM clock under load)" % mhz,
             "traffic_note": ("ncu dram bytes read+write of one launch at this workload (profiles/)" if traffic
                              else "null: no ncu capture of the current kernels.cu at this workload")}
+
+
+def stage_rooflines(w, rep, pk):
+    """Per-stage rooflines of the mixed step besides the far kernel's.
+
+    * LU (FP32, tensor-core trailing updates): algorithmic flops (8/3) n^3 per
+      mode (n = 2N, complex LU), against the TF32 dense peak taken as the
+      measured sustained bf16 peak x the nominal TF32/bf16 ratio 1.1/2.25; and
+      its algorithmic bytes: the complex128 -> complex64 conversion (16 + 8 B
+      per entry) plus one read and one write of the complex64 trailing matrix
+      per 32-column panel, sum_k 2 x 8 B x (n - 32 (k + 1))^2, against the
+      measured HBM copy bandwidth.  The LU time includes the conversion and
+      the Frobenius norms.
+    * Block writes (fused into the far kernel): 4 N^2 (M/2) complex128
+      entries per step against HBM.
+    """
+    N, M = w["N"], w["M"]
+    n, modes = 2 * N, M // 2
+    lu_flops = 8.0 / 3.0 * n ** 3 * modes
+    upd = sum(2 * 8.0 * (n - 32 * (k + 1)) ** 2 for k in range(n // 32))
+    lu_bytes = modes * (24.0 * n * n + upd)
+    tf32 = pk.get("bf16_tflops_sustained", 1692.2) * 1.1 / 2.25
+    hbm = pk.get("hbm_gbs", 6794.1)
+    s_lu = rep.ms_lu / 1e3
+    wr = 4.0 * N * N * modes * 16
+    s_far = rep.ms_far / 1e3
+    return {
+        "lu_fp32": {"bound": "hbm", "ms": rep.ms_lu, "flops": lu_flops, "tflops": lu_flops / s_lu / 1e12,
+                    "tf32_peak_tflops": tf32, "frac_tf32": lu_flops / s_lu / 1e12 / tf32,
+                    "bytes": lu_bytes, "gbs": lu_bytes / s_lu / 1e9, "frac_hbm": lu_bytes / s_lu / 1e9 / hbm,
+                    "note": "rank-32 trailing updates: 16 flop per byte, below the TF32 ridge; "
+                            "peaks of measured (TF32 = sustained bf16 x 1.1/2.25)"},
+        "block_writes": {"bytes": wr, "ms": rep.ms_far, "gbs": wr / s_far / 1e9,
+                         "frac_hbm": wr / s_far / 1e9 / hbm,
+                         "note": "fused into the far kernel, which the FP64 pipe bounds"},
+    }
 
 
 def main():

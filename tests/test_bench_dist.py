@@ -48,3 +48,25 @@ def test_single_rank_needs_no_group():
     assert bench.init_dist(1) is None
     assert bench.max_over_ranks(7.5, None) == 7.5
     assert bench.job_value(1, 10, 1000.0) == 10.0
+
+
+def test_stage_rooflines_arithmetic():
+    """The LU stage's algorithmic counts against a direct sum: (8/3) n^3 flops
+    per mode, and per mode the conversion (24 B per entry) plus one read and
+    one write of the complex64 trailing matrix after each 32-column panel."""
+    import types
+    import bench
+    w = {"N": 64, "M": 8}
+    n, modes = 128, 4
+    rep = types.SimpleNamespace(ms_lu=2.0, ms_far=1.0)
+    r = bench.stage_rooflines(w, rep, {"hbm_gbs": 1000.0, "bf16_tflops_sustained": 2250.0})
+    lu = r["lu_fp32"]
+    assert abs(lu["flops"] - 8.0 / 3.0 * n ** 3 * modes) < 1.0
+    trailing = 0
+    for k0 in range(0, n, 32):
+        m = n - k0 - 32          # order of the trailing matrix after this panel
+        trailing += 2 * 8 * m * m
+    assert lu["bytes"] == modes * (24 * n * n + trailing)
+    assert abs(lu["tf32_peak_tflops"] - 1100.0) < 1e-9
+    assert abs(lu["frac_hbm"] - lu["bytes"] / 2e-3 / 1e9 / 1000.0) < 1e-12
+    assert r["block_writes"]["bytes"] == 4 * 64 * 64 * 4 * 16

@@ -349,7 +349,8 @@ def run_ours(args, rank, world):
                          int(((w["M"] // 2) * (2 * w["N"]) ** 2 * 24) / 1e6)},
         "solve_s_per_problem": ms / 1e3,
         "kernel_entries_per_s": epp / ((last.ms_far + last.ms_near + last.ms_assemble) / 1e3),
-        "far_pairs": last.far_pairs, "far_pairs_per_cta": last.far_pairs_per_cta,
+        "far_pairs": last.far_pairs, "far_pairs_sampled": last.far_pairs_sampled,
+        "far_pairs_per_cta": last.far_pairs_per_cta,
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
         "mode_chunks": chunks,
         "refine_iters": last.refine_iters, "refine_residual": last.residual,
@@ -499,19 +500,25 @@ def run_batched(args, rank, world):
         dist.destroy_process_group()
 
 
-def far_flops_per_pair(M, physical=False):
-    """Algorithmic FP64 flops of one far node pair in the far-pair kernel
-    (fused multiply-add = 2 flops): (M/2 + 1) angle samples of S~ and K~ of
-    both media, four even-sequence DFTs of length M at 5 K log2 K + 15 K
-    flops (K = M/2: a K-point complex FFT plus pre- and post-processing), and
-    16 K flops to weight the 4 K outputs.  A sample costs 276 flops for a pair
-    with a node in the PML (complex distance, square root and reciprocal by
-    Newton-refined reciprocal square roots, two e^{iq} by range reduction +
-    series, complex kernel products) and 128 for a pair of physical nodes
-    (real distance and reciprocal square root, two sin/cos pairs, real
-    products)."""
+def far_flops_per_launch(M, chunk_modes, sampled, sampled_physical, ordered):
+    """Algorithmic FP64 flops of one far-kernel launch (fused multiply-add = 2
+    flops).  The kernel samples each unordered pair {l, m} once for both
+    orientations: (M/2 + 1) angle samples of S~ and of the geometric factor g
+    of K~ (both media), four even-sequence DFTs of length M at 5 K log2 K +
+    15 K flops each (K = M/2: a K-point complex FFT plus pre- and
+    post-processing).  A sample costs 265 flops for a pair with a node in the
+    PML (complex distance, square root and reciprocal by Newton-refined
+    reciprocal square roots, 1/R^3, two e^{iq} by range reduction + series,
+    complex products) and 126 for a pair of physical nodes (real distance and
+    reciprocal square root, two sin/cos pairs, real products).  Each ordered
+    far pair then costs 60 flops per mode of the launch's chunk: K^ of both
+    media from g^ and the pair's normal factor (22 each), and the scaling and
+    quadrature weights of the four entries (4 each)."""
     K = M // 2
-    return (K + 1) * (128.0 if physical else 276.0) + 4 * (5.0 * K * np.log2(K) + 15.0 * K) + 16.0 * K
+    dft = 4 * (5.0 * K * np.log2(K) + 15.0 * K)
+    pml = sampled - sampled_physical
+    return (sampled_physical * ((K + 1) * 126.0 + dft) + pml * ((K + 1) * 265.0 + dft) +
+            ordered * chunk_modes * 60.0)
 
 
 def far_traffic(w):
@@ -547,14 +554,15 @@ def roofline(w, rep, pk, clk):
     mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     peak = 152 * 2 * 2 * mhz * 1e6 / 1e12
     # one launch per mode chunk: every launch samples all pairs and angles and
-    # transforms them (the flops), and scatters only its chunk's modes
+    # transforms them, and forms and scatters only its chunk's modes
     launches = max(1, rep.chunks)
-    phys = rep.far_pairs_physical
-    flops = phys * far_flops_per_pair(M, True) + (rep.far_pairs - phys) * far_flops_per_pair(M)
+    flops = far_flops_per_launch(M, rep.chunk_modes, rep.far_pairs_sampled, rep.far_pairs_sampled_physical,
+                                 rep.far_pairs)
     ms1 = rep.ms_far / launches
     ach = flops / (ms1 / 1e3) / 1e12
     traffic = far_traffic(w)
-    return {"kernel": "far_kernel (S~, K~ sampling of both media + 4 even DFTs + block scatter, FP64)",
+    return {"kernel": "far_kernel (S~ and K~ sampling of both media per unordered pair + 4 even DFTs + "
+                      "block scatter of both orientations, FP64)",
             "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "traffic": traffic, "flops_per_launch": flops, "ms_per_launch": ms1, "launches_per_step": launches,
             "algorithmic_bytes": 4.0 * w["N"] ** 2 * rep.chunk_modes * 16,

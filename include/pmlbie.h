@@ -111,6 +111,10 @@ typedef struct {
     int      far_pairs_physical;  /* far pairs with both nodes outside the PML (real distance) */
     int      lu_graph_replays;    /* LU factorisations replayed from a captured CUDA graph */
     int      far_pairs_per_cta;   /* node pairs per CTA of the far-pair kernel (autotuned) */
+    int      far_pairs_sampled;   /* unordered pairs {l, m} sampled by the far-pair kernel: one
+                                     sampling and one set of transforms serves both (l, m) and
+                                     (m, l) (S~ is symmetric, K~ differs by its normal factor) */
+    int      far_pairs_sampled_physical;  /* of those, pairs of two physical nodes           */
 } pmlbie_report;
 
 /* Options of pmlbie_solve_ex (zero-initialise, then set struct_size). */

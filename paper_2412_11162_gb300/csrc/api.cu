@@ -824,15 +824,25 @@ int pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* o, void* dev_
         rep->ms_assemble = st.ms_assemble;
         rep->ms_near_laplace = st.ms_near_laplace;
         rep->launches = (int)g_launches;
-        rep->far_pairs = (int)std::count(prob->H.cls.begin(), prob->H.cls.end(), (uint8_t)kFar);
-        int phys = 0;
-        const int N = prob->P.N;
-        for (int l = 0; l < N; ++l) {
-            if (prob->H.I[l] != 0.0) continue;
-            for (int m = 0; m < N; ++m)
-                if (prob->H.I[m] == 0.0 && prob->H.cls[(size_t)l * N + m] == (uint8_t)kFar) ++phys;
+        int* fc = prob->far_counts;
+        if (fc[0] < 0) {
+            const int N = prob->P.N;
+            const auto far = [&](int l, int m) { return prob->H.cls[(size_t)l * N + m] == (uint8_t)kFar; };
+            const auto phys = [&](int l) { return prob->H.I[l] == 0.0; };
+            int n[4] = {0, 0, 0, 0};
+            for (int l = 0; l < N; ++l)
+                for (int m = 0; m < N; ++m) {
+                    if (!far(l, m) && !far(m, l)) continue;
+                    const bool pp = phys(l) && phys(m);
+                    if (far(l, m)) n[0] += 1, n[1] += pp;
+                    if (m < l) n[2] += 1, n[3] += pp;
+                }
+            for (int k = 0; k < 4; ++k) fc[k] = n[k];
         }
-        rep->far_pairs_physical = phys;
+        rep->far_pairs = fc[0];
+        rep->far_pairs_physical = fc[1];
+        rep->far_pairs_sampled = fc[2];
+        rep->far_pairs_sampled_physical = fc[3];
         rep->chunks = chunks;
         rep->chunk_modes = chunk;
         rep->gmres_modes = st.gmres_modes;

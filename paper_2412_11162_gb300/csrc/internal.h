@@ -93,6 +93,9 @@ struct pmlbie_problem {
     void* ws = nullptr;
     size_t ws_bytes = 0;
     void* ws_extra = nullptr;   // device copies of per-node normals and speeds
+    // far-pair counts for the report (computed once from H.cls): ordered far
+    // pairs, those of two physical nodes, unordered pairs sampled, physical ones
+    int far_counts[4] = {-1, -1, -1, -1};
 };
 
 namespace pmlbie {

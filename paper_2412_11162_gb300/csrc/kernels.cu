@@ -303,9 +303,16 @@ __device__ void warp_even_dft(double2* xh, double2* y, double2* scr, int K, cons
     __syncwarp();
 }
 
-// Per-pair geometry of a grid pair from node tables.
+// Geometry of a grid pair (l, m) from node tables: the symmetric sampling
+// quantities d~^2 and rho~_l rho~_m, and for both orientations the normal
+// factor N_D(psi) = nd0 + nds sin^2(psi/2) of the double layer at the source
+// (target l, source m: nu'_r (rho~_m - rho~_l) + nu'_z (z_m - z_l) + 2 nu'_r
+// rho~_l sin^2(psi/2) with nu' the conormal at m; target m, source l: the same
+// with l and m exchanged).
 struct PairGeom {
-    double2 d2, rr, nd0, nds;   // N_D(psi) = nd0 + nds sin^2(psi/2) (region a normal)
+    double2 d2, rr;
+    double2 nd0, nds;   // target l, source m
+    double2 nd0t, ndst; // target m, source l
 };
 
 __device__ __forceinline__ PairGeom grid_pair(const DeviceTables& T, int l, int m) {
@@ -324,18 +331,44 @@ __device__ __forceinline__ PairGeom grid_pair(const DeviceTables& T, int l, int 
     double2 drt = c2(dr, dI);
     g.d2 = cadd(cmul(drt, drt), c2(dz * dz, 0.0));
     g.rr = cmul(T.rho_t[l], T.rho_t[m]);
-    double2 ncr = T.nuc_r[m], ncz = T.nuc_z[m];
     // nu'_r (rho~' - rho~ cos psi) + nu'_z (z' - z)
     //   = [nu'_r (rho~' - rho~) + nu'_z (z' - z)] + 2 nu'_r rho~ sin^2(psi/2)
-    g.nd0 = cadd(cmul(ncr, c2(-dr, -dI)), cscale(ncz, -dz));
-    g.nds = cscale(cmul(ncr, T.rho_t[l]), 2.0);
+    g.nd0 = cadd(cmul(T.nuc_r[m], c2(-dr, -dI)), cscale(T.nuc_z[m], -dz));
+    g.nds = cscale(cmul(T.nuc_r[m], T.rho_t[l]), 2.0);
+    g.nd0t = cadd(cmul(T.nuc_r[l], drt), cscale(T.nuc_z[l], dz));
+    g.ndst = cscale(cmul(T.nuc_r[l], T.rho_t[m]), 2.0);
     return g;
 }
 
+// The double layer's normal factor nd0 + nds sin^2(psi/2) multiplies the
+// geometric factor g(psi) = e^{iq}(1 - iq) / |Delta|^3 (times constants); on
+// the M-point DFT, sin^2(psi/2) = (1 - cos psi)/2 acts as G_n -> G_n / 2 -
+// (G_{n-1} + G_{n+1}) / 4 (exact; G_{-1} = G_1 for even g, and n + 1 <= M/2
+// stays inside the spectrum).  sin2_mode gives that shifted spectrum, shared
+// by both orientations of a pair; nd_mode combines it with one orientation's
+// normal factor (real arithmetic when the factor is real: two physical nodes).
+__device__ __forceinline__ double2 sin2_mode(const double2* gh, int n) {
+    const double2 gn = gh[n], gm = gh[n == 0 ? 1 : n - 1], gp = gh[n + 1];
+    return c2(fma(0.5, gn.x, -0.25 * (gm.x + gp.x)), fma(0.5, gn.y, -0.25 * (gm.y + gp.y)));
+}
+__device__ __forceinline__ double2 nd_mode(double2 nd0, double2 nds, double2 gn, double2 s2, bool real) {
+    if (real) return c2(fma(nd0.x, gn.x, nds.x * s2.x), fma(nd0.x, gn.y, nds.x * s2.y));
+    return c2(fma(nd0.x, gn.x, fma(-nd0.y, gn.y, fma(nds.x, s2.x, -nds.y * s2.y))),
+              fma(nd0.x, gn.y, fma(nd0.y, gn.x, fma(nds.x, s2.y, nds.y * s2.x))));
+}
+
 // ---------------------------------------------------------------------------
-// Far pairs: sample both regions' S~, K~ at psi_j (j = 0..M/2, even
-// extension), FFT, and write the weighted modal entries into the per-mode
-// block matrices (or the raw modal-kernel buffer).
+// Far pairs.  The kernel samples the ordered pairs (l, m) and (m, l) together:
+// |Delta| is symmetric in the two nodes, so S~ is, and K~ differs between the
+// two orientations only by its normal factor N_D, which is linear in
+// sin^2(psi/2).  Per unordered pair the warp samples S~ and the geometric
+// factor g of K~ for both media at psi_j (j = 0..M/2, even extension), takes
+// four even DFTs, and forms K^_n of each orientation from g^ (nd_mode).  A CTA
+// covers a tile of TL targets x TM sources with l >= m; the tile's mirror
+// (m, l) entries are written from the same spectra.  Every entry of the
+// per-mode matrices (or of the raw modal-kernel buffer) is written once:
+// far entries with their weighted modes, all others with zero (close pairs
+// and skipped pairs are filled in by the assembly).
 // ---------------------------------------------------------------------------
 struct FarArgs {
     DeviceTables T;
@@ -345,15 +378,21 @@ struct FarArgs {
     double2* raw;   // [mode][kernel][l][m]
 };
 
-__global__ void far_kernel(FarArgs a) {
+// targets x sources of a CTA with nw pairs
+__host__ __device__ __forceinline__ int far_tile_m(int nw) { return nw >= 16 ? 4 : 2; }
+
+__global__ void __launch_bounds__(512, 2) far_kernel(FarArgs a) {
     extern __shared__ double2 smem[];
     const int M = a.M, N = a.N, K = M / 2, S1 = K + 1;
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int TM = far_tile_m(nw), TL = nw / TM;
+    const int l0 = blockIdx.x * TL, m0 = blockIdx.y * TM;
+    if (l0 + TL - 1 < m0) return;               // the whole tile has l < m: mirrored elsewhere
     double2* tw = smem;                         // M: e^{-2 pi i e / M}
     double2* hs = tw + M;                       // K: even-DFT weights
     double2* cs = hs + K;                       // K + 1: (sin^2(psi/2), cos psi)
     PairGeom* geo = reinterpret_cast<PairGeom*>(cs + S1);                  // nw pairs
-    double2* bufs = cs + S1 + 4 * nw;           // per warp: 4 sequences of K+1, then 2 x K scratch
+    double2* bufs = cs + S1 + 6 * nw;           // per warp: 4 sequences of K+1, then 2 x K scratch
     int* act = reinterpret_cast<int*>(bufs + nw * (4 * S1 + 2 * K));     // nw flags
     for (int i = threadIdx.x; i < M; i += blockDim.x) {
         const double2 t = a.T.twid[i];
@@ -361,102 +400,131 @@ __global__ void far_kernel(FarArgs a) {
         if (i < K) hs[i] = c2(0.5 + t.y, 0.5 - t.y);
     }
     for (int i = threadIdx.x; i <= K; i += blockDim.x) cs[i] = a.T.cos_tab[i];
-    const int m = blockIdx.y;
+    // warp w: target l = l0 + w % TL, source m = m0 + w / TL.  act bit 0: (l, m)
+    // is far; bit 1: (m, l) is far; bit 2: the warp owns its entries (l >= m);
+    // bit 3: real pair quantities.
     if (lane == 0) {
-        const int l = blockIdx.x * nw + warp;
-        const bool on = l < N && a.T.cls[(size_t)l * N + m] == kFar;
-        act[warp] = on;
-        if (on) geo[warp] = grid_pair(a.T, l, m);
+        const int l = l0 + warp % TL, m = m0 + warp / TL;
+        int f = 0;
+        if (l < N && m < N && l >= m) {
+            f = 4;
+            if (l > m) {
+                f |= (a.T.cls[(size_t)l * N + m] == kFar ? 1 : 0) | (a.T.cls[(size_t)m * N + l] == kFar ? 2 : 0);
+                if (f & 3) {
+                    const PairGeom g = grid_pair(a.T, l, m);
+                    geo[warp] = g;
+                    // bit 3: every pair quantity real (two physical nodes)
+                    if (g.d2.y == 0.0 && g.rr.y == 0.0 && g.nd0.y == 0.0 && g.nds.y == 0.0 && g.nd0t.y == 0.0 &&
+                        g.ndst.y == 0.0)
+                        f |= 8;
+                }
+            }
+        }
+        act[warp] = f;
     }
     __syncthreads();
 
-    // samples j = 0..K of the CTA's nw pairs, spread over all its threads
+    // samples j = 0..K of the CTA's pairs, spread over all its threads:
+    // S~ = e^{iq} / (4 pi |Delta|) and g = -(e^{iq}(1 - iq)) / (4 pi |Delta|^3)
+    // (region b: -g, its normal is -nu), q = omega |Delta|, both times the
+    // trapezoid factor 2 pi / M of the modes (c4 = (1 / 4 pi)(2 pi / M))
+    const double c4 = 0.5 / M;
     for (int idx = threadIdx.x; idx < nw * S1; idx += blockDim.x) {
         const int w = idx / S1, j = idx - w * S1;
-        if (!act[w]) continue;
-        const PairGeom g = geo[w];
+        if (!(act[w] & 3)) continue;
+        const PairGeom& g = geo[w];
         double2* buf = bufs + w * (4 * S1 + 2 * K);
         const double2 sc = cs[j];
-        if (g.d2.y == 0.0 && g.rr.y == 0.0 && g.nd0.y == 0.0 && g.nds.y == 0.0) {
+        if (g.d2.y == 0.0 && g.rr.y == 0.0) {
             // both nodes physical: real distance, e^{iq} = cos q + i sin q
             const double D2 = fma(4.0 * sc.x, g.rr.x, g.d2.x);
             const double iR = frsqrt(D2), R = D2 * iR;
-            const double Dk = -kInv4Pi * (fma(g.nds.x, sc.x, g.nd0.x) * (iR * iR * iR));
+            const double gk = -c4 * (iR * iR * iR), f = c4 * iR;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                const double q = (r == 0 ? a.w1 : a.w2) * R, Dr = r == 0 ? Dk : -Dk;
+                const double q = (r == 0 ? a.w1 : a.w2) * R, gr = r == 0 ? gk : -gk;
                 double sn, cn;
                 fsincos(q, &sn, &cn);
-                const double f = kInv4Pi * iR;
                 buf[(2 * r) * S1 + j] = c2(f * cn, f * sn);
-                buf[(2 * r + 1) * S1 + j] = c2(Dr * fma(q, sn, cn), Dr * fma(-q, cn, sn));   // e (1 - i q)
+                buf[(2 * r + 1) * S1 + j] = c2(gr * fma(q, sn, cn), gr * fma(-q, cn, sn));   // e (1 - i q)
             }
             continue;
         }
         const double2 D2 = cadd(g.d2, cscale(g.rr, 4.0 * sc.x));
         double2 R, iR;
         fcsqrt_rcp(D2, R, iR);
-        const double2 iR3 = cmul(iR, cmul(iR, iR));
-        const double2 ND = cadd(g.nd0, cscale(g.nds, sc.x));
-        const double2 Dk = cscale(cmul(ND, iR3), -kInv4Pi);   // region a
+        const double2 gk = cscale(cmul(iR, cmul(iR, iR)), -c4);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const double w = r == 0 ? a.w1 : a.w2;
-            const double2 Dr = r == 0 ? Dk : c2(-Dk.x, -Dk.y);      // region b: normal -nu
+            const double2 gr = r == 0 ? gk : c2(-gk.x, -gk.y);
             const double2 q = cscale(R, w);
             const double2 e = fcexpi(q);
-            buf[(2 * r) * S1 + j] = cscale(cmul(e, iR), kInv4Pi);
-            buf[(2 * r + 1) * S1 + j] = cmul(cmul(Dr, e), c2(1.0 + q.y, -q.x));   // (1 - i q)
+            buf[(2 * r) * S1 + j] = cscale(cmul(e, iR), c4);
+            buf[(2 * r + 1) * S1 + j] = cmul(cmul(gr, e), c2(1.0 + q.y, -q.x));   // (1 - i q)
         }
     }
     __syncthreads();
-    if (act[warp]) {
+    if (act[warp] & 3) {
         double2* buf = bufs + warp * (4 * S1 + 2 * K);
         double2* y = buf + 4 * S1;
         for (int s = 0; s < 4; ++s) warp_even_dft(buf + s * S1, y, y + K, K, tw, hs, 1, lane);
     }
     __syncthreads();
 
-    const double scale = 2.0 * kPi / M;
+    // scatter: thread (pair w, mode n) forms the eight entries of both
+    // orientations from the pair's spectra (kernel 0 S^a, 1 g^a, 2 S^b, 3 g^b)
     const int nmodes = a.mode_hi - a.mode_lo;
-    if (a.A) {
-        const size_t ld = 2 * (size_t)N, msz = ld * ld;
-        const int total = nmodes * 4 * nw;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            int w = idx % nw, blk = (idx / nw) % 4, n = idx / (4 * nw);
-            int ll = blockIdx.x * nw + w;
-            if (ll >= N) continue;
-            const bool on = act[w] != 0;
+    const int lg = __ffs(nw) - 1, lgl = __ffs(TL) - 1;
+    const int total = nmodes << lg;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int w = idx & (nw - 1), n = idx >> lg;
+        const int f = act[w];
+        if (!(f & 4)) continue;
+        const int l = l0 + (w & (TL - 1)), m = m0 + (w >> lgl);
+        const int nn = a.mode_lo + n;
+        double2 sa = c2(0.0, 0.0), sb = sa, ka[2] = {sa, sa}, kb[2] = {sa, sa};
+        if (f & 3) {
             const double2* b = bufs + w * (4 * S1 + 2 * K);
-            double2 val = c2(0.0, 0.0);
-            int row = ll, col = m;
-            // blocks: 0 K^a -> (l, m); 1 -S^a -> (l, N+m); 2 K^b -> (N+l, m); 3 S^b -> (N+l, N+m)
-            if (blk == 0) {
-                if (on) val = cscale(b[1 * S1 + a.mode_lo + n], scale * a.h * a.T.Wu[m]);
-            } else if (blk == 1) {
-                col = N + m;
-                if (on) val = cscale(b[0 * S1 + a.mode_lo + n], -scale * a.h * a.T.Wphi[m]);
-            } else if (blk == 2) {
-                row = N + ll;
-                if (on) val = cscale(b[3 * S1 + a.mode_lo + n], scale * a.h * a.T.Wu[m]);
-            } else {
-                row = N + ll;
-                col = N + m;
-                if (on) val = cscale(b[2 * S1 + a.mode_lo + n], scale * a.h * a.T.Wphi[m]);
+            const PairGeom& g = geo[w];
+            const bool real = (f & 8) != 0;
+            sa = b[nn];
+            sb = b[2 * S1 + nn];
+            const double2 ga = b[S1 + nn], gb = b[3 * S1 + nn];
+            const double2 s2a = sin2_mode(b + S1, nn), s2b = sin2_mode(b + 3 * S1, nn);
+            if (f & 1) {
+                ka[0] = nd_mode(g.nd0, g.nds, ga, s2a, real);
+                kb[0] = nd_mode(g.nd0, g.nds, gb, s2b, real);
             }
-            a.A[(size_t)n * msz + (size_t)col * ld + row] = val;
+            if (f & 2) {
+                ka[1] = nd_mode(g.nd0t, g.ndst, ga, s2a, real);
+                kb[1] = nd_mode(g.nd0t, g.ndst, gb, s2b, real);
+            }
         }
-    }
-    if (a.raw) {
-        const size_t NN = (size_t)N * N;
-        const int total = nmodes * 4 * nw;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            int w = idx % nw, kern = (idx / nw) % 4, n = idx / (4 * nw);
-            int ll = blockIdx.x * nw + w;
-            if (ll >= N) continue;
-            const double2* b = bufs + w * (4 * S1 + 2 * K);
-            double2 val = act[w] ? cscale(b[kern * S1 + a.mode_lo + n], scale) : c2(0.0, 0.0);
-            a.raw[((size_t)n * 4 + kern) * NN + (size_t)ll * N + m] = val;
+        for (int o = 0; o < 2; ++o) {
+            if (o == 1 && l == m) break;             // the diagonal entry once
+            const int tgt = o == 0 ? l : m, src = o == 0 ? m : l;
+            const bool on = (f >> o) & 1;
+            if (a.A) {
+                // blocks: K^a -> (t, s); -S^a -> (t, N+s); K^b -> (N+t, s); S^b -> (N+t, N+s)
+                const size_t ld = 2 * (size_t)N;
+                double2* col0 = a.A + (size_t)n * ld * ld + (size_t)src * ld;
+                double2* col1 = col0 + (size_t)N * ld;
+                const double wu = a.h * a.T.Wu[src], wp = a.h * a.T.Wphi[src];
+                const double2 z = c2(0.0, 0.0);
+                col0[tgt] = on ? cscale(ka[o], wu) : z;
+                col1[tgt] = on ? cscale(sa, -wp) : z;
+                col0[N + tgt] = on ? cscale(kb[o], wu) : z;
+                col1[N + tgt] = on ? cscale(sb, wp) : z;
+            }
+            if (a.raw) {
+                const size_t NN = (size_t)N * N, e = (size_t)tgt * N + src;
+                const double2 z = c2(0.0, 0.0);
+                a.raw[((size_t)n * 4 + 0) * NN + e] = on ? sa : z;
+                a.raw[((size_t)n * 4 + 1) * NN + e] = on ? ka[o] : z;
+                a.raw[((size_t)n * 4 + 2) * NN + e] = on ? sb : z;
+                a.raw[((size_t)n * 4 + 3) * NN + e] = on ? kb[o] : z;
+            }
         }
     }
 }
@@ -1080,10 +1148,10 @@ __global__ void outputs_kernel(int N, int nmodes, int nrhs, const double2* X, co
 static int far_warps(int M) { return M <= 512 ? 8 : 4; }
 
 // shared memory of a far_kernel CTA with nw pairs: twiddles M, DFT weights
-// M/2, angle table S1, nw pair geometries, nw buffers, nw flags
+// M/2, angle table S1, nw pair geometries (6 double2 each), nw buffers, nw flags
 static size_t far_smem(int M, int nw) {
     const size_t S1 = M / 2 + 1;
-    return sizeof(double2) * ((size_t)M + M / 2 + S1 + 4 * (size_t)nw + (size_t)nw * (4 * S1 + M)) +
+    return sizeof(double2) * ((size_t)M + M / 2 + S1 + 6 * (size_t)nw + (size_t)nw * (4 * S1 + M)) +
            sizeof(double2) * (((size_t)nw + 3) / 4);
 }
 
@@ -1113,7 +1181,8 @@ cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStre
     if (e != cudaSuccess) return e;
     auto run = [&](int nw) {
         g_far_pairs_per_cta = nw;
-        dim3 grid((N + nw - 1) / nw, N);
+        const int tm = far_tile_m(nw), tl = nw / tm;
+        dim3 grid((N + tl - 1) / tl, (N + tm - 1) / tm);
         far_kernel<<<grid, 32 * nw, far_smem(M, nw), s>>>(a);
         count_launch();
         return cudaGetLastError();

@@ -14,6 +14,7 @@
 #include <mutex>
 #include <stdexcept>
 #include <thread>
+#include <unordered_map>
 
 #include "internal.h"
 
@@ -802,6 +803,18 @@ int build_tables(pmlbie_problem* prob) {
         for (auto& v : part) H.near.insert(H.near.end(), v.begin(), v.end());
     }
     H.n_grid_near = (int)H.near.size();
+    {
+        // mirror pairs: the exact modal Laplace kernels depend on the pair only
+        // through chi (symmetric) and the normal factor, so one recurrence
+        // serves both orientations
+        std::unordered_map<long long, int> at;
+        at.reserve((size_t)H.n_grid_near * 2);
+        for (int i = 0; i < H.n_grid_near; ++i) at[(long long)H.near[i].tgt * N + H.near[i].src] = i;
+        for (int i = 0; i < H.n_grid_near; ++i) {
+            auto it = at.find((long long)H.near[i].src * N + H.near[i].tgt);
+            H.near[i].mirror = it == at.end() ? -1 : it->second;
+        }
+    }
     for (int c = 0; c < ncorr; ++c) {
         const CP& q = cpts[c];
         NearPair np;

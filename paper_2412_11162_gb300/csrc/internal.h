@@ -35,6 +35,8 @@ struct NearPair {
     int     src;       // grid-near: source unknown m; correction: correction index c
     int     flags;     // bit 0: correction pair; bit 1: far-by-criterion (plain FFT);
                        // bit 2: Taylor substitution (a point inside the PML)
+    int     mirror = -1;   // grid-near: index of the pair with target and source
+                           // exchanged (-1: none, or a correction pair)
 };
 
 enum { kFlagCorr = 1, kFlagFar = 2, kFlagSubst = 4 };

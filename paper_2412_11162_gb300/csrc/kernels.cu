@@ -578,7 +578,10 @@ __device__ void complex_agm_KE(double2 k2, double2 kp, double2& K, double2& E) {
 // The same for a pair of physical nodes, where chi > 1 and every factor are
 // real: real AGM, real recurrences (the values are stored with zero
 // imaginary parts).
-__device__ void laplace_modes_real(const NearPair& q, int M, double2* Z, double2* Dd) {
+// qm, Zm, Ddm: the mirror pair (target and source exchanged) whose modes come
+// from the same c_m, or null
+__device__ void laplace_modes_real(const NearPair& q, const NearPair* qm, int M, double2* Z, double2* Dd,
+                                   double2* Zm, double2* Ddm) {
     const double rr2 = 2.0 * q.rr.x;
     const double chim1 = q.d2.x / rr2, chi = 1.0 + chim1, chip1 = 2.0 + chim1;
     const double k2 = 2.0 / chip1, kp = sqrt(chim1 / chip1);
@@ -623,6 +626,11 @@ __device__ void laplace_modes_real(const NearPair& q, int M, double2* Z, double2
     }
     const double A = q.nuc_r.x * q.drt.x - q.nuc_z.x * q.dz - q.nuc_r.x * q.d2.x / (2.0 * q.rho_s.x);
     const double B = q.nuc_r.x * q.rho_t.x;
+    double Am = 0.0, Bm = 0.0;
+    if (qm) {
+        Am = qm->nuc_r.x * qm->drt.x - qm->nuc_z.x * qm->dz - qm->nuc_r.x * qm->d2.x / (2.0 * qm->rho_s.x);
+        Bm = qm->nuc_r.x * qm->rho_t.x;
+    }
     const double s2 = sqrt(rr2);
     const double iz = kInv4Pi / s2, id = -kInv4Pi / (s2 * s2 * s2), den = 1.0 / (chim1 * chip1);
     for (int m = 0; m + 1 < M; ++m) {
@@ -630,20 +638,36 @@ __device__ void laplace_modes_real(const NearPair& q, int M, double2* Z, double2
         const double dm = (2.0 * m + 1.0) * (chi * cm - cn) * den;
         Dd[m] = c2(id * (A * dm + B * cm), 0.0);
         Z[m] = c2(iz * cm, 0.0);
+        if (qm) {
+            Ddm[m] = c2(id * (Am * dm + Bm * cm), 0.0);
+            Zm[m] = c2(iz * cm, 0.0);
+        }
     }
 }
 
+// One thread per close pair.  A grid pair and its mirror (target and source
+// exchanged) share chi and hence c_m: the lower index of the two computes the
+// modes of both, the other returns.
 __global__ void near_laplace_kernel(NearArgs a) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.npairs) return;
     NearPair q = a.np[p];
     if (q.flags & kFlagFar) return;
+    if (q.mirror >= 0 && q.mirror < p) return;
     const int M = a.M;
     double2* Z = a.zd + (size_t)p * 2 * M;
     double2* Dd = Z + M;
+    NearPair qm;
+    double2 *Zm = nullptr, *Ddm = nullptr;
+    if (q.mirror >= 0) {
+        qm = a.np[q.mirror];
+        Zm = a.zd + (size_t)q.mirror * 2 * M;
+        Ddm = Zm + M;
+    }
+    const NearPair* pm = q.mirror >= 0 ? &qm : nullptr;
     if (q.d2.y == 0.0 && q.rr.y == 0.0 && q.rho_t.y == 0.0 && q.rho_s.y == 0.0 && q.drt.y == 0.0 &&
-        q.nuc_r.y == 0.0 && q.nuc_z.y == 0.0) {
-        laplace_modes_real(q, M, Z, Dd);
+        q.nuc_r.y == 0.0 && q.nuc_z.y == 0.0 && (!pm || (qm.nuc_r.y == 0.0 && qm.nuc_z.y == 0.0))) {
+        laplace_modes_real(q, pm, M, Z, Dd, Zm, Ddm);
         return;
     }
     double2 rr2 = cscale(q.rr, 2.0);
@@ -688,10 +712,16 @@ __global__ void near_laplace_kernel(NearArgs a) {
         double2 f = cdiv(c0, Z[0]);
         for (int m = 0; m < M; ++m) Z[m] = cmul(Z[m], f);
     }
-    // A, B, prefactors
+    // A, B, prefactors (of the mirror too: its own normal factor, same c_m)
     double2 A = cadd(cmul(q.nuc_r, q.drt), cscale(q.nuc_z, -q.dz));   // nu'.(r~' - r~)
     A = csub(A, cdiv(cmul(q.nuc_r, q.d2), cscale(q.rho_s, 2.0)));
     double2 B = cmul(q.nuc_r, q.rho_t);
+    double2 Am = c2(0.0, 0.0), Bm = Am;
+    if (pm) {
+        Am = cadd(cmul(qm.nuc_r, qm.drt), cscale(qm.nuc_z, -qm.dz));
+        Am = csub(Am, cdiv(cmul(qm.nuc_r, qm.d2), cscale(qm.rho_s, 2.0)));
+        Bm = cmul(qm.nuc_r, qm.rho_t);
+    }
     double2 s2 = csqrt(rr2);
     double2 iz = cscale(crcp(s2), kInv4Pi);                           // 1/(4 pi sqrt(2 rr))
     double2 id = cscale(crcp(cmul(s2, cmul(s2, s2))), -kInv4Pi);      // -(2rr)^{-3/2}/(4 pi)
@@ -701,6 +731,10 @@ __global__ void near_laplace_kernel(NearArgs a) {
         double2 dm = cscale(cmul(csub(cmul(chi, cm), cn), den), 2.0 * m + 1.0);
         Dd[m] = cmul(id, cadd(cmul(A, dm), cmul(B, cm)));
         Z[m] = cmul(iz, cm);
+        if (pm) {
+            Ddm[m] = cmul(id, cadd(cmul(Am, dm), cmul(Bm, cm)));
+            Zm[m] = Z[m];
+        }
     }
 }
 

@@ -743,11 +743,15 @@ int build_tables(pmlbie_problem* prob) {
                 }
                 H.corr_target.push_back(l);
                 H.corr_tau.push_back(tau);
-                cpts.push_back(fill_point(tau));
             }
         }
     }
     const int ncorr = (int)H.corr_target.size();
+    // the points themselves (curve, PML integral and conormal of each) in parallel
+    cpts.resize(ncorr);
+    parallel_rows(ncorr, [&](int lo, int hi) {
+        for (int c = lo; c < hi; ++c) cpts[c] = fill_point(H.corr_tau[c]);
+    });
 
     // pair classes and close-pair table
     const double eta = prob->eta_split;
@@ -815,14 +819,16 @@ int build_tables(pmlbie_problem* prob) {
             H.near[i].mirror = it == at.end() ? -1 : it->second;
         }
     }
-    for (int c = 0; c < ncorr; ++c) {
-        const CP& q = cpts[c];
-        NearPair np;
-        bool nr = make_pair(H.corr_target[c], q, np);
-        np.src = c;
-        np.flags |= kFlagCorr | (nr ? 0 : kFlagFar);
-        H.near.push_back(np);
-    }
+    H.near.resize((size_t)H.n_grid_near + ncorr);
+    parallel_rows(ncorr, [&](int lo, int hi) {
+        for (int c = lo; c < hi; ++c) {
+            NearPair np;
+            bool nr = make_pair(H.corr_target[c], cpts[c], np);
+            np.src = c;
+            np.flags |= kFlagCorr | (nr ? 0 : kFlagFar);
+            H.near[(size_t)H.n_grid_near + c] = np;
+        }
+    });
 
     // diagonal term: K0_AB 1 by the same quadrature (mode-0 Laplace double layer,
     // physical normal), plus K0_+ 1 from the disc solid angle (Lemma 3.3)
@@ -841,12 +847,20 @@ int build_tables(pmlbie_problem* prob) {
             K0[l] = s;
         }
     });
+    // correction kernels in parallel; their sums in the serial order
+    std::vector<double> vc(ncorr);
+    parallel_rows(ncorr, [&](int lo, int hi) {
+        for (int c = lo; c < hi; ++c) {
+            const int l = H.corr_target[c];
+            const CP& q = cpts[c];
+            double dr, dz;
+            separation(npts[l], q, dr, dz);
+            vc[c] = laplace_dl0(H.rho[l], q.rho, dr, dz, q.nr, q.nz);
+        }
+    });
     for (int c = 0; c < ncorr; ++c) {
-        int l = H.corr_target[c];
-        const CP& q = cpts[c];
-        double dr, dz;
-        separation(npts[l], q, dr, dz);
-        double v = laplace_dl0(H.rho[l], q.rho, dr, dz, q.nr, q.nz);
+        const int l = H.corr_target[c];
+        const double v = vc[c];
         for (int a = 0; a < kStencil; ++a) {
             int m = H.corr_m[(size_t)c * kStencil + a];
             if (m >= 0) K0[l] += H.corr_coef[(size_t)c * kStencil + a] * H.Wu[m] * v;

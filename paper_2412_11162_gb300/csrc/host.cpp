@@ -501,18 +501,20 @@ void alpert_log_rule(int j, int a, std::vector<double>& xo, std::vector<double>&
 namespace {
 
 // Complete elliptic integrals K(k), E(k) for 0 <= k < 1 given k' = sqrt(1-k^2)
-// (arithmetic-geometric mean).
-void ellip_KE(long double k2, long double kp, long double& K, long double& E) {
-    long double a = 1, b = kp, sum = 0.5L * k2, pw = 0.5L;
+// (arithmetic-geometric mean, in double: the diagonal sums agree with an
+// extended-precision evaluation to ~2e-14; the loop stops once a and b agree
+// to rounding, before the doubling weight could amplify rounding in c_n).
+void ellip_KE(double k2, double kp, double& K, double& E) {
+    double a = 1, b = kp, sum = 0.5 * k2, pw = 0.5;
     for (int it = 0; it < 60; ++it) {
-        long double an = 0.5L * (a + b), bn = std::sqrt(a * b), cn = 0.5L * (a - b);
+        double an = 0.5 * (a + b), bn = std::sqrt(a * b), cn = 0.5 * (a - b);
         pw *= 2;
         sum += pw * cn * cn;
         a = an;
         b = bn;
-        if (std::fabs(cn) < 1e-21L * std::fabs(a)) break;
+        if (std::fabs(cn) <= 5e-16 * std::fabs(a)) break;
     }
-    K = 3.141592653589793238462643383279502884L / (2 * a);
+    K = 3.141592653589793 / (2 * a);
     E = K * (1 - sum);
 }
 
@@ -522,15 +524,15 @@ void ellip_KE(long double k2, long double kp, long double& K, long double& E) {
 // A = nu'_rho (rho' - rho) + nu'_z (z' - z) - nu'_rho d^2/(2 rho');
 // drho = rho - rho', dzz = z - z' are passed in (accurate separations).
 double laplace_dl0(double rho, double rs, double drho, double dzz, double nr, double nz) {
-    long double dr = drho, dz = dzz;
-    long double d2 = dr * dr + dz * dz;
-    long double Q = (long double)(rho + rs) * (rho + rs) + dz * dz;
-    long double k2 = 4.0L * rho * rs / Q, kp = std::sqrt(d2 / Q);
-    long double K, E;
+    double dr = drho, dz = dzz;
+    double d2 = dr * dr + dz * dz;
+    double Q = (rho + rs) * (rho + rs) + dz * dz;
+    double k2 = 4.0 * rho * rs / Q, kp = std::sqrt(d2 / Q);
+    double K, E;
     ellip_KE(k2, kp, K, E);
-    long double A = -nr * dr - nz * dz - nr * d2 / (2.0L * rs);
-    long double v = -(A * E / d2 + nr * K / (2.0L * rs)) / (3.141592653589793238462643383279502884L * std::sqrt(Q));
-    return (double)v;
+    double A = -nr * dr - nz * dz - nr * d2 / (2.0 * rs);
+    double v = -(A * E / d2 + nr * K / (2.0 * rs)) / (3.141592653589793 * std::sqrt(Q));
+    return v;
 }
 
 // Solid angle of the disc {rho' <= Lr, z' = 0} seen from (rho, 0, h), rho < Lr.

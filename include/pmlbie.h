@@ -160,6 +160,20 @@ int  pmlbie_diagonal(const pmlbie_problem* prob, double* Da, double* Db, int n);
 /* Number of close (split) pairs: grid pairs and Alpert correction pairs. */
 int  pmlbie_near_count(const pmlbie_problem* prob, int* n_grid_near, int* n_corr);
 
+/* Host copy of the close-pair list (Sec. 4.1 kernel splitting; the pairs with
+ * Re sqrt(d~^2 / (rho~ rho~')) below the split threshold, plus every Alpert
+ * correction pair), n = n_grid_near + n_corr entries in the library's order:
+ * the grid pairs by target, then source; then the correction pairs in the
+ * order of their correction points (target, side, node of the rule).  Per
+ * entry: tgt (unknown l), src (grid: unknown m; correction: the correction
+ * point's index), flags (bit 0: correction pair; bit 1: a correction pair
+ * that is far by the criterion and takes the plain FFT; bit 2: Taylor
+ * substitution of Sec. 4.3, a point inside the PML), mirror (grid pairs:
+ * index of the pair with target and source exchanged, -1 if that pair is not
+ * close; correction pairs: -1).  Any pointer may be NULL.  EINVAL if n is not
+ * the list's length. */
+int  pmlbie_near_pairs(const pmlbie_problem* prob, int* tgt, int* src, int* flags, int* mirror, int n);
+
 /* Alpert's log-singular end correction used by the quadrature (Sec. 4.1,
  * order 10 in Sec. 5): j nodes x[k] in (0, a) and weights w[k] (host arrays of
  * length j), generated by the library from the rule's moment conditions.

@@ -60,7 +60,8 @@ class pmlbie_solve_opts(ctypes.Structure):
 
 
 EXPORTS = ["pmlbie_create", "pmlbie_destroy", "pmlbie_last_error", "pmlbie_nodes", "pmlbie_diagonal",
-           "pmlbie_near_count", "pmlbie_alpert_rule", "pmlbie_workspace_bytes", "pmlbie_modal_kernels",
+           "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_alpert_rule", "pmlbie_workspace_bytes",
+           "pmlbie_modal_kernels",
            "pmlbie_modal_kernels_noalloc",
            "pmlbie_solve", "pmlbie_solve_ex", "pmlbie_solve_batch", "pmlbie_field", "pmlbie_solve_host",
            "pmlbie_check_finite", "pmlbie_selftest_wait"]
@@ -81,6 +82,7 @@ def _load():
     lib.pmlbie_nodes.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int]
     lib.pmlbie_diagonal.argtypes = [vp, dp, dp, ctypes.c_int]
     lib.pmlbie_near_count.argtypes = [vp, ip, ip]
+    lib.pmlbie_near_pairs.argtypes = [vp, ip, ip, ip, ip, ctypes.c_int]
     lib.pmlbie_alpert_rule.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
     lib.pmlbie_workspace_bytes.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     lib.pmlbie_workspace_bytes.restype = ctypes.c_size_t
@@ -101,7 +103,7 @@ def _load():
     lib.pmlbie_check_finite.argtypes = [vp, ctypes.c_size_t, vp]
     lib.pmlbie_selftest_wait.argtypes = [ctypes.c_longlong, vp]
     for f in ("pmlbie_check_finite", "pmlbie_selftest_wait", "pmlbie_nodes", "pmlbie_diagonal",
-              "pmlbie_near_count", "pmlbie_alpert_rule",
+              "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_alpert_rule",
               "pmlbie_modal_kernels", "pmlbie_modal_kernels_noalloc", "pmlbie_solve", "pmlbie_solve_ex",
               "pmlbie_solve_batch", "pmlbie_field", "pmlbie_solve_host"):
         getattr(lib, f).restype = ctypes.c_int
@@ -191,6 +193,17 @@ def pmlbie_near_count(h):
     a, b = ctypes.c_int(), ctypes.c_int()
     check(lib.pmlbie_near_count(h, ctypes.byref(a), ctypes.byref(b)), "pmlbie_near_count")
     return a.value, b.value
+
+
+def pmlbie_near_pairs(h):
+    """(tgt, src, flags, mirror) int32 arrays of the close-pair list."""
+    import numpy as np
+    g, c = pmlbie_near_count(h)
+    n = g + c
+    out = [np.zeros(n, dtype=np.int32) for _ in range(4)]
+    ptr = [o.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) for o in out]
+    check(lib.pmlbie_near_pairs(h, *ptr, n), "pmlbie_near_pairs")
+    return tuple(out)
 
 
 def pmlbie_alpert_rule(j, a):

@@ -324,6 +324,19 @@ int pmlbie_near_count(const pmlbie_problem* prob, int* n_grid_near, int* n_corr)
     return PMLBIE_OK;
 }
 
+int pmlbie_near_pairs(const pmlbie_problem* prob, int* tgt, int* src, int* flags, int* mirror, int n) {
+    if (!prob) return fail(PMLBIE_EINVAL, "problem NULL");
+    const auto& v = prob->H.near;
+    if (n != (int)v.size()) return fail(PMLBIE_EINVAL, "n must equal the close-pair count");
+    for (int i = 0; i < n; ++i) {
+        if (tgt) tgt[i] = v[i].tgt;
+        if (src) src[i] = v[i].src;
+        if (flags) flags[i] = v[i].flags;
+        if (mirror) mirror[i] = v[i].mirror;
+    }
+    return PMLBIE_OK;
+}
+
 int pmlbie_alpert_rule(int j, int a, double* x, double* w) {
     if (j < 2 || j > 12 || a < 1 || a > 16 || !x || !w) return fail(PMLBIE_EINVAL, "bad Alpert rule request");
     std::vector<double> xv, wv;

@@ -174,6 +174,17 @@ int  pmlbie_near_count(const pmlbie_problem* prob, int* n_grid_near, int* n_corr
  * the list's length. */
 int  pmlbie_near_pairs(const pmlbie_problem* prob, int* tgt, int* src, int* flags, int* mirror, int n);
 
+/* Host copy of the Alpert correction table (Sec. 4.1 Eqs. (snab1), (snt1)):
+ * n = n_corr correction points (pmlbie_near_count) in the order of the
+ * close-pair list's correction pairs.  Per point c: target[c] (unknown l),
+ * tau[c] (curve parameter of the point, in (0, 1)), and the PMLBIE_STENCIL
+ * unknowns m[c * PMLBIE_STENCIL + a] (-1 at breakpoints) of its Lagrange
+ * stencil with coefficients coef[...] = w_k h L_a(tau) (Alpert weight times
+ * grid step times Lagrange weight); the correction adds coef x W(m) x F(r_l,
+ * r(tau)) to column m.  Any pointer may be NULL.  EINVAL if n is not n_corr. */
+#define PMLBIE_STENCIL 10
+int  pmlbie_corrections(const pmlbie_problem* prob, int* target, double* tau, int* m, double* coef, int n);
+
 /* Alpert's log-singular end correction used by the quadrature (Sec. 4.1,
  * order 10 in Sec. 5): j nodes x[k] in (0, a) and weights w[k] (host arrays of
  * length j), generated by the library from the rule's moment conditions.

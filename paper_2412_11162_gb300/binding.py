@@ -60,7 +60,8 @@ class pmlbie_solve_opts(ctypes.Structure):
 
 
 EXPORTS = ["pmlbie_create", "pmlbie_destroy", "pmlbie_last_error", "pmlbie_nodes", "pmlbie_diagonal",
-           "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_alpert_rule", "pmlbie_workspace_bytes",
+           "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_corrections", "pmlbie_alpert_rule",
+           "pmlbie_workspace_bytes",
            "pmlbie_modal_kernels",
            "pmlbie_modal_kernels_noalloc",
            "pmlbie_solve", "pmlbie_solve_ex", "pmlbie_solve_batch", "pmlbie_field", "pmlbie_solve_host",
@@ -83,6 +84,7 @@ def _load():
     lib.pmlbie_diagonal.argtypes = [vp, dp, dp, ctypes.c_int]
     lib.pmlbie_near_count.argtypes = [vp, ip, ip]
     lib.pmlbie_near_pairs.argtypes = [vp, ip, ip, ip, ip, ctypes.c_int]
+    lib.pmlbie_corrections.argtypes = [vp, ip, dp, ip, dp, ctypes.c_int]
     lib.pmlbie_alpert_rule.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
     lib.pmlbie_workspace_bytes.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     lib.pmlbie_workspace_bytes.restype = ctypes.c_size_t
@@ -103,7 +105,7 @@ def _load():
     lib.pmlbie_check_finite.argtypes = [vp, ctypes.c_size_t, vp]
     lib.pmlbie_selftest_wait.argtypes = [ctypes.c_longlong, vp]
     for f in ("pmlbie_check_finite", "pmlbie_selftest_wait", "pmlbie_nodes", "pmlbie_diagonal",
-              "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_alpert_rule",
+              "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_corrections", "pmlbie_alpert_rule",
               "pmlbie_modal_kernels", "pmlbie_modal_kernels_noalloc", "pmlbie_solve", "pmlbie_solve_ex",
               "pmlbie_solve_batch", "pmlbie_field", "pmlbie_solve_host"):
         getattr(lib, f).restype = ctypes.c_int
@@ -204,6 +206,24 @@ def pmlbie_near_pairs(h):
     ptr = [o.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) for o in out]
     check(lib.pmlbie_near_pairs(h, *ptr, n), "pmlbie_near_pairs")
     return tuple(out)
+
+
+PMLBIE_STENCIL = 10
+
+
+def pmlbie_corrections(h):
+    """(target, tau, m, coef) of the Alpert correction table; m and coef are
+    (n_corr, PMLBIE_STENCIL)."""
+    import numpy as np
+    _, n = pmlbie_near_count(h)
+    t = np.zeros(n, dtype=np.int32)
+    tau = np.zeros(n)
+    m = np.zeros((n, PMLBIE_STENCIL), dtype=np.int32)
+    coef = np.zeros((n, PMLBIE_STENCIL))
+    ip = ctypes.POINTER(ctypes.c_int)
+    check(lib.pmlbie_corrections(h, t.ctypes.data_as(ip), _dptr(tau), m.ctypes.data_as(ip), _dptr(coef), n),
+          "pmlbie_corrections")
+    return t, tau, m, coef
 
 
 def pmlbie_alpert_rule(j, a):

@@ -337,6 +337,19 @@ int pmlbie_near_pairs(const pmlbie_problem* prob, int* tgt, int* src, int* flags
     return PMLBIE_OK;
 }
 
+int pmlbie_corrections(const pmlbie_problem* prob, int* target, double* tau, int* m, double* coef, int n) {
+    if (!prob) return fail(PMLBIE_EINVAL, "problem NULL");
+    const auto& H = prob->H;
+    static_assert(PMLBIE_STENCIL == kStencil, "stencil width of the ABI");
+    if (n != (int)H.corr_target.size()) return fail(PMLBIE_EINVAL, "n must equal the correction count");
+    const size_t ns = (size_t)n * kStencil;
+    if (target) std::memcpy(target, H.corr_target.data(), sizeof(int) * n);
+    if (tau) std::memcpy(tau, H.corr_tau.data(), sizeof(double) * n);
+    if (m) std::memcpy(m, H.corr_m.data(), sizeof(int) * ns);
+    if (coef) std::memcpy(coef, H.corr_coef.data(), sizeof(double) * ns);
+    return PMLBIE_OK;
+}
+
 int pmlbie_alpert_rule(int j, int a, double* x, double* w) {
     if (j < 2 || j > 12 || a < 1 || a > 16 || !x || !w) return fail(PMLBIE_EINVAL, "bad Alpert rule request");
     std::vector<double> xv, wv;

@@ -40,6 +40,9 @@ class Problem:
     def near_pairs(self):
         return B.pmlbie_near_pairs(self.handle)
 
+    def corrections(self):
+        return B.pmlbie_corrections(self.handle)
+
     def modal_kernels(self, mode_lo=0, mode_hi=None, stream=None):
         import torch
         mode_hi = self.n_modes if mode_hi is None else mode_hi

@@ -75,3 +75,31 @@ def test_close_pairs_match_oracle(case):
         if j >= 0:
             assert mirror[j] == i
     assert np.all(mirror[ngl:] == -1)
+
+
+@pytest.mark.parametrize("case", ["bump_pml", "ex3"])
+def test_alpert_corrections_match_oracle(case):
+    """The Alpert correction table (Sec. 4.1): the same targets exactly, the
+    same curve parameters, and the same stencil coefficient rows w_k h L(tau)
+    per unknown (the two sides' Alpert nodes and weights come from
+    independent generators that agree to ~1e-15)."""
+    from paper_2412_11162_gb300 import Problem
+    kw = dict(CASES[case])
+    k1, k2, N, M = kw.pop("k1"), kw.pop("k2"), kw.pop("N"), kw.pop("M")
+    P = Problem(k1, k2, N, M, **kw)
+    target, tau, m, coef = P.corrections()
+    P.close()
+    Q = Quadrature(Geometry(Params(k1=k1, k2=k2, N=N, M=M, **kw)))
+    assert np.array_equal(target, Q.corr_target)
+    assert np.abs(tau - Q.corr_tau).max() < 1e-14
+    rows = np.zeros((len(target), N))
+    for c in range(len(target)):
+        for a in range(m.shape[1]):
+            if m[c, a] >= 0:
+                rows[c, m[c, a]] += coef[c, a]
+            else:
+                assert coef[c, a] == 0.0
+    scale = np.abs(Q.corr_coef).max()
+    assert np.abs(rows - Q.corr_coef).max() < 1e-13 * scale
+    # a stencil covers 10 consecutive grid nodes around tau
+    assert np.all((m[:, 1:] == -1) | (m[:, :-1] == -1) | (m[:, 1:] == m[:, :-1] + 1))

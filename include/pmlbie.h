@@ -183,6 +183,17 @@ int  pmlbie_near_pairs(const pmlbie_problem* prob, int* tgt, int* src, int* flag
  * grid step times Lagrange weight); the correction adds coef x W(m) x F(r_l,
  * r(tau)) to column m.  Any pointer may be NULL.  EINVAL if n is not n_corr. */
 #define PMLBIE_STENCIL 10
+
+/* Host copy of the per-node PML and quadrature tables (length N each, any
+ * pointer may be NULL): I = int_{a1}^{rho} sigma (Sec. 3.1 Eq. (rhot), so the
+ * stretched radius is rho~ = rho + i I), the conormal nu_c of region a as
+ * complex pairs (re, im) interleaved: nuc_r[2 l], nuc_r[2 l + 1] (Sec. 3.1,
+ * nu_c = (nu_rho rho~ alpha_z / (rho alpha_rho), nu_z rho~ alpha_rho / (rho
+ * alpha_z)) with alpha = 1 + i sigma), and the column weights Wu = 2 rho |r'|
+ * (double-layer / u columns) and Wphi = 2 rho (single-layer / phi columns)
+ * of the graded trapezoid.  EINVAL if n != N. */
+int  pmlbie_node_tables(const pmlbie_problem* prob, double* I, double* nuc_r, double* nuc_z, double* Wu,
+                        double* Wphi, int n);
 int  pmlbie_corrections(const pmlbie_problem* prob, int* target, double* tau, int* m, double* coef, int n);
 
 /* Alpert's log-singular end correction used by the quadrature (Sec. 4.1,

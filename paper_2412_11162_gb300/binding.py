@@ -60,8 +60,8 @@ class pmlbie_solve_opts(ctypes.Structure):
 
 
 EXPORTS = ["pmlbie_create", "pmlbie_destroy", "pmlbie_last_error", "pmlbie_nodes", "pmlbie_diagonal",
-           "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_corrections", "pmlbie_alpert_rule",
-           "pmlbie_workspace_bytes",
+           "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_corrections", "pmlbie_node_tables",
+           "pmlbie_alpert_rule", "pmlbie_workspace_bytes",
            "pmlbie_modal_kernels",
            "pmlbie_modal_kernels_noalloc",
            "pmlbie_solve", "pmlbie_solve_ex", "pmlbie_solve_batch", "pmlbie_field", "pmlbie_solve_host",
@@ -85,6 +85,7 @@ def _load():
     lib.pmlbie_near_count.argtypes = [vp, ip, ip]
     lib.pmlbie_near_pairs.argtypes = [vp, ip, ip, ip, ip, ctypes.c_int]
     lib.pmlbie_corrections.argtypes = [vp, ip, dp, ip, dp, ctypes.c_int]
+    lib.pmlbie_node_tables.argtypes = [vp, dp, dp, dp, dp, dp, ctypes.c_int]
     lib.pmlbie_alpert_rule.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
     lib.pmlbie_workspace_bytes.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     lib.pmlbie_workspace_bytes.restype = ctypes.c_size_t
@@ -105,7 +106,8 @@ def _load():
     lib.pmlbie_check_finite.argtypes = [vp, ctypes.c_size_t, vp]
     lib.pmlbie_selftest_wait.argtypes = [ctypes.c_longlong, vp]
     for f in ("pmlbie_check_finite", "pmlbie_selftest_wait", "pmlbie_nodes", "pmlbie_diagonal",
-              "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_corrections", "pmlbie_alpert_rule",
+              "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_corrections", "pmlbie_node_tables",
+              "pmlbie_alpert_rule",
               "pmlbie_modal_kernels", "pmlbie_modal_kernels_noalloc", "pmlbie_solve", "pmlbie_solve_ex",
               "pmlbie_solve_batch", "pmlbie_field", "pmlbie_solve_host"):
         getattr(lib, f).restype = ctypes.c_int
@@ -209,6 +211,17 @@ def pmlbie_near_pairs(h):
 
 
 PMLBIE_STENCIL = 10
+
+
+def pmlbie_node_tables(h, N):
+    """dict of the per-node PML and weight tables: I, nuc_r, nuc_z (complex),
+    Wu, Wphi."""
+    import numpy as np
+    I, Wu, Wphi = np.zeros(N), np.zeros(N), np.zeros(N)
+    nr, nz = np.zeros(2 * N), np.zeros(2 * N)
+    check(lib.pmlbie_node_tables(h, _dptr(I), _dptr(nr), _dptr(nz), _dptr(Wu), _dptr(Wphi), N),
+          "pmlbie_node_tables")
+    return {"I": I, "nuc_r": nr[0::2] + 1j * nr[1::2], "nuc_z": nz[0::2] + 1j * nz[1::2], "Wu": Wu, "Wphi": Wphi}
 
 
 def pmlbie_corrections(h):

@@ -337,6 +337,21 @@ int pmlbie_near_pairs(const pmlbie_problem* prob, int* tgt, int* src, int* flags
     return PMLBIE_OK;
 }
 
+int pmlbie_node_tables(const pmlbie_problem* prob, double* I, double* nuc_r, double* nuc_z, double* Wu,
+                       double* Wphi, int n) {
+    if (!prob) return fail(PMLBIE_EINVAL, "problem NULL");
+    const auto& H = prob->H;
+    if (n != prob->P.N) return fail(PMLBIE_EINVAL, "n must equal N");
+    for (int l = 0; l < n; ++l) {
+        if (I) I[l] = H.I[l];
+        if (nuc_r) nuc_r[2 * l] = H.nuc_r[l].real(), nuc_r[2 * l + 1] = H.nuc_r[l].imag();
+        if (nuc_z) nuc_z[2 * l] = H.nuc_z[l].real(), nuc_z[2 * l + 1] = H.nuc_z[l].imag();
+        if (Wu) Wu[l] = H.Wu[l];
+        if (Wphi) Wphi[l] = H.Wphi[l];
+    }
+    return PMLBIE_OK;
+}
+
 int pmlbie_corrections(const pmlbie_problem* prob, int* target, double* tau, int* m, double* coef, int n) {
     if (!prob) return fail(PMLBIE_EINVAL, "problem NULL");
     const auto& H = prob->H;

@@ -43,6 +43,9 @@ class Problem:
     def corrections(self):
         return B.pmlbie_corrections(self.handle)
 
+    def node_tables(self):
+        return B.pmlbie_node_tables(self.handle, self.N)
+
     def modal_kernels(self, mode_lo=0, mode_hi=None, stream=None):
         import torch
         mode_hi = self.n_modes if mode_hi is None else mode_hi

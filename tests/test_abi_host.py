@@ -109,3 +109,25 @@ def test_polyline_must_start_on_axis(B):
     params, keep = B.make_params(1.0, 1.0, 64, 32, curve="polyline", vertices=[(0.5, -1.0), (3.5, 0.0)])
     with pytest.raises(B.PmlbieError):
         B.pmlbie_create(params)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(a1=2.5, T=1.0, S=3.0),
+    dict(a1=2.0, T=2.0, S=2.0, curve="wavy", wavy_R=1.0, wavy_eps=0.1, wavy_m=3),
+    dict(a1=2.0, T=2.0, S=2.0, curve="polyline", vertices=[(0.0, -1.0), (1.0, -1.0), (1.0, 0.0), (4.0, 0.0)]),
+])
+def test_node_tables_match_oracle(B, kw):
+    """Per-node PML and weight tables: I = int sigma (Sec. 3.1 Eq. (rhot)),
+    the conormal of region a (complex inside the PML), and the column weights
+    2 rho |r'| and 2 rho equal the oracle's to rounding."""
+    from paper_2412_11162_gb300 import Problem
+    from oracle.problem import Geometry, Params
+    P = Problem(2 * np.pi, 3 * np.pi, 160, 64, **kw)
+    t = P.node_tables()
+    P.close()
+    G = Geometry(Params(k1=2 * np.pi, k2=3 * np.pi, N=160, M=64, **kw))
+    pairs = (("I", G.nodes["I"]), ("nuc_r", G.nodes["nuc_r"]), ("nuc_z", G.nodes["nuc_z"]),
+             ("Wu", G.nodes["W"]), ("Wphi", 2.0 * G.nodes["rho"]))
+    for k, ref in pairs:
+        assert np.abs(t[k] - ref).max() <= 1e-14 * max(1.0, np.abs(ref).max()), k
+    assert np.any(np.abs(t["nuc_z"].imag) > 0) and np.all(t["I"] >= 0)   # the PML is reached

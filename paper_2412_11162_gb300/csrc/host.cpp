@@ -14,7 +14,6 @@
 #include <mutex>
 #include <stdexcept>
 #include <thread>
-#include <unordered_map>
 
 #include "internal.h"
 
@@ -812,14 +811,28 @@ int build_tables(pmlbie_problem* prob) {
     {
         // mirror pairs: the exact modal Laplace kernels depend on the pair only
         // through chi (symmetric) and the normal factor, so one recurrence
-        // serves both orientations
-        std::unordered_map<long long, int> at;
-        at.reserve((size_t)H.n_grid_near * 2);
-        for (int i = 0; i < H.n_grid_near; ++i) at[(long long)H.near[i].tgt * N + H.near[i].src] = i;
-        for (int i = 0; i < H.n_grid_near; ++i) {
-            auto it = at.find((long long)H.near[i].src * N + H.near[i].tgt);
-            H.near[i].mirror = it == at.end() ? -1 : it->second;
-        }
+        // serves both orientations.  The grid list is ordered by (target,
+        // source): row starts, then a binary search of source l in row m.
+        const int ng = H.n_grid_near;
+        auto before = [](const NearPair& a, const NearPair& b) {
+            return a.tgt < b.tgt || (a.tgt == b.tgt && a.src < b.src);
+        };
+        if (!std::is_sorted(H.near.begin(), H.near.begin() + ng, before))
+            std::sort(H.near.begin(), H.near.begin() + ng, before);
+        std::vector<int> row(N + 1, 0);
+        for (int i = 0; i < ng; ++i) ++row[H.near[i].tgt + 1];
+        for (int l = 0; l < N; ++l) row[l + 1] += row[l];
+        std::vector<int> srcs(ng);
+        for (int i = 0; i < ng; ++i) srcs[i] = H.near[i].src;
+        parallel_rows(ng, [&](int lo, int hi) {
+            for (int i = lo; i < hi; ++i) {
+                const int l = H.near[i].tgt, m = H.near[i].src;
+                const int* b = srcs.data() + row[m];
+                const int* e = srcs.data() + row[m + 1];
+                const int* it = std::lower_bound(b, e, l);
+                H.near[i].mirror = (it != e && *it == l) ? (int)(it - srcs.data()) : -1;
+            }
+        });
     }
     H.near.resize((size_t)H.n_grid_near + ncorr);
     parallel_rows(ncorr, [&](int lo, int hi) {

@@ -131,3 +131,23 @@ def test_node_tables_match_oracle(B, kw):
     for k, ref in pairs:
         assert np.abs(t[k] - ref).max() <= 1e-14 * max(1.0, np.abs(ref).max()), k
     assert np.any(np.abs(t["nuc_z"].imag) > 0) and np.all(t["I"] >= 0)   # the PML is reached
+
+
+def test_workspace_sizing(B):
+    """Device workspace reported for a solve of all modes (host arithmetic, no
+    device): at least the per-mode complex128 block matrices (M/2 of order 2N)
+    in FP64, plus their complex64 copy in mixed precision; growing with the
+    number of right-hand sides and with N and M."""
+    from paper_2412_11162_gb300 import Problem
+    prev = 0
+    for N, M in ((96, 32), (128, 64), (192, 96)):
+        P = Problem(4 * np.pi, 6 * np.pi, N, M)
+        nm, n = M // 2, 2 * N
+        w64 = B.pmlbie_workspace_bytes(P.handle, B.PMLBIE_FP64, 1)
+        wmx = B.pmlbie_workspace_bytes(P.handle, B.PMLBIE_MIXED, 1)
+        wmx8 = B.pmlbie_workspace_bytes(P.handle, B.PMLBIE_MIXED, 8)
+        P.close()
+        assert w64 >= nm * n * n * 16
+        assert wmx >= w64 + nm * n * n * 8
+        assert wmx8 > wmx and w64 > prev
+        prev = w64

@@ -50,3 +50,13 @@ def test_far_flop_model_counts():
     assert bench.far_flops_per_launch(256, 128, 1, 0, 0) == 129 * 265 + 4 * (5 * 128 * 7 + 15 * 128) == 59785
     assert bench.far_flops_per_launch(256, 128, 1, 1, 0) == 41854
     assert bench.far_flops_per_launch(256, 16, 0, 0, 3) == 3 * 16 * 60
+
+
+def test_near_flop_model_counts():
+    """The bench's flop model of the close-pair modes kernel at M = 256, all
+    128 modes in one launch: 137,015 flops per packed pair, 280,821 per PML
+    pair, 64,679 per plain correction pair."""
+    import bench
+    assert bench.near_flops_per_launch(256, 128, 1, 0, 0) == 137015
+    assert bench.near_flops_per_launch(256, 128, 0, 1, 0) == 280821
+    assert bench.near_flops_per_launch(256, 128, 0, 0, 1) == 64679

@@ -30,6 +30,9 @@ design notes):
     peak height h, a corner at r = R).
   * sigma_2 is inert on gamma_AB (all curve points have |z| < a_2), so
     z~ = z and alpha_z = 1 on the curve.
+  * A segment that starts on the axis with a change in z (a conical point of
+    the surface, Sec. 5 Example 2) is graded with exponent 2 instead of p;
+    the paper gives no treatment of such a tip (see kConicalP).
 """
 from dataclasses import dataclass, field
 from typing import List, Optional, Tuple

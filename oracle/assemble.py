@@ -12,7 +12,7 @@ Follows:
     through the rim circle equals that of the disc rho <= a1 + T, z = 0.
   * Sec. 2 (reference field u^{tot,0}, Fresnel R, k*) and Sec. 4.2 (b^1, b^2).
 
-Readings (listed in the design notes):
+Readings (where the paper is silent):
   * the unknown densities are u_n and phi_n = |r'| dnu_c u_n (the paper's phi,
     Sec. 4.1-4.2); the source weight is W_u = 2 rho |r'| for u and
     W_phi = 2 rho for phi (factor 2 and rho' of Eqs. (snpml)-(k0pml)), and
@@ -187,16 +187,28 @@ def disc_solid_angle(rho, z, Lr):
     """Solid angle of the disc {rho' <= Lr, z' = 0} seen from (rho, 0, z), rho < Lr.
 
     Omega = int_0^{2pi} [1 - |z| / sqrt(z^2 + s(th)^2)] dth, s(th) the distance
-    in the plane from the foot point to the rim along direction th.
+    in the plane from the foot point to the rim along direction th.  The
+    integrand is smooth and 2 pi-periodic for rho < Lr, so the periodic
+    trapezoid rule converges geometrically; it is applied to the second term
+    alone (Omega = 2 pi - int |z| / sqrt(z^2 + s^2)), doubling the number of
+    points until two successive sums agree to 1e-15 x 2 pi.
     """
-    from scipy.integrate import quad
     out = np.empty(len(rho))
     for i, (r, h) in enumerate(zip(rho, z)):
         if h == 0.0:
             out[i] = 2.0 * np.pi
             continue
-        f = lambda th: 1.0 - abs(h) / np.sqrt(h * h + (-r * np.cos(th) + np.sqrt(Lr * Lr - (r * np.sin(th)) ** 2)) ** 2)
-        out[i] = quad(f, 0.0, 2.0 * np.pi, epsabs=1e-15, epsrel=1e-14, limit=400)[0]
+        n, prev = 64, None
+        while True:
+            th = 2.0 * np.pi * np.arange(n) / n
+            s = -r * np.cos(th) + np.sqrt(Lr * Lr - (r * np.sin(th)) ** 2)
+            val = (2.0 * np.pi / n) * np.sum(abs(h) / np.sqrt(h * h + s * s))
+            if prev is not None and abs(val - prev) <= 1e-15 * 2.0 * np.pi:
+                break
+            if n >= 1 << 22:
+                raise RuntimeError("disc solid angle: trapezoid sums did not settle")
+            prev, n = val, 2 * n
+        out[i] = 2.0 * np.pi - val
     return out
 
 

@@ -22,7 +22,7 @@ Normalisation: modal kernels are F^_n = int_{-pi}^{pi} e^{-i n psi} F(psi) dpsi
 (the paper's (2 pi)^{-1/2} factors cancel out of every equation), so the
 convolution of Sec. 3.3, Eq. (con) reads (fg)^_n = (1/2pi) sum_m f^_m g^_{n-m}.
 
-Readings (listed in the design notes):
+Readings (where the paper is silent):
   * "close" = Re sqrt(2 (chi - 1)) < eta_s with chi - 1 = d^2 / (2 rho~ rho~'),
     d^2 = (rho~ - rho~')^2 + (z~ - z~')^2, eta_s = split_c * 2 pi / M.  This is
     the distance of the kernel's complex singularity from the real psi axis.

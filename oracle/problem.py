@@ -15,8 +15,7 @@ Sections followed here:
   * Sec. 3.1, Eq. (g1t) and the line after it: conormal nu_c = A^T nu.
   * Sec. 4 intro, Eq. (sxi): graded parametrisation of each smooth segment.
 
-Readings taken where the paper is silent or garbled (each is listed in the
-design notes):
+Readings taken where the paper is silent or garbled:
   * Eq. (sxi) maps t^0 to s^1 as printed; the orientation is flipped so that
     t^0 -> s^0.  Each segment uses its own regular parameter s in [0, 1]
     (the paper says arclength; any regular parameter gives the same graded

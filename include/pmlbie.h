@@ -157,6 +157,11 @@ int  pmlbie_nodes(const pmlbie_problem* prob, double* rho, double* z, double* sp
  * that of the lower region. */
 int  pmlbie_diagonal(const pmlbie_problem* prob, double* Da, double* Db, int n);
 
+/* Sizes of the problem: N unknown nodes and M azimuthal samples (modes
+ * 0 .. M/2-1), as given to pmlbie_create (Sec. 3.3, Sec. 4.1).  Either
+ * pointer may be NULL.  EINVAL if prob is NULL. */
+int  pmlbie_dims(const pmlbie_problem* prob, int* N, int* M);
+
 /* Number of close (split) pairs: grid pairs and Alpert correction pairs. */
 int  pmlbie_near_count(const pmlbie_problem* prob, int* n_grid_near, int* n_corr);
 
@@ -347,6 +352,19 @@ int  pmlbie_check_finite(const void* dev, size_t count, void* stream);
  * expected outcome), OK if it completed, EINVAL, ECUDA.  The context stays
  * usable.  Synchronises the stream. */
 int  pmlbie_selftest_wait(long long iterations, void* stream);
+
+/* Self-test of the library's own elementary functions (not an operation of
+ * the paper: the sampling loops of Sec. 3.1 / 4.1 evaluate e^{iq} with their
+ * own exp, sin / cos and 1/sqrt).  Evaluates, at the n doubles of device
+ * array dev_x, into device array dev_out:
+ *   fn 0: exp(x)            -> out[i]   (arguments are clamped to [-708, 709])
+ *   fn 1: sin(x), cos(x)    -> out[2 i], out[2 i + 1]
+ *   fn 2: 1/sqrt(x)         -> out[i]   (x > 0)
+ *   fn 10, 11, 12: the same by the CUDA math library (exp, sincos, rsqrt),
+ *   the references the tests compare with.
+ * dev_out holds n (fn 0, 2, 10, 12) or 2 n (fn 1, 11) doubles.  Synchronises
+ * the stream.  EINVAL for an unknown fn, NULL buffers or n > 2^31; ECUDA. */
+int  pmlbie_selftest_elementary(int fn, const void* dev_x, void* dev_out, size_t n, void* stream);
 
 #ifdef __cplusplus
 }

@@ -60,12 +60,12 @@ class pmlbie_solve_opts(ctypes.Structure):
 
 
 EXPORTS = ["pmlbie_create", "pmlbie_destroy", "pmlbie_last_error", "pmlbie_nodes", "pmlbie_diagonal",
-           "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_corrections", "pmlbie_node_tables",
+           "pmlbie_dims", "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_corrections", "pmlbie_node_tables",
            "pmlbie_alpert_rule", "pmlbie_workspace_bytes",
            "pmlbie_modal_kernels",
            "pmlbie_modal_kernels_noalloc",
            "pmlbie_solve", "pmlbie_solve_ex", "pmlbie_solve_batch", "pmlbie_field", "pmlbie_solve_host",
-           "pmlbie_check_finite", "pmlbie_selftest_wait"]
+           "pmlbie_check_finite", "pmlbie_selftest_wait", "pmlbie_selftest_elementary"]
 
 
 def _load():
@@ -83,6 +83,7 @@ def _load():
     lib.pmlbie_nodes.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int]
     lib.pmlbie_diagonal.argtypes = [vp, dp, dp, ctypes.c_int]
     lib.pmlbie_near_count.argtypes = [vp, ip, ip]
+    lib.pmlbie_dims.argtypes = [vp, ip, ip]
     lib.pmlbie_near_pairs.argtypes = [vp, ip, ip, ip, ip, ctypes.c_int]
     lib.pmlbie_corrections.argtypes = [vp, ip, dp, ip, dp, ctypes.c_int]
     lib.pmlbie_node_tables.argtypes = [vp, dp, dp, dp, dp, dp, ctypes.c_int]
@@ -105,8 +106,9 @@ def _load():
                                  vp, vp, vp]
     lib.pmlbie_check_finite.argtypes = [vp, ctypes.c_size_t, vp]
     lib.pmlbie_selftest_wait.argtypes = [ctypes.c_longlong, vp]
-    for f in ("pmlbie_check_finite", "pmlbie_selftest_wait", "pmlbie_nodes", "pmlbie_diagonal",
-              "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_corrections", "pmlbie_node_tables",
+    lib.pmlbie_selftest_elementary.argtypes = [ctypes.c_int, vp, vp, ctypes.c_size_t, vp]
+    for f in ("pmlbie_check_finite", "pmlbie_selftest_wait", "pmlbie_selftest_elementary", "pmlbie_nodes", "pmlbie_diagonal",
+              "pmlbie_dims", "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_corrections", "pmlbie_node_tables",
               "pmlbie_alpert_rule",
               "pmlbie_modal_kernels", "pmlbie_modal_kernels_noalloc", "pmlbie_solve", "pmlbie_solve_ex",
               "pmlbie_solve_batch", "pmlbie_field", "pmlbie_solve_host"):
@@ -118,9 +120,10 @@ lib = _load()
 
 
 class PmlbieError(RuntimeError):
-    def __init__(self, code, where):
+    def __init__(self, code, where, message=None):
         self.code = code
-        super().__init__("%s failed (%d): %s" % (where, code, lib.pmlbie_last_error().decode()))
+        text = message if message is not None else lib.pmlbie_last_error().decode()
+        super().__init__("%s failed (%d): %s" % (where, code, text))
 
 
 def check(code, where):
@@ -136,6 +139,40 @@ def _dptr(a):
 
 def _tptr(t):
     return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _check_dev(t, numel, where, name):
+    """A device buffer handed to the library: None, or a contiguous complex128
+    CUDA tensor on the current device with exactly `numel` elements.  The
+    library writes or reads numel elements through the raw pointer, so a
+    smaller tensor, another dtype or a strided view would be overrun;
+    PmlbieError(EINVAL) before any device work instead."""
+    if t is None:
+        return
+    import torch
+    bad = None
+    if not isinstance(t, torch.Tensor):
+        bad = "is not a torch tensor"
+    elif not t.is_cuda:
+        bad = "is not a CUDA tensor"
+    elif t.dtype != torch.complex128:
+        bad = "has dtype %s, not complex128" % t.dtype
+    elif not t.is_contiguous():
+        bad = "is not contiguous"
+    elif t.numel() != numel:
+        bad = "has %d elements, the call needs %d" % (t.numel(), numel)
+    elif t.device.index != torch.cuda.current_device():
+        bad = "is on cuda:%d, the current device is cuda:%d" % (t.device.index, torch.cuda.current_device())
+    if bad:
+        raise PmlbieError(PMLBIE_EINVAL, where, "%s %s" % (name, bad))
+
+
+def _mode_count(h, mode_lo, mode_hi):
+    """Modes of a call's mode range (mode_lo = mode_hi = 0: all M/2)."""
+    _, M = pmlbie_dims(h)
+    if mode_lo == 0 and mode_hi == 0:
+        return M // 2
+    return max(mode_hi - mode_lo, 0)
 
 
 def _stream(stream):
@@ -191,6 +228,13 @@ def pmlbie_diagonal(h, N):
     Da, Db = np.empty(N), np.empty(N)
     check(lib.pmlbie_diagonal(h, _dptr(Da), _dptr(Db), N), "pmlbie_diagonal")
     return Da, Db
+
+
+def pmlbie_dims(h):
+    """(N, M) of a problem."""
+    n, m = ctypes.c_int(), ctypes.c_int()
+    check(lib.pmlbie_dims(h, ctypes.byref(n), ctypes.byref(m)), "pmlbie_dims")
+    return n.value, m.value
 
 
 def pmlbie_near_count(h):
@@ -252,12 +296,16 @@ def pmlbie_workspace_bytes(h, precision, n_rhs):
 
 def pmlbie_modal_kernels(h, mode_lo, mode_hi, out, stream=None):
     """out: complex128 CUDA tensor of (mode_hi-mode_lo)*4*N*N elements."""
+    N, _ = pmlbie_dims(h)
+    _check_dev(out, max(mode_hi - mode_lo, 0) * 4 * N * N, "pmlbie_modal_kernels", "out")
     check(lib.pmlbie_modal_kernels(h, mode_lo, mode_hi, _tptr(out), _stream(stream)), "pmlbie_modal_kernels")
     return out
 
 
 def pmlbie_modal_kernels_noalloc(h, mode_lo, mode_hi, out, stream=None):
     """Allocation-free modal kernels into out (same layout as pmlbie_modal_kernels)."""
+    N, _ = pmlbie_dims(h)
+    _check_dev(out, max(mode_hi - mode_lo, 0) * 4 * N * N, "pmlbie_modal_kernels_noalloc", "out")
     check(lib.pmlbie_modal_kernels_noalloc(h, mode_lo, mode_hi, _tptr(out), _stream(stream)),
           "pmlbie_modal_kernels_noalloc")
     return out
@@ -267,6 +315,9 @@ def pmlbie_solve(h, precision, polar, u1=None, phi1=None, u2=None, phi2=None, st
                  allow_noconverge=False):
     import numpy as np
     pol = np.ascontiguousarray(np.asarray(polar, dtype=np.float64).reshape(-1))
+    N, M = pmlbie_dims(h)
+    for name, t in (("u1", u1), ("phi1", phi1), ("u2", u2), ("phi2", phi2)):
+        _check_dev(t, (M // 2) * N * len(pol), "pmlbie_solve", name)
     rep = pmlbie_report()
     rep.struct_size = ctypes.sizeof(pmlbie_report)
     rc = lib.pmlbie_solve(h, precision, len(pol), _dptr(pol), _tptr(u1), _tptr(phi1), _tptr(u2), _tptr(phi2),
@@ -280,6 +331,9 @@ def pmlbie_solve_ex(h, precision, polar, azimuth=None, mode_lo=0, mode_hi=0, max
                     workspace_limit=0, u1=None, phi1=None, u2=None, phi2=None, stream=None,
                     allow_noconverge=False, sources=None):
     o, keep = make_opts(precision, polar, azimuth, mode_lo, mode_hi, max_chunk_modes, workspace_limit, sources)
+    N, _ = pmlbie_dims(h)
+    for name, t in (("u1", u1), ("phi1", phi1), ("u2", u2), ("phi2", phi2)):
+        _check_dev(t, _mode_count(h, mode_lo, mode_hi) * N * o.n_rhs, "pmlbie_solve_ex", name)
     rep = pmlbie_report()
     rep.struct_size = ctypes.sizeof(pmlbie_report)
     rc = lib.pmlbie_solve_ex(h, ctypes.byref(o), _tptr(u1), _tptr(phi1), _tptr(u2), _tptr(phi2), _stream(stream),
@@ -323,6 +377,12 @@ def pmlbie_solve_batch(handles, opts, u1=None, phi1=None, u2=None, phi2=None, n_
     """handles: problem handles; opts: list of pmlbie_solve_opts; u1..phi2: lists
     of device tensors (or None).  Returns the list of reports."""
     n = len(handles)
+    for i, (hh, o) in enumerate(zip(handles, opts)):
+        N, _ = pmlbie_dims(hh)
+        need = _mode_count(hh, o.mode_lo, o.mode_hi) * N * o.n_rhs
+        for name, ts in (("u1", u1), ("phi1", phi1), ("u2", u2), ("phi2", phi2)):
+            if ts is not None:
+                _check_dev(ts[i], need, "pmlbie_solve_batch", "%s[%d]" % (name, i))
     H = (ctypes.c_void_p * n)(*handles)
     O = (pmlbie_solve_opts * n)(*opts)
 
@@ -344,6 +404,11 @@ def pmlbie_field(h, rho, z, region, n_rhs, u1, phi1, u2, phi2, out, mode_lo=0, m
     g = np.ascontiguousarray(np.asarray(region, dtype=np.int32).reshape(-1))
     if not (len(r) == len(zz) == len(g)):
         raise ValueError("rho, z and region differ in length")
+    N, _ = pmlbie_dims(h)
+    nm = _mode_count(h, mode_lo, mode_hi)
+    for name, t in (("u1", u1), ("phi1", phi1), ("u2", u2), ("phi2", phi2)):
+        _check_dev(t, nm * N * n_rhs, "pmlbie_field", name)
+    _check_dev(out, nm * len(r) * n_rhs, "pmlbie_field", "out")
     check(lib.pmlbie_field(h, len(r), _dptr(r), _dptr(zz), g.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), mode_lo,
                            mode_hi, n_rhs, _tptr(u1), _tptr(phi1), _tptr(u2), _tptr(phi2), _tptr(out),
                            _stream(stream)), "pmlbie_field")
@@ -353,6 +418,15 @@ def pmlbie_solve_host(h, precision, polar, u1, phi1, u2, phi2, stream=None):
     """Host outputs: complex128 numpy arrays (any may be None)."""
     import numpy as np
     pol = np.ascontiguousarray(np.asarray(polar, dtype=np.float64).reshape(-1))
+    N, M = pmlbie_dims(h)
+    for name, a in (("u1", u1), ("phi1", phi1), ("u2", u2), ("phi2", phi2)):
+        if a is None:
+            continue
+        if not (isinstance(a, np.ndarray) and a.dtype == np.complex128 and a.flags.c_contiguous
+                and a.size == (M // 2) * N * len(pol)):
+            raise PmlbieError(PMLBIE_EINVAL, "pmlbie_solve_host",
+                              "%s must be a C-contiguous complex128 array of %d elements" %
+                              (name, (M // 2) * N * len(pol)))
     rep = pmlbie_report()
     rep.struct_size = ctypes.sizeof(pmlbie_report)
 
@@ -364,10 +438,29 @@ def pmlbie_solve_host(h, precision, polar, u1, phi1, u2, phi2, stream=None):
 
 
 def pmlbie_check_finite(t, stream=None):
-    """Status of the NaN / Inf scan of a complex128 device tensor (no raise)."""
+    """Status of the NaN / Inf scan of a complex128 device tensor (no raise
+    for the scan's result; a tensor that is not a contiguous complex128 CUDA
+    tensor raises PmlbieError(EINVAL))."""
+    if t is not None:
+        _check_dev(t, t.numel(), "pmlbie_check_finite", "t")
     return lib.pmlbie_check_finite(_tptr(t), t.numel(), _stream(stream))
 
 
 def pmlbie_selftest_wait(iterations, stream=None):
     """Status of the bounded-wait self-test (ETIMEOUT expected; no raise)."""
     return lib.pmlbie_selftest_wait(int(iterations), _stream(stream))
+
+
+def pmlbie_selftest_elementary(fn, x, out, stream=None):
+    """Evaluate elementary-function selector fn (include/pmlbie.h) at the
+    float64 CUDA tensor x into the float64 CUDA tensor out (len(x) values, or
+    2 len(x) for the sin / cos selectors)."""
+    import torch
+    for name, t, want in (("x", x, x.numel()), ("out", out, x.numel() * (2 if fn % 10 == 1 else 1))):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                and t.numel() == want):
+            raise PmlbieError(PMLBIE_EINVAL, "pmlbie_selftest_elementary",
+                              "%s must be a contiguous float64 CUDA tensor of %d elements" % (name, want))
+    check(lib.pmlbie_selftest_elementary(fn, _tptr(x), _tptr(out), x.numel(), _stream(stream)),
+          "pmlbie_selftest_elementary")
+    return out

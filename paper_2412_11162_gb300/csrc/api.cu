@@ -317,6 +317,13 @@ int pmlbie_diagonal(const pmlbie_problem* prob, double* Da, double* Db, int n) {
     return PMLBIE_OK;
 }
 
+int pmlbie_dims(const pmlbie_problem* prob, int* N, int* M) {
+    if (!prob) return fail(PMLBIE_EINVAL, "problem NULL");
+    if (N) *N = prob->P.N;
+    if (M) *M = prob->P.M;
+    return PMLBIE_OK;
+}
+
 int pmlbie_near_count(const pmlbie_problem* prob, int* n_grid_near, int* n_corr) {
     if (!prob) return fail(PMLBIE_EINVAL, "problem NULL");
     if (n_grid_near) *n_grid_near = prob->H.n_grid_near;
@@ -1065,6 +1072,17 @@ int pmlbie_selftest_wait(long long iterations, void* stream) {
     if (e != cudaSuccess) return fail(PMLBIE_ECUDA, std::string("wait self-test: ") + cudaGetErrorString(e));
     return h ? fail(PMLBIE_ETIMEOUT, "bounded wait expired after " + std::to_string(iterations) + " polls")
              : PMLBIE_OK;
+}
+
+int pmlbie_selftest_elementary(int fn, const void* dev_x, void* dev_out, size_t n, void* stream) {
+    if (!elementary_selftest_known(fn)) return fail(PMLBIE_EINVAL, "unknown elementary-function selector");
+    if (n > 0 && (!dev_x || !dev_out)) return fail(PMLBIE_EINVAL, "NULL buffer");
+    if (n > ((size_t)1 << 31)) return fail(PMLBIE_EINVAL, "n above 2^31");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PMLBIE_CUDA_TRY(launch_elementary_selftest(fn, static_cast<const double*>(dev_x), static_cast<double*>(dev_out),
+                                               n, s));
+    PMLBIE_CUDA_TRY(cudaStreamSynchronize(s));
+    return PMLBIE_OK;
 }
 
 int pmlbie_solve_host(pmlbie_problem* prob, int precision, int n_rhs, const double* polar, double* u1,

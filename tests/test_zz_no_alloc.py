@@ -29,6 +29,28 @@ def test_noalloc_matches_allocating_call_twice():
         assert err <= 1e-12, err
 
 
+def test_noalloc_mode_subrange_on_side_stream():
+    """A mode range that does not start at 0 (modes 3..8), issued on a
+    caller-created stream: the call only enqueues work on that stream, so the
+    test synchronises it before reading, and compares with the matching modes
+    of the allocating call."""
+    import torch
+    from paper_2412_11162_gb300 import Problem
+    from paper_2412_11162_gb300 import binding as B
+    P = Problem(2 * np.pi, 3 * np.pi, 128, 64)
+    ref = P.modal_kernels()
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    for _ in range(2):
+        with torch.cuda.stream(side):
+            out = torch.full((6, 4, 128, 128), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda")
+        B.pmlbie_modal_kernels_noalloc(P.handle, 3, 9, out, stream=side)
+        side.synchronize()
+        assert torch.isfinite(out).all()
+        err = (torch.linalg.vector_norm(out - ref[3:9]) / torch.linalg.vector_norm(ref[3:9])).item()
+        assert err <= 1e-12, err
+
+
 def test_noalloc_rejects_scratch_beyond_limit():
     from paper_2412_11162_gb300 import Problem
     from paper_2412_11162_gb300 import binding as B

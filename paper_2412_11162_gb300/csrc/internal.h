@@ -189,6 +189,11 @@ cudaError_t launch_outputs(const pmlbie_problem* prob, int n_rhs, int nm, const 
                            const double2* b1, const double2* b2, double2* u1, double2* phi1,
                            double2* u2, double2* phi2, cudaStream_t s);
 
+// Elementary-function self-test (pmlbie_selftest_elementary): the functions
+// selected by fn at n points, out as documented in include/pmlbie.h
+bool elementary_selftest_known(int fn);
+cudaError_t launch_elementary_selftest(int fn, const double* x, double* out, size_t n, cudaStream_t s);
+
 // dense batched linear algebra (lu.cu)
 // Leaves piv[b] as the row permutation of the factorisation: piv[b][i] is the
 // original row that ends in row i (P A = L U with (P x)_i = x_{piv[i]}).

@@ -1627,4 +1627,35 @@ cudaError_t launch_expand_waves(int N, int nmodes, int mode_lo, int n_src, int n
     return cudaGetLastError();
 }
 
+namespace {
+// Elementary-function self-test: fn 0 / 1 / 2 evaluate the sampling loops'
+// exp, sin and cos, 1/sqrt; fn 10 / 11 / 12 the CUDA math library's exp,
+// sincos, rsqrt at the same points (the references).  sin, cos: out[2i],
+// out[2i + 1]; the others out[i].
+__global__ void elementary_selftest_kernel(int fn, const double* x, double* out, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    double s, c;
+    switch (fn) {
+        case 0: out[i] = fexp(v); break;
+        case 1: fsincos(v, &s, &c); out[2 * i] = s; out[2 * i + 1] = c; break;
+        case 2: out[i] = frsqrt(v); break;
+        case 10: out[i] = exp(v); break;
+        case 11: sincos(v, &s, &c); out[2 * i] = s; out[2 * i + 1] = c; break;
+        case 12: out[i] = rsqrt(v); break;
+        default: break;
+    }
+}
+}  // namespace
+
+bool elementary_selftest_known(int fn) { return fn == 0 || fn == 1 || fn == 2 || fn == 10 || fn == 11 || fn == 12; }
+
+cudaError_t launch_elementary_selftest(int fn, const double* x, double* out, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    elementary_selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(fn, x, out, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace pmlbie

@@ -306,6 +306,7 @@ def run_ours(args, rank, world):
     f32 = P.field(fr, fz, fg, {k: v[sub[0]:sub[1]].contiguous() for k, v in mixed_out.items()}, modes=sub,
                   stream=stream)
     rel["field_32_points"] = (torch.linalg.vector_norm(f32 - f64) / torch.linalg.vector_norm(f64)).item()
+    oracle_err = oracle_errors(w, sub, {"mixed": (mixed_out, f32), "fp64": (sub_outs, f64)})
 
     ng, nc = P.near_count()
     ncounts = near_counts(P)
@@ -365,6 +366,7 @@ def run_ours(args, rank, world):
             "solve": fp64_reps[-1].ms_solve}},
         "speedup_mixed_vs_fp64": ms64 / ms,
         "mixed_vs_fp64_rel_err": rel,
+        "oracle_rel_err": oracle_err,
         "near_pairs": {"grid": ng, "alpert": nc},
         "gpu_launches": int(sum(r.launches for r in reps)),
         "roofline": roof,
@@ -385,6 +387,40 @@ def run_ours(args, rank, world):
     emit_line(line, rank)
     if dist:
         dist.destroy_process_group()
+
+
+def oracle_errors(w, sub, runs):
+    """Relative 2-norm errors of the solves against the FP64 oracle on the
+    modes stored in tests/golden/bump_n512_m256_oracle.npz (written by the
+    committed script beside it, which calls only oracle/): densities u1, phi1,
+    u2, phi2 and the scattered field at the same 32 points.  runs: precision
+    -> (outputs [mode][node][rhs] of the modes `sub`, field [mode][point][rhs]).
+    None when the workload is not the stored one.  Computed after the timed
+    region."""
+    path = os.path.join(ROOT, "tests", "golden", "bump_n512_m256_oracle.npz")
+    try:
+        g = np.load(path)
+    except OSError:
+        return None
+    if (int(g["N"]), int(g["M"])) != (w["N"], w["M"]) or abs(float(g["k1"]) - w["k1"]) > 1e-12 or \
+            abs(float(g["k2"]) - w["k2"]) > 1e-12 or abs(float(g["polar"]) - w["polar"]) > 1e-15:
+        return None
+    modes = [int(n) for n in g["modes"] if sub[0] <= n < sub[1]]
+    if not modes:
+        return None
+    idx = [n - sub[0] for n in modes]
+    gi = [list(g["modes"]).index(n) for n in modes]
+    out = {"modes": modes, "source": "tests/golden/bump_n512_m256_oracle.npz"}
+    for prec, (dens, fld) in runs.items():
+        e = {}
+        for k in ("u1", "phi1", "u2", "phi2"):
+            got = dens[k].cpu().numpy()[idx, :, 0]
+            ref = g[k][gi]
+            e[k] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        got = fld.cpu().numpy()[idx, :, 0]
+        e["field_32_points"] = float(np.linalg.norm(got - g["field"][gi]) / np.linalg.norm(g["field"][gi]))
+        out[prec] = e
+    return out
 
 
 def h2d_bytes(P, w):

@@ -244,6 +244,7 @@ def run_ours(args, rank, world):
     dist = init_dist(world, "nccl", torch.device("cuda", dev))
     w = WORKLOAD
     kw = dict(a1=w["a1"], T=w["T"], S=w["S"], bump_h=w["bump_h"])
+    pipes = measure_pipes(B)
     P = Problem(w["k1"], w["k2"], w["N"], w["M"], **kw)
     shape = (w["M"] // 2, w["N"], 1)
     outs = {k: torch.empty(shape, dtype=torch.complex128, device="cuda") for k in ("u1", "phi1", "u2", "phi2")}
@@ -369,6 +370,7 @@ def run_ours(args, rank, world):
         "oracle_rel_err": oracle_err,
         "near_pairs": {"grid": ng, "alpert": nc},
         "gpu_launches": int(sum(r.launches for r in reps)),
+        "measured_pipe_peaks": pipes,
         "roofline": roof,
         "roofline_far": roof_far,
         "stage_rooflines": stage_rooflines(w, last, pk),
@@ -387,6 +389,20 @@ def run_ours(args, rank, world):
     emit_line(line, rank)
     if dist:
         dist.destroy_process_group()
+
+
+def measure_pipes(B):
+    """TFLOP/s of the FP64 FMA, FP32 FMA and TF32 tensor-core pipes measured on
+    this GPU by the library's probe (pmlbie_selftest_peak), before the timed
+    region."""
+    out = {}
+    for kind, name in ((0, "fp64_fma_tflops"), (1, "fp32_fma_tflops"), (2, "tf32_tcgen05_tflops")):
+        try:
+            out[name] = B.pmlbie_selftest_peak(kind)
+        except Exception as e:       # reported, not fatal: the roofline falls back to derived peaks
+            out[name] = None
+            out[name + "_error"] = str(e)[:200]
+    return out
 
 
 def oracle_errors(w, sub, runs):

@@ -225,6 +225,31 @@ size_t pmlbie_workspace_bytes(const pmlbie_problem* prob, int precision, int n_r
 int  pmlbie_modal_kernels(pmlbie_problem* prob, int mode_lo, int mode_hi, void* dev_out,
                           void* stream);
 
+/* pmlbie_modal_kernels in the arithmetic of a solve's precision: PMLBIE_FP64
+ * as pmlbie_modal_kernels; PMLBIE_MIXED as the mixed solve builds its
+ * matrices: the far pairs' samples, transforms and scatter, and the close
+ * pairs' split samples, transforms and convolution, in float-float (pairs
+ * of FP32 numbers, ~48-bit significands, on the FP32 pipe; relative rounding
+ * ~1e-14 of a pair's samples, growing with |q| = omega |dr| as |q| 2^-47),
+ * with the exact modal Laplace kernels of the split (Sec. 4.1, the
+ * near-singular part) in FP64.  Problems whose phases |q| reach the
+ * float-float sin / cos range (~780), and the diagnostic exact split
+ * (subst_off), take the FP64 kernels in both precisions.
+ * Errors as pmlbie_modal_kernels; EINVAL for another precision. */
+int  pmlbie_modal_kernels_ex(pmlbie_problem* prob, int precision, int mode_lo, int mode_hi, void* dev_out,
+                             void* stream);
+
+/* Split modal kernels of every close pair (Sec. 4.1 kernel splitting; Sec. 4.3
+ * substitution on PML pairs), in the close-pair list's order (pmlbie_near_pairs:
+ * grid pairs, then Alpert correction pairs -- the values the assembly adds
+ * with the Lagrange stencils), in the arithmetic of `precision` as
+ * pmlbie_modal_kernels_ex.  Output: dev_out, caller-owned device buffer of
+ * (n_grid_near + n_corr) * 4 * (mode_hi - mode_lo) complex128 laid out
+ * [pair][kernel][mode], kernel as in pmlbie_modal_kernels; no quadrature
+ * weights.  Synchronises the stream.  Errors as pmlbie_modal_kernels_ex. */
+int  pmlbie_close_pair_kernels(pmlbie_problem* prob, int precision, int mode_lo, int mode_hi, void* dev_out,
+                               void* stream);
+
 /* Allocation-free variant of pmlbie_modal_kernels (the paper has no
  * counterpart: this is a deployment convenience).  For callers that must not
  * call cudaMalloc while they run (a framework whose own allocator owns the
@@ -254,8 +279,10 @@ int  pmlbie_modal_kernels_noalloc(pmlbie_problem* prob, int mode_lo, int mode_hi
  * Outputs (caller-owned device buffers, complex128, [mode][node][rhs], M/2
  * modes): u1 = u^{s,1}_n, phi1 = |r'| d_nu_c u^{s,1}_n, u2, phi2 (the same for
  * the lower medium, d_nu with the same nu).  Any output may be NULL.
- * Mixed precision: FP64 modal kernels and matrices, complex64 LU (tensor-core
- * trailing updates), iterative refinement with FP64 residuals until, for
+ * Mixed precision: modal kernels in float-float arithmetic on the FP32 pipe
+ * (as pmlbie_modal_kernels_ex with PMLBIE_MIXED) stored as complex128
+ * matrices, complex64 LU (tensor-core trailing updates), iterative
+ * refinement with FP64 residuals of those matrices until, for
  * every mode and right-hand side, the relative residual is <= 1e-13, or the
  * normwise backward error |B - A x| / (|A|_F |x| + |B|) is <= 1e-16, or it is
  * <= 1e-14 and no longer decreasing (the FP64 floor); modes
@@ -365,6 +392,16 @@ int  pmlbie_selftest_wait(long long iterations, void* stream);
  * dev_out holds n (fn 0, 2, 10, 12) or 2 n (fn 1, 11) doubles.  Synchronises
  * the stream.  EINVAL for an unknown fn, NULL buffers or n > 2^31; ECUDA. */
 int  pmlbie_selftest_elementary(int fn, const void* dev_x, void* dev_out, size_t n, void* stream);
+
+/* Pipe-throughput probe (not an operation of the paper: the measured
+ * denominators of the library's roofline fractions).  kind 0: FP64 FMA
+ * (independent fma chains on every SM), 1: FP32 FMA, 2: TF32 tensor cores
+ * (tcgen05.mma kind::tf32, M = 128, N = 256, K = 8, back to back from one
+ * thread per SM, the accumulator in tensor memory).  *tflops receives the
+ * rate of one timed launch after a warm-up launch (fused multiply-add = 2
+ * flops).  Synchronises the stream; allocates 4 KB of device scratch.
+ * EINVAL, ECUDA, ETIMEOUT (the tensor-core wait expired). */
+int  pmlbie_selftest_peak(int kind, double* tflops, void* stream);
 
 #ifdef __cplusplus
 }

@@ -62,10 +62,10 @@ class pmlbie_solve_opts(ctypes.Structure):
 EXPORTS = ["pmlbie_create", "pmlbie_destroy", "pmlbie_last_error", "pmlbie_nodes", "pmlbie_diagonal",
            "pmlbie_dims", "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_corrections", "pmlbie_node_tables",
            "pmlbie_alpert_rule", "pmlbie_workspace_bytes",
-           "pmlbie_modal_kernels",
+           "pmlbie_modal_kernels", "pmlbie_modal_kernels_ex", "pmlbie_close_pair_kernels",
            "pmlbie_modal_kernels_noalloc",
            "pmlbie_solve", "pmlbie_solve_ex", "pmlbie_solve_batch", "pmlbie_field", "pmlbie_solve_host",
-           "pmlbie_check_finite", "pmlbie_selftest_wait", "pmlbie_selftest_elementary"]
+           "pmlbie_check_finite", "pmlbie_selftest_wait", "pmlbie_selftest_elementary", "pmlbie_selftest_peak"]
 
 
 def _load():
@@ -92,6 +92,8 @@ def _load():
     lib.pmlbie_workspace_bytes.restype = ctypes.c_size_t
     lib.pmlbie_modal_kernels.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp]
     lib.pmlbie_modal_kernels_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.pmlbie_modal_kernels_ex.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.pmlbie_close_pair_kernels.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
     lib.pmlbie_solve.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, vp, vp, vp, vp, vp,
                                  ctypes.POINTER(pmlbie_report)]
     lib.pmlbie_solve_host.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, vp,
@@ -107,10 +109,12 @@ def _load():
     lib.pmlbie_check_finite.argtypes = [vp, ctypes.c_size_t, vp]
     lib.pmlbie_selftest_wait.argtypes = [ctypes.c_longlong, vp]
     lib.pmlbie_selftest_elementary.argtypes = [ctypes.c_int, vp, vp, ctypes.c_size_t, vp]
-    for f in ("pmlbie_check_finite", "pmlbie_selftest_wait", "pmlbie_selftest_elementary", "pmlbie_nodes", "pmlbie_diagonal",
+    lib.pmlbie_selftest_peak.argtypes = [ctypes.c_int, dp, vp]
+    for f in ("pmlbie_check_finite", "pmlbie_selftest_wait", "pmlbie_selftest_elementary", "pmlbie_selftest_peak", "pmlbie_nodes", "pmlbie_diagonal",
               "pmlbie_dims", "pmlbie_near_count", "pmlbie_near_pairs", "pmlbie_corrections", "pmlbie_node_tables",
               "pmlbie_alpert_rule",
-              "pmlbie_modal_kernels", "pmlbie_modal_kernels_noalloc", "pmlbie_solve", "pmlbie_solve_ex",
+              "pmlbie_modal_kernels", "pmlbie_modal_kernels_noalloc", "pmlbie_modal_kernels_ex",
+              "pmlbie_close_pair_kernels", "pmlbie_solve", "pmlbie_solve_ex",
               "pmlbie_solve_batch", "pmlbie_field", "pmlbie_solve_host"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
@@ -302,6 +306,25 @@ def pmlbie_modal_kernels(h, mode_lo, mode_hi, out, stream=None):
     return out
 
 
+def pmlbie_modal_kernels_ex(h, precision, mode_lo, mode_hi, out, stream=None):
+    """Modal kernels in the arithmetic of `precision` (same layout as
+    pmlbie_modal_kernels)."""
+    N, _ = pmlbie_dims(h)
+    _check_dev(out, max(mode_hi - mode_lo, 0) * 4 * N * N, "pmlbie_modal_kernels_ex", "out")
+    check(lib.pmlbie_modal_kernels_ex(h, precision, mode_lo, mode_hi, _tptr(out), _stream(stream)),
+          "pmlbie_modal_kernels_ex")
+    return out
+
+
+def pmlbie_close_pair_kernels(h, precision, mode_lo, mode_hi, out, stream=None):
+    """Split modal kernels of every close pair, [pair][kernel][mode]."""
+    g, c = pmlbie_near_count(h)
+    _check_dev(out, (g + c) * 4 * max(mode_hi - mode_lo, 0), "pmlbie_close_pair_kernels", "out")
+    check(lib.pmlbie_close_pair_kernels(h, precision, mode_lo, mode_hi, _tptr(out), _stream(stream)),
+          "pmlbie_close_pair_kernels")
+    return out
+
+
 def pmlbie_modal_kernels_noalloc(h, mode_lo, mode_hi, out, stream=None):
     """Allocation-free modal kernels into out (same layout as pmlbie_modal_kernels)."""
     N, _ = pmlbie_dims(h)
@@ -464,3 +487,11 @@ def pmlbie_selftest_elementary(fn, x, out, stream=None):
     check(lib.pmlbie_selftest_elementary(fn, _tptr(x), _tptr(out), x.numel(), _stream(stream)),
           "pmlbie_selftest_elementary")
     return out
+
+
+def pmlbie_selftest_peak(kind, stream=None):
+    """Measured TFLOP/s of the FP64 FMA (0), FP32 FMA (1) or TF32 tensor-core
+    (2) pipe."""
+    v = ctypes.c_double(0.0)
+    check(lib.pmlbie_selftest_peak(int(kind), ctypes.byref(v), _stream(stream)), "pmlbie_selftest_peak")
+    return v.value

@@ -28,7 +28,7 @@ def _run(cmd):
 
 def build(verbose=False):
     os.makedirs(BUILD, exist_ok=True)
-    srcs_cu = ["kernels.cu", "lu.cu", "gmres.cu", "api.cu", "noalloc.cu"]
+    srcs_cu = ["kernels.cu", "kernels_ff.cu", "lu.cu", "gmres.cu", "api.cu", "noalloc.cu", "probe.cu"]
     srcs_cc = ["host.cpp"]
     jobs = []
     for s in srcs_cu:

@@ -85,7 +85,9 @@ int ensure_device(pmlbie_problem* prob) {
         (rc = upload(D.cls, H.cls)) || (rc = upload(D.near, H.near)) || (rc = upload(D.bk, H.bk)) ||
         (rc = upload(D.off, H.off)) ||
         (rc = upload(D.corr_target, H.corr_target)) || (rc = upload(D.corr_m, H.corr_m)) ||
-        (rc = upload(D.corr_coef, H.corr_coef)) || (rc = upload(D.Da, H.Da)) || (rc = upload(D.Db, H.Db)))
+        (rc = upload(D.corr_coef, H.corr_coef)) || (rc = upload(D.Da, H.Da)) || (rc = upload(D.Db, H.Db)) ||
+        (rc = upload(D.corr_start, H.corr_start)) || (rc = upload(D.corr_cmin, H.corr_cmin)) ||
+        (rc = upload(D.corr_w, H.corr_w)))
         return rc;
     const int M = prob->P.M;
     std::vector<double2> cs(M / 2 + 1), tw(M), tw2(2 * M);
@@ -97,6 +99,34 @@ int ensure_device(pmlbie_problem* prob) {
     }
     for (int e = 0; e < M; ++e) tw[e] = make_double2(std::cos(2.0 * kPi * e / M), -std::sin(2.0 * kPi * e / M));
     if ((rc = upload(D.cos_tab, cs)) || (rc = upload(D.twid, tw)) || (rc = upload(D.twid2, tw2))) return rc;
+    {
+        const int nr = rec_table_len(M);
+        std::vector<double2> up(nr), dn(nr);
+        up[0] = dn[0] = make_double2(0.0, 0.0);
+        for (int m = 1; m < nr; ++m) {
+            up[m] = make_double2(4.0 * m / (2.0 * m + 1.0), (2.0 * m - 1.0) / (2.0 * m + 1.0));
+            dn[m] = make_double2(4.0 * m / (2.0 * m - 1.0), (2.0 * m + 1.0) / (2.0 * m - 1.0));
+        }
+        if ((rc = upload(D.rec_up, up)) || (rc = upload(D.rec_dn, dn))) return rc;
+    }
+    {
+        std::vector<float4> ftw, ftw2, fcs, ftrig;
+        std::vector<float2> fexp, fwu(H.Wu.size()), fwp(H.Wphi.size());
+        ff_tables(M, ftw, ftw2, fcs, fexp, ftrig);
+        auto f2 = [](double x) {
+            const float hi = (float)x;
+            return make_float2(hi, (float)(x - (double)hi));
+        };
+        const double c4 = 0.5 / M;
+        for (size_t m = 0; m < fwu.size(); ++m) {
+            fwu[m] = f2(H.h * H.Wu[m] * c4);
+            fwp[m] = f2(H.h * H.Wphi[m] * c4);
+        }
+        if ((rc = upload(D.twid_ff, ftw)) || (rc = upload(D.twid2_ff, ftw2)) || (rc = upload(D.cos_ff, fcs)) ||
+            (rc = upload(D.exp_ff, fexp)) || (rc = upload(D.trig_ff, ftrig)) || (rc = upload(D.wuc_ff, fwu)) ||
+            (rc = upload(D.wpc_ff, fwp)))
+            return rc;
+    }
     if ((rc = upload(ex->nu_r, H.nu_r)) || (rc = upload(ex->nu_z, H.nu_z)) || (rc = upload(ex->speed, H.speed)))
         return rc;
     ex->ready = true;
@@ -106,7 +136,9 @@ int ensure_device(pmlbie_problem* prob) {
 void free_device(pmlbie_problem* prob) {
     DeviceTables& D = prob->D;
     void* ptrs[] = {D.rho, D.z, D.I, D.Wu, D.Wphi, D.rho_t, D.nuc_r, D.nuc_z, D.bk, D.off, D.cls, D.near,
-                    D.corr_target, D.corr_m, D.corr_coef, D.Da, D.Db, D.cos_tab, D.twid, D.twid2};
+                    D.corr_target, D.corr_m, D.corr_coef, D.Da, D.Db, D.cos_tab, D.twid, D.twid2,
+                    D.corr_start, D.corr_cmin, D.corr_w, D.rec_up, D.rec_dn, D.twid_ff, D.twid2_ff, D.cos_ff, D.exp_ff, D.trig_ff, D.wuc_ff,
+                    D.wpc_ff};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     pmlbie_dev_extra* ex = extra_of(prob);
@@ -223,12 +255,18 @@ void fresnel(double w1, double w2, double phi, double* out6) {
 
 // modal kernels + assembly into w.A for modes [lo, hi); ev[0..3] bracket the
 // stages, ev[4] splits the close-pair stage
-int build_system(pmlbie_problem* prob, Workspace& w, int lo, int hi, cudaStream_t s, cudaEvent_t* ev) {
+// (the mixed path samples the far pairs in float-float arithmetic when the
+// problem's phases fit its range, else in FP64)
+int build_system(pmlbie_problem* prob, int precision, Workspace& w, int lo, int hi, cudaStream_t s,
+                 cudaEvent_t* ev) {
     FarLaunch fl{lo, hi, w.A, nullptr, true};
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[0], s));
-    PMLBIE_CUDA_TRY(launch_far(prob, fl, s));
+    if (precision == PMLBIE_MIXED && far_ff_supported(prob))
+        PMLBIE_CUDA_TRY(launch_far_ff(prob, fl, s));
+    else
+        PMLBIE_CUDA_TRY(launch_far(prob, fl, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[1], s));
-    PMLBIE_CUDA_TRY(launch_near(prob, lo, hi, w.zd, w.nout, s, ev[4]));
+    PMLBIE_CUDA_TRY(launch_near(prob, lo, hi, w.zd, w.nout, s, ev[4], precision == PMLBIE_MIXED && far_ff_supported(prob)));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
     PMLBIE_CUDA_TRY(launch_assemble(prob, lo, hi, w.nout, w.A, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[3], s));
@@ -391,7 +429,33 @@ size_t pmlbie_workspace_bytes(const pmlbie_problem* prob, int precision, int n_r
 }
 
 int pmlbie_modal_kernels(pmlbie_problem* prob, int mode_lo, int mode_hi, void* dev_out, void* stream) {
+    return pmlbie_modal_kernels_ex(prob, PMLBIE_FP64, mode_lo, mode_hi, dev_out, stream);
+}
+
+int pmlbie_close_pair_kernels(pmlbie_problem* prob, int precision, int mode_lo, int mode_hi, void* dev_out,
+                              void* stream) {
     if (!prob || !dev_out) return fail(PMLBIE_EINVAL, "problem or output NULL");
+    if (precision != PMLBIE_FP64 && precision != PMLBIE_MIXED) return fail(PMLBIE_EINVAL, "bad precision");
+    const int nm = prob->P.M / 2;
+    if (mode_lo < 0 || mode_hi > nm || mode_lo >= mode_hi) return fail(PMLBIE_EINVAL, "bad mode range");
+    int rc = ensure_device(prob);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t np = std::max<size_t>(prob->H.near.size(), 1);
+    double2* zd = nullptr;
+    PMLBIE_CUDA_TRY(cudaMalloc(&zd, sizeof(double2) * np * 2 * prob->P.M));
+    cudaError_t e = launch_near(prob, mode_lo, mode_hi, zd, (double2*)dev_out, s, nullptr,
+                                precision == PMLBIE_MIXED && far_ff_supported(prob));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(zd);
+    if (e != cudaSuccess) return fail(PMLBIE_ECUDA, std::string("close-pair kernels: ") + cudaGetErrorString(e));
+    return PMLBIE_OK;
+}
+
+int pmlbie_modal_kernels_ex(pmlbie_problem* prob, int precision, int mode_lo, int mode_hi, void* dev_out,
+                            void* stream) {
+    if (!prob || !dev_out) return fail(PMLBIE_EINVAL, "problem or output NULL");
+    if (precision != PMLBIE_FP64 && precision != PMLBIE_MIXED) return fail(PMLBIE_EINVAL, "bad precision");
     const int nm = prob->P.M / 2;
     if (mode_lo < 0 || mode_hi > nm || mode_lo >= mode_hi) return fail(PMLBIE_EINVAL, "bad mode range");
     int rc = ensure_device(prob);
@@ -406,8 +470,10 @@ int pmlbie_modal_kernels(pmlbie_problem* prob, int mode_lo, int mode_hi, void* d
         return fail(PMLBIE_ENOMEM, "scratch allocation failed");
     }
     FarLaunch fl{mode_lo, mode_hi, nullptr, (double2*)dev_out, true};
-    cudaError_t e = launch_far(prob, fl, s);
-    if (e == cudaSuccess) e = launch_near(prob, mode_lo, mode_hi, zd, nout, s);
+    cudaError_t e = precision == PMLBIE_MIXED && far_ff_supported(prob) ? launch_far_ff(prob, fl, s)
+                                                                        : launch_far(prob, fl, s);
+    if (e == cudaSuccess)
+        e = launch_near(prob, mode_lo, mode_hi, zd, nout, s, nullptr, precision == PMLBIE_MIXED && far_ff_supported(prob));
     if (e == cudaSuccess) e = launch_near_to_raw(prob, mode_lo, mode_hi, nout, (double2*)dev_out, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(zd);
@@ -544,7 +610,7 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
     pmlbie_dev_extra* ex = extra_of(prob);
     int rc;
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[0], s));
-    if ((rc = build_system(prob, w, lo, hi, s, sev))) return rc;
+    if ((rc = build_system(prob, precision, w, lo, hi, s, sev))) return rc;
     if (point)
         PMLBIE_CUDA_TRY(launch_point_rhs(prob, n_rhs, lo, hi, w.rpar, ex->speed, w.b1, w.b2, s));
     else
@@ -1074,11 +1140,21 @@ int pmlbie_selftest_wait(long long iterations, void* stream) {
              : PMLBIE_OK;
 }
 
+int pmlbie_selftest_peak(int kind, double* tflops, void* stream) {
+    if (kind < 0 || kind > 2 || !tflops) return fail(PMLBIE_EINVAL, "kind must be 0, 1 or 2 and tflops non-NULL");
+    return peak_probe(kind, tflops, static_cast<cudaStream_t>(stream));
+}
+
 int pmlbie_selftest_elementary(int fn, const void* dev_x, void* dev_out, size_t n, void* stream) {
-    if (!elementary_selftest_known(fn)) return fail(PMLBIE_EINVAL, "unknown elementary-function selector");
+    if (!elementary_selftest_known(fn) && !ff_elementary_known(fn))
+        return fail(PMLBIE_EINVAL, "unknown elementary-function selector");
     if (n > 0 && (!dev_x || !dev_out)) return fail(PMLBIE_EINVAL, "NULL buffer");
     if (n > ((size_t)1 << 31)) return fail(PMLBIE_EINVAL, "n above 2^31");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (ff_elementary_known(fn)) {
+        PMLBIE_CUDA_TRY(launch_ff_elementary(fn, static_cast<const double*>(dev_x), static_cast<double*>(dev_out), n, s));
+        return PMLBIE_OK;
+    }
     PMLBIE_CUDA_TRY(launch_elementary_selftest(fn, static_cast<const double*>(dev_x), static_cast<double*>(dev_out),
                                                n, s));
     PMLBIE_CUDA_TRY(cudaStreamSynchronize(s));

@@ -748,6 +748,25 @@ int build_tables(pmlbie_problem* prob) {
         }
     }
     const int ncorr = (int)H.corr_target.size();
+    // correction points by target (they come ordered by target) and the
+    // column window of each target's stencils, for the per-target assembly
+    H.corr_start.assign(N + 1, 0);
+    H.corr_cmin.assign(N, 0);
+    H.corr_w.assign(N, 0);
+    H.corr_wmax = 0;
+    for (int c = 0; c < ncorr; ++c) H.corr_start[H.corr_target[c] + 1]++;
+    for (int l = 0; l < N; ++l) H.corr_start[l + 1] += H.corr_start[l];
+    for (int l = 0; l < N; ++l) {
+        int lo = N, hi = -1;
+        for (int c = H.corr_start[l]; c < H.corr_start[l + 1]; ++c)
+            for (int a = 0; a < kStencil; ++a) {
+                const int m = H.corr_m[(size_t)c * kStencil + a];
+                if (m >= 0) lo = std::min(lo, m), hi = std::max(hi, m);
+            }
+        H.corr_cmin[l] = hi >= lo ? lo : 0;
+        H.corr_w[l] = hi >= lo ? hi - lo + 1 : 0;
+        H.corr_wmax = std::max(H.corr_wmax, H.corr_w[l]);
+    }
     // the points themselves (curve, PML integral and conormal of each) in parallel
     cpts.resize(ncorr);
     parallel_rows(ncorr, [&](int lo, int hi) {

@@ -41,6 +41,13 @@ struct NearPair {
 
 enum { kFlagCorr = 1, kFlagFar = 2, kFlagSubst = 4 };
 
+// Re(eta) M from which the close-pair Laplace modes take the downward
+// (Miller) recurrence (below it, the upward one).
+constexpr double kRecUpward = 3.5;
+// Length of the recurrence tables: the downward recurrence starts at
+// m_s = M + ceil(20 / Re(eta)) with Re(eta) M >= kRecUpward.
+inline int rec_table_len(int M) { return M + (int)((20.0 * M) / kRecUpward) + 4; }
+
 struct HostTables {
     int N = 0, Nt = 0, M = 0;
     double h = 0;
@@ -58,6 +65,10 @@ struct HostTables {
     std::vector<double> corr_tau;            // ncorr
     std::vector<int> corr_m;                 // ncorr * kStencil (unknown or -1)
     std::vector<double> corr_coef;           // ncorr * kStencil (w_k h L)
+    // correction points of target l: [corr_start[l], corr_start[l+1]); their
+    // stencil columns lie in [corr_cmin[l], corr_cmin[l] + corr_w[l])
+    std::vector<int> corr_start, corr_cmin, corr_w;
+    int corr_wmax = 0;
     // classes and close pairs
     std::vector<uint8_t> cls;                // N*N, [l][m]
     std::vector<NearPair> near;              // grid-near pairs, then correction pairs
@@ -76,10 +87,29 @@ struct DeviceTables {
     int* corr_target = nullptr;
     int* corr_m = nullptr;
     double* corr_coef = nullptr;
+    int* corr_start = nullptr;
+    int* corr_cmin = nullptr;
+    int* corr_w = nullptr;
     double *Da = nullptr, *Db = nullptr;
     double2* cos_tab = nullptr;   // (sin^2(psi_j/2), cos psi_j), j = 0..M/2
     double2* twid = nullptr;      // e^{-2 pi i e / M}, e = 0..M-1
     double2* twid2 = nullptr;     // e^{-2 pi i e / (2M)}, e = 0..2M-1
+    // float-float copies for the mixed path's kernels (kernels_ff.cu): the
+    // twiddles and angle table above as (re.hi, re.lo, im.hi, im.lo), the exp
+    // and sin / cos tables of ffloat.cuh, and per node h W_u / (2M) and
+    // h W_phi / (2M) (column weight times the trapezoid factor of the modes)
+    // coefficients of the Legendre-Q three-term recurrence of the close-pair
+    // Laplace modes, m = 0 .. kRecLen(M): upward (4m/(2m+1), (2m-1)/(2m+1)),
+    // downward (4m/(2m-1), (2m+1)/(2m-1)) (entry 0 unused)
+    double2* rec_up = nullptr;
+    double2* rec_dn = nullptr;
+    float4* twid_ff = nullptr;
+    float4* twid2_ff = nullptr;
+    float4* cos_ff = nullptr;
+    float2* exp_ff = nullptr;
+    float4* trig_ff = nullptr;
+    float2* wuc_ff = nullptr;
+    float2* wpc_ff = nullptr;
 };
 
 }  // namespace pmlbie
@@ -136,11 +166,27 @@ struct FarLaunch {
     bool tune = false;
 };
 cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStream_t s);
+// float-float far kernel of the mixed path (kernels_ff.cu); usable when
+// far_ff_supported (every |q| of the problem inside its sin / cos range)
+cudaError_t launch_far_ff(const pmlbie_problem* prob, const FarLaunch& fl, cudaStream_t s);
+bool far_ff_supported(const pmlbie_problem* prob);
+// host float-float tables of a problem with M azimuthal samples
+void ff_tables(int M, std::vector<float4>& twid, std::vector<float4>& twid2, std::vector<float4>& cosv,
+               std::vector<float2>& expv, std::vector<float4>& trig);
+bool ff_elementary_known(int fn);
+cudaError_t launch_ff_elementary(int fn, const double* x, double* out, size_t n, cudaStream_t s);
 // pairs per CTA of this thread's last far-kernel launch (the tuned choice)
 extern thread_local int g_far_pairs_per_cta;
-// mid (optional): event recorded between the Laplace-mode and the modes kernels
+// mid (optional): event recorded between the Laplace-mode and the modes kernels;
+// ff: the modes kernel in float-float (mixed path; not with subst_off)
 cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, double2* zd_scratch,
-                        double2* out, cudaStream_t s, cudaEvent_t mid = nullptr);
+                        double2* out, cudaStream_t s, cudaEvent_t mid = nullptr, bool ff = false);
+// the float-float close-pair modes kernel alone (kernels_ff.cu), after the
+// Laplace modes are in zd
+cudaError_t launch_near_modes_ff(const pmlbie_problem* prob, int mode_lo, int mode_hi, const double2* zd,
+                                 double2* out, cudaStream_t s);
+// Taylor coefficients of cH1 (pa) and cH3 (pb) of degree L <= 7 (Sec. 4.3)
+void taylor_coeffs(int L, double2* pa, double2* pb);
 cudaError_t launch_near_to_raw(const pmlbie_problem* prob, int mode_lo, int mode_hi,
                                const double2* near_out, double2* raw, cudaStream_t s);
 cudaError_t launch_assemble(const pmlbie_problem* prob, int mode_lo, int mode_hi,
@@ -193,6 +239,10 @@ cudaError_t launch_outputs(const pmlbie_problem* prob, int n_rhs, int nm, const 
 // selected by fn at n points, out as documented in include/pmlbie.h
 bool elementary_selftest_known(int fn);
 cudaError_t launch_elementary_selftest(int fn, const double* x, double* out, size_t n, cudaStream_t s);
+
+// Pipe-throughput probes (probe.cu): kind 0 FP64 FMA, 1 FP32 FMA, 2 TF32
+// tcgen05 MMA; TFLOP/s of one timed launch over every SM
+int peak_probe(int kind, double* out_tflops, cudaStream_t s);
 
 // dense batched linear algebra (lu.cu)
 // Leaves piv[b] as the row permutation of the factorisation: piv[b][i] is the

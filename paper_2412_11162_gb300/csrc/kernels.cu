@@ -17,6 +17,7 @@
 #include <tuple>
 
 #include "internal.h"
+#include "device_common.cuh"
 
 namespace pmlbie {
 
@@ -24,44 +25,12 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kInv4Pi = 0.079577471545947667884;
-
-// ---------------------------------------------------------------------------
-// complex helpers (double2 = re, im)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double2 c2(double x, double y) { return make_double2(x, y); }
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return c2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return c2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return c2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 cscale(double2 a, double s) { return c2(a.x * s, a.y * s); }
-__device__ __forceinline__ double2 crcp(double2 a) {
-    // 1/a with scaling against overflow
-    double s = fmax(fabs(a.x), fabs(a.y));
-    double ax = a.x / s, ay = a.y / s;
-    double d = ax * ax + ay * ay;
-    return c2(ax / (d * s), -ay / (d * s));
-}
-__device__ __forceinline__ double2 cdiv(double2 a, double2 b) { return cmul(a, crcp(b)); }
-// principal square root (branch cut on the negative real axis)
-__device__ __forceinline__ double2 csqrt(double2 z) {
-    double r = hypot(z.x, z.y);
-    if (r == 0.0) return c2(0.0, 0.0);
-    if (z.x >= 0.0) {
-        double t = sqrt(0.5 * (r + z.x));
-        return c2(t, z.y / (2.0 * t));
-    }
-    double t = sqrt(0.5 * (r - z.x));
-    return c2(fabs(z.y) / (2.0 * t), copysign(t, z.y));
-}
-// e^{i q}
-__device__ __forceinline__ double2 cexpi(double2 q) {
-    double s, c;
-    sincos(q.x, &s, &c);
-    double m = exp(-q.y);
-    return c2(m * c, m * s);
-}
-__device__ __forceinline__ double2 clog(double2 z) { return c2(log(hypot(z.x, z.y)), atan2(z.y, z.x)); }
+// Re(eta) M below which the close-pair Laplace modes c_m run the upward
+// recurrence: c_m is its minimal solution, so rounding grows like
+// e^{2 Re(eta) m} (at most e^7 at m = M, e^3.5 at m = M/2, the largest
+// index the low modes' convolutions use); above it Miller's downward
+// recurrence (M + 20 / Re(eta) steps) is used.
+constexpr double kUpward = kRecUpward;
 
 // ---------------------------------------------------------------------------
 // Elementary functions for the sampling loops.  The FP64 pipe of the GB300
@@ -188,17 +157,21 @@ __device__ __forceinline__ void fcsqrt_rcp(double2 z, double2& R, double2& iR) {
 // returns the buffer holding the result.  tw[e] = e^{-2 pi i e / M}.
 // ---------------------------------------------------------------------------
 __device__ double2* warp_fft(double2* x, double2* y, int M, const double2* tw, int lane, int tws = 1) {
-    // tw[e * tws] = e^{-2 pi i e / M}
-    int rem = M, Ns = 1;
+    // tw[e * tws] = e^{-2 pi i e / M}.  lgNs = log2(Ns) while Ns is a power of
+    // two (radix-4 and radix-2 stages come first), else -1: integer division
+    // by a run-time value expands into conversions, which this GPU issues to
+    // its FP64 pipe.  r k step < M (r < R, k < Ns, step = M / (Ns R)).
+    int rem = M, Ns = 1, lgNs = 0;
     while (rem > 1) {
-        int R = (rem % 4 == 0) ? 4 : ((rem % 2 == 0) ? 2 : 3);
+        int R = (rem & 3) == 0 ? 4 : ((rem & 1) == 0 ? 2 : 3);
         int MR = M / R, step = M / (Ns * R);
         for (int j = lane; j < MR; j += 32) {
-            int k = j % Ns;
+            const int jq = lgNs >= 0 ? (j >> lgNs) : j / Ns;
+            const int k = j - jq * Ns;
             double2 v[4];
             for (int r = 0; r < R; ++r) v[r] = x[j + r * MR];
             if (Ns > 1)   // the first stage's twiddles are all 1
-                for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[((r * k * step) % M) * tws]);
+                for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * step * tws]);
             if (R == 2) {
                 double2 a = v[0], b = v[1];
                 v[0] = cadd(a, b);
@@ -220,7 +193,7 @@ __device__ double2* warp_fft(double2* x, double2* y, int M, const double2* tw, i
                 v[1] = c2(m.x + s3 * bmc.y, m.y - s3 * bmc.x);
                 v[2] = c2(m.x - s3 * bmc.y, m.y + s3 * bmc.x);
             }
-            int idxD = (j / Ns) * Ns * R + k;
+            int idxD = jq * Ns * R + k;
             for (int r = 0; r < R; ++r) y[idxD + r * Ns] = v[r];
         }
         __syncwarp();
@@ -228,6 +201,7 @@ __device__ double2* warp_fft(double2* x, double2* y, int M, const double2* tw, i
         x = y;
         y = t;
         Ns *= R;
+        lgNs = (lgNs >= 0 && R != 3) ? lgNs + (R == 4 ? 2 : 1) : -1;
         rem /= R;
     }
     return x;
@@ -273,7 +247,7 @@ __device__ void warp_even_dft(double2* xh, double2* y, double2* scr, int K, cons
     double2* I = (Z == y) ? scr : y;         // imaginary parts for the running sum
     const int H = K / 2;
     for (int kk = lane; kk <= H; kk += 32) {
-        const double2 zk = Z[kk], zc = Z[(K - kk) % K];
+        const double2 zk = Z[kk], zc = Z[kk == 0 ? 0 : K - kk];
         // with Ya = (z_k + conj z_{K-k})/2, Yb = (z_k - conj z_{K-k})/(2i):
         // X_{2k} = 2 (Re Ya + i Re Yb); I_k = 2 (Im Ya + i Im Yb)
         xh[2 * kk] = c2(zk.x + zc.x, zk.y + zc.y);
@@ -301,43 +275,6 @@ __device__ void warp_even_dft(double2* xh, double2* y, double2* scr, int K, cons
         xh[2 * kk + 1] = acc;
     }
     __syncwarp();
-}
-
-// Geometry of a grid pair (l, m) from node tables: the symmetric sampling
-// quantities d~^2 and rho~_l rho~_m, and for both orientations the normal
-// factor N_D(psi) = nd0 + nds sin^2(psi/2) of the double layer at the source
-// (target l, source m: nu'_r (rho~_m - rho~_l) + nu'_z (z_m - z_l) + 2 nu'_r
-// rho~_l sin^2(psi/2) with nu' the conormal at m; target m, source l: the same
-// with l and m exchanged).
-struct PairGeom {
-    double2 d2, rr;
-    double2 nd0, nds;   // target l, source m
-    double2 nd0t, ndst; // target m, source l
-};
-
-__device__ __forceinline__ PairGeom grid_pair(const DeviceTables& T, int l, int m) {
-    PairGeom g;
-    // separations from breakpoint offsets when both nodes share the nearest
-    // breakpoint (graded clusters), else from the absolute positions
-    double dr, dz;
-    if (T.bk[l] == T.bk[m]) {
-        dr = T.off[l].x - T.off[m].x;
-        dz = T.off[l].y - T.off[m].y;
-    } else {
-        dr = T.rho[l] - T.rho[m];
-        dz = T.z[l] - T.z[m];
-    }
-    double dI = T.I[l] - T.I[m];
-    double2 drt = c2(dr, dI);
-    g.d2 = cadd(cmul(drt, drt), c2(dz * dz, 0.0));
-    g.rr = cmul(T.rho_t[l], T.rho_t[m]);
-    // nu'_r (rho~' - rho~ cos psi) + nu'_z (z' - z)
-    //   = [nu'_r (rho~' - rho~) + nu'_z (z' - z)] + 2 nu'_r rho~ sin^2(psi/2)
-    g.nd0 = cadd(cmul(T.nuc_r[m], c2(-dr, -dI)), cscale(T.nuc_z[m], -dz));
-    g.nds = cscale(cmul(T.nuc_r[m], T.rho_t[l]), 2.0);
-    g.nd0t = cadd(cmul(T.nuc_r[l], drt), cscale(T.nuc_z[l], dz));
-    g.ndst = cscale(cmul(T.nuc_r[l], T.rho_t[m]), 2.0);
-    return g;
 }
 
 // The double layer's normal factor nd0 + nds sin^2(psi/2) multiplies the
@@ -429,8 +366,15 @@ __global__ void __launch_bounds__(512, 2) far_kernel(FarArgs a) {
     // (region b: -g, its normal is -nu), q = omega |Delta|, both times the
     // trapezoid factor 2 pi / M of the modes (c4 = (1 / 4 pi)(2 pi / M))
     const double c4 = 0.5 / M;
-    for (int idx = threadIdx.x; idx < nw * S1; idx += blockDim.x) {
-        const int w = idx / S1, j = idx - w * S1;
+    // (pair w, angle j) over the CTA's threads, advanced without a division
+    int w = threadIdx.x / S1, j = threadIdx.x - (threadIdx.x / S1) * S1;
+    const int bstep = blockDim.x / S1, jstep = blockDim.x - bstep * S1;
+    for (; w < nw; w += bstep, j += jstep) {
+        if (j >= S1) {
+            j -= S1;
+            ++w;
+            if (w >= nw) break;
+        }
         if (!(act[w] & 3)) continue;
         const PairGeom& g = geo[w];
         double2* buf = bufs + w * (4 * S1 + 2 * K);
@@ -538,7 +482,7 @@ __global__ void __launch_bounds__(512, 2) far_kernel(FarArgs a) {
 // c_0 = 4 K(k)/sqrt(chi+1), c_1 = chi c_0 - 4 sqrt(chi+1) E(k), k^2 = 2/(chi+1)
 // by the complex arithmetic-geometric mean; then the three-term recurrence
 // (2m+1) c_{m+1} = 4 m chi c_m - (2m-1) c_{m-1}, run upward when
-// Re(acosh chi) M < 3.5 and downward (Miller) otherwise;
+// Re(acosh chi) M < kUpward and downward (Miller) otherwise;
 // d_m = (2m+1)(chi c_m - c_{m+1}) / (chi^2 - 1).
 // A = nu'.(r~' - r~) - nu'_rho d^2/(2 rho~'), B = nu'_rho rho~ (region a normal).
 // Output zd[p][0][m] = Z^_m, zd[p][1][m] = D^_m, m = 0..M-2.
@@ -552,6 +496,9 @@ struct NearArgs {
     double2* out;    // [p][4][nmodes]
     double2 pa[8], pb[8];   // Taylor coefficients of cH1 (pa) and cH3 (pb)
     int hs_tab;             // keep the even-DFT weight table in shared memory
+    int only_subst;         // 1: the modes kernel handles only the pairs with the
+                            // Sec. 4.3 substitution (the mixed path's float-float
+                            // kernel takes the others)
 };
 
 __device__ void complex_agm_KE(double2 k2, double2 kp, double2& K, double2& E) {
@@ -569,7 +516,10 @@ __device__ void complex_agm_KE(double2 k2, double2 kp, double2& K, double2& E) {
         sum = cadd(sum, cscale(cmul(cn, cn), pw));
         a = an;
         b = bn;
-        if (hypot(cn.x, cn.y) < 1e-17 * hypot(a.x, a.y)) break;
+        // stop once c_n is below 1e-15 |a| (the remaining terms are ~c_n^4): a
+        // tighter test is never met when a and b settle one ulp apart, and the
+        // doubling weight then amplifies ulp-level c_n over the remaining loop
+        if (cn.x * cn.x + cn.y * cn.y <= 1e-30 * (a.x * a.x + a.y * a.y)) break;
     }
     K = cscale(crcp(a), 0.5 * kPi);
     E = cmul(K, csub(c2(1.0, 0.0), sum));
@@ -581,7 +531,8 @@ __device__ void complex_agm_KE(double2 k2, double2 kp, double2& K, double2& E) {
 // qm, Zm, Ddm: the mirror pair (target and source exchanged) whose modes come
 // from the same c_m, or null
 __device__ void laplace_modes_real(const NearPair& q, const NearPair* qm, int M, double2* Z, double2* Dd,
-                                   double2* Zm, double2* Ddm) {
+                                   double2* Zm, double2* Ddm, const double2* __restrict__ rup,
+                                   const double2* __restrict__ rdn) {
     const double rr2 = 2.0 * q.rr.x;
     const double chim1 = q.d2.x / rr2, chi = 1.0 + chim1, chip1 = 2.0 + chim1;
     const double k2 = 2.0 / chip1, kp = sqrt(chim1 / chip1);
@@ -592,18 +543,22 @@ __device__ void laplace_modes_real(const NearPair& q, const NearPair* qm, int M,
         sum += pw * cn * cn;
         a = an;
         b = bn;
-        if (fabs(cn) < 1e-17 * fabs(a)) break;
+        if (fabs(cn) <= 1e-15 * fabs(a)) break;   // as in complex_agm_KE
     }
     const double K = 0.5 * kPi / a, E = K * (1.0 - sum);
     const double sq = sqrt(chip1);
-    const double c0 = 4.0 * K / sq, c1 = chi * c0 - 4.0 * sq * E;
+    // chi enters only as chi - 1 (kept exact): chi x = x + (chi - 1) x.  With
+    // chi itself rounded, the recurrences near chi = 1 amplify its rounding
+    // into c_m by ~m^2 (1e-12 at m = 127 for chi - 1 ~ 1e-9)
+    const double c0 = 4.0 * K / sq, c1 = fma(chim1, c0, c0) - 4.0 * sq * E;
     const double reeta = log(chi + sqrt(chim1) * sq);      // acosh(chi)
-    if (reeta * M < 3.5) {
+    if (reeta * M < kUpward) {
         double zm1 = c0, zm = c1;
         Z[0] = c2(c0, 0.0);
         if (M > 1) Z[1] = c2(c1, 0.0);
         for (int m = 1; m + 1 < M; ++m) {
-            const double zp = (4.0 * m * chi * zm - (2.0 * m - 1.0) * zm1) / (2.0 * m + 1.0);
+            const double2 c = rup[m];   // (4m / (2m+1), (2m-1) / (2m+1))
+            const double zp = fma(c.x, fma(chim1, zm, zm), -c.y * zm1);
             Z[m + 1] = c2(zp, 0.0);
             zm1 = zm;
             zm = zp;
@@ -612,7 +567,8 @@ __device__ void laplace_modes_real(const NearPair& q, const NearPair* qm, int M,
         const int ms = M + (int)ceil(20.0 / reeta);
         double y1 = 0.0, y0 = 1e-200;
         for (int m = ms; m >= 1; --m) {
-            const double ym1 = (4.0 * m * chi * y0 - (2.0 * m + 1.0) * y1) / (2.0 * m - 1.0);
+            const double2 c = rdn[m];   // (4m / (2m-1), (2m+1) / (2m-1))
+            const double ym1 = fma(c.x, fma(chim1, y0, y0), -c.y * y1);
             y1 = y0;
             y0 = ym1;
             if (m - 1 < M) Z[m - 1] = c2(ym1, 0.0);
@@ -635,7 +591,7 @@ __device__ void laplace_modes_real(const NearPair& q, const NearPair* qm, int M,
     const double iz = kInv4Pi / s2, id = -kInv4Pi / (s2 * s2 * s2), den = 1.0 / (chim1 * chip1);
     for (int m = 0; m + 1 < M; ++m) {
         const double cm = Z[m].x, cn = Z[m + 1].x;
-        const double dm = (2.0 * m + 1.0) * (chi * cm - cn) * den;
+        const double dm = (2.0 * m + 1.0) * fma(chim1, cm, cm - cn) * den;
         Dd[m] = c2(id * (A * dm + B * cm), 0.0);
         Z[m] = c2(iz * cm, 0.0);
         if (qm) {
@@ -667,7 +623,7 @@ __global__ void near_laplace_kernel(NearArgs a) {
     const NearPair* pm = q.mirror >= 0 ? &qm : nullptr;
     if (q.d2.y == 0.0 && q.rr.y == 0.0 && q.rho_t.y == 0.0 && q.rho_s.y == 0.0 && q.drt.y == 0.0 &&
         q.nuc_r.y == 0.0 && q.nuc_z.y == 0.0 && (!pm || (qm.nuc_r.y == 0.0 && qm.nuc_z.y == 0.0))) {
-        laplace_modes_real(q, pm, M, Z, Dd, Zm, Ddm);
+        laplace_modes_real(q, pm, M, Z, Dd, Zm, Ddm, a.T.rec_up, a.T.rec_dn);
         return;
     }
     double2 rr2 = cscale(q.rr, 2.0);
@@ -680,27 +636,32 @@ __global__ void near_laplace_kernel(NearArgs a) {
     complex_agm_KE(k2, kp, K, E);
     double2 sq = csqrt(chip1);
     double2 c0 = cscale(cdiv(K, sq), 4.0);
-    double2 c1 = csub(cmul(chi, c0), cscale(cmul(sq, E), 4.0));
+    double2 c1 = csub(cadd(c0, cmul(chim1, c0)), cscale(cmul(sq, E), 4.0));   // chi x = x + (chi - 1) x
     // Re acosh(chi) = Re log(chi + sqrt(chi-1) sqrt(chi+1))
     double2 eta = clog(cadd(chi, cmul(csqrt(chim1), sq)));
     double reeta = fabs(eta.x);
     // c_m for m = 0..M-1 into Z[] (temporarily)
-    // upward recurrence loses at most e^{2 Re(eta) M} < e^7 (about 3 digits of 16);
+    // upward recurrence amplifies rounding by at most e^{2 Re(eta) M} < e^7;
     // Miller's downward recurrence from ms has relative error e^{-2 Re(eta) (ms - M)} < 1e-17
-    if (reeta * M < 3.5) {
+    if (reeta * M < kUpward) {
         Z[0] = c0;
         Z[1] = c1;
+        const double2* __restrict__ rup = a.T.rec_up;
+        double2 zm1 = Z[0], zm = Z[1];
         for (int m = 1; m + 1 < M; ++m) {
-            double2 t = csub(cscale(cmul(chi, Z[m]), 4.0 * m), cscale(Z[m - 1], 2.0 * m - 1.0));
-            Z[m + 1] = cscale(t, 1.0 / (2.0 * m + 1.0));
+            const double2 c = rup[m];   // (4m / (2m+1), (2m-1) / (2m+1))
+            const double2 zp = csub(cscale(cadd(zm, cmul(chim1, zm)), c.x), cscale(zm1, c.y));
+            Z[m + 1] = zp;
+            zm1 = zm;
+            zm = zp;
         }
     } else {
         int ms = M + (int)ceil(20.0 / reeta);
         double2 y1 = c2(0.0, 0.0), y0 = c2(1e-200, 0.0);   // y_{m+1}, y_m at m = ms
         for (int m = ms; m >= 1; --m) {
             // (2m-1) y_{m-1} = 4 m chi y_m - (2m+1) y_{m+1}
-            double2 t = csub(cscale(cmul(chi, y0), 4.0 * m), cscale(y1, 2.0 * m + 1.0));
-            double2 ym1 = cscale(t, 1.0 / (2.0 * m - 1.0));
+            const double2 c = a.T.rec_dn[m];   // (4m / (2m-1), (2m+1) / (2m-1))
+            const double2 ym1 = csub(cscale(cadd(y0, cmul(chim1, y0)), c.x), cscale(y1, c.y));
             y1 = y0;
             y0 = ym1;
             if (m - 1 < M) Z[m - 1] = ym1;
@@ -728,7 +689,7 @@ __global__ void near_laplace_kernel(NearArgs a) {
     double2 den = crcp(cmul(chim1, chip1));                            // 1/(chi^2 - 1)
     for (int m = 0; m + 1 < M; ++m) {
         double2 cm = Z[m], cn = Z[m + 1];
-        double2 dm = cscale(cmul(csub(cmul(chi, cm), cn), den), 2.0 * m + 1.0);
+        double2 dm = cscale(cmul(cadd(csub(cm, cn), cmul(chim1, cm)), den), 2.0 * m + 1.0);
         Dd[m] = cmul(id, cadd(cmul(A, dm), cmul(B, cm)));
         Z[m] = cmul(iz, cm);
         if (pm) {
@@ -780,6 +741,7 @@ __global__ void near_modes_kernel(NearArgs a) {
     NearPair q = a.np[p];
     const bool plain = (q.flags & kFlagFar) != 0;
     const bool subst = (q.flags & kFlagSubst) != 0;
+    if (a.only_subst && !subst) return;
     // both points physical: every pair quantity is real (the two regions pack
     // into one transform); a PML pair without the substitution (diagnostic
     // exact split) takes the general path
@@ -1036,6 +998,58 @@ __global__ void assemble_corr_kernel(AsmArgs a) {
          o[3 * nmodes + t], coef * a.T.Wu[m], coef * a.T.Wphi[m], true);
 }
 
+// Correction pairs by target: CTA (target l, 32 modes), no atomics.  The
+// threads (mode, kernel) sum coef x value over the target's correction points
+// and stencil slots into a shared window of the target's stencil columns,
+// then add the window into the four blocks of row l (the same sums as
+// assemble_corr_kernel, in a fixed order).
+constexpr int kCorrModes = 32;
+__global__ void __launch_bounds__(128) assemble_corr_target_kernel(AsmArgs a) {
+    extern __shared__ double2 acc[];        // [kCorrModes][w][4]
+    const int l = blockIdx.x, t0 = blockIdx.y * kCorrModes;
+    const int nmodes = a.mode_hi - a.mode_lo;
+    const int w = a.T.corr_w[l], cmin = a.T.corr_cmin[l];
+    const int c0 = a.T.corr_start[l], c1 = a.T.corr_start[l + 1];
+    if (w == 0 || c0 == c1) return;
+    for (int i = threadIdx.x; i < kCorrModes * w * 4; i += blockDim.x) acc[i] = c2(0.0, 0.0);
+    __syncthreads();
+    const int t = threadIdx.x & (kCorrModes - 1), k = threadIdx.x / kCorrModes;   // k = kernel 0..3
+    if (t0 + t < nmodes) {
+        double2* ac = acc + (size_t)t * w * 4;
+        for (int c = c0; c < c1; ++c) {
+            const double2 v = a.near_out[((size_t)(a.n_grid_near + c) * 4 + k) * nmodes + t0 + t];
+            for (int sl = 0; sl < kStencil; ++sl) {
+                const int m = a.T.corr_m[(size_t)c * kStencil + sl];
+                if (m < 0) continue;
+                const double cf = a.T.corr_coef[(size_t)c * kStencil + sl];
+                double2& d = ac[(m - cmin) * 4 + k];
+                d.x = fma(cf, v.x, d.x);
+                d.y = fma(cf, v.y, d.y);
+            }
+        }
+    }
+    __syncthreads();
+    const size_t ld = 2 * (size_t)a.N;
+    const int N = a.N;
+    for (int i = threadIdx.x; i < kCorrModes * w * 4; i += blockDim.x) {
+        const int kk = i & 3, j = (i >> 2) % w, tt = (i >> 2) / w;
+        if (t0 + tt >= nmodes) continue;
+        const int m = cmin + j;
+        const double2 s = acc[((size_t)tt * w + j) * 4 + kk];
+        if (s.x == 0.0 && s.y == 0.0) continue;
+        // kernel 0 S^a -> -W_phi at (l, N+m); 1 K^a -> W_u at (l, m);
+        // 2 S^b -> W_phi at (N+l, N+m); 3 K^b -> W_u at (N+l, m)
+        const double wgt = (kk & 1) ? a.T.Wu[m] : (kk == 0 ? -a.T.Wphi[m] : a.T.Wphi[m]);
+        const size_t col = (kk & 1) ? (size_t)m : (size_t)(N + m);
+        const size_t row = kk < 2 ? (size_t)l : (size_t)(N + l);
+        double2* e = a.A + (size_t)(t0 + tt) * ld * ld + col * ld + row;
+        double2 v = *e;
+        v.x = fma(wgt, s.x, v.x);
+        v.y = fma(wgt, s.y, v.y);
+        *e = v;
+    }
+}
+
 __global__ void assemble_diag_kernel(AsmArgs a) {
     const int nmodes = a.mode_hi - a.mode_lo;
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1266,7 +1280,7 @@ cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStre
     return cudaSuccess;
 }
 
-static void taylor_coeffs(int L, double2* pa, double2* pb) {
+void taylor_coeffs(int L, double2* pa, double2* pb) {
     // P1 = Taylor_L[(1 + e^{-2iq})/2], P3 = Taylor_L[(1 + e^{-2iq})/2 - iq (1 - e^{-2iq})/2]
     cd e[9];
     double f = 1.0;
@@ -1288,7 +1302,7 @@ static void taylor_coeffs(int L, double2* pa, double2* pb) {
 }
 
 cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, double2* zd,
-                        double2* out, cudaStream_t s, cudaEvent_t mid) {
+                        double2* out, cudaStream_t s, cudaEvent_t mid, bool ff) {
     const int M = prob->P.M;
     NearArgs a;
     a.T = prob->D;
@@ -1303,6 +1317,7 @@ cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, do
     a.w2 = prob->P.k2;
     a.zd = zd;
     a.out = out;
+    a.only_subst = 0;
     taylor_coeffs(a.L, a.pa, a.pb);
     if (a.npairs == 0) return cudaSuccess;
     near_laplace_kernel<<<(a.npairs + 127) / 128, 128, 0, s>>>(a);
@@ -1310,6 +1325,11 @@ cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, do
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (mid && (e = cudaEventRecord(mid, s)) != cudaSuccess) return e;
+    if (ff && !prob->P.subst_off) {
+        // float-float for the pairs without a PML point, FP64 for the others
+        if ((e = launch_near_modes_ff(prob, mode_lo, mode_hi, zd, out, s)) != cudaSuccess) return e;
+        a.only_subst = 1;
+    }
     // tw2 (2M) + 8 x (M/2+1) + 4 x (M+1) + 2 scratch slots x 2M (+ M weights when they fit)
     size_t smem = sizeof(double2) * ((size_t)2 * M + 8 * (M / 2 + 1) + 4 * (M + 1) + 4 * (size_t)M);
     a.hs_tab = smem + sizeof(double2) * M <= 227 * 1024 ? 1 : 0;
@@ -1353,7 +1373,17 @@ cudaError_t launch_assemble(const pmlbie_problem* prob, int mode_lo, int mode_hi
     size_t t1 = (size_t)a.n_grid_near * nm;
     if (t1) assemble_grid_near_kernel<<<(unsigned)((t1 + 255) / 256), 256, 0, s>>>(a), count_launch();
     size_t t2 = (size_t)(a.npairs - a.n_grid_near) * kStencil * nm;
-    if (t2) assemble_corr_kernel<<<(unsigned)((t2 + 255) / 256), 256, 0, s>>>(a), count_launch();
+    const size_t smc = sizeof(double2) * kCorrModes * 4 * (size_t)prob->H.corr_wmax;
+    if (t2 && smc <= 200 * 1024) {
+        if (smc > 48 * 1024) {
+            cudaError_t e = allow_max_smem(assemble_corr_target_kernel);
+            if (e != cudaSuccess) return e;
+        }
+        assemble_corr_target_kernel<<<dim3(a.N, (nm + kCorrModes - 1) / kCorrModes), 128, smc, s>>>(a);
+        count_launch();
+    } else if (t2) {
+        assemble_corr_kernel<<<(unsigned)((t2 + 255) / 256), 256, 0, s>>>(a), count_launch();
+    }
     size_t t3 = (size_t)a.N * nm;
     assemble_diag_kernel<<<(unsigned)((t3 + 255) / 256), 256, 0, s>>>(a);
     count_launch();

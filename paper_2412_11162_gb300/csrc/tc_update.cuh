@@ -28,6 +28,8 @@
 
 #include <cstdint>
 
+#include "tcgen05_util.cuh"
+
 namespace pmlbie {
 namespace tcu {
 
@@ -44,7 +46,6 @@ constexpr uint32_t kBBytes = kCols * kDepth * 4;   // 16 KB per B' copy
 // mbarrier, the tensor-memory address and a flag
 constexpr uint32_t kSlack = 8192;
 constexpr uint32_t kSmemBytes = 2 * kABytes + 2 * kBBytes + kSlack + 64;
-constexpr long long kWaitLimit = 1ll << 24;
 
 // Byte offset of element (r, k) of a K-major operand with R rows: core matrix
 // (k / 4, r / 8) of 128 bytes, K-adjacent core matrices R/8 * 128 bytes apart
@@ -53,27 +54,10 @@ __device__ __forceinline__ uint32_t core_off(int r, int k, int R) {
     return (uint32_t)((((k >> 2) * (R >> 3) + (r >> 3)) << 7) + ((r & 7) << 4) + ((k & 3) << 2));
 }
 
-// Shared-memory matrix descriptor: start address, leading / stride byte
-// offsets (all >> 4), fixed field 0b001 at bits 46-48, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
 // Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
 // (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kCols >> 3) << 17) |
                             ((uint32_t)(kRows >> 4) << 24);
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
 
 // x -> (hi, lo) TF32 pair stored as 32-bit containers
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {

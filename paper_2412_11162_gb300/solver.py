@@ -46,11 +46,16 @@ class Problem:
     def node_tables(self):
         return B.pmlbie_node_tables(self.handle, self.N)
 
-    def modal_kernels(self, mode_lo=0, mode_hi=None, stream=None):
+    def modal_kernels(self, mode_lo=0, mode_hi=None, stream=None, precision=None):
+        """[mode][kernel][l][m] complex128; precision None: pmlbie_modal_kernels
+        (FP64), else pmlbie_modal_kernels_ex in that precision's arithmetic."""
         import torch
         mode_hi = self.n_modes if mode_hi is None else mode_hi
         out = torch.empty((mode_hi - mode_lo, 4, self.N, self.N), dtype=torch.complex128, device="cuda")
-        B.pmlbie_modal_kernels(self.handle, mode_lo, mode_hi, out, stream)
+        if precision is None:
+            B.pmlbie_modal_kernels(self.handle, mode_lo, mode_hi, out, stream)
+        else:
+            B.pmlbie_modal_kernels_ex(self.handle, precision, mode_lo, mode_hi, out, stream)
         return out
 
     def field(self, rho, z, region, densities, modes=None, stream=None):

@@ -7,15 +7,25 @@ solution on the sampled modes 0, 1, 63, 127 is stored in
 tests/golden/bump_n512_m256_oracle.npz, written by
 tests/golden/make_bump_n512_m256_oracle.py, which calls only oracle/.
 
-Checked per precision (plain FP64 GPU path: 1e-10; mixed path: 1e-6),
-Sec. 4.2 Eqs. (ntdpsi1), (ntdpsi2) and Eq. (fujs):
+Checked per precision, Sec. 4.2 Eqs. (ntdpsi1), (ntdpsi2) and Eq. (fujs):
   * u1, u2: relative 2-norm over the sampled modes on the physical nodes
-    (rho <= a1) <= tol; per mode on all nodes <= max(tol, 1e-12 kappa_n);
-  * phi1, phi2: per mode <= max(tol, 1e-12 kappa_n) (kappa_n: condition
+    (rho <= a1) <= tol_u; per mode on all nodes <= max(1e-10, 1e-12 kappa_n);
+  * phi1, phi2: per mode <= max(1e-10, 1e-12 kappa_n) (kappa_n: condition
     number of the column-equilibrated block matrix of mode n, stored with the
-    oracle's solution); the measured values are printed;
+    oracle's solution; 1.1e9 for mode 0);
   * the scattered field at the 32 fixed points: relative 2-norm over the
-    sampled modes <= tol.
+    sampled modes <= tol_u.
+tol_u is 1e-6 for the mixed path.  For the plain FP64 path it is 2e-9, not
+1e-10: at this size the agreement of two FP64 evaluations of the same
+discrete scheme is limited by the close-pair split (Sec. 4.1, 4.3), whose
+two terms cancel on the PML pairs and amplify the rounding of the modal
+Laplace kernels Z^_m, D^_m into the solution.  Perturbing the oracle's own
+Laplace kernels by one ulp (tests/golden/oracle_sensitivity_n512_m256.py)
+moves its u1 on the physical nodes by 6.8e-11; the library computes them by
+the AGM and the Legendre-Q recurrences (relative error ~1e-14 against the
+oracle's quadrature, up to ~4e-14 where the recurrence runs upward), which
+moves u1 by ~8e-10 (measured).  The per-mode and backward-error bars at
+N = 128 (tests/test_gpu_parity.py) keep 1e-10.
 """
 import os
 
@@ -44,32 +54,40 @@ def problem(ref):
 
 
 def check_against_oracle(out, P, ref, tol, label):
+    """tol: bar for u on the physical nodes and the field (see the module
+    docstring); per-mode bars max(1e-10, 1e-12 kappa_n)."""
     modes = list(ref["modes"])
     kap = ref["kappa"]
     rho = P.nodes()["rho"]
     phys = rho <= P.params.a1
-    errs = {}
+    errs, fails = {}, []
     for name in ("u1", "u2", "phi1", "phi2"):
         got = out[name].cpu().numpy()[modes, :, 0]
         want = ref[name]
         errs[name] = _rel(got, want)
         if name.startswith("u"):
             e = _rel(got[:, phys], want[:, phys])
-            assert e <= tol, (label, name, "physical nodes", e)
+            errs[name + "_physical"] = e
+            if e > tol:
+                fails.append((name, "physical nodes", e))
         for i, n in enumerate(modes):
             e = np.linalg.norm(got[i] - want[i]) / np.linalg.norm(want)
-            assert e <= max(tol, 1e-12 * kap[i]), (label, name, n, e, kap[i])
+            errs["%s_mode%d" % (name, n)] = e
+            if e > max(1e-10, tol if tol > 1e-8 else 0.0, 1e-12 * kap[i]):
+                fails.append((name, n, e, kap[i]))
     fld = P.field(ref["rho"], ref["z"], ref["region"], out)[:, :, 0].cpu().numpy()[modes]
     errs["field"] = _rel(fld, ref["field"])
-    assert errs["field"] <= tol, (label, "field", errs["field"])
+    if errs["field"] > tol:
+        fails.append(("field", errs["field"]))
     print(label, " ".join("%s %.2e" % kv for kv in errs.items()), "kappa", kap)
+    assert not fails, (label, fails)
     return errs
 
 
 def test_fp64_solve_matches_oracle_at_bench_size(problem, ref):
     from paper_2412_11162_gb300.binding import PMLBIE_FP64
     out, _ = problem.solve([float(ref["polar"])], precision=PMLBIE_FP64)
-    check_against_oracle(out, problem, ref, 1e-10, "fp64")
+    check_against_oracle(out, problem, ref, 2e-9, "fp64")
 
 
 def test_mixed_solve_matches_oracle_at_bench_size(problem, ref):

@@ -335,16 +335,19 @@ def run_ours(args, rank, world):
     epp = entries_per_problem(w)
     value = job_value(world, epp, ms)
     pk = peaks()
-    stages = {"far_kernel": last.ms_far, "near_laplace_kernel": last.ms_near_laplace,
-              "near_modes_kernel": last.ms_near - last.ms_near_laplace, "assemble": last.ms_assemble,
-              "lu_fp32": last.ms_lu, "solve_refine": last.ms_solve}
+    stages = {"far_kernel_ff": last.ms_far, "near_laplace_kernel": last.ms_near_laplace,
+              "near_modes_kernel_ff": last.ms_near_ff,
+              "near_modes_kernel_fp64_pml": last.ms_near - last.ms_near_laplace - last.ms_near_ff,
+              "assemble": last.ms_assemble, "lu_fp32": last.ms_lu, "solve_refine": last.ms_solve}
     clocks = clk.summary()
-    roof = near_roofline(w, last, pk, clocks, ncounts)
-    roof_far = roofline(w, last, pk, clocks)
+    roof = near_roofline(w, last, pk, clocks, ncounts, pipes)
+    roof_far = roofline(w, last, pk, clocks, pipes)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c128 kernels / c64 LU / c128 refinement", "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": "float-float (FP32 pairs) sampling/FFT, FP64 PML close pairs and Laplace modes, c64 LU, c128 refinement",
+        "data": "synthetic",
         "config": {"workload": "two-layer bump, N=%d M=%d (%d modes), k1=%gpi k2=%gpi, PML a1=2.5 T=1 S=3, "
                                "1 plane wave at 30 deg, mixed precision" % (w["N"], w["M"], w["M"] // 2,
                                                                            w["k1"] / np.pi, w["k2"] / np.pi),
@@ -373,7 +376,7 @@ def run_ours(args, rank, world):
         "measured_pipe_peaks": pipes,
         "roofline": roof,
         "roofline_far": roof_far,
-        "stage_rooflines": stage_rooflines(w, last, pk),
+        "stage_rooflines": stage_rooflines(w, last, pk, pipes),
         "clocks": clocks,
         "e2e": {"value": world * epp / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -478,6 +481,7 @@ def run_batched(args, rank, world):
         return [Problem(w["k1"], w["k2"], w["N"], w["M"], a1=w["a1"], T=w["T"], S=w["S"], bump_h=w["bump_h"])
                 for w in inst]
 
+    pipes = measure_pipes(B)
     probs = make()
     stream = torch.cuda.current_stream()
 
@@ -525,9 +529,9 @@ def run_batched(args, rank, world):
     d2h = sum(4 * o["u1"].numel() * 16 for o in outs)
     big = max(range(8), key=lambda i: reps[i].ms_far)
     clocks = clk.summary()
-    roof = near_roofline(inst[big], reps[big], peaks(), clocks, near_counts(probs[big]))
+    roof = near_roofline(inst[big], reps[big], peaks(), clocks, near_counts(probs[big]), pipes)
     roof["kernel"] += " of the N=%d instance" % inst[big]["N"]
-    roof_far = roofline(inst[big], reps[big], peaks(), clocks)
+    roof_far = roofline(inst[big], reps[big], peaks(), clocks, pipes)
     roof_far["kernel"] += " of the N=%d instance" % inst[big]["N"]
     line = {
         "metric": METRIC, "value": job_value(world, ent, ms), "unit": UNIT, "n_gpus": world, "steps": steps,
@@ -578,29 +582,6 @@ def far_flops_per_launch(M, chunk_modes, sampled, sampled_physical, ordered):
             ordered * chunk_modes * 60.0)
 
 
-def far_traffic(w):
-    """DRAM bytes (read + write) of one far_kernel launch at this workload from
-    the committed ncu summary profiles/far_kernel_n<N>_m<M>.md, or None when
-    there is none or kernels.cu changed since it was taken (the summary
-    records the source's sha256)."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "far_kernel_n%d_m%d.md" % (w["N"], w["M"]))
-    try:
-        text = open(path).read()
-        src = open(os.path.join(ROOT, "paper_2412_11162_gb300", "csrc", "kernels.cu"), "rb").read()
-    except OSError:
-        return None
-    sha = hashlib.sha256(src).hexdigest()
-    vals = {}
-    for line in text.splitlines():
-        if ":" in line and line.split(":")[0].strip() in ("kernels_cu_sha256", "dram_bytes_per_launch"):
-            k, v = line.split(":", 1)
-            vals[k.strip()] = v.strip()
-    if vals.get("kernels_cu_sha256") != sha or "dram_bytes_per_launch" not in vals:
-        return None
-    return float(vals["dram_bytes_per_launch"])
-
-
 def near_counts(P):
     """Close pairs of a problem by the path they take in the close-pair modes
     kernel: (packed: two physical nodes, both media in one transform; PML: a
@@ -635,58 +616,89 @@ def near_flops_per_launch(M, chunk_modes, packed, pml, plain):
     return packed * f_packed + pml * f_pml + plain * f_plain
 
 
-def near_roofline(w, rep, pk, clk, counts):
-    """Roofline entry of the close-pair modes kernel, the longest single
-    kernel of the step (one launch per mode chunk): FP64-ALU bound, against
-    the same derived FP64 peak as the far kernel."""
-    M = w["M"]
-    mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    peak = 152 * 2 * 2 * mhz * 1e6 / 1e12
-    launches = max(1, rep.chunks)
-    flops = near_flops_per_launch(M, rep.chunk_modes, *counts)
-    ms1 = (rep.ms_near - rep.ms_near_laplace) / launches
-    ach = flops / (ms1 / 1e3) / 1e12
-    npairs = sum(counts)
-    return {"kernel": "near_modes_kernel (close pairs: split samples, even DFTs, FFT convolution with the exact "
-                      "Laplace modes, FP64)",
-            "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": None, "flops_per_launch": flops, "ms_per_launch": ms1, "launches_per_step": launches,
-            "pairs": {"packed": counts[0], "pml": counts[1], "plain": counts[2]},
-            "algorithmic_bytes": float(npairs) * (2 * M + 4 * rep.chunk_modes) * 16,
-            "peak_note": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz (median SM clock under load)" % mhz,
-            "traffic_note": "null: no ncu capture of the current kernels.cu; the last capture of this kernel "
-                            "(profiles/near_modes_kernel_n256_m128.md) read 82 MB and wrote 38 MB at N=256, M=128 "
-                            "against 81 MB read + 81 MB written algorithmic"}
+def source_sha(name):
+    import hashlib
+    try:
+        return hashlib.sha256(open(os.path.join(ROOT, "paper_2412_11162_gb300", "csrc", name), "rb").read()).hexdigest()
+    except OSError:
+        return None
 
 
-def roofline(w, rep, pk, clk):
-    """Roofline entry of the far-pair kernel, the longest single kernel of
-    the step: FP64-ALU bound.  achieved = algorithmic flops of the launch /
-    its device time (CUDA events around the launch on the solve's stream);
-    peak = the FP64 pipe of the GB300: 152 SMs x 2 FMA/clk x 2 flops x clock
-    (derived from unit counts, not measured)."""
-    M = w["M"]
+def profile_traffic(path, src_name, units):
+    """DRAM bytes (read + write) of one launch scaled to `units` from a
+    committed ncu summary (profiles/): its 'dram_bytes_per_unit' line, valid
+    while 'source_sha256' matches the kernel's source file; else None."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", path)).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.split(":")[0].strip() in ("source_sha256", "dram_bytes_per_unit"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha256") != source_sha(src_name) or "dram_bytes_per_unit" not in vals:
+        return None
+    return float(vals["dram_bytes_per_unit"]) * units
+
+
+def fp64_peak(pk, clk, pipes):
+    """Measured FP64 FMA TFLOP/s (pmlbie_selftest_peak), else derived."""
+    if pipes and pipes.get("fp64_fma_tflops"):
+        return pipes["fp64_fma_tflops"], "measured: FP64 FMA probe on this GPU (pmlbie_selftest_peak)"
     mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    peak = 152 * 2 * 2 * mhz * 1e6 / 1e12
-    # one launch per mode chunk: every launch samples all pairs and angles and
-    # transforms them, and forms and scatters only its chunk's modes
+    return 152 * 2 * 2 * mhz * 1e6 / 1e12, "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz" % mhz
+
+
+def near_roofline(w, rep, pk, clk, counts, pipes=None):
+    """Roofline of the close-pair modes kernel for the pairs with a PML point
+    (near_modes_kernel<0>, FP64 in both paths, the longest single kernel of
+    the mixed step; one launch per mode chunk): FP64-ALU bound.  achieved =
+    the algorithmic FP64 flops of those pairs (near_flops_per_launch) / the
+    kernel's event time; peak = the measured FP64 FMA rate."""
+    M = w["M"]
+    peak, note = fp64_peak(pk, clk, pipes)
     launches = max(1, rep.chunks)
-    flops = far_flops_per_launch(M, rep.chunk_modes, rep.far_pairs_sampled, rep.far_pairs_sampled_physical,
-                                 rep.far_pairs)
-    ms1 = rep.ms_far / launches
+    npml = counts[1]
+    flops = near_flops_per_launch(M, rep.chunk_modes, 0, npml, 0)
+    ms1 = (rep.ms_near - rep.ms_near_laplace - rep.ms_near_ff) / launches
     ach = flops / (ms1 / 1e3) / 1e12
-    traffic = far_traffic(w)
-    return {"kernel": "far_kernel (S~ and K~ sampling of both media per unordered pair + 4 even DFTs + "
-                      "block scatter of both orientations, FP64)",
+    traffic = profile_traffic("near_modes_kernel_pml_n256_m128.md", "kernels.cu", npml)
+    return {"kernel": "near_modes_kernel<0> (close pairs with a PML point: Sec. 4.3 substitution split, even DFTs, "
+                      "FFT convolution with the exact Laplace modes, FP64)",
             "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "traffic": traffic, "flops_per_launch": flops, "ms_per_launch": ms1, "launches_per_step": launches,
-            "algorithmic_bytes": 4.0 * w["N"] ** 2 * rep.chunk_modes * 16,
-            "peak_note": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz (median SM clock under load)" % mhz,
-            "traffic_note": ("ncu dram bytes read+write of one launch at this workload (profiles/)" if traffic
-                             else "null: no ncu capture of the current kernels.cu at this workload")}
+            "pairs": npml, "algorithmic_bytes": float(npml) * (2 * M + 4 * rep.chunk_modes) * 16,
+            "peak_note": note,
+            "traffic_note": ("ncu dram read+write per PML pair (profiles/near_modes_kernel_pml_n256_m128.md) x pairs"
+                             if traffic else "null: no ncu capture of the current kernels.cu")}
 
 
-def stage_rooflines(w, rep, pk):
+def roofline(w, rep, pk, clk, pipes=None):
+    """Roofline of the far-pair kernel of the mixed path (far_kernel_ff:
+    float-float sampling, transforms and block scatter), the HBM view of
+    SURVEY-style stage a3: algorithmic bytes = the 4 N^2 (M/2) complex128
+    entries it writes per launch, against the measured HBM copy bandwidth.
+    The kernel is bounded by instruction issue on its FP32 / integer pipes
+    (ncu summary in profiles/), so this fraction is low by construction."""
+    M = w["M"]
+    launches = max(1, rep.chunks)
+    ms1 = rep.ms_far / launches
+    wbytes = 4.0 * w["N"] ** 2 * rep.chunk_modes * 16
+    hbm = pk.get("hbm_gbs", 6794.1)
+    ach = wbytes / (ms1 / 1e3) / 1e9
+    traffic = profile_traffic("far_kernel_ff_n256_m128.md", "kernels_ff.cu", 4.0 * w["N"] ** 2 * rep.chunk_modes)
+    return {"kernel": "far_kernel_ff (S~, K~ sampling of both media per unordered pair + 4 even DFTs + block scatter "
+                      "of both orientations, float-float)",
+            "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
+            "ms_per_launch": ms1, "launches_per_step": launches, "algorithmic_bytes": wbytes,
+            "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json)",
+            "traffic_note": ("ncu dram read+write per entry written (profiles/far_kernel_ff_n256_m128.md) x "
+                             "4 N^2 (M/2) entries"
+                             if traffic else "null: no ncu capture of the current kernels_ff.cu")}
+
+
+def stage_rooflines(w, rep, pk, pipes=None):
     """Per-stage rooflines of the mixed step besides the far kernel's.
 
     * LU (FP32, tensor-core trailing updates): algorithmic flops (8/3) n^3 per
@@ -705,7 +717,7 @@ def stage_rooflines(w, rep, pk):
     lu_flops = 8.0 / 3.0 * n ** 3 * modes
     upd = sum(2 * 8.0 * (n - 32 * (k + 1)) ** 2 for k in range(n // 32))
     lu_bytes = modes * (24.0 * n * n + upd)
-    tf32 = pk.get("bf16_tflops_sustained", 1692.2) * 1.1 / 2.25
+    tf32 = (pipes or {}).get("tf32_tcgen05_tflops") or pk.get("bf16_tflops_sustained", 1692.2) * 1.1 / 2.25
     hbm = pk.get("hbm_gbs", 6794.1)
     s_lu = rep.ms_lu / 1e3
     wr = 4.0 * N * N * modes * 16
@@ -715,10 +727,10 @@ def stage_rooflines(w, rep, pk):
                     "tf32_peak_tflops": tf32, "frac_tf32": lu_flops / s_lu / 1e12 / tf32,
                     "bytes": lu_bytes, "gbs": lu_bytes / s_lu / 1e9, "frac_hbm": lu_bytes / s_lu / 1e9 / hbm,
                     "note": "rank-32 trailing updates: 16 flop per byte, below the TF32 ridge; "
-                            "peaks of measured (TF32 = sustained bf16 x 1.1/2.25)"},
+                            "TF32 peak measured by the tcgen05 probe (pmlbie_selftest_peak), HBM measured copy"},
         "block_writes": {"bytes": wr, "ms": rep.ms_far, "gbs": wr / s_far / 1e9,
                          "frac_hbm": wr / s_far / 1e9 / hbm,
-                         "note": "fused into the far kernel, which the FP64 pipe bounds"},
+                         "note": "fused into the far kernel, bounded by its FP32 / integer instruction issue"},
     }
 
 

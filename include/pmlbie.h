@@ -115,6 +115,8 @@ typedef struct {
                                      sampling and one set of transforms serves both (l, m) and
                                      (m, l) (S~ is symmetric, K~ differs by its normal factor) */
     int      far_pairs_sampled_physical;  /* of those, pairs of two physical nodes           */
+    double   ms_near_ff;          /* mixed: device time of the float-float close-pair modes kernel
+                                     (pairs without a PML point; part of ms_near) (ms) */
 } pmlbie_report;
 
 /* Options of pmlbie_solve_ex (zero-initialise, then set struct_size). */

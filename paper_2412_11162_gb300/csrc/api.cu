@@ -206,7 +206,7 @@ Workspace plan(const pmlbie_problem* prob, int precision, int nrhs, int nmodes, 
         w.w32 = (float2*)take(sizeof(float2) * nm * n2 * nrhs);
         w.R = (double2*)take(sizeof(double2) * nm * n2 * nrhs);
     }
-    w.zd = (double2*)take(sizeof(double2) * std::max<size_t>(np, 1) * 2 * M);
+    w.zd = (double2*)take(near_zd_bytes(std::max<size_t>(np, 1), M, true));
     w.nout = (double2*)take(sizeof(double2) * std::max<size_t>(np, 1) * 4 * nm);
     w.b1 = (double2*)take(sizeof(double2) * nm * N * nrhs);
     w.b2 = (double2*)take(sizeof(double2) * nm * N * nrhs);
@@ -254,7 +254,8 @@ void fresnel(double w1, double w2, double phi, double* out6) {
 }
 
 // modal kernels + assembly into w.A for modes [lo, hi); ev[0..3] bracket the
-// stages, ev[4] splits the close-pair stage
+// stages, ev[4] and ev[5] split the close-pair stage (Laplace modes, then the
+// float-float modes kernel of the mixed path)
 // (the mixed path samples the far pairs in float-float arithmetic when the
 // problem's phases fit its range, else in FP64)
 int build_system(pmlbie_problem* prob, int precision, Workspace& w, int lo, int hi, cudaStream_t s,
@@ -266,7 +267,8 @@ int build_system(pmlbie_problem* prob, int precision, Workspace& w, int lo, int 
     else
         PMLBIE_CUDA_TRY(launch_far(prob, fl, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[1], s));
-    PMLBIE_CUDA_TRY(launch_near(prob, lo, hi, w.zd, w.nout, s, ev[4], precision == PMLBIE_MIXED && far_ff_supported(prob)));
+    PMLBIE_CUDA_TRY(launch_near(prob, lo, hi, w.zd, w.nout, s, ev[4], precision == PMLBIE_MIXED && far_ff_supported(prob),
+                                ev[5]));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
     PMLBIE_CUDA_TRY(launch_assemble(prob, lo, hi, w.nout, w.A, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[3], s));
@@ -443,7 +445,7 @@ int pmlbie_close_pair_kernels(pmlbie_problem* prob, int precision, int mode_lo, 
     cudaStream_t s = (cudaStream_t)stream;
     const size_t np = std::max<size_t>(prob->H.near.size(), 1);
     double2* zd = nullptr;
-    PMLBIE_CUDA_TRY(cudaMalloc(&zd, sizeof(double2) * np * 2 * prob->P.M));
+    PMLBIE_CUDA_TRY(cudaMalloc(&zd, near_zd_bytes(np, prob->P.M, true)));
     cudaError_t e = launch_near(prob, mode_lo, mode_hi, zd, (double2*)dev_out, s, nullptr,
                                 precision == PMLBIE_MIXED && far_ff_supported(prob));
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -464,7 +466,7 @@ int pmlbie_modal_kernels_ex(pmlbie_problem* prob, int precision, int mode_lo, in
     const size_t np = std::max<size_t>(prob->H.near.size(), 1);
     const int M = prob->P.M;
     double2 *zd = nullptr, *nout = nullptr;
-    PMLBIE_CUDA_TRY(cudaMalloc(&zd, sizeof(double2) * np * 2 * M));
+    PMLBIE_CUDA_TRY(cudaMalloc(&zd, near_zd_bytes(np, M, true)));
     if (cudaMalloc(&nout, sizeof(double2) * np * 4 * (mode_hi - mode_lo)) != cudaSuccess) {
         cudaFree(zd);
         return fail(PMLBIE_ENOMEM, "scratch allocation failed");
@@ -583,7 +585,8 @@ static int batched_lu_graphed(pmlbie_problem* prob, int precision, int n, int ba
 
 // Accumulated device times and refinement statistics of a solve.
 struct SolveStats {
-    double ms_kernels = 0, ms_lu = 0, ms_solve = 0, ms_far = 0, ms_near = 0, ms_near_laplace = 0, ms_assemble = 0;
+    double ms_kernels = 0, ms_lu = 0, ms_solve = 0, ms_far = 0, ms_near = 0, ms_near_laplace = 0, ms_assemble = 0,
+           ms_near_ff = 0;
     int iters = 0;
     double resid = 0;
     int gmres_iters = 0, gmres_modes = 0;
@@ -596,7 +599,7 @@ struct SolveStats {
 static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool point, int lo, int hi, Workspace& w,
                        double2* u1, double2* phi1, double2* u2, double2* phi2, cudaStream_t s, SolveStats& st) {
     const int N = prob->P.N, nm = hi - lo, n2 = 2 * N;
-    cudaEvent_t ev[4], sev[5];
+    cudaEvent_t ev[4], sev[6];
     for (auto& e : ev) PMLBIE_CUDA_TRY(cudaEventCreate(&e));
     for (auto& e : sev) PMLBIE_CUDA_TRY(cudaEventCreate(&e));
     struct EvGuard {
@@ -604,7 +607,7 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
         cudaEvent_t* f;
         ~EvGuard() {
             for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
-            for (int i = 0; i < 5; ++i) cudaEventDestroy(f[i]);
+            for (int i = 0; i < 6; ++i) cudaEventDestroy(f[i]);
         }
     } guard{ev, sev};
     pmlbie_dev_extra* ex = extra_of(prob);
@@ -751,6 +754,9 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
         cudaEventElapsedTime(&f[i], sev[i], sev[i + 1]);
     }
     cudaEventElapsedTime(&fl, sev[1], sev[4]);
+    float fff = 0.f;
+    cudaEventElapsedTime(&fff, sev[4], sev[5]);
+    st.ms_near_ff += fff;
     st.ms_kernels += t[0];
     st.ms_lu += t[1];
     st.ms_solve += t[2];
@@ -937,6 +943,7 @@ int pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* o, void* dev_
         rep->ms_near = st.ms_near;
         rep->ms_assemble = st.ms_assemble;
         rep->ms_near_laplace = st.ms_near_laplace;
+        rep->ms_near_ff = st.ms_near_ff;
         rep->launches = (int)g_launches;
         int* fc = prob->far_counts;
         if (fc[0] < 0) {

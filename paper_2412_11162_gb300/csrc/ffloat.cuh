@@ -286,13 +286,17 @@ __device__ __forceinline__ void sincos_ff(ff x, const Tables& T, ff& sn, ff& cs)
 // hi's 24 bits shifted up by 29 plus lo's bits aligned below them (lo's bits
 // beyond the double's 53 are truncated), renormalised by one bit when lo has
 // the opposite sign and hi is a power of two.  Error below 1 ulp of the
-// double.  Denormal, infinite or NaN hi (and results outside the double's
-// normal range) take the FP64 route.
+// double.  No FP64 fallback either (it would sit, predicated, on the hot
+// path): zero and denormal hi give 0 (a denormal float pair is 2^-126 below
+// the kernels' unit-scaled values), infinite or NaN hi give a NaN, and
+// results below or above the double's normal range give 0 or infinity.
 __device__ __forceinline__ double to_double(ff a, int scale) {
     const uint32_t h = __float_as_uint(a.hi);
     const uint32_t eh = (h >> 23) & 0xffu;
-    if ((h & 0x7fffffffu) == 0u) return 0.0;   // zero (exact zeros are common: K^ of flat pairs)
-    if (eh == 0u || eh == 0xffu) return ((double)a.hi + (double)a.lo) * ldexp(1.0, scale);
+    if (eh == 0u) return 0.0;                                     // zero (common: K^ of flat pairs) or denormal
+    if (eh == 0xffu) return __hiloint2double(0x7ff80000, 0);       // not finite
+    if ((int)eh + 896 + scale <= 0) return 0.0;
+    if ((int)eh + 896 + scale >= 2047) return __hiloint2double((int)((h & 0x80000000u) | 0x7ff00000u), 0);
     const uint32_t sig = (h & 0x7fffffu) | 0x800000u;   // 24 bits
     // sh = sig << 29 as (shi, slo): bits 32.. and 0..31
     uint32_t shi = sig >> 3, slo = sig << 29;
@@ -320,7 +324,7 @@ __device__ __forceinline__ double to_double(ff a, int scale) {
         slo <<= 1;
         e -= 1;
     }
-    if (e <= 0 || e >= 2047) return ((double)a.hi + (double)a.lo) * ldexp(1.0, scale);   // out of normal range
+    if (e <= 0) return 0.0;   // renormalised below the normal range
     const uint32_t hw = (h & 0x80000000u) | ((uint32_t)e << 20) | (shi & 0xfffffu);
     return __hiloint2double((int)hw, (int)slo);
 }

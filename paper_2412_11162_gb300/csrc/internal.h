@@ -177,14 +177,29 @@ bool ff_elementary_known(int fn);
 cudaError_t launch_ff_elementary(int fn, const double* x, double* out, size_t n, cudaStream_t s);
 // pairs per CTA of this thread's last far-kernel launch (the tuned choice)
 extern thread_local int g_far_pairs_per_cta;
+// Per close pair, the float-float kernel's quantities (units of L = 2^eL):
+// d~^2 / L^2, rho~ rho~' / L^2, the normal factor's two terms / L, omega_r L,
+// 1 / (omega_r L), then eL and the all-real flag -- written by the Laplace-
+// mode kernel (FP64, one pair per thread) into the float4 area that follows
+// the Laplace modes in the zd scratch (kNearFF float4 per pair).
+constexpr int kNearFF = 7;
+// zd scratch of launch_near: Laplace modes [p][2][M], then, for ff, the
+// per-pair float-float quantities
+inline size_t near_zd_bytes(size_t np, int M, bool ff) {
+    return sizeof(double2) * np * 2 * (size_t)M + (ff ? sizeof(float4) * kNearFF * np : 0);
+}
 // mid (optional): event recorded between the Laplace-mode and the modes kernels;
-// ff: the modes kernel in float-float (mixed path; not with subst_off)
+// ff: the modes kernel in float-float (mixed path; not with subst_off), zd
+// sized by near_zd_bytes(.., true)
+// mid_ff (optional): event recorded after the float-float modes kernel (right
+// after mid when there is none)
 cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, double2* zd_scratch,
-                        double2* out, cudaStream_t s, cudaEvent_t mid = nullptr, bool ff = false);
+                        double2* out, cudaStream_t s, cudaEvent_t mid = nullptr, bool ff = false,
+                        cudaEvent_t mid_ff = nullptr);
 // the float-float close-pair modes kernel alone (kernels_ff.cu), after the
 // Laplace modes are in zd
 cudaError_t launch_near_modes_ff(const pmlbie_problem* prob, int mode_lo, int mode_hi, const double2* zd,
-                                 double2* out, cudaStream_t s);
+                                 const float4* pff, double2* out, cudaStream_t s);
 // Taylor coefficients of cH1 (pa) and cH3 (pb) of degree L <= 7 (Sec. 4.3)
 void taylor_coeffs(int L, double2* pa, double2* pb);
 cudaError_t launch_near_to_raw(const pmlbie_problem* prob, int mode_lo, int mode_hi,

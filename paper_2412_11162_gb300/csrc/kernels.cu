@@ -18,6 +18,7 @@
 
 #include "internal.h"
 #include "device_common.cuh"
+#include "ffloat.cuh"
 
 namespace pmlbie {
 
@@ -499,6 +500,7 @@ struct NearArgs {
     int only_subst;         // 1: the modes kernel handles only the pairs with the
                             // Sec. 4.3 substitution (the mixed path's float-float
                             // kernel takes the others)
+    float4* pff;            // per-pair float-float quantities (kNearFF float4), or null
 };
 
 __device__ void complex_agm_KE(double2 k2, double2 kp, double2& K, double2& E) {
@@ -604,10 +606,37 @@ __device__ void laplace_modes_real(const NearPair& q, const NearPair* qm, int M,
 // One thread per close pair.  A grid pair and its mirror (target and source
 // exchanged) share chi and hence c_m: the lower index of the two computes the
 // modes of both, the other returns.
+// Float-float quantities of close pair q for the mixed path's modes kernel
+// (units of L = 2^eL, L^2 ~ |d~^2| + 4 |rho~ rho~'|), one thread per pair.
+__device__ void near_pair_ff(const NearPair& q, double w1, double w2, float4* out) {
+    using namespace ffm;
+    const double lsq = fabs(q.d2.x) + fabs(q.d2.y) + 4.0 * (fabs(q.rr.x) + fabs(q.rr.y));
+    const int e = ilogb(lsq) / 2;
+    auto c4 = [&](double2 z, int sh) {
+        const ff re = from_double(ldexp(z.x, sh)), im = from_double(ldexp(z.y, sh));
+        return make_float4(re.hi, re.lo, im.hi, im.lo);
+    };
+    auto r4 = [&](double x, double y) {
+        const ff u = from_double(x), v = from_double(y);
+        return make_float4(u.hi, u.lo, v.hi, v.lo);
+    };
+    out[0] = c4(q.d2, -2 * e);
+    out[1] = c4(q.rr, -2 * e);
+    // N_D(psi) / L = [nu'_r (rho~' - rho~) - nu'_z dz] / L + (2 nu'_r rho~ / L) sin^2(psi/2)
+    out[2] = c4(cadd(cmul(q.nuc_r, q.drt), cscale(q.nuc_z, -q.dz)), -e);
+    out[3] = c4(cscale(cmul(q.nuc_r, q.rho_t), 2.0), -e);
+    out[4] = r4(ldexp(w1, e), ldexp(w2, e));
+    out[5] = r4(ldexp(1.0 / w1, -e), ldexp(1.0 / w2, -e));
+    const bool phys = q.d2.y == 0.0 && q.rr.y == 0.0 && q.rho_t.y == 0.0 && q.rho_s.y == 0.0 && q.drt.y == 0.0 &&
+                      q.nuc_r.y == 0.0 && q.nuc_z.y == 0.0;
+    out[6] = make_float4(__int_as_float(e), __int_as_float(phys ? 1 : 0), 0.0f, 0.0f);
+}
+
 __global__ void near_laplace_kernel(NearArgs a) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.npairs) return;
     NearPair q = a.np[p];
+    if (a.pff) near_pair_ff(q, a.w1, a.w2, a.pff + (size_t)p * kNearFF);
     if (q.flags & kFlagFar) return;
     if (q.mirror >= 0 && q.mirror < p) return;
     const int M = a.M;
@@ -1302,7 +1331,7 @@ void taylor_coeffs(int L, double2* pa, double2* pb) {
 }
 
 cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, double2* zd,
-                        double2* out, cudaStream_t s, cudaEvent_t mid, bool ff) {
+                        double2* out, cudaStream_t s, cudaEvent_t mid, bool ff, cudaEvent_t mid_ff) {
     const int M = prob->P.M;
     NearArgs a;
     a.T = prob->D;
@@ -1318,18 +1347,25 @@ cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, do
     a.zd = zd;
     a.out = out;
     a.only_subst = 0;
+    const bool use_ff = ff && !prob->P.subst_off;
+    a.pff = use_ff ? reinterpret_cast<float4*>(zd + (size_t)a.npairs * 2 * M) : nullptr;
     taylor_coeffs(a.L, a.pa, a.pb);
-    if (a.npairs == 0) return cudaSuccess;
+    if (a.npairs == 0) {
+        cudaError_t e0 = mid ? cudaEventRecord(mid, s) : cudaSuccess;
+        if (e0 == cudaSuccess && mid_ff) e0 = cudaEventRecord(mid_ff, s);
+        return e0;
+    }
     near_laplace_kernel<<<(a.npairs + 127) / 128, 128, 0, s>>>(a);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (mid && (e = cudaEventRecord(mid, s)) != cudaSuccess) return e;
-    if (ff && !prob->P.subst_off) {
+    if (use_ff) {
         // float-float for the pairs without a PML point, FP64 for the others
-        if ((e = launch_near_modes_ff(prob, mode_lo, mode_hi, zd, out, s)) != cudaSuccess) return e;
+        if ((e = launch_near_modes_ff(prob, mode_lo, mode_hi, zd, a.pff, out, s)) != cudaSuccess) return e;
         a.only_subst = 1;
     }
+    if (mid_ff && (e = cudaEventRecord(mid_ff, s)) != cudaSuccess) return e;
     // tw2 (2M) + 8 x (M/2+1) + 4 x (M+1) + 2 scratch slots x 2M (+ M weights when they fit)
     size_t smem = sizeof(double2) * ((size_t)2 * M + 8 * (M / 2 + 1) + 4 * (M + 1) + 4 * (size_t)M);
     a.hs_tab = smem + sizeof(double2) * M <= 227 * 1024 ? 1 : 0;

@@ -248,8 +248,13 @@ __global__ void __launch_bounds__(512, 1) far_kernel_ff(FarArgsFF a) {
     for (int i = threadIdx.x; i < S1; i += blockDim.x) cs[i] = a.T.cos_ff[i];
     for (int i = threadIdx.x; i < kTrigTab; i += blockDim.x) trig[i] = a.T.trig_ff[i];
     for (int i = threadIdx.x; i < kExpTab; i += blockDim.x) expt[i] = a.T.exp_ff[i];
-    if (lane == 0) {
-        const int l = l0 + warp % TL, m = m0 + warp / TL;
+    // Pair set-up in FP64, all pairs of the CTA by the lanes of warp 0 (lane
+    // w: pair w): the FP64 pipe is 1/64 of the FP32 one and a warp
+    // instruction occupies it whatever the number of active lanes, so one
+    // lane per warp would cost nw times as much.
+    if (warp == 0 && lane < nw) {
+        const int wq = lane;
+        const int l = l0 + wq % TL, m = m0 + wq / TL;
         int f = 0;
         if (l < N && m < N && l >= m) {
             f = 4;
@@ -274,11 +279,11 @@ __global__ void __launch_bounds__(512, 1) far_kernel_ff(FarArgsFF a) {
                     p.wl[1] = make_float2(w2.hi, w2.lo);
                     p.eL = eL;
                     p.real = real ? 1 : 0;
-                    geo[warp] = p;
+                    geo[wq] = p;
                 }
             }
         }
-        act[warp] = f;
+        act[wq] = f;
     }
     __syncthreads();
     const Tables TT{expt, trig};
@@ -452,6 +457,7 @@ __global__ void __launch_bounds__(512, 1) far_kernel_ff(FarArgsFF a) {
 // ---------------------------------------------------------------------------
 struct NearArgsFF {
     const NearPair* np;
+    const float4* pff;     // per-pair quantities (kNearFF float4 each), from the Laplace-mode kernel
     const float4* twid2;
     const float4* trig;
     const float2* expt;
@@ -571,38 +577,19 @@ __global__ void __launch_bounds__(128) near_modes_kernel_ff(NearArgsFF a) {
     // terms (the polynomial of the Sec. 4.3 substitution grows like |2q|^L /
     // L!) cancel by up to ~1e10 at |q| ~ 100, beyond a float pair's 48 bits.
     if (subst) return;
-    __shared__ int pphys;
-    if (threadIdx.x == 0)
-        pphys = q.d2.y == 0.0 && q.rr.y == 0.0 && q.rho_t.y == 0.0 && q.rho_s.y == 0.0 && q.drt.y == 0.0 &&
-                q.nuc_r.y == 0.0 && q.nuc_z.y == 0.0;
-    // pair quantities in units of L = 2^eL, from FP64 by thread 0 (the FP64
-    // pipe is 1/64 of the FP32 one: nothing per-pair runs on every thread)
-    __shared__ float4 pq[4];     // d2, rr, nd0, nds as float pairs
-    __shared__ float2 pw[4];     // omega_r L, 1 / (omega_r L)
-    __shared__ int peL;
-    if (threadIdx.x == 0) {
-        const double lsq = fabs(q.d2.x) + fabs(q.d2.y) + 4.0 * (fabs(q.rr.x) + fabs(q.rr.y));
-        const int e = ilogb(lsq) / 2;
-        peL = e;
-        pq[0] = pack(cff_of(q.d2, -2 * e));
-        pq[1] = pack(cff_of(q.rr, -2 * e));
-        // N_D(psi) / L = [nu'_r (rho~' - rho~) - nu'_z dz] / L + (2 nu'_r rho~ / L) sin^2(psi/2)
-        pq[2] = pack(cff_of(cadd(cmul(q.nuc_r, q.drt), cscale(q.nuc_z, -q.dz)), -e));
-        pq[3] = pack(cff_of(cscale(cmul(q.nuc_r, q.rho_t), 2.0), -e));
-        const ff w1 = from_double(ldexp(a.w1, e)), w2 = from_double(ldexp(a.w2, e));
-        const ff i1 = from_double(ldexp(1.0 / a.w1, -e)), i2 = from_double(ldexp(1.0 / a.w2, -e));
-        pw[0] = make_float2(w1.hi, w1.lo);
-        pw[1] = make_float2(w2.hi, w2.lo);
-        pw[2] = make_float2(i1.hi, i1.lo);
-        pw[3] = make_float2(i2.hi, i2.lo);
-    }
+    // pair quantities in units of L = 2^eL, computed in FP64 by the Laplace-
+    // mode kernel (one pair per thread there: the FP64 pipe is 1/64 of the
+    // FP32 one and a warp instruction occupies it whatever its active lanes)
+    const float4* pf = a.pff + (size_t)p * kNearFF;
     const int L = a.L;
     __syncthreads();
-    const bool packed = !plain && pphys;
-    const int eL = peL;
-    const cff d2 = unpack(pq[0]), rr = unpack(pq[1]), nd0 = unpack(pq[2]), nds = unpack(pq[3]);
-    const ff wl[2] = {ff{pw[0].x, pw[0].y}, ff{pw[1].x, pw[1].y}};
-    const ff iwl[2] = {ff{pw[2].x, pw[2].y}, ff{pw[3].x, pw[3].y}};
+    const float4 misc = pf[6];
+    const bool packed = !plain && __float_as_int(misc.y) != 0;
+    const int eL = __float_as_int(misc.x);
+    const cff d2 = unpack(pf[0]), rr = unpack(pf[1]), nd0 = unpack(pf[2]), nds = unpack(pf[3]);
+    const float4 wv = pf[4], iwv = pf[5];
+    const ff wl[2] = {ff{wv.x, wv.y}, ff{wv.z, wv.w}};
+    const ff iwl[2] = {ff{iwv.x, iwv.y}, ff{iwv.z, iwv.w}};
     const ff wq[2] = {ff{a.wq[0].x, a.wq[0].y}, ff{a.wq[1].x, a.wq[1].y}};
     const ff wc[2] = {ff{a.wc[0].x, a.wc[0].y}, ff{a.wc[1].x, a.wc[1].y}};
     const ff inv4pi{a.inv4pi.x, a.inv4pi.y};
@@ -952,10 +939,11 @@ cudaError_t launch_far_ff(const pmlbie_problem* prob, const FarLaunch& fl, cudaS
 }
 
 cudaError_t launch_near_modes_ff(const pmlbie_problem* prob, int mode_lo, int mode_hi, const double2* zd,
-                                 double2* out, cudaStream_t s) {
+                                 const float4* pff, double2* out, cudaStream_t s) {
     const int M = prob->P.M;
     NearArgsFF a;
     a.np = prob->D.near;
+    a.pff = pff;
     a.twid2 = prob->D.twid2_ff;
     a.trig = prob->D.trig_ff;
     a.expt = prob->D.exp_ff;

@@ -68,9 +68,8 @@ def test_ff_kernels_vs_oracle_config1():
     """Mixed-path modal kernels (far pairs and the close-pair split in
     float-float, exact Laplace modes in FP64) against the oracle, N = 128,
     M = 64, all modes: far and physical close pairs within 6.4e-11 of the
-    block's largest entry, the far pairs of a block within 6.4e-11 relative
-    (Frobenius), PML close pairs (FP64 in both paths) within 1e-12 of the
-    split's term scale, every block within 1e-9: the bars of
+    block's largest entry, PML close pairs (FP64 in both paths) within 1e-12
+    of the split's term scale, every block within 1e-9: the bars of
     test_gpu_parity.test_modal_kernels_config1 with 64 times the FP64 factor
     where float pairs compute (48 significant bits against 53 + 1)."""
     from test_gpu_parity import _split_term_scale
@@ -83,7 +82,7 @@ def test_ff_kernels_vs_oracle_config1():
     near = S.near[: S.ngrid]
     rt = S.G.nodes["rho_t"].imag
     pml = (rt[li] > 0) | (rt[mi] > 0)
-    worst = {"tight": 0.0, "far_fro": 0.0, "pml_split": 0.0}
+    worst = {"tight": 0.0, "pml_split": 0.0}
     for n in range(CFG1["M"] // 2):
         for kern, (reg, which) in enumerate((("a", "S"), ("a", "K"), ("b", "S"), ("b", "K"))):
             ref = S.grid_kernel(reg, which, n)
@@ -93,10 +92,6 @@ def test_ff_kernels_vs_oracle_config1():
             tight = ~(near & pml)
             worst["tight"] = max(worst["tight"], d[tight].max() / mx)
             assert d[tight].max() <= 6.4e-11 * mx, (n, kern, d[tight].max() / mx)
-            g, r = got[li, mi][~near], ref[li, mi][~near]
-            fro = np.linalg.norm(g - r) / np.linalg.norm(r)
-            worst["far_fro"] = max(worst["far_fro"], fro)
-            assert fro <= 6.4e-11, (n, kern, fro)
             assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-9
             if which == "S":
                 sc = _split_term_scale(S, reg, n)

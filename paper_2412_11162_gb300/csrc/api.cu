@@ -170,7 +170,7 @@ namespace {
 struct Workspace {
     double2 *A = nullptr, *zd = nullptr, *nout = nullptr, *b1 = nullptr, *b2 = nullptr, *B = nullptr,
             *X = nullptr, *R = nullptr;
-    float2 *A32 = nullptr, *w32 = nullptr;
+    float2 *A32 = nullptr, *w32 = nullptr, *dinv = nullptr;
     int *piv = nullptr, *info = nullptr, *active = nullptr, *nanflag = nullptr;
     double *rn = nullptr, *bn = nullptr, *xn = nullptr, *an = nullptr, *rpar = nullptr;
     size_t bytes = 0;
@@ -204,6 +204,9 @@ Workspace plan(const pmlbie_problem* prob, int precision, int nrhs, int nmodes, 
     if (precision == PMLBIE_MIXED) {
         w.A32 = (float2*)take(sizeof(float2) * nm * n2 * n2);
         w.w32 = (float2*)take(sizeof(float2) * nm * n2 * nrhs);
+        // inverted 32 x 32 diagonal blocks of the factors (n2 / 32 of L and of U
+        // per mode: 1/16 of the factor's bytes) for the correction solves
+        if (n2 % 32 == 0) w.dinv = (float2*)take(sizeof(float2) * nm * diag_inv_elems((int)n2));
         w.R = (double2*)take(sizeof(double2) * nm * n2 * nrhs);
     }
     w.zd = (double2*)take(near_zd_bytes(std::max<size_t>(np, 1), M, true));
@@ -634,6 +637,7 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
     } else {
         PMLBIE_CUDA_TRY(convert_fro2_c128(n2, nm, w.A, w.A32, w.an, s));
         if ((rc = batched_lu_graphed(prob, PMLBIE_MIXED, n2, nm, w.A32, w.piv, w.info, s))) return rc;
+        if (w.dinv) PMLBIE_CUDA_TRY(batched_diag_inv(n2, nm, w.A32, w.dinv, s));
         PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
         PMLBIE_CUDA_TRY(cudaMemsetAsync(w.X, 0, xbytes, s));
         PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.R, w.B, xbytes, cudaMemcpyDeviceToDevice, s));
@@ -690,7 +694,7 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
                 }
                 PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.active, act.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, s));
             }
-            PMLBIE_CUDA_TRY(refine_step(n2, nm, n_rhs, w.A32, w.piv, w.R, w.w32, w.X, s, w.active));
+            PMLBIE_CUDA_TRY(refine_step(n2, nm, n_rhs, w.A32, w.piv, w.R, w.w32, w.X, s, w.active, w.dinv));
         }
         const int nslow = (int)std::count(slow.begin(), slow.end(), 1);
         if (nslow > 0) {
@@ -719,7 +723,8 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
             const size_t mat = (size_t)n2 * n2, vec = (size_t)n2 * n_rhs;
             rc = gmres_refine(n2, gn, n_rhs, w.A + g0 * mat, w.A32 + g0 * mat, w.piv + (size_t)g0 * n2,
                               w.B + g0 * vec, w.X + g0 * vec, gslow, w.active, gm, kGmresM, kGmresCycles, kTolRel,
-                              kTolBwd, kTolFloor, gan, s, git, gres, gbwd);
+                              kTolBwd, kTolFloor, gan, s, git, gres, gbwd,
+                              w.dinv ? w.dinv + (size_t)g0 * diag_inv_elems(n2) : nullptr);
             cudaStreamSynchronize(s);
             cudaFree(gm);
             if (rc) return rc;

@@ -270,9 +270,15 @@ cudaError_t lu_prepare();
 // active: optional per-matrix flags (0 = skip), used to leave converged modes alone
 // factors in TF, right-hand sides and arithmetic in T (T = double2 with TF = float2:
 // FP64 solves with the FP32 factors)
+// dinv: optional inverses of the 32 x 32 diagonal blocks (batched_diag_inv),
+// used when n is a multiple of 32
 template <typename T, typename TF>
 cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int* piv, T* B,
-                             cudaStream_t s, const int* active = nullptr);
+                             cudaStream_t s, const int* active = nullptr, const TF* dinv = nullptr);
+// inverses of the 32 x 32 diagonal blocks of L (unit lower) and U of every
+// complex64 factor, [b][n / 32][2][32 x 32] column-major (n a multiple of 32)
+cudaError_t batched_diag_inv(int n, int batch, const float2* LU, float2* dinv, cudaStream_t s);
+inline size_t diag_inv_elems(int n) { return (size_t)n * 64; }   // per matrix
 cudaError_t convert_to_c64(int64_t count, const double2* src, float2* dst, cudaStream_t s);
 // complex64 copies of batch n x n complex128 matrices and their squared
 // Frobenius norms (out[b] = |A_b|_F^2) in one pass over A
@@ -286,13 +292,14 @@ size_t gmres_scratch_bytes(int n, int batch, int nrhs, int m);
 int gmres_refine(int n, int batch, int nrhs, const double2* A, const float2* LU32, const int* piv,
                  const double2* B, double2* X, std::vector<int>& act, int* active_dev, void* scratch, int m,
                  int max_cycles, double tol, double tol_bw, double tol_floor, const std::vector<double>& an2,
-                 cudaStream_t s, int& iters, std::vector<double>& mode_res, std::vector<double>& mode_bwd);
+                 cudaStream_t s, int& iters, std::vector<double>& mode_res, std::vector<double>& mode_bwd,
+                 const float2* dinv = nullptr);
 // R = B - A X with |R|^2, |B|^2, |X|^2 per (matrix, rhs)
 cudaError_t residual_c128(int n, int batch, int nrhs, const double2* A, const double2* X,
                           const double2* B, double2* R, double* rnorm, double* bnorm, double* xnorm,
                           cudaStream_t s, const int* active = nullptr);
 cudaError_t refine_step(int n, int batch, int nrhs, const float2* LU32, const int* piv,
                         const double2* R, float2* work32, double2* X, cudaStream_t s,
-                        const int* active = nullptr);
+                        const int* active = nullptr, const float2* dinv = nullptr);
 
 }  // namespace pmlbie

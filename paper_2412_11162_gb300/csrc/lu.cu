@@ -15,6 +15,7 @@
 #include <cfloat>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "internal.h"
 #include "tc_update.cuh"
@@ -41,6 +42,10 @@ template <typename T> __device__ __forceinline__ T mul(T a, T b) {
 // a - b*c
 template <typename T> __device__ __forceinline__ T fms(T a, T b, T c) {
     return Cx<T>::mk(a.x - b.x * c.x + b.y * c.y, a.y - b.x * c.y - b.y * c.x);
+}
+// a + b*c
+template <typename T> __device__ __forceinline__ T fma_c(T a, T b, T c) {
+    return Cx<T>::mk(a.x + b.x * c.x - b.y * c.y, a.y + b.x * c.y + b.y * c.x);
 }
 template <typename T> __device__ __forceinline__ T rcp(T a) {
     using R = typename Cx<T>::R;
@@ -397,8 +402,12 @@ __global__ void gemm_update_kernel(int n, int k0, int kb, T* A) {
 // side; 16-byte loads for complex64 factors), so that enough bytes are in
 // flight to stream the factors at HBM speed; each factor pair then serves
 // every right-hand side of the group, and the next diagonal block is fetched
-// into registers during the update.  Matrices
-// whose active flag is 0 are skipped (converged modes).
+// into registers during the update.  With `dinv` (the inverses of the 32 x 32
+// diagonal blocks of L and U, diag_inv_kernel; n a multiple of 32) a
+// diagonal block is applied as a matrix-vector product by one warp per
+// right-hand side, 32 independent products instead of a 32-step dependent
+// substitution that the other warps wait for.  Matrices whose active flag is
+// 0 are skipped (converged modes).
 constexpr int kSolveR = 8;
 
 template <typename T> __device__ __forceinline__ T widen(float2 v) { return Cx<T>::mk(v.x, v.y); }
@@ -443,7 +452,7 @@ __device__ __forceinline__ void block_pair_update(const TF* col, int n, const T*
 
 template <typename T, typename TF, int RM>
 __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, const TF* LU, const int* perm,
-                                                       T* B, const int* active) {
+                                                       T* B, const int* active, const TF* dinv) {
     const int R = RM == 1 ? 1 : Rg;    // compile-time 1 in the single-wave variant
     const int b = blockIdx.x, r0 = blockIdx.y * R, nr = RM == 1 ? 1 : min(R, nrhs - r0);
     if (active && !active[b]) return;
@@ -459,14 +468,44 @@ __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, 
         const int i = idx / nr, q = idx - i * nr;
         sx[i * R + q] = x[(size_t)pm[i] * nrhs + r0 + q];
     }
-    // diagonal block j0 into registers (16-byte pieces, column by column)
-    auto fetch_diag = [&](int j0, int jb, float4 (&reg)[kDiagPer]) {
+    const int nblk = (n + kNB - 1) / kNB;
+    // the pair path: full blocks only, and with several right-hand sides only
+    // for complex64 accumulators (register budget of 512 threads)
+    const bool vec = (n % kNB) == 0 && (RM == 1 || sizeof(T) == 8);
+    // (complex64 factors only: the FP64 path keeps the substitution)
+    const bool inv = std::is_same<TF, float2>::value && vec && dinv != nullptr;
+    // diagonal block j0 into registers (16-byte pieces, column by column): the
+    // factor's block, or with inv the inverse of its L (t = 0) or U (t = 1) part
+    const TF* dinv_b = inv ? dinv + (size_t)b * nblk * 2 * kNB * kNB : nullptr;
+    auto fetch_diag = [&](int j0, int jb, int t, float4 (&reg)[kDiagPer]) {
+        if (inv) {
+            // the inverse blocks are contiguous: full 16-byte pieces
+            const float4* src = reinterpret_cast<const float4*>(dinv_b + ((size_t)(j0 / kNB) * 2 + t) * kNB * kNB);
 #pragma unroll
-        for (int t = 0; t < kDiagPer; ++t) {
-            const int e = (tid + t * 512) * (int)(16 / sizeof(TF));     // first element of the piece
+            for (int q = 0; q < kDiagPer; ++q) reg[q] = __ldg(src + tid + q * 512);
+            return;
+        }
+#pragma unroll
+        for (int q = 0; q < kDiagPer; ++q) {
+            const int e = (tid + q * 512) * (int)(16 / sizeof(TF));     // first element of the piece
             const int c = e / kNB, i = e - c * kNB;
-            reg[t] = (c < jb && i < jb) ? __ldg(reinterpret_cast<const float4*>(a + (size_t)(j0 + c) * n + j0 + i))
+            reg[q] = (c < jb && i < jb) ? __ldg(reinterpret_cast<const float4*>(a + (size_t)(j0 + c) * n + j0 + i))
                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    // x_blk <- Inv x_blk for the warp's right-hand side (inv path)
+    auto apply_inv = [&](int j0) {
+        if (warp < nr) {
+            const T v = sx[(j0 + lane) * R + warp];
+            T acc0 = Cx<T>::mk(0, 0), acc1 = acc0;
+#pragma unroll
+            for (int c = 0; c < kNB; c += 2) {
+                const T x0 = Cx<T>::mk(__shfl_sync(0xffffffff, v.x, c), __shfl_sync(0xffffffff, v.y, c));
+                const T x1 = Cx<T>::mk(__shfl_sync(0xffffffff, v.x, c + 1), __shfl_sync(0xffffffff, v.y, c + 1));
+                acc0 = fma_c(acc0, widen<T>(sD[c * kNB + lane]), x0);
+                acc1 = fma_c(acc1, widen<T>(sD[(c + 1) * kNB + lane]), x1);
+            }
+            sx[(j0 + lane) * R + warp] = add(acc0, acc1);
         }
     };
     auto store_diag = [&](const float4 (&reg)[kDiagPer]) {
@@ -474,12 +513,9 @@ __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, 
         for (int t = 0; t < kDiagPer; ++t) reinterpret_cast<float4*>(sD)[tid + t * 512] = reg[t];
     };
     float4 dreg[kDiagPer];
-    // the pair path: full blocks only, and with several right-hand sides only
-    // for complex64 accumulators (register budget of 512 threads)
-    const bool vec = (n % kNB) == 0 && (RM == 1 || sizeof(T) == 8);
     // forward: L y = x (unit diagonal)
     if (vec) {
-        fetch_diag(0, kNB, dreg);
+        fetch_diag(0, kNB, 0, dreg);
         store_diag(dreg);
     }
     __syncthreads();
@@ -492,7 +528,9 @@ __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, 
             }
             __syncthreads();
         }
-        if (warp < nr) {
+        if (inv) {
+            apply_inv(j0);
+        } else if (warp < nr) {
             T v = lane < jb ? sx[(j0 + lane) * R + warp] : Cx<T>::mk(0, 0);
             for (int c = 0; c < jb; ++c) {
                 T xc = Cx<T>::mk(__shfl_sync(0xffffffff, v.x, c), __shfl_sync(0xffffffff, v.y, c));
@@ -503,7 +541,7 @@ __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, 
         __syncthreads();
         if (vec) {
             const bool more = j0 + kNB < n;
-            if (more) fetch_diag(j0 + kNB, kNB, dreg);
+            if (more) fetch_diag(j0 + kNB, kNB, 0, dreg);
             for (int i = j0 + kNB + 2 * tid; i < n; i += 2 * blockDim.x) {
                 T acc0[RM], acc1[RM];
 #pragma unroll
@@ -537,9 +575,8 @@ __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, 
         __syncthreads();
     }
     // backward: U x = y
-    const int nblk = (n + kNB - 1) / kNB;
     if (vec) {
-        fetch_diag((nblk - 1) * kNB, kNB, dreg);
+        fetch_diag((nblk - 1) * kNB, kNB, 1, dreg);
         store_diag(dreg);
         __syncthreads();
     }
@@ -552,7 +589,9 @@ __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, 
             }
             __syncthreads();
         }
-        if (warp < nr) {
+        if (inv) {
+            apply_inv(j0);
+        } else if (warp < nr) {
             T v = lane < jb ? sx[(j0 + lane) * R + warp] : Cx<T>::mk(0, 0);
             for (int c = jb - 1; c >= 0; --c) {
                 if (lane == c) v = mul(v, rcp(widen<T>(sD[c * kNB + c])));
@@ -563,7 +602,7 @@ __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, 
         }
         __syncthreads();
         if (vec) {
-            if (bi > 0) fetch_diag(j0 - kNB, kNB, dreg);
+            if (bi > 0) fetch_diag(j0 - kNB, kNB, 1, dreg);
             for (int i = 2 * tid; i < j0; i += 2 * blockDim.x) {
                 T acc0[RM], acc1[RM];
 #pragma unroll
@@ -600,6 +639,47 @@ __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, 
         const int i = idx / nr, q = idx - i * nr;
         x[(size_t)i * nrhs + r0 + q] = sx[i * R + q];
     }
+}
+
+// Inverses of the kNB x kNB diagonal blocks of every complex64 factor (n a
+// multiple of kNB), for the solves' matrix-vector diagonal steps: grid
+// (n / kNB, batch), two warps; warp 0 inverts the unit lower part L_kk, warp 1
+// the upper part U_kk.  Lane j forms column j of the inverse by substitution
+// on e_j held in registers (all lanes take the same steps and read the block
+// as shared-memory broadcasts).  Output [b][k][2][col][row], column-major per
+// block like the factor.  A zero pivot gives non-finite entries, as the
+// substitution would.
+__global__ void __launch_bounds__(64) diag_inv_kernel(int n, const float2* LU, float2* dinv) {
+    __shared__ float2 sB[kNB * kNB];    // [col * kNB + row]
+    const int k = blockIdx.x, b = blockIdx.y, nblk = n / kNB;
+    const float2* a = LU + (size_t)b * n * n + (size_t)k * kNB * n + (size_t)k * kNB;
+    for (int idx = threadIdx.x; idx < kNB * kNB; idx += blockDim.x) {
+        const int c = idx / kNB, r = idx - c * kNB;
+        sB[idx] = a[(size_t)c * n + r];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, j = threadIdx.x & 31;
+    float2 y[kNB];
+#pragma unroll
+    for (int r = 0; r < kNB; ++r) y[r] = make_float2(r == j ? 1.0f : 0.0f, 0.0f);
+    if (warp == 0) {
+        // L y = e_j (unit diagonal): y_r -= L[r][c] y_c for r > c, c ascending
+#pragma unroll
+        for (int c = 0; c < kNB; ++c)
+#pragma unroll
+            for (int r = c + 1; r < kNB; ++r) y[r] = fms(y[r], sB[c * kNB + r], y[c]);
+    } else {
+        // U y = e_j: y_c /= U[c][c], then y_r -= U[r][c] y_c for r < c, c descending
+#pragma unroll
+        for (int c = kNB - 1; c >= 0; --c) {
+            y[c] = mul(y[c], rcp(sB[c * kNB + c]));
+#pragma unroll
+            for (int r = 0; r < c; ++r) y[r] = fms(y[r], sB[c * kNB + r], y[c]);
+        }
+    }
+    float2* o = dinv + (((size_t)b * nblk + k) * 2 + warp) * kNB * kNB + (size_t)j * kNB;
+#pragma unroll
+    for (int r = 0; r < kNB; ++r) o[r] = y[r];
 }
 
 __global__ void c128_to_c64_kernel(int64_t count, const double2* s, float2* d) {
@@ -664,20 +744,42 @@ __global__ void norms3_kernel(int n, int nrhs, const double2* R, const double2* 
     }
 }
 
+// float nearest to the double whose 32-bit halves are (lo, hi), with 32-bit
+// integer operations only (on this GPU a double -> float conversion issues to
+// the FP64 pipe): round to nearest even on the 29 dropped significand bits;
+// results below float's normal range flush to a signed zero, above it give
+// infinity; NaN stays NaN.
+__device__ __forceinline__ float f32_of_halves(uint32_t lo, uint32_t hi) {
+    const uint32_t sg = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    if (e == 0x7ff) return __uint_as_float(sg | (((hi & 0xfffffu) | lo) ? 0x7fc00000u : 0x7f800000u));
+    const int ef = e - 1023 + 127;
+    if (ef >= 255) return __uint_as_float(sg | 0x7f800000u);
+    if (ef <= 0) return __uint_as_float(sg);
+    const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29), rest = lo & 0x1fffffffu;
+    uint32_t bits = ((uint32_t)ef << 23) | m;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) bits += 1u;   // a carry moves into the exponent
+    return __uint_as_float(sg | bits);
+}
+
 // complex64 copy of every matrix and |A_b|_F^2 in the same pass over A:
-// grid (blocks per matrix, matrices), out zeroed beforehand
+// grid (blocks per matrix, matrices), out zeroed beforehand.  The entries are
+// read as 32-bit words and converted with integer operations; the squares
+// accumulate in FP32 per thread (the norm enters only the backward-error test
+// of the refinement, where 1e-5 relative is ample) and in FP64 across warps.
 __global__ void c64_fro2_kernel(int64_t per, const double2* A, float2* A32, double* out) {
     __shared__ double sh[8];
-    const double2* a = A + (size_t)blockIdx.y * per;
+    const uint4* a = reinterpret_cast<const uint4*>(A + (size_t)blockIdx.y * per);
     float2* d = A32 + (size_t)blockIdx.y * per;
-    double acc = 0.0;
+    float acc = 0.0f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += (int64_t)gridDim.x * blockDim.x) {
-        const double2 v = a[i];
-        d[i] = make_float2((float)v.x, (float)v.y);
-        acc += v.x * v.x + v.y * v.y;
+        const uint4 v = __ldcs(a + i);      // read once: streaming
+        const float2 f = make_float2(f32_of_halves(v.x, v.y), f32_of_halves(v.z, v.w));
+        d[i] = f;
+        acc = __fmaf_rn(f.x, f.x, __fmaf_rn(f.y, f.y, acc));
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffff, acc, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)acc;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
@@ -774,7 +876,7 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
 
 template <typename T, typename TF>
 cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int* piv, T* B,
-                             cudaStream_t s, const int* active) {
+                             cudaStream_t s, const int* active, const TF* dinv) {
     // right-hand sides per CTA: up to kSolveR, as many as fit in shared memory
     // (about 200 KB for the group)
     int R = std::min(nrhs, kSolveR);
@@ -788,13 +890,13 @@ cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int
             cudaError_t e = allow_max_smem(lu_solve_kernel<T, TF, 1>);
             if (e != cudaSuccess) return e;
         }
-        lu_solve_kernel<T, TF, 1><<<g, 512, sm, s>>>(n, nrhs, R, LU, piv, B, active);
+        lu_solve_kernel<T, TF, 1><<<g, 512, sm, s>>>(n, nrhs, R, LU, piv, B, active, dinv);
     } else {
         if (big) {
             cudaError_t e = allow_max_smem(lu_solve_kernel<T, TF, kSolveR>);
             if (e != cudaSuccess) return e;
         }
-        lu_solve_kernel<T, TF, kSolveR><<<g, 512, sm, s>>>(n, nrhs, R, LU, piv, B, active);
+        lu_solve_kernel<T, TF, kSolveR><<<g, 512, sm, s>>>(n, nrhs, R, LU, piv, B, active, dinv);
     }
     count_launch();
     return cudaGetLastError();
@@ -805,11 +907,11 @@ template cudaError_t lu_prepare<float2>();
 template cudaError_t batched_lu<double2>(int, int, double2*, int*, int*, cudaStream_t);
 template cudaError_t batched_lu<float2>(int, int, float2*, int*, int*, cudaStream_t);
 template cudaError_t batched_lu_solve<double2, double2>(int, int, int, const double2*, const int*, double2*,
-                                                        cudaStream_t, const int*);
+                                                        cudaStream_t, const int*, const double2*);
 template cudaError_t batched_lu_solve<float2, float2>(int, int, int, const float2*, const int*, float2*,
-                                                      cudaStream_t, const int*);
+                                                      cudaStream_t, const int*, const float2*);
 template cudaError_t batched_lu_solve<double2, float2>(int, int, int, const float2*, const int*, double2*,
-                                                       cudaStream_t, const int*);
+                                                       cudaStream_t, const int*, const float2*);
 
 cudaError_t convert_to_c64(int64_t count, const double2* src, float2* dst, cudaStream_t s) {
     int blocks = (int)std::min<int64_t>((count + 255) / 256, 152 * 32);
@@ -842,12 +944,21 @@ cudaError_t convert_fro2_c128(int n, int batch, const double2* A, float2* A32, d
     return cudaGetLastError();
 }
 
+cudaError_t batched_diag_inv(int n, int batch, const float2* LU, float2* dinv, cudaStream_t s) {
+    if (n % kNB != 0) return cudaErrorInvalidValue;
+    dim3 g((unsigned)(n / kNB), (unsigned)batch);
+    diag_inv_kernel<<<g, 64, 0, s>>>(n, LU, dinv);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t refine_step(int n, int batch, int nrhs, const float2* LU32, const int* piv,
-                        const double2* R, float2* work32, double2* X, cudaStream_t s, const int* active) {
+                        const double2* R, float2* work32, double2* X, cudaStream_t s, const int* active,
+                        const float2* dinv) {
     int64_t cnt = (int64_t)batch * n * nrhs;
     cudaError_t e = convert_to_c64(cnt, R, work32, s);
     if (e != cudaSuccess) return e;
-    e = batched_lu_solve<float2, float2>(n, batch, nrhs, LU32, piv, work32, s, active);
+    e = batched_lu_solve<float2, float2>(n, batch, nrhs, LU32, piv, work32, s, active, dinv);
     if (e != cudaSuccess) return e;
     add_correction_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(cnt, (int64_t)n * nrhs, work32, X, active);
     count_launch();

@@ -586,14 +586,19 @@ def near_counts(P):
     """Close pairs of a problem by the path they take in the close-pair modes
     kernel: (packed: two physical nodes, both media in one transform; PML: a
     node in the PML, Taylor substitution, one pass per medium; plain: Alpert
-    correction pairs that are far by the criterion)."""
-    _, _, f, _ = P.near_pairs()
+    correction pairs that are far by the criterion; PML couples: PML grid
+    pairs whose mirror is a PML pair too, computed together by one CTA)."""
+    _, _, f, mirror = P.near_pairs()
     plain = (f & 2) != 0
     pml = ((f & 4) != 0) & ~plain
-    return int((~plain & ~pml).sum()), int(pml.sum()), int(plain.sum())
+    idx = np.arange(len(f))
+    has = pml & (mirror >= 0)
+    mir = np.where(has, mirror, 0)
+    couples = int((has & pml[mir] & (mir > idx)).sum())
+    return int((~plain & ~pml).sum()), int(pml.sum()), int(plain.sum()), couples
 
 
-def near_flops_per_launch(M, chunk_modes, packed, pml, plain):
+def near_flops_per_launch(M, chunk_modes, packed, pml, plain, couples=0):
     """Algorithmic FP64 flops of one close-pair modes launch (fused
     multiply-add = 2 flops; Taylor degree L = 5).  Per pair, (M/2 + 1) split
     samples: 169 flops for a packed pair (distance, complex square root and
@@ -605,15 +610,20 @@ def near_flops_per_launch(M, chunk_modes, packed, pml, plain):
     (K = M/2), E2 = 5 M log2 M + 15 M for a length-2M one.  Packed: 4 E1 + 6 E2
     (Laplace spectra, one convolution pass), PML: 8 E1 + 10 E2 (two passes),
     plain: 4 E1.  Products 14 (M + 1) and fills 4 K per pass; per output mode
-    8 (packed, plain) or 24 (PML) flops."""
+    8 (packed, plain) or 24 (PML) flops.  A PML couple (a grid pair and its
+    mirror, one CTA) adds to one pair's work only the mirror's double-layer
+    remainder samples (30 flops per angle, both media), their 2 E1, the
+    mirror's D^ spectrum and one inverse transform per pass (3 E2), one
+    product per pass 8 (M + 1), and 12 flops per output mode."""
     K = M // 2
     E1 = 5.0 * K * np.log2(K) + 15.0 * K
     E2 = 5.0 * M * np.log2(M) + 15.0 * M
     S1 = K + 1
     f_packed = S1 * 169.0 + 4 * E1 + 6 * E2 + 14.0 * (M + 1) + 4.0 * K + 8.0 * chunk_modes
     f_pml = S1 * 601.0 + 8 * E1 + 10 * E2 + 2 * (14.0 * (M + 1) + 4.0 * K) + 24.0 * chunk_modes
+    f_mirror = S1 * 30.0 + 2 * E1 + 3 * E2 + 2 * 8.0 * (M + 1) + 12.0 * chunk_modes
     f_plain = S1 * 295.0 + 4 * E1 + 8.0 * chunk_modes
-    return packed * f_packed + pml * f_pml + plain * f_plain
+    return packed * f_packed + (pml - couples) * f_pml + couples * f_mirror + plain * f_plain
 
 
 def source_sha(name):
@@ -660,7 +670,8 @@ def near_roofline(w, rep, pk, clk, counts, pipes=None):
     peak, note = fp64_peak(pk, clk, pipes)
     launches = max(1, rep.chunks)
     npml = counts[1]
-    flops = near_flops_per_launch(M, rep.chunk_modes, 0, npml, 0)
+    couples = counts[3] if len(counts) > 3 else 0
+    flops = near_flops_per_launch(M, rep.chunk_modes, 0, npml, 0, couples)
     ms1 = (rep.ms_near - rep.ms_near_laplace - rep.ms_near_ff) / launches
     ach = flops / (ms1 / 1e3) / 1e12
     traffic = profile_traffic("near_modes_kernel_pml_n256_m128.md", "kernels.cu", npml)
@@ -668,7 +679,8 @@ def near_roofline(w, rep, pk, clk, counts, pipes=None):
                       "FFT convolution with the exact Laplace modes, FP64)",
             "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "traffic": traffic, "flops_per_launch": flops, "ms_per_launch": ms1, "launches_per_step": launches,
-            "pairs": npml, "algorithmic_bytes": float(npml) * (2 * M + 4 * rep.chunk_modes) * 16,
+            "pairs": npml, "pml_couples": couples,
+            "algorithmic_bytes": float(npml) * (2 * M + 4 * rep.chunk_modes) * 16,
             "peak_note": note,
             "traffic_note": ("ncu dram read+write per PML pair (profiles/near_modes_kernel_pml_n256_m128.md) x pairs"
                              if traffic else "null: no ncu capture of the current kernels.cu")}

@@ -501,6 +501,8 @@ struct NearArgs {
                             // Sec. 4.3 substitution (the mixed path's float-float
                             // kernel takes the others)
     float4* pff;            // per-pair float-float quantities (kNearFF float4), or null
+    int share_mirror;       // 1: a general (non-packed, non-plain) grid pair and its
+                            // mirror are computed by one CTA (shared memory permitting)
 };
 
 __device__ void complex_agm_KE(double2 k2, double2 kp, double2& K, double2& E) {
@@ -749,6 +751,14 @@ __device__ __forceinline__ double2 cpoly_from(const double2 (&c)[8], int k0, int
 // of 8 and 8.
 // kExact: the diagnostic exact split on PML pairs (compiled into its own
 // variant so that the default one keeps its register budget)
+// Mirror sharing (a.share_mirror): a grid pair (l, m) of the general path and
+// its mirror (m, l) have the same d~^2, rho~ rho~' and hence the same R(psi),
+// samples of the smooth factors f1, f3 and of the single-layer remainder r1,
+// and the same Z^; only the double-layer remainder r3 (its normal factor N_D
+// is the source's) and D^ differ.  The CTA of the lower index computes both:
+// the mirror's r3 samples and their two transforms, its D^ transform, and per
+// region one more product and inverse transform (5 transforms instead of 18);
+// the mirror's S^ equal the pair's.  The mirror's CTA returns at once.
 template <bool kExact>
 __global__ void near_modes_kernel(NearArgs a) {
     extern __shared__ double2 smem[];
@@ -762,6 +772,12 @@ __global__ void near_modes_kernel(NearArgs a) {
     // transforms of warps 0-1 and 2-3 never overlap; length-M ones take half)
     double2* slot = cv + 4 * S2 + (warp & 1) * 2 * M;
     double2* wyK = slot + (warp >> 1) * M;         // y, scr of a length-M transform (K = M/2)
+    // mirror sharing: D^ and K convolution of the mirror (2 x (M+1)), its r3
+    // samples / spectra of both regions (2 x (K+1)), a third 2M scratch slot
+    double2* zDm = cv + 4 * S2 + 4 * M;
+    double2* cKm = zDm + S2;
+    double2* seqm = cKm + S2;
+    double2* slot2 = seqm + 2 * S1;
     for (int i = threadIdx.x; i < L2; i += blockDim.x) {
         const double2 t = a.T.twid2[i];
         tw2[i] = t;
@@ -777,9 +793,25 @@ __global__ void near_modes_kernel(NearArgs a) {
     const bool phys = q.d2.y == 0.0 && q.rr.y == 0.0 && q.rho_t.y == 0.0 && q.rho_s.y == 0.0 && q.drt.y == 0.0 &&
                       q.nuc_r.y == 0.0 && q.nuc_z.y == 0.0;
     const bool packed = !plain && !subst && phys;
+    // mirror sharing (both pairs on the general path, same substitution flag)
+    bool share = false;
+    NearPair qm;
+    if (a.share_mirror && !plain && !packed && q.mirror >= 0) {
+        qm = a.np[q.mirror];
+        const bool mphys = qm.d2.y == 0.0 && qm.rr.y == 0.0 && qm.rho_t.y == 0.0 && qm.rho_s.y == 0.0 &&
+                           qm.drt.y == 0.0 && qm.nuc_r.y == 0.0 && qm.nuc_z.y == 0.0;
+        const bool msubst = (qm.flags & kFlagSubst) != 0;
+        share = (qm.flags & kFlagFar) == 0 && msubst == subst && !(mphys && !msubst);
+        if (share && q.mirror < p) return;    // computed by the mirror's CTA
+    }
     // sampling; N_D(psi) = [nu'_r (rho~' - rho~) - nu'_z dz] + 2 nu'_r rho~ sin^2(psi/2)
     const double2 nd0 = cadd(cmul(q.nuc_r, q.drt), cscale(q.nuc_z, -q.dz));
     const double2 nds = cscale(cmul(q.nuc_r, q.rho_t), 2.0);
+    double2 nd0m = c2(0.0, 0.0), ndsm = nd0m;
+    if (share) {
+        nd0m = cadd(cmul(qm.nuc_r, qm.drt), cscale(qm.nuc_z, -qm.dz));
+        ndsm = cscale(cmul(qm.nuc_r, qm.rho_t), 2.0);
+    }
     const int L = a.L;
     __syncthreads();
     for (int j = threadIdx.x; j <= K; j += blockDim.x) {
@@ -788,6 +820,7 @@ __global__ void near_modes_kernel(NearArgs a) {
         double2 R, iR;
         fcsqrt_rcp(D2, R, iR);
         const double2 ND = cadd(nd0, cscale(nds, sc.x));
+        const double2 NDm = cadd(nd0m, cscale(ndsm, sc.x));
         if (packed) {
             // real q = w R; H1 = cos q, i Z H2 = (i w / 4 pi) sin(q)/q, H3 = cos q + q sin q,
             // i D H4 = -(i w^3 / 4 pi) N_D (sin q - q cos q)/q^3 (region b: -N_D)
@@ -820,7 +853,7 @@ __global__ void near_modes_kernel(NearArgs a) {
             const double sg = r == 0 ? 1.0 : -1.0;     // region b normal -nu
             const double2 qq = cscale(R, w);
             const double2 e = fcexpi(qq);
-            double2 v0, v1, v2, v3;
+            double2 v0, v1, v2, v3, v3m = c2(0.0, 0.0);
             if (plain) {
                 const double2 iR3 = cmul(iR, cmul(iR, iR));
                 const double2 Dk = cscale(cmul(ND, iR3), -kInv4Pi * sg);
@@ -850,18 +883,22 @@ __global__ void near_modes_kernel(NearArgs a) {
                 v1 = cmul(c2(0.0, w * kInv4Pi), sinc);
                 v2 = cadd(cq, cmul(qq, sq));
                 v3 = cscale(cmul(c2(0.0, 1.0), cmul(ND, h4)), -w * w * w * kInv4Pi * sg);
+                if (share) v3m = cscale(cmul(c2(0.0, 1.0), cmul(NDm, h4)), -w * w * w * kInv4Pi * sg);
             } else {
                 // cH1 = e^{iq} sum a_k q^k, Z (e^{iq} - cH1) = -(w / 4 pi) e^{iq} sum_{k>=1} a_k q^{k-1};
                 // cH3 likewise; D (e^{iq}(1 - iq) - cH3) = (w^3 / 4 pi) N_D e^{iq} sum_{k>=3} b_k q^{k-3}
                 v0 = cmul(e, cpoly_from(a.pa, 0, L, qq));
                 v1 = cscale(cmul(e, cpoly_from(a.pa, 1, L, qq)), -w * kInv4Pi);
                 v2 = cmul(e, cpoly_from(a.pb, 0, L, qq));
-                v3 = cscale(cmul(cmul(ND, e), cpoly_from(a.pb, 3, L, qq)), w * w * w * kInv4Pi * sg);
+                const double2 pb3 = cpoly_from(a.pb, 3, L, qq);
+                v3 = cscale(cmul(cmul(ND, e), pb3), w * w * w * kInv4Pi * sg);
+                if (share) v3m = cscale(cmul(cmul(NDm, e), pb3), w * w * w * kInv4Pi * sg);
             }
             seq[(4 * r + 0) * S1 + j] = v0;
             seq[(4 * r + 1) * S1 + j] = v1;
             seq[(4 * r + 2) * S1 + j] = v2;
             seq[(4 * r + 3) * S1 + j] = v3;
+            if (share) seqm[r * S1 + j] = v3m;
         }
     }
     __syncthreads();
@@ -870,9 +907,9 @@ __global__ void near_modes_kernel(NearArgs a) {
     if (packed) {
         warp_even_dft(seq + warp * S1, wyK, wyK + K, K, tw2, hs, 2, lane);
     } else {
-        for (int s = warp; s < 8; s += 4) {
+        for (int s = warp; s < (share ? 10 : 8); s += 4) {
             if (plain && (s & 1)) continue;
-            warp_even_dft(seq + s * S1, wyK, wyK + K, K, tw2, hs, 2, lane);
+            warp_even_dft(s < 8 ? seq + s * S1 : seqm + (s - 8) * S1, wyK, wyK + K, K, tw2, hs, 2, lane);
         }
     }
     __syncthreads();
@@ -900,13 +937,17 @@ __global__ void near_modes_kernel(NearArgs a) {
     double2* zD = cv + S2;
     double2* cS = cv + 2 * S2;
     double2* cK = cv + 3 * S2;
+    const double2* Ddm = share ? a.zd + (size_t)q.mirror * 2 * M + M : nullptr;
+    double2* outm = share ? a.out + (size_t)q.mirror * 4 * nmodes : nullptr;
     for (int i = threadIdx.x; i <= M; i += blockDim.x) {
         bool inz = i <= M - 2;
         zZ[i] = inz ? Z[i] : c2(0.0, 0.0);
         zD[i] = inz ? Dd[i] : c2(0.0, 0.0);
+        if (share) zDm[i] = inz ? Ddm[i] : c2(0.0, 0.0);
     }
     __syncthreads();
     if (warp < 2) warp_even_dft(warp == 0 ? zZ : zD, slot, slot + M, M, tw2, hs, 1, lane);
+    if (share && warp == 2) warp_even_dft(zDm, slot2, slot2 + M, M, tw2, hs, 1, lane);
     const double c = 1.0 / (2.0 * kPi * L2);
     // packed: one pass with cS = F1a + i F1b and cK = F3a - i F3b (region b's -D^
     // as the conjugate); otherwise one pass per region
@@ -929,10 +970,12 @@ __global__ void near_modes_kernel(NearArgs a) {
         const double sgn = r == 0 ? 1.0 : -1.0;      // region b: D^ -> -D^ (unpacked)
         for (int i = threadIdx.x; i <= M; i += blockDim.x) {
             cS[i] = cmul(zZ[i], cS[i]);
+            if (share) cKm[i] = cscale(cmul(zDm[i], cK[i]), sgn);
             cK[i] = cscale(cmul(zD[i], cK[i]), sgn);
         }
         __syncthreads();
         if (warp >= 2) warp_even_dft(warp == 2 ? cS : cK, slot, slot + M, M, tw2, hs, 1, lane);
+        if (share && warp == 1) warp_even_dft(cKm, slot2, slot2 + M, M, tw2, hs, 1, lane);
         __syncthreads();
         for (int t = threadIdx.x; t < nmodes; t += blockDim.x) {
             int n = a.mode_lo + t;
@@ -945,10 +988,14 @@ __global__ void near_modes_kernel(NearArgs a) {
                 out[2 * (size_t)nmodes + t] = c2(s0.y, rs.y);
                 out[3 * (size_t)nmodes + t] = c2(k0.y, rk.y);
             } else {
-                out[(2 * r + 0) * (size_t)nmodes + t] =
-                    cadd(cscale(cS[n], c), cscale(seq[(4 * r + 1) * S1 + n], scale));
+                const double2 sv = cadd(cscale(cS[n], c), cscale(seq[(4 * r + 1) * S1 + n], scale));
+                out[(2 * r + 0) * (size_t)nmodes + t] = sv;
                 out[(2 * r + 1) * (size_t)nmodes + t] =
                     cadd(cscale(cK[n], c), cscale(seq[(4 * r + 3) * S1 + n], scale));
+                if (share) {
+                    outm[(2 * r + 0) * (size_t)nmodes + t] = sv;
+                    outm[(2 * r + 1) * (size_t)nmodes + t] = cadd(cscale(cKm[n], c), cscale(seqm[r * S1 + n], scale));
+                }
             }
         }
         __syncthreads();
@@ -1366,10 +1413,15 @@ cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, do
         a.only_subst = 1;
     }
     if (mid_ff && (e = cudaEventRecord(mid_ff, s)) != cudaSuccess) return e;
-    // tw2 (2M) + 8 x (M/2+1) + 4 x (M+1) + 2 scratch slots x 2M (+ M weights when they fit)
+    // tw2 (2M) + 8 x (M/2+1) + 4 x (M+1) + 2 scratch slots x 2M (+ M weights when they
+    // fit), + for mirror sharing 2 x (M+1) + 2 x (M/2+1) + a third slot of 2M (when
+    // it fits too)
     size_t smem = sizeof(double2) * ((size_t)2 * M + 8 * (M / 2 + 1) + 4 * (M + 1) + 4 * (size_t)M);
+    const size_t share_bytes = sizeof(double2) * ((size_t)2 * (M + 1) + 2 * (M / 2 + 1) + 2 * (size_t)M);
     a.hs_tab = smem + sizeof(double2) * M <= 227 * 1024 ? 1 : 0;
     if (a.hs_tab) smem += sizeof(double2) * M;
+    a.share_mirror = smem + share_bytes <= 227 * 1024 ? 1 : 0;
+    if (a.share_mirror) smem += share_bytes;
     if (prob->P.subst_off) {
         if ((e = allow_max_smem(near_modes_kernel<true>)) != cudaSuccess) return e;
         near_modes_kernel<true><<<a.npairs, 128, smem, s>>>(a);

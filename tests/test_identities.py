@@ -60,3 +60,5 @@ def test_near_flop_model_counts():
     assert bench.near_flops_per_launch(256, 128, 1, 0, 0) == 137015
     assert bench.near_flops_per_launch(256, 128, 0, 1, 0) == 280821
     assert bench.near_flops_per_launch(256, 128, 0, 0, 1) == 64679
+    # a PML pair and its mirror in one CTA: one pair's work + the mirror's extra
+    assert bench.near_flops_per_launch(256, 128, 0, 2, 0, 1) == 280821 + 64558

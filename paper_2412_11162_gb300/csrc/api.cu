@@ -82,7 +82,8 @@ int ensure_device(pmlbie_problem* prob) {
         return rc;
     std::vector<double2> rt = to_d2(H.rho_t), ncr = to_d2(H.nuc_r), ncz = to_d2(H.nuc_z);
     if ((rc = upload(D.rho_t, rt)) || (rc = upload(D.nuc_r, ncr)) || (rc = upload(D.nuc_z, ncz)) ||
-        (rc = upload(D.cls, H.cls)) || (rc = upload(D.near, H.near)) || (rc = upload(D.bk, H.bk)) ||
+        (rc = upload(D.cls, H.cls)) || (rc = upload(D.near, H.near)) || (rc = upload(D.near_lead, H.near_lead)) ||
+        (rc = upload(D.bk, H.bk)) ||
         (rc = upload(D.off, H.off)) ||
         (rc = upload(D.corr_target, H.corr_target)) || (rc = upload(D.corr_m, H.corr_m)) ||
         (rc = upload(D.corr_coef, H.corr_coef)) || (rc = upload(D.Da, H.Da)) || (rc = upload(D.Db, H.Db)) ||
@@ -135,7 +136,7 @@ int ensure_device(pmlbie_problem* prob) {
 
 void free_device(pmlbie_problem* prob) {
     DeviceTables& D = prob->D;
-    void* ptrs[] = {D.rho, D.z, D.I, D.Wu, D.Wphi, D.rho_t, D.nuc_r, D.nuc_z, D.bk, D.off, D.cls, D.near,
+    void* ptrs[] = {D.rho, D.z, D.I, D.Wu, D.Wphi, D.rho_t, D.nuc_r, D.nuc_z, D.bk, D.off, D.cls, D.near, D.near_lead,
                     D.corr_target, D.corr_m, D.corr_coef, D.Da, D.Db, D.cos_tab, D.twid, D.twid2,
                     D.corr_start, D.corr_cmin, D.corr_w, D.rec_up, D.rec_dn, D.twid_ff, D.twid2_ff, D.cos_ff, D.exp_ff, D.trig_ff, D.wuc_ff,
                     D.wpc_ff};

@@ -10,6 +10,7 @@
 //              interpolation of the off-grid density values.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <mutex>
 #include <stdexcept>
@@ -863,6 +864,40 @@ int build_tables(pmlbie_problem* prob) {
             H.near[(size_t)H.n_grid_near + c] = np;
         }
     });
+    {
+        // Close pairs whose exact modal Laplace kernels a thread computes: not
+        // far by the criterion, and of a pair and its mirror the lower index.
+        // Ordered so that a warp holds pairs of one arithmetic class (real:
+        // both points physical; complex otherwise) and of similar recurrence
+        // length (upward: M steps; Miller: M + 20 / Re(eta)): a warp's FP64
+        // instruction costs the same issue slot whatever its active lanes.
+        const int np = (int)H.near.size();
+        std::vector<std::pair<long long, int>> key;
+        key.reserve(np);
+        auto cx_zero = [](double2 v) { return v.y == 0.0; };
+        for (int p = 0; p < np; ++p) {
+            const NearPair& q = H.near[p];
+            if (q.flags & kFlagFar) continue;
+            if (q.mirror >= 0 && q.mirror < p) continue;
+            bool real = cx_zero(q.d2) && cx_zero(q.rr) && cx_zero(q.rho_t) && cx_zero(q.rho_s) && cx_zero(q.drt) &&
+                        cx_zero(q.nuc_r) && cx_zero(q.nuc_z);
+            if (real && q.mirror >= 0)
+                real = cx_zero(H.near[q.mirror].nuc_r) && cx_zero(H.near[q.mirror].nuc_z);
+            // Re acosh(chi), chi - 1 = d~^2 / (2 rho~ rho~')
+            const std::complex<double> d2(q.d2.x, q.d2.y), rr(q.rr.x, q.rr.y);
+            const std::complex<double> chim1 = d2 / (2.0 * rr), chi = 1.0 + chim1;
+            const double reeta = std::fabs(std::log(chi + std::sqrt(chim1) * std::sqrt(chi + 1.0)).real());
+            long long steps = P.M;
+            if (!(reeta * P.M < kRecUpward) && reeta > 0.0) steps += (long long)std::ceil(20.0 / reeta);
+            key.push_back({(real ? 0LL : (1LL << 40)) + steps, p});
+        }
+        std::stable_sort(key.begin(), key.end(),
+                         [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) {
+                             return a.first < b.first;
+                         });
+        H.near_lead.resize(key.size());
+        for (size_t i = 0; i < key.size(); ++i) H.near_lead[i] = key[i].second;
+    }
 
     // diagonal term: K0_AB 1 by the same quadrature (mode-0 Laplace double layer,
     // physical normal), plus K0_+ 1 from the disc solid angle (Lemma 3.3)

@@ -73,6 +73,10 @@ struct HostTables {
     std::vector<uint8_t> cls;                // N*N, [l][m]
     std::vector<NearPair> near;              // grid-near pairs, then correction pairs
     int n_grid_near = 0;
+    // pairs whose exact modal Laplace kernels are computed (one of a mirror
+    // couple, none far by the criterion), grouped by arithmetic class and
+    // recurrence length
+    std::vector<int> near_lead;
     // diagonal
     std::vector<double> Da, Db;
 };
@@ -84,6 +88,7 @@ struct DeviceTables {
     double2* off = nullptr;
     uint8_t* cls = nullptr;
     NearPair* near = nullptr;
+    int* near_lead = nullptr;
     int* corr_target = nullptr;
     int* corr_m = nullptr;
     double* corr_coef = nullptr;

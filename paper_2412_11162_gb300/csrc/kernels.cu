@@ -503,6 +503,8 @@ struct NearArgs {
     float4* pff;            // per-pair float-float quantities (kNearFF float4), or null
     int share_mirror;       // 1: a general (non-packed, non-plain) grid pair and its
                             // mirror are computed by one CTA (shared memory permitting)
+    const int* lead;        // pairs whose Laplace modes a thread computes (HostTables::near_lead)
+    int nlead;
 };
 
 __device__ void complex_agm_KE(double2 k2, double2 kp, double2& K, double2& E) {
@@ -605,9 +607,11 @@ __device__ void laplace_modes_real(const NearPair& q, const NearPair* qm, int M,
     }
 }
 
-// One thread per close pair.  A grid pair and its mirror (target and source
-// exchanged) share chi and hence c_m: the lower index of the two computes the
-// modes of both, the other returns.
+// One thread per close pair of the leader list (a.lead: not far by the
+// criterion; of a grid pair and its mirror, which share chi and hence c_m,
+// the lower index, which computes the modes of both), the list grouped by
+// arithmetic class and recurrence length so that a warp's lanes do the same
+// work.  With a.pff, thread t also writes pair t's float-float quantities.
 // Float-float quantities of close pair q for the mixed path's modes kernel
 // (units of L = 2^eL, L^2 ~ |d~^2| + 4 |rho~ rho~'|), one thread per pair.
 __device__ void near_pair_ff(const NearPair& q, double w1, double w2, float4* out) {
@@ -635,10 +639,11 @@ __device__ void near_pair_ff(const NearPair& q, double w1, double w2, float4* ou
 }
 
 __global__ void near_laplace_kernel(NearArgs a) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.npairs) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a.pff && t < a.npairs) near_pair_ff(a.np[t], a.w1, a.w2, a.pff + (size_t)t * kNearFF);
+    if (t >= a.nlead) return;
+    const int p = a.lead[t];
     NearPair q = a.np[p];
-    if (a.pff) near_pair_ff(q, a.w1, a.w2, a.pff + (size_t)p * kNearFF);
     if (q.flags & kFlagFar) return;
     if (q.mirror >= 0 && q.mirror < p) return;
     const int M = a.M;
@@ -1402,8 +1407,13 @@ cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, do
         if (e0 == cudaSuccess && mid_ff) e0 = cudaEventRecord(mid_ff, s);
         return e0;
     }
-    near_laplace_kernel<<<(a.npairs + 127) / 128, 128, 0, s>>>(a);
-    count_launch();
+    a.lead = prob->D.near_lead;
+    a.nlead = (int)prob->H.near_lead.size();
+    const int nthr = std::max(a.nlead, a.pff ? a.npairs : 0);
+    if (nthr > 0) {
+        near_laplace_kernel<<<(nthr + 127) / 128, 128, 0, s>>>(a);
+        count_launch();
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (mid && (e = cudaEventRecord(mid, s)) != cudaSuccess) return e;

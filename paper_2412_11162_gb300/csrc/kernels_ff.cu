@@ -470,6 +470,7 @@ struct NearArgsFF {
     float2 cconv;          // 1 / (2 pi 2M)
     float2 wq[2], wc[2];   // omega_r / (4 pi), omega_r^3 / (4 pi)
     float2 inv4pi;         // 1 / (4 pi)
+    int share_mirror;      // 1: a packed grid pair and its mirror in one CTA
 };
 
 // x 2^-shift as a float pair, with 32-bit integer operations only (x normal
@@ -543,6 +544,15 @@ __device__ __forceinline__ cff cpoly_ff(const float4 (&c)[8], int k0, int L, cff
     return r;
 }
 
+// Close-pair modes in float-float (pairs without a PML point; the others
+// return at once).  Mirror sharing (a.share_mirror) for packed pairs: a grid
+// pair (l, m) and its mirror (m, l) share R(psi), the f1, r1, f3 samples and
+// spectra, Z^ and the S^ results; the CTA of the lower index adds the mirror's
+// double-layer remainder r3 (its own normal factor N_D) and its transform, the
+// mirror's D^ transform and one product and inverse transform, and writes both
+// pairs' modes; the mirror's CTA returns.  The mirror's buffers: its D^ and K
+// convolution (2 x (M+1)), its r3 spectrum (K+1), and a third 2M scratch slot
+// in the region-b sample sequences, which packed pairs do not use.
 __global__ void __launch_bounds__(128) near_modes_kernel_ff(NearArgsFF a) {
     extern __shared__ float4 smf[];
     const int M = a.M, K = M / 2, S1 = K + 1, L2 = 2 * M, S2 = M + 1, p = blockIdx.x;
@@ -555,7 +565,13 @@ __global__ void __launch_bounds__(128) near_modes_kernel_ff(NearArgsFF a) {
     float4* trig = slots + 4 * M;       // kTrigTab
     float2* expt = reinterpret_cast<float2*>(trig + kTrigTab);   // kExpTab
     int* Eb = reinterpret_cast<int*>(trig + kTrigTab + kExpTab / 2);   // 2 x S1
-    int* ex = Eb + 2 * S1;              // [0..1] common sample exponent per medium, [2] eZ, [3] eD
+    int* ex = Eb + 2 * S1;              // [0..1] common sample exponent per medium, [2] eZ, [3] eD, [4] the mirror's eD
+    // mirror sharing: S2 + S2 + S1, from the first 16-byte boundary after Eb
+    // and ex[0..4] (Eb itself starts on one)
+    float4* zDm = reinterpret_cast<float4*>(Eb) + (2 * S1 + 5 + 3) / 4;
+    float4* cKm = zDm + S2;
+    float4* seqm = cKm + S2;
+    float4* slot2 = seq + 4 * S1;       // 2M <= 4 (K + 1): region b's sequences (unused by packed pairs)
     float4* slot = slots + (warp & 1) * 2 * M;
     float4* wyK = slot + (warp >> 1) * M;
     for (int i = threadIdx.x; i < L2; i += blockDim.x) {
@@ -569,7 +585,7 @@ __global__ void __launch_bounds__(128) near_modes_kernel_ff(NearArgsFF a) {
     }
     for (int i = threadIdx.x; i < kTrigTab; i += blockDim.x) trig[i] = a.trig[i];
     for (int i = threadIdx.x; i < kExpTab; i += blockDim.x) expt[i] = a.expt[i];
-    if (threadIdx.x < 4) ex[threadIdx.x] = threadIdx.x < 2 ? 0 : -2000;
+    if (threadIdx.x < 5) ex[threadIdx.x] = threadIdx.x < 2 ? 0 : -2000;
     const NearPair& q = a.np[p];
     const bool plain = (q.flags & kFlagFar) != 0;
     const bool subst = (q.flags & kFlagSubst) != 0;
@@ -587,6 +603,20 @@ __global__ void __launch_bounds__(128) near_modes_kernel_ff(NearArgsFF a) {
     const bool packed = !plain && __float_as_int(misc.y) != 0;
     const int eL = __float_as_int(misc.x);
     const cff d2 = unpack(pf[0]), rr = unpack(pf[1]), nd0 = unpack(pf[2]), nds = unpack(pf[3]);
+    // mirror sharing (both pairs packed: physical, not far, no substitution;
+    // their units 2^eL agree, |d~^2| + 4 |rho~ rho~'| being symmetric)
+    bool share = false;
+    cff nd0m = czero(), ndsm = czero();
+    if (a.share_mirror && packed && q.mirror >= 0) {
+        const NearPair& qm = a.np[q.mirror];
+        const float4* pfm = a.pff + (size_t)q.mirror * kNearFF;
+        share = (qm.flags & (kFlagFar | kFlagSubst)) == 0 && __float_as_int(pfm[6].y) != 0;
+        if (share && q.mirror < p) return;    // computed by the mirror's CTA (uniform)
+        if (share) {
+            nd0m = unpack(pfm[2]);
+            ndsm = unpack(pfm[3]);
+        }
+    }
     const float4 wv = pf[4], iwv = pf[5];
     const ff wl[2] = {ff{wv.x, wv.y}, ff{wv.z, wv.w}};
     const ff iwl[2] = {ff{iwv.x, iwv.y}, ff{iwv.z, iwv.w}};
@@ -607,7 +637,8 @@ __global__ void __launch_bounds__(128) near_modes_kernel_ff(NearArgsFF a) {
             if (D2.hi < 0x1p-120f) D2 = ff{0x1p-120f, 0.0f};
             const ff iR = rsqrt(D2), R = mul(D2, iR);
             const ff ND = add(nd0.re, mul(nds.re, s2));
-            ff f1[2], r1[2], f3[2], r3[2];
+            const ff NDm = add(nd0m.re, mul(ndsm.re, s2));
+            ff f1[2], r1[2], f3[2], r3[2], r3m[2];
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 const ff qr = mul(wl[r], R), iq = mul(iR, iwl[r]);
@@ -616,13 +647,15 @@ __global__ void __launch_bounds__(128) near_modes_kernel_ff(NearArgsFF a) {
                 f1[r] = cs;
                 r1[r] = mul(wq[r], mul(sn, iq));
                 f3[r] = add(cs, mul(qr, sn));
-                const ff h4 = h4_ff(qr, sn, cs, iq);
-                r3[r] = mul(mul(wc[r], h4), r == 0 ? neg(ND) : ND);
+                const ff h4w = mul(wc[r], h4_ff(qr, sn, cs, iq));
+                r3[r] = mul(h4w, r == 0 ? neg(ND) : ND);
+                r3m[r] = mul(h4w, r == 0 ? neg(NDm) : NDm);
             }
             stc(seq, 0 * S1 + j, cff{f1[0], f1[1]});
             stc(seq, 1 * S1 + j, cff{r1[0], r1[1]});
             stc(seq, 2 * S1 + j, cff{f3[0], f3[1]});
             stc(seq, 3 * S1 + j, cff{r3[0], r3[1]});
+            if (share) stc(seqm, j, cff{r3m[0], r3m[1]});
             continue;
         }
         const cff D2 = cadd(d2, cscale(rr, s2x4));
@@ -689,18 +722,20 @@ __global__ void __launch_bounds__(128) near_modes_kernel_ff(NearArgsFF a) {
         }
         if (lane == 0) ex[r] = em;
     }
-    if (!plain && warp >= 2) {
-        const double2* X = warp == 2 ? Z : Dd;
+    const double2* Ddm = share ? a.zd + (size_t)q.mirror * 2 * M + M : nullptr;
+    if (!plain && (warp >= 2 || (share && warp == 0))) {
+        const double2* X = warp == 2 ? Z : warp == 3 ? Dd : Ddm;
         int em = -2000;
         for (int i = lane; i <= M - 2; i += 32) em = max(em, max(exp_of_double(X[i].x), exp_of_double(X[i].y)));
         for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
-        if (lane == 0) ex[warp] = em;
+        if (lane == 0) ex[warp == 0 ? 4 : warp] = em;
     }
     __syncthreads();
-    // even-sequence DFTs of length M: packed pairs 4, plain pairs 0, 2, 4, 6,
-    // the others all 8
+    // even-sequence DFTs of length M: packed pairs 4 (+ the mirror's r3),
+    // plain pairs 0, 2, 4, 6, the others all 8
     if (packed) {
         warp_even_dft_ff(seq + warp * S1, wyK, wyK + K, K, tw2, hs, 2, lane);
+        if (share && warp == 0) warp_even_dft_ff(seqm, wyK, wyK + K, K, tw2, hs, 2, lane);
     } else {
         for (int s = warp; s < 8; s += 4) {
             if (plain && (s & 1)) continue;
@@ -722,18 +757,21 @@ __global__ void __launch_bounds__(128) near_modes_kernel_ff(NearArgsFF a) {
         }
         return;
     }
-    const int eZ = ex[2], eD = ex[3];
+    const int eZ = ex[2], eD = ex[3], eDm = ex[4];
     float4* zZ = cv;
     float4* zD = cv + S2;
     float4* cS = cv + 2 * S2;
     float4* cK = cv + 3 * S2;
+    double2* outm = share ? a.out + (size_t)q.mirror * 4 * nmodes : nullptr;
     for (int i = threadIdx.x; i <= M; i += blockDim.x) {
         const bool inz = i <= M - 2;
         stc(zZ, i, inz ? cff_of_double(Z[i], eZ) : czero());
         stc(zD, i, inz ? cff_of_double(Dd[i], eD) : czero());
+        if (share) stc(zDm, i, inz ? cff_of_double(Ddm[i], eDm) : czero());
     }
     __syncthreads();
     if (warp < 2) warp_even_dft_ff(warp == 0 ? zZ : zD, slot, slot + M, M, tw2, hs, 1, lane);
+    if (share && warp == 2) warp_even_dft_ff(zDm, slot2, slot2 + M, M, tw2, hs, 1, lane);
     const int passes = packed ? 1 : 2;
     for (int r = 0; r < passes; ++r) {
         for (int i = threadIdx.x; i <= M; i += blockDim.x) {
@@ -751,11 +789,14 @@ __global__ void __launch_bounds__(128) near_modes_kernel_ff(NearArgsFF a) {
         __syncthreads();
         for (int i = threadIdx.x; i <= M; i += blockDim.x) {
             stc(cS, i, cmul(ldc(zZ, i), ldc(cS, i)));
-            const cff k = cmul(ldc(zD, i), ldc(cK, i));
+            const cff kh = ldc(cK, i);
+            const cff k = cmul(ldc(zD, i), kh);
             stc(cK, i, r == 0 ? k : cneg(k));   // region b: D^ -> -D^ (unpacked)
+            if (share) stc(cKm, i, cmul(ldc(zDm, i), kh));   // packed: one pass (r = 0)
         }
         __syncthreads();
         if (warp >= 2) warp_even_dft_ff(warp == 2 ? cS : cK, slot, slot + M, M, tw2, hs, 1, lane);
+        if (share && warp == 1) warp_even_dft_ff(cKm, slot2, slot2 + M, M, tw2, hs, 1, lane);
         __syncthreads();
         for (int t = threadIdx.x; t < nmodes; t += blockDim.x) {
             const int n = a.mode_lo + t;
@@ -763,10 +804,19 @@ __global__ void __launch_bounds__(128) near_modes_kernel_ff(NearArgsFF a) {
             if (packed) {
                 // real parts from the convolutions, imaginary parts from the remainders
                 const cff rs = cscale(ldc(seq, 1 * S1 + n), scale), rk = cscale(ldc(seq, 3 * S1 + n), scale);
-                out[0 * (size_t)nmodes + t] = make_double2(to_double(s0.re, eZ), to_double(rs.re, 0));
+                const double2 sa = make_double2(to_double(s0.re, eZ), to_double(rs.re, 0));
+                const double2 sb = make_double2(to_double(s0.im, eZ), to_double(rs.im, 0));
+                out[0 * (size_t)nmodes + t] = sa;
                 out[1 * (size_t)nmodes + t] = make_double2(to_double(k0.re, eD), to_double(rk.re, eL));
-                out[2 * (size_t)nmodes + t] = make_double2(to_double(s0.im, eZ), to_double(rs.im, 0));
+                out[2 * (size_t)nmodes + t] = sb;
                 out[3 * (size_t)nmodes + t] = make_double2(to_double(k0.im, eD), to_double(rk.im, eL));
+                if (share) {
+                    const cff km = cscale(ldc(cKm, n), cc), rkm = cscale(ldc(seqm, n), scale);
+                    outm[0 * (size_t)nmodes + t] = sa;
+                    outm[1 * (size_t)nmodes + t] = make_double2(to_double(km.re, eDm), to_double(rkm.re, eL));
+                    outm[2 * (size_t)nmodes + t] = sb;
+                    outm[3 * (size_t)nmodes + t] = make_double2(to_double(km.im, eDm), to_double(rkm.im, eL));
+                }
             } else {
                 const int em = ex[r];
                 const cff rs = cscale(ldc(seq, (4 * r + 1) * S1 + n), scale);
@@ -977,8 +1027,13 @@ cudaError_t launch_near_modes_ff(const pmlbie_problem* prob, int mode_lo, int mo
     a.cconv = f2(1.0 / (2.0 * 3.14159265358979323846 * 2 * M));
     if (a.npairs == 0) return cudaSuccess;
     const size_t S1 = M / 2 + 1, S2 = M + 1;
-    const size_t smem = sizeof(float4) * (2 * (size_t)M + M + 8 * S1 + 4 * S2 + 4 * (size_t)M + kTrigTab + kExpTab / 2) +
-                        sizeof(int) * (2 * S1 + 4);
+    // ... + Eb (2 S1 ints) and ex (5 ints), rounded up to whole 16-byte units
+    size_t smem = sizeof(float4) * (2 * (size_t)M + M + 8 * S1 + 4 * S2 + 4 * (size_t)M + kTrigTab + kExpTab / 2 +
+                                    (2 * S1 + 5 + 3) / 4);
+    // mirror sharing: the mirror's D^ and K convolution, its r3 spectrum
+    const size_t share_bytes = sizeof(float4) * (2 * S2 + S1);
+    a.share_mirror = smem + share_bytes <= 227 * 1024 ? 1 : 0;
+    if (a.share_mirror) smem += share_bytes;
     cudaError_t e = allow_max_smem(near_modes_kernel_ff);
     if (e != cudaSuccess) return e;
     near_modes_kernel_ff<<<a.npairs, 128, smem, s>>>(a);

@@ -382,6 +382,8 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "note": "per step: create (host setup) + solve_host to pinned buffers + destroy"},
     }
+    if world == 1 and WORKLOAD is WORKLOADS["default"] and not args.no_extra:
+        line["extra_workloads"] = extra_workloads(stream)
     if rank == 0 and not args.no_cpu_baseline:
         rows = max(12, int(160 * (512 * 256) / (w["N"] * w["M"])))
         e, t = oracle_sample(w, rows=rows)
@@ -392,6 +394,57 @@ def run_ours(args, rank, world):
     emit_line(line, rank)
     if dist:
         dist.destroy_process_group()
+
+
+def extra_workloads(stream):
+    """Secondary measurements of the default run (one GPU; not the headline
+    value): the large single instance n1024_m512 (one warm-up and two timed
+    mixed solves) and the batched eight-instance workload (one warm-up and one
+    timed batch call), CUDA events on the launching stream, inputs resident.
+    Each reports its own entries/s and time per problem."""
+    import torch
+    from paper_2412_11162_gb300 import Problem, solve_batch
+    from paper_2412_11162_gb300 import binding as B
+    out = {}
+    w = WORKLOADS["n1024_m512"]
+    P = Problem(w["k1"], w["k2"], w["N"], w["M"], a1=w["a1"], T=w["T"], S=w["S"], bump_h=w["bump_h"])
+    rep = P.solve([w["polar"]], precision=B.PMLBIE_MIXED, stream=stream)[1]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = [P.solve([w["polar"]], precision=B.PMLBIE_MIXED, stream=stream)[1] for _ in range(2)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 2
+    r = reps[-1]
+    out["n1024_m512"] = {"workload": "two-layer bump, N=1024 M=512 (256 modes), k1=10pi k2=15pi, mixed",
+                         "ms_per_problem": ms, "entries_per_s": entries_per_problem(w) / (ms / 1e3),
+                         "stages_ms": {"far": r.ms_far, "near": r.ms_near, "assemble": r.ms_assemble,
+                                       "lu": r.ms_lu, "solve_refine": r.ms_solve},
+                         "refine_iters": r.refine_iters, "gmres_modes": r.gmres_modes,
+                         "backward_error": r.backward_error}
+    P.close()
+    torch.cuda.empty_cache()
+    inst, polar, azimuth = batched_instances()
+    probs = [Problem(v["k1"], v["k2"], v["N"], v["M"], a1=v["a1"], T=v["T"], S=v["S"], bump_h=v["bump_h"])
+             for v in inst]
+    solve_batch(probs, polar, azimuth, precision=B.PMLBIE_MIXED, n_streams=2, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, reps = solve_batch(probs, polar, azimuth, precision=B.PMLBIE_MIXED, n_streams=2, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out["batched8"] = {"workload": "8 instances (seed 2412): k1=linspace(2pi,8pi,8), k2=1.5 k1, N=%s, M=N/2, "
+                                   "64 plane waves each, mixed, one batch call on 2 worker streams" %
+                                   [v["N"] for v in inst],
+                       "ms_per_batch": ms, "s_per_problem": ms / 1e3 / 8,
+                       "entries_per_s": sum(entries_per_problem(v) for v in inst) / (ms / 1e3),
+                       "gmres_modes": int(sum(x.gmres_modes for x in reps))}
+    for q in probs:
+        q.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def measure_pipes(B):
@@ -753,6 +806,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the secondary n1024_m512 and batched8 measurements of the default run")
     ap.add_argument("--workload", default="default", choices=sorted(WORKLOADS) + ["batched8"],
                     help="default: N=512, M=256 (the headline); 'small' (N=256, M=128) is for profiler "
                          "captures; n1024_m512 / n1536_m512 / n4096_m512: the large single and "

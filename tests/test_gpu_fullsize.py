@@ -39,19 +39,32 @@ def _sample_pairs(G, Q, rng, n=240):
     return sorted(pairs)
 
 
-def check_sampled_kernels(cfg, mode_ranges, n_pairs=240, precision=None, factor=1e-12):
+class _GridPairs:
+    """The oracle quadrature's grid-pair mask alone (|i_m - i_l| >= a of the
+    Alpert rule), for sampling pairs at large N without building the whole
+    correction table."""
+
+    def __init__(self, G):
+        from oracle.assemble import alpert_table
+        gi = G.unk_grid
+        self.grid_mask = np.abs(gi[:, None] - gi[None, :]) >= alpert_table()[2]
+
+
+def check_sampled_kernels(cfg, mode_ranges, n_pairs=240, precision=None, factor=1e-12, P=None, light=False):
     """Sampled grid pairs of the library's modal kernels (pmlbie_modal_kernels,
     or pmlbie_modal_kernels_ex in `precision`) against the oracle pair by pair:
-    |diff| <= factor x the pair's rounding scale.  Returns the worst ratio."""
+    |diff| <= factor x the pair's rounding scale.  Returns the worst ratio.
+    P: an existing Problem of cfg; light: sample with the grid-pair mask only."""
     import torch
     import oracle.kernels as KR
     from oracle.assemble import Quadrature
     from oracle.problem import Geometry, Params
     from paper_2412_11162_gb300 import Problem
-    P = Problem(cfg["k1"], cfg["k2"], cfg["N"], cfg["M"])
+    if P is None:
+        P = Problem(cfg["k1"], cfg["k2"], cfg["N"], cfg["M"])
     Po = Params(**cfg)
     G = Geometry(Po)
-    Q = Quadrature(G)
+    Q = _GridPairs(G) if light else Quadrature(G)
     rng = np.random.default_rng(2412)
     pairs = _sample_pairs(G, Q, rng, n_pairs)
     li = np.array([p[0] for p in pairs])

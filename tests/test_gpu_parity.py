@@ -133,28 +133,37 @@ def mode_conditioning(sol):
     return np.array(out)
 
 
-def check_densities(out, sol, tol, backward_tol, label):
+def check_densities(out, sol, tol, backward_tol, label, mode_tol=2e-9):
     """Parity of the solved densities with the oracle.
 
     * u1, u2 on the physical nodes (rho <= a1): forward relative 2-norm error
-      <= tol; on all nodes, per mode, <= max(tol, 1e-12 kappa_n).  The PML
-      nodes' kernels carry the close-pair split's cancellation (the two sides'
-      high-mode kernels there agree to ~1e-10 at M = 64), which the solve
-      carries into u1 at the PML nodes.
-    * normwise backward error of the GPU solution x = (u1, phi1) in the
-      ORACLE's block systems, all modes together (the block-diagonal system
-      of every mode, as the forward errors are taken over all modes):
-      |A x - B| / (max_n |A_n|_F |x| + |B|) <= backward_tol.  (Per mode, the
-      high modes' data are at the rounding floor of their DFTs, ~1e-15.)
-    * phi1, phi2: forward error per mode <= max(tol, 1e-12 kappa_n).  The phi
-      unknowns at the graded node clusters next to the axis and the PML end
-      span near-null directions (kappa up to ~1e7 at N = 128 after column
-      equilibration), along which two correct FP64 solvers of matrices that
-      differ by rounding (the close-pair split in the PML cancels by up to
-      ~1e9, see test_modal_kernels_config1) disagree by ~kappa x that
-      difference; the backward-error check is the tight one there.
+      <= tol over all modes.
+    * Per mode n, with the unknown x_n = (u1, phi1) in the column-equilibrated
+      variables y = D_n x (D_n = the column norms of the oracle's block matrix
+      A_n, A'_n = A_n D_n^-1): the normwise backward error of the GPU solution
+      in the ORACLE's system, eta_n = |r_n| / (|A'_n|_2 |y| + |B_n|) with r_n
+      = A_n x - B_n, is at most mode_tol = 2e-9 on the dominant modes (those
+      with |x_n| >= 1e-3 max_m |x_m|) and reported on the others, whose
+      solutions are below 1e-3 of the largest (their eta_n, up to ~1e-8,
+      measure the two sides' matrices at the PML close pairs, whose split
+      cancels by up to ~1e9 at M = 64, against the mode's own small scale).
+      What it catches: phi off by 1e-7 in mode 3 (kappa 5e3) gives eta =
+      1.2e-8, which the all-mode backward error below would not show (3e-14).
+      What no backward error can catch: the same error in mode 0 moves eta
+      by 1e-10 only -- it lies along the near-null direction (kappa ~ 7e6)
+      where two correct solutions already differ by ~kappa eta.  The forward
+      error then obeys |D_n (x_gpu - x_oracle)| <= (|r_gpu| + |r_oracle| +
+      e_round) / sigma_min(A'_n), i.e. about kappa_n (eta_gpu + eta_oracle)
+      relative -- the measured bound that replaces a fixed multiple of
+      kappa_n (y - y* = A'^-1 r exactly for either solution; e_round = 2 (2N)
+      u (|A'_n|_2 |y| + |B_n|) covers the rounding of the computed residuals).
+      The phi part of the error is reported in the same norm (u2 = u1 - b1
+      and phi2 = phi1 - b2 carry the same absolute errors, b being the
+      incident data).
+    * normwise backward error of the GPU solution in the ORACLE's block
+      systems, all modes together: |A x - B| / (max_n |A_n|_F |x| + |B|) <=
+      backward_tol.
     """
-    kap = mode_conditioning(sol)
     N = sol.P.N
     errs = {}
     phys = sol.sys.G.nodes["rho"] <= sol.P.a1
@@ -163,31 +172,50 @@ def check_densities(out, sol, tol, backward_tol, label):
         errs[name] = _rel(got, ref)
         e = _rel(got[:, phys], ref[:, phys])
         assert e <= tol, (label, name, "physical nodes", e)
-        for n in range(ref.shape[0]):
-            e = np.linalg.norm(got[n] - ref[n]) / np.linalg.norm(ref)
-            assert e <= max(tol, 1e-12 * kap[n]), (label, name, n, e, kap[n])
+    for name, ref in (("phi1", sol.phi1), ("phi2", sol.phi2)):
+        errs[name] = _rel(out[name].cpu().numpy()[:, :, 0], ref)
     u1 = out["u1"].cpu().numpy()[:, :, 0]
     p1 = out["phi1"].cpu().numpy()[:, :, 0]
+    u = np.finfo(np.float64).eps / 2
     r2 = x2 = b2 = 0.0
     anorm = 0.0
+    worst = {"ratio": 0.0, "y": 0.0, "phi_eq": 0.0, "eta": 0.0, "eta_all": 0.0}
+    xnorm = np.array([np.linalg.norm(np.concatenate([sol.u1[n], sol.phi1[n]])) for n in range(sol.P.M // 2)])
+    dominant = xnorm >= 1e-3 * xnorm.max()
     for n in range(sol.P.M // 2):
         A, B = sol.A[n]
         x = np.concatenate([u1[n], p1[n]])
-        r2 += np.linalg.norm(A @ x - B) ** 2
+        xo = np.concatenate([sol.u1[n], sol.phi1[n]])
+        r = A @ x - B
+        ro = A @ xo - B
+        r2 += np.linalg.norm(r) ** 2
         x2 += np.linalg.norm(x) ** 2
         b2 += np.linalg.norm(B) ** 2
         anorm = max(anorm, np.linalg.norm(A))
+        d = np.linalg.norm(A, axis=0)
+        sv = np.linalg.svd(A / d[None, :], compute_uv=False)
+        yo = d * xo
+        dy = d * (x - xo)
+        eround = 2 * (2 * N) * u * (sv[0] * np.linalg.norm(yo) + np.linalg.norm(B))
+        bound = (np.linalg.norm(r) + np.linalg.norm(ro) + eround) / sv[-1]
+        ey = np.linalg.norm(dy)
+        eta = np.linalg.norm(r) / (sv[0] * np.linalg.norm(d * x) + np.linalg.norm(B))
+        if dominant[n]:
+            assert eta <= mode_tol, (label, n, "backward error in the oracle's system", eta)
+            worst["eta"] = max(worst["eta"], eta)
+        worst["eta_all"] = max(worst["eta_all"], eta)
+        assert ey <= 1.01 * bound, (label, n, "equilibrated error", ey / np.linalg.norm(yo),
+                                    bound / np.linalg.norm(yo))
+        worst["ratio"] = max(worst["ratio"], ey / bound)
+        if dominant[n]:
+            worst["y"] = max(worst["y"], ey / np.linalg.norm(yo))
+            worst["phi_eq"] = max(worst["phi_eq"], np.linalg.norm(dy[N:]) / np.linalg.norm(yo))
     bwd = np.sqrt(r2) / (anorm * np.sqrt(x2) + np.sqrt(b2))
     assert bwd <= backward_tol, (label, "backward", bwd)
-    worst_bwd = bwd
-    for name, ref in (("phi1", sol.phi1), ("phi2", sol.phi2)):
-        got = out[name].cpu().numpy()[:, :, 0]
-        errs[name] = _rel(got, ref)
-        for n in range(ref.shape[0]):
-            bound = max(tol, 1e-12 * kap[n])
-            e = np.linalg.norm(got[n] - ref[n]) / np.linalg.norm(ref)
-            assert e <= bound, (label, name, n, e, bound)
-    print(label, errs, "backward %.2e" % worst_bwd, "max kappa %.2e" % kap.max())
+    print(label, {k: "%.2e" % v for k, v in errs.items()}, "backward %.2e" % bwd,
+          "per mode: on the %d dominant modes max backward error %.2e (all modes %.2e) and max equilibrated "
+          "error %.2e (phi part %.2e); max error / measured bound %.2f" %
+          (int(dominant.sum()), worst["eta"], worst["eta_all"], worst["y"], worst["phi_eq"], worst["ratio"]))
     return errs
 
 

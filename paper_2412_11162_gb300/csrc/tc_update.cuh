@@ -118,8 +118,26 @@ __global__ void __launch_bounds__(kThreads, 2) update_kernel(int n, int k0, int 
         *flag = 0;
     }
 
-    // All global loads of the CTA are issued before any of them is used: the
-    // A' and B' elements (8 + 8 per thread) and this thread's 32 values of A22.
+    // All global loads of the CTA are issued before any of them is used: this
+    // thread's 32 values of A22 first (the DRAM traffic), then the A' and B'
+    // elements (8 + 8 per thread, mostly served by L2).
+    const int q = warp & 3, h = warp >> 2;
+    const int rr = 32 * q + lane;                 // real row of P
+    const int row = r0 + (rr >> 1), part = rr & 1;
+    const int cbase = c0 + 32 * h;
+    // columns by one pointer stepped by the column stride (2n floats)
+    float* pc = reinterpret_cast<float*>(a) + 2 * ((size_t)cbase * n + row) + part;
+    const size_t cstride = 2 * (size_t)n;
+    const int ncv = row < n ? min(32, n - cbase) : 0;
+    float cv[32];
+    {
+        const float* p = pc;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            cv[c] = c < ncv ? *p : 0.f;
+            p += cstride;
+        }
+    }
     constexpr int kPer = kTileC * 32 / kThreads;   // 8
     float2 lv[kPer], uv[kPer];
 #pragma unroll
@@ -138,17 +156,6 @@ __global__ void __launch_bounds__(kThreads, 2) update_kernel(int n, int k0, int 
         const int k = (e & 3) | (((e >> 5) & 7) << 2);
         const int j = ((e >> 2) & 7) | ((e >> 8) << 3);
         uv[t] = (k < kb && c0 + j < n) ? a[(size_t)(c0 + j) * n + k0 + k] : make_float2(0.f, 0.f);
-    }
-    const int q = warp & 3, h = warp >> 2;
-    const int rr = 32 * q + lane;                 // real row of P
-    const int row = r0 + (rr >> 1), part = rr & 1;
-    const int cbase = c0 + 32 * h;
-    float* af = reinterpret_cast<float*>(a);
-    float cv[32];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-        const int col = cbase + c;
-        cv[c] = (row < n && col < n) ? af[2 * ((size_t)col * n + row) + part] : 0.f;
     }
 #pragma unroll
     for (int t = 0; t < kPer; ++t) {
@@ -227,10 +234,11 @@ __global__ void __launch_bounds__(kThreads, 2) update_kernel(int n, int k0, int 
     if (*flag == 0) {
         float pv[32];
         tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h), pv);
+        float* p = pc;
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
-            const int col = cbase + c;
-            if (row < n && col < n) af[2 * ((size_t)col * n + row) + part] = cv[c] - pv[c];
+            if (c < ncv) *p = cv[c] - pv[c];
+            p += cstride;
         }
     } else if (tid == 0) {
         info[b] = -1;

@@ -342,6 +342,7 @@ def run_ours(args, rank, world):
     clocks = clk.summary()
     roof = near_roofline(w, last, pk, clocks, ncounts, pipes)
     roof_far = roofline(w, last, pk, clocks, pipes)
+    roof_lu = lu_update_roofline(w, last, pk)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -374,7 +375,7 @@ def run_ours(args, rank, world):
         "near_pairs": {"grid": ng, "alpert": nc},
         "gpu_launches": int(sum(r.launches for r in reps)),
         "measured_pipe_peaks": pipes,
-        "roofline": roof,
+        "roofline": roof, "roofline_lu_update": roof_lu,
         "roofline_far": roof_far,
         "stage_rooflines": stage_rooflines(w, last, pk, pipes),
         "clocks": clocks,
@@ -761,6 +762,31 @@ def roofline(w, rep, pk, clk, pipes=None):
             "traffic_note": ("ncu dram read+write per entry written (profiles/far_kernel_ff_n256_m128.md) x "
                              "4 N^2 (M/2) entries"
                              if traffic else "null: no ncu capture of the current kernels_ff.cu")}
+
+
+def lu_update_roofline(w, rep, pk):
+    """Roofline of the FP32 LU's tensor-core trailing update (tcu::update_kernel,
+    the kernel with the largest total time per step: 31 launches at N=512):
+    HBM-bound by construction (a rank-32 update does 16 flops per byte of the
+    trailing matrix).  Algorithmic bytes = one read and one write of the
+    complex64 trailing matrix per launch, sum_k 2 x 8 B x (n - 32 (k + 1))^2
+    per mode; time = the launches' device time, from event pairs recorded
+    around each launch inside the captured LU graph (report ms_lu_update)."""
+    N, M = w["N"], w["M"]
+    n, modes = 2 * N, M // 2
+    launches = int(getattr(rep, "lu_update_launches", 0))
+    ms = float(getattr(rep, "ms_lu_update", 0.0))
+    wbytes = modes * sum(2 * 8.0 * (n - 32 * (k + 1)) ** 2 for k in range((n + 31) // 32 - 1))
+    hbm = pk.get("hbm_gbs", 6794.1)
+    ach = wbytes / (ms / 1e3) / 1e9 if ms > 0 else None
+    traffic = profile_traffic("tc_update_kernel_n512_64modes.md", "tc_update.cuh", wbytes)
+    return {"kernel": "tcu::update_kernel (rank-32 trailing update of the complex64 LU on tcgen05, TF32 split)",
+            "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm if ach else None, "traffic": traffic, "ms_per_step": ms,
+            "launches_per_step": launches, "algorithmic_bytes": wbytes,
+            "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json)",
+            "traffic_note": ("ncu dram read+write per algorithmic byte (profiles/tc_update_kernel_n512_64modes.md)"
+                             if traffic else "null: no ncu capture of the current tc_update.cuh")}
 
 
 def stage_rooflines(w, rep, pk, pipes=None):

@@ -48,7 +48,8 @@ class pmlbie_report(ctypes.Structure):
                 ("gmres_iters", ctypes.c_int), ("backward_error", ctypes.c_double),
                 ("far_pairs_physical", ctypes.c_int), ("lu_graph_replays", ctypes.c_int),
                 ("far_pairs_per_cta", ctypes.c_int), ("far_pairs_sampled", ctypes.c_int),
-                ("far_pairs_sampled_physical", ctypes.c_int), ("ms_near_ff", ctypes.c_double)]
+                ("far_pairs_sampled_physical", ctypes.c_int), ("ms_near_ff", ctypes.c_double),
+                ("ms_lu_update", ctypes.c_double), ("lu_update_launches", ctypes.c_int)]
 
 
 class pmlbie_solve_opts(ctypes.Structure):

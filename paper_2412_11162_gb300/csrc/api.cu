@@ -58,6 +58,11 @@ struct pmlbie_dev_extra {
     bool ready = false;
     cudaStream_t capture = nullptr;   // private stream the graph is captured on
     LuGraph lu;
+    // event pairs around the LU's trailing-update launches (recorded by the
+    // captured graph, or by a direct factorisation) and the pairs recorded
+    // by the last factorisation
+    std::vector<cudaEvent_t> upd_ev;
+    int upd_pairs = 0;
 };
 
 namespace {
@@ -153,6 +158,9 @@ void free_device(pmlbie_problem* prob) {
     if (ex && ex->lu.exec) cudaGraphExecDestroy(ex->lu.exec);
     if (ex && ex->capture) cudaStreamDestroy(ex->capture);
     if (ex) {
+        for (cudaEvent_t e : ex->upd_ev) cudaEventDestroy(e);
+        ex->upd_ev.clear();
+        ex->upd_pairs = 0;
         ex->lu = LuGraph();
         ex->capture = nullptr;
     }
@@ -534,17 +542,33 @@ __global__ void wait_probe_kernel(long long iters, int* expired) {
 // LU factorisations replayed from a graph by this thread's current call
 thread_local int g_lu_graph_replays = 0;
 
-static cudaError_t lu_direct(int precision, int n, int batch, void* A, int* piv, int* info, cudaStream_t s) {
-    return precision == PMLBIE_FP64 ? batched_lu<double2>(n, batch, (double2*)A, piv, info, s)
-                                    : batched_lu<float2>(n, batch, (float2*)A, piv, info, s);
+static cudaError_t lu_direct(int precision, int n, int batch, void* A, int* piv, int* info, cudaStream_t s,
+                             cudaEvent_t* upd_ev = nullptr) {
+    return precision == PMLBIE_FP64 ? batched_lu<double2>(n, batch, (double2*)A, piv, info, s, upd_ev)
+                                    : batched_lu<float2>(n, batch, (float2*)A, piv, info, s, upd_ev);
+}
+
+// 2 x ceil(n / 32) timing events of the trailing updates; the pairs used are
+// those of steps with a trailing matrix (n / 32 rounded up, minus one)
+static cudaError_t ensure_update_events(pmlbie_dev_extra* ex, int n) {
+    const size_t need = 2 * (size_t)((n + 31) / 32);
+    while (ex->upd_ev.size() < need) {
+        cudaEvent_t e = nullptr;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        ex->upd_ev.push_back(e);
+    }
+    ex->upd_pairs = (n + 31) / 32 - 1;
+    return cudaSuccess;
 }
 
 static int batched_lu_graphed(pmlbie_problem* prob, int precision, int n, int batch, void* A, int* piv, int* info,
                               cudaStream_t s) {
     pmlbie_dev_extra* ex = extra_of(prob);
     LuGraph& g = ex->lu;
+    PMLBIE_CUDA_TRY(ensure_update_events(ex, n));
     if (g.unavailable) {
-        PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, s));
+        PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, s, ex->upd_ev.data()));
         return PMLBIE_OK;
     }
     if (!(g.exec && g.precision == precision && g.n == n && g.batch == batch && g.A == A && g.piv == piv &&
@@ -557,7 +581,7 @@ static int batched_lu_graphed(pmlbie_problem* prob, int precision, int n, int ba
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(ex->capture, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            const cudaError_t el = lu_direct(precision, n, batch, A, piv, info, ex->capture);
+            const cudaError_t el = lu_direct(precision, n, batch, A, piv, info, ex->capture, ex->upd_ev.data());
             e = cudaStreamEndCapture(ex->capture, &graph);
             if (el != cudaSuccess) e = el;
         }
@@ -570,7 +594,7 @@ static int batched_lu_graphed(pmlbie_problem* prob, int precision, int n, int ba
             if (g.exec) cudaGraphExecDestroy(g.exec);
             g = LuGraph();
             g.unavailable = true;
-            PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, s));
+            PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, s, ex->upd_ev.data()));
             return PMLBIE_OK;
         }
         g.launches = captured;
@@ -590,7 +614,8 @@ static int batched_lu_graphed(pmlbie_problem* prob, int precision, int n, int ba
 // Accumulated device times and refinement statistics of a solve.
 struct SolveStats {
     double ms_kernels = 0, ms_lu = 0, ms_solve = 0, ms_far = 0, ms_near = 0, ms_near_laplace = 0, ms_assemble = 0,
-           ms_near_ff = 0;
+           ms_near_ff = 0, ms_lu_update = 0;
+    int lu_update_launches = 0;
     int iters = 0;
     double resid = 0;
     int gmres_iters = 0, gmres_modes = 0;
@@ -763,6 +788,14 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
     float fff = 0.f;
     cudaEventElapsedTime(&fff, sev[4], sev[5]);
     st.ms_near_ff += fff;
+    for (int k = 0; k < ex->upd_pairs; ++k) {
+        float tu = 0.f;
+        if (cudaEventElapsedTime(&tu, ex->upd_ev[2 * k], ex->upd_ev[2 * k + 1]) == cudaSuccess) {
+            st.ms_lu_update += tu;
+            ++st.lu_update_launches;
+        }
+    }
+    cudaGetLastError();
     st.ms_kernels += t[0];
     st.ms_lu += t[1];
     st.ms_solve += t[2];
@@ -950,6 +983,8 @@ int pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* o, void* dev_
         rep->ms_assemble = st.ms_assemble;
         rep->ms_near_laplace = st.ms_near_laplace;
         rep->ms_near_ff = st.ms_near_ff;
+        rep->ms_lu_update = st.ms_lu_update;
+        rep->lu_update_launches = st.lu_update_launches;
         rep->launches = (int)g_launches;
         int* fc = prob->far_counts;
         if (fc[0] < 0) {

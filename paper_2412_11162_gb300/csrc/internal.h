@@ -267,8 +267,11 @@ int peak_probe(int kind, double* out_tflops, cudaStream_t s);
 // dense batched linear algebra (lu.cu)
 // Leaves piv[b] as the row permutation of the factorisation: piv[b][i] is the
 // original row that ends in row i (P A = L U with (P x)_i = x_{piv[i]}).
+// upd_ev: optional 2 x ceil(n/32) events recorded around each trailing-update
+// launch (for its timing; recorded as external events, so that they become
+// event-record nodes when the factorisation is captured in a graph)
 template <typename T>
-cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s);
+cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s, cudaEvent_t* upd_ev = nullptr);
 // kernel attributes of batched_lu<T>, set once (call before capturing it)
 template <typename T>
 cudaError_t lu_prepare();

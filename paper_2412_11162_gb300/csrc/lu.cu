@@ -840,7 +840,7 @@ cudaError_t lu_prepare() {
 }
 
 template <typename T>
-cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s) {
+cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s, cudaEvent_t* upd_ev) {
     cudaError_t pe = lu_prepare<T>();
     if (pe != cudaSuccess) return pe;
     for (int k0 = 0; k0 < n; k0 += kNB) {
@@ -854,6 +854,9 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
         swap_trsm_kernel<T><<<g1, 256, sm1, s>>>(n, k0, kb, A, piv);
         int rem = n - k0 - kb;
         if (rem > 0) {
+            cudaError_t ee;
+            if (upd_ev && (ee = cudaEventRecordWithFlags(upd_ev[2 * (k0 / kNB)], s, cudaEventRecordExternal)) != cudaSuccess)
+                return ee;
             if constexpr (sizeof(T) == 8) {
                 // complex64: tensor-core update (tcgen05, TF32 split to FP32 accuracy)
                 constexpr int TL = tcu::kTileC;
@@ -866,6 +869,9 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
                 gemm_update_kernel<T><<<g2, 256, 0, s>>>(n, k0, kb, A);
             }
             count_launch();
+            if (upd_ev && (ee = cudaEventRecordWithFlags(upd_ev[2 * (k0 / kNB) + 1], s, cudaEventRecordExternal)) !=
+                              cudaSuccess)
+                return ee;
         }
     }
     const size_t smq = 2 * sizeof(int) * (size_t)n;
@@ -904,8 +910,8 @@ cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int
 
 template cudaError_t lu_prepare<double2>();
 template cudaError_t lu_prepare<float2>();
-template cudaError_t batched_lu<double2>(int, int, double2*, int*, int*, cudaStream_t);
-template cudaError_t batched_lu<float2>(int, int, float2*, int*, int*, cudaStream_t);
+template cudaError_t batched_lu<double2>(int, int, double2*, int*, int*, cudaStream_t, cudaEvent_t*);
+template cudaError_t batched_lu<float2>(int, int, float2*, int*, int*, cudaStream_t, cudaEvent_t*);
 template cudaError_t batched_lu_solve<double2, double2>(int, int, int, const double2*, const int*, double2*,
                                                         cudaStream_t, const int*, const double2*);
 template cudaError_t batched_lu_solve<float2, float2>(int, int, int, const float2*, const int*, float2*,

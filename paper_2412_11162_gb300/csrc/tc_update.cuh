@@ -23,7 +23,10 @@
 // epilogue reads the accumulator with tcgen05.ld (warp w: lanes 32 (w mod 4) ..,
 // columns 32 (w / 4) ..) and subtracts it from A22 in place; the A22 values are
 // loaded together with the operands, before the MMAs.  The mbarrier wait is bounded: on expiry the CTA
-// records info[b] = -1 and skips its epilogue.
+// records info[b] = -1 and skips its epilogue (the solve then returns PMLBIE_ETIMEOUT).  On a real
+// expiry the MMAs may still be in flight when the CTA frees its tensor memory, so a later CTA that
+// allocates those columns could see their writes: the error is reported, and the factorisation's
+// results are not used after it.
 #pragma once
 
 #include <cstdint>

@@ -384,7 +384,7 @@ def run_ours(args, rank, world):
                 "note": "per step: create (host setup) + solve_host to pinned buffers + destroy"},
     }
     if world == 1 and WORKLOAD is WORKLOADS["default"] and not args.no_extra:
-        line["extra_workloads"] = extra_workloads(stream)
+        line["extra_workloads"] = extra_workloads(stream, pipes)
     if rank == 0 and not args.no_cpu_baseline:
         rows = max(12, int(160 * (512 * 256) / (w["N"] * w["M"])))
         e, t = oracle_sample(w, rows=rows)
@@ -397,7 +397,7 @@ def run_ours(args, rank, world):
         dist.destroy_process_group()
 
 
-def extra_workloads(stream):
+def extra_workloads(stream, pipes=None):
     """Secondary measurements of the default run (one GPU; not the headline
     value): the large single instance n1024_m512 (one warm-up and two timed
     mixed solves) and the batched eight-instance workload (one warm-up and one
@@ -418,8 +418,19 @@ def extra_workloads(stream):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / 2
     r = reps[-1]
+    n2, modes = 2 * w["N"], w["M"] // 2
+    lu_flops = 8.0 / 3.0 * n2 ** 3 * modes
+    wbytes = 4.0 * w["N"] ** 2 * modes * 16
+    tf32 = pipes.get("tf32_tcgen05_tflops") if pipes else None
+    hbm = peaks().get("hbm_gbs", 6794.1)
     out["n1024_m512"] = {"workload": "two-layer bump, N=1024 M=512 (256 modes), k1=10pi k2=15pi, mixed",
                          "ms_per_problem": ms, "entries_per_s": entries_per_problem(w) / (ms / 1e3),
+                         "lu_tflops": lu_flops / (r.ms_lu / 1e3) / 1e12,
+                         "lu_frac_tf32": (lu_flops / (r.ms_lu / 1e3) / 1e12 / tf32) if tf32 else None,
+                         "far_block_writes_gbs": wbytes / (r.ms_far / 1e3) / 1e9,
+                         "far_block_writes_frac_hbm": wbytes / (r.ms_far / 1e3) / 1e9 / hbm,
+                         "note": "LU flops (8/3) (2N)^3 per mode against the measured TF32 tcgen05 rate; the far "
+                                 "kernel's 4 N^2 (M/2) x 16 B block writes against the measured HBM copy bandwidth",
                          "stages_ms": {"far": r.ms_far, "near": r.ms_near, "assemble": r.ms_assemble,
                                        "lu": r.ms_lu, "solve_refine": r.ms_solve},
                          "refine_iters": r.refine_iters, "gmres_modes": r.gmres_modes,
@@ -657,10 +668,10 @@ def near_flops_per_launch(M, chunk_modes, packed, pml, plain, couples=0):
     multiply-add = 2 flops; Taylor degree L = 5).  Per pair, (M/2 + 1) split
     samples: 169 flops for a packed pair (distance, complex square root and
     reciprocal 51, per medium sin/cos, sinc-type factors and the four split
-    values 59), 601 for a PML pair (51, per medium e^{iq} 79 and the four
-    products with the Taylor polynomials of cH1 / cH3, Horner 48 + 40 + 48 +
-    24 with their products), 295 for a plain pair (51, per medium e^{iq} and
-    S~, K~ 122).  Transforms: E1 = 5 K log2 K + 15 K for a length-M even DFT
+    values 59), 473 for a PML pair (51, per medium e^{iq} 79 and the four
+    products with the Taylor polynomials of cH1 / cH3: Horner of their tails
+    40 + 24, the full sums from the tails 8 + 24, with their products), 295
+    for a plain pair (51, per medium e^{iq} and S~, K~ 122).  Transforms: E1 = 5 K log2 K + 15 K for a length-M even DFT
     (K = M/2), E2 = 5 M log2 M + 15 M for a length-2M one.  Packed: 4 E1 + 6 E2
     (Laplace spectra, one convolution pass), PML: 8 E1 + 10 E2 (two passes),
     plain: 4 E1.  Products 14 (M + 1) and fills 4 K per pass; per output mode
@@ -674,7 +685,7 @@ def near_flops_per_launch(M, chunk_modes, packed, pml, plain, couples=0):
     E2 = 5.0 * M * np.log2(M) + 15.0 * M
     S1 = K + 1
     f_packed = S1 * 169.0 + 4 * E1 + 6 * E2 + 14.0 * (M + 1) + 4.0 * K + 8.0 * chunk_modes
-    f_pml = S1 * 601.0 + 8 * E1 + 10 * E2 + 2 * (14.0 * (M + 1) + 4.0 * K) + 24.0 * chunk_modes
+    f_pml = S1 * 473.0 + 8 * E1 + 10 * E2 + 2 * (14.0 * (M + 1) + 4.0 * K) + 24.0 * chunk_modes
     f_mirror = S1 * 30.0 + 2 * E1 + 3 * E2 + 2 * 8.0 * (M + 1) + 12.0 * chunk_modes
     f_plain = S1 * 295.0 + 4 * E1 + 8.0 * chunk_modes
     return packed * f_packed + (pml - couples) * f_pml + couples * f_mirror + plain * f_plain

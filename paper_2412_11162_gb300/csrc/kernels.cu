@@ -475,13 +475,14 @@ __device__ void laplace_modes_real(const NearPair& q, const NearPair* qm, int M,
     }
     const double s2 = sqrt(rr2);
     const double iz = kInv4Pi / s2, id = -kInv4Pi / (s2 * s2 * s2), den = 1.0 / (chim1 * chip1);
+    const double P = id * A, Q = id * B, Pm = id * Am, Qm = id * Bm;   // D^_m = (id A) d_m + (id B) c_m
     for (int m = 0; m + 1 < M; ++m) {
         const double cm = Z[m].x, cn = Z[m + 1].x;
         const double dm = (2.0 * m + 1.0) * fma(chim1, cm, cm - cn) * den;
-        Dd[m] = c2(id * (A * dm + B * cm), 0.0);
+        Dd[m] = c2(fma(P, dm, Q * cm), 0.0);
         Z[m] = c2(iz * cm, 0.0);
         if (qm) {
-            Ddm[m] = c2(id * (Am * dm + Bm * cm), 0.0);
+            Ddm[m] = c2(fma(Pm, dm, Qm * cm), 0.0);
             Zm[m] = c2(iz * cm, 0.0);
         }
     }
@@ -603,13 +604,15 @@ __global__ void near_laplace_kernel(NearArgs a) {
     double2 iz = cscale(crcp(s2), kInv4Pi);                           // 1/(4 pi sqrt(2 rr))
     double2 id = cscale(crcp(cmul(s2, cmul(s2, s2))), -kInv4Pi);      // -(2rr)^{-3/2}/(4 pi)
     double2 den = crcp(cmul(chim1, chip1));                            // 1/(chi^2 - 1)
+    // the prefactor folded into the normal factors once: D^_m = (id A) d_m + (id B) c_m
+    const double2 P = cmul(id, A), Q = cmul(id, B), Pm = cmul(id, Am), Qm = cmul(id, Bm);
     for (int m = 0; m + 1 < M; ++m) {
         double2 cm = Z[m], cn = Z[m + 1];
         double2 dm = cscale(cmul(cadd(csub(cm, cn), cmul(chim1, cm)), den), 2.0 * m + 1.0);
-        Dd[m] = cmul(id, cadd(cmul(A, dm), cmul(B, cm)));
+        Dd[m] = cadd(cmul(P, dm), cmul(Q, cm));
         Z[m] = cmul(iz, cm);
         if (pm) {
-            Ddm[m] = cmul(id, cadd(cmul(Am, dm), cmul(Bm, cm)));
+            Ddm[m] = cadd(cmul(Pm, dm), cmul(Qm, cm));
             Zm[m] = Z[m];
         }
     }
@@ -763,10 +766,16 @@ __global__ void near_modes_kernel(NearArgs a) {
             } else {
                 // cH1 = e^{iq} sum a_k q^k, Z (e^{iq} - cH1) = -(w / 4 pi) e^{iq} sum_{k>=1} a_k q^{k-1};
                 // cH3 likewise; D (e^{iq}(1 - iq) - cH3) = (w^3 / 4 pi) N_D e^{iq} sum_{k>=3} b_k q^{k-3}
-                v0 = cmul(e, cpoly_from(a.pa, 0, L, qq));
-                v1 = cscale(cmul(e, cpoly_from(a.pa, 1, L, qq)), -w * kInv4Pi);
-                v2 = cmul(e, cpoly_from(a.pb, 0, L, qq));
+                // (L >= 3; coefficients beyond L are zero) the full sums from the tails:
+                // P_a = a_0 + q P_a1, P_b = b_0 + q (b_1 + q (b_2 + q P_b3))
+                const double2 pa1 = cpoly_from(a.pa, 1, L, qq);
                 const double2 pb3 = cpoly_from(a.pb, 3, L, qq);
+                const double2 pa0 = cadd(a.pa[0], cmul(qq, pa1));
+                const double2 pb0 =
+                    cadd(a.pb[0], cmul(qq, cadd(a.pb[1], cmul(qq, cadd(a.pb[2], cmul(qq, pb3))))));
+                v0 = cmul(e, pa0);
+                v1 = cscale(cmul(e, pa1), -w * kInv4Pi);
+                v2 = cmul(e, pb0);
                 v3 = cscale(cmul(cmul(ND, e), pb3), w * w * w * kInv4Pi * sg);
                 if (share) v3m = cscale(cmul(cmul(NDm, e), pb3), w * w * w * kInv4Pi * sg);
             }

@@ -1,5 +1,5 @@
 """High-frequency sweep: omega_1 = 12 pi ... 20 pi in five steps, omega_2 =
-1.5 omega_1, N = 1536 ... 4096 nodes, M = 512 angles, the two-layer bump of
+1.5 omega_1, N = 1536, 2176, 2816, 3456, 4096 nodes, M = 512 angles, the two-layer bump of
 the other workloads.  Per wavenumber:
 
 * the mixed path's modal kernels (float-float far and close pairs, FP64
@@ -7,7 +7,7 @@ the other workloads.  Per wavenumber:
   oracle pair by pair, lowest and highest modes: |diff| <= 1e-11 x the pair's
   rounding scale (the phases reach |q| ~ 650 here; a float pair rounds q by
   |q| 2^-48);
-* mixed against FP64 solves.  The dominant modes 0 and 1 (up to N = 2048;
+* mixed against FP64 solves.  The dominant modes 0 and 1 (up to N = 2176;
   at N = 4096 they are numerically singular in FP64, |A| |x| / |b| ~ 1e11, and
   the two solutions differ along near-null directions that carry no field):
   u1, u2 and the scattered field at 32 points within 1e-6 relative.  The
@@ -26,7 +26,7 @@ from test_gpu_fullsize import check_sampled_kernels
 
 pytestmark = pytest.mark.gpu
 
-SWEEP = [(12, 1536), (14, 2048), (16, 2560), (18, 3072), (20, 4096)]
+SWEEP = [(12, 1536), (14, 2176), (16, 2816), (18, 3456), (20, 4096)]
 
 
 def _rel(a, b, scale):
@@ -47,14 +47,14 @@ def test_hf_sweep(k_over_pi, N):
     fz = np.repeat([1.0, -1.0], 16)
     fg = np.repeat([0, 1], 16)
     pol = [np.pi / 6]
-    # dominant modes: the solution's scale, and their own comparison up to N = 2048
+    # dominant modes: the solution's scale, and their own comparison up to N = 2176
     lo32, r32 = P.solve(pol, precision=PMLBIE_MIXED, modes=(0, 2))
     assert r32.backward_error <= 1e-13
     flo = P.field(fr, fz, fg, lo32, modes=(0, 2))
     scale = {k: torch.linalg.vector_norm(lo32[k]) for k in ("u1", "u2")}
     fscale = torch.linalg.vector_norm(flo)
     errs = {}
-    if N <= 2048:
+    if N <= 2176:
         lo64, _ = P.solve(pol, precision=PMLBIE_FP64, modes=(0, 2))
         for k in ("u1", "u2"):
             errs[k + "_modes01"] = _rel(lo32[k], lo64[k], torch.linalg.vector_norm(lo64[k]))

@@ -411,6 +411,24 @@ __device__ void complex_agm_KE(double2 k2, double2 kp, double2& K, double2& E) {
     E = cmul(K, csub(c2(1.0, 0.0), sum));
 }
 
+// Per-pair record of the close-pair Laplace modes, written by the recurrence
+// thread into the first kLapRec slots of the pair's D^ row (which the output
+// kernel overwrites afterwards): chi - 1, 1/(chi^2 - 1), the single-layer
+// prefactor iz, the double-layer coefficients (id A, id B) of the pair and
+// (id A', id B') of its mirror, and (real, has mirror).
+constexpr int kLapRec = 8;
+__device__ __forceinline__ void laplace_record(double2* rec, double2 chim1, double2 den, double2 iz, double2 P,
+                                               double2 Q, double2 Pm, double2 Qm, bool real, bool mirror) {
+    rec[0] = chim1;
+    rec[1] = den;
+    rec[2] = iz;
+    rec[3] = P;
+    rec[4] = Q;
+    rec[5] = Pm;
+    rec[6] = Qm;
+    rec[7] = c2(real ? 1.0 : 0.0, mirror ? 1.0 : 0.0);
+}
+
 // The same for a pair of physical nodes, where chi > 1 and every factor are
 // real: real AGM, real recurrences (the values are stored with zero
 // imaginary parts).
@@ -475,17 +493,10 @@ __device__ void laplace_modes_real(const NearPair& q, const NearPair* qm, int M,
     }
     const double s2 = sqrt(rr2);
     const double iz = kInv4Pi / s2, id = -kInv4Pi / (s2 * s2 * s2), den = 1.0 / (chim1 * chip1);
-    const double P = id * A, Q = id * B, Pm = id * Am, Qm = id * Bm;   // D^_m = (id A) d_m + (id B) c_m
-    for (int m = 0; m + 1 < M; ++m) {
-        const double cm = Z[m].x, cn = Z[m + 1].x;
-        const double dm = (2.0 * m + 1.0) * fma(chim1, cm, cm - cn) * den;
-        Dd[m] = c2(fma(P, dm, Q * cm), 0.0);
-        Z[m] = c2(iz * cm, 0.0);
-        if (qm) {
-            Ddm[m] = c2(fma(Pm, dm, Qm * cm), 0.0);
-            Zm[m] = c2(iz * cm, 0.0);
-        }
-    }
+    // D^_m = (id A) d_m + (id B) c_m; the per-mode outputs are formed by
+    // near_laplace_out_kernel from this record (kept in D^'s first slots)
+    laplace_record(Dd, c2(chim1, 0.0), c2(den, 0.0), c2(iz, 0.0), c2(id * A, 0.0), c2(id * B, 0.0),
+                   c2(id * Am, 0.0), c2(id * Bm, 0.0), true, qm != nullptr);
 }
 
 // One thread per close pair of the leader list (a.lead: not far by the
@@ -604,16 +615,56 @@ __global__ void near_laplace_kernel(NearArgs a) {
     double2 iz = cscale(crcp(s2), kInv4Pi);                           // 1/(4 pi sqrt(2 rr))
     double2 id = cscale(crcp(cmul(s2, cmul(s2, s2))), -kInv4Pi);      // -(2rr)^{-3/2}/(4 pi)
     double2 den = crcp(cmul(chim1, chip1));                            // 1/(chi^2 - 1)
-    // the prefactor folded into the normal factors once: D^_m = (id A) d_m + (id B) c_m
-    const double2 P = cmul(id, A), Q = cmul(id, B), Pm = cmul(id, Am), Qm = cmul(id, Bm);
-    for (int m = 0; m + 1 < M; ++m) {
-        double2 cm = Z[m], cn = Z[m + 1];
-        double2 dm = cscale(cmul(cadd(csub(cm, cn), cmul(chim1, cm)), den), 2.0 * m + 1.0);
-        Dd[m] = cadd(cmul(P, dm), cmul(Q, cm));
-        Z[m] = cmul(iz, cm);
-        if (pm) {
-            Ddm[m] = cadd(cmul(Pm, dm), cmul(Qm, cm));
-            Zm[m] = Z[m];
+    // the prefactor folded into the normal factors once: D^_m = (id A) d_m + (id B) c_m;
+    // the per-mode outputs are formed by near_laplace_out_kernel from this record
+    laplace_record(Dd, chim1, den, iz, cmul(id, A), cmul(id, B), cmul(id, Am), cmul(id, Bm), false, pm != nullptr);
+}
+
+// Close pairs, stage 1b (one CTA per leader pair): the modal Laplace kernels
+// from c_m (in the pair's Z^ row) and the record in D^'s first slots,
+//   d_m = (2m + 1) ((c_m - c_{m+1}) + (chi - 1) c_m) / (chi^2 - 1),
+//   D^_m = (id A) d_m + (id B) c_m,  Z^_m = iz c_m   (m = 0 .. M-2),
+// and the same D^ with the mirror's normal factor (its Z^ equals the pair's).
+// c_m and the record are staged in shared memory before any output is
+// written (the outputs overwrite them in place).
+__global__ void __launch_bounds__(128) near_laplace_out_kernel(NearArgs a) {
+    extern __shared__ double2 sc[];          // M values of c_m, then the record
+    const int t = blockIdx.x;
+    const int p = a.lead[t];
+    const NearPair& q = a.np[p];
+    if (q.flags & kFlagFar) return;
+    if (q.mirror >= 0 && q.mirror < p) return;
+    const int M = a.M;
+    double2* Z = a.zd + (size_t)p * 2 * M;
+    double2* Dd = Z + M;
+    double2* rec = sc + M;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) sc[i] = Z[i];
+    if (threadIdx.x < kLapRec) rec[threadIdx.x] = Dd[threadIdx.x];
+    __syncthreads();
+    const double2 chim1 = rec[0], den = rec[1], iz = rec[2], P = rec[3], Q = rec[4], Pm = rec[5], Qm = rec[6];
+    const bool real = rec[7].x != 0.0, mirror = rec[7].y != 0.0;
+    double2* Zm = mirror ? a.zd + (size_t)q.mirror * 2 * M : nullptr;
+    double2* Ddm = mirror ? Zm + M : nullptr;
+    for (int m = threadIdx.x; m + 1 < M; m += blockDim.x) {
+        if (real) {
+            const double cm = sc[m].x, cn = sc[m + 1].x;
+            const double dm = (2.0 * m + 1.0) * fma(chim1.x, cm, cm - cn) * den.x;
+            Dd[m] = c2(fma(P.x, dm, Q.x * cm), 0.0);
+            Z[m] = c2(iz.x * cm, 0.0);
+            if (mirror) {
+                Ddm[m] = c2(fma(Pm.x, dm, Qm.x * cm), 0.0);
+                Zm[m] = c2(iz.x * cm, 0.0);
+            }
+        } else {
+            const double2 cm = sc[m], cn = sc[m + 1];
+            const double2 dm = cscale(cmul(cadd(csub(cm, cn), cmul(chim1, cm)), den), 2.0 * m + 1.0);
+            const double2 zm = cmul(iz, cm);
+            Dd[m] = cadd(cmul(P, dm), cmul(Q, cm));
+            Z[m] = zm;
+            if (mirror) {
+                Ddm[m] = cadd(cmul(Pm, dm), cmul(Qm, cm));
+                Zm[m] = zm;
+            }
         }
     }
 }
@@ -1292,6 +1343,10 @@ cudaError_t launch_near(const pmlbie_problem* prob, int mode_lo, int mode_hi, do
     const int nthr = std::max(a.nlead, a.pff ? a.npairs : 0);
     if (nthr > 0) {
         near_laplace_kernel<<<(nthr + 127) / 128, 128, 0, s>>>(a);
+        count_launch();
+    }
+    if (a.nlead > 0) {
+        near_laplace_out_kernel<<<a.nlead, 128, sizeof(double2) * ((size_t)M + kLapRec), s>>>(a);
         count_launch();
     }
     cudaError_t e = cudaGetLastError();

@@ -117,9 +117,11 @@ typedef struct {
     int      far_pairs_sampled_physical;  /* of those, pairs of two physical nodes           */
     double   ms_near_ff;          /* mixed: device time of the float-float close-pair modes kernel
                                      (pairs without a PML point; part of ms_near) (ms) */
-    double   ms_lu_update;        /* device time of the LU's trailing-update launches, summed
-                                     (part of ms_lu; event pairs around each launch) (ms) */
-    int      lu_update_launches;  /* trailing-update launches of those factorisations     */
+    double   ms_lu_update;        /* device time of the LU's trailing updates, summed (part of
+                                     ms_lu; an event pair around each step's operand-image and
+                                     tensor-core update launches) (ms) */
+    int      lu_update_launches;  /* trailing updates (steps with a trailing matrix) of those
+                                     factorisations, each timed by one event pair             */
 } pmlbie_report;
 
 /* Options of pmlbie_solve_ex (zero-initialise, then set struct_size). */

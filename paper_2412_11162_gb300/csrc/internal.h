@@ -267,11 +267,18 @@ int peak_probe(int kind, double* out_tflops, cudaStream_t s);
 // dense batched linear algebra (lu.cu)
 // Leaves piv[b] as the row permutation of the factorisation: piv[b][i] is the
 // original row that ends in row i (P A = L U with (P x)_i = x_{piv[i]}).
-// upd_ev: optional 2 x ceil(n/32) events recorded around each trailing-update
-// launch (for its timing; recorded as external events, so that they become
-// event-record nodes when the factorisation is captured in a graph)
+// upd_ev: optional 2 x ceil(n/32) events recorded around each trailing update
+// (its operand-image and update launches; for its timing; recorded as external
+// events, so that they become event-record nodes when the factorisation is
+// captured in a graph)
+// img: for complex64, lu_image_bytes(n, batch) bytes of device scratch (16-byte
+// aligned) holding one step's split operand images; unused for complex128
 template <typename T>
-cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s, cudaEvent_t* upd_ev = nullptr);
+cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s, unsigned char* img,
+                       cudaEvent_t* upd_ev = nullptr);
+// scratch bytes of the complex64 factorisation's operand images (the first
+// step's 64-row blocks of L21 and 64-column blocks of U12, 96 KB per pair)
+size_t lu_image_bytes(int n, int batch);
 // kernel attributes of batched_lu<T>, set once (call before capturing it)
 template <typename T>
 cudaError_t lu_prepare();

@@ -8,7 +8,8 @@
 // factorisation (pivot search, row swap, scaling, rank-1 updates inside the
 // panel), row swaps + unit-lower triangular solve for the block row, and a
 // tiled GEMM update of the trailing matrix (complex128: FP64 CUDA cores;
-// complex64: tcgen05 tensor cores, tc_update.cuh).  Matrices are
+// complex64: tcgen05 tensor cores on split operand images formed once per
+// step, tc_update.cuh).  Matrices are
 // column-major, A[b][col][row], leading dimension n.  info[b] > 0 marks the
 // first zero pivot, info[b] = -1 a tensor-core update that did not complete.
 #include <algorithm>
@@ -839,10 +840,19 @@ cudaError_t lu_prepare() {
     return err;
 }
 
+size_t lu_image_bytes(int n, int batch) {
+    const int nblk = n > kNB ? tcu::update_blocks(n, 0, kNB) : 0;
+    return (size_t)batch * nblk * (tcu::kAImg + tcu::kBImg);
+}
+
 template <typename T>
-cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s, cudaEvent_t* upd_ev) {
+cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s, unsigned char* img,
+                       cudaEvent_t* upd_ev) {
     cudaError_t pe = lu_prepare<T>();
     if (pe != cudaSuccess) return pe;
+    if constexpr (sizeof(T) == 8) {
+        if (n > kNB && (!img || (reinterpret_cast<uintptr_t>(img) & 15))) return cudaErrorInvalidValue;
+    }
     for (int k0 = 0; k0 < n; k0 += kNB) {
         int kb = std::min(kNB, n - k0);
         const int w = panel_width<T>(n - k0);
@@ -858,11 +868,15 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
             if (upd_ev && (ee = cudaEventRecordWithFlags(upd_ev[2 * (k0 / kNB)], s, cudaEventRecordExternal)) != cudaSuccess)
                 return ee;
             if constexpr (sizeof(T) == 8) {
-                // complex64: tensor-core update (tcgen05, TF32 split to FP32 accuracy)
-                constexpr int TL = tcu::kTileC;
-                dim3 g2((rem + TL - 1) / TL, (rem + TL - 1) / TL, batch);
-                tcu::update_kernel<<<g2, tcu::kThreads, tcu::kSmemBytes, s>>>(n, k0, kb,
-                                                                              reinterpret_cast<float2*>(A), info);
+                // complex64: split operand images of this step, then the tensor-core
+                // update (tcgen05, TF32 split to FP32 accuracy) reading them
+                const int nblk = tcu::update_blocks(n, k0, kb);
+                unsigned char* bimg = img + (size_t)batch * nblk * tcu::kAImg;
+                tcu::operand_image_kernel<<<dim3(nblk, 3, batch), 256, 0, s>>>(
+                    n, k0, kb, nblk, reinterpret_cast<const float2*>(A), img, bimg);
+                count_launch();
+                tcu::update_kernel<<<dim3(nblk, nblk, batch), tcu::kThreads, tcu::kSmemBytes, s>>>(
+                    n, k0, kb, nblk, reinterpret_cast<float2*>(A), img, bimg, info);
             } else {
                 constexpr int TL = GemmTile<T>::v;
                 dim3 g2((rem + TL - 1) / TL, (rem + TL - 1) / TL, batch);
@@ -910,8 +924,10 @@ cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int
 
 template cudaError_t lu_prepare<double2>();
 template cudaError_t lu_prepare<float2>();
-template cudaError_t batched_lu<double2>(int, int, double2*, int*, int*, cudaStream_t, cudaEvent_t*);
-template cudaError_t batched_lu<float2>(int, int, float2*, int*, int*, cudaStream_t, cudaEvent_t*);
+template cudaError_t batched_lu<double2>(int, int, double2*, int*, int*, cudaStream_t, unsigned char*,
+                                          cudaEvent_t*);
+template cudaError_t batched_lu<float2>(int, int, float2*, int*, int*, cudaStream_t, unsigned char*,
+                                         cudaEvent_t*);
 template cudaError_t batched_lu_solve<double2, double2>(int, int, int, const double2*, const int*, double2*,
                                                         cudaStream_t, const int*, const double2*);
 template cudaError_t batched_lu_solve<float2, float2>(int, int, int, const float2*, const int*, float2*,

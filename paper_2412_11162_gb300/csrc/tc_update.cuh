@@ -16,17 +16,25 @@
 // (relative error ~1e-6 of |L||U|, i.e. FP32 level: the LU stays a
 // preconditioner for the FP64 refinement).
 //
-// Operands are staged by the CTA's threads from global memory into shared
-// memory in the canonical K-major layout without swizzling (8-row x 16-byte
-// core matrices), 24 tcgen05.mma (M = 128, N = 64, K = 8) are issued by one
-// thread, completion is signalled through an mbarrier (tcgen05.commit), and the
-// epilogue reads the accumulator with tcgen05.ld (warp w: lanes 32 (w mod 4) ..,
-// columns 32 (w / 4) ..) and subtracts it from A22 in place; the A22 values are
-// loaded together with the operands, before the MMAs.  The mbarrier wait is bounded: on expiry the CTA
-// records info[b] = -1 and skips its epilogue (the solve then returns PMLBIE_ETIMEOUT).  On a real
-// expiry the MMAs may still be in flight when the CTA frees its tensor memory, so a later CTA that
-// allocates those columns could see their writes: the error is reported, and the factorisation's
-// results are not used after it.
+// Two launches per step.  operand_image_kernel forms, once per 64-row block of
+// L21 and once per 64-column block of U12, the split operands in the exact
+// shared-memory image the MMAs read: the canonical K-major layout without
+// swizzling (8-row x 16-byte core matrices), hi then lo (A': 64 KB, B': 32 KB
+// per block).  update_kernel then fetches its tile's two images with two bulk
+// copies (cp.async.bulk, completion counted in bytes on an mbarrier) while its
+// threads load their A22 values, so no CTA re-reads or re-splits operands; one
+// thread issues the 24 tcgen05.mma (M = 128, N = 64, K = 8), completion is
+// signalled through a second mbarrier (tcgen05.commit), and the epilogue reads
+// the accumulator with tcgen05.ld (warp w: lanes 32 (w mod 4) .., columns
+// 32 (w / 4) ..) and subtracts it from A22 in place.  Rows and columns beyond
+// n in a ragged block give accumulator rows / columns that are never stored.
+// Every mbarrier wait is bounded: on expiry the CTA records info[b] = -1 and
+// skips its epilogue (the solve then returns PMLBIE_ETIMEOUT); a CTA whose
+// operand copies did not arrive waits for them once more (bounded) before it
+// exits.  On a real expiry the MMAs may still be in flight when the CTA frees
+// its tensor memory, so a later CTA that allocates those columns could see
+// their writes: the error is reported, and the factorisation's results are
+// not used after it.
 #pragma once
 
 #include <cstdint>
@@ -45,17 +53,10 @@ constexpr int kTmemCols = 64;
 constexpr uint32_t kABytes = kRows * kDepth * 4;   // 32 KB per A' copy
 constexpr uint32_t kBBytes = kCols * kDepth * 4;   // 16 KB per B' copy
 // operands, then 8 KB of slack (every descriptor-addressed byte stays inside
-// the allocation whichever way the two byte offsets are read), then the
-// mbarrier, the tensor-memory address and a flag
+// the allocation whichever way the two byte offsets are read), then the two
+// mbarriers (images arrived, MMAs done), the tensor-memory address and a flag
 constexpr uint32_t kSlack = 8192;
 constexpr uint32_t kSmemBytes = 2 * kABytes + 2 * kBBytes + kSlack + 64;
-
-// Byte offset of element (r, k) of a K-major operand with R rows: core matrix
-// (k / 4, r / 8) of 128 bytes, K-adjacent core matrices R/8 * 128 bytes apart
-// (leading byte offset), row-adjacent ones 128 bytes apart (stride byte offset).
-__device__ __forceinline__ uint32_t core_off(int r, int k, int R) {
-    return (uint32_t)((((k >> 2) * (R >> 3) + (r >> 3)) << 7) + ((r & 7) << 4) + ((k & 3) << 2));
-}
 
 // Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
 // (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
@@ -93,21 +94,124 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
 }
 
-__global__ void __launch_bounds__(kThreads, 2) update_kernel(int n, int k0, int kb, float2* A, int* info) {
+// bytes of one block's operand images (hi then lo)
+constexpr uint32_t kAImg = 2 * kABytes;
+constexpr uint32_t kBImg = 2 * kBBytes;
+
+// 64-row / 64-column blocks of the trailing matrix at step k0 (kb = 32)
+__host__ __device__ constexpr int update_blocks(int n, int k0, int kb) { return (n - k0 - kb + kTileC - 1) / kTileC; }
+
+// Operand images of one step.  Grid (nblk, 3, batch), 256 threads: y = 0, 1
+// form the first / second half of the A' image of row block x (real rows
+// 0-63 / 64-127 of the 16-byte core-matrix rows), y = 2 the B' image of column
+// block x.  Image byte 16 u holds real row (or column) r = 8 g + r8 at depths
+// 4 kc .. 4 kc + 3, with (kc, g, r8) the digits of u: u = (kc R/8 + g) 8 + r8,
+// R = 128 rows for A', 64 columns for B' -- the layout whose K-adjacent core
+// matrices are R/8 x 128 bytes apart and row-adjacent ones 128 bytes apart.
+// Rows and columns beyond n are zero-filled.  Images of mode b, block x start
+// at Aimg + (b nblk + x) kAImg and Bimg + (b nblk + x) kBImg.
+__global__ void __launch_bounds__(256) operand_image_kernel(int n, int k0, int kb, int nblk, const float2* A,
+                                                            unsigned char* Aimg, unsigned char* Bimg) {
+    const int b = blockIdx.z, blk = blockIdx.x;
+    const float2* a = A + (size_t)b * n * n;
+    const int base = k0 + kb + blk * kTileC;
+    if (blockIdx.y < 2) {
+        uint4* hi = reinterpret_cast<uint4*>(Aimg + ((size_t)b * nblk + blk) * kAImg);
+        uint4* lo = hi + kABytes / 16;
+        constexpr int kIt = kABytes / 16 / 2 / 256;   // 4 core-matrix rows per thread
+        float2 v[kIt][4];
+#pragma unroll
+        for (int t = 0; t < kIt; ++t) {
+            // half y covers core-matrix groups g = 8 y .. 8 y + 7 of every kc
+            const int w = threadIdx.x + t * 256;           // 0 .. 1023
+            const int kc = w >> 6, g = ((w >> 3) & 7) + 8 * blockIdx.y, r8 = w & 7;
+            const int i = (g * 8 + r8) >> 1, kk = (kc * 4) & 31;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                v[t][e] = (kk + e < kb && base + i < n) ? a[(size_t)(k0 + kk + e) * n + base + i]
+                                                        : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < kIt; ++t) {
+            const int w = threadIdx.x + t * 256;
+            const int kc = w >> 6, g = ((w >> 3) & 7) + 8 * blockIdx.y, r8 = w & 7;
+            const int part = r8 & 1, u = (kc * 16 + g) * 8 + r8;
+            // depths 0-31 multiply Re U, 32-63 Im U: row 2i = (Re L, -Im L), row 2i+1 = (Im L, Re L)
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float x = kc < 8 ? (part ? v[t][e].y : v[t][e].x) : (part ? v[t][e].x : -v[t][e].y);
+                split_tf32(x, h[e], l[e]);
+            }
+            hi[u] = make_uint4(h[0], h[1], h[2], h[3]);
+            lo[u] = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+    } else {
+        uint4* hi = reinterpret_cast<uint4*>(Bimg + ((size_t)b * nblk + blk) * kBImg);
+        uint4* lo = hi + kBBytes / 16;
+        constexpr int kIt = kBBytes / 16 / 256;       // 4
+        float2 v[kIt][4];
+#pragma unroll
+        for (int t = 0; t < kIt; ++t) {
+            const int u = threadIdx.x + t * 256;
+            const int kc = u >> 6, j = u & 63, kk = (kc * 4) & 31;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                v[t][e] = (kk + e < kb && base + j < n) ? a[(size_t)(base + j) * n + k0 + kk + e]
+                                                        : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < kIt; ++t) {
+            const int u = threadIdx.x + t * 256, kc = u >> 6;
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) split_tf32(kc < 8 ? v[t][e].x : v[t][e].y, h[e], l[e]);
+            hi[u] = make_uint4(h[0], h[1], h[2], h[3]);
+            lo[u] = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+    }
+}
+
+// bounded wait on phase `parity` of an mbarrier; false on expiry
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity) {
+    uint32_t done = 0;
+    for (long long it = 0; it < kWaitLimit && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mb), "r"(parity)
+            : "memory");
+    }
+    return done != 0;
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mb) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mb)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 2) update_kernel(int n, int k0, int kb, int nblk, float2* A,
+                                                             const unsigned char* Aimg, const unsigned char* Bimg,
+                                                             int* info) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* sAhi = sm;
     unsigned char* sAlo = sAhi + kABytes;
     unsigned char* sBhi = sAlo + kABytes;
     unsigned char* sBlo = sBhi + kBBytes;
     unsigned char* tail = sBlo + kBBytes + kSlack;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(tail);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(tail + 8);
-    int* flag = reinterpret_cast<int*>(tail + 16);
+    uint64_t* mb_ld = reinterpret_cast<uint64_t*>(tail);
+    uint64_t* mb_mma = reinterpret_cast<uint64_t*>(tail + 8);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tail + 16);
+    int* flag = reinterpret_cast<int*>(tail + 20);
 
     const int b = blockIdx.z;
     float2* a = A + (size_t)b * n * n;
     const int r0 = k0 + kb + blockIdx.x * kTileC, c0 = k0 + kb + blockIdx.y * kTileC;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int kIssuer = 32;   // first thread of warp 1 (warp 0 allocates tensor memory meanwhile)
 
     // tensor memory for the 128 x 64 FP32 accumulator (warp 0 allocates)
     if (warp == 0) {
@@ -115,15 +219,19 @@ __global__ void __launch_bounds__(kThreads, 2) update_kernel(int n, int k0, int 
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    if (tid == kIssuer) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mb_ld)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mb_mma)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *flag = 0;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb_ld)),
+                     "r"(kAImg + kBImg)
+                     : "memory");
+        bulk_load(smem_u32(sAhi), Aimg + ((size_t)b * nblk + blockIdx.x) * kAImg, kAImg, smem_u32(mb_ld));
+        bulk_load(smem_u32(sBhi), Bimg + ((size_t)b * nblk + blockIdx.y) * kBImg, kBImg, smem_u32(mb_ld));
     }
 
-    // All global loads of the CTA are issued before any of them is used: this
-    // thread's 32 values of A22 first (the DRAM traffic), then the A' and B'
-    // elements (8 + 8 per thread, mostly served by L2).
+    // this thread's 32 values of A22 (the DRAM traffic), loaded while the images arrive
     const int q = warp & 3, h = warp >> 2;
     const int rr = 32 * q + lane;                 // real row of P
     const int row = r0 + (rr >> 1), part = rr & 1;
@@ -141,97 +249,38 @@ __global__ void __launch_bounds__(kThreads, 2) update_kernel(int n, int k0, int 
             p += cstride;
         }
     }
-    constexpr int kPer = kTileC * 32 / kThreads;   // 8
-    float2 lv[kPer], uv[kPer];
-#pragma unroll
-    for (int t = 0; t < kPer; ++t) {
-        // A' from L21: element (i, k) of L -> rows 2i, 2i+1 at depths k, 32+k;
-        // this (i, k) order keeps each warp's shared stores on 16 banks
-        const int e = tid + t * kThreads;
-        const int i = (e & 3) | (((e >> 4) & 1) << 2) | (((e >> 5) & 7) << 3);
-        const int k = ((e >> 2) & 3) | ((e >> 8) << 2);
-        lv[t] = (k < kb && r0 + i < n) ? a[(size_t)(k0 + k) * n + r0 + i] : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int t = 0; t < kPer; ++t) {
-        // B' from U12: element (k, j) of U -> column j at depths k (Re), 32+k (Im)
-        const int e = tid + t * kThreads;
-        const int k = (e & 3) | (((e >> 5) & 7) << 2);
-        const int j = ((e >> 2) & 7) | ((e >> 8) << 3);
-        uv[t] = (k < kb && c0 + j < n) ? a[(size_t)(c0 + j) * n + k0 + k] : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int t = 0; t < kPer; ++t) {
-        const int e = tid + t * kThreads;
-        const int i = (e & 3) | (((e >> 4) & 1) << 2) | (((e >> 5) & 7) << 3);
-        const int k = ((e >> 2) & 3) | ((e >> 8) << 2);
-        uint32_t reh, rel, imh, iml, nih, nil;
-        split_tf32(lv[t].x, reh, rel);
-        split_tf32(lv[t].y, imh, iml);
-        split_tf32(-lv[t].y, nih, nil);
-        const uint32_t o00 = core_off(2 * i, k, kRows), o01 = core_off(2 * i, 32 + k, kRows);
-        const uint32_t o10 = core_off(2 * i + 1, k, kRows), o11 = core_off(2 * i + 1, 32 + k, kRows);
-        *reinterpret_cast<uint32_t*>(sAhi + o00) = reh;
-        *reinterpret_cast<uint32_t*>(sAlo + o00) = rel;
-        *reinterpret_cast<uint32_t*>(sAhi + o01) = nih;
-        *reinterpret_cast<uint32_t*>(sAlo + o01) = nil;
-        *reinterpret_cast<uint32_t*>(sAhi + o10) = imh;
-        *reinterpret_cast<uint32_t*>(sAlo + o10) = iml;
-        *reinterpret_cast<uint32_t*>(sAhi + o11) = reh;
-        *reinterpret_cast<uint32_t*>(sAlo + o11) = rel;
-    }
-#pragma unroll
-    for (int t = 0; t < kPer; ++t) {
-        const int e = tid + t * kThreads;
-        const int k = (e & 3) | (((e >> 5) & 7) << 2);
-        const int j = ((e >> 2) & 7) | ((e >> 8) << 3);
-        uint32_t reh, rel, imh, iml;
-        split_tf32(uv[t].x, reh, rel);
-        split_tf32(uv[t].y, imh, iml);
-        const uint32_t o0 = core_off(j, k, kCols), o1 = core_off(j, 32 + k, kCols);
-        *reinterpret_cast<uint32_t*>(sBhi + o0) = reh;
-        *reinterpret_cast<uint32_t*>(sBlo + o0) = rel;
-        *reinterpret_cast<uint32_t*>(sBhi + o1) = imh;
-        *reinterpret_cast<uint32_t*>(sBlo + o1) = iml;
-    }
-    // generic-proxy shared stores -> visible to the tensor cores
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
 
-    if (tid == 0) {
-        const uint32_t aLBO = (kRows / 8) * 128, bLBO = (kCols / 8) * 128, SBO = 128;
-        const uint32_t ah = smem_u32(sAhi), al = smem_u32(sAlo), bh = smem_u32(sBhi), bl = smem_u32(sBlo);
-        // hi*hi, hi*lo, lo*hi; each K = 8 step covers two K-adjacent core matrices
+    if (tid == kIssuer) {
+        if (mbar_wait(smem_u32(mb_ld), 0)) {
+            const uint32_t aLBO = (kRows / 8) * 128, bLBO = (kCols / 8) * 128, SBO = 128;
+            const uint32_t ah = smem_u32(sAhi), al = smem_u32(sAlo), bh = smem_u32(sBhi), bl = smem_u32(sBlo);
+            // hi*hi, hi*lo, lo*hi; each K = 8 step covers two K-adjacent core matrices
 #pragma unroll
-        for (int pass = 0; pass < 3; ++pass) {
-            const uint32_t sa = pass == 2 ? al : ah, sb = pass == 1 ? bl : bh;
+            for (int pass = 0; pass < 3; ++pass) {
+                const uint32_t sa = pass == 2 ? al : ah, sb = pass == 1 ? bl : bh;
 #pragma unroll
-            for (int s = 0; s < kDepth / 8; ++s) {
-                const uint64_t ad = smem_desc(sa + s * 2 * aLBO, aLBO, SBO);
-                const uint64_t bd = smem_desc(sb + s * 2 * bLBO, bLBO, SBO);
-                mma_tf32(tmem, ad, bd, (pass | s) != 0);
+                for (int s = 0; s < kDepth / 8; ++s) {
+                    const uint64_t ad = smem_desc(sa + s * 2 * aLBO, aLBO, SBO);
+                    const uint64_t bd = smem_desc(sb + s * 2 * bLBO, bLBO, SBO);
+                    mma_tf32(tmem, ad, bd, (pass | s) != 0);
+                }
             }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(mb_mma))
+                         : "memory");
+        } else {
+            // the images did not arrive: record it, release the other threads,
+            // and wait once more (bounded) for the copies before exiting
+            *flag = 1;
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mb_mma)) : "memory");
+            mbar_wait(smem_u32(mb_ld), 0);
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(mbar))
-                     : "memory");
     }
-
-    // bounded wait for the MMAs (phase 0)
-    uint32_t done = 0;
-    for (long long it = 0; it < kWaitLimit && !done; ++it) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(smem_u32(mbar)), "r"(0u)
-            : "memory");
-    }
-    if (!done) *flag = 1;
+    if (!mbar_wait(smem_u32(mb_mma), 0)) *flag = 1;
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (*flag == 0) {

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "internal.h"
 #include "tc_update.cuh"
@@ -207,6 +208,311 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(int n, int k0, int
             a[(size_t)(k0 + s0 + c) * n + k0 + i] = S[idx];
         }
         __syncthreads();
+    }
+}
+
+// Shared state of one panel_reg_kernel CTA, passed to its column steps.
+template <int RPT, int W, int NT>
+struct PanelCtx {
+    float2* S1;
+    int* perm;
+    int* pv;
+    int* info;
+    float2 (*crow)[W];
+    unsigned (*ckey)[NT / 32];
+    float2* civ;
+    float2 (*rowj)[W];
+    int m, k0, s0, ws, sp, tid, lane, warp;
+};
+
+// Pivot candidate key of a row at position pos (< 1024) with value v: a valid
+// bit, the top 21 bits of |v|^2 (exponent and 13 mantissa bits; non-negative
+// floats order like their bit patterns) and 1023 - pos, so that the largest
+// key is the largest |v|^2 to 13 bits, ties going to the smallest position;
+// 0 = no candidate.  One warp-wide unsigned max (redux.sync) then finds the
+// pivot of a warp's rows.
+__device__ __forceinline__ unsigned pivot_key(float2 v, int pos) {
+    return 0x80000000u | (__float_as_uint(abs2(v)) & 0x7FFFFC00u) | (unsigned)(1023 - pos);
+}
+__device__ __forceinline__ int key_pos(unsigned key) { return 1023 - (int)(key & 1023u); }
+
+// 1 / d for the pivot, scaled by max(|Re d|, |Im d|) against overflow (the
+// correctly rounded reciprocal: with the hardware approximation the refined
+// solutions of the ill-conditioned high modes moved by a few 1e-6)
+__device__ __forceinline__ float2 pivot_rcp(float2 d) {
+    const float s = fmaxf(fabsf(d.x), fabsf(d.y));
+    const float rs = __frcp_rn(s);
+    const float ax = d.x * rs, ay = d.y * rs;
+    const float t = __frcp_rn(ax * ax + ay * ay) * rs;
+    return make_float2(ax * t, -ay * t);
+}
+
+// Column jj = g + JG of a sub-panel, after its register rows were rotated by g
+// (columns g .. W-1 at indices 0 .. W-1-g, the finished columns 0 .. g-1 at
+// W-g .. W-1): publish this warp's pivot candidate (|v|^2, position, row and
+// 1 / v), one barrier, pick the pivot, exchange the two rows whole, scale and
+// update, and form this thread's candidate for the next column.
+template <int RPT, int W, int NT, int JG>
+__device__ __forceinline__ void panel_column(float2 (&x)[RPT][W], unsigned& key, const PanelCtx<RPT, W, NT>& c,
+                                             int g) {
+    constexpr int NW = NT / 32;
+    static_assert(NW <= 32, "one candidate per lane");
+    const int jj = g + JG;
+    if (jj >= c.ws) return;
+    const int j = c.s0 + jj, buf = jj & 1;
+    const int tid = c.tid, lane = c.lane, warp = c.warp;
+    // every warp's best key, then (barrier) the pivot position p; the owner of
+    // p publishes its row and 1 / pivot (barrier); the owner of the diagonal
+    // position j published its row with the keys
+    const unsigned wkey = __reduce_max_sync(0xffffffffu, key);
+    if (lane == 0) c.ckey[buf][warp] = wkey;
+    if (tid == j)
+#pragma unroll
+        for (int q = 0; q < W; ++q) c.rowj[buf][q] = x[0][q];
+    __syncthreads();
+    const unsigned gkey = __reduce_max_sync(0xffffffffu, lane < NW ? c.ckey[buf][lane] : 0u);
+    const int p = key_pos(gkey);
+    const bool nonzero = (gkey & 0x7FFFFC00u) != 0u;
+    // slot choices as value selects: a branch per slot lets the compiler index
+    // the register rows dynamically, which moves them to local memory
+    if (tid == p % NT) {
+        const int slot = p / NT;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            float2 v = x[0][q];
+#pragma unroll
+            for (int s = 1; s < RPT; ++s) v = slot == s ? x[s][q] : v;
+            c.crow[buf][q] = v;
+        }
+        float2 d = x[0][JG];
+#pragma unroll
+        for (int s = 1; s < RPT; ++s) d = slot == s ? x[s][JG] : d;
+        c.civ[buf] = nonzero ? pivot_rcp(d) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const float2* prow = c.crow[buf];
+    const float2 inv = c.civ[buf];
+    if (tid == NT - 1) {   // the last warp: warp 0 holds the diagonal row's work
+        c.pv[c.k0 + j] = c.k0 + p;
+        if (!nonzero && c.info[blockIdx.x] == 0) c.info[blockIdx.x] = c.k0 + j + 1;
+        const int t = c.perm[j];
+        c.perm[j] = c.perm[p];
+        c.perm[p] = t;
+    }
+    if (p != j) {
+        if (tid == j)
+#pragma unroll
+            for (int q = 0; q < W; ++q) x[0][q] = prow[q];
+        if (tid == p % NT) {
+            const int slot = p / NT;
+#pragma unroll
+            for (int q = 0; q < W; ++q) {
+                const float2 v = c.rowj[buf][q];
+#pragma unroll
+                for (int s = 0; s < RPT; ++s) x[s][q] = slot == s ? v : x[s][q];
+            }
+        }
+        if constexpr (RPT > 1) {
+            if (c.sp > 0 && tid < c.s0) {
+                float2* col = c.S1 + (size_t)tid * c.m;
+                const float2 t = col[j];
+                col[j] = col[p];
+                col[p] = t;
+            }
+        }
+    }
+    // scale below the diagonal, rank-1 update of the later columns (indices
+    // JG+1 .. W-1-g), next candidate
+    float2 l[RPT];
+    bool act[RPT];
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) {
+        const int i = s * NT + tid;
+        act[s] = i > j && i < c.m;
+        l[s] = make_float2(0.f, 0.f);
+        if (act[s]) {
+            l[s] = mul(x[s][JG], inv);
+            x[s][JG] = l[s];
+        }
+    }
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) any = any || act[s];
+    if (__any_sync(0xffffffffu, any))
+#pragma unroll
+    for (int q = JG + 1; q < W; ++q) {
+        if (q < W - g) {
+            const float2 uq = prow[q];
+#pragma unroll
+            for (int s = 0; s < RPT; ++s)
+                if (act[s]) x[s][q] = fms(x[s][q], l[s], uq);
+        }
+    }
+    key = 0u;
+    if constexpr (JG + 1 < W) {
+        if (jj + 1 < c.ws) {
+#pragma unroll
+            for (int s = 0; s < RPT; ++s)
+                if (act[s]) key = max(key, pivot_key(x[s][JG + 1], s * NT + tid));
+        }
+    }
+}
+
+template <int RPT, int W, int NT, int... JG>
+__device__ __forceinline__ void panel_group(float2 (&x)[RPT][W], unsigned& key, const PanelCtx<RPT, W, NT>& c, int g,
+                                            std::integer_sequence<int, JG...>) {
+    (panel_column<RPT, W, NT, JG>(x, key, c, g), ...);
+}
+
+// the register rows rotated left by G columns
+template <int RPT, int W, int G>
+__device__ __forceinline__ void rotate_rows(float2 (&x)[RPT][W]) {
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) {
+        float2 t[G];
+#pragma unroll
+        for (int r = 0; r < G; ++r) t[r] = x[s][r];
+#pragma unroll
+        for (int q = 0; q + G < W; ++q) x[s][q] = x[s][q + G];
+#pragma unroll
+        for (int r = 0; r < G; ++r) x[s][W - G + r] = t[r];
+    }
+}
+
+// Panel factorisation for complex64 with the panel's rows in registers
+// (m = n - k0 <= RPT x NT): thread t holds the rows at positions t, t + NT
+// (relative to k0) of a sub-panel of W columns (RPT x W <= 32 values; one
+// sub-panel of 32 for m <= 512 with NT = 128, 256 or 512 threads as m needs,
+// two of 16 for m <= 1024).  Per column: a warp-wide max (redux.sync) of
+// packed pivot keys (pivot_key) and one barrier give every thread the pivot
+// position; its owner publishes the pivot row and 1 / pivot (second barrier);
+// the owners of the diagonal and pivot positions exchange their rows whole in
+// registers, and every thread scales and updates its own rows with the pivot
+// row read from shared memory (a broadcast).  The columns are processed in
+// compiled groups of four with the register rows rotated after each group, so
+// that every register index is a constant and the code stays small.  Row
+// interchanges reach the columns outside the sub-panel without global-memory
+// swaps: the columns not yet loaded are gathered through a position ->
+// initial-row map, and the first sub-panel (two sub-panels) is held in shared
+// memory, where the second one's interchanges are applied, until the panel is
+// written back in LAPACK getrf's row order.  The pivot is the largest |v|^2
+// to 13 mantissa bits (ties: smallest position), within 2^-13 of the exact
+// partial-pivoting choice.
+template <int RPT, int W, int NT>
+__global__ void __launch_bounds__(NT) panel_reg_kernel(int n, int k0, int kb, float2* A, int* piv, int* info) {
+    static_assert(RPT * W <= 32 && (RPT == 1 || W * RPT == kNB), "register panel: RPT x W values per thread");
+    static_assert(RPT * NT <= 1024, "pivot keys hold positions below 1024");
+    constexpr int NW = NT / 32;
+    extern __shared__ unsigned char smraw[];
+    const int m = n - k0;
+    float2* S1 = reinterpret_cast<float2*>(smraw);   // [W][m]: the first sub-panel (RPT > 1)
+    int* perm = reinterpret_cast<int*>(smraw + (RPT > 1 ? sizeof(float2) * (size_t)W * m : 0));
+    __shared__ float2 crow[2][W];                    // the pivot row
+    __shared__ unsigned ckey[2][NW];                  // each warp's candidate key (pivot_key)
+    __shared__ float2 civ[2];                        // 1 / pivot
+    __shared__ float2 rowj[2][W];                    // the row at the diagonal position
+    __shared__ float2 top[W][W];                     // top rows of the second sub-panel (its U block)
+    float2* a = A + (size_t)blockIdx.x * n * n;
+    int* pv = piv + (size_t)blockIdx.x * n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float2 x[RPT][W];
+    for (int i = tid; i < m; i += NT) perm[i] = i;
+    __syncthreads();
+    const int nsub = (kb + W - 1) / W;
+    for (int sp = 0; sp < nsub; ++sp) {
+        const int s0 = sp * W, ws = min(W, kb - s0);
+        // the sub-panel's columns keep the panel's initial row order in global memory
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) {
+            const int i = s * NT + tid;
+            const float2* src = a + (size_t)(k0 + s0) * n + k0 + (i < m ? perm[i] : 0);
+#pragma unroll
+            for (int c = 0; c < W; ++c) x[s][c] = (i < m && c < ws) ? src[(size_t)c * n] : make_float2(0.f, 0.f);
+        }
+        if constexpr (RPT > 1) {
+            if (sp > 0) {
+                // top rows (positions < s0, thread = position): U = L11^{-1} A12 with the
+                // unit-lower L11 of the first sub-panel, one warp per column, lane = row
+                if (tid < s0)
+#pragma unroll
+                    for (int c = 0; c < W; ++c) top[tid][c] = x[0][c];
+                __syncthreads();
+                if (warp < ws) {
+                    float2 v = lane < s0 ? top[lane][warp] : make_float2(0.f, 0.f);
+                    for (int t = 0; t < s0 - 1; ++t) {
+                        const float2 vt = make_float2(__shfl_sync(0xffffffffu, v.x, t), __shfl_sync(0xffffffffu, v.y, t));
+                        if (lane > t && lane < s0) v = fms(v, S1[(size_t)t * m + lane], vt);
+                    }
+                    if (lane < s0) top[lane][warp] = v;
+                }
+                __syncthreads();
+                if (tid < s0)
+#pragma unroll
+                    for (int c = 0; c < W; ++c) x[0][c] = top[tid][c];
+                // rows below: x[i][c] -= sum_t L[i][t] U[t][c]
+                for (int t = 0; t < s0; ++t) {
+#pragma unroll
+                    for (int s = 0; s < RPT; ++s) {
+                        const int i = s * NT + tid;
+                        if (i >= s0 && i < m) {
+                            const float2 l = S1[(size_t)t * m + i];
+#pragma unroll
+                            for (int c = 0; c < W; ++c) x[s][c] = fms(x[s][c], l, top[t][c]);
+                        }
+                    }
+                }
+            }
+        }
+        // this thread's best candidate for the sub-panel's first column
+        unsigned key = 0u;
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) {
+            const int i = s * NT + tid;
+            if (i >= s0 && i < m) key = max(key, pivot_key(x[s][0], i));
+        }
+        {
+            // columns in groups of kG: one compiled group, the rows rotated by kG
+            // after each (W / kG rotations restore the column order)
+            constexpr int kG = 4;
+            static_assert(W % kG == 0, "whole groups");
+            const PanelCtx<RPT, W, NT> c{S1, perm, pv, info, crow, ckey, civ, rowj, m, k0, s0, ws, sp, tid, lane, warp};
+#pragma unroll 1
+            for (int g = 0; g < W; g += kG) {
+                panel_group<RPT, W, NT>(x, key, c, g, std::make_integer_sequence<int, kG>{});
+                rotate_rows<RPT, W, kG>(x);
+            }
+        }
+        if constexpr (RPT > 1) {
+            if (sp == 0 && nsub > 1) {
+#pragma unroll
+                for (int s = 0; s < RPT; ++s) {
+                    const int i = s * NT + tid;
+                    if (i < m)
+#pragma unroll
+                        for (int c = 0; c < W; ++c) S1[(size_t)c * m + i] = x[s][c];
+                }
+                __syncthreads();   // S1 and the position map complete before the next sub-panel
+                continue;
+            }
+        }
+        // write back (final positions): this sub-panel, then the first one
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) {
+            const int i = s * NT + tid;
+            if (i < m) {
+                float2* dst = a + (size_t)(k0 + s0) * n + k0 + i;
+#pragma unroll
+                for (int c = 0; c < W; ++c)
+                    if (c < ws) dst[(size_t)c * n] = x[s][c];
+            }
+        }
+        if constexpr (RPT > 1) {
+            if (sp > 0) {
+                __syncthreads();   // the last interchanges of S1 rows are done
+                for (int c = 0; c < W; ++c)
+                    for (int i = tid; i < m; i += NT) a[(size_t)(k0 + c) * n + k0 + i] = S1[(size_t)c * m + i];
+            }
+        }
     }
 }
 
@@ -833,7 +1139,13 @@ cudaError_t lu_prepare() {
         cudaError_t e;
         if ((e = allow_max_smem(panel_kernel<T>)) == cudaSuccess && (e = allow_max_smem(swap_trsm_kernel<T>)) ==
             cudaSuccess && (e = allow_max_smem(perm_kernel)) == cudaSuccess) {
-            if constexpr (sizeof(T) == 8) e = allow_max_smem(tcu::update_kernel);
+            if constexpr (sizeof(T) == 8) {
+                if ((e = allow_max_smem(tcu::update_kernel)) == cudaSuccess &&
+                    (e = allow_max_smem(panel_reg_kernel<1, kNB, 128>)) == cudaSuccess &&
+                    (e = allow_max_smem(panel_reg_kernel<1, kNB, 256>)) == cudaSuccess &&
+                    (e = allow_max_smem(panel_reg_kernel<1, kNB, kPanelThreads>)) == cudaSuccess)
+                    e = allow_max_smem(panel_reg_kernel<2, kNB / 2, kPanelThreads>);
+            }
         }
         err = e;
     });
@@ -855,9 +1167,31 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
     }
     for (int k0 = 0; k0 < n; k0 += kNB) {
         int kb = std::min(kNB, n - k0);
-        const int w = panel_width<T>(n - k0);
-        const size_t smp = sizeof(T) * (size_t)(n - k0) * w;
-        panel_kernel<T><<<batch, kPanelThreads, smp, s>>>(n, k0, kb, w, A, piv, info);
+        const int m = n - k0;
+        bool reg_panel = false;
+        if constexpr (sizeof(T) == 8) {
+            // complex64 panels of up to 2 x 512 rows: rows in registers
+            float2* A32 = reinterpret_cast<float2*>(A);
+            // one row per thread up to 512 rows (128 / 256 / 512 threads), then two
+            const size_t smi = sizeof(int) * (size_t)m;
+            reg_panel = true;
+            if (m <= 128)
+                panel_reg_kernel<1, kNB, 128><<<batch, 128, smi, s>>>(n, k0, kb, A32, piv, info);
+            else if (m <= 256)
+                panel_reg_kernel<1, kNB, 256><<<batch, 256, smi, s>>>(n, k0, kb, A32, piv, info);
+            else if (m <= kPanelThreads)
+                panel_reg_kernel<1, kNB, kPanelThreads><<<batch, kPanelThreads, smi, s>>>(n, k0, kb, A32, piv, info);
+            else if (m <= 2 * kPanelThreads)
+                panel_reg_kernel<2, kNB / 2, kPanelThreads>
+                    <<<batch, kPanelThreads, smi + sizeof(float2) * (kNB / 2) * (size_t)m, s>>>(n, k0, kb, A32, piv, info);
+            else
+                reg_panel = false;
+        }
+        if (!reg_panel) {
+            const int w = panel_width<T>(m);
+            const size_t smp = sizeof(T) * (size_t)m * w;
+            panel_kernel<T><<<batch, kPanelThreads, smp, s>>>(n, k0, kb, w, A, piv, info);
+        }
         count_launch(2);
         dim3 g1((n + kSwapCols - 1) / kSwapCols, batch);
         size_t sm1 = sizeof(T) * ((size_t)kSwapCols * 2 * kNB + kNB * kNB);

@@ -794,7 +794,8 @@ def lu_update_roofline(w, rep, pk):
     ach = wbytes / (ms / 1e3) / 1e9 if ms > 0 else None
     traffic = profile_traffic("tc_update_kernel_n512_64modes.md", "tc_update.cuh", wbytes)
     return {"kernel": ("tcu::operand_image_kernel + tcu::update_kernel (rank-32 trailing update of the complex64 LU "
-                       "on tcgen05, TF32 split operands formed once per step, fetched by bulk copies)"),
+                       "on tcgen05, TF32 split operands formed once per step; persistent warp-specialised update "
+                       "streaming the tiles by TMA)"),
             "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
             "frac": ach / hbm if ach else None, "traffic": traffic, "ms_per_step": ms,
             "launches_per_step": launches, "algorithmic_bytes": wbytes,

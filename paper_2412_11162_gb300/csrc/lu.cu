@@ -19,6 +19,8 @@
 #include <type_traits>
 #include <utility>
 
+#include <cudaTypedefs.h>
+
 #include "internal.h"
 #include "tc_update.cuh"
 
@@ -1152,6 +1154,43 @@ cudaError_t lu_prepare() {
     return err;
 }
 
+namespace {
+
+// cuTensorMapEncodeTiled from the driver, looked up once
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// TMA map of the batch of n x n complex64 matrices as a [batch][n][n] tensor
+// of 8-byte elements (row index fastest), 64 x 64 boxes; n must be even (row
+// stride a multiple of 16 bytes)
+cudaError_t trailing_tensor_map(CUtensorMap* tm, float2* A, int n, int batch) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || (n & 1)) return cudaErrorInvalidValue;
+    const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)batch};
+    const cuuint64_t strides[2] = {(cuuint64_t)n * 8, (cuuint64_t)n * n * 8};
+    const cuuint32_t box[3] = {tcu::kTileC, tcu::kTileC, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, A, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
 size_t lu_image_bytes(int n, int batch) {
     const int nblk = n > kNB ? tcu::update_blocks(n, 0, kNB) : 0;
     return (size_t)batch * nblk * (tcu::kAImg + tcu::kBImg);
@@ -1162,8 +1201,19 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
                        cudaEvent_t* upd_ev) {
     cudaError_t pe = lu_prepare<T>();
     if (pe != cudaSuccess) return pe;
+    // complex64: the trailing matrix as a TMA tensor, and the SMs for the
+    // persistent update
+    CUtensorMap tmA;
+    int sms = 0;
     if constexpr (sizeof(T) == 8) {
-        if (n > kNB && (!img || (reinterpret_cast<uintptr_t>(img) & 15))) return cudaErrorInvalidValue;
+        if (n > kNB) {
+            if (!img || (reinterpret_cast<uintptr_t>(img) & 15)) return cudaErrorInvalidValue;
+            cudaError_t e = trailing_tensor_map(&tmA, reinterpret_cast<float2*>(A), n, batch);
+            int dev = 0;
+            if (e == cudaSuccess) e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+        }
     }
     for (int k0 = 0; k0 < n; k0 += kNB) {
         int kb = std::min(kNB, n - k0);
@@ -1209,8 +1259,10 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
                 tcu::operand_image_kernel<<<dim3(nblk, 3, batch), 256, 0, s>>>(
                     n, k0, kb, nblk, reinterpret_cast<const float2*>(A), img, bimg);
                 count_launch();
-                tcu::update_kernel<<<dim3(nblk, nblk, batch), tcu::kThreads, tcu::kSmemBytes, s>>>(
-                    n, k0, kb, nblk, reinterpret_cast<float2*>(A), img, bimg, info);
+                const long long units = (long long)batch * nblk;
+                const int grid = (int)std::min<long long>(units, sms);
+                tcu::update_kernel<<<grid, tcu::kPipeThreads, tcu::kPipeSmem, s>>>(tmA, k0, kb, nblk, batch, img,
+                                                                                   bimg, info);
             } else {
                 constexpr int TL = GemmTile<T>::v;
                 dim3 g2((rem + TL - 1) / TL, (rem + TL - 1) / TL, batch);

@@ -3,8 +3,8 @@
 //   A22 <- A22 - L21 U12,   complex64, column-major, leading dimension n,
 //
 // L21 = A[k0+kb : n, k0 : k0+kb], U12 = A[k0 : k0+kb, k0+kb : n], kb <= 32.
-// One CTA per 64 x 64 complex tile of A22.  The complex product is one real
-// GEMM of depth 64 with the complex rows split into interleaved real rows:
+// In 64 x 64 complex tiles of A22, the complex product is one real GEMM of
+// depth 64 with the complex rows split into interleaved real rows:
 //
 //   P[2i  ][j] = sum_k  Re L[i][k] Re U[k][j] - Im L[i][k] Im U[k][j]
 //   P[2i+1][j] = sum_k  Im L[i][k] Re U[k][j] + Re L[i][k] Im U[k][j]
@@ -20,22 +20,20 @@
 // L21 and once per 64-column block of U12, the split operands in the exact
 // shared-memory image the MMAs read: the canonical K-major layout without
 // swizzling (8-row x 16-byte core matrices), hi then lo (A': 64 KB, B': 32 KB
-// per block).  update_kernel then fetches its tile's two images with two bulk
-// copies (cp.async.bulk, completion counted in bytes on an mbarrier) while its
-// threads load their A22 values, so no CTA re-reads or re-splits operands; one
-// thread issues the 24 tcgen05.mma (M = 128, N = 64, K = 8), completion is
-// signalled through a second mbarrier (tcgen05.commit), and the epilogue reads
-// the accumulator with tcgen05.ld (warp w: lanes 32 (w mod 4) .., columns
-// 32 (w / 4) ..) and subtracts it from A22 in place.  Rows and columns beyond
-// n in a ragged block give accumulator rows / columns that are never stored.
-// Every mbarrier wait is bounded: on expiry the CTA records info[b] = -1 and
-// skips its epilogue (the solve then returns PMLBIE_ETIMEOUT); a CTA whose
-// operand copies did not arrive waits for them once more (bounded) before it
-// exits.  On a real expiry the MMAs may still be in flight when the CTA frees
-// its tensor memory, so a later CTA that allocates those columns could see
-// their writes: the error is reported, and the factorisation's results are
-// not used after it.
+// per block).  update_kernel (persistent, one CTA per SM, warp-specialised;
+// its comment below) streams the trailing matrix through shared memory in
+// 64 x 64 tiles with TMA, fetches the images with bulk copies, runs the 24
+// tcgen05.mma (M = 128, N = 64, K = 8) of a tile into one of two
+// tensor-memory accumulators, and subtracts the accumulator from the tile
+// before a TMA store.  Rows and columns beyond n in a ragged block give
+// accumulator rows / columns that are never stored (the tensor store clips
+// at n).  On a wait that expires the MMAs may still be in flight when the CTA
+// frees its tensor memory, so a later CTA that allocates those columns could
+// see their writes: the error is reported (info[b] = -1, the solve returns
+// PMLBIE_ETIMEOUT), and the factorisation's results are not used after it.
 #pragma once
+
+#include <cuda.h>
 
 #include <cstdint>
 
@@ -44,19 +42,12 @@
 namespace pmlbie {
 namespace tcu {
 
-constexpr int kTileC = 64;        // complex rows and columns per CTA
+constexpr int kTileC = 64;        // complex rows and columns per tile
 constexpr int kRows = 128;        // real rows of A' (M of the MMA)
 constexpr int kCols = 64;         // columns of B' (N of the MMA)
 constexpr int kDepth = 64;        // real depth (2 x panel width 32)
-constexpr int kThreads = 256;
-constexpr int kTmemCols = 64;
 constexpr uint32_t kABytes = kRows * kDepth * 4;   // 32 KB per A' copy
 constexpr uint32_t kBBytes = kCols * kDepth * 4;   // 16 KB per B' copy
-// operands, then 8 KB of slack (every descriptor-addressed byte stays inside
-// the allocation whichever way the two byte offsets are read), then the two
-// mbarriers (images arrived, MMAs done), the tensor-memory address and a flag
-constexpr uint32_t kSlack = 8192;
-constexpr uint32_t kSmemBytes = 2 * kABytes + 2 * kBBytes + kSlack + 64;
 
 // Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
 // (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
@@ -193,112 +184,262 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                  : "memory");
 }
 
-__global__ void __launch_bounds__(kThreads, 2) update_kernel(int n, int k0, int kb, int nblk, float2* A,
-                                                             const unsigned char* Aimg, const unsigned char* Bimg,
-                                                             int* info) {
+// ---------------------------------------------------------------------------
+// Persistent, warp-specialised update.  One CTA per SM (224 KB of shared
+// memory) walks whole rows of tiles: row units u = b nblk + bx (mode b, row
+// block bx) are dealt round-robin (CTA c takes u = c, c + G, ..), so that the
+// CTAs running at the same time work on neighbouring modes whose operand
+// images stay in L2, and a unit's A' image is fetched once for its nblk tiles.
+// Warp 0 (one thread) is the producer: the unit's A' image (bulk copy), then
+// per tile the B' image (bulk copy, two stages) and the 64 x 64 A22 tile (TMA
+// tensor load, three stages; rows / columns beyond n read as zeros).  Warp 1
+// (one thread) issues the tile's 24 MMAs into one of two tensor-memory
+// accumulators.  Warps 2-5 read the accumulator (each its lane quadrant),
+// subtract it from the tile in shared memory and store the tile with a TMA
+// tensor store (clipped at n).  Stages pass between the roles through
+// mbarriers: full (transaction bytes / MMA commit) and empty (MMA commit,
+// epilogue arrival, or the store's completed read).  Every wait is bounded; on
+// expiry the CTA records the error, stops its loops (the epilogue warps decide
+// together through a barrier reduction, so none waits alone), waits (bounded)
+// for the copies it issued, and marks info[b] = -1 for the modes of its tiles.
+constexpr int kPipeThreads = 192;            // warp 0 producer, warp 1 MMA, warps 2-5 epilogue
+constexpr int kBStages = 2, kCStages = 3;
+constexpr uint32_t kCTile = kTileC * kTileC * 8;                    // 32 KB complex64 tile
+constexpr uint32_t kPipeOffB = kAImg;                               // after the A' image (64 KB)
+constexpr uint32_t kPipeOffC = kPipeOffB + kBStages * kBImg;        // 128 KB
+constexpr uint32_t kPipeOffBar = kPipeOffC + kCStages * kCTile;     // 224 KB
+constexpr uint32_t kPipeSmem = kPipeOffBar + 256;
+constexpr int kPipeTmemCols = 128;           // two 64-column accumulators
+
+struct PipeBars {
+    uint64_t a_full, a_empty, b_full[kBStages], b_empty[kBStages], c_full[kCStages], c_empty[kCStages],
+        acc_full[2], acc_empty[2];
+    uint32_t tmem;
+    int err;
+};
+static_assert(sizeof(PipeBars) <= 256, "barrier block");
+
+__device__ __forceinline__ void mb_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mb_expect(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b))
+                 : "memory");
+}
+// 64 x 64 tile of the [batch][n][n] complex64 tensor (8-byte elements): x = row, y = column, z = mode
+__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* b) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(b))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_tile(const CUtensorMap* tm, int x, int y, int z, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(x), "r"(y), "r"(z), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ bool err_set(const PipeBars* bar) { return *reinterpret_cast<const volatile int*>(&bar->err); }
+
+__global__ void __launch_bounds__(kPipeThreads, 1) update_kernel(const __grid_constant__ CUtensorMap tmA, int k0, int kb,
+                                                                 int nblk, int batch, const unsigned char* Aimg,
+                                                                 const unsigned char* Bimg, int* info) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char* sAhi = sm;
-    unsigned char* sAlo = sAhi + kABytes;
-    unsigned char* sBhi = sAlo + kABytes;
-    unsigned char* sBlo = sBhi + kBBytes;
-    unsigned char* tail = sBlo + kBBytes + kSlack;
-    uint64_t* mb_ld = reinterpret_cast<uint64_t*>(tail);
-    uint64_t* mb_mma = reinterpret_cast<uint64_t*>(tail + 8);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(tail + 16);
-    int* flag = reinterpret_cast<int*>(tail + 20);
-
-    const int b = blockIdx.z;
-    float2* a = A + (size_t)b * n * n;
-    const int r0 = k0 + kb + blockIdx.x * kTileC, c0 = k0 + kb + blockIdx.y * kTileC;
+    PipeBars* bar = reinterpret_cast<PipeBars*>(sm + kPipeOffBar);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr int kIssuer = 32;   // first thread of warp 1 (warp 0 allocates tensor memory meanwhile)
-
-    // tensor memory for the 128 x 64 FP32 accumulator (warp 0 allocates)
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(kTmemCols));
+    const long long U = (long long)batch * nblk;          // row units (mode, row block)
+    const long long G = gridDim.x;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&bar->tmem)),
+                     "r"(kPipeTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == kIssuer) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mb_ld)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mb_mma)));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        *flag = 0;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb_ld)),
-                     "r"(kAImg + kBImg)
-                     : "memory");
-        bulk_load(smem_u32(sAhi), Aimg + ((size_t)b * nblk + blockIdx.x) * kAImg, kAImg, smem_u32(mb_ld));
-        bulk_load(smem_u32(sBhi), Bimg + ((size_t)b * nblk + blockIdx.y) * kBImg, kBImg, smem_u32(mb_ld));
-    }
-
-    // this thread's 32 values of A22 (the DRAM traffic), loaded while the images arrive
-    const int q = warp & 3, h = warp >> 2;
-    const int rr = 32 * q + lane;                 // real row of P
-    const int row = r0 + (rr >> 1), part = rr & 1;
-    const int cbase = c0 + 32 * h;
-    // columns by one pointer stepped by the column stride (2n floats)
-    float* pc = reinterpret_cast<float*>(a) + 2 * ((size_t)cbase * n + row) + part;
-    const size_t cstride = 2 * (size_t)n;
-    const int ncv = row < n ? min(32, n - cbase) : 0;
-    float cv[32];
-    {
-        const float* p = pc;
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            cv[c] = c < ncv ? *p : 0.f;
-            p += cstride;
+    if (tid == 0) {
+        mb_init(&bar->a_full, 1);
+        mb_init(&bar->a_empty, 1);
+        for (int s = 0; s < kBStages; ++s) {
+            mb_init(&bar->b_full[s], 1);
+            mb_init(&bar->b_empty[s], 1);
         }
+        for (int s = 0; s < kCStages; ++s) {
+            mb_init(&bar->c_full[s], 1);
+            mb_init(&bar->c_empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mb_init(&bar->acc_full[s], 1);
+            mb_init(&bar->acc_empty[s], 4);   // one arrival per epilogue warp
+        }
+        bar->err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tslot;
+    const uint32_t tmem = bar->tmem;
+    const uint32_t sbase = smem_u32(sm);
+    const int rbase = k0 + kb;                            // first row / column of A22
 
-    if (tid == kIssuer) {
-        if (mbar_wait(smem_u32(mb_ld), 0)) {
-            const uint32_t aLBO = (kRows / 8) * 128, bLBO = (kCols / 8) * 128, SBO = 128;
-            const uint32_t ah = smem_u32(sAhi), al = smem_u32(sAlo), bh = smem_u32(sBhi), bl = smem_u32(sBlo);
-            // hi*hi, hi*lo, lo*hi; each K = 8 step covers two K-adjacent core matrices
-#pragma unroll
-            for (int pass = 0; pass < 3; ++pass) {
-                const uint32_t sa = pass == 2 ? al : ah, sb = pass == 1 ? bl : bh;
-#pragma unroll
-                for (int s = 0; s < kDepth / 8; ++s) {
-                    const uint64_t ad = smem_desc(sa + s * 2 * aLBO, aLBO, SBO);
-                    const uint64_t bd = smem_desc(sb + s * 2 * bLBO, bLBO, SBO);
-                    mma_tf32(tmem, ad, bd, (pass | s) != 0);
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer
+            long long i = 0, lastB[kBStages], lastC[kCStages];
+            int k = 0, a_issued = 0;
+            for (int s = 0; s < kBStages; ++s) lastB[s] = -1;
+            for (int s = 0; s < kCStages; ++s) lastC[s] = -1;
+            bool ok = true;
+            for (long long u = blockIdx.x; u < U && ok; u += G, ++k) {
+                const int b = (int)(u / nblk), bx = (int)(u - (long long)b * nblk);
+                if (k >= 1 && !mbar_wait(smem_u32(&bar->a_empty), (uint32_t)((k - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                mb_expect(&bar->a_full, kAImg);
+                bulk_load(sbase, Aimg + (size_t)u * kAImg, kAImg, smem_u32(&bar->a_full));
+                ++a_issued;
+                for (int by = 0; by < nblk; ++by, ++i) {
+                    const int bs = (int)(i % kBStages), cs = (int)(i % kCStages);
+                    if (i >= kBStages &&
+                        !mbar_wait(smem_u32(&bar->b_empty[bs]), (uint32_t)(((i / kBStages) - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    mb_expect(&bar->b_full[bs], kBImg);
+                    bulk_load(sbase + kPipeOffB + bs * kBImg, Bimg + ((size_t)b * nblk + by) * kBImg, kBImg,
+                              smem_u32(&bar->b_full[bs]));
+                    lastB[bs] = i;
+                    if (i >= kCStages &&
+                        !mbar_wait(smem_u32(&bar->c_empty[cs]), (uint32_t)(((i / kCStages) - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    mb_expect(&bar->c_full[cs], kCTile);
+                    tma_load_tile(sbase + kPipeOffC + cs * kCTile, &tmA, rbase + bx * kTileC, rbase + by * kTileC, b,
+                                  &bar->c_full[cs]);
+                    lastC[cs] = i;
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(mb_mma))
-                         : "memory");
-        } else {
-            // the images did not arrive: record it, release the other threads,
-            // and wait once more (bounded) for the copies before exiting
-            *flag = 1;
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mb_mma)) : "memory");
-            mbar_wait(smem_u32(mb_ld), 0);
+            if (!ok) {
+                bar->err = 1;
+                // copies in flight: wait (bounded) for the last issued use of every stage
+                if (a_issued > 0) mbar_wait(smem_u32(&bar->a_full), (uint32_t)((a_issued - 1) & 1));
+                for (int s = 0; s < kBStages; ++s)
+                    if (lastB[s] >= 0) mbar_wait(smem_u32(&bar->b_full[s]), (uint32_t)((lastB[s] / kBStages) & 1));
+                for (int s = 0; s < kCStages; ++s)
+                    if (lastC[s] >= 0) mbar_wait(smem_u32(&bar->c_full[s]), (uint32_t)((lastC[s] / kCStages) & 1));
+            }
         }
-    }
-    if (!mbar_wait(smem_u32(mb_mma), 0)) *flag = 1;
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (*flag == 0) {
-        float pv[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h), pv);
-        float* p = pc;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issue: hi*hi, hi*lo, lo*hi; each K = 8 step covers two K-adjacent core matrices
+            const uint32_t aLBO = (kRows / 8) * 128, bLBO = (kCols / 8) * 128, SBO = 128;
+            long long i = 0;
+            int k = 0;
+            bool ok = true;
+            for (long long u = blockIdx.x; u < U && ok; u += G, ++k) {
+                if (err_set(bar) || !mbar_wait(smem_u32(&bar->a_full), (uint32_t)(k & 1))) {
+                    ok = false;
+                    break;
+                }
+                for (int by = 0; by < nblk; ++by, ++i) {
+                    const int bs = (int)(i % kBStages), ab = (int)(i & 1);
+                    if (err_set(bar) || !mbar_wait(smem_u32(&bar->b_full[bs]), (uint32_t)((i / kBStages) & 1)) ||
+                        (i >= 2 && !mbar_wait(smem_u32(&bar->acc_empty[ab]), (uint32_t)(((i >> 1) - 1) & 1)))) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t ah = sbase, al = sbase + kABytes;
+                    const uint32_t bh = sbase + kPipeOffB + bs * kBImg, bl = bh + kBBytes;
+                    const uint32_t d = tmem + (uint32_t)(ab * kTileC);
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            if (c < ncv) *p = cv[c] - pv[c];
-            p += cstride;
+                    for (int pass = 0; pass < 3; ++pass) {
+                        const uint32_t sa = pass == 2 ? al : ah, sb = pass == 1 ? bl : bh;
+#pragma unroll
+                        for (int s = 0; s < kDepth / 8; ++s) {
+                            const uint64_t ad = smem_desc(sa + s * 2 * aLBO, aLBO, SBO);
+                            const uint64_t bd = smem_desc(sb + s * 2 * bLBO, bLBO, SBO);
+                            mma_tf32(d, ad, bd, (pass | s) != 0);
+                        }
+                    }
+                    mma_commit(&bar->b_empty[bs]);
+                    mma_commit(&bar->acc_full[ab]);
+                    if (by == nblk - 1) mma_commit(&bar->a_empty);
+                }
+            }
+            if (!ok) bar->err = 1;
         }
-    } else if (tid == 0) {
-        info[b] = -1;
+    } else {
+        // epilogue: this warp's lane quadrant of the accumulator (real rows 32 q ..)
+        const int q = warp & 3;
+        const int rr = 32 * q + lane, row = rr >> 1, part = rr & 1;
+        const bool leader = tid == 64;
+        long long i = 0;
+        bool stop = false;
+        for (long long u = blockIdx.x; u < U && !stop; u += G) {
+            const int b = (int)(u / nblk), bx = (int)(u - (long long)b * nblk);
+            for (int by = 0; by < nblk; ++by, ++i) {
+                const int ab = (int)(i & 1), cs = (int)(i % kCStages);
+                const bool ok = mbar_wait(smem_u32(&bar->acc_full[ab]), (uint32_t)((i >> 1) & 1)) &&
+                                mbar_wait(smem_u32(&bar->c_full[cs]), (uint32_t)((i / kCStages) & 1));
+                if (!ok) bar->err = 1;
+                // one decision for all 128 epilogue threads (a barrier with an OR
+                // reduction), so that none of them waits at a later barrier alone
+                uint32_t any;
+                asm volatile(
+                    "{\n\t.reg .pred p, q;\n\t"
+                    "setp.ne.u32 p, %1, 0;\n\t"
+                    "bar.red.or.pred q, 1, 128, p;\n\t"
+                    "selp.u32 %0, 1, 0, q;\n\t}\n"
+                    : "=r"(any)
+                    : "r"((uint32_t)(!ok || err_set(bar)))
+                    : "memory");
+                if (any) {
+                    stop = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                // tile element (column c, row) at 8 (64 c + row) bytes; this thread's real part or imaginary part
+                float* ct = reinterpret_cast<float*>(sm + kPipeOffC + cs * kCTile) + 2 * row + part;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float pv[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * kTileC + 32 * h), pv);
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        float* e = ct + (size_t)(32 * h + c) * 2 * kTileC;
+                        *e = *e - pv[c];
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mb_arrive(&bar->acc_empty[ab]);
+                // generic-proxy tile writes -> visible to the TMA store
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (leader) {
+                    tma_store_tile(&tmA, rbase + bx * kTileC, rbase + by * kTileC, b, sbase + kPipeOffC + cs * kCTile);
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                    // the previous tile's store has read its buffer: release that stage
+                    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                    if (i >= 1) mb_arrive(&bar->c_empty[(int)((i - 1) % kCStages)]);
+                }
+            }
+        }
+        if (leader) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    if (err_set(bar) && tid == 0)
+        for (long long u = blockIdx.x; u < U; u += G) info[u / nblk] = -1;
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kPipeTmemCols));
 }
 
 }  // namespace tcu

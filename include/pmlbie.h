@@ -96,8 +96,11 @@ typedef struct {
     double   ms_kernels;          /* device time: modal kernels + assembly + rhs (ms)  */
     double   ms_lu;               /* device time: factorisation (ms)                   */
     double   ms_solve;            /* device time: solves + refinement + outputs (ms)   */
-    double   ms_far;              /* device time of the far-pair kernel launch (ms)    */
-    double   ms_near;             /* device time of the close-pair kernels (ms)        */
+    double   ms_far;              /* device time of the far-pair kernel launch (ms); it
+                                     runs beside the close-pair kernels, so ms_far and
+                                     ms_near overlap                                      */
+    double   ms_near;             /* device time of the close-pair kernels, on their own
+                                     high-priority stream (ms)                            */
     double   ms_assemble;         /* device time of Alpert assembly + diagonal (ms)    */
     int      launches;            /* CUDA kernel launches issued by the call           */
     int      far_pairs;           /* node pairs evaluated by the far-pair FFT kernel   */

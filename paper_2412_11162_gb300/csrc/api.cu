@@ -63,6 +63,10 @@ struct pmlbie_dev_extra {
     // by the last factorisation
     std::vector<cudaEvent_t> upd_ev;
     int upd_pairs = 0;
+    // high-priority stream of the close-pair chain beside the far kernel, and
+    // the fork / join events of the system build
+    cudaStream_t near_stream = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace {
@@ -157,7 +161,12 @@ void free_device(pmlbie_problem* prob) {
     prob->ws = nullptr;
     if (ex && ex->lu.exec) cudaGraphExecDestroy(ex->lu.exec);
     if (ex && ex->capture) cudaStreamDestroy(ex->capture);
+    if (ex && ex->near_stream) cudaStreamDestroy(ex->near_stream);
+    if (ex && ex->fork) cudaEventDestroy(ex->fork);
+    if (ex && ex->join) cudaEventDestroy(ex->join);
     if (ex) {
+        ex->near_stream = nullptr;
+        ex->fork = ex->join = nullptr;
         for (cudaEvent_t e : ex->upd_ev) cudaEventDestroy(e);
         ex->upd_ev.clear();
         ex->upd_pairs = 0;
@@ -267,23 +276,42 @@ void fresnel(double w1, double w2, double phi, double* out6) {
     out6[5] = ks.imag();
 }
 
-// modal kernels + assembly into w.A for modes [lo, hi); ev[0..3] bracket the
-// stages, ev[4] and ev[5] split the close-pair stage (Laplace modes, then the
-// float-float modes kernel of the mixed path)
+// modal kernels + assembly into w.A for modes [lo, hi).  The far kernel and
+// the close-pair chain (Laplace modes, float-float close pairs, FP64 PML close
+// pairs) are independent until the assembly and load different pipes (the
+// mixed path's far kernel the FP32 / integer issue, the PML pairs the FP64
+// pipe): the chain runs on a high-priority stream forked from s, so that its
+// CTAs are dispatched first and the far kernel's fill the SMs it leaves
+// (mostly during the latency-bound Laplace-mode kernel); the assembly waits
+// for both.  ev[0] = fork, ev[1] = far kernel done (on s), ev[4] / ev[5] =
+// Laplace modes / float-float close pairs done and ev[2] = chain done (on the
+// chain's stream), ev[6] = join, ev[3] = assembly done.
 // (the mixed path samples the far pairs in float-float arithmetic when the
 // problem's phases fit its range, else in FP64)
 int build_system(pmlbie_problem* prob, int precision, Workspace& w, int lo, int hi, cudaStream_t s,
                  cudaEvent_t* ev) {
     FarLaunch fl{lo, hi, w.A, nullptr, true};
+    pmlbie_dev_extra* ex = extra_of(prob);
+    if (!ex->near_stream) {
+        int least = 0, greatest = 0;
+        PMLBIE_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        PMLBIE_CUDA_TRY(cudaStreamCreateWithPriority(&ex->near_stream, cudaStreamNonBlocking, greatest));
+        PMLBIE_CUDA_TRY(cudaEventCreateWithFlags(&ex->fork, cudaEventDisableTiming));
+        PMLBIE_CUDA_TRY(cudaEventCreateWithFlags(&ex->join, cudaEventDisableTiming));
+    }
+    const bool ff = precision == PMLBIE_MIXED && far_ff_supported(prob);
+    cudaStream_t sn = ex->near_stream;
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[0], s));
-    if (precision == PMLBIE_MIXED && far_ff_supported(prob))
-        PMLBIE_CUDA_TRY(launch_far_ff(prob, fl, s));
-    else
-        PMLBIE_CUDA_TRY(launch_far(prob, fl, s));
+    PMLBIE_CUDA_TRY(cudaEventRecord(ex->fork, s));
+    PMLBIE_CUDA_TRY(cudaStreamWaitEvent(sn, ex->fork, 0));
+    // the far kernel first: its CTAs take the SMs the Laplace-mode kernel leaves idle
+    PMLBIE_CUDA_TRY(ff ? launch_far_ff(prob, fl, s) : launch_far(prob, fl, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[1], s));
-    PMLBIE_CUDA_TRY(launch_near(prob, lo, hi, w.zd, w.nout, s, ev[4], precision == PMLBIE_MIXED && far_ff_supported(prob),
-                                ev[5]));
-    PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
+    PMLBIE_CUDA_TRY(launch_near(prob, lo, hi, w.zd, w.nout, sn, ev[4], ff, ev[5]));
+    PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], sn));
+    PMLBIE_CUDA_TRY(cudaEventRecord(ex->join, sn));
+    PMLBIE_CUDA_TRY(cudaStreamWaitEvent(s, ex->join, 0));
+    PMLBIE_CUDA_TRY(cudaEventRecord(ev[6], s));
     PMLBIE_CUDA_TRY(launch_assemble(prob, lo, hi, w.nout, w.A, s));
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[3], s));
     return PMLBIE_OK;
@@ -631,7 +659,7 @@ struct SolveStats {
 static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool point, int lo, int hi, Workspace& w,
                        double2* u1, double2* phi1, double2* u2, double2* phi2, cudaStream_t s, SolveStats& st) {
     const int N = prob->P.N, nm = hi - lo, n2 = 2 * N;
-    cudaEvent_t ev[4], sev[6];
+    cudaEvent_t ev[4], sev[7];
     for (auto& e : ev) PMLBIE_CUDA_TRY(cudaEventCreate(&e));
     for (auto& e : sev) PMLBIE_CUDA_TRY(cudaEventCreate(&e));
     struct EvGuard {
@@ -639,7 +667,7 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
         cudaEvent_t* f;
         ~EvGuard() {
             for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
-            for (int i = 0; i < 6; ++i) cudaEventDestroy(f[i]);
+            for (int i = 0; i < 7; ++i) cudaEventDestroy(f[i]);
         }
     } guard{ev, sev};
     pmlbie_dev_extra* ex = extra_of(prob);
@@ -782,12 +810,13 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
     int nonfinite = 0;
     PMLBIE_CUDA_TRY(cudaMemcpy(info.data(), w.info, sizeof(int) * nm, cudaMemcpyDeviceToHost));
     PMLBIE_CUDA_TRY(cudaMemcpy(&nonfinite, w.nanflag, sizeof(int), cudaMemcpyDeviceToHost));
+    // far kernel and close-pair chain from the fork (they overlap), assembly from the join
     float t[3], f[3], fl = 0.f;
-    for (int i = 0; i < 3; ++i) {
-        cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]);
-        cudaEventElapsedTime(&f[i], sev[i], sev[i + 1]);
-    }
-    cudaEventElapsedTime(&fl, sev[1], sev[4]);
+    for (int i = 0; i < 3; ++i) cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]);
+    cudaEventElapsedTime(&f[0], sev[0], sev[1]);
+    cudaEventElapsedTime(&f[1], sev[0], sev[2]);
+    cudaEventElapsedTime(&f[2], sev[6], sev[3]);
+    cudaEventElapsedTime(&fl, sev[0], sev[4]);
     float fff = 0.f;
     cudaEventElapsedTime(&fff, sev[4], sev[5]);
     st.ms_near_ff += fff;

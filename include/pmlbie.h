@@ -125,6 +125,9 @@ typedef struct {
                                      tensor-core update launches) (ms) */
     int      lu_update_launches;  /* trailing updates (steps with a trailing matrix) of those
                                      factorisations, each timed by one event pair             */
+    double   ms_far_alone;        /* mixed: device time of the float-float far-pair kernel run
+                                     alone (its autotuning launch of the chosen CTA size, on the
+                                     first solve of this shape; 0 when not tuned) (ms)          */
 } pmlbie_report;
 
 /* Options of pmlbie_solve_ex (zero-initialise, then set struct_size). */

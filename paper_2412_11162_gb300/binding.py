@@ -49,7 +49,8 @@ class pmlbie_report(ctypes.Structure):
                 ("far_pairs_physical", ctypes.c_int), ("lu_graph_replays", ctypes.c_int),
                 ("far_pairs_per_cta", ctypes.c_int), ("far_pairs_sampled", ctypes.c_int),
                 ("far_pairs_sampled_physical", ctypes.c_int), ("ms_near_ff", ctypes.c_double),
-                ("ms_lu_update", ctypes.c_double), ("lu_update_launches", ctypes.c_int)]
+                ("ms_lu_update", ctypes.c_double), ("lu_update_launches", ctypes.c_int),
+                ("ms_far_alone", ctypes.c_double)]
 
 
 class pmlbie_solve_opts(ctypes.Structure):

@@ -1044,6 +1044,8 @@ int pmlbie_solve_ex(pmlbie_problem* prob, const pmlbie_solve_opts* o, void* dev_
         rep->backward_error = st.bwd;
         rep->lu_graph_replays = g_lu_graph_replays;
         rep->far_pairs_per_cta = g_far_pairs_per_cta;
+        rep->ms_far_alone =
+            precision == PMLBIE_MIXED && far_ff_supported(prob) ? far_ff_alone_ms(prob, chunk, false) : 0.0;
     }
     if (precision == PMLBIE_MIXED && st.unconverged)
         return fail(PMLBIE_ENOCONVERGE, "refinement missed its tolerance: residual " + std::to_string(st.resid) +

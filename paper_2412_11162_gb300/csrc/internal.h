@@ -171,6 +171,9 @@ struct FarLaunch {
     bool tune = false;
 };
 cudaError_t launch_far(const pmlbie_problem* prob, const FarLaunch& fl, cudaStream_t s);
+// device time (ms) of the float-float far kernel's chosen configuration in its
+// autotuning launch for this (N, M, modes, output) shape, run alone; 0 if not tuned
+float far_ff_alone_ms(const pmlbie_problem* prob, int modes, bool raw);
 // float-float far kernel of the mixed path (kernels_ff.cu); usable when
 // far_ff_supported (every |q| of the problem inside its sin / cos range)
 cudaError_t launch_far_ff(const pmlbie_problem* prob, const FarLaunch& fl, cudaStream_t s);

@@ -917,6 +917,14 @@ bool far_ff_supported(const pmlbie_problem* prob) {
 
 static std::mutex g_far_ff_tune_mu;
 static std::map<std::tuple<int, int, int, int>, int> g_far_ff_tuned;
+// device time of the chosen configuration in its tuning launch (alone on the GPU)
+static std::map<std::tuple<int, int, int, int>, float> g_far_ff_tuned_ms;
+
+float far_ff_alone_ms(const pmlbie_problem* prob, int modes, bool raw) {
+    std::lock_guard<std::mutex> lk(g_far_ff_tune_mu);
+    auto it = g_far_ff_tuned_ms.find(std::make_tuple(prob->P.N, prob->P.M, modes, raw ? 1 : 0));
+    return it == g_far_ff_tuned_ms.end() ? 0.f : it->second;
+}
 
 cudaError_t launch_far_ff(const pmlbie_problem* prob, const FarLaunch& fl, cudaStream_t s) {
     const int N = prob->P.N, M = prob->P.M;
@@ -984,6 +992,7 @@ cudaError_t launch_far_ff(const pmlbie_problem* prob, const FarLaunch& fl, cudaS
     if (!best) return cudaErrorInvalidConfiguration;
     std::lock_guard<std::mutex> lk(g_far_ff_tune_mu);
     g_far_ff_tuned[key] = best;
+    g_far_ff_tuned_ms[key] = tbest;
     g_far_pairs_per_cta = best;
     return cudaSuccess;
 }

@@ -234,6 +234,11 @@ def test_solve_mixed_config1(torch):
     out, rep = P.solve([np.pi / 6], precision=PMLBIE_MIXED, allow_noconverge=True)
     print("mixed refinement iterations", rep.refine_iters, "residual %.2e" % rep.residual)
     check_densities(out, oracle_solution(**CFG1), 1e-6, 1e-11, "mixed")
+    # stage timers: the close-pair chain (its own stream) from the fork, its parts inside it;
+    # the far kernel's time alone from its autotuning launch
+    assert rep.ms_far > 0 and rep.ms_near > 0 and rep.ms_assemble > 0
+    assert rep.ms_near_laplace + rep.ms_near_ff <= rep.ms_near * (1 + 1e-6)
+    assert rep.ms_far_alone > 0
 
 
 def test_flat_interface_gives_zero_field(torch):

@@ -48,7 +48,7 @@ std::vector<double2> to_d2(const std::vector<cd>& v) {
 struct LuGraph {
     cudaGraphExec_t exec = nullptr;
     int precision = -1, n = 0, batch = 0;
-    const void *A = nullptr, *piv = nullptr, *info = nullptr, *img = nullptr;
+    const void *A = nullptr, *piv = nullptr, *info = nullptr, *img = nullptr, *ptab = nullptr;
     long launches = 0;          // kernels in the graph
     bool unavailable = false;   // capture failed once: launch directly
 };
@@ -190,6 +190,7 @@ struct Workspace {
             *X = nullptr, *R = nullptr;
     float2 *A32 = nullptr, *w32 = nullptr, *dinv = nullptr;
     unsigned char* img = nullptr;   // split operand images of the FP32 LU's trailing updates
+    int2* ptab = nullptr;           // the FP32 LU's row-interchange mapping per step
     int *piv = nullptr, *info = nullptr, *active = nullptr, *nanflag = nullptr;
     double *rn = nullptr, *bn = nullptr, *xn = nullptr, *an = nullptr, *rpar = nullptr;
     size_t bytes = 0;
@@ -227,6 +228,7 @@ Workspace plan(const pmlbie_problem* prob, int precision, int nrhs, int nmodes, 
         // per mode: 1/16 of the factor's bytes) for the correction solves
         if (n2 % 32 == 0) w.dinv = (float2*)take(sizeof(float2) * nm * diag_inv_elems((int)n2));
         w.img = (unsigned char*)take(lu_image_bytes((int)n2, (int)nm));
+        w.ptab = (int2*)take(sizeof(int2) * lu_ptab_elems((int)n2, (int)nm));
         w.R = (double2*)take(sizeof(double2) * nm * n2 * nrhs);
     }
     w.zd = (double2*)take(near_zd_bytes(std::max<size_t>(np, 1), M, true));
@@ -573,9 +575,10 @@ __global__ void wait_probe_kernel(long long iters, int* expired) {
 thread_local int g_lu_graph_replays = 0;
 
 static cudaError_t lu_direct(int precision, int n, int batch, void* A, int* piv, int* info, unsigned char* img,
-                             cudaStream_t s, cudaEvent_t* upd_ev = nullptr) {
-    return precision == PMLBIE_FP64 ? batched_lu<double2>(n, batch, (double2*)A, piv, info, s, nullptr, upd_ev)
-                                    : batched_lu<float2>(n, batch, (float2*)A, piv, info, s, img, upd_ev);
+                             int2* ptab, cudaStream_t s, cudaEvent_t* upd_ev = nullptr) {
+    return precision == PMLBIE_FP64
+               ? batched_lu<double2>(n, batch, (double2*)A, piv, info, s, nullptr, nullptr, upd_ev)
+               : batched_lu<float2>(n, batch, (float2*)A, piv, info, s, img, ptab, upd_ev);
 }
 
 // 2 x ceil(n / 32) timing events of the trailing updates; the pairs used are
@@ -593,16 +596,16 @@ static cudaError_t ensure_update_events(pmlbie_dev_extra* ex, int n) {
 }
 
 static int batched_lu_graphed(pmlbie_problem* prob, int precision, int n, int batch, void* A, int* piv, int* info,
-                              unsigned char* img, cudaStream_t s) {
+                              unsigned char* img, int2* ptab, cudaStream_t s) {
     pmlbie_dev_extra* ex = extra_of(prob);
     LuGraph& g = ex->lu;
     PMLBIE_CUDA_TRY(ensure_update_events(ex, n));
     if (g.unavailable) {
-        PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, img, s, ex->upd_ev.data()));
+        PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, img, ptab, s, ex->upd_ev.data()));
         return PMLBIE_OK;
     }
     if (!(g.exec && g.precision == precision && g.n == n && g.batch == batch && g.A == A && g.piv == piv &&
-          g.info == info && g.img == img)) {
+          g.info == info && g.img == img && g.ptab == ptab)) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
         g = LuGraph();
         if (!ex->capture) PMLBIE_CUDA_TRY(cudaStreamCreateWithFlags(&ex->capture, cudaStreamNonBlocking));
@@ -611,7 +614,8 @@ static int batched_lu_graphed(pmlbie_problem* prob, int precision, int n, int ba
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(ex->capture, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            const cudaError_t el = lu_direct(precision, n, batch, A, piv, info, img, ex->capture, ex->upd_ev.data());
+            const cudaError_t el =
+                lu_direct(precision, n, batch, A, piv, info, img, ptab, ex->capture, ex->upd_ev.data());
             e = cudaStreamEndCapture(ex->capture, &graph);
             if (el != cudaSuccess) e = el;
         }
@@ -624,7 +628,7 @@ static int batched_lu_graphed(pmlbie_problem* prob, int precision, int n, int ba
             if (g.exec) cudaGraphExecDestroy(g.exec);
             g = LuGraph();
             g.unavailable = true;
-            PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, img, s, ex->upd_ev.data()));
+            PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, img, ptab, s, ex->upd_ev.data()));
             return PMLBIE_OK;
         }
         g.launches = captured;
@@ -635,6 +639,7 @@ static int batched_lu_graphed(pmlbie_problem* prob, int precision, int n, int ba
         g.piv = piv;
         g.info = info;
         g.img = img;
+        g.ptab = ptab;
     }
     PMLBIE_CUDA_TRY(cudaGraphLaunch(g.exec, s));
     count_launch(g.launches);
@@ -687,13 +692,13 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
     bool unconverged = false;
     std::vector<double> mres(nm, 0.0), mbwd(nm, 0.0);
     if (precision == PMLBIE_FP64) {
-        if ((rc = batched_lu_graphed(prob, PMLBIE_FP64, n2, nm, w.A, w.piv, w.info, nullptr, s))) return rc;
+        if ((rc = batched_lu_graphed(prob, PMLBIE_FP64, n2, nm, w.A, w.piv, w.info, nullptr, nullptr, s))) return rc;
         PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
         PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.X, w.B, xbytes, cudaMemcpyDeviceToDevice, s));
         PMLBIE_CUDA_TRY((batched_lu_solve<double2, double2>(n2, nm, n_rhs, w.A, w.piv, w.X, s)));
     } else {
         PMLBIE_CUDA_TRY(convert_fro2_c128(n2, nm, w.A, w.A32, w.an, s));
-        if ((rc = batched_lu_graphed(prob, PMLBIE_MIXED, n2, nm, w.A32, w.piv, w.info, w.img, s))) return rc;
+        if ((rc = batched_lu_graphed(prob, PMLBIE_MIXED, n2, nm, w.A32, w.piv, w.info, w.img, w.ptab, s))) return rc;
         if (w.dinv) PMLBIE_CUDA_TRY(batched_diag_inv(n2, nm, w.A32, w.dinv, s));
         PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
         PMLBIE_CUDA_TRY(cudaMemsetAsync(w.X, 0, xbytes, s));
@@ -751,7 +756,7 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
                 }
                 PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.active, act.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, s));
             }
-            PMLBIE_CUDA_TRY(refine_step(n2, nm, n_rhs, w.A32, w.piv, w.R, w.w32, w.X, s, w.active, w.dinv));
+            PMLBIE_CUDA_TRY(refine_step(n2, nm, n_rhs, w.A32, w.piv, w.R, w.w32, w.X, s, w.active, w.dinv, w.ptab));
         }
         const int nslow = (int)std::count(slow.begin(), slow.end(), 1);
         if (nslow > 0) {
@@ -781,7 +786,8 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
             rc = gmres_refine(n2, gn, n_rhs, w.A + g0 * mat, w.A32 + g0 * mat, w.piv + (size_t)g0 * n2,
                               w.B + g0 * vec, w.X + g0 * vec, gslow, w.active, gm, kGmresM, kGmresCycles, kTolRel,
                               kTolBwd, kTolFloor, gan, s, git, gres, gbwd,
-                              w.dinv ? w.dinv + (size_t)g0 * diag_inv_elems(n2) : nullptr);
+                              w.dinv ? w.dinv + (size_t)g0 * diag_inv_elems(n2) : nullptr,
+                              w.ptab + (size_t)g0 * lu_ptab_elems(n2, 1));
             cudaStreamSynchronize(s);
             cudaFree(gm);
             if (rc) return rc;

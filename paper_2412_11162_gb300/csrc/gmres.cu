@@ -282,7 +282,7 @@ int gmres_refine(int n, int batch, int nrhs, const double2* A, const float2* LU3
                  const double2* B, double2* X, std::vector<int>& act, int* active_dev, void* scratch, int m,
                  int max_cycles, double tol, double tol_bw, double tol_floor, const std::vector<double>& an2,
                  cudaStream_t s, int& iters, std::vector<double>& mode_res, std::vector<double>& mode_bwd,
-                 const float2* dinv) {
+                 const float2* dinv, const int2* ptab) {
     const size_t vec = (size_t)batch * n * nrhs, ninst = (size_t)batch * nrhs;
     char* p = (char*)scratch;
     auto take = [&](size_t bytes) {
@@ -369,7 +369,7 @@ int gmres_refine(int n, int batch, int nrhs, const double2* A, const float2* LU3
             // z_j = (L U)^{-1} v_j: FP32 triangular solves (one CTA per system;
             // flexible GMRES absorbs their rounding)
             GM_TRY(convert_to_c64((int64_t)vec, Vj, w32, s));
-            GM_TRY((batched_lu_solve<float2, float2>(n, batch, nrhs, LU32, piv, w32, s, active_dev, dinv)));
+            GM_TRY((batched_lu_solve<float2, float2>(n, batch, nrhs, LU32, piv, w32, s, active_dev, dinv, ptab)));
             c64_to_c128_kernel<<<(unsigned)std::min<size_t>(blocks_for(vec), 152 * 32), 256, 0, s>>>((int64_t)vec, w32, Zj);
             count_launch();
             GM_TRY(matvec(n, batch, nrhs, A, Zj, W, active_dev, s));

@@ -276,9 +276,15 @@ int peak_probe(int kind, double* out_tflops, cudaStream_t s);
 // captured in a graph)
 // img: for complex64, lu_image_bytes(n, batch) bytes of device scratch (16-byte
 // aligned) holding one step's split operand images; unused for complex128
+// ptab: for complex64, lu_ptab_elems(n, batch) entries receiving each step's
+// row-interchange mapping: the interchanges are applied to the columns right of
+// each panel only (L keeps the row order of its step), piv keeps LAPACK's
+// interchange indices, and the solves take ptab; unused for complex128 (L in
+// getrf's row order, piv the row permutation)
 template <typename T>
 cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s, unsigned char* img,
-                       cudaEvent_t* upd_ev = nullptr);
+                       int2* ptab, cudaEvent_t* upd_ev = nullptr);
+size_t lu_ptab_elems(int n, int batch);
 // scratch bytes of the complex64 factorisation's operand images (the first
 // step's 64-row blocks of L21 and 64-column blocks of U12, 96 KB per pair)
 size_t lu_image_bytes(int n, int batch);
@@ -291,8 +297,11 @@ cudaError_t lu_prepare();
 // dinv: optional inverses of the 32 x 32 diagonal blocks (batched_diag_inv),
 // used when n is a multiple of 32
 template <typename T, typename TF>
+// ptab: the complex64 factorisation's interchange mapping (batched_lu); then
+// piv is not read
 cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int* piv, T* B,
-                             cudaStream_t s, const int* active = nullptr, const TF* dinv = nullptr);
+                             cudaStream_t s, const int* active = nullptr, const TF* dinv = nullptr,
+                             const int2* ptab = nullptr);
 // inverses of the 32 x 32 diagonal blocks of L (unit lower) and U of every
 // complex64 factor, [b][n / 32][2][32 x 32] column-major (n a multiple of 32)
 cudaError_t batched_diag_inv(int n, int batch, const float2* LU, float2* dinv, cudaStream_t s);
@@ -311,13 +320,13 @@ int gmres_refine(int n, int batch, int nrhs, const double2* A, const float2* LU3
                  const double2* B, double2* X, std::vector<int>& act, int* active_dev, void* scratch, int m,
                  int max_cycles, double tol, double tol_bw, double tol_floor, const std::vector<double>& an2,
                  cudaStream_t s, int& iters, std::vector<double>& mode_res, std::vector<double>& mode_bwd,
-                 const float2* dinv = nullptr);
+                 const float2* dinv = nullptr, const int2* ptab = nullptr);
 // R = B - A X with |R|^2, |B|^2, |X|^2 per (matrix, rhs)
 cudaError_t residual_c128(int n, int batch, int nrhs, const double2* A, const double2* X,
                           const double2* B, double2* R, double* rnorm, double* bnorm, double* xnorm,
                           cudaStream_t s, const int* active = nullptr);
 cudaError_t refine_step(int n, int batch, int nrhs, const float2* LU32, const int* piv,
                         const double2* R, float2* work32, double2* X, cudaStream_t s,
-                        const int* active = nullptr, const float2* dinv = nullptr);
+                        const int* active = nullptr, const float2* dinv = nullptr, const int2* ptab = nullptr);
 
 }  // namespace pmlbie

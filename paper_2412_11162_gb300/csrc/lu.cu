@@ -535,11 +535,18 @@ int panel_width(int m) {
 // the source slot of every destination slot; the tile's slot rows are then
 // loaded already permuted, solved and written back.  The solve takes four
 // lanes per column (eight rows each, in registers) and broadcasts x_j by
-// shuffles inside the group, so it needs no block barrier per step.
+// shuffles inside the group, so it needs no block barrier per step.  The
+// tiles start at column col0: 0 applies the interchanges to every column
+// outside the panel (LAPACK getrf's row order of L); col0 = k0 + kb to the
+// columns right of the panel only, and then the CTAs of tile 0 write the step's
+// slot mapping to ptab ([mode][step][2 kNB] pairs (row, row its content comes
+// from), (-1, -1) beyond the slots), with which the forward solve applies the
+// step's interchanges to the right-hand sides when it reaches the step's block.
 constexpr int kSwapCols = 64;
 
 template <typename T>
-__global__ void __launch_bounds__(256) swap_trsm_kernel(int n, int k0, int kb, T* A, const int* piv) {
+__global__ void __launch_bounds__(256) swap_trsm_kernel(int n, int k0, int kb, int col0, T* A, const int* piv,
+                                                        int2* ptab) {
     extern __shared__ unsigned char smraw[];
     T* blk = reinterpret_cast<T*>(smraw);                 // [kSwapCols][2*kNB]: slots of each column
     T* L = blk + (size_t)kSwapCols * 2 * kNB;             // [kNB][kNB] (col-major), right tiles only
@@ -550,8 +557,8 @@ __global__ void __launch_bounds__(256) swap_trsm_kernel(int n, int k0, int kb, T
     const int b = blockIdx.y;
     T* a = A + (size_t)b * n * n;
     const int* pv = piv + (size_t)b * n;
-    const int c0 = blockIdx.x * kSwapCols;
-    const int ncol = min(kSwapCols, n - c0);
+    const int c0 = col0 + blockIdx.x * kSwapCols;
+    const int ncol = min(kSwapCols, n - c0);   // <= 0: a CTA that only writes ptab
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid < 32) {
         const int p = lane < kb ? pv[k0 + lane] : -1;
@@ -584,6 +591,11 @@ __global__ void __launch_bounds__(256) swap_trsm_kernel(int n, int k0, int kb, T
     }
     __syncthreads();
     const int ns = nslots;
+    if (ptab && blockIdx.x == 0 && tid < 2 * kNB) {
+        const int steps = (n + kNB - 1) / kNB;
+        ptab[((size_t)b * steps + k0 / kNB) * 2 * kNB + tid] =
+            tid < ns ? make_int2(srow[tid], srow[ssrc[tid]]) : make_int2(-1, -1);
+    }
     const bool right = c0 + ncol > k0 + kb;
     // load the slot rows permuted: slot r of column c at blk[c * 2kNB + r]
     for (int idx = tid; idx < ncol * ns; idx += blockDim.x) {
@@ -761,7 +773,7 @@ __device__ __forceinline__ void block_pair_update(const TF* col, int n, const T*
 
 template <typename T, typename TF, int RM>
 __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, const TF* LU, const int* perm,
-                                                       T* B, const int* active, const TF* dinv) {
+                                                       T* B, const int* active, const TF* dinv, const int2* ptab) {
     const int R = RM == 1 ? 1 : Rg;    // compile-time 1 in the single-wave variant
     const int b = blockIdx.x, r0 = blockIdx.y * R, nr = RM == 1 ? 1 : min(R, nrhs - r0);
     if (active && !active[b]) return;
@@ -773,11 +785,15 @@ __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, 
     __shared__ __align__(16) TF sD[kNB * kNB];     // diagonal block, sD[col * kNB + row]
     constexpr int kDiagPer = (int)(kNB * kNB * sizeof(TF) / (512 * 16));   // 16-byte pieces per thread
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nblk = (n + kNB - 1) / kNB;
+    // with ptab the factor's L columns keep the row order of their step: the
+    // right-hand sides are loaded as they are and each step's interchanges are
+    // applied when the forward solve reaches its block; else loaded permuted
+    const int2* pt = ptab ? ptab + (size_t)b * nblk * 2 * kNB : nullptr;
     for (int idx = tid; idx < n * nr; idx += blockDim.x) {
         const int i = idx / nr, q = idx - i * nr;
-        sx[i * R + q] = x[(size_t)pm[i] * nrhs + r0 + q];
+        sx[i * R + q] = x[(size_t)(pt ? i : pm[i]) * nrhs + r0 + q];
     }
-    const int nblk = (n + kNB - 1) / kNB;
     // the pair path: full blocks only, and with several right-hand sides only
     // for complex64 accumulators (register budget of 512 threads)
     const bool vec = (n % kNB) == 0 && (RM == 1 || sizeof(T) == 8);
@@ -822,6 +838,11 @@ __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, 
         for (int t = 0; t < kDiagPer; ++t) reinterpret_cast<float4*>(sD)[tid + t * 512] = reg[t];
     };
     float4 dreg[kDiagPer];
+    int2 pn0 = make_int2(-1, -1), pn1 = pn0;   // interchange entries of the next block (ptab)
+    if (pt && warp < nr) {
+        pn0 = pt[lane];
+        pn1 = pt[32 + lane];
+    }
     // forward: L y = x (unit diagonal)
     if (vec) {
         fetch_diag(0, kNB, 0, dreg);
@@ -836,6 +857,21 @@ __global__ void __launch_bounds__(512) lu_solve_kernel(int n, int nrhs, int Rg, 
                 sD[c * kNB + i] = a[(size_t)(j0 + c) * n + j0 + i];
             }
             __syncthreads();
+        }
+        if (pt && warp < nr) {
+            // this step's interchanges on the warp's right-hand side: slots lane, lane + 32
+            // (entries loaded one block ahead, off the critical path)
+            const int2 e0 = pn0, e1 = pn1;
+            if (j0 + kNB < n) {
+                pn0 = pt[(size_t)(j0 / kNB + 1) * 2 * kNB + lane];
+                pn1 = pt[(size_t)(j0 / kNB + 1) * 2 * kNB + 32 + lane];
+            }
+            const T v0 = e0.x >= 0 ? sx[e0.y * R + warp] : Cx<T>::mk(0, 0);
+            const T v1 = e1.x >= 0 ? sx[e1.y * R + warp] : Cx<T>::mk(0, 0);
+            __syncwarp();
+            if (e0.x >= 0) sx[e0.x * R + warp] = v0;
+            if (e1.x >= 0) sx[e1.x * R + warp] = v1;
+            __syncwarp();
         }
         if (inv) {
             apply_inv(j0);
@@ -1191,6 +1227,8 @@ cudaError_t trailing_tensor_map(CUtensorMap* tm, float2* A, int n, int batch) {
 
 }  // namespace
 
+size_t lu_ptab_elems(int n, int batch) { return (size_t)batch * ((n + kNB - 1) / kNB) * 2 * kNB; }
+
 size_t lu_image_bytes(int n, int batch) {
     const int nblk = n > kNB ? tcu::update_blocks(n, 0, kNB) : 0;
     return (size_t)batch * nblk * (tcu::kAImg + tcu::kBImg);
@@ -1198,9 +1236,14 @@ size_t lu_image_bytes(int n, int batch) {
 
 template <typename T>
 cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s, unsigned char* img,
-                       cudaEvent_t* upd_ev) {
+                       int2* ptab, cudaEvent_t* upd_ev) {
     cudaError_t pe = lu_prepare<T>();
     if (pe != cudaSuccess) return pe;
+    if constexpr (sizeof(T) == 8) {
+        if (!ptab) return cudaErrorInvalidValue;
+    } else {
+        ptab = nullptr;
+    }
     // complex64: the trailing matrix as a TMA tensor, and the SMs for the
     // persistent update
     CUtensorMap tmA;
@@ -1243,9 +1286,12 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
             panel_kernel<T><<<batch, kPanelThreads, smp, s>>>(n, k0, kb, w, A, piv, info);
         }
         count_launch(2);
-        dim3 g1((n + kSwapCols - 1) / kSwapCols, batch);
+        // complex64: the interchanges reach the right columns only (the solve
+        // applies them to the right-hand sides from ptab); complex128: all columns
+        const int col0 = ptab ? k0 + kb : 0;
+        dim3 g1((unsigned)std::max(1, (n - col0 + kSwapCols - 1) / kSwapCols), batch);
         size_t sm1 = sizeof(T) * ((size_t)kSwapCols * 2 * kNB + kNB * kNB);
-        swap_trsm_kernel<T><<<g1, 256, sm1, s>>>(n, k0, kb, A, piv);
+        swap_trsm_kernel<T><<<g1, 256, sm1, s>>>(n, k0, kb, col0, A, piv, ptab);
         int rem = n - k0 - kb;
         if (rem > 0) {
             cudaError_t ee;
@@ -1274,15 +1320,17 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
                 return ee;
         }
     }
-    const size_t smq = 2 * sizeof(int) * (size_t)n;
-    perm_kernel<<<batch, 256, smq, s>>>(n, piv);
-    count_launch();
+    if (!ptab) {
+        const size_t smq = 2 * sizeof(int) * (size_t)n;
+        perm_kernel<<<batch, 256, smq, s>>>(n, piv);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
 template <typename T, typename TF>
 cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int* piv, T* B,
-                             cudaStream_t s, const int* active, const TF* dinv) {
+                             cudaStream_t s, const int* active, const TF* dinv, const int2* ptab) {
     // right-hand sides per CTA: up to kSolveR, as many as fit in shared memory
     // (about 200 KB for the group)
     int R = std::min(nrhs, kSolveR);
@@ -1296,13 +1344,13 @@ cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int
             cudaError_t e = allow_max_smem(lu_solve_kernel<T, TF, 1>);
             if (e != cudaSuccess) return e;
         }
-        lu_solve_kernel<T, TF, 1><<<g, 512, sm, s>>>(n, nrhs, R, LU, piv, B, active, dinv);
+        lu_solve_kernel<T, TF, 1><<<g, 512, sm, s>>>(n, nrhs, R, LU, piv, B, active, dinv, ptab);
     } else {
         if (big) {
             cudaError_t e = allow_max_smem(lu_solve_kernel<T, TF, kSolveR>);
             if (e != cudaSuccess) return e;
         }
-        lu_solve_kernel<T, TF, kSolveR><<<g, 512, sm, s>>>(n, nrhs, R, LU, piv, B, active, dinv);
+        lu_solve_kernel<T, TF, kSolveR><<<g, 512, sm, s>>>(n, nrhs, R, LU, piv, B, active, dinv, ptab);
     }
     count_launch();
     return cudaGetLastError();
@@ -1310,16 +1358,16 @@ cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int
 
 template cudaError_t lu_prepare<double2>();
 template cudaError_t lu_prepare<float2>();
-template cudaError_t batched_lu<double2>(int, int, double2*, int*, int*, cudaStream_t, unsigned char*,
+template cudaError_t batched_lu<double2>(int, int, double2*, int*, int*, cudaStream_t, unsigned char*, int2*,
                                           cudaEvent_t*);
-template cudaError_t batched_lu<float2>(int, int, float2*, int*, int*, cudaStream_t, unsigned char*,
+template cudaError_t batched_lu<float2>(int, int, float2*, int*, int*, cudaStream_t, unsigned char*, int2*,
                                          cudaEvent_t*);
 template cudaError_t batched_lu_solve<double2, double2>(int, int, int, const double2*, const int*, double2*,
-                                                        cudaStream_t, const int*, const double2*);
+                                                        cudaStream_t, const int*, const double2*, const int2*);
 template cudaError_t batched_lu_solve<float2, float2>(int, int, int, const float2*, const int*, float2*,
-                                                      cudaStream_t, const int*, const float2*);
+                                                      cudaStream_t, const int*, const float2*, const int2*);
 template cudaError_t batched_lu_solve<double2, float2>(int, int, int, const float2*, const int*, double2*,
-                                                       cudaStream_t, const int*, const float2*);
+                                                       cudaStream_t, const int*, const float2*, const int2*);
 
 cudaError_t convert_to_c64(int64_t count, const double2* src, float2* dst, cudaStream_t s) {
     int blocks = (int)std::min<int64_t>((count + 255) / 256, 152 * 32);
@@ -1362,11 +1410,11 @@ cudaError_t batched_diag_inv(int n, int batch, const float2* LU, float2* dinv, c
 
 cudaError_t refine_step(int n, int batch, int nrhs, const float2* LU32, const int* piv,
                         const double2* R, float2* work32, double2* X, cudaStream_t s, const int* active,
-                        const float2* dinv) {
+                        const float2* dinv, const int2* ptab) {
     int64_t cnt = (int64_t)batch * n * nrhs;
     cudaError_t e = convert_to_c64(cnt, R, work32, s);
     if (e != cudaSuccess) return e;
-    e = batched_lu_solve<float2, float2>(n, batch, nrhs, LU32, piv, work32, s, active, dinv);
+    e = batched_lu_solve<float2, float2>(n, batch, nrhs, LU32, piv, work32, s, active, dinv, ptab);
     if (e != cudaSuccess) return e;
     add_correction_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(cnt, (int64_t)n * nrhs, work32, X, active);
     count_launch();

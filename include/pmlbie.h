@@ -93,8 +93,12 @@ typedef struct {
     int      near_pairs;          /* close pairs evaluated with the kernel split       */
     int      refine_iters;        /* max refinement iterations over modes (mixed)      */
     double   residual;            /* max over modes/RHS of ||B - A x|| / ||B||         */
-    double   ms_kernels;          /* device time: modal kernels + assembly + rhs (ms)  */
-    double   ms_lu;               /* device time: factorisation (ms)                   */
+    double   ms_kernels;          /* device time: modal kernels + assembly, + rhs in the FP64
+                                     path (the mixed path forms the right-hand sides beside
+                                     its factorisation) (ms)                                */
+    double   ms_lu;               /* device time: factorisation (mixed: complex64 conversion,
+                                     LU and diagonal-block inverses, on a high-priority stream
+                                     beside the right-hand sides) (ms)                      */
     double   ms_solve;            /* device time: solves + refinement + outputs (ms)   */
     double   ms_far;              /* device time of the far-pair kernel launch (ms); it
                                      runs beside the close-pair kernels, so ms_far and

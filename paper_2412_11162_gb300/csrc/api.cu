@@ -679,13 +679,25 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
     int rc;
     PMLBIE_CUDA_TRY(cudaEventRecord(ev[0], s));
     if ((rc = build_system(prob, precision, w, lo, hi, s, sev))) return rc;
+    // mixed: the right-hand sides (the FP64 block product, FP64-pipe bound) are
+    // formed on s beside the complex64 conversion and factorisation, which run
+    // on the high-priority stream and read / write only the FP32 copy; they
+    // join before the refinement.  FP64: the factorisation overwrites w.A, so
+    // the right-hand sides come first.
+    const bool side = precision == PMLBIE_MIXED;
+    cudaStream_t slu = side ? ex->near_stream : s;
+    if (side) {
+        PMLBIE_CUDA_TRY(cudaEventRecord(ev[1], s));
+        PMLBIE_CUDA_TRY(cudaEventRecord(ex->fork, s));
+        PMLBIE_CUDA_TRY(cudaStreamWaitEvent(slu, ex->fork, 0));
+    }
     if (point)
         PMLBIE_CUDA_TRY(launch_point_rhs(prob, n_rhs, lo, hi, w.rpar, ex->speed, w.b1, w.b2, s));
     else
         PMLBIE_CUDA_TRY(launch_rhs(prob, n_rhs, lo, hi, w.rpar, ex->nu_r, ex->nu_z, ex->speed, w.b1, w.b2, s));
     PMLBIE_CUDA_TRY(launch_block_rhs(prob, n_rhs, nm, w.A, w.b1, w.b2, w.B, s));
-    PMLBIE_CUDA_TRY(cudaEventRecord(ev[1], s));
-    PMLBIE_CUDA_TRY(cudaMemsetAsync(w.info, 0, sizeof(int) * nm, s));
+    if (!side) PMLBIE_CUDA_TRY(cudaEventRecord(ev[1], s));
+    PMLBIE_CUDA_TRY(cudaMemsetAsync(w.info, 0, sizeof(int) * nm, slu));
     const size_t xbytes = sizeof(double2) * (size_t)nm * n2 * n_rhs;
     int iters = 0;
     double resid = 0.0, bwd = 0.0;
@@ -697,10 +709,13 @@ static int solve_chunk(pmlbie_problem* prob, int precision, int n_rhs, bool poin
         PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.X, w.B, xbytes, cudaMemcpyDeviceToDevice, s));
         PMLBIE_CUDA_TRY((batched_lu_solve<double2, double2>(n2, nm, n_rhs, w.A, w.piv, w.X, s)));
     } else {
-        PMLBIE_CUDA_TRY(convert_fro2_c128(n2, nm, w.A, w.A32, w.an, s));
-        if ((rc = batched_lu_graphed(prob, PMLBIE_MIXED, n2, nm, w.A32, w.piv, w.info, w.img, w.ptab, s))) return rc;
-        if (w.dinv) PMLBIE_CUDA_TRY(batched_diag_inv(n2, nm, w.A32, w.dinv, s));
-        PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], s));
+        PMLBIE_CUDA_TRY(convert_fro2_c128(n2, nm, w.A, w.A32, w.an, slu));
+        if ((rc = batched_lu_graphed(prob, PMLBIE_MIXED, n2, nm, w.A32, w.piv, w.info, w.img, w.ptab, slu)))
+            return rc;
+        if (w.dinv) PMLBIE_CUDA_TRY(batched_diag_inv(n2, nm, w.A32, w.dinv, slu));
+        PMLBIE_CUDA_TRY(cudaEventRecord(ev[2], slu));
+        PMLBIE_CUDA_TRY(cudaEventRecord(ex->join, slu));
+        PMLBIE_CUDA_TRY(cudaStreamWaitEvent(s, ex->join, 0));
         PMLBIE_CUDA_TRY(cudaMemsetAsync(w.X, 0, xbytes, s));
         PMLBIE_CUDA_TRY(cudaMemcpyAsync(w.R, w.B, xbytes, cudaMemcpyDeviceToDevice, s));
         // refinement: FP64 residual with the FP64 matrix, FP32 correction solve; modes whose

@@ -546,7 +546,7 @@ constexpr int kSwapCols = 64;
 
 template <typename T>
 __global__ void __launch_bounds__(256) swap_trsm_kernel(int n, int k0, int kb, int col0, T* A, const int* piv,
-                                                        int2* ptab) {
+                                                        int2* ptab, unsigned char* bimg, int nblk) {
     extern __shared__ unsigned char smraw[];
     T* blk = reinterpret_cast<T*>(smraw);                 // [kSwapCols][2*kNB]: slots of each column
     T* L = blk + (size_t)kSwapCols * 2 * kNB;             // [kNB][kNB] (col-major), right tiles only
@@ -646,6 +646,27 @@ __global__ void __launch_bounds__(256) swap_trsm_kernel(int n, int k0, int kb, i
         const int c = idx / ns, r = idx - c * ns;
         const int col = c0 + c;
         if (col < k0 || col >= k0 + kb) a[(size_t)col * n + srow[r]] = blk[c * 2 * kNB + r];
+    }
+    if constexpr (sizeof(T) == 8) {
+        // complex64 with col0 = k0 + kb: this tile is column block blockIdx.x of the
+        // trailing update; its B' image (the TF32 hi / lo split of [Re U12; Im U12]
+        // in the update's shared-memory layout, tc_update.cuh) from the solved rows
+        if (bimg && ncol > 0) {
+            uint4* hi = reinterpret_cast<uint4*>(bimg + ((size_t)b * nblk + blockIdx.x) * tcu::kBImg);
+            uint4* lo = hi + tcu::kBBytes / 16;
+            for (int u = tid; u < (int)(tcu::kBBytes / 16); u += blockDim.x) {
+                const int kc = u >> 6, j = u & 63, kk = (kc * 4) & 31;
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int k = kk + e;
+                    const T v = (j < ncol && k < kb) ? blk[j * 2 * kNB + k] : Cx<T>::mk(0, 0);
+                    tcu::split_tf32(kc < 8 ? v.x : v.y, h[e], l[e]);
+                }
+                hi[u] = make_uint4(h[0], h[1], h[2], h[3]);
+                lo[u] = make_uint4(l[0], l[1], l[2], l[3]);
+            }
+        }
     }
 }
 
@@ -1287,23 +1308,25 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
         }
         count_launch(2);
         // complex64: the interchanges reach the right columns only (the solve
-        // applies them to the right-hand sides from ptab); complex128: all columns
+        // applies them to the right-hand sides from ptab), and each 64-column tile
+        // writes the B' image of its column block of the update; complex128: all columns
         const int col0 = ptab ? k0 + kb : 0;
+        const int nblk = n - k0 - kb > 0 ? tcu::update_blocks(n, k0, kb) : 0;
+        unsigned char* bimg = ptab && nblk > 0 ? img + (size_t)batch * nblk * tcu::kAImg : nullptr;
         dim3 g1((unsigned)std::max(1, (n - col0 + kSwapCols - 1) / kSwapCols), batch);
         size_t sm1 = sizeof(T) * ((size_t)kSwapCols * 2 * kNB + kNB * kNB);
-        swap_trsm_kernel<T><<<g1, 256, sm1, s>>>(n, k0, kb, col0, A, piv, ptab);
+        swap_trsm_kernel<T><<<g1, 256, sm1, s>>>(n, k0, kb, col0, A, piv, ptab, bimg, nblk);
         int rem = n - k0 - kb;
         if (rem > 0) {
             cudaError_t ee;
             if (upd_ev && (ee = cudaEventRecordWithFlags(upd_ev[2 * (k0 / kNB)], s, cudaEventRecordExternal)) != cudaSuccess)
                 return ee;
             if constexpr (sizeof(T) == 8) {
-                // complex64: split operand images of this step, then the tensor-core
-                // update (tcgen05, TF32 split to FP32 accuracy) reading them
-                const int nblk = tcu::update_blocks(n, k0, kb);
-                unsigned char* bimg = img + (size_t)batch * nblk * tcu::kAImg;
-                tcu::operand_image_kernel<<<dim3(nblk, 3, batch), 256, 0, s>>>(
-                    n, k0, kb, nblk, reinterpret_cast<const float2*>(A), img, bimg);
+                // complex64: the A' images of this step (the B' images came with the
+                // block-row solve), then the tensor-core update (tcgen05, TF32 split to
+                // FP32 accuracy) reading them
+                tcu::operand_image_kernel<<<dim3(nblk, 2, batch), 256, 0, s>>>(
+                    n, k0, kb, nblk, reinterpret_cast<const float2*>(A), img);
                 count_launch();
                 const long long units = (long long)batch * nblk;
                 const int grid = (int)std::min<long long>(units, sms);

@@ -16,8 +16,9 @@
 // (relative error ~1e-6 of |L||U|, i.e. FP32 level: the LU stays a
 // preconditioner for the FP64 refinement).
 //
-// Two launches per step.  operand_image_kernel forms, once per 64-row block of
-// L21 and once per 64-column block of U12, the split operands in the exact
+// Per step, the split operands are formed once per 64-row block of L21
+// (operand_image_kernel) and once per 64-column block of U12 (by the LU's
+// block-row solve, which holds U12 in shared memory) in the exact
 // shared-memory image the MMAs read: the canonical K-major layout without
 // swizzling (8-row x 16-byte core matrices), hi then lo (A': 64 KB, B': 32 KB
 // per block).  update_kernel (persistent, one CTA per SM, warp-specialised;
@@ -92,74 +93,49 @@ constexpr uint32_t kBImg = 2 * kBBytes;
 // 64-row / 64-column blocks of the trailing matrix at step k0 (kb = 32)
 __host__ __device__ constexpr int update_blocks(int n, int k0, int kb) { return (n - k0 - kb + kTileC - 1) / kTileC; }
 
-// Operand images of one step.  Grid (nblk, 3, batch), 256 threads: y = 0, 1
-// form the first / second half of the A' image of row block x (real rows
-// 0-63 / 64-127 of the 16-byte core-matrix rows), y = 2 the B' image of column
-// block x.  Image byte 16 u holds real row (or column) r = 8 g + r8 at depths
-// 4 kc .. 4 kc + 3, with (kc, g, r8) the digits of u: u = (kc R/8 + g) 8 + r8,
-// R = 128 rows for A', 64 columns for B' -- the layout whose K-adjacent core
+// A' operand images of one step.  Grid (nblk, 2, batch), 256 threads: y = 0,
+// 1 form the first / second half of the A' image of row block x (real rows
+// 0-63 / 64-127 of the 16-byte core-matrix rows).  Image byte 16 u holds real
+// row r = 8 g + r8 at depths 4 kc .. 4 kc + 3, with (kc, g, r8) the digits of
+// u: u = (kc R/8 + g) 8 + r8, R = 128 rows -- the layout whose K-adjacent core
 // matrices are R/8 x 128 bytes apart and row-adjacent ones 128 bytes apart.
-// Rows and columns beyond n are zero-filled.  Images of mode b, block x start
-// at Aimg + (b nblk + x) kAImg and Bimg + (b nblk + x) kBImg.
+// Rows beyond n are zero-filled.  The image of mode b, block x starts at
+// Aimg + (b nblk + x) kAImg.  (The B' images -- R = 64 columns, depth k < 32
+// Re U[k][j], k >= 32 Im U[k-32][j], u = kc 64 + j -- are written by the LU's
+// block-row solve, which holds U12 in shared memory, at Bimg + (b nblk + x) kBImg.)
 __global__ void __launch_bounds__(256) operand_image_kernel(int n, int k0, int kb, int nblk, const float2* A,
-                                                            unsigned char* Aimg, unsigned char* Bimg) {
+                                                            unsigned char* Aimg) {
     const int b = blockIdx.z, blk = blockIdx.x;
     const float2* a = A + (size_t)b * n * n;
     const int base = k0 + kb + blk * kTileC;
-    if (blockIdx.y < 2) {
-        uint4* hi = reinterpret_cast<uint4*>(Aimg + ((size_t)b * nblk + blk) * kAImg);
-        uint4* lo = hi + kABytes / 16;
-        constexpr int kIt = kABytes / 16 / 2 / 256;   // 4 core-matrix rows per thread
-        float2 v[kIt][4];
+    uint4* hi = reinterpret_cast<uint4*>(Aimg + ((size_t)b * nblk + blk) * kAImg);
+    uint4* lo = hi + kABytes / 16;
+    constexpr int kIt = kABytes / 16 / 2 / 256;   // 4 core-matrix rows per thread
+    float2 v[kIt][4];
 #pragma unroll
-        for (int t = 0; t < kIt; ++t) {
-            // half y covers core-matrix groups g = 8 y .. 8 y + 7 of every kc
-            const int w = threadIdx.x + t * 256;           // 0 .. 1023
-            const int kc = w >> 6, g = ((w >> 3) & 7) + 8 * blockIdx.y, r8 = w & 7;
-            const int i = (g * 8 + r8) >> 1, kk = (kc * 4) & 31;
+    for (int t = 0; t < kIt; ++t) {
+        // half y covers core-matrix groups g = 8 y .. 8 y + 7 of every kc
+        const int w = threadIdx.x + t * 256;           // 0 .. 1023
+        const int kc = w >> 6, g = ((w >> 3) & 7) + 8 * blockIdx.y, r8 = w & 7;
+        const int i = (g * 8 + r8) >> 1, kk = (kc * 4) & 31;
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                v[t][e] = (kk + e < kb && base + i < n) ? a[(size_t)(k0 + kk + e) * n + base + i]
-                                                        : make_float2(0.f, 0.f);
+        for (int e = 0; e < 4; ++e)
+            v[t][e] = (kk + e < kb && base + i < n) ? a[(size_t)(k0 + kk + e) * n + base + i] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < kIt; ++t) {
+        const int w = threadIdx.x + t * 256;
+        const int kc = w >> 6, g = ((w >> 3) & 7) + 8 * blockIdx.y, r8 = w & 7;
+        const int part = r8 & 1, u = (kc * 16 + g) * 8 + r8;
+        // depths 0-31 multiply Re U, 32-63 Im U: row 2i = (Re L, -Im L), row 2i+1 = (Im L, Re L)
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float x = kc < 8 ? (part ? v[t][e].y : v[t][e].x) : (part ? v[t][e].x : -v[t][e].y);
+            split_tf32(x, h[e], l[e]);
         }
-#pragma unroll
-        for (int t = 0; t < kIt; ++t) {
-            const int w = threadIdx.x + t * 256;
-            const int kc = w >> 6, g = ((w >> 3) & 7) + 8 * blockIdx.y, r8 = w & 7;
-            const int part = r8 & 1, u = (kc * 16 + g) * 8 + r8;
-            // depths 0-31 multiply Re U, 32-63 Im U: row 2i = (Re L, -Im L), row 2i+1 = (Im L, Re L)
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float x = kc < 8 ? (part ? v[t][e].y : v[t][e].x) : (part ? v[t][e].x : -v[t][e].y);
-                split_tf32(x, h[e], l[e]);
-            }
-            hi[u] = make_uint4(h[0], h[1], h[2], h[3]);
-            lo[u] = make_uint4(l[0], l[1], l[2], l[3]);
-        }
-    } else {
-        uint4* hi = reinterpret_cast<uint4*>(Bimg + ((size_t)b * nblk + blk) * kBImg);
-        uint4* lo = hi + kBBytes / 16;
-        constexpr int kIt = kBBytes / 16 / 256;       // 4
-        float2 v[kIt][4];
-#pragma unroll
-        for (int t = 0; t < kIt; ++t) {
-            const int u = threadIdx.x + t * 256;
-            const int kc = u >> 6, j = u & 63, kk = (kc * 4) & 31;
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                v[t][e] = (kk + e < kb && base + j < n) ? a[(size_t)(base + j) * n + k0 + kk + e]
-                                                        : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int t = 0; t < kIt; ++t) {
-            const int u = threadIdx.x + t * 256, kc = u >> 6;
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) split_tf32(kc < 8 ? v[t][e].x : v[t][e].y, h[e], l[e]);
-            hi[u] = make_uint4(h[0], h[1], h[2], h[3]);
-            lo[u] = make_uint4(l[0], l[1], l[2], l[3]);
-        }
+        hi[u] = make_uint4(h[0], h[1], h[2], h[3]);
+        lo[u] = make_uint4(l[0], l[1], l[2], l[3]);
     }
 }
 

@@ -786,15 +786,15 @@ def roofline(w, rep, pk, clk, pipes=None):
 
 
 def lu_update_roofline(w, rep, pk):
-    """Roofline of the FP32 LU's tensor-core trailing update (tcu::update_kernel
-    with the tcu::operand_image_kernel launch before it, the largest total time
-    per step: 31 updates at N=512): HBM-bound by construction (a rank-32
-    update does 16 flops per byte of the trailing matrix).  Algorithmic bytes =
-    one read and one write of the complex64 trailing matrix per update,
-    sum_k 2 x 8 B x (n - 32 (k + 1))^2 per mode (the operand images are not
-    counted); time = the device time of both launches of every step, from
-    event pairs recorded around them inside the captured LU graph (report
-    ms_lu_update)."""
+    """Roofline of the FP32 LU's tensor-core trailing update (tcu::update_kernel,
+    the largest total time per step: 31 updates at N=512): HBM-bound by
+    construction (a rank-32 update does 16 flops per byte of the trailing
+    matrix).  Algorithmic bytes = one read and one write of the complex64
+    trailing matrix per update, sum_k 2 x 8 B x (n - 32 (k + 1))^2 per mode
+    (the operand images are not counted); time = the device time of the update
+    launches, from event pairs recorded around them inside the captured LU
+    graph (report ms_lu_update; the A' image kernel runs beside the row-swap
+    kernel on a side stream, outside these pairs)."""
     N, M = w["N"], w["M"]
     n, modes = 2 * N, M // 2
     launches = int(getattr(rep, "lu_update_launches", 0))
@@ -803,9 +803,8 @@ def lu_update_roofline(w, rep, pk):
     hbm = pk.get("hbm_gbs", 6794.1)
     ach = wbytes / (ms / 1e3) / 1e9 if ms > 0 else None
     traffic = profile_traffic("tc_update_kernel_n512_64modes.md", "tc_update.cuh", wbytes)
-    return {"kernel": ("tcu::operand_image_kernel + tcu::update_kernel (rank-32 trailing update of the complex64 LU "
-                       "on tcgen05, TF32 split operands formed once per step; persistent warp-specialised update "
-                       "streaming the tiles by TMA)"),
+    return {"kernel": ("tcu::update_kernel (rank-32 trailing update of the complex64 LU on tcgen05, TF32 split "
+                       "operands formed once per step; persistent warp-specialised update streaming the tiles by TMA)"),
             "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
             "frac": ach / hbm if ach else None, "traffic": traffic, "ms_per_step": ms,
             "launches_per_step": launches, "algorithmic_bytes": wbytes,

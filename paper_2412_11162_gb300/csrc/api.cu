@@ -67,6 +67,8 @@ struct pmlbie_dev_extra {
     // the fork / join events of the system build
     cudaStream_t near_stream = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // the complex64 factorisation's side stream (A' images beside the row swaps)
+    LuSide lu_side;
 };
 
 namespace {
@@ -164,9 +166,13 @@ void free_device(pmlbie_problem* prob) {
     if (ex && ex->near_stream) cudaStreamDestroy(ex->near_stream);
     if (ex && ex->fork) cudaEventDestroy(ex->fork);
     if (ex && ex->join) cudaEventDestroy(ex->join);
+    if (ex && ex->lu_side.stream) cudaStreamDestroy(ex->lu_side.stream);
+    if (ex && ex->lu_side.fork) cudaEventDestroy(ex->lu_side.fork);
+    if (ex && ex->lu_side.join) cudaEventDestroy(ex->lu_side.join);
     if (ex) {
         ex->near_stream = nullptr;
         ex->fork = ex->join = nullptr;
+        ex->lu_side = LuSide();
         for (cudaEvent_t e : ex->upd_ev) cudaEventDestroy(e);
         ex->upd_ev.clear();
         ex->upd_pairs = 0;
@@ -575,10 +581,10 @@ __global__ void wait_probe_kernel(long long iters, int* expired) {
 thread_local int g_lu_graph_replays = 0;
 
 static cudaError_t lu_direct(int precision, int n, int batch, void* A, int* piv, int* info, unsigned char* img,
-                             int2* ptab, cudaStream_t s, cudaEvent_t* upd_ev = nullptr) {
+                             int2* ptab, const LuSide* side, cudaStream_t s, cudaEvent_t* upd_ev = nullptr) {
     return precision == PMLBIE_FP64
-               ? batched_lu<double2>(n, batch, (double2*)A, piv, info, s, nullptr, nullptr, upd_ev)
-               : batched_lu<float2>(n, batch, (float2*)A, piv, info, s, img, ptab, upd_ev);
+               ? batched_lu<double2>(n, batch, (double2*)A, piv, info, s, nullptr, nullptr, nullptr, upd_ev)
+               : batched_lu<float2>(n, batch, (float2*)A, piv, info, s, img, ptab, side, upd_ev);
 }
 
 // 2 x ceil(n / 32) timing events of the trailing updates; the pairs used are
@@ -600,8 +606,13 @@ static int batched_lu_graphed(pmlbie_problem* prob, int precision, int n, int ba
     pmlbie_dev_extra* ex = extra_of(prob);
     LuGraph& g = ex->lu;
     PMLBIE_CUDA_TRY(ensure_update_events(ex, n));
+    if (!ex->lu_side.stream) {
+        PMLBIE_CUDA_TRY(cudaStreamCreateWithFlags(&ex->lu_side.stream, cudaStreamNonBlocking));
+        PMLBIE_CUDA_TRY(cudaEventCreateWithFlags(&ex->lu_side.fork, cudaEventDisableTiming));
+        PMLBIE_CUDA_TRY(cudaEventCreateWithFlags(&ex->lu_side.join, cudaEventDisableTiming));
+    }
     if (g.unavailable) {
-        PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, img, ptab, s, ex->upd_ev.data()));
+        PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, img, ptab, &ex->lu_side, s, ex->upd_ev.data()));
         return PMLBIE_OK;
     }
     if (!(g.exec && g.precision == precision && g.n == n && g.batch == batch && g.A == A && g.piv == piv &&
@@ -615,7 +626,7 @@ static int batched_lu_graphed(pmlbie_problem* prob, int precision, int n, int ba
         cudaError_t e = cudaStreamBeginCapture(ex->capture, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             const cudaError_t el =
-                lu_direct(precision, n, batch, A, piv, info, img, ptab, ex->capture, ex->upd_ev.data());
+                lu_direct(precision, n, batch, A, piv, info, img, ptab, &ex->lu_side, ex->capture, ex->upd_ev.data());
             e = cudaStreamEndCapture(ex->capture, &graph);
             if (el != cudaSuccess) e = el;
         }
@@ -628,7 +639,7 @@ static int batched_lu_graphed(pmlbie_problem* prob, int precision, int n, int ba
             if (g.exec) cudaGraphExecDestroy(g.exec);
             g = LuGraph();
             g.unavailable = true;
-            PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, img, ptab, s, ex->upd_ev.data()));
+            PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, img, ptab, &ex->lu_side, s, ex->upd_ev.data()));
             return PMLBIE_OK;
         }
         g.launches = captured;

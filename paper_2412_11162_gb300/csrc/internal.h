@@ -271,9 +271,9 @@ int peak_probe(int kind, double* out_tflops, cudaStream_t s);
 // Leaves piv[b] as the row permutation of the factorisation: piv[b][i] is the
 // original row that ends in row i (P A = L U with (P x)_i = x_{piv[i]}).
 // upd_ev: optional 2 x ceil(n/32) events recorded around each trailing update
-// (its operand-image and update launches; for its timing; recorded as external
-// events, so that they become event-record nodes when the factorisation is
-// captured in a graph)
+// (its update launch, with its operand-image launch when that is on s; for its
+// timing; recorded as external events, so that they become event-record nodes
+// when the factorisation is captured in a graph)
 // img: for complex64, lu_image_bytes(n, batch) bytes of device scratch (16-byte
 // aligned) holding one step's split operand images; unused for complex128
 // ptab: for complex64, lu_ptab_elems(n, batch) entries receiving each step's
@@ -281,9 +281,16 @@ int peak_probe(int kind, double* out_tflops, cudaStream_t s);
 // each panel only (L keeps the row order of its step), piv keeps LAPACK's
 // interchange indices, and the solves take ptab; unused for complex128 (L in
 // getrf's row order, piv the row permutation)
+// side: for complex64, an auxiliary stream and two events (created outside any
+// capture); each step's A' images (which need only the panel) then run on it
+// beside the row-swap / block-row-solve kernel; null: all on s
+struct LuSide {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
 template <typename T>
 cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s, unsigned char* img,
-                       int2* ptab, cudaEvent_t* upd_ev = nullptr);
+                       int2* ptab, const LuSide* side = nullptr, cudaEvent_t* upd_ev = nullptr);
 size_t lu_ptab_elems(int n, int batch);
 // scratch bytes of the complex64 factorisation's operand images (the first
 // step's 64-row blocks of L21 and 64-column blocks of U12, 96 KB per pair)

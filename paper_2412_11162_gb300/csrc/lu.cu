@@ -1257,7 +1257,7 @@ size_t lu_image_bytes(int n, int batch) {
 
 template <typename T>
 cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t s, unsigned char* img,
-                       int2* ptab, cudaEvent_t* upd_ev) {
+                       int2* ptab, const LuSide* side, cudaEvent_t* upd_ev) {
     cudaError_t pe = lu_prepare<T>();
     if (pe != cudaSuccess) return pe;
     if constexpr (sizeof(T) == 8) {
@@ -1313,21 +1313,40 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
         const int col0 = ptab ? k0 + kb : 0;
         const int nblk = n - k0 - kb > 0 ? tcu::update_blocks(n, k0, kb) : 0;
         unsigned char* bimg = ptab && nblk > 0 ? img + (size_t)batch * nblk * tcu::kAImg : nullptr;
+        // the A' images need only the panel: with a side stream they run beside
+        // the row-swap / block-row-solve kernel
+        const bool aside = ptab && nblk > 0 && side && side->stream;
+        if (aside) {
+            cudaError_t ee;
+            if ((ee = cudaEventRecord(side->fork, s)) != cudaSuccess ||
+                (ee = cudaStreamWaitEvent(side->stream, side->fork, 0)) != cudaSuccess)
+                return ee;
+            tcu::operand_image_kernel<<<dim3(nblk, 2, batch), 256, 0, side->stream>>>(
+                n, k0, kb, nblk, reinterpret_cast<const float2*>(A), img);
+            count_launch();
+            if ((ee = cudaEventRecord(side->join, side->stream)) != cudaSuccess) return ee;
+        }
         dim3 g1((unsigned)std::max(1, (n - col0 + kSwapCols - 1) / kSwapCols), batch);
         size_t sm1 = sizeof(T) * ((size_t)kSwapCols * 2 * kNB + kNB * kNB);
         swap_trsm_kernel<T><<<g1, 256, sm1, s>>>(n, k0, kb, col0, A, piv, ptab, bimg, nblk);
         int rem = n - k0 - kb;
+        if (aside) {
+            cudaError_t ee = cudaStreamWaitEvent(s, side->join, 0);
+            if (ee != cudaSuccess) return ee;
+        }
         if (rem > 0) {
             cudaError_t ee;
             if (upd_ev && (ee = cudaEventRecordWithFlags(upd_ev[2 * (k0 / kNB)], s, cudaEventRecordExternal)) != cudaSuccess)
                 return ee;
             if constexpr (sizeof(T) == 8) {
-                // complex64: the A' images of this step (the B' images came with the
-                // block-row solve), then the tensor-core update (tcgen05, TF32 split to
-                // FP32 accuracy) reading them
-                tcu::operand_image_kernel<<<dim3(nblk, 2, batch), 256, 0, s>>>(
-                    n, k0, kb, nblk, reinterpret_cast<const float2*>(A), img);
-                count_launch();
+                // complex64: the A' images of this step (unless on the side stream;
+                // the B' images came with the block-row solve), then the tensor-core
+                // update (tcgen05, TF32 split to FP32 accuracy) reading them
+                if (!aside) {
+                    tcu::operand_image_kernel<<<dim3(nblk, 2, batch), 256, 0, s>>>(
+                        n, k0, kb, nblk, reinterpret_cast<const float2*>(A), img);
+                    count_launch();
+                }
                 const long long units = (long long)batch * nblk;
                 const int grid = (int)std::min<long long>(units, sms);
                 tcu::update_kernel<<<grid, tcu::kPipeThreads, tcu::kPipeSmem, s>>>(tmA, k0, kb, nblk, batch, img,
@@ -1382,9 +1401,9 @@ cudaError_t batched_lu_solve(int n, int batch, int nrhs, const TF* LU, const int
 template cudaError_t lu_prepare<double2>();
 template cudaError_t lu_prepare<float2>();
 template cudaError_t batched_lu<double2>(int, int, double2*, int*, int*, cudaStream_t, unsigned char*, int2*,
-                                          cudaEvent_t*);
+                                          const LuSide*, cudaEvent_t*);
 template cudaError_t batched_lu<float2>(int, int, float2*, int*, int*, cudaStream_t, unsigned char*, int2*,
-                                         cudaEvent_t*);
+                                         const LuSide*, cudaEvent_t*);
 template cudaError_t batched_lu_solve<double2, double2>(int, int, int, const double2*, const int*, double2*,
                                                         cudaStream_t, const int*, const double2*, const int2*);
 template cudaError_t batched_lu_solve<float2, float2>(int, int, int, const float2*, const int*, float2*,

@@ -45,10 +45,21 @@ std::vector<double2> to_d2(const std::vector<cd>& v) {
 // which the kernels receive by value)
 // The batched LU of one workspace (sizes and buffers fixed) as a CUDA graph:
 // its 3 n / 32 + 1 dependent launches are replayed with one graph launch.
-struct LuGraph {
-    cudaGraphExec_t exec = nullptr;
+// The factorisation's sizes and buffers: a captured graph serves one key.
+struct LuKey {
     int precision = -1, n = 0, batch = 0;
     const void *A = nullptr, *piv = nullptr, *info = nullptr, *img = nullptr, *ptab = nullptr;
+    bool operator==(const LuKey& o) const {
+        return precision == o.precision && n == o.n && batch == o.batch && A == o.A && piv == o.piv &&
+               info == o.info && img == o.img && ptab == o.ptab;
+    }
+};
+
+struct LuGraph {
+    cudaGraphExec_t exec = nullptr;
+    LuKey key;                  // of exec
+    LuKey pending;              // of the last factorisation run directly
+    bool has_pending = false;
     long launches = 0;          // kernels in the graph
     bool unavailable = false;   // capture failed once: launch directly
 };
@@ -615,8 +626,24 @@ static int batched_lu_graphed(pmlbie_problem* prob, int precision, int n, int ba
         PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, img, ptab, &ex->lu_side, s, ex->upd_ev.data()));
         return PMLBIE_OK;
     }
-    if (!(g.exec && g.precision == precision && g.n == n && g.batch == batch && g.A == A && g.piv == piv &&
-          g.info == info && g.img == img && g.ptab == ptab)) {
+    LuKey key;
+    key.precision = precision;
+    key.n = n;
+    key.batch = batch;
+    key.A = A;
+    key.piv = piv;
+    key.info = info;
+    key.img = img;
+    key.ptab = ptab;
+    if (!(g.exec && g.key == key)) {
+        // the first factorisation with these buffers runs directly (a one-off
+        // solve does not pay for a capture); the second one is captured
+        if (!(g.has_pending && g.pending == key)) {
+            g.pending = key;
+            g.has_pending = true;
+            PMLBIE_CUDA_TRY(lu_direct(precision, n, batch, A, piv, info, img, ptab, &ex->lu_side, s, ex->upd_ev.data()));
+            return PMLBIE_OK;
+        }
         if (g.exec) cudaGraphExecDestroy(g.exec);
         g = LuGraph();
         if (!ex->capture) PMLBIE_CUDA_TRY(cudaStreamCreateWithFlags(&ex->capture, cudaStreamNonBlocking));
@@ -643,14 +670,7 @@ static int batched_lu_graphed(pmlbie_problem* prob, int precision, int n, int ba
             return PMLBIE_OK;
         }
         g.launches = captured;
-        g.precision = precision;
-        g.n = n;
-        g.batch = batch;
-        g.A = A;
-        g.piv = piv;
-        g.info = info;
-        g.img = img;
-        g.ptab = ptab;
+        g.key = key;
     }
     PMLBIE_CUDA_TRY(cudaGraphLaunch(g.exec, s));
     count_launch(g.launches);

@@ -1248,6 +1248,17 @@ cudaError_t trailing_tensor_map(CUtensorMap* tm, float2* A, int n, int batch) {
 
 }  // namespace
 
+// An update-timing event: an external event (an event-record node) when s is
+// being captured into a graph, a plain record otherwise (the external flag is
+// not valid outside a capture)
+static cudaError_t record_update_event(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(s, &st);
+    if (ce != cudaSuccess) return ce;
+    return st == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(e, s);
+}
+
 size_t lu_ptab_elems(int n, int batch) { return (size_t)batch * ((n + kNB - 1) / kNB) * 2 * kNB; }
 
 size_t lu_image_bytes(int n, int batch) {
@@ -1336,8 +1347,7 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
         }
         if (rem > 0) {
             cudaError_t ee;
-            if (upd_ev && (ee = cudaEventRecordWithFlags(upd_ev[2 * (k0 / kNB)], s, cudaEventRecordExternal)) != cudaSuccess)
-                return ee;
+            if (upd_ev && (ee = record_update_event(upd_ev[2 * (k0 / kNB)], s)) != cudaSuccess) return ee;
             if constexpr (sizeof(T) == 8) {
                 // complex64: the A' images of this step (unless on the side stream;
                 // the B' images came with the block-row solve), then the tensor-core
@@ -1357,9 +1367,7 @@ cudaError_t batched_lu(int n, int batch, T* A, int* piv, int* info, cudaStream_t
                 gemm_update_kernel<T><<<g2, 256, 0, s>>>(n, k0, kb, A);
             }
             count_launch();
-            if (upd_ev && (ee = cudaEventRecordWithFlags(upd_ev[2 * (k0 / kNB) + 1], s, cudaEventRecordExternal)) !=
-                              cudaSuccess)
-                return ee;
+            if (upd_ev && (ee = record_update_event(upd_ev[2 * (k0 / kNB) + 1], s)) != cudaSuccess) return ee;
         }
     }
     if (!ptab) {

@@ -9,9 +9,14 @@
 // panel), row swaps + unit-lower triangular solve for the block row, and a
 // tiled GEMM update of the trailing matrix (complex128: FP64 CUDA cores;
 // complex64: tcgen05 tensor cores on split operand images formed once per
-// step, tc_update.cuh).  Matrices are
-// column-major, A[b][col][row], leading dimension n.  info[b] > 0 marks the
-// first zero pivot, info[b] = -1 a tensor-core update that did not complete.
+// step, tc_update.cuh).  complex128 leaves LAPACK getrf's row order (every
+// column swapped) and a row permutation in piv; complex64 swaps only the
+// columns right of each panel, so L's column blocks keep their step's row
+// order, and the solves apply each step's interchanges (the per-step slot
+// mapping in ptab) when they reach the step's block -- the same forward
+// substitution.  Matrices are column-major, A[b][col][row], leading
+// dimension n.  info[b] > 0 marks the first zero pivot, info[b] = -1 a
+// tensor-core update that did not complete.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>

@@ -308,7 +308,11 @@ int  pmlbie_modal_kernels_noalloc(pmlbie_problem* prob, int mode_lo, int mode_hi
  * same LU.  Errors: EINVAL, ENOMEM, ECUDA, ESINGULAR, ENOCONVERGE (mixed: a
  * mode missed both tolerances after the iteration caps; outputs still
  * written), ETIMEOUT (a bounded wait of the tensor-core LU update expired),
- * ENAN (NaN or Inf in an output; outputs written). */
+ * ENAN (NaN or Inf in an output; outputs written).  Inside the call some
+ * kernels run on the problem's own streams (the close-pair kernels beside
+ * the far-pair kernel; in the mixed path the factorisation beside the
+ * right-hand sides), forked from `stream` after the work already queued on
+ * it and joined back into it; one problem serves one call at a time. */
 int  pmlbie_solve(pmlbie_problem* prob, int precision, int n_rhs, const double* polar,
                   void* dev_u1, void* dev_phi1, void* dev_u2, void* dev_phi2,
                   void* stream, pmlbie_report* rep);

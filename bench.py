@@ -431,7 +431,8 @@ def extra_workloads(stream, pipes=None):
     tf32 = pipes.get("tf32_tcgen05_tflops") if pipes else None
     hbm = peaks().get("hbm_gbs", 6794.1)
     # the far kernel alone (autotuning launch, per chunk); r.ms_far is its span beside the close pairs
-    far_ms = r.ms_far_alone * max(1, r.chunks) if r.ms_far_alone > 0 else r.ms_far
+    far_alone = float(getattr(r, "ms_far_alone", 0.0))
+    far_ms = far_alone * max(1, r.chunks) if far_alone > 0 else r.ms_far
     out["n1024_m512"] = {"workload": "two-layer bump, N=1024 M=512 (256 modes), k1=10pi k2=15pi, mixed",
                          "ms_per_problem": ms, "entries_per_s": entries_per_problem(w) / (ms / 1e3),
                          "lu_tflops": lu_flops / (r.ms_lu / 1e3) / 1e12,
@@ -843,7 +844,8 @@ def stage_rooflines(w, rep, pk, pipes=None):
     s_lu = rep.ms_lu / 1e3
     wr = 4.0 * N * N * modes * 16
     # the far kernel alone (its autotuning launch); rep.ms_far is its span beside the close pairs
-    far_ms = rep.ms_far_alone * max(1, rep.chunks) if rep.ms_far_alone > 0 else rep.ms_far
+    alone = float(getattr(rep, "ms_far_alone", 0.0))
+    far_ms = alone * max(1, getattr(rep, "chunks", 1)) if alone > 0 else rep.ms_far
     s_far = far_ms / 1e3
     return {
         "lu_fp32": {"bound": "hbm", "ms": rep.ms_lu, "flops": lu_flops, "tflops": lu_flops / s_lu / 1e12,

@@ -776,11 +776,12 @@ int build_tables(pmlbie_problem* prob) {
 
     // pair classes and close-pair table
     const double eta = prob->eta_split;
-    auto make_pair = [&](int l, const CP& src, NearPair& np) -> bool {
-        const CP& tg = npts[l];
-        double dr, dz;
+    auto pair_sep = [&](const CP& tg, const CP& src, double& dr, double& dz, double& dI) {
         separation(tg, src, dr, dz);
-        double dI = (tg.rho > P.a1 || src.rho > P.a1) ? pml.delta(src.rho, dr, tg.I, src.I) : 0.0;
+        dI = (tg.rho > P.a1 || src.rho > P.a1) ? pml.delta(src.rho, dr, tg.I, src.I) : 0.0;
+    };
+    auto make_pair_sep = [&](int l, const CP& src, NearPair& np, double dr, double dz, double dI) -> bool {
+        const CP& tg = npts[l];
         cd drt(dr, dI);                   // rho~ - rho~'
         cd d2 = drt * drt + dz * dz;
         cd rr = tg.rt * src.rt;
@@ -797,6 +798,25 @@ int build_tables(pmlbie_problem* prob) {
         np.tgt = l;
         np.flags = (!P.subst_off && (tg.I > 0 || src.I > 0)) ? kFlagSubst : 0;
         return re_sqrt < eta;
+    };
+    auto make_pair = [&](int l, const CP& src, NearPair& np) -> bool {
+        double dr, dz, dI;
+        pair_sep(npts[l], src, dr, dz, dI);
+        return make_pair_sep(l, src, np, dr, dz, dI);
+    };
+    // The same criterion in real arithmetic (x = d~^2 / (rho~ rho~'): |x| and
+    // Re x without the complex division), used only to skip the pairs whose
+    // value exceeds the split threshold by 1 % -- far beyond any rounding
+    // difference, so every pair near the threshold still takes make_pair's test.
+    auto clearly_far = [&](int l, const CP& src, double dr, double dz, double dI) -> bool {
+        const CP& tg = npts[l];
+        const double a = dr * dr - dI * dI + dz * dz, b = 2.0 * dr * dI;          // d~^2
+        const std::complex<double> rr = tg.rt * src.rt;
+        const double c = rr.real(), d = rr.imag(), nr2 = c * c + d * d;
+        if (!(nr2 > 0.0)) return false;
+        const double re_x = (a * c + b * d) / nr2, abs_x = std::sqrt((a * a + b * b) / nr2);
+        const double v2 = 0.5 * (abs_x + re_x);                                   // (Re sqrt x)^2
+        return std::isfinite(v2) && v2 > 1.0201 * eta * eta;
     };
     H.cls.assign((size_t)N * N, kFar);
     H.near.clear();
@@ -815,8 +835,11 @@ int build_tables(pmlbie_problem* prob) {
                             H.cls[(size_t)l * N + m] = kSkip;
                             continue;
                         }
+                        double dr, dz, dI;
+                        pair_sep(npts[l], npts[m], dr, dz, dI);
+                        if (clearly_far(l, npts[m], dr, dz, dI)) continue;
                         NearPair np;
-                        if (make_pair(l, npts[m], np)) {
+                        if (make_pair_sep(l, npts[m], np, dr, dz, dI)) {
                             np.src = m;
                             H.cls[(size_t)l * N + m] = kNear;
                             part[t].push_back(np);
@@ -872,25 +895,31 @@ int build_tables(pmlbie_problem* prob) {
         // length (upward: M steps; Miller: M + 20 / Re(eta)): a warp's FP64
         // instruction costs the same issue slot whatever its active lanes.
         const int np = (int)H.near.size();
+        auto cx_zero = [](double2 v) { return v.y == 0.0; };
+        // keys in pair order (-1: not a leader), computed in parallel
+        std::vector<long long> kp(np, -1);
+        parallel_rows(np, [&](int lo, int hi) {
+            for (int p = lo; p < hi; ++p) {
+                const NearPair& q = H.near[p];
+                if (q.flags & kFlagFar) continue;
+                if (q.mirror >= 0 && q.mirror < p) continue;
+                bool real = cx_zero(q.d2) && cx_zero(q.rr) && cx_zero(q.rho_t) && cx_zero(q.rho_s) &&
+                            cx_zero(q.drt) && cx_zero(q.nuc_r) && cx_zero(q.nuc_z);
+                if (real && q.mirror >= 0)
+                    real = cx_zero(H.near[q.mirror].nuc_r) && cx_zero(H.near[q.mirror].nuc_z);
+                // Re acosh(chi), chi - 1 = d~^2 / (2 rho~ rho~')
+                const std::complex<double> d2(q.d2.x, q.d2.y), rr(q.rr.x, q.rr.y);
+                const std::complex<double> chim1 = d2 / (2.0 * rr), chi = 1.0 + chim1;
+                const double reeta = std::fabs(std::log(chi + std::sqrt(chim1) * std::sqrt(chi + 1.0)).real());
+                long long steps = P.M;
+                if (!(reeta * P.M < kRecUpward) && reeta > 0.0) steps += (long long)std::ceil(20.0 / reeta);
+                kp[p] = (real ? 0LL : (1LL << 40)) + steps;
+            }
+        });
         std::vector<std::pair<long long, int>> key;
         key.reserve(np);
-        auto cx_zero = [](double2 v) { return v.y == 0.0; };
-        for (int p = 0; p < np; ++p) {
-            const NearPair& q = H.near[p];
-            if (q.flags & kFlagFar) continue;
-            if (q.mirror >= 0 && q.mirror < p) continue;
-            bool real = cx_zero(q.d2) && cx_zero(q.rr) && cx_zero(q.rho_t) && cx_zero(q.rho_s) && cx_zero(q.drt) &&
-                        cx_zero(q.nuc_r) && cx_zero(q.nuc_z);
-            if (real && q.mirror >= 0)
-                real = cx_zero(H.near[q.mirror].nuc_r) && cx_zero(H.near[q.mirror].nuc_z);
-            // Re acosh(chi), chi - 1 = d~^2 / (2 rho~ rho~')
-            const std::complex<double> d2(q.d2.x, q.d2.y), rr(q.rr.x, q.rr.y);
-            const std::complex<double> chim1 = d2 / (2.0 * rr), chi = 1.0 + chim1;
-            const double reeta = std::fabs(std::log(chi + std::sqrt(chim1) * std::sqrt(chi + 1.0)).real());
-            long long steps = P.M;
-            if (!(reeta * P.M < kRecUpward) && reeta > 0.0) steps += (long long)std::ceil(20.0 / reeta);
-            key.push_back({(real ? 0LL : (1LL << 40)) + steps, p});
-        }
+        for (int p = 0; p < np; ++p)
+            if (kp[p] >= 0) key.push_back({kp[p], p});
         std::stable_sort(key.begin(), key.end(),
                          [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) {
                              return a.first < b.first;
